@@ -1,0 +1,502 @@
+/*
+ * SubQuad all-candidates affinity stage -- the ORACLE.
+ *
+ * This file is test infrastructure.  It is a plain, slow, single-threaded C
+ * restatement of what the method computes, written from the paper and the
+ * readings listed with each function, in FP64 wherever the quantity is
+ * floating point.  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg load it; the library path never does, and it shares no
+ * code, header, table or helper with the CUDA sources.
+ *
+ * Notation: n sequences s_i of length L_i over the 20 amino acids (codes 0..19
+ * in the order ACDEFGHIKLMNPQRSTVWY), H hash functions grouped into B bands of
+ * R rows, candidate set C of unordered pairs (i < j).
+ *
+ * Parity status: every function below is pinned by tests against something
+ * other than itself (hand-worked alignments, brute-force enumeration,
+ * textbook reductions, library routines, statistical bounds, finite
+ * differences); the pin is named beside each function.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define P31 2147483647ULL /* 2^31 - 1 */
+
+/* ------------------------------------------------------------------------- */
+/* BLOSUM62 (Henikoff & Henikoff 1992), transcribed in the customary NCBI row
+ * order ARNDCQEGHILKMFPSTWYV and re-indexed to the alphabetical code order.
+ * Pins: symmetry, diagonal strict row maximum, spot entries, and a
+ * cell-by-cell comparison with the library's separately typed table.        */
+/* ------------------------------------------------------------------------- */
+static const char NCBI_ORDER[21] = "ARNDCQEGHILKMFPSTWYV";
+static const char CODE_ORDER[21] = "ACDEFGHIKLMNPQRSTVWY";
+static const int BLOSUM62_NCBI[20][20] = {
+    /*        A   R   N   D   C   Q   E   G   H   I   L   K   M   F   P   S   T   W   Y   V */
+    /* A */ { 4, -1, -2, -2,  0, -1, -1,  0, -2, -1, -1, -1, -1, -2, -1,  1,  0, -3, -2,  0},
+    /* R */ {-1,  5,  0, -2, -3,  1,  0, -2,  0, -3, -2,  2, -1, -3, -2, -1, -1, -3, -2, -3},
+    /* N */ {-2,  0,  6,  1, -3,  0,  0,  0,  1, -3, -3,  0, -2, -3, -2,  1,  0, -4, -2, -3},
+    /* D */ {-2, -2,  1,  6, -3,  0,  2, -1, -1, -3, -4, -1, -3, -3, -1,  0, -1, -4, -3, -3},
+    /* C */ { 0, -3, -3, -3,  9, -3, -4, -3, -3, -1, -1, -3, -1, -2, -3, -1, -1, -2, -2, -1},
+    /* Q */ {-1,  1,  0,  0, -3,  5,  2, -2,  0, -3, -2,  1,  0, -3, -1,  0, -1, -2, -1, -2},
+    /* E */ {-1,  0,  0,  2, -4,  2,  5, -2,  0, -3, -3,  1, -2, -3, -1,  0, -1, -3, -2, -2},
+    /* G */ { 0, -2,  0, -1, -3, -2, -2,  6, -2, -4, -4, -2, -3, -3, -2,  0, -2, -2, -3, -3},
+    /* H */ {-2,  0,  1, -1, -3,  0,  0, -2,  8, -3, -3, -1, -2, -1, -2, -1, -2, -2,  2, -3},
+    /* I */ {-1, -3, -3, -3, -1, -3, -3, -4, -3,  4,  2, -3,  1,  0, -3, -2, -1, -3, -1,  3},
+    /* L */ {-1, -2, -3, -4, -1, -2, -3, -4, -3,  2,  4, -2,  2,  0, -3, -2, -1, -2, -1,  1},
+    /* K */ {-1,  2,  0, -1, -3,  1,  1, -2, -1, -3, -2,  5, -1, -3, -1,  0, -1, -3, -2, -2},
+    /* M */ {-1, -1, -2, -3, -1,  0, -2, -3, -2,  1,  2, -1,  5,  0, -2, -1, -1, -1, -1,  1},
+    /* F */ {-2, -3, -3, -3, -2, -3, -3, -3, -1,  0,  0, -3,  0,  6, -4, -2, -2,  1,  3, -1},
+    /* P */ {-1, -2, -2, -1, -3, -1, -1, -2, -2, -3, -3, -1, -2, -4,  7, -1, -1, -4, -3, -2},
+    /* S */ { 1, -1,  1,  0, -1,  0,  0,  0, -1, -2, -2,  0, -1, -2, -1,  4,  1, -3, -2, -2},
+    /* T */ { 0, -1,  0, -1, -1, -1, -1, -2, -2, -1, -1, -1, -1, -2, -1,  1,  5, -2, -2,  0},
+    /* W */ {-3, -3, -4, -4, -2, -2, -3, -2, -2, -3, -2, -3, -1,  1, -4, -3, -2, 11,  2, -3},
+    /* Y */ {-2, -2, -2, -3, -2, -1, -2, -3,  2, -1, -1, -2, -1,  3, -3, -2, -2,  2,  7, -1},
+    /* V */ { 0, -3, -3, -3, -1, -2, -2, -3, -3,  3,  1, -2,  1, -1, -2, -2,  0, -3, -1,  4},
+};
+
+static int ncbi_index(char letter)
+{
+    for (int r = 0; r < 20; ++r)
+        if (NCBI_ORDER[r] == letter) return r;
+    return -1;
+}
+
+/* out[20*a + b] = BLOSUM62(letter a, letter b), a, b in code order. */
+void oracle_blosum62(int32_t *out)
+{
+    for (int a = 0; a < 20; ++a)
+        for (int b = 0; b < 20; ++b)
+            out[20 * a + b] = BLOSUM62_NCBI[ncbi_index(CODE_ORDER[a])][ncbi_index(CODE_ORDER[b])];
+}
+
+/* ------------------------------------------------------------------------- */
+/* MinHash signatures (Algorithm 1, preprocessing; sketch size M = H; the
+ * sampling-error discussion of the appendix "Sampling Error Bounds").
+ * Readings: the set of a sequence is its set of overlapping k-mers; a k-mer is
+ * the base-20 integer x = sum_m code(s[p+m]) * 20^(k-1-m); hash t is
+ * h_t(x) = (a_t x + b_t) mod (2^31 - 1); sig[i][t] = min over the k-mers of s_i.
+ * Pins: brute-force min over k-mers in a test; collision rate against exact
+ * k-mer Jaccard within the binomial error of the appendix bound.             */
+/* ------------------------------------------------------------------------- */
+uint64_t oracle_kmer_code(const uint8_t *s, int k)
+{
+    uint64_t x = 0;
+    for (int m = 0; m < k; ++m) x = x * 20u + s[m];
+    return x;
+}
+
+void oracle_sign(const uint8_t *codes, int code_stride, const uint8_t *lens, int64_t n, int k, int H,
+                 const uint32_t *a, const uint32_t *b, uint32_t *sig /* [n][H] */)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const uint8_t *s = codes + i * (int64_t)code_stride;
+        int L = lens[i];
+        for (int t = 0; t < H; ++t) {
+            uint64_t best = UINT64_MAX;
+            for (int p = 0; p + k <= L; ++p) {
+                uint64_t x = oracle_kmer_code(s + p, k);
+                uint64_t h = ((uint64_t)a[t] * x + (uint64_t)b[t]) % P31;
+                if (h < best) best = h;
+            }
+            sig[i * H + t] = (uint32_t)best; /* L >= k is a precondition */
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* LSH banding and candidate list CAND (Algorithm 1, preprocessing; the index
+ * of "Optimized Indexing Mechanism"; the candidate set C of the complexity
+ * appendix).  Readings: band b is hash rows b*R .. b*R+R-1; its key is the
+ * exact R-tuple; a bucket is the set of sequences with one key; its members,
+ * ranked by ascending id, fall into chunks of `cap` consecutive ranks
+ * (cap <= 0: one chunk); C is the set of pairs i < j that share a chunk in at
+ * least one band.  Pin: brute-force pair test of this definition in a test.  */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t key[8];
+    uint32_t id;
+} band_rec;
+
+static int g_rows; /* qsort has no context argument; single-threaded by design */
+
+static int cmp_band_rec(const void *pa, const void *pb)
+{
+    const band_rec *x = (const band_rec *)pa, *y = (const band_rec *)pb;
+    for (int r = 0; r < g_rows; ++r) {
+        if (x->key[r] < y->key[r]) return -1;
+        if (x->key[r] > y->key[r]) return 1;
+    }
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+static int cmp_u64(const void *pa, const void *pb)
+{
+    uint64_t x = *(const uint64_t *)pa, y = *(const uint64_t *)pb;
+    return (x > y) - (x < y);
+}
+
+typedef struct {
+    uint64_t *v;
+    int64_t len, cap;
+} u64vec;
+
+static int u64vec_push(u64vec *vec, uint64_t x)
+{
+    if (vec->len == vec->cap) {
+        int64_t nc = vec->cap ? 2 * vec->cap : 1024;
+        uint64_t *nv = (uint64_t *)realloc(vec->v, (size_t)nc * sizeof(uint64_t));
+        if (!nv) return -1;
+        vec->v = nv;
+        vec->cap = nc;
+    }
+    vec->v[vec->len++] = x;
+    return 0;
+}
+
+/* Returns |C| (or -1 on allocation failure); writes min(|C|, out_capacity)
+ * pairs, lexicographically sorted, as out[2q] = i, out[2q+1] = j. */
+int64_t oracle_candidates(const uint32_t *sig /* [n][H] */, int64_t n, int H, int bands, int rows,
+                          int cap, uint32_t *out, int64_t out_capacity)
+{
+    if (rows < 1 || rows > 8 || bands * rows > H) return -1;
+    band_rec *recs = (band_rec *)malloc((size_t)(n > 0 ? n : 1) * sizeof(band_rec));
+    u64vec all = {0, 0, 0};
+    if (!recs) return -1;
+    g_rows = rows;
+    for (int b = 0; b < bands; ++b) {
+        for (int64_t i = 0; i < n; ++i) {
+            memset(recs[i].key, 0, sizeof(recs[i].key));
+            for (int r = 0; r < rows; ++r) recs[i].key[r] = sig[i * H + b * rows + r];
+            recs[i].id = (uint32_t)i;
+        }
+        qsort(recs, (size_t)n, sizeof(band_rec), cmp_band_rec);
+        int64_t s = 0;
+        while (s < n) {
+            int64_t e = s + 1;
+            while (e < n && memcmp(recs[e].key, recs[s].key, sizeof(uint32_t) * (size_t)rows) == 0) ++e;
+            for (int64_t u = s; u < e; ++u)
+                for (int64_t v = u + 1; v < e; ++v) {
+                    int same_chunk = cap <= 0 || ((u - s) / cap == (v - s) / cap);
+                    if (same_chunk &&
+                        u64vec_push(&all, ((uint64_t)recs[u].id << 32) | recs[v].id) != 0) {
+                        free(recs);
+                        free(all.v);
+                        return -1;
+                    }
+                }
+            s = e;
+        }
+    }
+    free(recs);
+    if (all.len > 0) qsort(all.v, (size_t)all.len, sizeof(uint64_t), cmp_u64);
+    int64_t count = 0;
+    for (int64_t q = 0; q < all.len; ++q) {
+        if (q > 0 && all.v[q] == all.v[q - 1]) continue;
+        if (count < out_capacity) {
+            out[2 * count] = (uint32_t)(all.v[q] >> 32);
+            out[2 * count + 1] = (uint32_t)(all.v[q] & 0xffffffffu);
+        }
+        ++count;
+    }
+    free(all.v);
+    return count;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Affine-gap local alignment (Smith-Waterman with Gotoh's three matrices) --
+ * the alignment channel a^(1) of Algorithm 1's affinity computation.
+ * Reading: a gap of length l costs o + (l-1) e.  For i = 1..La, j = 1..Lb:
+ *   E(i,j) = max(E(i,j-1) - e, H(i,j-1) - o)          gap in a (b_j unpaired)
+ *   F(i,j) = max(F(i-1,j) - e, H(i-1,j) - o)          gap in b (a_i unpaired)
+ *   H(i,j) = max(0, H(i-1,j-1) + M[a_i][b_j], E(i,j), F(i,j))
+ * with H(0,.) = H(.,0) = 0 and E(.,0) = F(0,.) = -2^20; score = max H.
+ * Pins: hand-worked alignments (tests/golden), exhaustive enumeration of all
+ * local alignments of short strings, Kadane reduction (infinite gaps),
+ * longest-common-substring reduction (identity matrix), self-score identity. */
+/* ------------------------------------------------------------------------- */
+#define SW_NEG (-(1 << 20))
+#define SW_MAXL 64
+
+int32_t oracle_sw(const uint8_t *a, int La, const uint8_t *b, int Lb, const int32_t *M /* [20][20] */,
+                  int o, int e)
+{
+    static int32_t Hm[SW_MAXL + 1][SW_MAXL + 1], Em[SW_MAXL + 1][SW_MAXL + 1], Fm[SW_MAXL + 1][SW_MAXL + 1];
+    if (La > SW_MAXL || Lb > SW_MAXL || La < 0 || Lb < 0) return -1;
+    int32_t best = 0;
+    for (int i = 0; i <= La; ++i) {
+        Hm[i][0] = 0;
+        Em[i][0] = SW_NEG;
+    }
+    for (int j = 0; j <= Lb; ++j) {
+        Hm[0][j] = 0;
+        Fm[0][j] = SW_NEG;
+    }
+    for (int i = 1; i <= La; ++i)
+        for (int j = 1; j <= Lb; ++j) {
+            int32_t ee = Em[i][j - 1] - e, eo = Hm[i][j - 1] - o;
+            int32_t ff = Fm[i - 1][j] - e, fo = Hm[i - 1][j] - o;
+            Em[i][j] = ee > eo ? ee : eo;
+            Fm[i][j] = ff > fo ? ff : fo;
+            int32_t h = Hm[i - 1][j - 1] + M[20 * a[i - 1] + b[j - 1]];
+            if (Em[i][j] > h) h = Em[i][j];
+            if (Fm[i][j] > h) h = Fm[i][j];
+            if (h < 0) h = 0;
+            Hm[i][j] = h;
+            if (h > best) best = h;
+        }
+    return best;
+}
+
+/* scores[p] = S(s_pairs[2p], s_pairs[2p+1]) */
+void oracle_sw_pairs(const uint8_t *codes, int code_stride, const uint8_t *lens, const uint32_t *pairs,
+                     int64_t m, const int32_t *M, int o, int e, int32_t *scores)
+{
+    for (int64_t p = 0; p < m; ++p) {
+        uint32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+        scores[p] = oracle_sw(codes + (int64_t)i * code_stride, lens[i], codes + (int64_t)j * code_stride,
+                              lens[j], M, o, e);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Per-pair gated fusion (Eq. alpha, Eq. wm, Eq. afused) with M = 2 channels:
+ * a^(1) = s = S_ij / sqrt(S_ii S_jj) (normalised alignment, reading: geometric
+ * mean of self-scores), a^(2) = c' = (1 + c)/2 with c the embedding cosine
+ * (reading: shifted to [0,1]).  Channel scores are g^(1) = MLP(f), g^(2) = 0,
+ * with f = [s, c, |L_i - L_j|] and MLP = w2 . ReLU(W1 f + b1) + b2, so Eq. wm
+ * gives w^(1) = alpha = sigma(g) (Eq. alpha's sigmoid) and
+ * fused = alpha s + (1 - alpha) c'.
+ * params (float32, converted exactly): W1 [h][3] row-major, b1 [h], w2 [h], b2.
+ * Pins: two-way softmax from a library routine, cosine from a library
+ * routine, limits alpha -> 0 / 1, range [0, 1].                              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double s, c, delta, alpha, g, fused, ni, nj;
+} fuse_state;
+
+static void fuse_pair(const uint32_t *pairs, int64_t p, const int32_t *sw, const int32_t *self,
+                      const uint8_t *lens, const float *emb, int d, const float *params, int h,
+                      double *z /* [h] */, fuse_state *st)
+{
+    uint32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+    const float *ei = emb + (int64_t)i * d, *ej = emb + (int64_t)j * d;
+    double prod = (double)self[i] * (double)self[j];
+    st->s = prod > 0.0 ? (double)sw[p] / sqrt(prod) : 0.0;
+    double dot = 0.0, sii = 0.0, sjj = 0.0;
+    for (int k = 0; k < d; ++k) {
+        dot += (double)ei[k] * (double)ej[k];
+        sii += (double)ei[k] * (double)ei[k];
+        sjj += (double)ej[k] * (double)ej[k];
+    }
+    st->ni = sqrt(sii);
+    st->nj = sqrt(sjj);
+    st->c = (st->ni > 0.0 && st->nj > 0.0) ? dot / (st->ni * st->nj) : 0.0;
+    st->delta = fabs((double)lens[i] - (double)lens[j]);
+    const float *W1 = params, *b1 = params + 3 * h, *w2 = params + 4 * h, *b2 = params + 5 * h;
+    double g = (double)b2[0];
+    for (int k = 0; k < h; ++k) {
+        z[k] = (double)W1[3 * k] * st->s + (double)W1[3 * k + 1] * st->c + (double)W1[3 * k + 2] * st->delta +
+               (double)b1[k];
+        g += (double)w2[k] * (z[k] > 0.0 ? z[k] : 0.0);
+    }
+    st->g = g;
+    st->alpha = 1.0 / (1.0 + exp(-g));
+    st->fused = st->alpha * st->s + (1.0 - st->alpha) * 0.5 * (1.0 + st->c);
+}
+
+int oracle_fuse_forward(const uint32_t *pairs, int64_t m, const int32_t *sw, const int32_t *self,
+                        const uint8_t *lens, const float *emb, int d, const float *params, int h,
+                        double *fused, double *alpha /* nullable */, double *snorm /* nullable */,
+                        double *cosine /* nullable */)
+{
+    double *z = (double *)malloc((size_t)(h > 0 ? h : 1) * sizeof(double));
+    if (!z) return -1;
+    for (int64_t p = 0; p < m; ++p) {
+        fuse_state st;
+        fuse_pair(pairs, p, sw, self, lens, emb, d, params, h, z, &st);
+        fused[p] = st.fused;
+        if (alpha) alpha[p] = st.alpha;
+        if (snorm) snorm[p] = st.s;
+        if (cosine) cosine[p] = st.c;
+    }
+    free(z);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of the fusion (gate training, Eq. fine_tune's meta-network
+ * parameters).  Closed-form chain rule through fused, alpha, the MLP and the
+ * cosine; the alignment channel is integer and not differentiated; the ReLU
+ * subgradient at 0 is 0.  grad_params accumulates (caller zeroes); grad_emb
+ * (nullable) accumulates dL/de_i and dL/de_j.
+ * Pin: central finite differences of the forward + loss in a test.          */
+/* ------------------------------------------------------------------------- */
+int oracle_fuse_backward(const uint32_t *pairs, int64_t m, const int32_t *sw, const int32_t *self,
+                         const uint8_t *lens, const float *emb, int d, const float *params, int h,
+                         const double *dL_dfused, double *grad_params, double *grad_emb)
+{
+    double *z = (double *)malloc((size_t)(h > 0 ? h : 1) * sizeof(double));
+    if (!z) return -1;
+    const float *W1 = params, *w2 = params + 4 * h;
+    double *gW1 = grad_params, *gb1 = grad_params + 3 * h, *gw2 = grad_params + 4 * h, *gb2 = grad_params + 5 * h;
+    for (int64_t p = 0; p < m; ++p) {
+        fuse_state st;
+        fuse_pair(pairs, p, sw, self, lens, emb, d, params, h, z, &st);
+        double dA = dL_dfused[p];
+        double cprime = 0.5 * (1.0 + st.c);
+        double d_alpha = dA * (st.s - cprime);
+        double d_g = d_alpha * st.alpha * (1.0 - st.alpha);
+        double d_c = dA * (1.0 - st.alpha) * 0.5;
+        gb2[0] += d_g;
+        for (int k = 0; k < h; ++k) {
+            double u = z[k] > 0.0 ? z[k] : 0.0;
+            gw2[k] += d_g * u;
+            double d_z = z[k] > 0.0 ? d_g * (double)w2[k] : 0.0;
+            gW1[3 * k] += d_z * st.s;
+            gW1[3 * k + 1] += d_z * st.c;
+            gW1[3 * k + 2] += d_z * st.delta;
+            gb1[k] += d_z;
+            d_c += d_z * (double)W1[3 * k + 1];
+        }
+        if (grad_emb && st.ni > 0.0 && st.nj > 0.0) {
+            uint32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+            const float *ei = emb + (int64_t)i * d, *ej = emb + (int64_t)j * d;
+            double inv = 1.0 / (st.ni * st.nj);
+            for (int k = 0; k < d; ++k) {
+                grad_emb[(int64_t)i * d + k] += d_c * ((double)ej[k] * inv - st.c * (double)ei[k] / (st.ni * st.ni));
+                grad_emb[(int64_t)j * d + k] += d_c * ((double)ei[k] * inv - st.c * (double)ej[k] / (st.nj * st.nj));
+            }
+        }
+    }
+    free(z);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Training objective for the gate (reading: weighted binary cross-entropy of
+ * the fused score against family-match labels; weight of a pair = inverse
+ * frequency of its subgroup among the batch's pairs, normalised so the weights
+ * sum to the number of pairs).  pair group g(p) = subgroup(i) if nonzero else
+ * subgroup(j); label y_p = 1 iff i and j are in the same (non-background)
+ * family.  p = clamp(fused, 1e-7, 1 - 1e-7).
+ * Pins: torch's binary_cross_entropy with weights; the weights' sum.         */
+/* ------------------------------------------------------------------------- */
+void oracle_pair_labels(const uint32_t *pairs, int64_t m, const int32_t *family, const int32_t *subgroup,
+                        uint8_t *label, int32_t *group)
+{
+    for (int64_t p = 0; p < m; ++p) {
+        uint32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+        label[p] = (uint8_t)(family[i] >= 0 && family[i] == family[j]);
+        group[p] = subgroup[i] != 0 ? subgroup[i] : subgroup[j];
+    }
+}
+
+int oracle_pair_weights(const int32_t *group, int64_t m, int num_groups, double *weight)
+{
+    int64_t *count = (int64_t *)calloc((size_t)num_groups, sizeof(int64_t));
+    if (!count) return -1;
+    for (int64_t p = 0; p < m; ++p) {
+        if (group[p] < 0 || group[p] >= num_groups) {
+            free(count);
+            return -1;
+        }
+        count[group[p]]++;
+    }
+    double total = 0.0;
+    for (int64_t p = 0; p < m; ++p) total += (double)m / (double)count[group[p]]; /* 1 / pi_g */
+    for (int64_t p = 0; p < m; ++p) weight[p] = ((double)m / (double)count[group[p]]) * (double)m / total;
+    free(count);
+    return 0;
+}
+
+#define BCE_EPS 1e-7
+
+double oracle_bce_loss(const double *fused, const uint8_t *label, const double *weight, int64_t m,
+                       double *dL_dfused /* nullable */)
+{
+    double wsum = 0.0, acc = 0.0;
+    for (int64_t p = 0; p < m; ++p) wsum += weight[p];
+    for (int64_t p = 0; p < m; ++p) {
+        double q = fused[p];
+        int inside = q > BCE_EPS && q < 1.0 - BCE_EPS;
+        if (q < BCE_EPS) q = BCE_EPS;
+        if (q > 1.0 - BCE_EPS) q = 1.0 - BCE_EPS;
+        double y = (double)label[p];
+        acc += weight[p] * -(y * log(q) + (1.0 - y) * log(1.0 - q));
+        if (dL_dfused) dL_dfused[p] = inside ? weight[p] * (q - y) / (q * (1.0 - q)) / wsum : 0.0;
+    }
+    return acc / wsum;
+}
+
+/* Adam with bias correction (reading: beta1 0.9, beta2 0.999, eps 1e-8), one
+ * step t >= 1 on P parameters.  Pin: torch.optim.Adam.                      */
+void oracle_adam(double *param, const double *grad, double *m1, double *m2, int64_t P, int t, double lr,
+                 double beta1, double beta2, double eps)
+{
+    double bc1 = 1.0 - pow(beta1, (double)t), bc2 = 1.0 - pow(beta2, (double)t);
+    for (int64_t k = 0; k < P; ++k) {
+        m1[k] = beta1 * m1[k] + (1.0 - beta1) * grad[k];
+        m2[k] = beta2 * m2[k] + (1.0 - beta2) * grad[k] * grad[k];
+        double mhat = m1[k] / bc1, vhat = m2[k] / bc2;
+        param[k] -= lr * mhat / (sqrt(vhat) + eps);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cross-donor top-k retrieval over the candidate graph (recall@k is the
+ * paper's retrieval quality measure).  For query q, the candidates are the
+ * sequences j with {q, j} in C and donor(j) != donor(q); they are ranked by
+ * (S(q,j) descending, j ascending) and the first k kept; unused slots are
+ * id 0xffffffff, score -1.  Pin: brute force in a test.                      */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t score;
+    uint32_t id;
+} scored_id;
+
+static int cmp_scored(const void *pa, const void *pb)
+{
+    const scored_id *x = (const scored_id *)pa, *y = (const scored_id *)pb;
+    if (x->score != y->score) return x->score > y->score ? -1 : 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+int oracle_topk(const uint32_t *pairs, const int32_t *scores, int64_t m, const int32_t *donor,
+                const uint32_t *queries, int64_t nq, int k, uint32_t *top_id, int32_t *top_score)
+{
+    scored_id *buf = NULL;
+    int64_t cap = 0;
+    for (int64_t qi = 0; qi < nq; ++qi) {
+        uint32_t q = queries[qi];
+        int64_t len = 0;
+        for (int64_t p = 0; p < m; ++p) {
+            uint32_t i = pairs[2 * p], j = pairs[2 * p + 1], other;
+            if (i == q) other = j;
+            else if (j == q) other = i;
+            else continue;
+            if (donor[other] == donor[q]) continue;
+            if (len == cap) {
+                int64_t nc = cap ? 2 * cap : 256;
+                scored_id *nb = (scored_id *)realloc(buf, (size_t)nc * sizeof(scored_id));
+                if (!nb) {
+                    free(buf);
+                    return -1;
+                }
+                buf = nb;
+                cap = nc;
+            }
+            buf[len].score = scores[p];
+            buf[len].id = other;
+            ++len;
+        }
+        if (len > 0) qsort(buf, (size_t)len, sizeof(scored_id), cmp_scored);
+        for (int r = 0; r < k; ++r) {
+            top_id[qi * k + r] = r < len ? buf[r].id : 0xffffffffu;
+            top_score[qi * k + r] = r < len ? buf[r].score : -1;
+        }
+    }
+    free(buf);
+    return 0;
+}
