@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the affinity stage on one donor of 1,000,000 synthetic CDR3-like
+sequences: candidate pairs scored per second through the whole hot path
+(pack -> MinHash sign -> LSH band/candidates/dedup -> self-scores -> Smith-
+Waterman -> gated fusion), plus SW GCUPS, per-stage times, the dominant stage's
+roofline, the oracle as a CPU baseline and an end-to-end number with host
+buffers.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank processes its own donor repertoire (seeded by rank):
+weak scaling, no data-path collective; rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "candidate pairs scored/s and SW GCUPS on 1 GB300 (% of int/DPX peak), batched vs plain"
+UNIT = "pairs/s"
+# Smith-Waterman algorithmic int32 operations per DP cell: H-diagonal + score,
+# max3-with-0, H - open, E add-max, F add-max, running best max.
+SW_OPS_PER_CELL = 6
+# INT32 lane operations per SM per clock on sm_103a, measured by the ALU
+# microbenchmark recorded in profiles/alu_peak_gb300.md; times 152 SMs and the
+# 2070 MHz maximum SM clock gives the integer roof.
+INT_LANE_OPS_PER_SM_CLK = 64.0
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=1_000_000, help="sequences per donor (default: the 1M donor)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-sample-n", type=int, default=500_000, help="oracle sample for the cpu_baseline key")
+    p.add_argument("--ref-sample-n", type=int, default=200_000, help="oracle sample per step of --impl reference")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def alu_peak_gops():
+    return INT_LANE_OPS_PER_SM_CLK * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source has not changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        table = json.load(fh)
+    entry = table.get(kernel)
+    if not entry:
+        return None
+    src = os.path.join(ROOT, entry["source"])
+    if not os.path.exists(src):
+        return None
+    with open(src, "rb") as fh:
+        digest = hashlib.sha256(fh.read()).hexdigest()
+    return entry["dram_bytes_per_launch"] if digest == entry.get("source_sha256") else None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(gpu_index), "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if len(r) > 5 + k and "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline / reference arm: the oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def oracle_step(n_sample: int, seed: int = 0):
+    """One pass of the oracle over a donor repertoire of n_sample sequences
+    (same generator, families of 25, same hashing).  Returns (pairs, seconds)."""
+    import oracle
+    from paper_2602_17330_gb300 import pipeline, synth
+
+    cfg = pipeline.DONOR_1M
+    rep = synth.donor_repertoire(n_sample, seed=seed)
+    a, b = synth.hash_coefficients(cfg.hashes, seed=0)
+    emb = synth.unit_embeddings(rep.n, cfg.d, seed=seed)
+    params = synth.gate_parameters(cfg.hidden, seed=0)
+    t0 = time.perf_counter()
+    sig = oracle.sign(rep.codes, rep.lens, cfg.k, a, b)
+    pairs = oracle.candidates(sig, cfg.bands, cfg.rows, cfg.bucket_cap)
+    self_sc = oracle.self_scores(rep.codes, rep.lens, cfg.gap_open, cfg.gap_extend)
+    sw = oracle.sw_pairs(rep.codes, rep.lens, pairs, cfg.gap_open, cfg.gap_extend)
+    oracle.fuse_forward(pairs, sw, self_sc, rep.lens, emb, params, cfg.hidden)
+    return pairs.shape[0], time.perf_counter() - t0
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    n = args.ref_sample_n
+    for _ in range(args.warmup):
+        oracle_step(n)
+    tot_pairs, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        p, s = oracle_step(n)
+        tot_pairs += p
+        tot_s += s
+    value = tot_pairs / tot_s
+    sample = f"oracle, single thread, on a {n:,}-sequence donor from the same generator, full pipeline per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64",
+        "data": "synthetic", "config": {"workload": f"donor_{n}", "n": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+
+    from paper_2602_17330_gb300 import _build, pipeline, subquad, synth
+
+    if rank == 0 or not os.path.exists(subquad.LIB_PATH):
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    base = pipeline.DONOR_1M
+    cfg = base if args.n == base.n else pipeline.Workload(f"donor_{args.n}", args.n, bucket_cap=base.bucket_cap)
+
+    rep = synth.donor_repertoire(cfg.n, seed=rank)
+    a, b = synth.hash_coefficients(cfg.hashes, seed=0)
+    emb = synth.unit_embeddings(rep.n, cfg.d, seed=rank)
+    params = synth.gate_parameters(cfg.hidden, seed=0)
+
+    stream = torch.cuda.Stream(device=dev)
+    ctx = subquad.Context(local_rank, stream=stream)
+    pipe = pipeline.Pipeline(ctx, cfg)
+    with torch.cuda.stream(stream):
+        x = pipe.upload(rep, a, b, emb, params)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        for _ in range(max(args.warmup, 1)):
+            out = pipe.forward(x)
+    stream.synchronize()
+    ctx.check()
+    pairs_np = out["pairs"].cpu().numpy().view(np.uint32)
+    m = int(pairs_np.shape[0])
+    cells = pipeline.cells_of(rep.lens, pairs_np)
+
+    stage_names = ["pack", "sign", "band", "self", "align", "fuse"]
+    steps = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = ctx.launch_count()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()  # evict L2 between steps (outside the events)
+            ev = {"start": torch.cuda.Event(enable_timing=True)}
+            ev["start"].record(stream)
+
+            def mark(name, ev=ev):
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                ev[name] = e
+
+            pipe.forward(x, marks=mark)
+            steps.append(ev)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop() if sampler else None
+    launches = ctx.launch_count() - launches0
+    ctx.check()
+
+    step_ms = [e["start"].elapsed_time(e["fuse"]) for e in steps]
+    stage_ms = {}
+    prev = "start"
+    for s in stage_names:
+        stage_ms[s] = statistics.mean(e[prev].elapsed_time(e[s]) for e in steps)
+        prev = s
+    total_ms = sum(step_ms)
+
+    # whole job: units over all ranks / max time over ranks
+    if world > 1:
+        t = torch.tensor([total_ms, float(m) * args.steps], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        max_ms, total_units = float(tmax[0]), float(t[1])
+    else:
+        max_ms, total_units = total_ms, float(m) * args.steps
+    value = total_units / (max_ms / 1e3)
+
+    # roofline of the dominant stage
+    hbm_peak, peak_kind = measured_peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    align_s = stage_ms["align"] / 1e3
+    gcups = cells / align_s / 1e9
+    alu_peak = alu_peak_gops()
+    if dom == "align":
+        achieved = cells * SW_OPS_PER_CELL / align_s / 1e9
+        roof = {"kernel": "align_plain_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                "unit": "Gop/s", "frac": achieved / alu_peak, "traffic": traffic_for("align_plain_kernel"),
+                "peak_source": "INT32 lane-ops/clk/SM (microbenchmark) x 152 SMs x 2070 MHz"}
+    elif dom == "band":
+        algo = 4 * cfg.hashes * cfg.n + 8 * m
+        achieved = algo / (stage_ms["band"] / 1e3) / 1e9
+        roof = {"kernel": "band stage (insert, sort, chunk, emit, pair sort)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic_for("band_stage"),
+                "peak_source": f"{peak_kind} copy bandwidth"}
+    elif dom == "sign":
+        evals = float((np.maximum(rep.lens.astype(np.int64) - cfg.k + 1, 0)).sum()) * cfg.hashes
+        achieved = evals * 6 / (stage_ms["sign"] / 1e3) / 1e9
+        roof = {"kernel": "sign_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
+                "frac": achieved / alu_peak, "traffic": traffic_for("sign_kernel"),
+                "peak_source": "INT32 lane-ops/clk/SM (microbenchmark) x 152 SMs x 2070 MHz"}
+    else:
+        algo = m * (8 + 4 + 4) + cfg.n * (4 * cfg.d + 4 + cfg.pack_stride)
+        achieved = algo / (stage_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": f"{dom} stage", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic_for(f"{dom}_stage"),
+                "peak_source": f"{peak_kind} copy bandwidth"}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, pipe, rep, a, b, emb, params, stream, dev, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_s = args.cpu_sample_n
+        p_s, sec = oracle_step(n_s)
+        cpu = {"value": p_s / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"single-threaded oracle, full pipeline on a {n_s:,}-sequence donor from the same "
+                         f"generator ({p_s:,} pairs, {sec:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32/f32", "data": "synthetic",
+            "config": {"workload": f"{cfg.name}: {cfg.n:,} CDR3-like sequences per GPU, families of 25, 50 rare "
+                                   f"subgroups; 3-mers, {cfg.hashes} hashes in {cfg.bands}x{cfg.rows} bands, "
+                                   f"bucket cap {cfg.bucket_cap}; BLOSUM62 o{cfg.gap_open} e{cfg.gap_extend}; "
+                                   f"d={cfg.d}, gate 3-{cfg.hidden}-1",
+                       "n": cfg.n, "pairs_per_step": m, "cells_per_step": cells, "l2": "flushed between steps",
+                       "sw_kernel": "plain (one pair per thread, per-warp unrolled height)"},
+            "sw_gcups": gcups, "sw_frac_of_int_peak": gcups * SW_OPS_PER_CELL / alu_peak,
+            "stages_ms": stage_ms, "wall_s": wall,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, pipe, rep, a, b, emb, params, stream, dev, world):
+    import numpy as np
+    import torch
+
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+            dict(codes=rep.codes, lens=rep.lens, a=a.view(np.int32), b=b.view(np.int32),
+                 emb=np.ascontiguousarray(emb, dtype=np.float32), params=params).items()}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    outs = []
+    with torch.cuda.stream(stream):
+        dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+
+        def one_step():
+            for k in host:
+                dev_in[k].copy_(host[k], non_blocking=True)
+            out = pipe.forward(dev_in)
+            m = int(out["pairs"].shape[0])
+            res = [torch.empty((m, 2), dtype=torch.int32, pin_memory=True),
+                   torch.empty((m,), dtype=torch.int32, pin_memory=True),
+                   torch.empty((m,), dtype=torch.float32, pin_memory=True)]
+            res[0].copy_(out["pairs"], non_blocking=True)
+            res[1].copy_(out["sw"], non_blocking=True)
+            res[2].copy_(out["fused"], non_blocking=True)
+            return m, res
+
+        for _ in range(max(args.warmup, 1)):
+            one_step()
+        stream.synchronize()
+        t = []
+        d2h = 0
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m, res = one_step()
+            e1.record(stream)
+            outs.append(m)
+            d2h = sum(r.numel() * r.element_size() for r in res)
+            t.append((e0, e1))
+        stream.synchronize()
+    total = sum(e0.elapsed_time(e1) for e0, e1 in t)
+    units = float(sum(outs))
+    if world > 1:
+        tt = torch.tensor([total], dtype=torch.float64, device=dev)
+        uu = torch.tensor([units], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(uu, op=torch.distributed.ReduceOp.SUM)
+        total, units = float(tt), float(uu)
+    return {"value": units / (total / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * subquad.h -- C ABI of the GB300 (sm_103a) library for SubQuad's
+ * all-candidates affinity stage: MinHash signing, LSH banding with candidate
+ * emission and deduplication, affine-gap local alignment with BLOSUM62, and
+ * the per-pair gated fusion of alignment and embedding channels with its
+ * adjoint for gate training.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers documented as "device" point to memory the CALLER allocated on
+ *   the context's device; the library only reads or writes them.  Pointers
+ *   documented as "host" are ordinary host memory.  The library owns only the
+ *   context and its scratch workspace.
+ * - Every call is asynchronous on the context's stream unless its comment says
+ *   it synchronises.  Inputs must stay valid until the stream has passed the
+ *   call.
+ * - Return value: SUBQUAD_OK (0) or a negative subquad_status.  No call aborts
+ *   the process.  Argument errors are detected on the host before any work is
+ *   queued.  Errors found by kernels (an invalid residue code or length in
+ *   subquad_pack, an exhausted iteration bound) are recorded in a sticky
+ *   device-side word and reported by the next synchronising call
+ *   (subquad_band_candidates, subquad_check) as SUBQUAD_ERR_INPUT or
+ *   SUBQUAD_ERR_TIMEOUT.
+ * - Residue codes are 0..19 in the order ACDEFGHIKLMNPQRSTVWY.
+ * - A pair list is uint32 [m][2], pair p = (pairs[2p], pairs[2p+1]).
+ * - One context per host thread / stream; a context is not thread-safe.
+ */
+#ifndef SUBQUAD_H
+#define SUBQUAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct subquad_ctx subquad_ctx;
+
+typedef enum {
+    SUBQUAD_OK = 0,
+    SUBQUAD_ERR_ARG = -1,      /* invalid argument (null pointer, size, alignment, range) */
+    SUBQUAD_ERR_CAPACITY = -2, /* output buffer too small; required size returned */
+    SUBQUAD_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+    SUBQUAD_ERR_TIMEOUT = -4,  /* a bounded device-side loop ran out of iterations */
+    SUBQUAD_ERR_NOMEM = -5,    /* scratch allocation failed */
+    SUBQUAD_ERR_INPUT = -6     /* input data invalid (residue code >= 20, length out of range) */
+} subquad_status;
+
+/* Human-readable text for a status code (static storage). */
+const char *subquad_strerror(int status);
+
+/* Library ABI version: major*10000 + minor*100 + patch. */
+int subquad_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Create a context bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The scoring matrix
+ * starts as BLOSUM62.  *out receives the context. */
+int subquad_create(subquad_ctx **out, int device, void *cuda_stream);
+
+/* Release the context and its scratch (synchronises its stream). */
+int subquad_destroy(subquad_ctx *ctx);
+
+/* Re-bind the context to another stream of the same device. */
+int subquad_set_stream(subquad_ctx *ctx, void *cuda_stream);
+
+/* Synchronise the stream and report (then clear) the sticky device error. */
+int subquad_check(subquad_ctx *ctx);
+
+/* Bytes of context-owned device scratch currently allocated (host query). */
+int64_t subquad_scratch_bytes(const subquad_ctx *ctx);
+
+/* Number of CUDA kernels this context has launched so far (host query). */
+int64_t subquad_launch_count(const subquad_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Scoring matrix (affinity channel a^(1) of Algorithm 1)                   */
+/* ------------------------------------------------------------------------ */
+
+/* Host-only, needs no GPU: write the library's built-in BLOSUM62
+ * (Henikoff & Henikoff 1992) as int8 [20][20] in code order to host `out`. */
+int subquad_default_matrix(int8_t *out);
+
+/* Host `matrix` int8 [20][20] (row = first sequence's residue), or NULL for
+ * BLOSUM62.  Entries must lie in [-64, 63].  Takes effect for later calls. */
+int subquad_set_matrix(subquad_ctx *ctx, const int8_t *matrix);
+
+/* ------------------------------------------------------------------------ */
+/* Sequence packing (Algorithm 1, preprocessing: trim/pad)                   */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes per packed sequence for sequences of at most max_len residues:
+ * 16 for max_len <= 24, 32 for max_len <= 30, 0 if unsupported. */
+int subquad_pack_stride(int max_len);
+
+/* Pack residue codes into fixed records of `pack_stride` bytes (16 or 32).
+ * codes: device uint8 [n][code_stride]; lens: device uint8 [n], 1 <= len <=
+ * max length of the stride; packed_out: device, n*pack_stride bytes, 16-byte
+ * aligned.  Record layout: little-endian 64-bit words, residue r in bits
+ * 5*(r%12) .. 5*(r%12)+4 of word r/12; the length in bits 60..63 of word 0
+ * (low nibble) and word 1 (high nibble).  Invalid codes/lengths set
+ * SUBQUAD_ERR_INPUT in the sticky device error. */
+int subquad_pack(subquad_ctx *ctx, const uint8_t *codes, int code_stride, const uint8_t *lens, int64_t n,
+                 int pack_stride, void *packed_out);
+
+/* ------------------------------------------------------------------------ */
+/* (a1) MinHash signatures -- Algorithm 1 preprocessing ("compute MinHash    */
+/* sketches"); sketch size M = bands*rows as in the appendix on sampling     */
+/* error bounds.                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* sig_out[b][i][r] = min over the k-mers x of sequence i of
+ *   (a[t] * x + b[t]) mod (2^31 - 1),  t = b*rows + r,
+ * x = base-20 value of the k-mer, first residue most significant.
+ * packed: device records from subquad_pack; a, b: device uint32 [bands*rows],
+ * a[t] in [1, 2^31-2], b[t] in [0, 2^31-2] (not checked); sig_out: device
+ * uint32 [bands][n][rows].  1 <= k <= 6, k <= every length (a shorter sequence
+ * has no k-mer and gets 0xffffffff in every row), bands*rows <= 512,
+ * 1 <= rows <= 8. */
+int subquad_sign(subquad_ctx *ctx, const void *packed, int pack_stride, int64_t n, int k, int bands, int rows,
+                 const uint32_t *a, const uint32_t *b, uint32_t *sig_out);
+
+/* ------------------------------------------------------------------------ */
+/* (a2) LSH banding, candidate emission and deduplication -- Algorithm 1     */
+/* preprocessing ("build MinHash index; generate candidate list CAND"), the  */
+/* contiguous bucket layout of "Optimized Indexing Mechanism", and the       */
+/* candidate set C of the retrieval-complexity appendix.                     */
+/* ------------------------------------------------------------------------ */
+
+/* Band b's key of sequence i is the exact tuple sig[b][i][0..rows-1].  A
+ * bucket is the set of sequences sharing a key; ranked by ascending id, its
+ * members fall into chunks of `bucket_cap` consecutive ranks (bucket_cap <= 0:
+ * one chunk).  C = pairs i < j sharing a chunk in at least one band.
+ * sig: device, layout of subquad_sign.  pairs_out: device uint32
+ * [pairs_capacity][2]; receives C sorted lexicographically.
+ * *num_pairs_out (host) receives |C|.  If |C| > pairs_capacity the call
+ * returns SUBQUAD_ERR_CAPACITY, *num_pairs_out holds the required count and
+ * the contents of pairs_out are unspecified.  n < 2^31.  SYNCHRONISES the
+ * stream (the pair count is read back). */
+int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows,
+                            int32_t bucket_cap, uint32_t *pairs_out, int64_t pairs_capacity,
+                            int64_t *num_pairs_out);
+
+/* ------------------------------------------------------------------------ */
+/* (a3) Affine-gap local alignment -- the alignment channel computed for     */
+/* every candidate pair in Algorithm 1's affinity loop.  The paper's own GPU  */
+/* kernel is an edit-distance DP (GPU appendix, edit-distance kernel); this  */
+/* is Gotoh's local form with the context's scoring matrix.                  */
+/* ------------------------------------------------------------------------ */
+
+/* scores_out[p] = max over local alignments of pairs[p] with a gap of length
+ * l costing gap_open + (l-1)*gap_extend:
+ *   E(i,j) = max(E(i,j-1) - e, H(i,j-1) - o)
+ *   F(i,j) = max(F(i-1,j) - e, H(i-1,j) - o)
+ *   H(i,j) = max(0, H(i-1,j-1) + M[a_i][b_j], E(i,j), F(i,j)),  score = max H.
+ * packed: device records; pairs: device uint32 [m][2]; scores_out: device
+ * int32 [m].  0 <= gap_extend, gap_open <= 1000. */
+int subquad_align_score(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs, int64_t m,
+                        int gap_open, int gap_extend, int32_t *scores_out);
+
+/* self_out[i] = score of sequence i aligned with itself (the normaliser of
+ * the fused score).  self_out: device int32 [n]. */
+int subquad_self_scores(subquad_ctx *ctx, const void *packed, int pack_stride, int64_t n, int gap_open,
+                        int gap_extend, int32_t *self_out);
+
+/* ------------------------------------------------------------------------ */
+/* (a4) Per-pair gated fusion -- Eq. alpha, Eq. wm and Eq. afused with two   */
+/* channels: a1 = s = S_ij / sqrt(S_ii S_jj), a2 = (1 + cos(e_i, e_j)) / 2.   */
+/* g = w2 . ReLU(W1 [s, c, |L_i - L_j|] + b1) + b2, alpha = sigmoid(g) (the  */
+/* softmax of Eq. wm over logits (g, 0)), fused = alpha a1 + (1-alpha) a2.    */
+/* ------------------------------------------------------------------------ */
+
+/* pairs: device uint32 [m][2]; sw: device int32 [m]; self_scores: device
+ * int32 [n]; packed: device records (lengths); emb: device float [n][d],
+ * 16-byte aligned, d % 4 == 0, 4 <= d <= 1024; gate_params: device float
+ * [5*hidden+1] = W1 [hidden][3] row-major, b1 [hidden], w2 [hidden], b2;
+ * 1 <= hidden <= 64.  fused_out: device float [m]; alpha_out: device float
+ * [m] or NULL. */
+int subquad_fuse_forward(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                         const int32_t *self_scores, const void *packed, int pack_stride, const float *emb, int d,
+                         const float *gate_params, int hidden, float *fused_out, float *alpha_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SUBQUAD_H */

@@ -1,0 +1,401 @@
+// (a2) LSH banding, candidate emission and deduplication (Algorithm 1,
+// preprocessing: "build MinHash index; generate candidate list CAND").
+//
+// Per group of bands (all bands at once unless the keys would overflow 32
+// bits):
+//  1. insert every (band, sequence) key -- the exact R-tuple -- into a
+//     per-band open-addressing table whose slots hold the id of the first
+//     inserter; equal keys meet at one slot, so the slot index is an exact
+//     bucket id;
+//  2. stable radix sort of (band * S + slot, id): each bucket becomes one
+//     contiguous run with its members in ascending id order (the contiguous
+//     bucket blocks of the paper's index);
+//  3. run starts by a max-scan of head positions; rank in bucket = position -
+//     run start; chunk = rank / cap; every element records, per band, the sorted
+//     position of its chunk head (its "chunk id" G[i][b]);
+//  4. chunks with >= 2 members are compacted and their pair counts scanned;
+//  5. each warp takes 32 consecutive pair indices, finds their chunks, decodes
+//     (u, v) and keeps pair (i, j) only if no earlier band already puts i and j
+//     in one chunk (first-band ownership), so every pair of C is emitted once;
+//  6. after all groups: read back |C| (the call's only host synchronisation),
+//     then radix-sort the pairs into lexicographic order.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr uint32_t kEmpty = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t mix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    h *= 0x846ca68bu;
+    h ^= h >> 16;
+    return h;
+}
+
+__device__ __forceinline__ void load_key(const uint32_t *__restrict__ p, int rows, uint32_t k[8])
+{
+    if (rows == 4) {
+        uint4 v = *reinterpret_cast<const uint4 *>(p);
+        k[0] = v.x;
+        k[1] = v.y;
+        k[2] = v.z;
+        k[3] = v.w;
+    } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (r < rows) k[r] = p[r];
+    }
+}
+
+__device__ __forceinline__ bool key_equal(const uint32_t *__restrict__ p, int rows, const uint32_t k[8])
+{
+    uint32_t o[8];
+    load_key(p, rows, o);
+    bool eq = true;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+        if (r < rows) eq = eq && o[r] == k[r];
+    return eq;
+}
+
+// Step 1: exact bucket id (= table slot) per (band, sequence).
+__global__ void __launch_bounds__(256) band_insert_kernel(const uint32_t *__restrict__ sig, int64_t n, int rows,
+                                                          int band0, int gbands, int log_s,
+                                                          uint32_t *__restrict__ table, uint32_t *__restrict__ keys,
+                                                          uint32_t *__restrict__ vals, uint32_t *err)
+{
+    const int64_t total = (int64_t)gbands * n;
+    const uint32_t smask = (1u << log_s) - 1u;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int gb = (int)(e / n);
+        const uint32_t i = (uint32_t)(e - (int64_t)gb * n);
+        const uint32_t *band_sig = sig + (int64_t)(band0 + gb) * n * rows;
+        uint32_t k[8];
+        load_key(band_sig + (int64_t)i * rows, rows, k);
+        uint32_t h = 0x9e3779b9u ^ (uint32_t)rows;
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (r < rows) h = mix32(h ^ k[r]);
+        uint32_t *tab = table + ((int64_t)gb << log_s);
+        uint32_t slot = h & smask;
+        bool found = false;
+        // the table is at most half full, so a free slot is always reached
+        for (uint32_t probe = 0; probe <= smask; ++probe) {
+            uint32_t cur = tab[slot];
+            if (cur == kEmpty) {
+                cur = atomicCAS(&tab[slot], kEmpty, i);
+                if (cur == kEmpty) {
+                    found = true;
+                    break;
+                }
+            }
+            if (key_equal(band_sig + (int64_t)cur * rows, rows, k)) {
+                found = true;
+                break;
+            }
+            slot = (slot + 1) & smask;
+        }
+        if (!found) atomicOr(err, SQ_DEVERR_TIMEOUT);
+        keys[e] = ((uint32_t)gb << log_s) | slot;
+        vals[e] = i;
+    }
+}
+
+// Step 3a: head positions of runs of equal keys (0 elsewhere), for a max-scan.
+__global__ void band_heads_kernel(const uint32_t *__restrict__ keys, int64_t count, uint32_t *__restrict__ head_pos)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        head_pos[e] = (e == 0 || keys[e] != keys[e - 1]) ? (uint32_t)e : 0u;
+}
+
+struct ChunkInfo {
+    uint32_t head;  // sorted position of the element's chunk head
+    bool is_head, is_last;
+};
+
+__device__ __forceinline__ ChunkInfo chunk_info(const uint32_t *__restrict__ run_start, int64_t count, int64_t e,
+                                                int cap)
+{
+    ChunkInfo c;
+    const uint32_t rs = run_start[e];
+    const uint32_t rank = (uint32_t)e - rs;
+    c.head = cap > 0 ? rs + (rank / (uint32_t)cap) * (uint32_t)cap : rs;
+    c.is_head = (uint32_t)e == c.head;
+    c.is_last = e + 1 == count || run_start[e + 1] != rs || (cap > 0 && (rank + 1) % (uint32_t)cap == 0);
+    return c;
+}
+
+// Step 3b: chunk ids per (sequence, band) and flags of chunks with >= 2 members.
+__global__ void band_chunks_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                                   const uint32_t *__restrict__ run_start, int64_t count, int cap, int log_s,
+                                   int band0, int bands, uint32_t *__restrict__ chunk_of, uint32_t *__restrict__ flags)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        ChunkInfo c = chunk_info(run_start, count, e, cap);
+        const int b = band0 + (int)(keys[e] >> log_s);
+        chunk_of[(int64_t)vals[e] * bands + b] = c.head;
+        flags[e] = (c.is_head && !c.is_last) ? 1u : 0u;
+    }
+}
+
+// Step 4: compacted chunk heads, sizes and pair counts.
+__global__ void band_chunk_list_kernel(const uint32_t *__restrict__ run_start, const uint32_t *__restrict__ flags,
+                                       const uint32_t *__restrict__ cidx, int64_t count, int cap,
+                                       uint32_t *__restrict__ heads, uint32_t *__restrict__ sizes,
+                                       uint64_t *__restrict__ npairs)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        if (flags[e]) heads[cidx[e]] = (uint32_t)e;
+        ChunkInfo c = chunk_info(run_start, count, e, cap);
+        if (c.is_last && !c.is_head) {
+            const uint32_t s = (uint32_t)e - c.head + 1;
+            const uint32_t ci = cidx[c.head];
+            sizes[ci] = s;
+            npairs[ci] = (uint64_t)s * (s - 1) / 2;
+        }
+    }
+}
+
+// (u, v), u < v, of the t-th pair of a chunk of size s in row-major order.
+__device__ __forceinline__ void decode_pair(uint64_t t, uint32_t s, uint32_t &u, uint32_t &v)
+{
+    // estimate u from the quadratic in float, then correct it exactly
+    const uint64_t twos1 = 2 * (uint64_t)s - 1;
+    const uint64_t d = twos1 * twos1 - 8 * t;  // > 0 for t < s(s-1)/2
+    int64_t ue = (int64_t)(((float)twos1 - sqrtf((float)d)) * 0.5f);
+    if (ue < 0) ue = 0;
+    if (ue > (int64_t)s - 2) ue = (int64_t)s - 2;
+    auto row_start = [s](int64_t uu) { return (uint64_t)uu * (2 * (uint64_t)s - uu - 1) / 2; };
+    for (int it = 0; it < 64 && ue > 0 && row_start(ue) > t; ++it) --ue;
+    for (int it = 0; it < 64 && ue + 1 <= (int64_t)s - 2 && row_start(ue + 1) <= t; ++it) ++ue;
+    u = (uint32_t)ue;
+    v = (uint32_t)(ue + 1 + (int64_t)(t - row_start(ue)));
+}
+
+// Step 5: owned pairs of this band group, appended to out.
+__global__ void __launch_bounds__(256) band_emit_kernel(
+    const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ heads,
+    const uint32_t *__restrict__ sizes, const uint64_t *__restrict__ poff, const uint32_t *__restrict__ d_nchunks,
+    const uint64_t *__restrict__ d_total, int log_s, int band0, int bands, const uint32_t *__restrict__ chunk_of,
+    uint32_t *__restrict__ out, int64_t capacity, unsigned long long *__restrict__ d_count, uint32_t *err)
+{
+    const uint32_t nc = *d_nchunks;
+    const uint64_t total = *d_total;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_id = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t q0 = (uint64_t)warp_id * 32; q0 < total; q0 += (uint64_t)nwarps * 32) {
+        // chunk of q0: largest c with poff[c] <= q0 (every chunk has >= 1 pair)
+        uint32_t c0 = 0;
+        if (lane == 0) {
+            uint32_t lo = 0, hi = nc;
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (poff[mid] <= q0) lo = mid;
+                else hi = mid;
+            }
+            c0 = lo;
+        }
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        const uint64_t q = q0 + lane;
+        bool owned = false;
+        uint32_t i = 0, j = 0;
+        if (q < total) {
+            uint32_t lo = c0, hi = min(nc, c0 + (uint32_t)lane + 1);
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (poff[mid] <= q) lo = mid;
+                else hi = mid;
+            }
+            const uint32_t h = heads[lo], s = sizes[lo];
+            uint32_t u, v;
+            decode_pair(q - poff[lo], s, u, v);
+            if (u >= v || v >= s) {  // cannot happen for a consistent chunk list
+                atomicOr(err, SQ_DEVERR_TIMEOUT);
+                u = 0;
+                v = 1;
+            }
+            i = vals[h + u];
+            j = vals[h + v];
+            const int b = band0 + (int)(keys[h] >> log_s);
+            owned = true;
+            const uint32_t *gi = chunk_of + (int64_t)i * bands;
+            const uint32_t *gj = chunk_of + (int64_t)j * bands;
+            for (int bb = 0; bb < b; ++bb)
+                if (gi[bb] == gj[bb]) {
+                    owned = false;
+                    break;
+                }
+        }
+        const uint32_t mask = __ballot_sync(0xffffffffu, owned);
+        unsigned long long base = 0;
+        if (lane == 0 && mask) base = atomicAdd(d_count, (unsigned long long)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (owned) {
+            const unsigned long long pos = base + __popc(mask & ((1u << lane) - 1u));
+            if (pos < (unsigned long long)capacity) reinterpret_cast<uint2 *>(out)[pos] = make_uint2(i, j);
+        }
+    }
+}
+
+// raw pair count of the group = offset of the last chunk + its pairs
+__global__ void band_total_kernel(const uint64_t *__restrict__ poff, const uint32_t *__restrict__ sizes,
+                                  const uint32_t *__restrict__ d_nchunks, uint64_t *__restrict__ d_total)
+{
+    const uint32_t nc = *d_nchunks;
+    uint64_t total = 0;
+    if (nc > 0) {
+        const uint64_t s = sizes[nc - 1];
+        total = poff[nc - 1] + s * (s - 1) / 2;
+    }
+    *d_total = total;
+}
+
+__global__ void pairs_to_keys_kernel(const uint32_t *__restrict__ pairs, int64_t m, int nbits,
+                                     uint64_t *__restrict__ keys)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
+        keys[p] = ((uint64_t)ij.x << nbits) | ij.y;
+    }
+}
+
+__global__ void keys_to_pairs_kernel(const uint64_t *__restrict__ keys, int64_t m, int nbits, uint32_t *__restrict__ pairs)
+{
+    const uint64_t mask = (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1ull);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[p];
+        reinterpret_cast<uint2 *>(pairs)[p] = make_uint2((uint32_t)(k >> nbits), (uint32_t)(k & mask));
+    }
+}
+
+int bits_for(uint64_t v)  // number of bits needed to hold values 0..v
+{
+    int b = 1;
+    while (b < 64 && (v >> b) != 0) ++b;
+    return b;
+}
+
+}  // namespace
+
+extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows,
+                                       int32_t bucket_cap, uint32_t *pairs_out, int64_t pairs_capacity,
+                                       int64_t *num_pairs_out)
+{
+    SQ_ENTER(ctx);
+    if (!num_pairs_out || n < 0 || n >= (int64_t(1) << 31) || bands < 1 || rows < 1 || rows > 8 ||
+        bands * rows > 512 || pairs_capacity < 0)
+        return SUBQUAD_ERR_ARG;
+    *num_pairs_out = 0;
+    if (n < 2) return subquad_check(ctx);
+    if (!sig || (pairs_capacity > 0 && !pairs_out)) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(sig) % 16 || reinterpret_cast<uintptr_t>(pairs_out) % 8) return SUBQUAD_ERR_ARG;
+    const int cap = (bucket_cap <= 0 || bucket_cap >= n) ? 0 : bucket_cap;
+
+    // table of S >= 2n slots per band; a group of G bands keeps G*S <= 2^32
+    int log_s = bits_for((uint64_t)(2 * n - 1));
+    const int64_t S = int64_t(1) << log_s;
+    int G = (int)std::min<int64_t>(bands, (int64_t(1) << 32) / S);
+    if (G < 1) return SUBQUAD_ERR_ARG;
+    const int64_t mg = (int64_t)G * n;
+
+    auto layout = [&](SqArena &a) {
+        struct L {
+            uint32_t *chunk_of, *table, *k0, *v0, *k1, *v1, *sizes;
+            uint64_t *npairs;
+            void *tmp;
+        } l;
+        l.chunk_of = a.take<uint32_t>((size_t)n * bands);
+        l.table = a.take<uint32_t>((size_t)G * S);
+        l.k0 = a.take<uint32_t>(mg);
+        l.v0 = a.take<uint32_t>(mg);
+        l.k1 = a.take<uint32_t>(mg);
+        l.v1 = a.take<uint32_t>(mg);
+        l.sizes = a.take<uint32_t>(mg);
+        l.npairs = a.take<uint64_t>(mg);
+        l.tmp = a.take<char>(std::max(sq_radix_tmp_bytes(mg), sq_scan_tmp_bytes(mg)));
+        return l;
+    };
+    SqArena measure(nullptr);
+    layout(measure);
+    SQ_TRY(sq_scratch_reserve(ctx, measure.off));
+    SqArena arena(ctx->scratch);
+    auto L = layout(arena);
+    const size_t tmp_bytes = std::max(sq_radix_tmp_bytes(mg), sq_scan_tmp_bytes(mg));
+
+    unsigned long long *d_count = reinterpret_cast<unsigned long long *>(ctx->d_small);
+    uint32_t *d_nchunks = reinterpret_cast<uint32_t *>(ctx->d_small + 1);
+    uint64_t *d_total = ctx->d_small + 2;
+    SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 8 * sizeof(uint64_t), ctx->stream));
+
+    for (int band0 = 0; band0 < bands; band0 += G) {
+        const int gb = std::min(G, bands - band0);
+        const int64_t count = (int64_t)gb * n;
+        const unsigned grid = sq_grid(ctx, count, 256, 8);
+        SQ_TRY_CUDA(cudaMemsetAsync(L.table, 0xff, (size_t)gb * S * sizeof(uint32_t), ctx->stream));
+        band_insert_kernel<<<grid, 256, 0, ctx->stream>>>(sig, n, rows, band0, gb, log_s, L.table, L.k0, L.v0,
+                                                          ctx->d_err);
+        SQ_LAUNCH_CHECK();
+        bool in_alt = false;
+        const int key_bits = log_s + bits_for((uint64_t)(gb - 1));
+        SQ_TRY(sq_radix_sort_u32(ctx, L.k0, L.v0, L.k1, L.v1, count, 0, key_bits, &in_alt, L.tmp, tmp_bytes));
+        uint32_t *K = in_alt ? L.k1 : L.k0, *V = in_alt ? L.v1 : L.v0;
+        uint32_t *run_start = in_alt ? L.k0 : L.k1;  // free after the sort
+        uint32_t *flags = in_alt ? L.v0 : L.v1;
+        band_heads_kernel<<<grid, 256, 0, ctx->stream>>>(K, count, run_start);
+        SQ_LAUNCH_CHECK();
+        SQ_TRY(sq_scan_u32(ctx, run_start, run_start, count, true, true, nullptr, L.tmp, tmp_bytes));
+        band_chunks_kernel<<<grid, 256, 0, ctx->stream>>>(K, V, run_start, count, cap, log_s, band0, bands, L.chunk_of,
+                                                          flags);
+        SQ_LAUNCH_CHECK();
+        uint32_t *cidx = L.table;  // the hash table is no longer needed
+        SQ_TRY(sq_scan_u32(ctx, flags, cidx, count, false, false, d_nchunks, L.tmp, tmp_bytes));
+        uint32_t *heads = L.table + count;  // S >= 2n, so the table holds both
+        band_chunk_list_kernel<<<grid, 256, 0, ctx->stream>>>(run_start, flags, cidx, count, cap, heads, L.sizes,
+                                                              L.npairs);
+        SQ_LAUNCH_CHECK();
+        // pair counts -> offsets.  Only the first nchunks entries are written;
+        // the scan runs over `count` entries, and the prefix of entry c depends
+        // on entries < c only, so the unwritten tail never reaches a used offset.
+        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, count, nullptr, L.tmp, tmp_bytes));
+        band_total_kernel<<<1, 1, 0, ctx->stream>>>(L.npairs, L.sizes, d_nchunks, d_total);
+        SQ_LAUNCH_CHECK();
+        band_emit_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(
+            K, V, heads, L.sizes, L.npairs, d_nchunks, d_total, log_s, band0, bands, L.chunk_of, pairs_out,
+            pairs_capacity, d_count, ctx->d_err);
+        SQ_LAUNCH_CHECK();
+    }
+    SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_small, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int64_t count = (int64_t)ctx->h_pinned[0];
+    const uint32_t err = (uint32_t)(ctx->h_pinned[1] & 0xffffffffu);
+    *num_pairs_out = count;
+    if (err) return subquad_check(ctx);
+    if (count > pairs_capacity) return SUBQUAD_ERR_CAPACITY;
+    if (count > 1) {
+        const int nb = bits_for((uint64_t)(n - 1));
+        SqArena a2(nullptr);
+        a2.take<uint64_t>(count);
+        a2.take<uint64_t>(count);
+        a2.take<char>(sq_radix_tmp_bytes(count));
+        SQ_TRY(sq_scratch_reserve(ctx, a2.off));
+        SqArena a3(ctx->scratch);
+        uint64_t *k0 = a3.take<uint64_t>(count);
+        uint64_t *k1 = a3.take<uint64_t>(count);
+        void *tmp = a3.take<char>(sq_radix_tmp_bytes(count));
+        const unsigned grid = sq_grid(ctx, count, 256, 8);
+        pairs_to_keys_kernel<<<grid, 256, 0, ctx->stream>>>(pairs_out, count, nb, k0);
+        SQ_LAUNCH_CHECK();
+        bool in_alt = false;
+        SQ_TRY(sq_radix_sort_u64(ctx, k0, k1, count, 0, 2 * nb, &in_alt, tmp, sq_radix_tmp_bytes(count)));
+        keys_to_pairs_kernel<<<grid, 256, 0, ctx->stream>>>(in_alt ? k1 : k0, count, nb, pairs_out);
+        SQ_LAUNCH_CHECK();
+    }
+    return SUBQUAD_OK;
+}

@@ -1,0 +1,231 @@
+// Context, scoring matrix, error reporting and sequence packing.
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.cuh"
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+void sq_note_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+// BLOSUM62 (Henikoff & Henikoff 1992), typed here in the alphabetical code
+// order ACDEFGHIKLMNPQRSTVWY, row = first residue.
+static const int8_t kBlosum62[20][20] = {
+    //  A   C   D   E   F   G   H   I   K   L   M   N   P   Q   R   S   T   V   W   Y
+    {4, 0, -2, -1, -2, 0, -2, -1, -1, -1, -1, -2, -1, -1, -1, 1, 0, 0, -3, -2},           // A
+    {0, 9, -3, -4, -2, -3, -3, -1, -3, -1, -1, -3, -3, -3, -3, -1, -1, -1, -2, -2},       // C
+    {-2, -3, 6, 2, -3, -1, -1, -3, -1, -4, -3, 1, -1, 0, -2, 0, -1, -3, -4, -3},          // D
+    {-1, -4, 2, 5, -3, -2, 0, -3, 1, -3, -2, 0, -1, 2, 0, 0, -1, -2, -3, -2},             // E
+    {-2, -2, -3, -3, 6, -3, -1, 0, -3, 0, 0, -3, -4, -3, -3, -2, -2, -1, 1, 3},           // F
+    {0, -3, -1, -2, -3, 6, -2, -4, -2, -4, -3, 0, -2, -2, -2, 0, -2, -3, -2, -3},         // G
+    {-2, -3, -1, 0, -1, -2, 8, -3, -1, -3, -2, 1, -2, 0, 0, -1, -2, -3, -2, 2},           // H
+    {-1, -1, -3, -3, 0, -4, -3, 4, -3, 2, 1, -3, -3, -3, -3, -2, -1, 3, -3, -1},          // I
+    {-1, -3, -1, 1, -3, -2, -1, -3, 5, -2, -1, 0, -1, 1, 2, 0, -1, -2, -3, -2},           // K
+    {-1, -1, -4, -3, 0, -4, -3, 2, -2, 4, 2, -3, -3, -2, -2, -2, -1, 1, -2, -1},          // L
+    {-1, -1, -3, -2, 0, -3, -2, 1, -1, 2, 5, -2, -2, 0, -1, -1, -1, 1, -1, -1},           // M
+    {-2, -3, 1, 0, -3, 0, 1, -3, 0, -3, -2, 6, -2, 0, 0, 1, 0, -3, -4, -2},               // N
+    {-1, -3, -1, -1, -4, -2, -2, -3, -1, -3, -2, -2, 7, -1, -2, -1, -1, -2, -4, -3},      // P
+    {-1, -3, 0, 2, -3, -2, 0, -3, 1, -2, 0, 0, -1, 5, 1, 0, -1, -2, -2, -1},              // Q
+    {-1, -3, -2, 0, -3, -2, 0, -3, 2, -2, -1, 0, -2, 1, 5, -1, -1, -3, -3, -2},           // R
+    {1, -1, 0, 0, -2, 0, -1, -2, 0, -2, -1, 1, -1, 0, -1, 4, 1, -2, -3, -2},              // S
+    {0, -1, -1, -1, -2, -2, -2, -1, -1, -1, -1, 0, -1, -1, -1, 1, 5, 0, -2, -2},          // T
+    {0, -1, -3, -2, -1, -3, -3, 3, -2, 1, 1, -3, -2, -2, -3, -2, 0, 4, -3, -1},           // V
+    {-3, -2, -4, -3, 1, -2, -2, -3, -3, -2, -1, -4, -4, -2, -3, -3, -2, -3, 11, 2},       // W
+    {-2, -2, -3, -2, 3, -3, 2, -1, -2, -1, -1, -2, -3, -1, -2, -2, -2, -1, 2, 7},         // Y
+};
+
+extern "C" const char *subquad_strerror(int status)
+{
+    switch (status) {
+    case SUBQUAD_OK: return "ok";
+    case SUBQUAD_ERR_ARG: return "invalid argument";
+    case SUBQUAD_ERR_CAPACITY: return "output capacity too small";
+    case SUBQUAD_ERR_CUDA: return g_last_cuda != cudaSuccess ? cudaGetErrorString(g_last_cuda) : "CUDA error";
+    case SUBQUAD_ERR_TIMEOUT: return "device loop exceeded its iteration bound";
+    case SUBQUAD_ERR_NOMEM: return "scratch allocation failed";
+    case SUBQUAD_ERR_INPUT: return "invalid input data (residue code or length)";
+    default: return "unknown status";
+    }
+}
+
+extern "C" int subquad_version(void) { return 100; }
+
+extern "C" int subquad_default_matrix(int8_t *out)
+{
+    if (!out) return SUBQUAD_ERR_ARG;
+    memcpy(out, kBlosum62, sizeof(kBlosum62));
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_create(subquad_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return SUBQUAD_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    SQ_TRY_CUDA(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return SUBQUAD_ERR_ARG;
+    subquad_ctx *ctx = new (std::nothrow) subquad_ctx();
+    if (!ctx) return SUBQUAD_ERR_NOMEM;
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    memcpy(ctx->h_matrix, kBlosum62, sizeof(kBlosum62));
+    ctx->matrix_symmetric = true;
+    SqDeviceGuard guard(ctx);
+    cudaError_t e = guard.ok ? cudaSuccess : cudaErrorInvalidDevice;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_small, 8 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 8 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, 256, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        sq_note_cuda_error(e);
+        subquad_destroy(ctx);
+        return SUBQUAD_ERR_CUDA;
+    }
+    *out = ctx;
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_destroy(subquad_ctx *ctx)
+{
+    if (!ctx) return SUBQUAD_OK;
+    {
+        SqDeviceGuard guard(ctx);
+        if (guard.ok) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->scratch);
+            cudaFree(ctx->d_table);
+            cudaFree(ctx->d_err);
+            cudaFree(ctx->d_small);
+            cudaFreeHost(ctx->h_pinned);
+        }
+    }
+    delete ctx;
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_set_stream(subquad_ctx *ctx, void *cuda_stream)
+{
+    SQ_ENTER(ctx);
+    // scratch is reused in stream order: finish the old stream's work first
+    SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_check(subquad_ctx *ctx)
+{
+    SQ_ENTER(ctx);
+    SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    uint32_t err = (uint32_t)(ctx->h_pinned[0] & 0xffffffffu);
+    SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));
+    if (err & SQ_DEVERR_INPUT) return SUBQUAD_ERR_INPUT;
+    if (err & SQ_DEVERR_TIMEOUT) return SUBQUAD_ERR_TIMEOUT;
+    return SUBQUAD_OK;
+}
+
+extern "C" int64_t subquad_scratch_bytes(const subquad_ctx *ctx) { return ctx ? (int64_t)ctx->scratch_cap : -1; }
+
+extern "C" int64_t subquad_launch_count(const subquad_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int sq_scratch_reserve(subquad_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->scratch_cap) return SUBQUAD_OK;
+    size_t want = bytes + bytes / 4 + (1u << 20);
+    // in-flight work on this stream may still use the old block
+    SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->scratch, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SUBQUAD_ERR_NOMEM;
+    }
+    ctx->scratch_cap = want;
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_set_matrix(subquad_ctx *ctx, const int8_t *matrix)
+{
+    SQ_ENTER(ctx);
+    const int8_t *src = matrix ? matrix : &kBlosum62[0][0];
+    for (int k = 0; k < 400; ++k)
+        if (src[k] < -64 || src[k] > 63) return SUBQUAD_ERR_ARG;
+    memcpy(ctx->h_matrix, src, 400);
+    bool sym = true;
+    for (int a = 0; a < 20; ++a)
+        for (int b = 0; b < 20; ++b) sym = sym && ctx->h_matrix[20 * a + b] == ctx->h_matrix[20 * b + a];
+    ctx->matrix_symmetric = sym;
+    ctx->table_gap_open = -1;  // rebuild the device table on next use
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_pack_stride(int max_len)
+{
+    if (max_len >= 1 && max_len <= 24) return 16;
+    if (max_len >= 1 && max_len <= 30) return 32;
+    return 0;
+}
+
+// One thread per sequence: validate, then write 2 or 4 little-endian 64-bit
+// words with 12 five-bit residues each and the length split over the top
+// nibbles of words 0 and 1.
+template <int WORDS>
+__global__ void pack_kernel(const uint8_t *__restrict__ codes, int code_stride, const uint8_t *__restrict__ lens,
+                            int64_t n, uint64_t *__restrict__ out, uint32_t *err)
+{
+    const int max_len = WORDS == 2 ? 24 : 30;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int L = lens[i];
+        bool bad = L < 1 || L > max_len || L > code_stride;
+        uint64_t w[WORDS];
+#pragma unroll
+        for (int k = 0; k < WORDS; ++k) w[k] = 0;
+        const uint8_t *row = codes + i * (int64_t)code_stride;
+        for (int p = 0; p < L && p < max_len && p < code_stride; ++p) {
+            uint32_t c = row[p];
+            bad |= c >= 20u;
+            uint64_t v = (uint64_t)(c & 31u) << (5 * (p % 12));
+#pragma unroll
+            for (int k = 0; k < WORDS; ++k)
+                if (p / 12 == k) w[k] |= v;
+        }
+        if (bad) {
+            atomicOr(err, SQ_DEVERR_INPUT);
+#pragma unroll
+            for (int k = 0; k < WORDS; ++k) w[k] = 0;
+            L = 0;
+        }
+        w[0] |= (uint64_t)(L & 15) << 60;
+        w[1] |= (uint64_t)(L >> 4) << 60;
+        uint64_t *dst = out + i * WORDS;
+        if (WORDS == 2) {
+            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(w[0], w[1]);
+        } else {
+            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(w[0], w[1]);
+            reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(w[2 % WORDS], w[3 % WORDS]);
+        }
+    }
+}
+
+extern "C" int subquad_pack(subquad_ctx *ctx, const uint8_t *codes, int code_stride, const uint8_t *lens, int64_t n,
+                            int pack_stride, void *packed_out)
+{
+    SQ_ENTER(ctx);
+    if (n < 0 || (n > 0 && (!codes || !lens || !packed_out)) || code_stride < 1) return SUBQUAD_ERR_ARG;
+    if (pack_stride != 16 && pack_stride != 32) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(packed_out) % 16) return SUBQUAD_ERR_ARG;
+    if (n == 0) return SUBQUAD_OK;
+    unsigned grid = sq_grid(ctx, n, 256);
+    if (pack_stride == 16)
+        pack_kernel<2><<<grid, 256, 0, ctx->stream>>>(codes, code_stride, lens, n, (uint64_t *)packed_out, ctx->d_err);
+    else
+        pack_kernel<4><<<grid, 256, 0, ctx->stream>>>(codes, code_stride, lens, n, (uint64_t *)packed_out, ctx->d_err);
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
+}

@@ -1,0 +1,123 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "subquad.h"
+
+// Sticky device-side error bits (OR-ed by kernels, read by subquad_check and
+// by synchronising calls).
+enum : uint32_t {
+    SQ_DEVERR_INPUT = 1u,
+    SQ_DEVERR_TIMEOUT = 2u,
+};
+
+struct subquad_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int8_t h_matrix[400];   // scoring matrix, row = first sequence's residue
+    bool matrix_symmetric = true;
+    int32_t *d_table = nullptr;  // lane-replicated alignment table (see align.cu)
+    int table_gap_open = -1;     // gap-open folded into d_table (-1: not built)
+    uint32_t *d_err = nullptr;   // sticky device error word
+    uint64_t *h_pinned = nullptr;  // pinned host staging, 8 words
+    uint64_t *d_small = nullptr;   // small device scalars (counters), 8 words
+    void *scratch = nullptr;
+    size_t scratch_cap = 0;
+    int64_t launches = 0;  // kernels launched through this context
+};
+
+// Last CUDA error seen by the library on this thread (for diagnostics).
+void sq_note_cuda_error(cudaError_t e);
+
+#define SQ_TRY_CUDA(call)                                  \
+    do {                                                   \
+        cudaError_t sq_e_ = (call);                        \
+        if (sq_e_ != cudaSuccess) {                        \
+            sq_note_cuda_error(sq_e_);                     \
+            return SUBQUAD_ERR_CUDA;                       \
+        }                                                  \
+    } while (0)
+
+#define SQ_TRY(call)                                       \
+    do {                                                   \
+        int sq_s_ = (call);                                \
+        if (sq_s_ != SUBQUAD_OK) return sq_s_;             \
+    } while (0)
+
+#define SQ_LAUNCH_CHECK()                                  \
+    do {                                                   \
+        ++ctx->launches;                                   \
+        SQ_TRY_CUDA(cudaGetLastError());                   \
+    } while (0)
+
+// Makes ctx->device current for the scope of an entry point and restores the
+// caller's device afterwards.
+struct SqDeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit SqDeviceGuard(const subquad_ctx *ctx)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != ctx->device) ok = cudaSetDevice(ctx->device) == cudaSuccess;
+    }
+    ~SqDeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+#define SQ_ENTER(ctx)                                      \
+    if (!(ctx)) return SUBQUAD_ERR_ARG;                    \
+    SqDeviceGuard sq_guard_(ctx);                          \
+    if (!sq_guard_.ok) return SUBQUAD_ERR_CUDA
+
+// Make sure ctx->scratch holds at least `bytes` (stream-ordered reallocation).
+int sq_scratch_reserve(subquad_ctx *ctx, size_t bytes);
+
+// Bump allocator over a scratch block.  With base == nullptr it only measures.
+struct SqArena {
+    char *base;
+    size_t off = 0;
+    explicit SqArena(void *b) : base(static_cast<char *>(b)) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// Grid size for a grid-stride kernel: enough CTAs to fill the machine.
+inline unsigned sq_grid(const subquad_ctx *ctx, int64_t work, int threads, int per_sm = 8)
+{
+    int64_t need = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)ctx->num_sms * per_sm;
+    if (need < 1) need = 1;
+    return (unsigned)(need < cap ? need : cap);
+}
+
+// Packed sequence records (see subquad_pack in subquad.h).
+__device__ __forceinline__ int sq_record_len(uint64_t w0, uint64_t w1)
+{
+    return (int)((w0 >> 60) | ((w1 >> 60) << 4));
+}
+
+// Device-wide primitives (primitives.cu).
+int sq_scan_u32(subquad_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t count, bool inclusive, bool max_op,
+                uint32_t *total_out /* device, nullable */, void *tmp, size_t tmp_bytes);
+int sq_scan_u64(subquad_ctx *ctx, const uint64_t *in, uint64_t *out, int64_t count, uint64_t *total_out,
+                void *tmp, size_t tmp_bytes);
+size_t sq_scan_tmp_bytes(int64_t count);
+// Stable LSD radix sort of (key, value) uint32 pairs on bits [begin_bit, end_bit).
+// Returns via *result_in_alt whether the sorted data ended in the alt buffers.
+int sq_radix_sort_u32(subquad_ctx *ctx, uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                      int64_t count, int begin_bit, int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes);
+// Stable LSD radix sort of uint64 keys on bits [begin_bit, end_bit).
+int sq_radix_sort_u64(subquad_ctx *ctx, uint64_t *keys, uint64_t *keys_alt, int64_t count, int begin_bit,
+                      int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes);
+size_t sq_radix_tmp_bytes(int64_t count);

@@ -1,0 +1,105 @@
+"""The affinity stage end to end on one GPU: pack -> sign -> band/candidates ->
+self-scores -> align -> fuse, through the C ABI (``subquad.Context``).
+
+A ``Workload`` names the method's parameters; a ``Pipeline`` keeps device
+buffers between steps so a step does no allocation once warmed up.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    n: int
+    k: int = 3
+    bands: int = 16
+    rows: int = 4
+    bucket_cap: int = 0
+    gap_open: int = 10
+    gap_extend: int = 1
+    d: int = 64
+    hidden: int = 16
+    pack_stride: int = 16
+
+    @property
+    def hashes(self) -> int:
+        return self.bands * self.rows
+
+
+# 1,000 sequences / 100 families, 3-mers, 64 hashes in 16 bands of 4, no cap,
+# BLOSUM62 open 10 extend 1, d = 64, gate 3-16-1
+TINY = Workload("tiny_1k", 1000)
+# one donor of 1,000,000 sequences, 20,000 families of 25, 50 rare subgroups,
+# the same hashing with buckets capped at 2,048
+DONOR_1M = Workload("donor_1m", 1_000_000, bucket_cap=2048)
+
+
+class Pipeline:
+    def __init__(self, ctx, cfg: Workload):
+        self.ctx = ctx
+        self.cfg = cfg
+        self.torch = ctx.torch
+        self.pairs_buf = None
+        self.sw_buf = None
+        self.fused_buf = None
+
+    def upload(self, rep, a, b, emb, params):
+        """Host numpy inputs -> device tensors (not part of a step)."""
+        torch, dev = self.torch, self.ctx.device
+        return dict(codes=torch.from_numpy(rep.codes).to(dev), lens=torch.from_numpy(rep.lens).to(dev),
+                    a=torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev),
+                    b=torch.from_numpy(np.ascontiguousarray(b).view(np.int32)).to(dev),
+                    emb=torch.from_numpy(np.ascontiguousarray(emb, dtype=np.float32)).to(dev),
+                    params=torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).to(dev))
+
+    def _ensure(self, m: int):
+        torch, dev = self.torch, self.ctx.device
+        if self.sw_buf is None or self.sw_buf.shape[0] < m:
+            self.sw_buf = torch.empty((m,), dtype=torch.int32, device=dev)
+            self.fused_buf = torch.empty((m,), dtype=torch.float32, device=dev)
+
+    def forward(self, x, marks=None):
+        """One pass of the whole hot path on device-resident inputs.
+
+        ``marks``, when given, is a callable invoked with a stage name after each
+        stage is queued (the benchmark records CUDA events there)."""
+        cfg, ctx = self.cfg, self.ctx
+        mark = marks or (lambda name: None)
+        n = int(x["lens"].shape[0])
+        packed = ctx.pack(x["codes"], x["lens"], cfg.pack_stride)
+        mark("pack")
+        sig = ctx.sign(packed, n, cfg.k, x["a"], x["b"], cfg.bands, cfg.rows)
+        mark("sign")
+        if self.pairs_buf is None:
+            self.pairs_buf = self.torch.empty((max(1 << 16, 8 * n), 2), dtype=self.torch.int32, device=ctx.device)
+        pairs = ctx.band_candidates(sig, n, cfg.bands, cfg.rows, cfg.bucket_cap, out=self.pairs_buf)
+        if pairs.data_ptr() != self.pairs_buf.data_ptr():
+            self.pairs_buf = pairs  # grown after a capacity retry
+        mark("band")
+        m = int(pairs.shape[0])
+        self._ensure(m)
+        self_sc = ctx.self_scores(packed, cfg.gap_open, cfg.gap_extend)
+        mark("self")
+        sw = ctx.align_score(packed, pairs, cfg.gap_open, cfg.gap_extend, out=self.sw_buf[:m])
+        mark("align")
+        fused = ctx.fuse_forward(pairs, sw, self_sc, packed, x["emb"], x["params"], cfg.hidden,
+                                 out=self.fused_buf[:m])
+        mark("fuse")
+        return dict(packed=packed, sig=sig, pairs=pairs, self=self_sc, sw=sw, fused=fused)
+
+    def forward_numpy(self, rep, a, b, emb, params):
+        out = self.forward(self.upload(rep, a, b, emb, params))
+        self.ctx.check()
+        return dict(sig=out["sig"].cpu().numpy().view(np.uint32), pairs=out["pairs"].cpu().numpy().view(np.uint32),
+                    self=out["self"].cpu().numpy(), sw=out["sw"].cpu().numpy(), fused=out["fused"].cpu().numpy())
+
+
+def cells_of(lens: np.ndarray, pairs: np.ndarray) -> int:
+    """Dynamic-programming cells of a pair list: sum of L_i * L_j."""
+    if pairs.shape[0] == 0:
+        return 0
+    return int((lens[pairs[:, 0]].astype(np.int64) * lens[pairs[:, 1]].astype(np.int64)).sum())

@@ -1,0 +1,261 @@
+"""Python binding of libsubquad (the C ABI declared in include/subquad.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+PyTorch supplies device memory and the stream; tensors are passed to the C
+entry points as raw device pointers.  There is no CPU path: if the shared
+library is missing or fails to load, every call raises.
+
+Two layers:
+* ``lib()`` -- the ctypes handle, with ``subquad_*`` functions under their C
+  names and signatures;
+* ``Context`` -- owns a ``subquad_ctx`` bound to a device and a stream, with one
+  method per entry point (``ctx.sign(...)`` calls ``subquad_sign``), allocating
+  outputs as torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsubquad.so")
+
+SUBQUAD_OK = 0
+SUBQUAD_ERR_ARG = -1
+SUBQUAD_ERR_CAPACITY = -2
+SUBQUAD_ERR_CUDA = -3
+SUBQUAD_ERR_TIMEOUT = -4
+SUBQUAD_ERR_NOMEM = -5
+SUBQUAD_ERR_INPUT = -6
+
+_c = ctypes
+_P = _c.c_void_p
+_I64 = _c.c_int64
+
+# name -> (restype, argtypes); every function declared in include/subquad.h
+SIGNATURES = {
+    "subquad_strerror": (_c.c_char_p, [_c.c_int]),
+    "subquad_version": (_c.c_int, []),
+    "subquad_create": (_c.c_int, [_c.POINTER(_P), _c.c_int, _P]),
+    "subquad_destroy": (_c.c_int, [_P]),
+    "subquad_set_stream": (_c.c_int, [_P, _P]),
+    "subquad_check": (_c.c_int, [_P]),
+    "subquad_scratch_bytes": (_I64, [_P]),
+    "subquad_launch_count": (_I64, [_P]),
+    "subquad_default_matrix": (_c.c_int, [_P]),
+    "subquad_set_matrix": (_c.c_int, [_P, _P]),
+    "subquad_pack_stride": (_c.c_int, [_c.c_int]),
+    "subquad_pack": (_c.c_int, [_P, _P, _c.c_int, _P, _I64, _c.c_int, _P]),
+    "subquad_sign": (_c.c_int, [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _c.c_int, _P, _P, _P]),
+    "subquad_band_candidates": (_c.c_int, [_P, _P, _I64, _c.c_int, _c.c_int, _c.c_int32, _P, _I64,
+                                           _c.POINTER(_I64)]),
+    "subquad_align_score": (_c.c_int, [_P, _P, _c.c_int, _P, _I64, _c.c_int, _c.c_int, _P]),
+    "subquad_self_scores": (_c.c_int, [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _P]),
+    "subquad_fuse_forward": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P, _c.c_int, _P, _P]),
+}
+
+_lib = None
+
+
+class SubquadError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        text = lib().subquad_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {text} (status {status})")
+
+
+def lib():
+    """Load libsubquad.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libsubquad.so not found at {LIB_PATH}; build it with __graft_entry__.build()")
+    handle = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(handle, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = handle
+    return handle
+
+
+def _check(status: int, where: str) -> None:
+    if status != SUBQUAD_OK:
+        raise SubquadError(status, where)
+
+
+def default_matrix():
+    """The library's built-in BLOSUM62 as a list of 400 ints (host-only)."""
+    buf = (ctypes.c_int8 * 400)()
+    _check(lib().subquad_default_matrix(ctypes.cast(buf, _P)), "subquad_default_matrix")
+    return list(buf)
+
+
+def pack_stride(max_len: int) -> int:
+    return int(lib().subquad_pack_stride(max_len))
+
+
+def _ptr(t):
+    return None if t is None else _P(t.data_ptr())
+
+
+class Context:
+    """A subquad_ctx bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        handle = _P()
+        _check(lib().subquad_create(ctypes.byref(handle), device, _P(stream.cuda_stream)), "subquad_create")
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().subquad_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- context ---------------------------------------------------------------
+    def set_stream(self, stream):
+        _check(lib().subquad_set_stream(self.handle, _P(stream.cuda_stream)), "subquad_set_stream")
+        self.stream = stream
+
+    def check(self):
+        _check(lib().subquad_check(self.handle), "subquad_check")
+
+    def scratch_bytes(self) -> int:
+        return int(lib().subquad_scratch_bytes(self.handle))
+
+    def launch_count(self) -> int:
+        return int(lib().subquad_launch_count(self.handle))
+
+    def set_matrix(self, matrix=None):
+        if matrix is None:
+            _check(lib().subquad_set_matrix(self.handle, None), "subquad_set_matrix")
+            return
+        buf = (ctypes.c_int8 * 400)(*[int(v) for v in list(matrix)])
+        _check(lib().subquad_set_matrix(self.handle, ctypes.cast(buf, _P)), "subquad_set_matrix")
+
+    # -- helpers ---------------------------------------------------------------
+    def _dev(self, t, dtype):
+        t = t.to(self.device)
+        if t.dtype != dtype:
+            raise TypeError(f"expected {dtype}, got {t.dtype}")
+        return t.contiguous()
+
+    def _empty(self, shape, dtype):
+        return self.torch.empty(shape, dtype=dtype, device=self.device)
+
+    # -- entry points ----------------------------------------------------------
+    def pack(self, codes, lens, stride: int):
+        """codes uint8 [n, code_stride], lens uint8 [n] -> packed uint8 [n, stride]."""
+        torch = self.torch
+        codes = self._dev(codes, torch.uint8)
+        lens = self._dev(lens, torch.uint8)
+        n = int(lens.shape[0])
+        out = self._empty((n, stride), torch.uint8)
+        _check(lib().subquad_pack(self.handle, _ptr(codes), int(codes.shape[1]) if n else 1, _ptr(lens), n, stride,
+                                  _ptr(out)), "subquad_pack")
+        return out
+
+    def sign(self, packed, n: int, k: int, a, b, bands: int, rows: int):
+        """-> int32 [bands, n, rows] (uint32 bit patterns)."""
+        torch = self.torch
+        a = self._dev(a, torch.int32)
+        b = self._dev(b, torch.int32)
+        out = self._empty((bands, n, rows), torch.int32)
+        _check(lib().subquad_sign(self.handle, _ptr(packed), int(packed.shape[1]), n, k, bands, rows, _ptr(a),
+                                  _ptr(b), _ptr(out)), "subquad_sign")
+        return out
+
+    def band_candidates(self, sig, n: int, bands: int, rows: int, bucket_cap: int = 0, capacity: int | None = None,
+                        out=None):
+        """-> int32 [|C|, 2] sorted candidate pairs.  Retries once with the
+        required capacity when the first guess is too small."""
+        torch = self.torch
+        if out is None:
+            capacity = capacity if capacity is not None else max(1 << 16, 8 * n)
+            out = self._empty((capacity, 2), torch.int32)
+        else:
+            capacity = int(out.shape[0])
+        count = _I64(0)
+        st = lib().subquad_band_candidates(self.handle, _ptr(sig), n, bands, rows, bucket_cap, _ptr(out), capacity,
+                                           ctypes.byref(count))
+        if st == SUBQUAD_ERR_CAPACITY:
+            out = self._empty((int(count.value), 2), torch.int32)
+            st = lib().subquad_band_candidates(self.handle, _ptr(sig), n, bands, rows, bucket_cap, _ptr(out),
+                                               int(count.value), ctypes.byref(count))
+        _check(st, "subquad_band_candidates")
+        return out[: int(count.value)]
+
+    def align_score(self, packed, pairs, gap_open: int = 10, gap_extend: int = 1, out=None):
+        torch = self.torch
+        m = int(pairs.shape[0])
+        out = self._empty((m,), torch.int32) if out is None else out
+        _check(lib().subquad_align_score(self.handle, _ptr(packed), int(packed.shape[1]), _ptr(pairs), m, gap_open,
+                                         gap_extend, _ptr(out)), "subquad_align_score")
+        return out
+
+    def self_scores(self, packed, gap_open: int = 10, gap_extend: int = 1, out=None):
+        torch = self.torch
+        n = int(packed.shape[0])
+        out = self._empty((n,), torch.int32) if out is None else out
+        _check(lib().subquad_self_scores(self.handle, _ptr(packed), int(packed.shape[1]), n, gap_open, gap_extend,
+                                         _ptr(out)), "subquad_self_scores")
+        return out
+
+    def fuse_forward(self, pairs, sw, self_sc, packed, emb, params, hidden: int, want_alpha: bool = False,
+                     out=None, alpha=None):
+        torch = self.torch
+        m = int(pairs.shape[0])
+        emb = self._dev(emb, torch.float32)
+        params = self._dev(params, torch.float32)
+        out = self._empty((m,), torch.float32) if out is None else out
+        if want_alpha and alpha is None:
+            alpha = self._empty((m,), torch.float32)
+        _check(lib().subquad_fuse_forward(self.handle, _ptr(pairs), m, _ptr(sw), _ptr(self_sc), _ptr(packed),
+                                          int(packed.shape[1]), _ptr(emb), int(emb.shape[1]), _ptr(params), hidden,
+                                          _ptr(out), _ptr(alpha) if want_alpha else None), "subquad_fuse_forward")
+        return (out, alpha) if want_alpha else out
+
+
+# module-level names matching the C entry points, taking a Context first
+def subquad_pack(ctx: Context, *a, **k):
+    return ctx.pack(*a, **k)
+
+
+def subquad_sign(ctx: Context, *a, **k):
+    return ctx.sign(*a, **k)
+
+
+def subquad_band_candidates(ctx: Context, *a, **k):
+    return ctx.band_candidates(*a, **k)
+
+
+def subquad_align_score(ctx: Context, *a, **k):
+    return ctx.align_score(*a, **k)
+
+
+def subquad_self_scores(ctx: Context, *a, **k):
+    return ctx.self_scores(*a, **k)
+
+
+def subquad_fuse_forward(ctx: Context, *a, **k):
+    return ctx.fuse_forward(*a, **k)

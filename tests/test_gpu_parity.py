@@ -1,0 +1,323 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, element by
+element, on seeded inputs.  Signatures, candidate sets and alignment scores
+must be bit-exact; fused scores must satisfy |x - y| <= 1e-5 * max(|y|, 1e-3)
+against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2602_17330_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FUSED_RTOL = 1e-5
+FUSED_FLOOR = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    from paper_2602_17330_gb300 import _build, subquad
+
+    _build.build()
+    c = subquad.Context(0)
+    yield c
+    c.close()
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def gpu_sig(ctx, torch, rep, k, a, b, bands, rows, stride):
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), stride)
+    sig = ctx.sign(packed, rep.n, k, torch.from_numpy(a.view(np.int32)), torch.from_numpy(b.view(np.int32)),
+                   bands, rows)
+    return packed, sig
+
+
+def oracle_sig_layout(sig_oracle, bands, rows):
+    n = sig_oracle.shape[0]
+    return sig_oracle.reshape(n, bands, rows).transpose(1, 0, 2)
+
+
+def assert_fused_close(got, want):
+    err = np.abs(got.astype(np.float64) - want)
+    bound = FUSED_RTOL * np.maximum(np.abs(want), FUSED_FLOOR)
+    assert (err <= bound).all(), f"max err {err.max():.3e}, worst ratio {(err / bound).max():.3f}"
+
+
+# --------------------------------------------------------------------------
+# (a1) signatures
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6])
+def test_sign_bitexact_tiny(ctx, torch, oracle_mod, k):
+    rep = synth.tiny_repertoire()
+    a, b = synth.hash_coefficients(64, seed=k)
+    _, sig = gpu_sig(ctx, torch, rep, k, a, b, 16, 4, 16)
+    want = oracle_sig_layout(oracle_mod.sign(rep.codes, rep.lens, k, a, b), 16, 4)
+    assert (to_np(sig).view(np.uint32) == want).all()
+    ctx.check()
+
+
+@pytest.mark.parametrize("bands,rows", [(32, 4), (16, 2), (8, 3), (5, 7), (64, 1)])
+def test_sign_bitexact_long_sequences_stride32(ctx, torch, oracle_mod, bands, rows):
+    rep = synth.zipf_repertoire(3000, seed=1, hi=200)
+    assert rep.lens.max() > 24
+    a, b = synth.hash_coefficients(bands * rows, seed=2)
+    _, sig = gpu_sig(ctx, torch, rep, 3, a, b, bands, rows, 32)
+    want = oracle_sig_layout(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), bands, rows)
+    assert (to_np(sig).view(np.uint32) == want).all()
+
+
+def test_sign_extreme_coefficients(ctx, torch, oracle_mod):
+    rep = synth.tiny_repertoire()
+    P = (1 << 31) - 1
+    a = np.array([P - 1, P - 2, 1, 2, (1 << 30) + 7, 123457, P - 1, 1], dtype=np.uint32)
+    b = np.array([P - 1, 0, P - 1, 0, P - 2, 7, 0, 0], dtype=np.uint32)
+    _, sig = gpu_sig(ctx, torch, rep, 6, a, b, 2, 4, 16)
+    want = oracle_sig_layout(oracle_mod.sign(rep.codes, rep.lens, 6, a, b), 2, 4)
+    assert (to_np(sig).view(np.uint32) == want).all()
+
+
+def test_sequence_shorter_than_k_gets_empty_signature(ctx, torch):
+    codes, lens = synth.encode(["CA", "CASF"])
+    a, b = synth.hash_coefficients(8)
+    _, sig = gpu_sig(ctx, torch, synth.Repertoire(codes, lens, np.zeros(2, np.int32), np.zeros(2, np.int32),
+                                                  np.ones(20) / 20), 3, a, b, 2, 4, 16)
+    s = to_np(sig).view(np.uint32)
+    assert (s[:, 0, :] == 0xFFFFFFFF).all()
+    assert (s[:, 1, :] != 0xFFFFFFFF).all()
+
+
+def test_invalid_codes_are_reported(ctx, torch):
+    from paper_2602_17330_gb300 import subquad
+
+    codes, lens = synth.encode(["CASSF", "CASSF"])
+    codes[1, 2] = 25
+    ctx.pack(torch.from_numpy(codes), torch.from_numpy(lens), 16)
+    with pytest.raises(subquad.SubquadError) as ei:
+        ctx.check()
+    assert ei.value.status == subquad.SUBQUAD_ERR_INPUT
+    ctx.check()  # the sticky error was cleared
+    bad_len = lens.copy()
+    bad_len[0] = 25  # > 24 does not fit the 16-byte record
+    ctx.pack(torch.from_numpy(codes[:1]), torch.from_numpy(bad_len[:1]), 16)
+    with pytest.raises(subquad.SubquadError):
+        ctx.check()
+
+
+# --------------------------------------------------------------------------
+# (a2) candidates
+# --------------------------------------------------------------------------
+
+def gpu_candidates_from_sig(ctx, torch, sig_np, bands, rows, cap):
+    """sig_np: uint32 [n, H] in the oracle's layout."""
+    n = sig_np.shape[0]
+    lay = np.ascontiguousarray(oracle_sig_layout(sig_np, bands, rows)).view(np.int32)
+    sig = torch.from_numpy(lay).to(ctx.device)
+    return to_np(ctx.band_candidates(sig, n, bands, rows, cap)).view(np.uint32)
+
+
+@pytest.mark.parametrize("cap", [0, 1, 2, 3, 7])
+def test_candidates_bitexact_planted_buckets(ctx, torch, oracle_mod, cap):
+    rng = np.random.default_rng(100 + cap)
+    n, bands, rows = 3000, 5, 3
+    sig = rng.integers(0, 4, (n, bands * rows)).astype(np.uint32)  # buckets of every size
+    sig[:, 1::3] += np.uint32((1 << 31) - 10)
+    got = gpu_candidates_from_sig(ctx, torch, sig, bands, rows, cap)
+    want = oracle_mod.candidates(sig, bands, rows, cap)
+    assert got.shape == want.shape and (got == want).all()
+
+
+def test_candidates_bitexact_tiny(ctx, torch, oracle_mod):
+    rep = synth.tiny_repertoire()
+    a, b = synth.hash_coefficients(64)
+    _, sig = gpu_sig(ctx, torch, rep, 3, a, b, 16, 4, 16)
+    got = to_np(ctx.band_candidates(sig, rep.n, 16, 4, 0)).view(np.uint32)
+    want = oracle_mod.candidates(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), 16, 4, 0)
+    assert got.shape == want.shape and (got == want).all()
+
+
+@pytest.mark.parametrize("cap", [0, 2048, 4])
+def test_candidates_bitexact_donor_20k(ctx, torch, oracle_mod, cap):
+    rep = synth.donor_repertoire(20_000, seed=3)
+    a, b = synth.hash_coefficients(64, seed=3)
+    _, sig = gpu_sig(ctx, torch, rep, 3, a, b, 16, 4, 16)
+    got = to_np(ctx.band_candidates(sig, rep.n, 16, 4, cap)).view(np.uint32)
+    want = oracle_mod.candidates(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), 16, 4, cap)
+    assert got.shape == want.shape and (got == want).all()
+
+
+def test_candidates_capacity_error_reports_required_count(ctx, torch, oracle_mod):
+    from paper_2602_17330_gb300 import subquad
+    import ctypes
+
+    rep = synth.tiny_repertoire()
+    a, b = synth.hash_coefficients(64)
+    _, sig = gpu_sig(ctx, torch, rep, 3, a, b, 16, 4, 16)
+    want = oracle_mod.candidates(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), 16, 4, 0)
+    out = torch.empty((5, 2), dtype=torch.int32, device=ctx.device)
+    cnt = ctypes.c_int64(0)
+    st = subquad.lib().subquad_band_candidates(ctx.handle, ctypes.c_void_p(sig.data_ptr()), rep.n, 16, 4, 0,
+                                                ctypes.c_void_p(out.data_ptr()), 5, ctypes.byref(cnt))
+    assert st == subquad.SUBQUAD_ERR_CAPACITY and cnt.value == want.shape[0]
+
+
+def test_candidates_degenerate_inputs(ctx, torch):
+    one = torch.zeros((4, 1, 4), dtype=torch.int32, device=ctx.device)
+    assert ctx.band_candidates(one, 1, 4, 4, 0).shape[0] == 0
+    same = torch.zeros((2, 50, 2), dtype=torch.int32, device=ctx.device)  # one bucket per band
+    got = to_np(ctx.band_candidates(same, 50, 2, 2, 0))
+    assert got.shape[0] == 50 * 49 // 2
+    got = to_np(ctx.band_candidates(same, 50, 2, 2, 10))
+    assert got.shape[0] == 5 * 45
+
+
+# --------------------------------------------------------------------------
+# (a3) alignment
+# --------------------------------------------------------------------------
+
+def test_align_all_pairs_tiny_bitexact(ctx, torch, oracle_mod):
+    rep = synth.tiny_repertoire()
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 16)
+    iu, ju = np.triu_indices(rep.n, 1)
+    pairs = np.stack([iu, ju], 1).astype(np.uint32)
+    got = to_np(ctx.align_score(packed, torch.from_numpy(pairs.view(np.int32)).to(ctx.device)))
+    want = oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)
+    assert (got == want).all()
+    self_got = to_np(ctx.self_scores(packed))
+    assert (self_got == oracle_mod.self_scores(rep.codes, rep.lens)).all()
+
+
+@pytest.mark.parametrize("m", [1, 31, 33, 1000, 4097])
+def test_align_ragged_counts_stride32(ctx, torch, oracle_mod, m):
+    rep = synth.zipf_repertoire(4000, seed=5, hi=100)
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 32)
+    rng = np.random.default_rng(m)
+    pairs = rng.integers(0, rep.n, (m, 2)).astype(np.uint32)
+    pairs[0] = [int(np.argmax(rep.lens)), int(np.argmin(rep.lens))]
+    got = to_np(ctx.align_score(packed, torch.from_numpy(pairs.view(np.int32)).to(ctx.device)))
+    assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)).all()
+    assert (to_np(ctx.self_scores(packed)) == oracle_mod.self_scores(rep.codes, rep.lens)).all()
+
+
+@pytest.mark.parametrize("o,e", [(10, 1), (0, 0), (3, 3), (11, 1), (1000, 1000), (5, 2)])
+def test_align_gap_parameters(ctx, torch, oracle_mod, o, e):
+    rep = synth.tiny_repertoire(seed=2)
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 16)
+    rng = np.random.default_rng(o * 7 + e)
+    pairs = rng.integers(0, rep.n, (3000, 2)).astype(np.uint32)
+    got = to_np(ctx.align_score(packed, torch.from_numpy(pairs.view(np.int32)).to(ctx.device), o, e))
+    assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs, o, e)).all()
+
+
+def test_align_custom_matrices(ctx, torch, oracle_mod):
+    rep = synth.tiny_repertoire(seed=4)
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 16)
+    rng = np.random.default_rng(9)
+    pairs = rng.integers(0, rep.n, (2000, 2)).astype(np.uint32)
+    tp = torch.from_numpy(pairs.view(np.int32)).to(ctx.device)
+    try:
+        ident = np.full((20, 20), -64, dtype=np.int32)
+        np.fill_diagonal(ident, 1)
+        ctx.set_matrix(ident.ravel())
+        got = to_np(ctx.align_score(packed, tp, 1000, 1000))
+        assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs, 1000, 1000, ident)).all()
+        asym = rng.integers(-6, 9, (20, 20)).astype(np.int32)  # not symmetric: no operand swap allowed
+        ctx.set_matrix(asym.ravel())
+        got = to_np(ctx.align_score(packed, tp, 4, 1))
+        assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs, 4, 1, asym)).all()
+    finally:
+        ctx.set_matrix(None)
+    got = to_np(ctx.align_score(packed, tp))
+    assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)).all()
+
+
+def test_align_empty(ctx, torch):
+    rep = synth.tiny_repertoire()
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 16)
+    pairs = torch.zeros((0, 2), dtype=torch.int32, device=ctx.device)
+    assert ctx.align_score(packed, pairs).shape[0] == 0
+
+
+# --------------------------------------------------------------------------
+# (a4) fusion
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,hidden,scale", [(64, 16, False), (128, 32, True), (4, 1, True), (36, 64, False)])
+def test_fuse_forward_within_tolerance(ctx, torch, oracle_mod, d, hidden, scale):
+    rep = synth.tiny_repertoire()
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 16)
+    rng = np.random.default_rng(d)
+    pairs = np.unique(np.sort(rng.integers(0, rep.n, (20_001, 2)), axis=1), axis=0)
+    pairs = pairs[pairs[:, 0] < pairs[:, 1]].astype(np.uint32)
+    emb = synth.family_embeddings(rep.family, d, seed=d)
+    if scale:
+        emb = np.ascontiguousarray(emb * rng.uniform(0.2, 5.0, (rep.n, 1)).astype(np.float32))
+    params = synth.gate_parameters(hidden, seed=hidden)
+    tp = torch.from_numpy(pairs.view(np.int32)).to(ctx.device)
+    sw = ctx.align_score(packed, tp)
+    self_sc = ctx.self_scores(packed)
+    fused, alpha = ctx.fuse_forward(tp, sw, self_sc, packed, torch.from_numpy(emb), torch.from_numpy(params), hidden,
+                                    want_alpha=True)
+    want = oracle_mod.fuse_forward(pairs, to_np(sw), to_np(self_sc), rep.lens, emb, params, hidden)
+    assert_fused_close(to_np(fused), want["fused"])
+    assert_fused_close(to_np(alpha), want["alpha"])
+
+
+# --------------------------------------------------------------------------
+# full-size workload: one donor of 1,000,000 sequences, as the benchmark runs it
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def donor_1m(ctx, torch, oracle_mod):
+    from paper_2602_17330_gb300 import pipeline
+
+    rep = synth.donor_repertoire(1_000_000, seed=0)
+    cfg = pipeline.DONOR_1M
+    a, b = synth.hash_coefficients(cfg.hashes, seed=0)
+    emb = synth.unit_embeddings(rep.n, cfg.d, seed=0)
+    params = synth.gate_parameters(cfg.hidden, seed=0)
+    run = pipeline.Pipeline(ctx, cfg)
+    out = run.forward_numpy(rep, a, b, emb, params)
+    return dict(rep=rep, a=a, b=b, emb=emb, params=params, out=out, cfg=cfg)
+
+
+def test_full_size_signatures_sampled(donor_1m, oracle_mod):
+    d = donor_1m
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(d["rep"].n, 20_000, replace=False))
+    want = oracle_mod.sign(d["rep"].codes[idx], d["rep"].lens[idx], 3, d["a"], d["b"])
+    got = d["out"]["sig"][:, idx, :].transpose(1, 0, 2).reshape(len(idx), -1)
+    assert (got == want).all()
+
+
+def test_full_size_candidates_exact(donor_1m, oracle_mod):
+    d = donor_1m
+    sig = oracle_mod.sign(d["rep"].codes, d["rep"].lens, 3, d["a"], d["b"])
+    want = oracle_mod.candidates(sig, d["cfg"].bands, d["cfg"].rows, d["cfg"].bucket_cap)
+    got = d["out"]["pairs"]
+    assert got.shape == want.shape and (got == want).all()
+
+
+def test_full_size_scores_and_fusion_sampled(donor_1m, oracle_mod):
+    d = donor_1m
+    rep, out = d["rep"], d["out"]
+    rng = np.random.default_rng(1)
+    sel = np.sort(rng.choice(out["pairs"].shape[0], 30_000, replace=False))
+    pairs = out["pairs"][sel]
+    assert (out["sw"][sel] == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)).all()
+    seqs = np.unique(pairs.ravel())
+    want_self = oracle_mod.sw_pairs(rep.codes, rep.lens, np.stack([seqs, seqs], 1))
+    assert (out["self"][seqs] == want_self).all()
+    want = oracle_mod.fuse_forward(pairs, out["sw"][sel], out["self"], rep.lens, d["emb"], d["params"],
+                                   d["cfg"].hidden)
+    assert_fused_close(out["fused"][sel], want["fused"])
