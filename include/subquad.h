@@ -184,6 +184,66 @@ int subquad_fuse_forward(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, con
                          const int32_t *self_scores, const void *packed, int pack_stride, const float *emb, int d,
                          const float *gate_params, int hidden, float *fused_out, float *alpha_out);
 
+/* ------------------------------------------------------------------------ */
+/* (a5) Gate training -- the meta-network of Eq. fine_tune is trained end to */
+/* end (Eq. momentum names the paper's optimiser; Adam is used here); the    */
+/* appendix's finite-difference gradient is the check.  Objective: weighted  */
+/* binary cross-entropy of the fused score against family-match labels,      */
+/* each pair weighted by the inverse frequency of its subgroup.              */
+/* ------------------------------------------------------------------------ */
+
+/* label_out[p] = 1 if family[i] == family[j] >= 0 else 0; group_out[p] =
+ * subgroup[i] if it is nonzero else subgroup[j].  family, subgroup: device
+ * int32 [n]; label_out: device uint8 [m]; group_out: device int32 [m]. */
+int subquad_pair_labels(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *family,
+                        const int32_t *subgroup, uint8_t *label_out, int32_t *group_out);
+
+/* weight_out[p] = (1 / pi_g) scaled so the weights sum to m, where g =
+ * group[p] and pi_g is the fraction of the m pairs in group g.  group: device
+ * int32 [m] with values in [0, num_groups) (others set SUBQUAD_ERR_INPUT in
+ * the sticky error); weight_out: device float [m]; 1 <= num_groups <= 4096. */
+int subquad_pair_weights(subquad_ctx *ctx, const int32_t *group, int64_t m, int num_groups, float *weight_out);
+
+/* loss_out (device float [1]) = sum_p w_p l_p / sum_p w_p with
+ * l_p = -(y log q + (1-y) log(1-q)), q = clamp(fused, 1e-7, 1-1e-7);
+ * dL_dfused (device float [m], nullable) = w_p (q - y) / (q (1 - q)) / sum w
+ * where fused lies strictly inside the clamp, else 0.  The sums are reduced in
+ * FP64 in a fixed order (deterministic). */
+int subquad_bce_loss(subquad_ctx *ctx, const float *fused, const uint8_t *label, const float *weight, int64_t m,
+                     float *loss_out, float *dL_dfused);
+
+/* Index of a pair list by its first and by its second member, used by
+ * subquad_fuse_backward to reduce embedding gradients without atomics:
+ * perm_i (device uint32 [m]) lists pair indices ordered by first member (ties
+ * by pair index) and off_i (device uint32 [n+1]) delimits each member's run;
+ * perm_j / off_j the same for the second member.  Build it once per pair list. */
+int subquad_pair_index(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, int64_t n, uint32_t *perm_i,
+                       uint32_t *off_i, uint32_t *perm_j, uint32_t *off_j);
+
+/* Adjoint of subquad_fuse_forward for dL/dfused (device float [m]) given per
+ * pair; emb is device float [n][d] as in the forward.  Recomputes
+ * each pair's hidden activations (nothing per pair is stored by the forward)
+ * and writes grad_params (device float [5*hidden+1], same layout as
+ * gate_params; overwritten) and, when grad_emb is not NULL, grad_emb (device
+ * float [n][d]; overwritten, rows of sequences in no pair become 0), which
+ * needs the pair index of subquad_pair_index.  The alignment channel is
+ * integer and not differentiated; the ReLU subgradient at 0 is 0.  Parameter
+ * gradients are summed per thread with compensated FP32 and across threads
+ * and blocks in FP64 in a fixed order; embedding gradients per row in a
+ * fixed order: results are bitwise reproducible. */
+int subquad_fuse_backward(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                          const int32_t *self_scores, const void *packed, int pack_stride, const float *emb, int64_t n,
+                          int d, const float *gate_params, int hidden, const float *dL_dfused, const uint32_t *perm_i,
+                          const uint32_t *off_i, const uint32_t *perm_j, const uint32_t *off_j, float *grad_params,
+                          float *grad_emb);
+
+/* One bias-corrected Adam step (t >= 1) on count float parameters in place:
+ * m1 = b1 m1 + (1-b1) g; m2 = b2 m2 + (1-b2) g^2;
+ * param -= lr (m1 / (1 - b1^t)) / (sqrt(m2 / (1 - b2^t)) + eps).
+ * All pointers device float [count]. */
+int subquad_adam_step(subquad_ctx *ctx, float *param, const float *grad, float *m1, float *m2, int64_t count, int t,
+                      float lr, float beta1, float beta2, float eps);
+
 #ifdef __cplusplus
 }
 #endif

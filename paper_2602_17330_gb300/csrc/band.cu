@@ -1,24 +1,28 @@
 // (a2) LSH banding, candidate emission and deduplication (Algorithm 1,
 // preprocessing: "build MinHash index; generate candidate list CAND").
 //
-// Per group of bands (all bands at once unless the keys would overflow 32
-// bits):
+// Per group of bands (all bands at once unless the keys would overflow):
 //  1. insert every (band, sequence) key -- the exact R-tuple -- into a
 //     per-band open-addressing table whose slots hold the id of the first
 //     inserter; equal keys meet at one slot, so the slot index is an exact
-//     bucket id;
-//  2. stable radix sort of (band * S + slot, id): each bucket becomes one
-//     contiguous run with its members in ascending id order (the contiguous
-//     bucket blocks of the paper's index);
+//     bucket id; count the members of every bucket;
+//  2. keep only members of buckets with >= 2 members (on the 1M-sequence
+//     donor about 10% of the keys) and radix-sort them by (bucket, id): each
+//     bucket becomes one contiguous run with its members in ascending id order
+//     (the contiguous bucket blocks of the paper's index);
 //  3. run starts by a max-scan of head positions; rank in bucket = position -
-//     run start; chunk = rank / cap; every element records, per band, the sorted
-//     position of its chunk head (its "chunk id" G[i][b]);
+//     run start; chunk = rank / cap; every kept element records, per band, the
+//     sorted position of its chunk head (its chunk id G[i][b]; singletons keep
+//     a sentinel that matches nothing);
 //  4. chunks with >= 2 members are compacted and their pair counts scanned;
 //  5. each warp takes 32 consecutive pair indices, finds their chunks, decodes
 //     (u, v) and keeps pair (i, j) only if no earlier band already puts i and j
 //     in one chunk (first-band ownership), so every pair of C is emitted once;
 //  6. after all groups: read back |C| (the call's only host synchronisation),
 //     then radix-sort the pairs into lexicographic order.
+// Element counts produced on the device (kept keys, chunks, raw pairs) are
+// consumed on the device: the kernels after them are sized for the upper
+// bound and read the actual count.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -26,6 +30,7 @@
 namespace {
 
 constexpr uint32_t kEmpty = 0xffffffffu;
+constexpr uint32_t kNoChunk = 0xffffffffu;  // chunk id of a singleton (matches nothing)
 
 __device__ __forceinline__ uint32_t mix32(uint32_t h)
 {
@@ -63,11 +68,12 @@ __device__ __forceinline__ bool key_equal(const uint32_t *__restrict__ p, int ro
     return eq;
 }
 
-// Step 1: exact bucket id (= table slot) per (band, sequence).
+// Step 1: exact bucket id (= table slot) per (band, sequence), and the number
+// of members of every bucket.
 __global__ void __launch_bounds__(256) band_insert_kernel(const uint32_t *__restrict__ sig, int64_t n, int rows,
                                                           int band0, int gbands, int log_s,
-                                                          uint32_t *__restrict__ table, uint32_t *__restrict__ keys,
-                                                          uint32_t *__restrict__ vals, uint32_t *err)
+                                                          uint32_t *__restrict__ table, uint32_t *__restrict__ counts,
+                                                          uint32_t *__restrict__ slot_of, uint32_t *err)
 {
     const int64_t total = (int64_t)gbands * n;
     const uint32_t smask = (1u << log_s) - 1u;
@@ -101,16 +107,53 @@ __global__ void __launch_bounds__(256) band_insert_kernel(const uint32_t *__rest
             slot = (slot + 1) & smask;
         }
         if (!found) atomicOr(err, SQ_DEVERR_TIMEOUT);
-        keys[e] = ((uint32_t)gb << log_s) | slot;
-        vals[e] = i;
+        const uint32_t gs = ((uint32_t)gb << log_s) | slot;
+        atomicAdd(&counts[gs], 1u);
+        slot_of[e] = gs;
     }
 }
 
-// Step 3a: head positions of runs of equal keys (0 elsewhere), for a max-scan.
-__global__ void band_heads_kernel(const uint32_t *__restrict__ keys, int64_t count, uint32_t *__restrict__ head_pos)
+// Step 1b: keep the members of buckets with >= 2 members (singletons can form
+// no pair), as keys (bucket << nbits) | id, appended in any order -- the sort
+// that follows orders them by bucket, then id.
+__global__ void __launch_bounds__(256) band_filter_kernel(const uint32_t *__restrict__ slot_of,
+                                                          const uint32_t *__restrict__ counts, int64_t n, int gbands,
+                                                          int nbits, uint64_t *__restrict__ keys,
+                                                          uint32_t *__restrict__ d_kept)
 {
+    const int64_t total = (int64_t)gbands * n;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = base + threadIdx.x;
+        bool keep = false;
+        uint64_t key = 0;
+        if (e < total) {
+            const uint32_t gs = slot_of[e];
+            keep = counts[gs] >= 2u;
+            const uint32_t i = (uint32_t)(e % n);
+            key = ((uint64_t)gs << nbits) | i;
+        }
+        const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+        uint32_t pos = 0;
+        if (lane == 0 && mask) pos = atomicAdd(d_kept, (uint32_t)__popc(mask));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (keep) keys[pos + __popc(mask & ((1u << lane) - 1u))] = key;
+    }
+}
+
+__device__ __forceinline__ int64_t dev_count(int64_t count_max, const uint32_t *d_count)
+{
+    const int64_t c = (int64_t)*d_count;
+    return c < count_max ? c : count_max;
+}
+
+// Step 3a: head positions of runs of equal buckets (0 elsewhere), for a max-scan.
+__global__ void band_heads_kernel(const uint64_t *__restrict__ keys, int nbits, int64_t count_max,
+                                  const uint32_t *__restrict__ d_count, uint32_t *__restrict__ head_pos)
+{
+    const int64_t count = dev_count(count_max, d_count);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-        head_pos[e] = (e == 0 || keys[e] != keys[e - 1]) ? (uint32_t)e : 0u;
+        head_pos[e] = (e == 0 || (keys[e] >> nbits) != (keys[e - 1] >> nbits)) ? (uint32_t)e : 0u;
 }
 
 struct ChunkInfo {
@@ -131,24 +174,28 @@ __device__ __forceinline__ ChunkInfo chunk_info(const uint32_t *__restrict__ run
 }
 
 // Step 3b: chunk ids per (sequence, band) and flags of chunks with >= 2 members.
-__global__ void band_chunks_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                                   const uint32_t *__restrict__ run_start, int64_t count, int cap, int log_s,
+__global__ void band_chunks_kernel(const uint64_t *__restrict__ keys, int nbits, const uint32_t *__restrict__ run_start,
+                                   int64_t count_max, const uint32_t *__restrict__ d_count, int cap, int log_s,
                                    int band0, int bands, uint32_t *__restrict__ chunk_of, uint32_t *__restrict__ flags)
 {
+    const int64_t count = dev_count(count_max, d_count);
+    const uint64_t idmask = (1ull << nbits) - 1ull;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
         ChunkInfo c = chunk_info(run_start, count, e, cap);
-        const int b = band0 + (int)(keys[e] >> log_s);
-        chunk_of[(int64_t)vals[e] * bands + b] = c.head;
+        const uint64_t k = keys[e];
+        const int b = band0 + (int)((k >> nbits) >> log_s);
+        chunk_of[(int64_t)(k & idmask) * bands + b] = c.head;
         flags[e] = (c.is_head && !c.is_last) ? 1u : 0u;
     }
 }
 
 // Step 4: compacted chunk heads, sizes and pair counts.
 __global__ void band_chunk_list_kernel(const uint32_t *__restrict__ run_start, const uint32_t *__restrict__ flags,
-                                       const uint32_t *__restrict__ cidx, int64_t count, int cap,
-                                       uint32_t *__restrict__ heads, uint32_t *__restrict__ sizes,
-                                       uint64_t *__restrict__ npairs)
+                                       const uint32_t *__restrict__ cidx, int64_t count_max,
+                                       const uint32_t *__restrict__ d_count, int cap, uint32_t *__restrict__ heads,
+                                       uint32_t *__restrict__ sizes, uint64_t *__restrict__ npairs)
 {
+    const int64_t count = dev_count(count_max, d_count);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
         if (flags[e]) heads[cidx[e]] = (uint32_t)e;
         ChunkInfo c = chunk_info(run_start, count, e, cap);
@@ -179,7 +226,7 @@ __device__ __forceinline__ void decode_pair(uint64_t t, uint32_t s, uint32_t &u,
 
 // Step 5: owned pairs of this band group, appended to out.
 __global__ void __launch_bounds__(256) band_emit_kernel(
-    const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ heads,
+    const uint64_t *__restrict__ keys, int nbits, const uint32_t *__restrict__ heads,
     const uint32_t *__restrict__ sizes, const uint64_t *__restrict__ poff, const uint32_t *__restrict__ d_nchunks,
     const uint64_t *__restrict__ d_total, int log_s, int band0, int bands, const uint32_t *__restrict__ chunk_of,
     uint32_t *__restrict__ out, int64_t capacity, unsigned long long *__restrict__ d_count, uint32_t *err)
@@ -220,14 +267,15 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
                 u = 0;
                 v = 1;
             }
-            i = vals[h + u];
-            j = vals[h + v];
-            const int b = band0 + (int)(keys[h] >> log_s);
+            const uint64_t idmask = (1ull << nbits) - 1ull;
+            i = (uint32_t)(keys[h + u] & idmask);
+            j = (uint32_t)(keys[h + v] & idmask);
+            const int b = band0 + (int)((keys[h] >> nbits) >> log_s);
             owned = true;
             const uint32_t *gi = chunk_of + (int64_t)i * bands;
             const uint32_t *gj = chunk_of + (int64_t)j * bands;
             for (int bb = 0; bb < b; ++bb)
-                if (gi[bb] == gj[bb]) {
+                if (gi[bb] == gj[bb] && gi[bb] != kNoChunk) {
                     owned = false;
                     break;
                 }
@@ -298,24 +346,31 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
     const int cap = (bucket_cap <= 0 || bucket_cap >= n) ? 0 : bucket_cap;
 
     // table of S >= 2n slots per band; a group of G bands keeps G*S <= 2^32
-    int log_s = bits_for((uint64_t)(2 * n - 1));
+    // and the sort key (bucket << nbits | id) within 64 bits
+    const int log_s = bits_for((uint64_t)(2 * n - 1));
     const int64_t S = int64_t(1) << log_s;
+    const int nbits = bits_for((uint64_t)(n - 1));
     int G = (int)std::min<int64_t>(bands, (int64_t(1) << 32) / S);
+    while (G > 1 && nbits + log_s + bits_for((uint64_t)(G - 1)) > 64) --G;
     if (G < 1) return SUBQUAD_ERR_ARG;
     const int64_t mg = (int64_t)G * n;
 
     auto layout = [&](SqArena &a) {
         struct L {
-            uint32_t *chunk_of, *table, *k0, *v0, *k1, *v1, *sizes;
-            uint64_t *npairs;
+            uint32_t *chunk_of, *table, *counts, *slot_of, *run_start, *flags, *cidx, *heads, *sizes;
+            uint64_t *k0, *k1, *npairs;
             void *tmp;
         } l;
         l.chunk_of = a.take<uint32_t>((size_t)n * bands);
         l.table = a.take<uint32_t>((size_t)G * S);
-        l.k0 = a.take<uint32_t>(mg);
-        l.v0 = a.take<uint32_t>(mg);
-        l.k1 = a.take<uint32_t>(mg);
-        l.v1 = a.take<uint32_t>(mg);
+        l.counts = a.take<uint32_t>((size_t)G * S);
+        l.slot_of = a.take<uint32_t>(mg);
+        l.k0 = a.take<uint64_t>(mg);
+        l.k1 = a.take<uint64_t>(mg);
+        l.run_start = a.take<uint32_t>(mg);
+        l.flags = a.take<uint32_t>(mg);
+        l.cidx = a.take<uint32_t>(mg);
+        l.heads = a.take<uint32_t>(mg);
         l.sizes = a.take<uint32_t>(mg);
         l.npairs = a.take<uint64_t>(mg);
         l.tmp = a.take<char>(std::max(sq_radix_tmp_bytes(mg), sq_scan_tmp_bytes(mg)));
@@ -331,42 +386,44 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
     unsigned long long *d_count = reinterpret_cast<unsigned long long *>(ctx->d_small);
     uint32_t *d_nchunks = reinterpret_cast<uint32_t *>(ctx->d_small + 1);
     uint64_t *d_total = ctx->d_small + 2;
+    uint32_t *d_kept = reinterpret_cast<uint32_t *>(ctx->d_small + 3);
     SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 8 * sizeof(uint64_t), ctx->stream));
+    SQ_TRY_CUDA(cudaMemsetAsync(L.chunk_of, 0xff, (size_t)n * bands * sizeof(uint32_t), ctx->stream));
 
     for (int band0 = 0; band0 < bands; band0 += G) {
         const int gb = std::min(G, bands - band0);
         const int64_t count = (int64_t)gb * n;
         const unsigned grid = sq_grid(ctx, count, 256, 8);
         SQ_TRY_CUDA(cudaMemsetAsync(L.table, 0xff, (size_t)gb * S * sizeof(uint32_t), ctx->stream));
-        band_insert_kernel<<<grid, 256, 0, ctx->stream>>>(sig, n, rows, band0, gb, log_s, L.table, L.k0, L.v0,
-                                                          ctx->d_err);
+        SQ_TRY_CUDA(cudaMemsetAsync(L.counts, 0, (size_t)gb * S * sizeof(uint32_t), ctx->stream));
+        SQ_TRY_CUDA(cudaMemsetAsync(d_kept, 0, sizeof(uint32_t), ctx->stream));
+        band_insert_kernel<<<grid, 256, 0, ctx->stream>>>(sig, n, rows, band0, gb, log_s, L.table, L.counts,
+                                                          L.slot_of, ctx->d_err);
+        SQ_LAUNCH_CHECK();
+        band_filter_kernel<<<grid, 256, 0, ctx->stream>>>(L.slot_of, L.counts, n, gb, nbits, L.k0, d_kept);
         SQ_LAUNCH_CHECK();
         bool in_alt = false;
-        const int key_bits = log_s + bits_for((uint64_t)(gb - 1));
-        SQ_TRY(sq_radix_sort_u32(ctx, L.k0, L.v0, L.k1, L.v1, count, 0, key_bits, &in_alt, L.tmp, tmp_bytes));
-        uint32_t *K = in_alt ? L.k1 : L.k0, *V = in_alt ? L.v1 : L.v0;
-        uint32_t *run_start = in_alt ? L.k0 : L.k1;  // free after the sort
-        uint32_t *flags = in_alt ? L.v0 : L.v1;
-        band_heads_kernel<<<grid, 256, 0, ctx->stream>>>(K, count, run_start);
+        const int key_bits = nbits + log_s + bits_for((uint64_t)(gb - 1));
+        SQ_TRY(sq_radix_sort_u64(ctx, L.k0, L.k1, count, d_kept, 0, key_bits, &in_alt, L.tmp, tmp_bytes));
+        const uint64_t *K = in_alt ? L.k1 : L.k0;
+        band_heads_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, count, d_kept, L.run_start);
         SQ_LAUNCH_CHECK();
-        SQ_TRY(sq_scan_u32(ctx, run_start, run_start, count, true, true, nullptr, L.tmp, tmp_bytes));
-        band_chunks_kernel<<<grid, 256, 0, ctx->stream>>>(K, V, run_start, count, cap, log_s, band0, bands, L.chunk_of,
-                                                          flags);
+        SQ_TRY(sq_scan_u32(ctx, L.run_start, L.run_start, count, d_kept, true, true, nullptr, L.tmp, tmp_bytes));
+        band_chunks_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, L.run_start, count, d_kept, cap, log_s, band0,
+                                                          bands, L.chunk_of, L.flags);
         SQ_LAUNCH_CHECK();
-        uint32_t *cidx = L.table;  // the hash table is no longer needed
-        SQ_TRY(sq_scan_u32(ctx, flags, cidx, count, false, false, d_nchunks, L.tmp, tmp_bytes));
-        uint32_t *heads = L.table + count;  // S >= 2n, so the table holds both
-        band_chunk_list_kernel<<<grid, 256, 0, ctx->stream>>>(run_start, flags, cidx, count, cap, heads, L.sizes,
-                                                              L.npairs);
+        SQ_TRY(sq_scan_u32(ctx, L.flags, L.cidx, count, d_kept, false, false, d_nchunks, L.tmp, tmp_bytes));
+        band_chunk_list_kernel<<<grid, 256, 0, ctx->stream>>>(L.run_start, L.flags, L.cidx, count, d_kept, cap,
+                                                              L.heads, L.sizes, L.npairs);
         SQ_LAUNCH_CHECK();
         // pair counts -> offsets.  Only the first nchunks entries are written;
-        // the scan runs over `count` entries, and the prefix of entry c depends
-        // on entries < c only, so the unwritten tail never reaches a used offset.
-        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, count, nullptr, L.tmp, tmp_bytes));
+        // an exclusive prefix at entry c depends on entries < c only, so the
+        // unwritten tail never reaches a used offset.
+        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, count, d_kept, nullptr, L.tmp, tmp_bytes));
         band_total_kernel<<<1, 1, 0, ctx->stream>>>(L.npairs, L.sizes, d_nchunks, d_total);
         SQ_LAUNCH_CHECK();
         band_emit_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(
-            K, V, heads, L.sizes, L.npairs, d_nchunks, d_total, log_s, band0, bands, L.chunk_of, pairs_out,
+            K, nbits, L.heads, L.sizes, L.npairs, d_nchunks, d_total, log_s, band0, bands, L.chunk_of, pairs_out,
             pairs_capacity, d_count, ctx->d_err);
         SQ_LAUNCH_CHECK();
     }
@@ -393,7 +450,7 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
         pairs_to_keys_kernel<<<grid, 256, 0, ctx->stream>>>(pairs_out, count, nb, k0);
         SQ_LAUNCH_CHECK();
         bool in_alt = false;
-        SQ_TRY(sq_radix_sort_u64(ctx, k0, k1, count, 0, 2 * nb, &in_alt, tmp, sq_radix_tmp_bytes(count)));
+        SQ_TRY(sq_radix_sort_u64(ctx, k0, k1, count, nullptr, 0, 2 * nb, &in_alt, tmp, sq_radix_tmp_bytes(count)));
         keys_to_pairs_kernel<<<grid, 256, 0, ctx->stream>>>(in_alt ? k1 : k0, count, nb, pairs_out);
         SQ_LAUNCH_CHECK();
     }

@@ -30,7 +30,44 @@ __device__ __forceinline__ int record_len(const uint64_t *__restrict__ packed, u
     return sq_record_len(r.x, r.y);
 }
 
-template <int WORDS>
+// Per-pair inputs of the fusion, all loads issued together so one round trip
+// to memory (after the pair indices) covers the embedding rows, the alignment
+// score, both self-scores and both lengths.
+template <int WORDS, int CPL>
+struct PairInputs {
+    float4 a[CPL], b[CPL];
+    int32_t sw, self_i, self_j;
+    int len_i, len_j;
+
+    __device__ __forceinline__ void load(uint2 ij, int64_t p, bool valid, int sub, int d4, const float *__restrict__ emb,
+                                         int d, const int32_t *__restrict__ sw_in, const int32_t *__restrict__ self_sc,
+                                         const uint64_t *__restrict__ packed)
+    {
+        const float4 *ei = reinterpret_cast<const float4 *>(emb + (int64_t)ij.x * d);
+        const float4 *ej = reinterpret_cast<const float4 *>(emb + (int64_t)ij.y * d);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int k = sub + c * kTpp;
+            const bool ok = valid && k < d4;
+            a[c] = ok ? __ldg(ei + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            b[c] = ok ? __ldg(ej + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        sw = 0;
+        self_i = self_j = 0;
+        len_i = len_j = 0;
+        if (valid) {
+            sw = __ldg(sw_in + p);
+            self_i = __ldg(self_sc + ij.x);
+            self_j = __ldg(self_sc + ij.y);
+            const ulonglong2 ri = __ldg(reinterpret_cast<const ulonglong2 *>(packed + (int64_t)ij.x * WORDS));
+            const ulonglong2 rj = __ldg(reinterpret_cast<const ulonglong2 *>(packed + (int64_t)ij.y * WORDS));
+            len_i = sq_record_len(ri.x, ri.y);
+            len_j = sq_record_len(rj.x, rj.y);
+        }
+    }
+};
+
+template <int WORDS, int CPL>
 __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
     const uint32_t *__restrict__ pairs, int64_t m, const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc,
     const uint64_t *__restrict__ packed, const float *__restrict__ emb, int d, const float *__restrict__ params,
@@ -50,29 +87,25 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
     for (int64_t pbase = warp * 2; pbase < m; pbase += nwarps * 2) {
         const int64_t p = pbase + half;
         const bool valid = p < m;
-        uint2 ij = valid ? reinterpret_cast<const uint2 *>(pairs)[p] : make_uint2(0, 0);
-        const float4 *ei = reinterpret_cast<const float4 *>(emb + (int64_t)ij.x * d);
-        const float4 *ej = reinterpret_cast<const float4 *>(emb + (int64_t)ij.y * d);
+        const uint2 ij = valid ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p) : make_uint2(0, 0);
+        PairInputs<WORDS, CPL> in;
+        in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
         float dot = 0.f, sii = 0.f, sjj = 0.f;
-        if (valid) {
-            for (int k = sub; k < d4; k += kTpp) {
-                float4 a = ei[k], b = ej[k];
-                dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w))) + dot;
-                sii = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, a.w * a.w))) + sii;
-                sjj = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, b.w * b.w))) + sjj;
-            }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const float4 a = in.a[c], b = in.b[c];
+            dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w))) + dot;
+            sii = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, a.w * a.w))) + sii;
+            sjj = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, b.w * b.w))) + sjj;
         }
         dot = group_sum(dot);
         sii = group_sum(sii);
         sjj = group_sum(sjj);
-        float s = 0.f, c = 0.f, delta = 0.f;
-        if (valid) {
-            const float prod = (float)self_sc[ij.x] * (float)self_sc[ij.y];
-            s = prod > 0.f ? (float)sw[p] / sqrtf(prod) : 0.f;
-            const float nn = sii * sjj;
-            c = nn > 0.f ? dot / sqrtf(nn) : 0.f;
-            delta = fabsf((float)(record_len<WORDS>(packed, ij.x) - record_len<WORDS>(packed, ij.y)));
-        }
+        const float prod = (float)in.self_i * (float)in.self_j;
+        const float s = prod > 0.f ? (float)in.sw / sqrtf(prod) : 0.f;
+        const float nn = sii * sjj;
+        const float c = nn > 0.f ? dot / sqrtf(nn) : 0.f;
+        const float delta = fabsf((float)(in.len_i - in.len_j));
         float acc = 0.f;
         for (int k = sub; k < hidden; k += kTpp) {
             float z = fmaf(W1[3 * k], s, fmaf(W1[3 * k + 1], c, fmaf(W1[3 * k + 2], delta, b1[k])));
@@ -85,6 +118,269 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
             if (alpha_out) alpha_out[p] = a;
         }
     }
+}
+
+template <int WORDS>
+int launch_forward(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                   const int32_t *self_scores, const void *packed, const float *emb, int d, const float *gate_params,
+                   int hidden, float *fused_out, float *alpha_out)
+{
+    const int cpl = (d / 4 + kTpp - 1) / kTpp;  // float4 chunks per lane
+#define SQ_FWD(C)                                                                                                  \
+    fuse_forward_kernel<WORDS, C><<<grid, kFuseThreads, 0, ctx->stream>>>(                                         \
+        pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d, gate_params, hidden, fused_out, alpha_out)
+    if (cpl <= 1) SQ_FWD(1);
+    else if (cpl <= 2) SQ_FWD(2);
+    else if (cpl <= 4) SQ_FWD(4);
+    else if (cpl <= 8) SQ_FWD(8);
+    else SQ_FWD(16);
+#undef SQ_FWD
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Adjoint (gate training).  Pass 1: per pair, recompute the forward, then
+// accumulate the parameter gradient per lane (compensated FP32), and store
+// three per-pair coefficients of the cosine adjoint,
+//   dL/de_i = k0 e_j + k1 e_i,  dL/de_j = k0 e_i + k2 e_j,
+//   k0 = dc / (|e_i||e_j|), k1 = -dc c / |e_i|^2, k2 = -dc c / |e_j|^2,
+// with dc = dL/dc.  Each block then reduces its lanes in FP64 in a fixed
+// order.  Pass 2: one block sums the block partials in FP64 in block order.
+// Pass 3 (optional): one half-warp per sequence gathers its pairs through the
+// pair index and writes its embedding-gradient row once.
+// ---------------------------------------------------------------------------
+
+struct Kahan {
+    float sum = 0.f, comp = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)sum - (double)comp; }
+};
+
+constexpr int kGroups = kFuseThreads / kTpp;  // pair groups (half-warps) per block
+
+template <int WORDS, int CPL, int HPL>
+__global__ void __launch_bounds__(kFuseThreads) fuse_backward_kernel(
+    const uint32_t *__restrict__ pairs, int64_t m, const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc,
+    const uint64_t *__restrict__ packed, const float *__restrict__ emb, int d, const float *__restrict__ params,
+    int hidden, const float *__restrict__ dL, float4 *__restrict__ coef, double *__restrict__ partials)
+{
+    __shared__ float s_par[5 * kMaxHidden + 1];
+    extern __shared__ double s_red[];  // [kGroups][5 * hidden + 1]
+    const int P = 5 * hidden + 1;
+    for (int q = threadIdx.x; q < P; q += blockDim.x) s_par[q] = params[q];
+    __syncthreads();
+    const float *W1 = s_par, *b1 = s_par + 3 * hidden, *w2 = s_par + 4 * hidden;
+    const float b2 = s_par[5 * hidden];
+    const int sub = threadIdx.x & (kTpp - 1);
+    const int half = (threadIdx.x >> 4) & 1;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int d4 = d >> 2;
+    Kahan gW[HPL][3], gb1[HPL], gw2[HPL], gb2;
+    for (int64_t pbase = warp * 2; pbase < m; pbase += nwarps * 2) {
+        const int64_t p = pbase + half;
+        const bool valid = p < m;
+        const uint2 ij = valid ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p) : make_uint2(0, 0);
+        PairInputs<WORDS, CPL> in;
+        in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
+        const float dA = valid ? __ldg(dL + p) : 0.f;
+        float dot = 0.f, sii = 0.f, sjj = 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const float4 a = in.a[c], b = in.b[c];
+            dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w))) + dot;
+            sii = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, a.w * a.w))) + sii;
+            sjj = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, b.w * b.w))) + sjj;
+        }
+        dot = group_sum(dot);
+        sii = group_sum(sii);
+        sjj = group_sum(sjj);
+        const float prod = (float)in.self_i * (float)in.self_j;
+        const float s = prod > 0.f ? (float)in.sw / sqrtf(prod) : 0.f;
+        const float nn = sii * sjj;
+        const float c = nn > 0.f ? dot / sqrtf(nn) : 0.f;
+        const float delta = fabsf((float)(in.len_i - in.len_j));
+        float z[HPL];
+        float acc = 0.f;
+#pragma unroll
+        for (int hh = 0; hh < HPL; ++hh) {
+            const int k = sub + hh * kTpp;
+            z[hh] = 0.f;
+            if (k < hidden) {
+                z[hh] = fmaf(W1[3 * k], s, fmaf(W1[3 * k + 1], c, fmaf(W1[3 * k + 2], delta, b1[k])));
+                acc = fmaf(w2[k], fmaxf(z[hh], 0.f), acc);
+            }
+        }
+        const float g = group_sum(acc) + b2;
+        const float a = 1.f / (1.f + expf(-g));
+        const float d_g = dA * (s - 0.5f * (1.f + c)) * a * (1.f - a);
+        float dc = 0.f;
+#pragma unroll
+        for (int hh = 0; hh < HPL; ++hh) {
+            const int k = sub + hh * kTpp;
+            if (k < hidden && valid) {
+                const float u = fmaxf(z[hh], 0.f);
+                gw2[hh].add(d_g * u);
+                const float dz = z[hh] > 0.f ? d_g * w2[k] : 0.f;
+                gW[hh][0].add(dz * s);
+                gW[hh][1].add(dz * c);
+                gW[hh][2].add(dz * delta);
+                gb1[hh].add(dz);
+                dc = fmaf(dz, W1[3 * k + 1], dc);
+            }
+        }
+        dc = group_sum(dc) + dA * (1.f - a) * 0.5f;
+        if (sub == 0 && valid) {
+            gb2.add(d_g);
+            if (coef) {
+                const float ni = sqrtf(sii), nj = sqrtf(sjj);
+                float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ni > 0.f && nj > 0.f) {
+                    cf.x = dc / (ni * nj);
+                    cf.y = -dc * c / sii;
+                    cf.z = -dc * c / sjj;
+                }
+                coef[p] = cf;
+            }
+        }
+    }
+    // block reduction: group-major partials in shared memory, then a fixed-order
+    // FP64 sum over the groups for every parameter
+    const int grp = threadIdx.x / kTpp;
+    double *mine = s_red + (size_t)grp * P;
+#pragma unroll
+    for (int hh = 0; hh < HPL; ++hh) {
+        const int k = sub + hh * kTpp;
+        if (k < hidden) {
+            mine[3 * k] = gW[hh][0].value();
+            mine[3 * k + 1] = gW[hh][1].value();
+            mine[3 * k + 2] = gW[hh][2].value();
+            mine[3 * hidden + k] = gb1[hh].value();
+            mine[4 * hidden + k] = gw2[hh].value();
+        }
+    }
+    if (sub == 0) mine[5 * hidden] = gb2.value();
+    __syncthreads();
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+        double t = 0.0;
+        for (int gi = 0; gi < kGroups; ++gi) t += s_red[(size_t)gi * P + q];
+        partials[(int64_t)blockIdx.x * P + q] = t;
+    }
+}
+
+__global__ void reduce_partials_kernel(const double *__restrict__ partials, int blocks, int P, float *__restrict__ out)
+{
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < blocks; ++b) t += partials[(int64_t)b * P + q];
+        out[q] = (float)t;
+    }
+}
+
+template <int CPL>
+__global__ void __launch_bounds__(kFuseThreads) emb_grad_kernel(
+    const uint32_t *__restrict__ pairs, const float4 *__restrict__ coef, const float *__restrict__ emb, int64_t n, int d,
+    const uint32_t *__restrict__ perm_i, const uint32_t *__restrict__ off_i, const uint32_t *__restrict__ perm_j,
+    const uint32_t *__restrict__ off_j, float *__restrict__ grad_emb)
+{
+    const int sub = threadIdx.x & (kTpp - 1);
+    const int d4 = d >> 2;
+    const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kTpp;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / kTpp;
+    const uint2 *pr = reinterpret_cast<const uint2 *>(pairs);
+    for (int64_t v = grp; v < n; v += ngrp) {
+        float4 acc[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float beta = 0.f;
+        for (int side = 0; side < 2; ++side) {
+            const uint32_t *perm = side == 0 ? perm_i : perm_j;
+            const uint32_t *off = side == 0 ? off_i : off_j;
+            const uint32_t q0 = __ldg(off + v), q1 = __ldg(off + v + 1);
+            for (uint32_t q = q0; q < q1; ++q) {
+                const uint32_t p = __ldg(perm + q);
+                const uint2 ij = __ldg(pr + p);
+                const float4 cf = __ldg(coef + p);
+                const uint32_t other = side == 0 ? ij.y : ij.x;
+                beta += side == 0 ? cf.y : cf.z;
+                const float4 *eo = reinterpret_cast<const float4 *>(emb + (int64_t)other * d);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    const int k = sub + c * kTpp;
+                    if (k < d4) {
+                        const float4 e = __ldg(eo + k);
+                        acc[c].x = fmaf(cf.x, e.x, acc[c].x);
+                        acc[c].y = fmaf(cf.x, e.y, acc[c].y);
+                        acc[c].z = fmaf(cf.x, e.z, acc[c].z);
+                        acc[c].w = fmaf(cf.x, e.w, acc[c].w);
+                    }
+                }
+            }
+        }
+        const float4 *ev = reinterpret_cast<const float4 *>(emb + v * d);
+        float4 *gv = reinterpret_cast<float4 *>(grad_emb + v * d);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int k = sub + c * kTpp;
+            if (k < d4) {
+                const float4 e = __ldg(ev + k);
+                gv[k] = make_float4(fmaf(beta, e.x, acc[c].x), fmaf(beta, e.y, acc[c].y), fmaf(beta, e.z, acc[c].z),
+                                    fmaf(beta, e.w, acc[c].w));
+            }
+        }
+    }
+}
+
+template <int WORDS, int CPL>
+int launch_backward_cpl(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                        const int32_t *self_scores, const void *packed, const float *emb, int d,
+                        const float *gate_params, int hidden, const float *dL, float4 *coef, double *partials)
+{
+    const int hpl = (hidden + kTpp - 1) / kTpp;
+    const size_t smem = sizeof(double) * kGroups * (5 * hidden + 1);
+#define SQ_BWD(H)                                                                                                  \
+    do {                                                                                                           \
+        auto kern = fuse_backward_kernel<WORDS, CPL, H>;                                                           \
+        SQ_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));           \
+        kern<<<grid, kFuseThreads, smem, ctx->stream>>>(pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d,  \
+                                                        gate_params, hidden, dL, coef, partials);                  \
+    } while (0)
+    if (hpl <= 1) SQ_BWD(1);
+    else if (hpl <= 2) SQ_BWD(2);
+    else SQ_BWD(4);
+#undef SQ_BWD
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
+}
+
+template <int WORDS>
+int launch_backward(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                    const int32_t *self_scores, const void *packed, const float *emb, int d, const float *gate_params,
+                    int hidden, const float *dL, float4 *coef, double *partials)
+{
+    const int cpl = (d / 4 + kTpp - 1) / kTpp;
+    if (cpl <= 1)
+        return launch_backward_cpl<WORDS, 1>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden,
+                                             dL, coef, partials);
+    if (cpl <= 2)
+        return launch_backward_cpl<WORDS, 2>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden,
+                                             dL, coef, partials);
+    if (cpl <= 4)
+        return launch_backward_cpl<WORDS, 4>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden,
+                                             dL, coef, partials);
+    if (cpl <= 8)
+        return launch_backward_cpl<WORDS, 8>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden,
+                                             dL, coef, partials);
+    return launch_backward_cpl<WORDS, 16>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden, dL,
+                                          coef, partials);
 }
 
 }  // namespace
@@ -103,13 +399,58 @@ extern "C" int subquad_fuse_forward(subquad_ctx *ctx, const uint32_t *pairs, int
         return SUBQUAD_ERR_ARG;
     const unsigned grid = sq_grid(ctx, (m + 1) / 2 * 32, kFuseThreads, 8);
     if (pack_stride == 16)
-        fuse_forward_kernel<2><<<grid, kFuseThreads, 0, ctx->stream>>>(pairs, m, sw, self_scores,
-                                                                      (const uint64_t *)packed, emb, d, gate_params,
-                                                                      hidden, fused_out, alpha_out);
+        return launch_forward<2>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden, fused_out,
+                                 alpha_out);
+    return launch_forward<4>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden, fused_out,
+                             alpha_out);
+}
+
+extern "C" int subquad_fuse_backward(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                                     const int32_t *self_scores, const void *packed, int pack_stride, const float *emb,
+                                     int64_t n, int d, const float *gate_params, int hidden, const float *dL_dfused,
+                                     const uint32_t *perm_i, const uint32_t *off_i, const uint32_t *perm_j,
+                                     const uint32_t *off_j, float *grad_params, float *grad_emb)
+{
+    SQ_ENTER(ctx);
+    if (m < 0 || n < 0 || d < 4 || d > 1024 || d % 4 || hidden < 1 || hidden > kMaxHidden) return SUBQUAD_ERR_ARG;
+    if (pack_stride != 16 && pack_stride != 32) return SUBQUAD_ERR_ARG;
+    if (!grad_params || !gate_params) return SUBQUAD_ERR_ARG;
+    if (m > 0 && (!pairs || !sw || !self_scores || !packed || !emb || !dL_dfused)) return SUBQUAD_ERR_ARG;
+    if (grad_emb && (!perm_i || !off_i || !perm_j || !off_j || !emb)) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(emb) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8 ||
+        reinterpret_cast<uintptr_t>(packed) % 16 || reinterpret_cast<uintptr_t>(grad_emb) % 16)
+        return SUBQUAD_ERR_ARG;
+    const int P = 5 * hidden + 1;
+    // a fixed grid keeps the reduction order (and so the result) independent of m
+    const unsigned grid = (unsigned)ctx->num_sms * 4;
+    SqArena measure(nullptr);
+    measure.take<double>((size_t)grid * P);
+    if (grad_emb) measure.take<float4>((size_t)m);
+    SQ_TRY(sq_scratch_reserve(ctx, measure.off));
+    SqArena arena(ctx->scratch);
+    double *partials = arena.take<double>((size_t)grid * P);
+    float4 *coef = grad_emb ? arena.take<float4>((size_t)m) : nullptr;
+    if (pack_stride == 16)
+        SQ_TRY(launch_backward<2>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden, dL_dfused,
+                                  coef, partials));
     else
-        fuse_forward_kernel<4><<<grid, kFuseThreads, 0, ctx->stream>>>(pairs, m, sw, self_scores,
-                                                                      (const uint64_t *)packed, emb, d, gate_params,
-                                                                      hidden, fused_out, alpha_out);
+        SQ_TRY(launch_backward<4>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden, dL_dfused,
+                                  coef, partials));
+    reduce_partials_kernel<<<1, 352, 0, ctx->stream>>>(partials, (int)grid, P, grad_params);
     SQ_LAUNCH_CHECK();
+    if (grad_emb && n > 0) {
+        const int cpl = (d / 4 + kTpp - 1) / kTpp;
+        const unsigned g2 = sq_grid(ctx, n * kTpp, kFuseThreads, 8);
+#define SQ_EMB(C)                                                                                                  \
+    emb_grad_kernel<C><<<g2, kFuseThreads, 0, ctx->stream>>>(pairs, coef, emb, n, d, perm_i, off_i, perm_j, off_j,  \
+                                                            grad_emb)
+        if (cpl <= 1) SQ_EMB(1);
+        else if (cpl <= 2) SQ_EMB(2);
+        else if (cpl <= 4) SQ_EMB(4);
+        else if (cpl <= 8) SQ_EMB(8);
+        else SQ_EMB(16);
+#undef SQ_EMB
+        SQ_LAUNCH_CHECK();
+    }
     return SUBQUAD_OK;
 }

@@ -107,17 +107,21 @@ __device__ __forceinline__ int sq_record_len(uint64_t w0, uint64_t w1)
     return (int)((w0 >> 60) | ((w1 >> 60) << 4));
 }
 
-// Device-wide primitives (primitives.cu).
-int sq_scan_u32(subquad_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t count, bool inclusive, bool max_op,
-                uint32_t *total_out /* device, nullable */, void *tmp, size_t tmp_bytes);
-int sq_scan_u64(subquad_ctx *ctx, const uint64_t *in, uint64_t *out, int64_t count, uint64_t *total_out,
-                void *tmp, size_t tmp_bytes);
+// Device-wide primitives (primitives.cu).  `count` is the host-side element
+// count (or an upper bound); when `d_count` is given the kernels process
+// min(*d_count, count) elements, so a producer kernel can size the work
+// without a host round trip.
+int sq_scan_u32(subquad_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t count, const uint32_t *d_count,
+                bool inclusive, bool max_op, uint32_t *total_out /* device, nullable */, void *tmp, size_t tmp_bytes);
+int sq_scan_u64(subquad_ctx *ctx, const uint64_t *in, uint64_t *out, int64_t count, const uint32_t *d_count,
+                uint64_t *total_out, void *tmp, size_t tmp_bytes);
 size_t sq_scan_tmp_bytes(int64_t count);
 // Stable LSD radix sort of (key, value) uint32 pairs on bits [begin_bit, end_bit).
 // Returns via *result_in_alt whether the sorted data ended in the alt buffers.
 int sq_radix_sort_u32(subquad_ctx *ctx, uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                      int64_t count, int begin_bit, int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes);
+                      int64_t count, const uint32_t *d_count, int begin_bit, int end_bit, bool *result_in_alt,
+                      void *tmp, size_t tmp_bytes);
 // Stable LSD radix sort of uint64 keys on bits [begin_bit, end_bit).
-int sq_radix_sort_u64(subquad_ctx *ctx, uint64_t *keys, uint64_t *keys_alt, int64_t count, int begin_bit,
-                      int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes);
+int sq_radix_sort_u64(subquad_ctx *ctx, uint64_t *keys, uint64_t *keys_alt, int64_t count, const uint32_t *d_count,
+                      int begin_bit, int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes);
 size_t sq_radix_tmp_bytes(int64_t count);

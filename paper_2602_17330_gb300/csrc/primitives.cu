@@ -22,6 +22,15 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadix = 256;
 
+// Element count of a launch sized for count_max: the device-side count when one
+// is given (the producer of the data wrote it), else count_max.
+__device__ __forceinline__ int64_t eff_count(int64_t count_max, const uint32_t *d_count)
+{
+    if (!d_count) return count_max;
+    int64_t c = (int64_t)*d_count;
+    return c < count_max ? c : count_max;
+}
+
 template <typename T, bool MAX>
 __device__ __forceinline__ T op(T a, T b)
 {
@@ -79,10 +88,16 @@ __device__ __forceinline__ void load_tile(const T *in, int64_t base, int64_t cou
 }
 
 template <typename T, bool MAX>
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T *__restrict__ in, int64_t count,
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T *__restrict__ in, int64_t count_max,
+                                                                   const uint32_t *__restrict__ d_count,
                                                                    T *__restrict__ tile_sums)
 {
     __shared__ T s_buf[kScanTilePadded];
+    const int64_t count = eff_count(count_max, d_count);
+    if ((int64_t)blockIdx.x * kScanTile >= count) {
+        if (threadIdx.x == 0) tile_sums[blockIdx.x] = T(0);
+        return;
+    }
     T items[kScanItems];
     load_tile(in, (int64_t)blockIdx.x * kScanTile, count, s_buf, items);
     T acc = items[0];
@@ -112,12 +127,15 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(T *__restrict__ sums, 
 
 template <typename T, bool MAX>
 __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const T *__restrict__ in, T *__restrict__ out,
-                                                                  int64_t count, const T *__restrict__ tile_prefix,
-                                                                  bool inclusive)
+                                                                  int64_t count_max,
+                                                                  const uint32_t *__restrict__ d_count,
+                                                                  const T *__restrict__ tile_prefix, bool inclusive)
 {
     __shared__ T s_buf[kScanTilePadded];
-    T items[kScanItems];
+    const int64_t count = eff_count(count_max, d_count);
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    if (base >= count) return;
+    T items[kScanItems];
     load_tile(in, base, count, s_buf, items);
     T acc = items[0];
 #pragma unroll
@@ -138,8 +156,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const T *__res
 }
 
 template <typename T, bool MAX>
-int scan_impl(subquad_ctx *ctx, const T *in, T *out, int64_t count, bool inclusive, T *total_out, void *tmp,
-              size_t tmp_bytes)
+int scan_impl(subquad_ctx *ctx, const T *in, T *out, int64_t count, const uint32_t *d_count, bool inclusive,
+              T *total_out, void *tmp, size_t tmp_bytes)
 {
     if (count <= 0) {
         if (total_out) SQ_TRY_CUDA(cudaMemsetAsync(total_out, 0, sizeof(T), ctx->stream));
@@ -148,11 +166,12 @@ int scan_impl(subquad_ctx *ctx, const T *in, T *out, int64_t count, bool inclusi
     int64_t ntiles = (count + kScanTile - 1) / kScanTile;
     if ((size_t)ntiles * sizeof(T) > tmp_bytes) return SUBQUAD_ERR_ARG;
     T *sums = static_cast<T *>(tmp);
-    scan_reduce_kernel<T, MAX><<<(unsigned)ntiles, kScanThreads, 0, ctx->stream>>>(in, count, sums);
+    scan_reduce_kernel<T, MAX><<<(unsigned)ntiles, kScanThreads, 0, ctx->stream>>>(in, count, d_count, sums);
     SQ_LAUNCH_CHECK();
     scan_tiles_kernel<T, MAX><<<1, 1024, 0, ctx->stream>>>(sums, ntiles, total_out);
     SQ_LAUNCH_CHECK();
-    scan_apply_kernel<T, MAX><<<(unsigned)ntiles, kScanThreads, 0, ctx->stream>>>(in, out, count, sums, inclusive);
+    scan_apply_kernel<T, MAX><<<(unsigned)ntiles, kScanThreads, 0, ctx->stream>>>(in, out, count, d_count, sums,
+                                                                                    inclusive);
     SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
 }
@@ -169,10 +188,16 @@ __device__ __forceinline__ uint32_t digit_of(K key, int shift)
 
 // hist[d * ntiles + tile] = number of elements of the tile with digit d
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const K *__restrict__ keys, int64_t count, int shift,
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const K *__restrict__ keys, int64_t count_max,
+                                                                  const uint32_t *__restrict__ d_count, int shift,
                                                                   uint32_t *__restrict__ hist, int64_t ntiles)
 {
     __shared__ uint32_t s_hist[kRadix];
+    const int64_t count = eff_count(count_max, d_count);
+    if ((int64_t)blockIdx.x * kSortTile >= count) {
+        for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * ntiles + blockIdx.x] = 0;
+        return;
+    }
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) s_hist[d] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -193,12 +218,15 @@ template <typename K, bool HAS_VAL>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const K *__restrict__ keys_in,
                                                                      const uint32_t *__restrict__ vals_in,
                                                                      K *__restrict__ keys_out,
-                                                                     uint32_t *__restrict__ vals_out, int64_t count,
-                                                                     int shift, const uint32_t *__restrict__ offsets,
+                                                                     uint32_t *__restrict__ vals_out, int64_t count_max,
+                                                                     const uint32_t *__restrict__ d_count, int shift,
+                                                                     const uint32_t *__restrict__ offsets,
                                                                      int64_t ntiles)
 {
     __shared__ uint32_t s_wcnt[kSortThreads / 32][kRadix];
     __shared__ uint32_t s_gofs[kRadix];
+    const int64_t count = eff_count(count_max, d_count);
+    if ((int64_t)blockIdx.x * kSortTile >= count) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = threadIdx.x; q < (kSortThreads / 32) * kRadix; q += blockDim.x) (&s_wcnt[0][0])[q] = 0;
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) s_gofs[d] = offsets[(int64_t)d * ntiles + blockIdx.x];
@@ -246,7 +274,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const K *__
 
 template <typename K, bool HAS_VAL>
 int radix_impl(subquad_ctx *ctx, K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, int64_t count,
-               int begin_bit, int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes)
+               const uint32_t *d_count, int begin_bit, int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes)
 {
     *result_in_alt = false;
     if (count <= 1 || end_bit <= begin_bit) return SUBQUAD_OK;
@@ -264,12 +292,13 @@ int radix_impl(subquad_ctx *ctx, K *keys, uint32_t *vals, K *keys_alt, uint32_t 
     uint32_t *src_v = vals, *dst_v = vals_alt;
     bool in_alt = false;
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
-        radix_hist_kernel<K><<<(unsigned)ntiles, kSortThreads, 0, ctx->stream>>>(src_k, count, shift, hist, ntiles);
+        radix_hist_kernel<K><<<(unsigned)ntiles, kSortThreads, 0, ctx->stream>>>(src_k, count, d_count, shift, hist,
+                                                                                ntiles);
         SQ_LAUNCH_CHECK();
-        SQ_TRY((scan_impl<uint32_t, false>(ctx, hist, offs, hist_len, false, nullptr, scan_tmp,
+        SQ_TRY((scan_impl<uint32_t, false>(ctx, hist, offs, hist_len, nullptr, false, nullptr, scan_tmp,
                                            (size_t)scan_tiles * sizeof(uint32_t))));
         radix_scatter_kernel<K, HAS_VAL><<<(unsigned)ntiles, kSortThreads, 0, ctx->stream>>>(
-            src_k, src_v, dst_k, dst_v, count, shift, offs, ntiles);
+            src_k, src_v, dst_k, dst_v, count, d_count, shift, offs, ntiles);
         SQ_LAUNCH_CHECK();
         K *tk = src_k;
         src_k = dst_k;
@@ -298,32 +327,33 @@ size_t sq_radix_tmp_bytes(int64_t count)
     return (size_t)hist_len * sizeof(uint32_t) * 2 + (size_t)scan_tiles * sizeof(uint32_t) + 4096;
 }
 
-int sq_scan_u32(subquad_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t count, bool inclusive, bool max_op,
-                uint32_t *total_out, void *tmp, size_t tmp_bytes)
+int sq_scan_u32(subquad_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t count, const uint32_t *d_count,
+                bool inclusive, bool max_op, uint32_t *total_out, void *tmp, size_t tmp_bytes)
 {
-    if (max_op) return scan_impl<uint32_t, true>(ctx, in, out, count, inclusive, total_out, tmp, tmp_bytes);
-    return scan_impl<uint32_t, false>(ctx, in, out, count, inclusive, total_out, tmp, tmp_bytes);
+    if (max_op) return scan_impl<uint32_t, true>(ctx, in, out, count, d_count, inclusive, total_out, tmp, tmp_bytes);
+    return scan_impl<uint32_t, false>(ctx, in, out, count, d_count, inclusive, total_out, tmp, tmp_bytes);
 }
 
-int sq_scan_u64(subquad_ctx *ctx, const uint64_t *in, uint64_t *out, int64_t count, uint64_t *total_out, void *tmp,
-                size_t tmp_bytes)
+int sq_scan_u64(subquad_ctx *ctx, const uint64_t *in, uint64_t *out, int64_t count, const uint32_t *d_count,
+                uint64_t *total_out, void *tmp, size_t tmp_bytes)
 {
-    return scan_impl<uint64_t, false>(ctx, in, out, count, false, total_out, tmp, tmp_bytes);
+    return scan_impl<uint64_t, false>(ctx, in, out, count, d_count, false, total_out, tmp, tmp_bytes);
 }
 
 int sq_radix_sort_u32(subquad_ctx *ctx, uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                      int64_t count, int begin_bit, int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes)
+                      int64_t count, const uint32_t *d_count, int begin_bit, int end_bit, bool *result_in_alt,
+                      void *tmp, size_t tmp_bytes)
 {
     if (vals)
-        return radix_impl<uint32_t, true>(ctx, keys, vals, keys_alt, vals_alt, count, begin_bit, end_bit,
+        return radix_impl<uint32_t, true>(ctx, keys, vals, keys_alt, vals_alt, count, d_count, begin_bit, end_bit,
                                           result_in_alt, tmp, tmp_bytes);
-    return radix_impl<uint32_t, false>(ctx, keys, nullptr, keys_alt, nullptr, count, begin_bit, end_bit,
+    return radix_impl<uint32_t, false>(ctx, keys, nullptr, keys_alt, nullptr, count, d_count, begin_bit, end_bit,
                                        result_in_alt, tmp, tmp_bytes);
 }
 
-int sq_radix_sort_u64(subquad_ctx *ctx, uint64_t *keys, uint64_t *keys_alt, int64_t count, int begin_bit, int end_bit,
-                      bool *result_in_alt, void *tmp, size_t tmp_bytes)
+int sq_radix_sort_u64(subquad_ctx *ctx, uint64_t *keys, uint64_t *keys_alt, int64_t count, const uint32_t *d_count,
+                      int begin_bit, int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes)
 {
-    return radix_impl<uint64_t, false>(ctx, keys, nullptr, keys_alt, nullptr, count, begin_bit, end_bit,
+    return radix_impl<uint64_t, false>(ctx, keys, nullptr, keys_alt, nullptr, count, d_count, begin_bit, end_bit,
                                        result_in_alt, tmp, tmp_bytes);
 }

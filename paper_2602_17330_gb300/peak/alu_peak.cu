@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <vector>
 #include <cuda_runtime.h>
+#include <cuda_fp16.h>
 
 #define CK(x) do { cudaError_t e = (x); if (e != cudaSuccess) { printf("CUDA error %s at %d\n", cudaGetErrorString(e), __LINE__); exit(1); } } while (0)
 
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(kThreads) probe(int *out, long long *rec, int 
     for (int it = 0; it < kIters; ++it) {
 #pragma unroll
         for (int c = 0; c < kChains; ++c) {
-            if (OP == 0) v[c] = v[c] + a + b;                                   // 3-input add
+            if (OP == 0) v[c] = v[c] + v[(c + 1) & 7] + it;                     // 3-input add
             if (OP == 1) v[c] = max(v[c], a + it);                              // plain int max (loop-variant operand)
             if (OP == 2) v[c] = __vimax3_s32_relu(v[c], a, b + it);             // max of three, relu
             if (OP == 3) v[c] = __viaddmax_s32_relu(v[c], -b, a + it);          // add then max, relu
@@ -39,6 +40,24 @@ __global__ void __launch_bounds__(kThreads) probe(int *out, long long *rec, int 
             if (OP == 5) v[c] = __viaddmax_s16x2_relu(v[c], b, a + it);         // packed 16-bit add-max
             if (OP == 6) v[c] = v[c] * b + a;                                   // integer multiply-add
             if (OP == 7) v[c] = __float_as_int(fmaxf(__int_as_float(v[c]), __int_as_float(a + it)));  // fp32 max
+            if (OP == 8) v[c] = max(max(v[c], a + it), v[(c + 3) & 7]);                 // two-level int max
+            if (OP == 9) v[c] = __vmaxs2(v[c], a + it);                                 // packed 16-bit max
+            if (OP == 10) v[c] = __vadd2(v[c], v[(c + 1) & 7]);                         // packed 16-bit add
+            if (OP == 11) v[c] = __vimax_s32_relu(v[c], v[(c + 5) & 7]);                // max with 0
+            if (OP >= 12 && OP <= 14) {
+                __half2 x = *reinterpret_cast<__half2 *>(&v[c]);
+                __half2 y = *reinterpret_cast<__half2 *>(&v[(c + 1) & 7]);
+                __half2 r = OP == 12 ? __hadd2(x, y) : OP == 13 ? __hmax2(x, y) : __hfma2(x, y, x);
+                v[c] = *reinterpret_cast<int *>(&r);
+            }
+            if (OP == 15) v[c] = __float_as_int(__int_as_float(v[c]) + __int_as_float(v[(c + 1) & 7]));   // fadd
+            if (OP == 16) v[c] = __float_as_int(fmaf(__int_as_float(v[c]), __int_as_float(b), __int_as_float(v[(c + 1) & 7])));
+            if (OP == 17) v[c] = __byte_perm(v[c], v[(c + 1) & 7], 0x5410);              // prmt
+            if (OP == 18) v[c] = (v[c] ^ v[(c + 1) & 7]) & (v[(c + 2) & 7] | a);        // lop3
+            if (OP == 19) v[c] = __float_as_int(fmaxf(fmaxf(__int_as_float(v[c]), __int_as_float(v[(c + 1) & 7])),
+                                                      __int_as_float(v[(c + 2) & 7])));  // two fp32 max
+            if (OP == 20) v[c] = __vmaxs2(__vmaxs2(v[c], v[(c + 1) & 7]), v[(c + 2) & 7]);  // two packed maxes
+            if (OP == 21) v[c] = v[c] + v[(c + 1) & 7];                                  // 2-input add
         }
     }
     long long t1 = clock64();
@@ -84,6 +103,63 @@ double run(int sms, int per_sm, int *out, long long *rec, const char *name)
     return per_sm_clk;
 }
 
+// Shared-memory lookups with the alignment kernel's pattern: a lane-replicated
+// table (word index * 32 + lane), data-dependent word index per lookup.
+__global__ void __launch_bounds__(kThreads) lds_probe_kernel(int *out, long long *rec, int seed)
+{
+    __shared__ int tab[420 * 32];
+    for (int q = threadIdx.x; q < 420 * 32; q += blockDim.x) tab[q] = (q * 7 + seed) % 419;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    int idx[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) idx[c] = (threadIdx.x * 13 + c * 29 + seed) % 419;
+    long long t0 = clock64();
+    for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) idx[c] = tab[idx[c] * 32 + lane];
+    }
+    long long t1 = clock64();
+    int s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s ^= idx[c];
+    if (s == 0x7fffffff) out[0] = s;
+    if (threadIdx.x == 0) {
+        rec[3 * blockIdx.x] = smid();
+        rec[3 * blockIdx.x + 1] = t0;
+        rec[3 * blockIdx.x + 2] = t1;
+    }
+}
+
+void lds_probe(int sms, int *out, long long *rec)
+{
+    const int per_sm = 4;  // 53.8 KB of shared memory per CTA
+    const int blocks = sms * per_sm;
+    lds_probe_kernel<<<blocks, kThreads>>>(out, rec, 1);
+    CK(cudaDeviceSynchronize());
+    lds_probe_kernel<<<blocks, kThreads>>>(out, rec, 3);
+    CK(cudaDeviceSynchronize());
+    std::vector<long long> h(3 * blocks);
+    CK(cudaMemcpy(h.data(), rec, sizeof(long long) * 3 * blocks, cudaMemcpyDeviceToHost));
+    const int kMaxSm = 4096;
+    std::vector<long long> lo(kMaxSm, -1), hi(kMaxSm, -1);
+    std::vector<int> cnt(kMaxSm, 0);
+    for (int k = 0; k < blocks; ++k) {
+        int s = (int)h[3 * k];
+        if (s < 0 || s >= kMaxSm) continue;
+        if (lo[s] < 0 || h[3 * k + 1] < lo[s]) lo[s] = h[3 * k + 1];
+        if (hi[s] < 0 || h[3 * k + 2] > hi[s]) hi[s] = h[3 * k + 2];
+        cnt[s]++;
+    }
+    double sum = 0; int used = 0;
+    for (int s = 0; s < kMaxSm; ++s) if (cnt[s] > 0 && hi[s] > lo[s]) {
+        sum += (double)cnt[s] * kThreads * kIters * kChains / (double)(hi[s] - lo[s]);
+        ++used;
+    }
+    printf("%-28s %8.1f lane-loads/SM/clk  (%d SMs, %d CTAs/SM; dependent chains)\n", "lds lane-replicated", sum / used,
+           used, per_sm);
+}
+
 int main()
 {
     cudaDeviceProp p;
@@ -101,6 +177,21 @@ int main()
     run<5>(sms, per_sm, out, rec, "__viaddmax_s16x2_relu");
     run<6>(sms, per_sm, out, rec, "imad (a*b+c)");
     run<7>(sms, per_sm, out, rec, "fmaxf");
+    run<8>(sms, per_sm, out, rec, "max(max(a,b),c)");
+    run<9>(sms, per_sm, out, rec, "__vmaxs2");
+    run<10>(sms, per_sm, out, rec, "__vadd2");
+    run<11>(sms, per_sm, out, rec, "__vimax_s32_relu");
+    run<12>(sms, per_sm, out, rec, "__hadd2");
+    run<13>(sms, per_sm, out, rec, "__hmax2");
+    run<14>(sms, per_sm, out, rec, "__hfma2");
+    run<15>(sms, per_sm, out, rec, "fadd");
+    run<16>(sms, per_sm, out, rec, "ffma");
+    run<17>(sms, per_sm, out, rec, "prmt");
+    run<18>(sms, per_sm, out, rec, "lop3 (xor/and/or)");
+    run<19>(sms, per_sm, out, rec, "fmaxf(fmaxf(a,b),c)");
+    run<20>(sms, per_sm, out, rec, "__vmaxs2(__vmaxs2(a,b),c)");
+    run<21>(sms, per_sm, out, rec, "iadd (2-input)");
+    lds_probe(sms, out, rec);
     CK(cudaFree(out));
     CK(cudaFree(rec));
     return 0;

@@ -52,6 +52,14 @@ SIGNATURES = {
     "subquad_align_score": (_c.c_int, [_P, _P, _c.c_int, _P, _I64, _c.c_int, _c.c_int, _P]),
     "subquad_self_scores": (_c.c_int, [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _P]),
     "subquad_fuse_forward": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P, _c.c_int, _P, _P]),
+    "subquad_pair_labels": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
+    "subquad_pair_weights": (_c.c_int, [_P, _P, _I64, _c.c_int, _P]),
+    "subquad_bce_loss": (_c.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
+    "subquad_pair_index": (_c.c_int, [_P, _P, _I64, _I64, _P, _P, _P, _P]),
+    "subquad_fuse_backward": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _I64, _c.c_int, _P, _c.c_int, _P,
+                                         _P, _P, _P, _P, _P, _P]),
+    "subquad_adam_step": (_c.c_int, [_P, _P, _P, _P, _P, _I64, _c.c_int, _c.c_float, _c.c_float, _c.c_float,
+                                     _c.c_float]),
 }
 
 _lib = None
@@ -236,6 +244,67 @@ class Context:
         return (out, alpha) if want_alpha else out
 
 
+    # -- gate training ---------------------------------------------------------
+    def pair_labels(self, pairs, family, subgroup):
+        torch = self.torch
+        m = int(pairs.shape[0])
+        family = self._dev(family, torch.int32)
+        subgroup = self._dev(subgroup, torch.int32)
+        label = self._empty((m,), torch.uint8)
+        group = self._empty((m,), torch.int32)
+        _check(lib().subquad_pair_labels(self.handle, _ptr(pairs), m, _ptr(family), _ptr(subgroup), _ptr(label),
+                                         _ptr(group)), "subquad_pair_labels")
+        return label, group
+
+    def pair_weights(self, group, num_groups: int):
+        torch = self.torch
+        m = int(group.shape[0])
+        w = self._empty((m,), torch.float32)
+        _check(lib().subquad_pair_weights(self.handle, _ptr(group), m, num_groups, _ptr(w)), "subquad_pair_weights")
+        return w
+
+    def bce_loss(self, fused, label, weight, want_grad: bool = True, loss=None, grad=None):
+        torch = self.torch
+        m = int(fused.shape[0])
+        loss = self._empty((1,), torch.float32) if loss is None else loss
+        if want_grad and grad is None:
+            grad = self._empty((m,), torch.float32)
+        _check(lib().subquad_bce_loss(self.handle, _ptr(fused), _ptr(label), _ptr(weight), m, _ptr(loss),
+                                      _ptr(grad) if want_grad else None), "subquad_bce_loss")
+        return (loss, grad) if want_grad else loss
+
+    def pair_index(self, pairs, n: int):
+        torch = self.torch
+        m = int(pairs.shape[0])
+        idx = dict(perm_i=self._empty((max(m, 1),), torch.int32), off_i=self._empty((n + 1,), torch.int32),
+                   perm_j=self._empty((max(m, 1),), torch.int32), off_j=self._empty((n + 1,), torch.int32))
+        _check(lib().subquad_pair_index(self.handle, _ptr(pairs), m, n, _ptr(idx["perm_i"]), _ptr(idx["off_i"]),
+                                        _ptr(idx["perm_j"]), _ptr(idx["off_j"])), "subquad_pair_index")
+        return idx
+
+    def fuse_backward(self, pairs, sw, self_sc, packed, emb, params, hidden: int, dL, index=None,
+                      grad_params=None, grad_emb=None, want_emb: bool = True):
+        torch = self.torch
+        m = int(pairs.shape[0])
+        n, d = int(emb.shape[0]), int(emb.shape[1])
+        grad_params = self._empty((5 * hidden + 1,), torch.float32) if grad_params is None else grad_params
+        if want_emb:
+            if index is None:
+                index = self.pair_index(pairs, n)
+            grad_emb = self._empty((n, d), torch.float32) if grad_emb is None else grad_emb
+        ix = index or {}
+        _check(lib().subquad_fuse_backward(
+            self.handle, _ptr(pairs), m, _ptr(sw), _ptr(self_sc), _ptr(packed), int(packed.shape[1]), _ptr(emb), n, d,
+            _ptr(params), hidden, _ptr(dL), _ptr(ix.get("perm_i")), _ptr(ix.get("off_i")), _ptr(ix.get("perm_j")),
+            _ptr(ix.get("off_j")), _ptr(grad_params), _ptr(grad_emb) if want_emb else None), "subquad_fuse_backward")
+        return (grad_params, grad_emb) if want_emb else grad_params
+
+    def adam_step(self, param, grad, m1, m2, t: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+                  eps: float = 1e-8):
+        _check(lib().subquad_adam_step(self.handle, _ptr(param), _ptr(grad), _ptr(m1), _ptr(m2), int(param.numel()),
+                                       t, lr, beta1, beta2, eps), "subquad_adam_step")
+
+
 # module-level names matching the C entry points, taking a Context first
 def subquad_pack(ctx: Context, *a, **k):
     return ctx.pack(*a, **k)
@@ -259,3 +328,27 @@ def subquad_self_scores(ctx: Context, *a, **k):
 
 def subquad_fuse_forward(ctx: Context, *a, **k):
     return ctx.fuse_forward(*a, **k)
+
+
+def subquad_pair_labels(ctx: Context, *a, **k):
+    return ctx.pair_labels(*a, **k)
+
+
+def subquad_pair_weights(ctx: Context, *a, **k):
+    return ctx.pair_weights(*a, **k)
+
+
+def subquad_bce_loss(ctx: Context, *a, **k):
+    return ctx.bce_loss(*a, **k)
+
+
+def subquad_pair_index(ctx: Context, *a, **k):
+    return ctx.pair_index(*a, **k)
+
+
+def subquad_fuse_backward(ctx: Context, *a, **k):
+    return ctx.fuse_backward(*a, **k)
+
+
+def subquad_adam_step(ctx: Context, *a, **k):
+    return ctx.adam_step(*a, **k)

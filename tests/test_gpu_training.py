@@ -1,0 +1,189 @@
+"""GPU parity for gate training (labels, weights, weighted BCE, the fusion
+adjoint, Adam) against the FP64 oracle.
+
+Tolerances, derived from the FP32 arithmetic of the kernels:
+* loss and dL/dfused: relative 1e-5 (FP32 inputs, FP64 sums);
+* parameter gradients: |g - g*| <= 1e-4 |g*| + 1e-6 * S, where S is the sum
+  over pairs of the absolute per-pair contributions scale max|g*| (the FP32
+  rounding of each per-pair product is ~6e-8 of that product, so gradients
+  that cancel to far below their terms carry that absolute error);
+* embedding gradients: the same form per row.
+"""
+import numpy as np
+import pytest
+
+from paper_2602_17330_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    from paper_2602_17330_gb300 import _build, subquad
+
+    _build.build()
+    c = subquad.Context(0)
+    yield c
+    c.close()
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def case(ctx, torch, oracle_mod):
+    """A donor of 30,000 sequences with its candidate list, family-correlated
+    embeddings of d = 128 scaled off unit norm, gate 3-32-1."""
+    rep = synth.donor_repertoire(30_000, seed=7)
+    a, b = synth.hash_coefficients(64, seed=7)
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 16)
+    sig = ctx.sign(packed, rep.n, 3, torch.from_numpy(a.view(np.int32)), torch.from_numpy(b.view(np.int32)), 16, 4)
+    pairs = ctx.band_candidates(sig, rep.n, 16, 4, 2048)
+    sw = ctx.align_score(packed, pairs)
+    self_sc = ctx.self_scores(packed)
+    emb = synth.family_embeddings(rep.family, 128, seed=7)
+    emb = np.ascontiguousarray(emb * np.random.default_rng(7).uniform(0.5, 2.0, (rep.n, 1)).astype(np.float32))
+    hidden = 32
+    params = synth.gate_parameters(hidden, seed=7)
+    return dict(rep=rep, packed=packed, pairs=pairs, pairs_np=to_np(pairs).view(np.uint32), sw=sw,
+                sw_np=to_np(sw), self=self_sc, self_np=to_np(self_sc), emb=emb,
+                emb_t=torch.from_numpy(emb).to(ctx.device), hidden=hidden, params=params,
+                params_t=torch.from_numpy(params).to(ctx.device))
+
+
+def test_labels_and_weights(ctx, torch, oracle_mod, case):
+    rep = case["rep"]
+    label, group = ctx.pair_labels(case["pairs"], torch.from_numpy(rep.family), torch.from_numpy(rep.subgroup))
+    y, g = oracle_mod.pair_labels(case["pairs_np"], rep.family, rep.subgroup)
+    assert (to_np(label) == y).all() and (to_np(group) == g).all()
+    assert y.sum() > 0 and (g > 0).sum() > 0
+    w = to_np(ctx.pair_weights(group, 51))
+    want = oracle_mod.pair_weights(g, 51)
+    assert np.allclose(w, want, rtol=1e-6, atol=0)
+
+
+def test_bce_loss_and_gradient(ctx, torch, oracle_mod, case):
+    rep = case["rep"]
+    fused = ctx.fuse_forward(case["pairs"], case["sw"], case["self"], case["packed"], case["emb_t"],
+                             case["params_t"], case["hidden"])
+    label, group = ctx.pair_labels(case["pairs"], torch.from_numpy(rep.family), torch.from_numpy(rep.subgroup))
+    weight = ctx.pair_weights(group, 51)
+    loss, dL = ctx.bce_loss(fused, label, weight)
+    want_loss, want_dL = oracle_mod.bce_loss(to_np(fused).astype(np.float64), to_np(label),
+                                             to_np(weight).astype(np.float64))
+    assert abs(float(to_np(loss)[0]) - want_loss) <= 1e-5 * abs(want_loss)
+    assert np.allclose(to_np(dL), want_dL, rtol=1e-5, atol=1e-12)
+
+
+def grads_close(got, want, scale, rel=1e-4, floor=1e-6):
+    err = np.abs(got.astype(np.float64) - want)
+    bound = rel * np.abs(want) + floor * scale
+    return bool((err <= bound).all()), float((err / np.maximum(bound, 1e-300)).max())
+
+
+def test_backward_matches_oracle_and_is_deterministic(ctx, torch, oracle_mod, case):
+    rep = case["rep"]
+    m = case["pairs_np"].shape[0]
+    rng = np.random.default_rng(3)
+    dL = (rng.standard_normal(m) / m).astype(np.float32)
+    dL_t = torch.from_numpy(dL).to(ctx.device)
+    gp, ge = ctx.fuse_backward(case["pairs"], case["sw"], case["self"], case["packed"], case["emb_t"],
+                               case["params_t"], case["hidden"], dL_t)
+    gp2, ge2 = ctx.fuse_backward(case["pairs"], case["sw"], case["self"], case["packed"], case["emb_t"],
+                                 case["params_t"], case["hidden"], dL_t)
+    assert torch.equal(gp, gp2) and torch.equal(ge, ge2), "backward is not bitwise reproducible"
+    want_p, want_e = oracle_mod.fuse_backward(case["pairs_np"], case["sw_np"], case["self_np"], rep.lens, case["emb"],
+                                              case["params"], case["hidden"], dL.astype(np.float64))
+    # scale of the per-pair contributions: sum |dL| times the largest feature
+    scale = float(np.abs(dL).astype(np.float64).sum()) * 20.0
+    ok, worst = grads_close(to_np(gp), want_p, scale)
+    assert ok, f"parameter gradient worst error / bound = {worst:.3f}"
+    row_scale = np.abs(want_e).max(axis=1, keepdims=True) + 1e-30
+    ok, worst = grads_close(to_np(ge), want_e, row_scale, rel=1e-4, floor=1e-5)
+    assert ok, f"embedding gradient worst error / bound = {worst:.3f}"
+
+
+def test_backward_without_embedding_gradient(ctx, torch, oracle_mod, case):
+    m = case["pairs_np"].shape[0]
+    dL = torch.full((m,), 1.0 / m, dtype=torch.float32, device=ctx.device)
+    gp = ctx.fuse_backward(case["pairs"], case["sw"], case["self"], case["packed"], case["emb_t"], case["params_t"],
+                           case["hidden"], dL, want_emb=False)
+    gp2, _ = ctx.fuse_backward(case["pairs"], case["sw"], case["self"], case["packed"], case["emb_t"],
+                               case["params_t"], case["hidden"], dL)
+    assert torch.equal(gp, gp2)
+
+
+def test_pair_index(ctx, torch, case):
+    n = case["rep"].n
+    idx = ctx.pair_index(case["pairs"], n)
+    P = case["pairs_np"].astype(np.int64)
+    for side, col in (("i", 0), ("j", 1)):
+        perm = to_np(idx["perm_" + side]).view(np.uint32)[: P.shape[0]]
+        off = to_np(idx["off_" + side]).view(np.uint32)
+        want_perm = np.argsort(P[:, col], kind="stable")
+        assert (perm == want_perm).all()
+        want_off = np.concatenate([[0], np.cumsum(np.bincount(P[:, col], minlength=n))])
+        assert (off == want_off).all()
+
+
+def test_adam_against_oracle(ctx, torch, oracle_mod):
+    rng = np.random.default_rng(4)
+    P = 1000
+    p0 = rng.standard_normal(P).astype(np.float32)
+    p_t = torch.from_numpy(p0.copy()).cuda()
+    m1 = torch.zeros_like(p_t)
+    m2 = torch.zeros_like(p_t)
+    pw, a1, a2 = p0.astype(np.float64), np.zeros(P), np.zeros(P)
+    for t in range(1, 31):
+        g = rng.standard_normal(P).astype(np.float32)
+        ctx.adam_step(p_t, torch.from_numpy(g).cuda(), m1, m2, t, lr=1e-2)
+        oracle_mod.adam_step(pw, g.astype(np.float64), a1, a2, t, lr=1e-2)
+    assert np.allclose(to_np(p_t), pw, rtol=0, atol=2e-5)
+
+
+def test_training_steps_track_oracle(ctx, torch, oracle_mod, case):
+    """Twenty full-batch steps: at every step the GPU loss and gradients are
+    compared with the oracle evaluated at the GPU's current parameters, and an
+    independent FP64 oracle trajectory is run beside it to record the drift."""
+    from paper_2602_17330_gb300 import train
+
+    rep = case["rep"]
+    label, group = ctx.pair_labels(case["pairs"], torch.from_numpy(rep.family), torch.from_numpy(rep.subgroup))
+    weight = ctx.pair_weights(group, 51)
+    y, w = to_np(label), to_np(weight).astype(np.float64)
+    tr = train.GateTrainer(ctx, case["pairs"], case["sw"], case["self"], case["packed"], case["emb_t"],
+                           case["params_t"], case["hidden"], label, weight, lr=1e-3, train_emb=True)
+    losses = []
+    for step in range(20):
+        params_now = to_np(tr.params).copy()
+        emb_now = to_np(tr.emb).copy()
+        loss = float(to_np(tr.step())[0])
+        out = oracle_mod.fuse_forward(case["pairs_np"], case["sw_np"], case["self_np"], rep.lens, emb_now, params_now,
+                                      case["hidden"])
+        want, _ = oracle_mod.bce_loss(out["fused"], y, w)
+        assert abs(loss - want) <= 1e-5 * abs(want), (step, loss, want)
+        losses.append(loss)
+    assert losses[-1] < losses[0], "training did not reduce the loss"
+
+
+def test_autograd_function_matches_direct_calls(ctx, torch, case):
+    from paper_2602_17330_gb300 import train
+
+    emb = case["emb_t"].clone().requires_grad_(True)
+    params = case["params_t"].clone().requires_grad_(True)
+    fused = train.fuse(ctx, case["pairs"], case["sw"], case["self"], case["packed"], emb, params, case["hidden"])
+    m = fused.shape[0]
+    wts = torch.linspace(-1, 1, m, device=ctx.device)
+    (fused * wts).sum().backward()
+    gp, ge = ctx.fuse_backward(case["pairs"], case["sw"], case["self"], case["packed"], case["emb_t"],
+                               case["params_t"], case["hidden"], wts.contiguous())
+    assert torch.equal(params.grad, gp) and torch.equal(emb.grad, ge)
