@@ -77,6 +77,17 @@ int64_t subquad_scratch_bytes(const subquad_ctx *ctx);
 /* Number of CUDA kernels this context has launched so far (host query). */
 int64_t subquad_launch_count(const subquad_ctx *ctx);
 
+/* Tuning knobs (no counterpart in the paper: launch shapes chosen per device
+ * by measurement, e.g. by the package's autotuner).  Host-only; they take
+ * effect for later calls and never change results.
+ *   SUBQUAD_TUNE_ALIGN_SHAPE: batched alignment launch shape, 0 = 256 threads
+ *     x 2 blocks per SM, 1 = 128 threads x 3 blocks per SM (default 1);
+ *   SUBQUAD_TUNE_BAND_L2_MB: L2 share in MB for the banding hash tables; bands
+ *     are inserted in groups whose tables fit it (default 48). */
+enum { SUBQUAD_TUNE_ALIGN_SHAPE = 0, SUBQUAD_TUNE_BAND_L2_MB = 1, SUBQUAD_TUNE_COUNT = 2 };
+int subquad_set_tuning(subquad_ctx *ctx, int key, int value);
+int subquad_get_tuning(const subquad_ctx *ctx, int key, int *value);
+
 /* ------------------------------------------------------------------------ */
 /* Scoring matrix (affinity channel a^(1) of Algorithm 1)                   */
 /* ------------------------------------------------------------------------ */
@@ -166,6 +177,16 @@ int subquad_align_score(subquad_ctx *ctx, const void *packed, int pack_stride, c
  * the fused score).  self_out: device int32 [n]. */
 int subquad_self_scores(subquad_ctx *ctx, const void *packed, int pack_stride, int64_t n, int gap_open,
                         int gap_extend, int32_t *self_out);
+
+/* Batched form of subquad_align_score / subquad_self_scores (same arguments,
+ * identical results): pairs are first binned by (shorter length, longer
+ * length) into a length-ordered work list held in context scratch (the
+ * length-binned queues of the hardware-aware batching, Eq. batch), so every
+ * warp aligns pairs of one shape with an exact unrolled height. */
+int subquad_align_score_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs,
+                               int64_t m, int gap_open, int gap_extend, int32_t *scores_out);
+int subquad_self_scores_binned(subquad_ctx *ctx, const void *packed, int pack_stride, int64_t n, int gap_open,
+                               int gap_extend, int32_t *self_out);
 
 /* ------------------------------------------------------------------------ */
 /* (a4) Per-pair gated fusion -- Eq. alpha, Eq. wm and Eq. afused with two   */

@@ -10,8 +10,8 @@
 // other sequence streams through the columns.  Per row the thread keeps
 // E(i, j-1) and H(i, j-1) - o in registers, and the substitution scores come
 // from a lane-replicated table in shared memory (entry (a, b) of lane l at word
-// (a*20 + b)*32 + l, so a warp's 32 lookups hit 32 distinct banks) that already
-// holds M[a][b] + o.  E and F are clamped at 0 (values below 0 can never lift
+// (a*21 + b)*32 + l, so a warp's 32 lookups hit 32 distinct banks) that already
+// holds M[a][b] + o (a and b = 20 is the padding residue).  E and F are clamped at 0 (values below 0 can never lift
 // H above its floor of 0, so the maximum is unchanged), and each cell is
 //   t = (H(i-1,j-1) - o) + (M + o)
 //   E = max(E - e, H(i,j-1) - o, 0)           (DPX add-max-relu)
@@ -24,9 +24,12 @@
 namespace {
 
 constexpr int kLanes = 32;
-constexpr int kTabRows = 21;  // 20 residues + the padding residue
-constexpr int kTabWords = kTabRows * 20 * kLanes;
-constexpr int32_t kPadScore = -30000;
+constexpr int kTabRows = 21;  // 20 residues + the padding residue (rows and columns)
+constexpr int kTabWords = kTabRows * kTabRows * kLanes;
+// Substitution score of the padding residue.  Any value <= 0 keeps padded
+// rows/columns from raising the maximum (their cells are bounded by the real
+// cells above/left of them); -64 keeps every 16-bit intermediate in range.
+constexpr int32_t kPadScore = -64;
 constexpr int kAlignThreads = 256;
 
 template <int WORDS>
@@ -57,7 +60,7 @@ __device__ __forceinline__ int32_t sw_pair(const Rec<WORDS> &q, int Lq, const Re
     for (int p = 0; p < NQ; ++p) {
         uint32_t code = (uint32_t)(q.w[p / 12] >> (5 * (p % 12))) & 31u;
         code = p < Lq ? min(code, 19u) : 20u;  // records from subquad_pack hold codes < 20
-        qoff[p] = (code * 20u * kLanes + (uint32_t)lane) * 4u;
+        qoff[p] = (code * kTabRows * kLanes + (uint32_t)lane) * 4u;
         E[p] = 0;
         HM[p] = -o;
     }
@@ -155,9 +158,9 @@ int ensure_table(subquad_ctx *ctx, int gap_open)
     if (ctx->d_table && ctx->table_gap_open == gap_open) return SUBQUAD_OK;
     static thread_local int32_t host[kTabWords];
     for (int a = 0; a < kTabRows; ++a)
-        for (int b = 0; b < 20; ++b) {
-            int32_t v = a < 20 ? (int32_t)ctx->h_matrix[20 * a + b] + gap_open : kPadScore;
-            for (int l = 0; l < kLanes; ++l) host[(a * 20 + b) * kLanes + l] = v;
+        for (int b = 0; b < kTabRows; ++b) {
+            const int32_t v = (a < 20 && b < 20 ? (int32_t)ctx->h_matrix[20 * a + b] : kPadScore) + gap_open;
+            for (int l = 0; l < kLanes; ++l) host[(a * kTabRows + b) * kLanes + l] = v;
         }
     if (!ctx->d_table) SQ_TRY_CUDA(cudaMalloc(&ctx->d_table, sizeof(int32_t) * kTabWords));
     // earlier work on the stream may still read the previous table
@@ -188,6 +191,305 @@ int launch_align(subquad_ctx *ctx, const void *packed, int pack_stride, const ui
     return SUBQUAD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Length-binned scheduling.  Pairs are counted into bins by (query length,
+// target length), a single block turns the counts into offsets, and a
+// warp-aggregated scatter writes the bin-ordered work list.  The alignment
+// kernel then gives each warp 32 consecutive entries of the list: their
+// lengths agree, so the unrolled height is the exact query length and no lane
+// idles waiting for a longer target.
+// ---------------------------------------------------------------------------
+constexpr int kBins = 32 * 32;
+
+template <int WORDS, bool SELF>
+__global__ void bin_count_kernel(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs, int64_t m,
+                                 bool symmetric, uint16_t *__restrict__ bin_of, uint32_t *__restrict__ counts)
+{
+    constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        uint32_t bin = 0xffffu;
+        if (p < m) {
+            uint32_t i, j;
+            if (SELF) {
+                i = j = (uint32_t)p;
+            } else {
+                const uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
+                i = ij.x;
+                j = ij.y;
+            }
+            const ulonglong2 ri = reinterpret_cast<const ulonglong2 *>(packed + (int64_t)i * WORDS)[0];
+            const ulonglong2 rj = reinterpret_cast<const ulonglong2 *>(packed + (int64_t)j * WORDS)[0];
+            const int La = min(sq_record_len(ri.x, ri.y), MAXLEN), Lb = min(sq_record_len(rj.x, rj.y), MAXLEN);
+            const int Lq = symmetric ? min(La, Lb) : La, Lt = symmetric ? max(La, Lb) : Lb;
+            bin = (uint32_t)(Lq * 32 + Lt);
+            bin_of[p] = (uint16_t)bin;
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+        if (bin != 0xffffu && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[bin], (uint32_t)__popc(peers));
+    }
+}
+
+__global__ void __launch_bounds__(1024) bin_offsets_kernel(uint32_t *__restrict__ counts)
+{
+    __shared__ uint32_t s[kBins];
+    s[threadIdx.x] = counts[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < kBins; ++b) {
+            const uint32_t c = s[b];
+            s[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    counts[threadIdx.x] = s[threadIdx.x];
+}
+
+__global__ void bin_scatter_kernel(const uint16_t *__restrict__ bin_of, int64_t m, uint32_t *__restrict__ cursor,
+                                   uint32_t *__restrict__ order)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        const uint32_t bin = p < m ? bin_of[p] : 0xffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+        const int leader = __ffs(peers) - 1;
+        uint32_t pos = 0;
+        if (bin != 0xffffu && lane == leader) pos = atomicAdd(&cursor[bin], (uint32_t)__popc(peers));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (bin != 0xffffu) order[pos + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)p;
+    }
+}
+
+// Two pairs per thread in packed 16-bit halves (pair P low, pair Q high).  Per
+// cell: two table lookups packed with one byte permute, then
+//   E = max(E - e, H(i,j-1) - o, 0)   F = max(F - e, H(i-1,j) - o, 0)  (DPX add-max-relu)
+//   H = max((H(i-1,j-1) - o) + (M + o), max(E, F), 0)                  (packed max, DPX add-max-relu)
+// Every intermediate lies in [-1064, 2953] for |M| <= 64, o, e <= 1000 and
+// lengths <= 30, so 16-bit lanes are exact.  A pair shorter than the other
+// one in its thread is padded with the padding residue in both dimensions.
+__device__ __forceinline__ uint32_t pack2(int32_t lo, int32_t hi)
+{
+    return ((uint32_t)lo & 0xffffu) | ((uint32_t)hi << 16);
+}
+
+template <int WORDS>
+struct TargetStream {
+    uint64_t cur;
+    int left, word;
+    const Rec<WORDS> *t;
+    __device__ __forceinline__ explicit TargetStream(const Rec<WORDS> &r) : cur(r.w[0]), left(12), word(0), t(&r) {}
+    __device__ __forceinline__ uint32_t next()
+    {
+        const uint32_t b = min((uint32_t)cur & 31u, 19u);
+        cur >>= 5;
+        if (--left == 0) {
+            ++word;
+            cur = word == 1 ? t->w[1] : t->w[2 % WORDS];
+            left = 12;
+        }
+        return b;
+    }
+};
+
+template <int WORDS, int NQ>
+__device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, const Rec<WORDS> &tP, int LtP,
+                                             const Rec<WORDS> &qQ, int LqQ, const Rec<WORDS> &tQ, int LtQ,
+                                             const char *__restrict__ s_tab, int lane, int o, int e)
+{
+    uint32_t qoffP[NQ], qoffQ[NQ], E[NQ], HM[NQ];
+    const uint32_t neg_o = pack2(-o, -o), neg_e = pack2(-e, -e);
+#pragma unroll
+    for (int p = 0; p < NQ; ++p) {
+        uint32_t cp = (uint32_t)(qP.w[p / 12] >> (5 * (p % 12))) & 31u;
+        uint32_t cq = (uint32_t)(qQ.w[p / 12] >> (5 * (p % 12))) & 31u;
+        cp = p < LqP ? min(cp, 19u) : 20u;
+        cq = p < LqQ ? min(cq, 19u) : 20u;
+        qoffP[p] = (cp * kTabRows * kLanes + (uint32_t)lane) * 4u;
+        qoffQ[p] = (cq * kTabRows * kLanes + (uint32_t)lane) * 4u;
+        E[p] = 0u;
+        HM[p] = neg_o;
+    }
+    uint32_t best = 0u;
+    TargetStream<WORDS> sP(tP), sQ(tQ);
+    const int Lt = max(LtP, LtQ);
+    for (int j = 0; j < Lt; ++j) {
+        const uint32_t bP = sP.next(), bQ = sQ.next();
+        const char *colP = s_tab + (j < LtP ? bP : 20u) * (kLanes * 4);
+        const char *colQ = s_tab + (j < LtQ ? bQ : 20u) * (kLanes * 4);
+        uint32_t hm_diag = neg_o, hm_up = neg_o, F = 0u;
+#pragma unroll
+        for (int p = 0; p < NQ; ++p) {
+            const uint32_t lo = *reinterpret_cast<const uint32_t *>(colP + qoffP[p]);
+            const uint32_t hi = *reinterpret_cast<const uint32_t *>(colQ + qoffQ[p]);
+            const uint32_t s_o = __byte_perm(lo, hi, 0x5410);
+            const uint32_t e_new = __viaddmax_s16x2_relu(E[p], neg_e, HM[p]);
+            F = __viaddmax_s16x2_relu(F, neg_e, hm_up);
+            const uint32_t h = __viaddmax_s16x2_relu(hm_diag, s_o, __vmaxs2(e_new, F));
+            hm_diag = HM[p];
+            HM[p] = __vadd2(h, neg_o);
+            hm_up = HM[p];
+            E[p] = e_new;
+            best = __vmaxs2(best, h);
+        }
+    }
+    return best;
+}
+
+template <int WORDS, bool SELF>
+__device__ __forceinline__ void load_oriented(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs,
+                                              uint32_t p, bool symmetric, Rec<WORDS> &A, int &La, Rec<WORDS> &B,
+                                              int &Lb)
+{
+    constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
+    uint32_t i, j;
+    if (SELF) {
+        i = j = p;
+    } else {
+        const uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
+        i = ij.x;
+        j = ij.y;
+    }
+    A.load(packed, i);
+    La = min(A.len(), MAXLEN);
+    if (SELF) {
+        B = A;
+        Lb = La;
+    } else {
+        B.load(packed, j);
+        Lb = min(B.len(), MAXLEN);
+    }
+    if (symmetric && Lb < La) {
+        const Rec<WORDS> T = A;
+        A = B;
+        B = T;
+        const int tl = La;
+        La = Lb;
+        Lb = tl;
+    }
+}
+
+// Launch shapes of the batched kernel: 0 = 256 threads, 2 blocks per SM (128
+// registers); 1 = 128 threads, 3 blocks per SM (168 registers, no spills up
+// to 24 rows).  Chosen by the context's tuning (see subquad_set_tuning).
+template <int CFG>
+struct BinnedShape {
+    static constexpr int threads = CFG == 0 ? 256 : 128;
+    static constexpr int blocks = CFG == 0 ? 2 : 3;
+};
+
+template <int WORDS, bool SELF, int CFG>
+__global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::blocks)
+    align_binned_kernel(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs,
+                        const uint32_t *__restrict__ order, int64_t m, const int32_t *__restrict__ table, int o, int e,
+                        bool symmetric, int32_t *__restrict__ out)
+{
+    extern __shared__ int32_t s_tab_words[];
+    for (int q = threadIdx.x; q < kTabWords / 4; q += blockDim.x)
+        reinterpret_cast<int4 *>(s_tab_words)[q] = reinterpret_cast<const int4 *>(table)[q];
+    __syncthreads();
+    const char *s_tab = reinterpret_cast<const char *>(s_tab_words);
+    constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // each warp takes 64 consecutive entries of the bin-ordered list: entry
+    // base + lane in the low halves, base + 32 + lane in the high halves
+    for (int64_t base = warp * 64; base < m; base += nwarps * 64) {
+        const int64_t qP = base + lane, qQ = base + 32 + lane;
+        const bool vP = qP < m, vQ = qQ < m;
+        Rec<WORDS> AP, BP, AQ, BQ;
+        int LaP = 0, LbP = 0, LaQ = 0, LbQ = 0;
+        uint32_t pP = 0, pQ = 0;
+        if (vP) {
+            pP = order[qP];
+            load_oriented<WORDS, SELF>(packed, pairs, pP, symmetric, AP, LaP, BP, LbP);
+        } else {
+            AP.w[0] = AP.w[1] = BP.w[0] = BP.w[1] = 0;
+            if (WORDS == 4) AP.w[2 % WORDS] = BP.w[2 % WORDS] = 0;
+        }
+        if (vQ) {
+            pQ = order[qQ];
+            load_oriented<WORDS, SELF>(packed, pairs, pQ, symmetric, AQ, LaQ, BQ, LbQ);
+        } else {
+            AQ = AP;
+            BQ = BP;
+            LaQ = LaP;
+            LbQ = LbP;
+        }
+        const int wmax = __reduce_max_sync(0xffffffffu, max(LaP, LaQ));
+        if (!vP) continue;
+        uint32_t sc;
+        switch ((wmax + 1) >> 1) {
+#define SQ_CASE(H)                                                                                                 \
+    case H:                                                                                                        \
+        sc = sw_pair2<WORDS, (H < 1 ? 2 : (2 * H <= MAXLEN ? 2 * H : MAXLEN))>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ,  \
+                                                                              s_tab, lane, o, e);                   \
+        break;
+            SQ_CASE(0) SQ_CASE(1) SQ_CASE(2) SQ_CASE(3) SQ_CASE(4) SQ_CASE(5) SQ_CASE(6) SQ_CASE(7) SQ_CASE(8)
+            SQ_CASE(9) SQ_CASE(10) SQ_CASE(11) SQ_CASE(12)
+#undef SQ_CASE
+        default:
+            sc = sw_pair2<WORDS, MAXLEN>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e);
+            break;
+        }
+        out[pP] = (int32_t)(sc & 0xffffu);
+        if (vQ) out[pQ] = (int32_t)(sc >> 16);
+    }
+}
+
+template <bool SELF>
+int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs, int64_t m, int o,
+                  int e, int32_t *out)
+{
+    if (m >= (int64_t(1) << 32)) return SUBQUAD_ERR_ARG;
+    SqArena measure(nullptr);
+    measure.take<uint32_t>(kBins);
+    measure.take<uint16_t>(m);
+    measure.take<uint32_t>(m);
+    SQ_TRY(sq_scratch_reserve(ctx, measure.off));
+    SqArena a(ctx->scratch);
+    uint32_t *counts = a.take<uint32_t>(kBins);
+    uint16_t *bin_of = a.take<uint16_t>(m);
+    uint32_t *order = a.take<uint32_t>(m);
+    SQ_TRY_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * kBins, ctx->stream));
+    const unsigned g = sq_grid(ctx, m, 256, 8);
+    const uint64_t *pk = static_cast<const uint64_t *>(packed);
+    if (pack_stride == 16)
+        bin_count_kernel<2, SELF><<<g, 256, 0, ctx->stream>>>(pk, pairs, m, ctx->matrix_symmetric, bin_of, counts);
+    else
+        bin_count_kernel<4, SELF><<<g, 256, 0, ctx->stream>>>(pk, pairs, m, ctx->matrix_symmetric, bin_of, counts);
+    SQ_LAUNCH_CHECK();
+    bin_offsets_kernel<<<1, kBins, 0, ctx->stream>>>(counts);
+    SQ_LAUNCH_CHECK();
+    bin_scatter_kernel<<<g, 256, 0, ctx->stream>>>(bin_of, m, counts, order);
+    SQ_LAUNCH_CHECK();
+    const size_t smem = sizeof(int32_t) * kTabWords;
+#define SQ_BINNED(W, C)                                                                                            \
+    do {                                                                                                           \
+        auto k = align_binned_kernel<W, SELF, C>;                                                                  \
+        SQ_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));             \
+        const unsigned grid = sq_grid(ctx, (m + 1) / 2, BinnedShape<C>::threads, BinnedShape<C>::blocks);         \
+        k<<<grid, BinnedShape<C>::threads, smem, ctx->stream>>>(pk, pairs, order, m, ctx->d_table, o, e,           \
+                                                               ctx->matrix_symmetric, out);                        \
+    } while (0)
+    const int cfg = ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE];
+    if (pack_stride == 16) {
+        if (cfg == 0) SQ_BINNED(2, 0);
+        else SQ_BINNED(2, 1);
+    } else {
+        if (cfg == 0) SQ_BINNED(4, 0);
+        else SQ_BINNED(4, 1);
+    }
+#undef SQ_BINNED
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
+}
+
 }  // namespace
 
 extern "C" int subquad_align_score(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs,
@@ -214,4 +516,31 @@ extern "C" int subquad_self_scores(subquad_ctx *ctx, const void *packed, int pac
     if (reinterpret_cast<uintptr_t>(packed) % 16) return SUBQUAD_ERR_ARG;
     SQ_TRY(ensure_table(ctx, gap_open));
     return launch_align<true>(ctx, packed, pack_stride, nullptr, n, gap_open, gap_extend, self_out);
+}
+
+extern "C" int subquad_align_score_binned(subquad_ctx *ctx, const void *packed, int pack_stride,
+                                          const uint32_t *pairs, int64_t m, int gap_open, int gap_extend,
+                                          int32_t *scores_out)
+{
+    SQ_ENTER(ctx);
+    if (m < 0 || gap_open < 0 || gap_open > 1000 || gap_extend < 0 || gap_extend > 1000) return SUBQUAD_ERR_ARG;
+    if (pack_stride != 16 && pack_stride != 32) return SUBQUAD_ERR_ARG;
+    if (m == 0) return SUBQUAD_OK;
+    if (!packed || !pairs || !scores_out) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(packed) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8) return SUBQUAD_ERR_ARG;
+    SQ_TRY(ensure_table(ctx, gap_open));
+    return launch_binned<false>(ctx, packed, pack_stride, pairs, m, gap_open, gap_extend, scores_out);
+}
+
+extern "C" int subquad_self_scores_binned(subquad_ctx *ctx, const void *packed, int pack_stride, int64_t n,
+                                          int gap_open, int gap_extend, int32_t *self_out)
+{
+    SQ_ENTER(ctx);
+    if (n < 0 || gap_open < 0 || gap_open > 1000 || gap_extend < 0 || gap_extend > 1000) return SUBQUAD_ERR_ARG;
+    if (pack_stride != 16 && pack_stride != 32) return SUBQUAD_ERR_ARG;
+    if (n == 0) return SUBQUAD_OK;
+    if (!packed || !self_out) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(packed) % 16) return SUBQUAD_ERR_ARG;
+    SQ_TRY(ensure_table(ctx, gap_open));
+    return launch_binned<true>(ctx, packed, pack_stride, nullptr, n, gap_open, gap_extend, self_out);
 }

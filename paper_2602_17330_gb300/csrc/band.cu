@@ -1,7 +1,7 @@
 // (a2) LSH banding, candidate emission and deduplication (Algorithm 1,
 // preprocessing: "build MinHash index; generate candidate list CAND").
 //
-// Per group of bands (all bands at once unless the keys would overflow):
+// Bands are inserted in groups whose hash tables fit a share of L2:
 //  1. insert every (band, sequence) key -- the exact R-tuple -- into a
 //     per-band open-addressing table whose slots hold the id of the first
 //     inserter; equal keys meet at one slot, so the slot index is an exact
@@ -68,76 +68,103 @@ __device__ __forceinline__ bool key_equal(const uint32_t *__restrict__ p, int ro
     return eq;
 }
 
-// Step 1: exact bucket id (= table slot) per (band, sequence), and the number
-// of members of every bucket.
+// Block-wide exclusive position of each flagged thread in an append buffer:
+// one global atomic per block instead of one per warp, so a single hot counter
+// is touched 8x less often.
+__device__ __forceinline__ unsigned long long block_append(bool flag, unsigned long long *counter,
+                                                           unsigned long long *s_base, uint32_t *s_warp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t mask = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) s_warp[warp] = __popc(mask);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int w = 0; w < nw; ++w) {
+            const uint32_t c = s_warp[w];
+            s_warp[w] = run;
+            run += c;
+        }
+        *s_base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long pos = *s_base + s_warp[warp] + __popc(mask & ((1u << lane) - 1u));
+    __syncthreads();
+    return pos;
+}
+
+// Step 1: exact bucket id (= table slot) per (band, sequence).  A slot holds
+// the id of its first inserter (whose key it stands for) in bits 0..30; bit 31
+// is set, by a plain store, as soon as a second member arrives.  Only the
+// first member of a bucket uses an atomic (the claiming CAS), so a bucket of
+// hundreds of members adds no contended atomics.  blockIdx.y = band in group.
+constexpr uint32_t kShared = 0x80000000u;
+
 __global__ void __launch_bounds__(256) band_insert_kernel(const uint32_t *__restrict__ sig, int64_t n, int rows,
-                                                          int band0, int gbands, int log_s,
-                                                          uint32_t *__restrict__ table, uint32_t *__restrict__ counts,
+                                                          int band0, int log_s, uint32_t *__restrict__ table,
                                                           uint32_t *__restrict__ slot_of, uint32_t *err)
 {
-    const int64_t total = (int64_t)gbands * n;
+    const int gb = blockIdx.y;
     const uint32_t smask = (1u << log_s) - 1u;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int gb = (int)(e / n);
-        const uint32_t i = (uint32_t)(e - (int64_t)gb * n);
-        const uint32_t *band_sig = sig + (int64_t)(band0 + gb) * n * rows;
+    const uint32_t *band_sig = sig + (int64_t)(band0 + gb) * n * rows;
+    uint32_t *tab = table + ((int64_t)gb << log_s);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t k[8];
-        load_key(band_sig + (int64_t)i * rows, rows, k);
+        load_key(band_sig + i * rows, rows, k);
         uint32_t h = 0x9e3779b9u ^ (uint32_t)rows;
 #pragma unroll
         for (int r = 0; r < 8; ++r)
             if (r < rows) h = mix32(h ^ k[r]);
-        uint32_t *tab = table + ((int64_t)gb << log_s);
         uint32_t slot = h & smask;
         bool found = false;
         // the table is at most half full, so a free slot is always reached
         for (uint32_t probe = 0; probe <= smask; ++probe) {
             uint32_t cur = tab[slot];
             if (cur == kEmpty) {
-                cur = atomicCAS(&tab[slot], kEmpty, i);
+                cur = atomicCAS(&tab[slot], kEmpty, (uint32_t)i);
                 if (cur == kEmpty) {
                     found = true;
                     break;
                 }
             }
-            if (key_equal(band_sig + (int64_t)cur * rows, rows, k)) {
+            if (key_equal(band_sig + (int64_t)(cur & ~kShared) * rows, rows, k)) {
+                // the owner id never changes once claimed, so storing owner|flag
+                // can only ever write the same value
+                if (!(cur & kShared)) tab[slot] = cur | kShared;
                 found = true;
                 break;
             }
             slot = (slot + 1) & smask;
         }
         if (!found) atomicOr(err, SQ_DEVERR_TIMEOUT);
-        const uint32_t gs = ((uint32_t)gb << log_s) | slot;
-        atomicAdd(&counts[gs], 1u);
-        slot_of[e] = gs;
+        slot_of[(int64_t)gb * n + i] = slot;
     }
 }
 
 // Step 1b: keep the members of buckets with >= 2 members (singletons can form
-// no pair), as keys (bucket << nbits) | id, appended in any order -- the sort
-// that follows orders them by bucket, then id.
+// no pair), as keys ((band << log_s | slot) << nbits) | id, appended in any
+// order -- the sort that follows orders them by band, bucket, then id.  A
+// member is kept if its bucket's slot is flagged shared.
 __global__ void __launch_bounds__(256) band_filter_kernel(const uint32_t *__restrict__ slot_of,
-                                                          const uint32_t *__restrict__ counts, int64_t n, int gbands,
-                                                          int nbits, uint64_t *__restrict__ keys,
-                                                          uint32_t *__restrict__ d_kept)
+                                                          const uint32_t *__restrict__ table, int64_t n, int band0,
+                                                          int log_s, int nbits, uint64_t *__restrict__ keys,
+                                                          unsigned long long *__restrict__ d_kept)
 {
-    const int64_t total = (int64_t)gbands * n;
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = base + threadIdx.x;
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_warp[32];
+    const int gb = blockIdx.y;
+    const uint32_t *tab = table + ((int64_t)gb << log_s);
+    const uint32_t *slots = slot_of + (int64_t)gb * n;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
         bool keep = false;
-        uint64_t key = 0;
-        if (e < total) {
-            const uint32_t gs = slot_of[e];
-            keep = counts[gs] >= 2u;
-            const uint32_t i = (uint32_t)(e % n);
-            key = ((uint64_t)gs << nbits) | i;
+        uint32_t slot = 0;
+        if (i < n) {
+            slot = slots[i];
+            keep = (tab[slot] & kShared) != 0u;
         }
-        const uint32_t mask = __ballot_sync(0xffffffffu, keep);
-        uint32_t pos = 0;
-        if (lane == 0 && mask) pos = atomicAdd(d_kept, (uint32_t)__popc(mask));
-        pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (keep) keys[pos + __popc(mask & ((1u << lane) - 1u))] = key;
+        const unsigned long long pos = block_append(keep, d_kept, &s_base, s_warp);
+        if (keep) keys[pos] = ((((uint64_t)(band0 + gb) << log_s) | slot) << nbits) | (uint64_t)i;
     }
 }
 
@@ -183,7 +210,7 @@ __global__ void band_chunks_kernel(const uint64_t *__restrict__ keys, int nbits,
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
         ChunkInfo c = chunk_info(run_start, count, e, cap);
         const uint64_t k = keys[e];
-        const int b = band0 + (int)((k >> nbits) >> log_s);
+        const int b = (int)((k >> nbits) >> log_s);
         chunk_of[(int64_t)(k & idmask) * bands + b] = c.head;
         flags[e] = (c.is_head && !c.is_last) ? 1u : 0u;
     }
@@ -231,15 +258,17 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
     const uint64_t *__restrict__ d_total, int log_s, int band0, int bands, const uint32_t *__restrict__ chunk_of,
     uint32_t *__restrict__ out, int64_t capacity, unsigned long long *__restrict__ d_count, uint32_t *err)
 {
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_warp[32];
     const uint32_t nc = *d_nchunks;
     const uint64_t total = *d_total;
     const int lane = threadIdx.x & 31;
-    const int64_t warp_id = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t q0 = (uint64_t)warp_id * 32; q0 < total; q0 += (uint64_t)nwarps * 32) {
+    // block-uniform trip count (block_append synchronises the block)
+    for (uint64_t b0 = (uint64_t)blockIdx.x * blockDim.x; b0 < total; b0 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q0 = b0 + (threadIdx.x & ~31u);
         // chunk of q0: largest c with poff[c] <= q0 (every chunk has >= 1 pair)
         uint32_t c0 = 0;
-        if (lane == 0) {
+        if (lane == 0 && q0 < total) {
             uint32_t lo = 0, hi = nc;
             while (hi - lo > 1) {
                 uint32_t mid = (lo + hi) >> 1;
@@ -270,7 +299,7 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
             const uint64_t idmask = (1ull << nbits) - 1ull;
             i = (uint32_t)(keys[h + u] & idmask);
             j = (uint32_t)(keys[h + v] & idmask);
-            const int b = band0 + (int)((keys[h] >> nbits) >> log_s);
+            const int b = (int)((keys[h] >> nbits) >> log_s);
             owned = true;
             const uint32_t *gi = chunk_of + (int64_t)i * bands;
             const uint32_t *gj = chunk_of + (int64_t)j * bands;
@@ -280,14 +309,8 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
                     break;
                 }
         }
-        const uint32_t mask = __ballot_sync(0xffffffffu, owned);
-        unsigned long long base = 0;
-        if (lane == 0 && mask) base = atomicAdd(d_count, (unsigned long long)__popc(mask));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (owned) {
-            const unsigned long long pos = base + __popc(mask & ((1u << lane) - 1u));
-            if (pos < (unsigned long long)capacity) reinterpret_cast<uint2 *>(out)[pos] = make_uint2(i, j);
-        }
+        const unsigned long long pos = block_append(owned, d_count, &s_base, s_warp);
+        if (owned && pos < (unsigned long long)capacity) reinterpret_cast<uint2 *>(out)[pos] = make_uint2(i, j);
     }
 }
 
@@ -345,35 +368,37 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
     if (reinterpret_cast<uintptr_t>(sig) % 16 || reinterpret_cast<uintptr_t>(pairs_out) % 8) return SUBQUAD_ERR_ARG;
     const int cap = (bucket_cap <= 0 || bucket_cap >= n) ? 0 : bucket_cap;
 
-    // table of S >= 2n slots per band; a group of G bands keeps G*S <= 2^32
-    // and the sort key (bucket << nbits | id) within 64 bits
+    // Table of S >= 2n 32-bit slots per band.  Bands are inserted in groups
+    // whose tables fit a share of L2 (the random probes then stay on chip);
+    // the kept keys of all bands are sorted and chunked together.
     const int log_s = bits_for((uint64_t)(2 * n - 1));
     const int64_t S = int64_t(1) << log_s;
     const int nbits = bits_for((uint64_t)(n - 1));
-    int G = (int)std::min<int64_t>(bands, (int64_t(1) << 32) / S);
-    while (G > 1 && nbits + log_s + bits_for((uint64_t)(G - 1)) > 64) --G;
-    if (G < 1) return SUBQUAD_ERR_ARG;
-    const int64_t mg = (int64_t)G * n;
+    const int key_bits = nbits + log_s + bits_for((uint64_t)(bands - 1));
+    if (key_bits > 64) return SUBQUAD_ERR_ARG;
+    const int64_t l2_budget = (int64_t)ctx->tune[SUBQUAD_TUNE_BAND_L2_MB] << 20;
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(bands, l2_budget / (S * 4)));
+    const int64_t mg = (int64_t)G * n;       // elements per insert group
+    const int64_t mall = (int64_t)bands * n;  // upper bound of kept keys
 
     auto layout = [&](SqArena &a) {
         struct L {
-            uint32_t *chunk_of, *table, *counts, *slot_of, *run_start, *flags, *cidx, *heads, *sizes;
+            uint32_t *chunk_of, *table, *slot_of, *run_start, *flags, *cidx, *heads, *sizes;
             uint64_t *k0, *k1, *npairs;
             void *tmp;
         } l;
         l.chunk_of = a.take<uint32_t>((size_t)n * bands);
         l.table = a.take<uint32_t>((size_t)G * S);
-        l.counts = a.take<uint32_t>((size_t)G * S);
         l.slot_of = a.take<uint32_t>(mg);
-        l.k0 = a.take<uint64_t>(mg);
-        l.k1 = a.take<uint64_t>(mg);
-        l.run_start = a.take<uint32_t>(mg);
-        l.flags = a.take<uint32_t>(mg);
-        l.cidx = a.take<uint32_t>(mg);
-        l.heads = a.take<uint32_t>(mg);
-        l.sizes = a.take<uint32_t>(mg);
-        l.npairs = a.take<uint64_t>(mg);
-        l.tmp = a.take<char>(std::max(sq_radix_tmp_bytes(mg), sq_scan_tmp_bytes(mg)));
+        l.k0 = a.take<uint64_t>(mall);
+        l.k1 = a.take<uint64_t>(mall);
+        l.run_start = a.take<uint32_t>(mall);
+        l.flags = a.take<uint32_t>(mall);
+        l.cidx = a.take<uint32_t>(mall);
+        l.heads = a.take<uint32_t>(mall);
+        l.sizes = a.take<uint32_t>(mall);
+        l.npairs = a.take<uint64_t>(mall);
+        l.tmp = a.take<char>(std::max(sq_radix_tmp_bytes(mall), sq_scan_tmp_bytes(mall)));
         return l;
     };
     SqArena measure(nullptr);
@@ -381,49 +406,48 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
     SQ_TRY(sq_scratch_reserve(ctx, measure.off));
     SqArena arena(ctx->scratch);
     auto L = layout(arena);
-    const size_t tmp_bytes = std::max(sq_radix_tmp_bytes(mg), sq_scan_tmp_bytes(mg));
+    const size_t tmp_bytes = std::max(sq_radix_tmp_bytes(mall), sq_scan_tmp_bytes(mall));
 
     unsigned long long *d_count = reinterpret_cast<unsigned long long *>(ctx->d_small);
     uint32_t *d_nchunks = reinterpret_cast<uint32_t *>(ctx->d_small + 1);
     uint64_t *d_total = ctx->d_small + 2;
-    uint32_t *d_kept = reinterpret_cast<uint32_t *>(ctx->d_small + 3);
+    unsigned long long *d_kept64 = reinterpret_cast<unsigned long long *>(ctx->d_small + 3);
+    const uint32_t *d_kept = reinterpret_cast<const uint32_t *>(ctx->d_small + 3);  // low word (< 2^32 keys)
     SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 8 * sizeof(uint64_t), ctx->stream));
     SQ_TRY_CUDA(cudaMemsetAsync(L.chunk_of, 0xff, (size_t)n * bands * sizeof(uint32_t), ctx->stream));
 
     for (int band0 = 0; band0 < bands; band0 += G) {
         const int gb = std::min(G, bands - band0);
-        const int64_t count = (int64_t)gb * n;
-        const unsigned grid = sq_grid(ctx, count, 256, 8);
+        const dim3 grid(sq_grid(ctx, n, 256, (8 + gb - 1) / gb), gb);
         SQ_TRY_CUDA(cudaMemsetAsync(L.table, 0xff, (size_t)gb * S * sizeof(uint32_t), ctx->stream));
-        SQ_TRY_CUDA(cudaMemsetAsync(L.counts, 0, (size_t)gb * S * sizeof(uint32_t), ctx->stream));
-        SQ_TRY_CUDA(cudaMemsetAsync(d_kept, 0, sizeof(uint32_t), ctx->stream));
-        band_insert_kernel<<<grid, 256, 0, ctx->stream>>>(sig, n, rows, band0, gb, log_s, L.table, L.counts,
-                                                          L.slot_of, ctx->d_err);
+        band_insert_kernel<<<grid, 256, 0, ctx->stream>>>(sig, n, rows, band0, log_s, L.table, L.slot_of, ctx->d_err);
         SQ_LAUNCH_CHECK();
-        band_filter_kernel<<<grid, 256, 0, ctx->stream>>>(L.slot_of, L.counts, n, gb, nbits, L.k0, d_kept);
+        band_filter_kernel<<<grid, 256, 0, ctx->stream>>>(L.slot_of, L.table, n, band0, log_s, nbits, L.k0, d_kept64);
         SQ_LAUNCH_CHECK();
+    }
+    {
+        const unsigned grid = sq_grid(ctx, mall, 256, 8);
         bool in_alt = false;
-        const int key_bits = nbits + log_s + bits_for((uint64_t)(gb - 1));
-        SQ_TRY(sq_radix_sort_u64(ctx, L.k0, L.k1, count, d_kept, 0, key_bits, &in_alt, L.tmp, tmp_bytes));
+        SQ_TRY(sq_radix_sort_u64(ctx, L.k0, L.k1, mall, d_kept, 0, key_bits, &in_alt, L.tmp, tmp_bytes));
         const uint64_t *K = in_alt ? L.k1 : L.k0;
-        band_heads_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, count, d_kept, L.run_start);
+        band_heads_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, mall, d_kept, L.run_start);
         SQ_LAUNCH_CHECK();
-        SQ_TRY(sq_scan_u32(ctx, L.run_start, L.run_start, count, d_kept, true, true, nullptr, L.tmp, tmp_bytes));
-        band_chunks_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, L.run_start, count, d_kept, cap, log_s, band0,
-                                                          bands, L.chunk_of, L.flags);
+        SQ_TRY(sq_scan_u32(ctx, L.run_start, L.run_start, mall, d_kept, true, true, nullptr, L.tmp, tmp_bytes));
+        band_chunks_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, L.run_start, mall, d_kept, cap, log_s, 0, bands,
+                                                          L.chunk_of, L.flags);
         SQ_LAUNCH_CHECK();
-        SQ_TRY(sq_scan_u32(ctx, L.flags, L.cidx, count, d_kept, false, false, d_nchunks, L.tmp, tmp_bytes));
-        band_chunk_list_kernel<<<grid, 256, 0, ctx->stream>>>(L.run_start, L.flags, L.cidx, count, d_kept, cap,
+        SQ_TRY(sq_scan_u32(ctx, L.flags, L.cidx, mall, d_kept, false, false, d_nchunks, L.tmp, tmp_bytes));
+        band_chunk_list_kernel<<<grid, 256, 0, ctx->stream>>>(L.run_start, L.flags, L.cidx, mall, d_kept, cap,
                                                               L.heads, L.sizes, L.npairs);
         SQ_LAUNCH_CHECK();
         // pair counts -> offsets.  Only the first nchunks entries are written;
         // an exclusive prefix at entry c depends on entries < c only, so the
         // unwritten tail never reaches a used offset.
-        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, count, d_kept, nullptr, L.tmp, tmp_bytes));
+        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, mall, d_kept, nullptr, L.tmp, tmp_bytes));
         band_total_kernel<<<1, 1, 0, ctx->stream>>>(L.npairs, L.sizes, d_nchunks, d_total);
         SQ_LAUNCH_CHECK();
         band_emit_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(
-            K, nbits, L.heads, L.sizes, L.npairs, d_nchunks, d_total, log_s, band0, bands, L.chunk_of, pairs_out,
+            K, nbits, L.heads, L.sizes, L.npairs, d_nchunks, d_total, log_s, 0, bands, L.chunk_of, pairs_out,
             pairs_capacity, d_count, ctx->d_err);
         SQ_LAUNCH_CHECK();
     }

@@ -1,13 +1,15 @@
 // (a4) Per-pair gated fusion of the alignment and embedding channels
-// (Eq. alpha, Eq. wm, Eq. afused with M = 2 channels).
+// (Eq. alpha, Eq. wm, Eq. afused with M = 2 channels), and its adjoint.
 //
-// A half-warp (16 lanes) owns one pair: each lane loads float4 slices of e_i
-// and e_j (coalesced 256-byte rows for d = 64), the dot product and both
-// squared norms are reduced with shuffles (a pairwise tree, so FP32 rounding
-// grows with log2(d)), each lane then evaluates hidden units k = lane,
-// lane + 16, ... of the gate MLP from parameters staged in shared memory, and
-// a second shuffle tree gives the logit g.  alpha = sigmoid(g) is the
-// two-logit softmax of Eq. wm with logits (g, 0).
+// Forward: four lanes own one pair (eight pairs per warp).  Each lane loads
+// d/16 float4 slices of e_i and e_j (for d = 64 a pair's two rows are read as
+// 4 x 64-byte pieces), accumulates the dot product and both squared norms,
+// and two shuffle levels finish them; each lane then evaluates hidden units
+// k = lane, lane + 4, ... of the gate MLP from parameters staged in shared
+// memory, and two more shuffle levels give the logit g.  alpha = sigmoid(g)
+// is the two-logit softmax of Eq. wm with logits (g, 0).  The kernel is
+// instruction-bound at 16 lanes per pair, so the split favours fewer
+// shuffles and more work per lane.
 #include "internal.cuh"
 
 namespace {
@@ -23,6 +25,15 @@ __device__ __forceinline__ float group_sum(float v)
     return v;
 }
 
+constexpr int kTppF = 4;  // lanes per pair in the forward kernel
+
+__device__ __forceinline__ float quad_sum(float v)
+{
+    v += __shfl_xor_sync(0xffffffffu, v, 2, kTppF);
+    v += __shfl_xor_sync(0xffffffffu, v, 1, kTppF);
+    return v;
+}
+
 template <int WORDS>
 __device__ __forceinline__ int record_len(const uint64_t *__restrict__ packed, uint32_t i)
 {
@@ -33,7 +44,7 @@ __device__ __forceinline__ int record_len(const uint64_t *__restrict__ packed, u
 // Per-pair inputs of the fusion, all loads issued together so one round trip
 // to memory (after the pair indices) covers the embedding rows, the alignment
 // score, both self-scores and both lengths.
-template <int WORDS, int CPL>
+template <int WORDS, int CPL, int TPP = kTpp>
 struct PairInputs {
     float4 a[CPL], b[CPL];
     int32_t sw, self_i, self_j;
@@ -47,7 +58,7 @@ struct PairInputs {
         const float4 *ej = reinterpret_cast<const float4 *>(emb + (int64_t)ij.y * d);
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
-            const int k = sub + c * kTpp;
+            const int k = sub + c * TPP;
             const bool ok = valid && k < d4;
             a[c] = ok ? __ldg(ei + k) : make_float4(0.f, 0.f, 0.f, 0.f);
             b[c] = ok ? __ldg(ej + k) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -78,43 +89,44 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
     __syncthreads();
     const float *W1 = s_par, *b1 = s_par + 3 * hidden, *w2 = s_par + 4 * hidden;
     const float b2 = s_par[5 * hidden];
-    const int sub = threadIdx.x & (kTpp - 1);
-    const int half = (threadIdx.x >> 4) & 1;
+    constexpr int kPairsPerWarp = 32 / kTppF;
+    const int sub = threadIdx.x & (kTppF - 1);
+    const int slot = (threadIdx.x & 31) / kTppF;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int d4 = d >> 2;
     // the trip count is uniform per warp, so full-warp shuffles are safe
-    for (int64_t pbase = warp * 2; pbase < m; pbase += nwarps * 2) {
-        const int64_t p = pbase + half;
+    for (int64_t pbase = warp * kPairsPerWarp; pbase < m; pbase += nwarps * kPairsPerWarp) {
+        const int64_t p = pbase + slot;
         const bool valid = p < m;
         const uint2 ij = valid ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p) : make_uint2(0, 0);
-        PairInputs<WORDS, CPL> in;
+        PairInputs<WORDS, CPL, kTppF> in;
         in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
         float dot = 0.f, sii = 0.f, sjj = 0.f;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             const float4 a = in.a[c], b = in.b[c];
-            dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w))) + dot;
-            sii = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, a.w * a.w))) + sii;
-            sjj = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, b.w * b.w))) + sjj;
+            dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, dot))));
+            sii = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, sii))));
+            sjj = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, sjj))));
         }
-        dot = group_sum(dot);
-        sii = group_sum(sii);
-        sjj = group_sum(sjj);
+        dot = quad_sum(dot);
+        sii = quad_sum(sii);
+        sjj = quad_sum(sjj);
         const float prod = (float)in.self_i * (float)in.self_j;
-        const float s = prod > 0.f ? (float)in.sw / sqrtf(prod) : 0.f;
+        const float s = prod > 0.f ? (float)in.sw * rsqrtf(prod) : 0.f;
         const float nn = sii * sjj;
-        const float c = nn > 0.f ? dot / sqrtf(nn) : 0.f;
+        const float c = nn > 0.f ? dot * rsqrtf(nn) : 0.f;
         const float delta = fabsf((float)(in.len_i - in.len_j));
         float acc = 0.f;
-        for (int k = sub; k < hidden; k += kTpp) {
+        for (int k = sub; k < hidden; k += kTppF) {
             float z = fmaf(W1[3 * k], s, fmaf(W1[3 * k + 1], c, fmaf(W1[3 * k + 2], delta, b1[k])));
             acc = fmaf(w2[k], fmaxf(z, 0.f), acc);
         }
-        const float g = group_sum(acc) + b2;
+        const float g = quad_sum(acc) + b2;
         if (valid && sub == 0) {
-            const float a = 1.f / (1.f + expf(-g));
-            fused[p] = a * s + (1.f - a) * 0.5f * (1.f + c);
+            const float a = __fdividef(1.f, 1.f + __expf(-g));
+            fused[p] = fmaf(a, s - 0.5f * (1.f + c), 0.5f * (1.f + c));
             if (alpha_out) alpha_out[p] = a;
         }
     }
@@ -125,7 +137,7 @@ int launch_forward(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64
                    const int32_t *self_scores, const void *packed, const float *emb, int d, const float *gate_params,
                    int hidden, float *fused_out, float *alpha_out)
 {
-    const int cpl = (d / 4 + kTpp - 1) / kTpp;  // float4 chunks per lane
+    const int cpl = (d / 4 + kTppF - 1) / kTppF;  // float4 chunks per lane
 #define SQ_FWD(C)                                                                                                  \
     fuse_forward_kernel<WORDS, C><<<grid, kFuseThreads, 0, ctx->stream>>>(                                         \
         pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d, gate_params, hidden, fused_out, alpha_out)
@@ -133,7 +145,9 @@ int launch_forward(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64
     else if (cpl <= 2) SQ_FWD(2);
     else if (cpl <= 4) SQ_FWD(4);
     else if (cpl <= 8) SQ_FWD(8);
-    else SQ_FWD(16);
+    else if (cpl <= 16) SQ_FWD(16);
+    else if (cpl <= 32) SQ_FWD(32);
+    else SQ_FWD(64);
 #undef SQ_FWD
     SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
@@ -397,7 +411,7 @@ extern "C" int subquad_fuse_forward(subquad_ctx *ctx, const uint32_t *pairs, int
     if (reinterpret_cast<uintptr_t>(emb) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8 ||
         reinterpret_cast<uintptr_t>(packed) % 16)
         return SUBQUAD_ERR_ARG;
-    const unsigned grid = sq_grid(ctx, (m + 1) / 2 * 32, kFuseThreads, 8);
+    const unsigned grid = sq_grid(ctx, (m + 7) / 8 * 32, kFuseThreads, 8);
     if (pack_stride == 16)
         return launch_forward<2>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden, fused_out,
                                  alpha_out);

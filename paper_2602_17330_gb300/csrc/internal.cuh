@@ -27,6 +27,7 @@ struct subquad_ctx {
     void *scratch = nullptr;
     size_t scratch_cap = 0;
     int64_t launches = 0;  // kernels launched through this context
+    int tune[SUBQUAD_TUNE_COUNT];  // tuning knobs, see subquad_set_tuning
 };
 
 // Last CUDA error seen by the library on this thread (for diagnostics).

@@ -24,6 +24,7 @@ class Workload:
     d: int = 64
     hidden: int = 16
     pack_stride: int = 16
+    binned: bool = True  # length-binned alignment (False: pairs in input order)
 
     @property
     def hashes(self) -> int:
@@ -82,9 +83,9 @@ class Pipeline:
         mark("band")
         m = int(pairs.shape[0])
         self._ensure(m)
-        self_sc = ctx.self_scores(packed, cfg.gap_open, cfg.gap_extend)
+        self_sc = ctx.self_scores(packed, cfg.gap_open, cfg.gap_extend, binned=cfg.binned)
         mark("self")
-        sw = ctx.align_score(packed, pairs, cfg.gap_open, cfg.gap_extend, out=self.sw_buf[:m])
+        sw = ctx.align_score(packed, pairs, cfg.gap_open, cfg.gap_extend, out=self.sw_buf[:m], binned=cfg.binned)
         mark("align")
         fused = ctx.fuse_forward(pairs, sw, self_sc, packed, x["emb"], x["params"], cfg.hidden,
                                  out=self.fused_buf[:m])
@@ -93,9 +94,13 @@ class Pipeline:
 
     def forward_numpy(self, rep, a, b, emb, params):
         out = self.forward(self.upload(rep, a, b, emb, params))
+        cfg = self.cfg
+        other = self.ctx.align_score(out["packed"], out["pairs"], cfg.gap_open, cfg.gap_extend, binned=not cfg.binned)
         self.ctx.check()
-        return dict(sig=out["sig"].cpu().numpy().view(np.uint32), pairs=out["pairs"].cpu().numpy().view(np.uint32),
-                    self=out["self"].cpu().numpy(), sw=out["sw"].cpu().numpy(), fused=out["fused"].cpu().numpy())
+        res = dict(sig=out["sig"].cpu().numpy().view(np.uint32), pairs=out["pairs"].cpu().numpy().view(np.uint32),
+                   self=out["self"].cpu().numpy(), sw=out["sw"].cpu().numpy(), fused=out["fused"].cpu().numpy())
+        res["sw_binned" if not cfg.binned else "sw_plain"] = other.cpu().numpy()
+        return res
 
 
 def cells_of(lens: np.ndarray, pairs: np.ndarray) -> int:

@@ -28,6 +28,9 @@ SUBQUAD_ERR_TIMEOUT = -4
 SUBQUAD_ERR_NOMEM = -5
 SUBQUAD_ERR_INPUT = -6
 
+TUNE_ALIGN_SHAPE = 0
+TUNE_BAND_L2_MB = 1
+
 _c = ctypes
 _P = _c.c_void_p
 _I64 = _c.c_int64
@@ -42,6 +45,8 @@ SIGNATURES = {
     "subquad_check": (_c.c_int, [_P]),
     "subquad_scratch_bytes": (_I64, [_P]),
     "subquad_launch_count": (_I64, [_P]),
+    "subquad_set_tuning": (_c.c_int, [_P, _c.c_int, _c.c_int]),
+    "subquad_get_tuning": (_c.c_int, [_P, _c.c_int, _c.POINTER(_c.c_int)]),
     "subquad_default_matrix": (_c.c_int, [_P]),
     "subquad_set_matrix": (_c.c_int, [_P, _P]),
     "subquad_pack_stride": (_c.c_int, [_c.c_int]),
@@ -51,6 +56,8 @@ SIGNATURES = {
                                            _c.POINTER(_I64)]),
     "subquad_align_score": (_c.c_int, [_P, _P, _c.c_int, _P, _I64, _c.c_int, _c.c_int, _P]),
     "subquad_self_scores": (_c.c_int, [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _P]),
+    "subquad_align_score_binned": (_c.c_int, [_P, _P, _c.c_int, _P, _I64, _c.c_int, _c.c_int, _P]),
+    "subquad_self_scores_binned": (_c.c_int, [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _P]),
     "subquad_fuse_forward": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P, _c.c_int, _P, _P]),
     "subquad_pair_labels": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "subquad_pair_weights": (_c.c_int, [_P, _P, _I64, _c.c_int, _P]),
@@ -154,6 +161,14 @@ class Context:
     def launch_count(self) -> int:
         return int(lib().subquad_launch_count(self.handle))
 
+    def set_tuning(self, key: int, value: int):
+        _check(lib().subquad_set_tuning(self.handle, key, value), "subquad_set_tuning")
+
+    def get_tuning(self, key: int) -> int:
+        v = ctypes.c_int(0)
+        _check(lib().subquad_get_tuning(self.handle, key, ctypes.byref(v)), "subquad_get_tuning")
+        return int(v.value)
+
     def set_matrix(self, matrix=None):
         if matrix is None:
             _check(lib().subquad_set_matrix(self.handle, None), "subquad_set_matrix")
@@ -213,20 +228,24 @@ class Context:
         _check(st, "subquad_band_candidates")
         return out[: int(count.value)]
 
-    def align_score(self, packed, pairs, gap_open: int = 10, gap_extend: int = 1, out=None):
+    def align_score(self, packed, pairs, gap_open: int = 10, gap_extend: int = 1, out=None, binned: bool = False):
+        """binned=False: subquad_align_score (pairs in input order);
+        binned=True: subquad_align_score_binned (length-binned work list)."""
         torch = self.torch
         m = int(pairs.shape[0])
         out = self._empty((m,), torch.int32) if out is None else out
-        _check(lib().subquad_align_score(self.handle, _ptr(packed), int(packed.shape[1]), _ptr(pairs), m, gap_open,
-                                         gap_extend, _ptr(out)), "subquad_align_score")
+        name = "subquad_align_score_binned" if binned else "subquad_align_score"
+        _check(getattr(lib(), name)(self.handle, _ptr(packed), int(packed.shape[1]), _ptr(pairs), m, gap_open,
+                                    gap_extend, _ptr(out)), name)
         return out
 
-    def self_scores(self, packed, gap_open: int = 10, gap_extend: int = 1, out=None):
+    def self_scores(self, packed, gap_open: int = 10, gap_extend: int = 1, out=None, binned: bool = False):
         torch = self.torch
         n = int(packed.shape[0])
         out = self._empty((n,), torch.int32) if out is None else out
-        _check(lib().subquad_self_scores(self.handle, _ptr(packed), int(packed.shape[1]), n, gap_open, gap_extend,
-                                         _ptr(out)), "subquad_self_scores")
+        name = "subquad_self_scores_binned" if binned else "subquad_self_scores"
+        _check(getattr(lib(), name)(self.handle, _ptr(packed), int(packed.shape[1]), n, gap_open, gap_extend,
+                                    _ptr(out)), name)
         return out
 
     def fuse_forward(self, pairs, sw, self_sc, packed, emb, params, hidden: int, want_alpha: bool = False,
@@ -324,6 +343,14 @@ def subquad_align_score(ctx: Context, *a, **k):
 
 def subquad_self_scores(ctx: Context, *a, **k):
     return ctx.self_scores(*a, **k)
+
+
+def subquad_align_score_binned(ctx: Context, *a, **k):
+    return ctx.align_score(*a, binned=True, **k)
+
+
+def subquad_self_scores_binned(ctx: Context, *a, **k):
+    return ctx.self_scores(*a, binned=True, **k)
 
 
 def subquad_fuse_forward(ctx: Context, *a, **k):

@@ -185,37 +185,40 @@ def test_candidates_degenerate_inputs(ctx, torch):
 # (a3) alignment
 # --------------------------------------------------------------------------
 
-def test_align_all_pairs_tiny_bitexact(ctx, torch, oracle_mod):
+@pytest.mark.parametrize("binned", [False, True])
+def test_align_all_pairs_tiny_bitexact(ctx, torch, oracle_mod, binned):
     rep = synth.tiny_repertoire()
     packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 16)
     iu, ju = np.triu_indices(rep.n, 1)
     pairs = np.stack([iu, ju], 1).astype(np.uint32)
-    got = to_np(ctx.align_score(packed, torch.from_numpy(pairs.view(np.int32)).to(ctx.device)))
+    got = to_np(ctx.align_score(packed, torch.from_numpy(pairs.view(np.int32)).to(ctx.device), binned=binned))
     want = oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)
     assert (got == want).all()
-    self_got = to_np(ctx.self_scores(packed))
+    self_got = to_np(ctx.self_scores(packed, binned=binned))
     assert (self_got == oracle_mod.self_scores(rep.codes, rep.lens)).all()
 
 
+@pytest.mark.parametrize("binned", [False, True])
 @pytest.mark.parametrize("m", [1, 31, 33, 1000, 4097])
-def test_align_ragged_counts_stride32(ctx, torch, oracle_mod, m):
+def test_align_ragged_counts_stride32(ctx, torch, oracle_mod, m, binned):
     rep = synth.zipf_repertoire(4000, seed=5, hi=100)
     packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 32)
     rng = np.random.default_rng(m)
     pairs = rng.integers(0, rep.n, (m, 2)).astype(np.uint32)
     pairs[0] = [int(np.argmax(rep.lens)), int(np.argmin(rep.lens))]
-    got = to_np(ctx.align_score(packed, torch.from_numpy(pairs.view(np.int32)).to(ctx.device)))
+    got = to_np(ctx.align_score(packed, torch.from_numpy(pairs.view(np.int32)).to(ctx.device), binned=binned))
     assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)).all()
-    assert (to_np(ctx.self_scores(packed)) == oracle_mod.self_scores(rep.codes, rep.lens)).all()
+    assert (to_np(ctx.self_scores(packed, binned=binned)) == oracle_mod.self_scores(rep.codes, rep.lens)).all()
 
 
+@pytest.mark.parametrize("binned", [False, True])
 @pytest.mark.parametrize("o,e", [(10, 1), (0, 0), (3, 3), (11, 1), (1000, 1000), (5, 2)])
-def test_align_gap_parameters(ctx, torch, oracle_mod, o, e):
+def test_align_gap_parameters(ctx, torch, oracle_mod, o, e, binned):
     rep = synth.tiny_repertoire(seed=2)
     packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 16)
     rng = np.random.default_rng(o * 7 + e)
     pairs = rng.integers(0, rep.n, (3000, 2)).astype(np.uint32)
-    got = to_np(ctx.align_score(packed, torch.from_numpy(pairs.view(np.int32)).to(ctx.device), o, e))
+    got = to_np(ctx.align_score(packed, torch.from_numpy(pairs.view(np.int32)).to(ctx.device), o, e, binned=binned))
     assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs, o, e)).all()
 
 
@@ -233,12 +236,52 @@ def test_align_custom_matrices(ctx, torch, oracle_mod):
         assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs, 1000, 1000, ident)).all()
         asym = rng.integers(-6, 9, (20, 20)).astype(np.int32)  # not symmetric: no operand swap allowed
         ctx.set_matrix(asym.ravel())
-        got = to_np(ctx.align_score(packed, tp, 4, 1))
-        assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs, 4, 1, asym)).all()
+        want = oracle_mod.sw_pairs(rep.codes, rep.lens, pairs, 4, 1, asym)
+        assert (to_np(ctx.align_score(packed, tp, 4, 1)) == want).all()
+        assert (to_np(ctx.align_score(packed, tp, 4, 1, binned=True)) == want).all()
     finally:
         ctx.set_matrix(None)
     got = to_np(ctx.align_score(packed, tp))
     assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)).all()
+
+
+@pytest.mark.parametrize("shape", [0, 1])
+@pytest.mark.parametrize("stride,maker", [(16, "donor"), (32, "zipf")])
+def test_align_binned_launch_shapes(ctx, torch, oracle_mod, shape, stride, maker):
+    from paper_2602_17330_gb300 import subquad
+
+    rep = synth.donor_repertoire(6000, seed=11) if maker == "donor" else synth.zipf_repertoire(6000, seed=11, hi=300)
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), stride)
+    rng = np.random.default_rng(shape + stride)
+    pairs = rng.integers(0, rep.n, (20_011, 2)).astype(np.uint32)
+    tp = torch.from_numpy(pairs.view(np.int32)).to(ctx.device)
+    old = ctx.get_tuning(subquad.TUNE_ALIGN_SHAPE)
+    try:
+        ctx.set_tuning(subquad.TUNE_ALIGN_SHAPE, shape)
+        got = to_np(ctx.align_score(packed, tp, binned=True))
+        self_got = to_np(ctx.self_scores(packed, binned=True))
+    finally:
+        ctx.set_tuning(subquad.TUNE_ALIGN_SHAPE, old)
+    assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)).all()
+    assert (self_got == oracle_mod.self_scores(rep.codes, rep.lens)).all()
+
+
+def test_autotune_picks_a_candidate_and_keeps_results(ctx, torch, oracle_mod):
+    from paper_2602_17330_gb300 import autotune, subquad
+
+    rep = synth.donor_repertoire(20_000, seed=12)
+    a, b = synth.hash_coefficients(64, seed=12)
+    packed, sig = gpu_sig(ctx, torch, rep, 3, a, b, 16, 4, 16)
+    pairs = ctx.band_candidates(sig, rep.n, 16, 4, 2048)
+    res = autotune.autotune(ctx, packed, pairs, sig=sig, n=rep.n, bands=16, rows=4, bucket_cap=2048, reps=2,
+                            use_cache=False)
+    assert int(res["choice"][str(subquad.TUNE_ALIGN_SHAPE)]) in (0, 1)
+    assert int(res["choice"][str(subquad.TUNE_BAND_L2_MB)]) in autotune.CANDIDATES[subquad.TUNE_BAND_L2_MB]
+    pairs2 = to_np(ctx.band_candidates(sig, rep.n, 16, 4, 2048)).view(np.uint32)
+    want = oracle_mod.candidates(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), 16, 4, 2048)
+    assert (pairs2 == want).all()
+    sw = to_np(ctx.align_score(packed, pairs, binned=True))
+    assert (sw == oracle_mod.sw_pairs(rep.codes, rep.lens, want)).all()
 
 
 def test_align_empty(ctx, torch):
@@ -315,6 +358,7 @@ def test_full_size_scores_and_fusion_sampled(donor_1m, oracle_mod):
     sel = np.sort(rng.choice(out["pairs"].shape[0], 30_000, replace=False))
     pairs = out["pairs"][sel]
     assert (out["sw"][sel] == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)).all()
+    assert (out["sw_plain"][sel] == out["sw"][sel]).all()
     seqs = np.unique(pairs.ravel())
     want_self = oracle_mod.sw_pairs(rep.codes, rep.lens, np.stack([seqs, seqs], 1))
     assert (out["self"][seqs] == want_self).all()
