@@ -258,6 +258,27 @@ int subquad_fuse_backward(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, co
                           const uint32_t *off_i, const uint32_t *perm_j, const uint32_t *off_j, float *grad_params,
                           float *grad_emb);
 
+/* Parameter gradient of subquad_fuse_backward (grad_params only, same
+ * arguments and the same result) for callers that cannot let the library
+ * allocate device memory: a training step running while a caching allocator
+ * holds the device's free memory, a loop that must not take cudaMalloc's
+ * implicit device synchronisation, or a host whose policy forbids driver
+ * allocations.  The paper has no counterpart; this is an interface choice.
+ * The call allocates nothing: its block partials live in one 2 MiB
+ * file-scope device array that every GPU loading the library keeps until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress), so make it before any stream capture.  It
+ * returns SUBQUAD_ERR_ARG when (4 x SMs) x (5 hidden + 1) doubles exceed
+ * 2 MiB (on a 152-SM GB300 every hidden <= 64 fits).  All calls share the
+ * array, which keeps the last call's contents (each call overwrites every
+ * partial it reads, so nothing needs clearing): calls whose GPU work overlaps
+ * -- on different streams or contexts -- race and must be serialised by the
+ * caller. */
+int subquad_fuse_backward_params_noalloc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                                         const int32_t *self_scores, const void *packed, int pack_stride,
+                                         const float *emb, int d, const float *gate_params, int hidden,
+                                         const float *dL_dfused, float *grad_params);
+
 /* One bias-corrected Adam step (t >= 1) on count float parameters in place:
  * m1 = b1 m1 + (1-b1) g; m2 = b2 m2 + (1-b2) g^2;
  * param -= lr (m1 / (1 - b1^t)) / (sqrt(m2 / (1 - b2^t)) + eps).

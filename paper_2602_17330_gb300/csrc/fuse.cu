@@ -10,6 +10,8 @@
 // is the two-logit softmax of Eq. wm with logits (g, 0).  The kernel is
 // instruction-bound at 16 lanes per pair, so the split favours fewer
 // shuffles and more work per lane.
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace {
@@ -466,5 +468,78 @@ extern "C" int subquad_fuse_backward(subquad_ctx *ctx, const uint32_t *pairs, in
 #undef SQ_EMB
         SQ_LAUNCH_CHECK();
     }
+    return SUBQUAD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free parameter gradient
+// ---------------------------------------------------------------------------
+// Some callers cannot let a library call cudaMalloc: a training step that runs
+// while a caching allocator owns the device's free memory, code that must not
+// take cudaMalloc's implicit device synchronisation inside a latency-bound
+// loop, or hosts whose allocation policy forbids driver allocations.  For them
+// the parameter gradient of the fusion adjoint can keep its block partials in
+// this file-scope device array instead of context scratch.  Every GPU that
+// loads the library holds the array until the process exits.
+constexpr size_t kStaticPartialBytes = size_t(2) << 20;  // 2 MiB
+constexpr size_t kStaticPartialDoubles = kStaticPartialBytes / sizeof(double);
+static __device__ __align__(256) double g_static_partials[kStaticPartialDoubles];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+double *g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_partials on `device` (which must be current):
+// the host-side symbol is only a stand-in, so the address is looked up once
+// per device and cached.
+int static_partials(int device, double **out)
+{
+    if (device < 0 || device >= kMaxDevices) return SUBQUAD_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[device]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_partials);
+        if (e != cudaSuccess) {
+            sq_note_cuda_error(e);
+            return SUBQUAD_ERR_CUDA;
+        }
+        g_static_ptr[device] = static_cast<double *>(ptr);
+    }
+    *out = g_static_ptr[device];
+    return SUBQUAD_OK;
+}
+
+}  // namespace
+
+extern "C" int subquad_fuse_backward_params_noalloc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m,
+                                                    const int32_t *sw, const int32_t *self_scores, const void *packed,
+                                                    int pack_stride, const float *emb, int d,
+                                                    const float *gate_params, int hidden, const float *dL_dfused,
+                                                    float *grad_params)
+{
+    SQ_ENTER(ctx);
+    if (m < 0 || d < 4 || d > 1024 || d % 4 || hidden < 1 || hidden > kMaxHidden) return SUBQUAD_ERR_ARG;
+    if (pack_stride != 16 && pack_stride != 32) return SUBQUAD_ERR_ARG;
+    if (!grad_params || !gate_params) return SUBQUAD_ERR_ARG;
+    if (m > 0 && (!pairs || !sw || !self_scores || !packed || !emb || !dL_dfused)) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(emb) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8 ||
+        reinterpret_cast<uintptr_t>(packed) % 16)
+        return SUBQUAD_ERR_ARG;
+    const int P = 5 * hidden + 1;
+    const unsigned grid = (unsigned)ctx->num_sms * 4;  // the same grid as subquad_fuse_backward
+    if ((size_t)grid * P > kStaticPartialDoubles) return SUBQUAD_ERR_ARG;  // partials would not fit
+    double *partials = nullptr;
+    SQ_TRY(static_partials(ctx->device, &partials));
+    // every block overwrites all of its P partials, so nothing needs clearing
+    if (pack_stride == 16)
+        SQ_TRY(launch_backward<2>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden, dL_dfused,
+                                  nullptr, partials));
+    else
+        SQ_TRY(launch_backward<4>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden, dL_dfused,
+                                  nullptr, partials));
+    reduce_partials_kernel<<<1, 352, 0, ctx->stream>>>(partials, (int)grid, P, grad_params);
+    SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
 }

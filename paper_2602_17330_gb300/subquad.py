@@ -65,6 +65,8 @@ SIGNATURES = {
     "subquad_pair_index": (_c.c_int, [_P, _P, _I64, _I64, _P, _P, _P, _P]),
     "subquad_fuse_backward": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _I64, _c.c_int, _P, _c.c_int, _P,
                                          _P, _P, _P, _P, _P, _P]),
+    "subquad_fuse_backward_params_noalloc": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P,
+                                                        _c.c_int, _P, _P]),
     "subquad_adam_step": (_c.c_int, [_P, _P, _P, _P, _P, _I64, _c.c_int, _c.c_float, _c.c_float, _c.c_float,
                                      _c.c_float]),
 }
@@ -318,6 +320,17 @@ class Context:
             _ptr(ix.get("off_j")), _ptr(grad_params), _ptr(grad_emb) if want_emb else None), "subquad_fuse_backward")
         return (grad_params, grad_emb) if want_emb else grad_params
 
+    def fuse_backward_params_noalloc(self, pairs, sw, self_sc, packed, emb, params, hidden: int, dL, out=None):
+        """Parameter gradient only, with no device allocation by the library
+        (block partials in a static device array; see include/subquad.h)."""
+        torch = self.torch
+        m = int(pairs.shape[0])
+        out = self._empty((5 * hidden + 1,), torch.float32) if out is None else out
+        _check(lib().subquad_fuse_backward_params_noalloc(
+            self.handle, _ptr(pairs), m, _ptr(sw), _ptr(self_sc), _ptr(packed), int(packed.shape[1]), _ptr(emb),
+            int(emb.shape[1]), _ptr(params), hidden, _ptr(dL), _ptr(out)), "subquad_fuse_backward_params_noalloc")
+        return out
+
     def adam_step(self, param, grad, m1, m2, t: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
                   eps: float = 1e-8):
         _check(lib().subquad_adam_step(self.handle, _ptr(param), _ptr(grad), _ptr(m1), _ptr(m2), int(param.numel()),
@@ -375,6 +388,10 @@ def subquad_pair_index(ctx: Context, *a, **k):
 
 def subquad_fuse_backward(ctx: Context, *a, **k):
     return ctx.fuse_backward(*a, **k)
+
+
+def subquad_fuse_backward_params_noalloc(ctx: Context, *a, **k):
+    return ctx.fuse_backward_params_noalloc(*a, **k)
 
 
 def subquad_adam_step(ctx: Context, *a, **k):
