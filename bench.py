@@ -49,6 +49,7 @@ def parse_args():
     p.add_argument("--n", type=int, default=1_000_000, help="sequences per donor (default: the 1M donor)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shapes")
     p.add_argument("--cpu-sample-n", type=int, default=500_000, help="oracle sample for the cpu_baseline key")
     p.add_argument("--ref-sample-n", type=int, default=200_000, help="oracle sample per step of --impl reference")
     return p.parse_args()
@@ -209,10 +210,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ctx.check()
     from paper_2602_17330_gb300 import autotune
 
+    tuning = {"choice": "defaults"}
     with torch.cuda.stream(stream):
-        tuning = autotune.autotune(ctx, out["packed"], out["pairs"], sig=out["sig"], n=cfg.n, bands=cfg.bands,
-                                   rows=cfg.rows, bucket_cap=cfg.bucket_cap, gap_open=cfg.gap_open,
-                                   gap_extend=cfg.gap_extend, reps=3, use_cache=False)
+        if not args.no_autotune:
+            tuning = autotune.autotune(ctx, out["packed"], out["pairs"], sig=out["sig"], n=cfg.n, bands=cfg.bands,
+                                       rows=cfg.rows, bucket_cap=cfg.bucket_cap, gap_open=cfg.gap_open,
+                                       gap_extend=cfg.gap_extend, reps=3, use_cache=False)
         out = pipe.forward(x)
     stream.synchronize()
     pairs_np = out["pairs"].cpu().numpy().view(np.uint32)

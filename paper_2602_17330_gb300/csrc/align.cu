@@ -201,34 +201,65 @@ int launch_align(subquad_ctx *ctx, const void *packed, int pack_stride, const ui
 // ---------------------------------------------------------------------------
 constexpr int kBins = 32 * 32;
 
+// Bin of a work item: (query length, target length) after orientation.
 template <int WORDS, bool SELF>
-__global__ void bin_count_kernel(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs, int64_t m,
-                                 bool symmetric, uint16_t *__restrict__ bin_of, uint32_t *__restrict__ counts)
+__device__ __forceinline__ uint32_t bin_of_item(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs,
+                                                int64_t p, bool symmetric)
 {
     constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+    uint32_t i, j;
+    if (SELF) {
+        i = j = (uint32_t)p;
+    } else {
+        const uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
+        i = ij.x;
+        j = ij.y;
+    }
+    const ulonglong2 ri = reinterpret_cast<const ulonglong2 *>(packed + (int64_t)i * WORDS)[0];
+    const ulonglong2 rj = reinterpret_cast<const ulonglong2 *>(packed + (int64_t)j * WORDS)[0];
+    const int La = min(sq_record_len(ri.x, ri.y), MAXLEN), Lb = min(sq_record_len(rj.x, rj.y), MAXLEN);
+    const int Lq = symmetric ? min(La, Lb) : La, Lt = symmetric ? max(La, Lb) : Lb;
+    return (uint32_t)(Lq * 32 + Lt);
+}
+
+// Warp-aggregated shared-memory add: the peers with the same bin add once.
+__device__ __forceinline__ uint32_t warp_smem_add(uint32_t *s_arr, uint32_t bin, bool valid)
+{
+    const uint32_t key = valid ? bin : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&s_arr[bin], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+// Each block histograms one contiguous range of items in shared memory and
+// adds its non-zero bins to the global counts: one global atomic per block
+// and bin, instead of one per warp on a few hot bins.
+template <int WORDS, bool SELF>
+__global__ void __launch_bounds__(256) bin_count_kernel(const uint64_t *__restrict__ packed,
+                                                        const uint32_t *__restrict__ pairs, int64_t m, bool symmetric,
+                                                        uint16_t *__restrict__ bin_of, uint32_t *__restrict__ counts)
+{
+    __shared__ uint32_t s_hist[kBins];
+    for (int b = threadIdx.x; b < kBins; b += blockDim.x) s_hist[b] = 0;
+    __syncthreads();
+    const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * per, hi = min(m, lo + per);
+    for (int64_t base = lo; base < hi; base += blockDim.x) {
         const int64_t p = base + threadIdx.x;
-        uint32_t bin = 0xffffu;
-        if (p < m) {
-            uint32_t i, j;
-            if (SELF) {
-                i = j = (uint32_t)p;
-            } else {
-                const uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
-                i = ij.x;
-                j = ij.y;
-            }
-            const ulonglong2 ri = reinterpret_cast<const ulonglong2 *>(packed + (int64_t)i * WORDS)[0];
-            const ulonglong2 rj = reinterpret_cast<const ulonglong2 *>(packed + (int64_t)j * WORDS)[0];
-            const int La = min(sq_record_len(ri.x, ri.y), MAXLEN), Lb = min(sq_record_len(rj.x, rj.y), MAXLEN);
-            const int Lq = symmetric ? min(La, Lb) : La, Lt = symmetric ? max(La, Lb) : Lb;
-            bin = (uint32_t)(Lq * 32 + Lt);
+        const bool valid = p < hi;
+        uint32_t bin = 0;
+        if (valid) {
+            bin = bin_of_item<WORDS, SELF>(packed, pairs, p, symmetric);
             bin_of[p] = (uint16_t)bin;
         }
-        const uint32_t peers = __match_any_sync(0xffffffffu, bin);
-        if (bin != 0xffffu && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[bin], (uint32_t)__popc(peers));
+        warp_smem_add(s_hist, bin, valid);
     }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kBins; b += blockDim.x)
+        if (s_hist[b]) atomicAdd(&counts[b], s_hist[b]);
 }
 
 __global__ void __launch_bounds__(1024) bin_offsets_kernel(uint32_t *__restrict__ counts)
@@ -248,20 +279,34 @@ __global__ void __launch_bounds__(1024) bin_offsets_kernel(uint32_t *__restrict_
     counts[threadIdx.x] = s[threadIdx.x];
 }
 
-__global__ void bin_scatter_kernel(const uint16_t *__restrict__ bin_of, int64_t m, uint32_t *__restrict__ cursor,
-                                   uint32_t *__restrict__ order)
+// Same block ranges as bin_count_kernel: the block reserves one slice of each
+// bin with a single global atomic, then places its items in shared memory.
+__global__ void __launch_bounds__(256) bin_scatter_kernel(const uint16_t *__restrict__ bin_of, int64_t m,
+                                                          uint32_t *__restrict__ cursor, uint32_t *__restrict__ order)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+    __shared__ uint32_t s_cnt[kBins];
+    __shared__ uint32_t s_base[kBins];
+    for (int b = threadIdx.x; b < kBins; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * per, hi = min(m, lo + per);
+    for (int64_t base = lo; base < hi; base += blockDim.x) {
         const int64_t p = base + threadIdx.x;
-        const uint32_t bin = p < m ? bin_of[p] : 0xffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, bin);
-        const int leader = __ffs(peers) - 1;
-        uint32_t pos = 0;
-        if (bin != 0xffffu && lane == leader) pos = atomicAdd(&cursor[bin], (uint32_t)__popc(peers));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (bin != 0xffffu) order[pos + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)p;
+        const bool valid = p < hi;
+        warp_smem_add(s_cnt, valid ? bin_of[p] : 0u, valid);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kBins; b += blockDim.x) {
+        s_base[b] = s_cnt[b] ? atomicAdd(&cursor[b], s_cnt[b]) : 0u;
+        s_cnt[b] = 0;
+    }
+    __syncthreads();
+    for (int64_t base = lo; base < hi; base += blockDim.x) {
+        const int64_t p = base + threadIdx.x;
+        const bool valid = p < hi;
+        const uint32_t bin = valid ? bin_of[p] : 0u;
+        const uint32_t r = warp_smem_add(s_cnt, bin, valid);
+        if (valid) order[s_base[bin] + r] = (uint32_t)p;
     }
 }
 

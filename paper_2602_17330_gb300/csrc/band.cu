@@ -426,24 +426,30 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
         SQ_LAUNCH_CHECK();
     }
     {
-        const unsigned grid = sq_grid(ctx, mall, 256, 8);
+        // read the kept count back so the sort and scans below launch grids
+        // for the kept keys (~10% of bands*n), not for the upper bound
+        SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 3, ctx->d_small + 3, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+        SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+        const int64_t kept = std::min<int64_t>((int64_t)ctx->h_pinned[3], mall);
+        const unsigned grid = sq_grid(ctx, std::max<int64_t>(kept, 1), 256, 8);
         bool in_alt = false;
-        SQ_TRY(sq_radix_sort_u64(ctx, L.k0, L.k1, mall, d_kept, 0, key_bits, &in_alt, L.tmp, tmp_bytes));
+        SQ_TRY(sq_radix_sort_u64(ctx, L.k0, L.k1, kept, nullptr, 0, key_bits, &in_alt, L.tmp, tmp_bytes));
         const uint64_t *K = in_alt ? L.k1 : L.k0;
-        band_heads_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, mall, d_kept, L.run_start);
+        band_heads_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, kept, d_kept, L.run_start);
         SQ_LAUNCH_CHECK();
-        SQ_TRY(sq_scan_u32(ctx, L.run_start, L.run_start, mall, d_kept, true, true, nullptr, L.tmp, tmp_bytes));
-        band_chunks_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, L.run_start, mall, d_kept, cap, log_s, 0, bands,
+        SQ_TRY(sq_scan_u32(ctx, L.run_start, L.run_start, kept, nullptr, true, true, nullptr, L.tmp, tmp_bytes));
+        band_chunks_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, L.run_start, kept, d_kept, cap, log_s, 0, bands,
                                                           L.chunk_of, L.flags);
         SQ_LAUNCH_CHECK();
-        SQ_TRY(sq_scan_u32(ctx, L.flags, L.cidx, mall, d_kept, false, false, d_nchunks, L.tmp, tmp_bytes));
-        band_chunk_list_kernel<<<grid, 256, 0, ctx->stream>>>(L.run_start, L.flags, L.cidx, mall, d_kept, cap,
+        SQ_TRY(sq_scan_u32(ctx, L.flags, L.cidx, kept, nullptr, false, false, d_nchunks, L.tmp, tmp_bytes));
+        band_chunk_list_kernel<<<grid, 256, 0, ctx->stream>>>(L.run_start, L.flags, L.cidx, kept, d_kept, cap,
                                                               L.heads, L.sizes, L.npairs);
         SQ_LAUNCH_CHECK();
         // pair counts -> offsets.  Only the first nchunks entries are written;
         // an exclusive prefix at entry c depends on entries < c only, so the
         // unwritten tail never reaches a used offset.
-        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, mall, d_kept, nullptr, L.tmp, tmp_bytes));
+        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, kept, nullptr, nullptr, L.tmp, tmp_bytes));
         band_total_kernel<<<1, 1, 0, ctx->stream>>>(L.npairs, L.sizes, d_nchunks, d_total);
         SQ_LAUNCH_CHECK();
         band_emit_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(
