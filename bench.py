@@ -31,10 +31,12 @@ UNIT = "pairs/s"
 # Smith-Waterman algorithmic int32 operations per DP cell: H-diagonal + score,
 # max3-with-0, H - open, E add-max, F add-max, running best max.
 SW_OPS_PER_CELL = 6
-# INT32 lane operations per SM per clock on sm_103a, measured by the ALU
-# microbenchmark recorded in profiles/alu_peak_gb300.md; times 152 SMs and the
-# 2070 MHz maximum SM clock gives the integer roof.
-INT_LANE_OPS_PER_SM_CLK = 64.0
+# Integer lane operations per SM per clock on sm_103a: the fastest integer
+# issue rate measured by `python -m paper_2602_17330_gb300.peak` (2-input add
+# and min/max at 128; 3-input add, multiply-add and every DPX operation at 64;
+# summary in profiles/alu_peak_gb300.md).  Times 152 SMs and the 2070 MHz
+# maximum SM clock gives the integer roof.
+INT_LANE_OPS_PER_SM_CLK = 128.0
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 512 << 20
@@ -228,6 +230,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     launches0 = ctx.launch_count()
+    ctx.profile(True)
+    ctx.profile_reset()
     sampler = ClockSampler(local_rank) if rank == 0 else None
     wall0 = time.perf_counter()
     with torch.cuda.stream(stream):
@@ -247,6 +251,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     wall = time.perf_counter() - wall0
     clocks = sampler.stop() if sampler else None
     launches = ctx.launch_count() - launches0
+    kernel_prof = ctx.profile_read()
+    ctx.profile(False)
     ctx.check()
 
     step_ms = [e["start"].elapsed_time(e["fuse"]) for e in steps]
@@ -284,36 +290,52 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             stream.synchronize()
             sw_ms["binned" if binned else "plain"] = statistics.mean(a.elapsed_time(b) for a, b in times)
 
-    # roofline of the dominant stage
+    # roofline of the dominant kernel, from the library's live per-kernel event
+    # timings over the timed region (same stream as the launches)
     hbm_peak, peak_kind = measured_peaks()
-    dom = max(stage_ms, key=stage_ms.get)
+    alu_peak = alu_peak_gops()
     align_s = stage_ms["align"] / 1e3
     gcups = cells / align_s / 1e9
-    alu_peak = alu_peak_gops()
-    if dom == "align":
-        kname = "align_binned_kernel" if cfg.binned else "align_plain_kernel"
-        achieved = cells * SW_OPS_PER_CELL / align_s / 1e9
-        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "Gop/s", "frac": achieved / alu_peak, "traffic": traffic_for(kname),
-                "peak_source": "INT32 lane-ops/clk/SM (microbenchmark) x 152 SMs x 2070 MHz"}
-    elif dom == "band":
-        algo = 4 * cfg.hashes * cfg.n + 8 * m
-        achieved = algo / (stage_ms["band"] / 1e3) / 1e9
-        roof = {"kernel": "band stage (insert, sort, chunk, emit, pair sort)", "bound": "hbm", "achieved": achieved,
-                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic_for("band_stage"),
-                "peak_source": f"{peak_kind} copy bandwidth"}
-    elif dom == "sign":
-        evals = float((np.maximum(rep.lens.astype(np.int64) - cfg.k + 1, 0)).sum()) * cfg.hashes
-        achieved = evals * 6 / (stage_ms["sign"] / 1e3) / 1e9
-        roof = {"kernel": "sign_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
-                "frac": achieved / alu_peak, "traffic": traffic_for("sign_kernel"),
-                "peak_source": "INT32 lane-ops/clk/SM (microbenchmark) x 152 SMs x 2070 MHz"}
-    else:
-        algo = m * (8 + 4 + 4) + cfg.n * (4 * cfg.d + 4 + cfg.pack_stride)
-        achieved = algo / (stage_ms[dom] / 1e3) / 1e9
-        roof = {"kernel": f"{dom} stage", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic_for(f"{dom}_stage"),
-                "peak_source": f"{peak_kind} copy bandwidth"}
+    L = rep.lens.astype(np.int64)
+    hash_evals = float(np.maximum(L - cfg.k + 1, 0).sum()) * cfg.hashes
+    self_cells = float((L * L).sum())
+    # algorithmic work per step of each tagged kernel: (bound, amount, unit, what)
+    algo = {
+        "sign": ("alu", 6.0 * hash_evals, "ops", "6 integer ops per hash evaluation"),
+        "band_insert": ("hbm", 4.0 * cfg.hashes * cfg.n, "bytes", "signatures read once"),
+        "band_emit": ("hbm", 8.0 * m, "bytes", "unique pairs written once"),
+        "band_pairsort": ("hbm", 16.0 * m, "bytes", "pairs read and written once"),
+        "align": ("alu", SW_OPS_PER_CELL * cells, "ops", f"{SW_OPS_PER_CELL} int32 ops per DP cell"),
+        "align_bin": ("hbm", 12.0 * m, "bytes", "pair list read, order written"),
+        "self": ("alu", SW_OPS_PER_CELL * self_cells, "ops", f"{SW_OPS_PER_CELL} int32 ops per DP cell"),
+        "fuse": ("hbm", 16.0 * m + cfg.n * (4.0 * cfg.d + 4 + cfg.pack_stride), "bytes",
+                 "16 B per pair + each embedding row, self-score and record once"),
+    }
+    kernel_names = {"sign": "sign_kernel", "band_insert": "band_insert_kernel + band_filter_kernel",
+                    "band_emit": "band chunking + band_emit_kernel", "band_pairsort": "pair radix sort",
+                    "align": "align_binned_kernel" if cfg.binned else "align_plain_kernel",
+                    "align_bin": "bin_count/offsets/scatter", "self": "self-score alignment kernel",
+                    "fuse": "fuse_forward_kernel"}
+    stage_roof = {}
+    for name, (bound, amount, unit, what) in algo.items():
+        ms, launches_k = kernel_prof.get(name, (0.0, 0))
+        if launches_k == 0 or ms <= 0:
+            continue
+        per_launch_ms = ms / launches_k
+        per_launch_amount = amount * args.steps / launches_k
+        achieved = per_launch_amount / (per_launch_ms / 1e3) / 1e9
+        peak = alu_peak if bound == "alu" else hbm_peak
+        stage_roof[name] = {"kernel": kernel_names[name], "bound": bound, "ms_per_step": ms / args.steps,
+                            "launches_per_step": launches_k / args.steps, "achieved": achieved, "peak": peak,
+                            "unit": "Gop/s" if bound == "alu" else "GB/s", "frac": achieved / peak,
+                            "algorithmic": what}
+    dom = max(stage_roof, key=lambda k: stage_roof[k]["ms_per_step"])
+    d = stage_roof[dom]
+    roof = {"kernel": d["kernel"], "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
+            "unit": d["unit"], "frac": d["frac"], "traffic": traffic_for(dom),
+            "peak_source": ("integer issue 128 lane-ops/SM/clk (measured) x 152 SMs x 2070 MHz" if d["bound"] == "alu"
+                            else f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"),
+            "algorithmic": d["algorithmic"]}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -342,7 +364,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "sw_gcups": gcups, "sw_frac_of_int_peak": gcups * SW_OPS_PER_CELL / alu_peak,
             "sw_gcups_plain": cells / (sw_ms["plain"] / 1e3) / 1e9,
             "sw_gcups_binned": cells / (sw_ms["binned"] / 1e3) / 1e9,
-            "stages_ms": stage_ms, "wall_s": wall, "autotune": tuning["choice"],
+            "stages_ms": stage_ms, "kernel_rooflines": stage_roof, "wall_s": wall, "autotune": tuning["choice"],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

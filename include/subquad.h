@@ -88,6 +88,28 @@ enum { SUBQUAD_TUNE_ALIGN_SHAPE = 0, SUBQUAD_TUNE_BAND_L2_MB = 1, SUBQUAD_TUNE_C
 int subquad_set_tuning(subquad_ctx *ctx, int key, int value);
 int subquad_get_tuning(const subquad_ctx *ctx, int key, int *value);
 
+/* Opt-in per-kernel timing (no counterpart in the paper): while enabled,
+ * the library records a CUDA event pair on the context stream around each
+ * launch tagged below; subquad_profile_read synchronises the stream and
+ * returns the summed milliseconds and the number of tagged launches since the
+ * last reset.  Leave it disabled while capturing a CUDA graph. */
+enum {
+    SUBQUAD_PROF_SIGN = 0,          /* sign_kernel */
+    SUBQUAD_PROF_BAND = 1,          /* the whole banding stage of one call */
+    SUBQUAD_PROF_BAND_INSERT = 2,   /* hash insert + singleton filter, per band group */
+    SUBQUAD_PROF_BAND_SORT = 3,     /* sort of the kept keys */
+    SUBQUAD_PROF_BAND_EMIT = 4,     /* chunking + pair emission */
+    SUBQUAD_PROF_BAND_PAIRSORT = 5, /* final sort of the pairs */
+    SUBQUAD_PROF_ALIGN = 6,         /* align_plain_kernel or align_binned_kernel (pairs) */
+    SUBQUAD_PROF_ALIGN_BIN = 7,     /* length binning of the work list */
+    SUBQUAD_PROF_SELF = 8,          /* self-score alignment kernel */
+    SUBQUAD_PROF_FUSE = 9,          /* fuse_forward_kernel */
+    SUBQUAD_PROF_COUNT = 10
+};
+int subquad_profile_enable(subquad_ctx *ctx, int on);
+int subquad_profile_reset(subquad_ctx *ctx);
+int subquad_profile_read(subquad_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
+
 /* ------------------------------------------------------------------------ */
 /* Scoring matrix (affinity channel a^(1) of Algorithm 1)                   */
 /* ------------------------------------------------------------------------ */
@@ -156,6 +178,20 @@ int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, int64_t n, in
                             int32_t bucket_cap, uint32_t *pairs_out, int64_t pairs_capacity,
                             int64_t *num_pairs_out);
 
+/* Batched, graph-capturable form (the hardware-aware batching of Eq. batch):
+ * many repertoires in one call and no host synchronisation.  donor (device
+ * int32 [n], or NULL) confines buckets to one donor, so the result equals
+ * running each donor separately (with global ids).  |C| is written to the
+ * device word *d_num_pairs; pairs beyond pairs_capacity are dropped and set
+ * SUBQUAD_ERR_CAPACITY in the sticky device error.  Kernels are sized for the
+ * upper bounds and read the counts on the device.  A call of the same
+ * (n, bands, rows, pairs_capacity) reserves the context scratch; once that
+ * has happened the call allocates nothing and may be captured in a CUDA
+ * graph. */
+int subquad_band_candidates_async(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows,
+                                  int32_t bucket_cap, const int32_t *donor, uint32_t *pairs_out,
+                                  int64_t pairs_capacity, uint64_t *d_num_pairs);
+
 /* ------------------------------------------------------------------------ */
 /* (a3) Affine-gap local alignment -- the alignment channel computed for     */
 /* every candidate pair in Algorithm 1's affinity loop.  The paper's own GPU  */
@@ -188,6 +224,13 @@ int subquad_align_score_binned(subquad_ctx *ctx, const void *packed, int pack_st
 int subquad_self_scores_binned(subquad_ctx *ctx, const void *packed, int pack_stride, int64_t n, int gap_open,
                                int gap_extend, int32_t *self_out);
 
+/* subquad_align_score_binned for a pair count held on the device (*d_m,
+ * at most m_max pairs are read): the graph-capturable form used after
+ * subquad_band_candidates_async. */
+int subquad_align_score_binned_async(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs,
+                                     const uint64_t *d_m, int64_t m_max, int gap_open, int gap_extend,
+                                     int32_t *scores_out);
+
 /* ------------------------------------------------------------------------ */
 /* (a4) Per-pair gated fusion -- Eq. alpha, Eq. wm and Eq. afused with two   */
 /* channels: a1 = s = S_ij / sqrt(S_ii S_jj), a2 = (1 + cos(e_i, e_j)) / 2.   */
@@ -204,6 +247,33 @@ int subquad_self_scores_binned(subquad_ctx *ctx, const void *packed, int pack_st
 int subquad_fuse_forward(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
                          const int32_t *self_scores, const void *packed, int pack_stride, const float *emb, int d,
                          const float *gate_params, int hidden, float *fused_out, float *alpha_out);
+
+/* ------------------------------------------------------------------------ */
+/* (a7) Cross-donor retrieval -- recall@k of the nearest cross-repertoire    */
+/* partners is the paper's retrieval quality measure (scalability and        */
+/* cross-repertoire sections).                                               */
+/* ------------------------------------------------------------------------ */
+
+/* For each query q = queries[r]: the candidates are the sequences j with
+ * {q, j} in the pair list and donor[j] != donor[q], ranked by (scores[p]
+ * descending, j ascending); the first k go to top_id[r][0..k) and
+ * top_score[r][0..k), padded with id 0xffffffff and score -1.  pairs /
+ * scores: device uint32 [m][2] / int32 [m] (unique pairs); donor: device
+ * int32 [n]; perm_i .. off_j: the pair index of subquad_pair_index; queries:
+ * device uint32 [nq]; top_id / top_score: device [nq][k]; 1 <= k <= 256.
+ * A query id >= n sets SUBQUAD_ERR_INPUT in the sticky error. */
+int subquad_topk_candidates(subquad_ctx *ctx, const uint32_t *pairs, const int32_t *scores, int64_t m, int64_t n,
+                            const int32_t *donor, const uint32_t *perm_i, const uint32_t *off_i,
+                            const uint32_t *perm_j, const uint32_t *off_j, const uint32_t *queries, int64_t nq,
+                            int k, uint32_t *top_id, int32_t *top_score);
+
+/* The exhaustive reference for recall@k: for each query, the k best of ALL
+ * sequences of other donors by local-alignment score (as subquad_align_score,
+ * same tie rule and output layout as subquad_topk_candidates).  packed: device
+ * records of the n sequences.  Work is nq * n alignments. */
+int subquad_topk_bruteforce(subquad_ctx *ctx, const void *packed, int pack_stride, int64_t n, const int32_t *donor,
+                            int gap_open, int gap_extend, const uint32_t *queries, int64_t nq, int k,
+                            uint32_t *top_id, int32_t *top_score);
 
 /* ------------------------------------------------------------------------ */
 /* (a5) Gate training -- the meta-network of Eq. fine_tune is trained end to */
@@ -285,6 +355,13 @@ int subquad_fuse_backward_params_noalloc(subquad_ctx *ctx, const uint32_t *pairs
  * All pointers device float [count]. */
 int subquad_adam_step(subquad_ctx *ctx, float *param, const float *grad, float *m1, float *m2, int64_t count, int t,
                       float lr, float beta1, float beta2, float eps);
+
+/* subquad_fuse_forward for a pair count held on the device (*d_m, at most
+ * m_max pairs): the graph-capturable form. */
+int subquad_fuse_forward_async(subquad_ctx *ctx, const uint32_t *pairs, const uint64_t *d_m, int64_t m_max,
+                               const int32_t *sw, const int32_t *self_scores, const void *packed, int pack_stride,
+                               const float *emb, int d, const float *gate_params, int hidden, float *fused_out,
+                               float *alpha_out);
 
 #ifdef __cplusplus
 }

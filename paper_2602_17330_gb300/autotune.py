@@ -22,7 +22,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning.json")
 
 CANDIDATES = {
     subquad.TUNE_ALIGN_SHAPE: (0, 1),
-    subquad.TUNE_BAND_L2_MB: (16, 32, 48, 64, 96),
+    subquad.TUNE_BAND_L2_MB: (8, 16, 32, 48, 64),
 }
 
 

@@ -176,6 +176,7 @@ int launch_align(subquad_ctx *ctx, const void *packed, int pack_stride, const ui
 {
     const size_t smem = sizeof(int32_t) * kTabWords;
     const unsigned grid = sq_grid(ctx, m, kAlignThreads, 2);
+    SqProfScope prof(ctx, SELF ? SUBQUAD_PROF_SELF : SUBQUAD_PROF_ALIGN);
     if (pack_stride == 16) {
         auto k = align_plain_kernel<2, SELF>;
         SQ_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -200,6 +201,15 @@ int launch_align(subquad_ctx *ctx, const void *packed, int pack_stride, const ui
 // idles waiting for a longer target.
 // ---------------------------------------------------------------------------
 constexpr int kBins = 32 * 32;
+
+// Item count of a launch sized for m_max: *d_m when the caller keeps the count
+// on the device (graph-captured pipelines), else m_max.
+__device__ __forceinline__ int64_t items(int64_t m_max, const unsigned long long *d_m)
+{
+    if (!d_m) return m_max;
+    const int64_t c = (int64_t)*d_m;
+    return c < m_max ? c : m_max;
+}
 
 // Bin of a work item: (query length, target length) after orientation.
 template <int WORDS, bool SELF>
@@ -239,10 +249,12 @@ __device__ __forceinline__ uint32_t warp_smem_add(uint32_t *s_arr, uint32_t bin,
 // and bin, instead of one per warp on a few hot bins.
 template <int WORDS, bool SELF>
 __global__ void __launch_bounds__(256) bin_count_kernel(const uint64_t *__restrict__ packed,
-                                                        const uint32_t *__restrict__ pairs, int64_t m, bool symmetric,
+                                                        const uint32_t *__restrict__ pairs, int64_t m_max,
+                                                        const unsigned long long *__restrict__ d_m, bool symmetric,
                                                         uint16_t *__restrict__ bin_of, uint32_t *__restrict__ counts)
 {
     __shared__ uint32_t s_hist[kBins];
+    const int64_t m = items(m_max, d_m);
     for (int b = threadIdx.x; b < kBins; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
     const int64_t per = (m + gridDim.x - 1) / gridDim.x;
@@ -281,10 +293,12 @@ __global__ void __launch_bounds__(1024) bin_offsets_kernel(uint32_t *__restrict_
 
 // Same block ranges as bin_count_kernel: the block reserves one slice of each
 // bin with a single global atomic, then places its items in shared memory.
-__global__ void __launch_bounds__(256) bin_scatter_kernel(const uint16_t *__restrict__ bin_of, int64_t m,
+__global__ void __launch_bounds__(256) bin_scatter_kernel(const uint16_t *__restrict__ bin_of, int64_t m_max,
+                                                          const unsigned long long *__restrict__ d_m,
                                                           uint32_t *__restrict__ cursor, uint32_t *__restrict__ order)
 {
     __shared__ uint32_t s_cnt[kBins];
+    const int64_t m = items(m_max, d_m);
     __shared__ uint32_t s_base[kBins];
     for (int b = threadIdx.x; b < kBins; b += blockDim.x) s_cnt[b] = 0;
     __syncthreads();
@@ -430,10 +444,11 @@ struct BinnedShape {
 template <int WORDS, bool SELF, int CFG>
 __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::blocks)
     align_binned_kernel(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs,
-                        const uint32_t *__restrict__ order, int64_t m, const int32_t *__restrict__ table, int o, int e,
-                        bool symmetric, int32_t *__restrict__ out)
+                        const uint32_t *__restrict__ order, int64_t m_max, const unsigned long long *__restrict__ d_m,
+                        const int32_t *__restrict__ table, int o, int e, bool symmetric, int32_t *__restrict__ out)
 {
     extern __shared__ int32_t s_tab_words[];
+    const int64_t m = items(m_max, d_m);
     for (int q = threadIdx.x; q < kTabWords / 4; q += blockDim.x)
         reinterpret_cast<int4 *>(s_tab_words)[q] = reinterpret_cast<const int4 *>(table)[q];
     __syncthreads();
@@ -489,7 +504,7 @@ __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::b
 
 template <bool SELF>
 int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs, int64_t m, int o,
-                  int e, int32_t *out)
+                  int e, int32_t *out, const unsigned long long *d_m = nullptr)
 {
     if (m >= (int64_t(1) << 32)) return SUBQUAD_ERR_ARG;
     SqArena measure(nullptr);
@@ -501,25 +516,33 @@ int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const u
     uint32_t *counts = a.take<uint32_t>(kBins);
     uint16_t *bin_of = a.take<uint16_t>(m);
     uint32_t *order = a.take<uint32_t>(m);
+    SqProfScope prof_bin(ctx, SUBQUAD_PROF_ALIGN_BIN);
     SQ_TRY_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * kBins, ctx->stream));
     const unsigned g = sq_grid(ctx, m, 256, 8);
     const uint64_t *pk = static_cast<const uint64_t *>(packed);
     if (pack_stride == 16)
-        bin_count_kernel<2, SELF><<<g, 256, 0, ctx->stream>>>(pk, pairs, m, ctx->matrix_symmetric, bin_of, counts);
+        bin_count_kernel<2, SELF><<<g, 256, 0, ctx->stream>>>(pk, pairs, m, d_m, ctx->matrix_symmetric, bin_of, counts);
     else
-        bin_count_kernel<4, SELF><<<g, 256, 0, ctx->stream>>>(pk, pairs, m, ctx->matrix_symmetric, bin_of, counts);
+        bin_count_kernel<4, SELF><<<g, 256, 0, ctx->stream>>>(pk, pairs, m, d_m, ctx->matrix_symmetric, bin_of, counts);
     SQ_LAUNCH_CHECK();
     bin_offsets_kernel<<<1, kBins, 0, ctx->stream>>>(counts);
     SQ_LAUNCH_CHECK();
-    bin_scatter_kernel<<<g, 256, 0, ctx->stream>>>(bin_of, m, counts, order);
+    bin_scatter_kernel<<<g, 256, 0, ctx->stream>>>(bin_of, m, d_m, counts, order);
     SQ_LAUNCH_CHECK();
+    prof_bin.finish();
+    SqProfScope prof(ctx, SELF ? SUBQUAD_PROF_SELF : SUBQUAD_PROF_ALIGN);
     const size_t smem = sizeof(int32_t) * kTabWords;
 #define SQ_BINNED(W, C)                                                                                            \
     do {                                                                                                           \
         auto k = align_binned_kernel<W, SELF, C>;                                                                  \
-        SQ_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));             \
+        static bool attr_set[64] = {};                                                                             \
+        const int dev_slot = ctx->device & 63;                                                                     \
+        if (!attr_set[dev_slot]) {                                                                                 \
+            SQ_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));         \
+            attr_set[dev_slot] = true;                                                                             \
+        }                                                                                                          \
         const unsigned grid = sq_grid(ctx, (m + 1) / 2, BinnedShape<C>::threads, BinnedShape<C>::blocks);         \
-        k<<<grid, BinnedShape<C>::threads, smem, ctx->stream>>>(pk, pairs, order, m, ctx->d_table, o, e,           \
+        k<<<grid, BinnedShape<C>::threads, smem, ctx->stream>>>(pk, pairs, order, m, d_m, ctx->d_table, o, e,      \
                                                                ctx->matrix_symmetric, out);                        \
     } while (0)
     const int cfg = ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE];
@@ -536,6 +559,8 @@ int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const u
 }
 
 }  // namespace
+
+int sq_ensure_align_table(subquad_ctx *ctx, int gap_open) { return ensure_table(ctx, gap_open); }
 
 extern "C" int subquad_align_score(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs,
                                    int64_t m, int gap_open, int gap_extend, int32_t *scores_out)
@@ -588,4 +613,20 @@ extern "C" int subquad_self_scores_binned(subquad_ctx *ctx, const void *packed, 
     if (reinterpret_cast<uintptr_t>(packed) % 16) return SUBQUAD_ERR_ARG;
     SQ_TRY(ensure_table(ctx, gap_open));
     return launch_binned<true>(ctx, packed, pack_stride, nullptr, n, gap_open, gap_extend, self_out);
+}
+
+extern "C" int subquad_align_score_binned_async(subquad_ctx *ctx, const void *packed, int pack_stride,
+                                                const uint32_t *pairs, const uint64_t *d_m, int64_t m_max,
+                                                int gap_open, int gap_extend, int32_t *scores_out)
+{
+    SQ_ENTER(ctx);
+    if (!d_m || m_max < 0 || gap_open < 0 || gap_open > 1000 || gap_extend < 0 || gap_extend > 1000)
+        return SUBQUAD_ERR_ARG;
+    if (pack_stride != 16 && pack_stride != 32) return SUBQUAD_ERR_ARG;
+    if (m_max == 0) return SUBQUAD_OK;
+    if (!packed || !pairs || !scores_out) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(packed) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8) return SUBQUAD_ERR_ARG;
+    SQ_TRY(ensure_table(ctx, gap_open));
+    return launch_binned<false>(ctx, packed, pack_stride, pairs, m_max, gap_open, gap_extend, scores_out,
+                                reinterpret_cast<const unsigned long long *>(d_m));
 }

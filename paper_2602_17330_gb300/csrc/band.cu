@@ -100,44 +100,62 @@ __device__ __forceinline__ unsigned long long block_append(bool flag, unsigned l
 // hundreds of members adds no contended atomics.  blockIdx.y = band in group.
 constexpr uint32_t kShared = 0x80000000u;
 
+constexpr int kInsIlp = 4;  // elements per thread in the singleton filter
+
+__device__ __forceinline__ uint32_t key_hash(const uint32_t k[8], int rows)
+{
+    uint32_t h = 0x9e3779b9u ^ (uint32_t)rows;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+        if (r < rows) h = mix32(h ^ k[r]);
+    return h;
+}
+
+// Probe from `slot` until the element's key is claimed or found (the slow path
+// after a first probe that hit another key).
+// Equal keys: the same R-tuple and, in a batch of donors, the same donor.
+__device__ __forceinline__ bool same_key(const uint32_t *band_sig, int rows, uint32_t owner, const uint32_t k[8],
+                                         const int32_t *donor, int32_t my_donor)
+{
+    return key_equal(band_sig + (int64_t)owner * rows, rows, k) && (!donor || donor[owner] == my_donor);
+}
+
+__device__ __forceinline__ uint32_t probe_from(uint32_t *tab, uint32_t slot, uint32_t smask, const uint32_t k[8],
+                                               uint32_t i, const uint32_t *band_sig, int rows, const int32_t *donor,
+                                               int32_t my_donor, uint32_t *err)
+{
+    for (uint32_t probe = 0; probe <= smask; ++probe) {
+        uint32_t cur = tab[slot];
+        if (cur == kEmpty) {
+            cur = atomicCAS(&tab[slot], kEmpty, i);
+            if (cur == kEmpty) return slot;
+        }
+        if (same_key(band_sig, rows, cur & ~kShared, k, donor, my_donor)) {
+            if (!(cur & kShared)) tab[slot] = cur | kShared;
+            return slot;
+        }
+        slot = (slot + 1) & smask;
+    }
+    atomicOr(err, SQ_DEVERR_TIMEOUT);  // unreachable: the table is at most half full
+    return 0;
+}
+
 __global__ void __launch_bounds__(256) band_insert_kernel(const uint32_t *__restrict__ sig, int64_t n, int rows,
-                                                          int band0, int log_s, uint32_t *__restrict__ table,
-                                                          uint32_t *__restrict__ slot_of, uint32_t *err)
+                                                          int band0, int log_s, const int32_t *__restrict__ donor,
+                                                          uint32_t *__restrict__ table, uint32_t *__restrict__ slot_of,
+                                                          uint32_t *err)
 {
     const int gb = blockIdx.y;
     const uint32_t smask = (1u << log_s) - 1u;
     const uint32_t *band_sig = sig + (int64_t)(band0 + gb) * n * rows;
     uint32_t *tab = table + ((int64_t)gb << log_s);
+    uint32_t *slots = slot_of + (int64_t)gb * n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t k[8];
         load_key(band_sig + i * rows, rows, k);
-        uint32_t h = 0x9e3779b9u ^ (uint32_t)rows;
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-            if (r < rows) h = mix32(h ^ k[r]);
-        uint32_t slot = h & smask;
-        bool found = false;
-        // the table is at most half full, so a free slot is always reached
-        for (uint32_t probe = 0; probe <= smask; ++probe) {
-            uint32_t cur = tab[slot];
-            if (cur == kEmpty) {
-                cur = atomicCAS(&tab[slot], kEmpty, (uint32_t)i);
-                if (cur == kEmpty) {
-                    found = true;
-                    break;
-                }
-            }
-            if (key_equal(band_sig + (int64_t)(cur & ~kShared) * rows, rows, k)) {
-                // the owner id never changes once claimed, so storing owner|flag
-                // can only ever write the same value
-                if (!(cur & kShared)) tab[slot] = cur | kShared;
-                found = true;
-                break;
-            }
-            slot = (slot + 1) & smask;
-        }
-        if (!found) atomicOr(err, SQ_DEVERR_TIMEOUT);
-        slot_of[(int64_t)gb * n + i] = slot;
+        const int32_t dn = donor ? donor[i] : 0;
+        const uint32_t home = mix32(key_hash(k, rows) ^ (uint32_t)dn) & smask;
+        slots[i] = probe_from(tab, home, smask, k, (uint32_t)i, band_sig, rows, donor, dn, err);
     }
 }
 
@@ -155,16 +173,27 @@ __global__ void __launch_bounds__(256) band_filter_kernel(const uint32_t *__rest
     const int gb = blockIdx.y;
     const uint32_t *tab = table + ((int64_t)gb << log_s);
     const uint32_t *slots = slot_of + (int64_t)gb * n;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        bool keep = false;
-        uint32_t slot = 0;
-        if (i < n) {
-            slot = slots[i];
-            keep = (tab[slot] & kShared) != 0u;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * kInsIlp;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kInsIlp + threadIdx.x;
+         base - threadIdx.x < n; base += step) {
+        uint32_t slot[kInsIlp];
+        bool keep[kInsIlp];
+#pragma unroll
+        for (int q = 0; q < kInsIlp; ++q) {
+            const int64_t i = base + (int64_t)q * blockDim.x;
+            slot[q] = i < n ? slots[i] : 0u;
         }
-        const unsigned long long pos = block_append(keep, d_kept, &s_base, s_warp);
-        if (keep) keys[pos] = ((((uint64_t)(band0 + gb) << log_s) | slot) << nbits) | (uint64_t)i;
+#pragma unroll
+        for (int q = 0; q < kInsIlp; ++q) {
+            const int64_t i = base + (int64_t)q * blockDim.x;
+            keep[q] = i < n && (tab[slot[q]] & kShared) != 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kInsIlp; ++q) {
+            const int64_t i = base + (int64_t)q * blockDim.x;
+            const unsigned long long pos = block_append(keep[q], d_kept, &s_base, s_warp);
+            if (keep[q]) keys[pos] = ((((uint64_t)(band0 + gb) << log_s) | slot[q]) << nbits) | (uint64_t)i;
+        }
     }
 }
 
@@ -327,22 +356,44 @@ __global__ void band_total_kernel(const uint64_t *__restrict__ poff, const uint3
     *d_total = total;
 }
 
-__global__ void pairs_to_keys_kernel(const uint32_t *__restrict__ pairs, int64_t m, int nbits,
-                                     uint64_t *__restrict__ keys)
+__device__ __forceinline__ int64_t count_or(int64_t m, const unsigned long long *d_m)
 {
+    if (!d_m) return m;
+    const int64_t c = (int64_t)*d_m;
+    return c < m ? c : m;
+}
+
+__global__ void pairs_to_keys_kernel(const uint32_t *__restrict__ pairs, int64_t m_max,
+                                     const unsigned long long *__restrict__ d_m, int nbits, uint64_t *__restrict__ keys)
+{
+    const int64_t m = count_or(m_max, d_m);
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
         uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
         keys[p] = ((uint64_t)ij.x << nbits) | ij.y;
     }
 }
 
-__global__ void keys_to_pairs_kernel(const uint64_t *__restrict__ keys, int64_t m, int nbits, uint32_t *__restrict__ pairs)
+__global__ void keys_to_pairs_kernel(const uint64_t *__restrict__ keys, int64_t m_max,
+                                     const unsigned long long *__restrict__ d_m, int nbits,
+                                     uint32_t *__restrict__ pairs)
 {
+    const int64_t m = count_or(m_max, d_m);
     const uint64_t mask = (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1ull);
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
         uint64_t k = keys[p];
         reinterpret_cast<uint2 *>(pairs)[p] = make_uint2((uint32_t)(k >> nbits), (uint32_t)(k & mask));
     }
+}
+
+// Async finish: publish |C|, flag an overflow, clamp the count used below.
+__global__ void band_finish_kernel(const unsigned long long *__restrict__ d_count, int64_t capacity,
+                                   unsigned long long *__restrict__ d_out, unsigned long long *__restrict__ d_clamped,
+                                   uint32_t *err)
+{
+    const unsigned long long c = *d_count;
+    if (d_out) *d_out = c;
+    if (c > (unsigned long long)capacity) atomicOr(err, SQ_DEVERR_CAPACITY);
+    *d_clamped = c < (unsigned long long)capacity ? c : (unsigned long long)capacity;
 }
 
 int bits_for(uint64_t v)  // number of bits needed to hold values 0..v
@@ -354,19 +405,22 @@ int bits_for(uint64_t v)  // number of bits needed to hold values 0..v
 
 }  // namespace
 
-extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows,
-                                       int32_t bucket_cap, uint32_t *pairs_out, int64_t pairs_capacity,
-                                       int64_t *num_pairs_out)
+namespace {
+
+// The banding stage.  Synchronous form (d_num_pairs == nullptr): reads back the
+// kept-key count (to size the sort) and |C| (to size the final sort and check
+// the capacity).  Asynchronous form: no host synchronisation at all -- the
+// counts stay on the device, kernels are sized for their upper bounds and read
+// the actual counts, |C| goes to *d_num_pairs and an overflow of the capacity
+// sets the sticky CAPACITY error -- so the call can be captured in a graph once
+// a call of the same shape has reserved the scratch.
+int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows, int32_t bucket_cap,
+             const int32_t *donor, uint32_t *pairs_out, int64_t pairs_capacity, int64_t *num_pairs_out,
+             unsigned long long *d_num_pairs)
 {
-    SQ_ENTER(ctx);
-    if (!num_pairs_out || n < 0 || n >= (int64_t(1) << 31) || bands < 1 || rows < 1 || rows > 8 ||
-        bands * rows > 512 || pairs_capacity < 0)
-        return SUBQUAD_ERR_ARG;
-    *num_pairs_out = 0;
-    if (n < 2) return subquad_check(ctx);
-    if (!sig || (pairs_capacity > 0 && !pairs_out)) return SUBQUAD_ERR_ARG;
-    if (reinterpret_cast<uintptr_t>(sig) % 16 || reinterpret_cast<uintptr_t>(pairs_out) % 8) return SUBQUAD_ERR_ARG;
+    const bool async = d_num_pairs != nullptr;
     const int cap = (bucket_cap <= 0 || bucket_cap >= n) ? 0 : bucket_cap;
+    SqProfScope prof(ctx, SUBQUAD_PROF_BAND);
 
     // Table of S >= 2n 32-bit slots per band.  Bands are inserted in groups
     // whose tables fit a share of L2 (the random probes then stay on chip);
@@ -380,12 +434,14 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
     const int G = (int)std::max<int64_t>(1, std::min<int64_t>(bands, l2_budget / (S * 4)));
     const int64_t mg = (int64_t)G * n;       // elements per insert group
     const int64_t mall = (int64_t)bands * n;  // upper bound of kept keys
+    const int nb = bits_for((uint64_t)(n - 1));
+    const int64_t final_cap = std::max<int64_t>(pairs_capacity, 1);
 
     auto layout = [&](SqArena &a) {
         struct L {
             uint32_t *chunk_of, *table, *slot_of, *run_start, *flags, *cidx, *heads, *sizes;
-            uint64_t *k0, *k1, *npairs;
-            void *tmp;
+            uint64_t *k0, *k1, *npairs, *p0, *p1;
+            void *tmp, *ptmp;
         } l;
         l.chunk_of = a.take<uint32_t>((size_t)n * bands);
         l.table = a.take<uint32_t>((size_t)G * S);
@@ -399,6 +455,10 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
         l.sizes = a.take<uint32_t>(mall);
         l.npairs = a.take<uint64_t>(mall);
         l.tmp = a.take<char>(std::max(sq_radix_tmp_bytes(mall), sq_scan_tmp_bytes(mall)));
+        // the asynchronous form sorts the pairs in its own scratch (sized by the capacity)
+        l.p0 = async ? a.take<uint64_t>(final_cap) : nullptr;
+        l.p1 = async ? a.take<uint64_t>(final_cap) : nullptr;
+        l.ptmp = async ? a.take<char>(sq_radix_tmp_bytes(final_cap)) : nullptr;
         return l;
     };
     SqArena measure(nullptr);
@@ -413,49 +473,78 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
     uint64_t *d_total = ctx->d_small + 2;
     unsigned long long *d_kept64 = reinterpret_cast<unsigned long long *>(ctx->d_small + 3);
     const uint32_t *d_kept = reinterpret_cast<const uint32_t *>(ctx->d_small + 3);  // low word (< 2^32 keys)
+    unsigned long long *d_clamped = reinterpret_cast<unsigned long long *>(ctx->d_small + 4);
     SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 8 * sizeof(uint64_t), ctx->stream));
     SQ_TRY_CUDA(cudaMemsetAsync(L.chunk_of, 0xff, (size_t)n * bands * sizeof(uint32_t), ctx->stream));
 
     for (int band0 = 0; band0 < bands; band0 += G) {
         const int gb = std::min(G, bands - band0);
         const dim3 grid(sq_grid(ctx, n, 256, (8 + gb - 1) / gb), gb);
+        const dim3 fgrid(sq_grid(ctx, (n + kInsIlp - 1) / kInsIlp, 256, (8 + gb - 1) / gb), gb);
+        SqProfScope prof_ins(ctx, SUBQUAD_PROF_BAND_INSERT);
         SQ_TRY_CUDA(cudaMemsetAsync(L.table, 0xff, (size_t)gb * S * sizeof(uint32_t), ctx->stream));
-        band_insert_kernel<<<grid, 256, 0, ctx->stream>>>(sig, n, rows, band0, log_s, L.table, L.slot_of, ctx->d_err);
+        band_insert_kernel<<<grid, 256, 0, ctx->stream>>>(sig, n, rows, band0, log_s, donor, L.table, L.slot_of,
+                                                          ctx->d_err);
         SQ_LAUNCH_CHECK();
-        band_filter_kernel<<<grid, 256, 0, ctx->stream>>>(L.slot_of, L.table, n, band0, log_s, nbits, L.k0, d_kept64);
+        band_filter_kernel<<<fgrid, 256, 0, ctx->stream>>>(L.slot_of, L.table, n, band0, log_s, nbits, L.k0, d_kept64);
         SQ_LAUNCH_CHECK();
     }
     {
-        // read the kept count back so the sort and scans below launch grids
-        // for the kept keys (~10% of bands*n), not for the upper bound
-        SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 3, ctx->d_small + 3, sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                                    ctx->stream));
-        SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
-        const int64_t kept = std::min<int64_t>((int64_t)ctx->h_pinned[3], mall);
+        // synchronous form: read the kept count back so the sort and scans
+        // below launch grids for the kept keys (~10% of bands*n)
+        int64_t kept = mall;
+        const uint32_t *dk = d_kept;
+        if (!async) {
+            SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 3, ctx->d_small + 3, sizeof(uint64_t),
+                                        cudaMemcpyDeviceToHost, ctx->stream));
+            SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+            kept = std::min<int64_t>((int64_t)ctx->h_pinned[3], mall);
+            dk = nullptr;
+        }
         const unsigned grid = sq_grid(ctx, std::max<int64_t>(kept, 1), 256, 8);
         bool in_alt = false;
-        SQ_TRY(sq_radix_sort_u64(ctx, L.k0, L.k1, kept, nullptr, 0, key_bits, &in_alt, L.tmp, tmp_bytes));
+        {
+            SqProfScope prof_sort(ctx, SUBQUAD_PROF_BAND_SORT);
+            SQ_TRY(sq_radix_sort_u64(ctx, L.k0, L.k1, kept, dk, 0, key_bits, &in_alt, L.tmp, tmp_bytes));
+        }
+        SqProfScope prof_emit(ctx, SUBQUAD_PROF_BAND_EMIT);
         const uint64_t *K = in_alt ? L.k1 : L.k0;
         band_heads_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, kept, d_kept, L.run_start);
         SQ_LAUNCH_CHECK();
-        SQ_TRY(sq_scan_u32(ctx, L.run_start, L.run_start, kept, nullptr, true, true, nullptr, L.tmp, tmp_bytes));
+        SQ_TRY(sq_scan_u32(ctx, L.run_start, L.run_start, kept, dk, true, true, nullptr, L.tmp, tmp_bytes));
         band_chunks_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, L.run_start, kept, d_kept, cap, log_s, 0, bands,
                                                           L.chunk_of, L.flags);
         SQ_LAUNCH_CHECK();
-        SQ_TRY(sq_scan_u32(ctx, L.flags, L.cidx, kept, nullptr, false, false, d_nchunks, L.tmp, tmp_bytes));
+        SQ_TRY(sq_scan_u32(ctx, L.flags, L.cidx, kept, dk, false, false, d_nchunks, L.tmp, tmp_bytes));
         band_chunk_list_kernel<<<grid, 256, 0, ctx->stream>>>(L.run_start, L.flags, L.cidx, kept, d_kept, cap,
                                                               L.heads, L.sizes, L.npairs);
         SQ_LAUNCH_CHECK();
         // pair counts -> offsets.  Only the first nchunks entries are written;
         // an exclusive prefix at entry c depends on entries < c only, so the
         // unwritten tail never reaches a used offset.
-        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, kept, nullptr, nullptr, L.tmp, tmp_bytes));
+        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, kept, dk, nullptr, L.tmp, tmp_bytes));
         band_total_kernel<<<1, 1, 0, ctx->stream>>>(L.npairs, L.sizes, d_nchunks, d_total);
         SQ_LAUNCH_CHECK();
         band_emit_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(
             K, nbits, L.heads, L.sizes, L.npairs, d_nchunks, d_total, log_s, 0, bands, L.chunk_of, pairs_out,
             pairs_capacity, d_count, ctx->d_err);
         SQ_LAUNCH_CHECK();
+    }
+    if (async) {
+        band_finish_kernel<<<1, 1, 0, ctx->stream>>>(d_count, pairs_capacity, d_num_pairs, d_clamped, ctx->d_err);
+        SQ_LAUNCH_CHECK();
+        if (pairs_capacity > 1) {
+            const unsigned grid = sq_grid(ctx, pairs_capacity, 256, 8);
+            pairs_to_keys_kernel<<<grid, 256, 0, ctx->stream>>>(pairs_out, pairs_capacity, d_clamped, nb, L.p0);
+            SQ_LAUNCH_CHECK();
+            bool in_alt = false;
+            SQ_TRY(sq_radix_sort_u64(ctx, L.p0, L.p1, pairs_capacity, reinterpret_cast<const uint32_t *>(d_clamped),
+                                     0, 2 * nb, &in_alt, L.ptmp, sq_radix_tmp_bytes(final_cap)));
+            keys_to_pairs_kernel<<<grid, 256, 0, ctx->stream>>>(in_alt ? L.p1 : L.p0, pairs_capacity, d_clamped, nb,
+                                                                pairs_out);
+            SQ_LAUNCH_CHECK();
+        }
+        return SUBQUAD_OK;
     }
     SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_small, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
     SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
@@ -466,7 +555,6 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
     if (err) return subquad_check(ctx);
     if (count > pairs_capacity) return SUBQUAD_ERR_CAPACITY;
     if (count > 1) {
-        const int nb = bits_for((uint64_t)(n - 1));
         SqArena a2(nullptr);
         a2.take<uint64_t>(count);
         a2.take<uint64_t>(count);
@@ -477,12 +565,52 @@ extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, in
         uint64_t *k1 = a3.take<uint64_t>(count);
         void *tmp = a3.take<char>(sq_radix_tmp_bytes(count));
         const unsigned grid = sq_grid(ctx, count, 256, 8);
-        pairs_to_keys_kernel<<<grid, 256, 0, ctx->stream>>>(pairs_out, count, nb, k0);
+        SqProfScope prof_ps(ctx, SUBQUAD_PROF_BAND_PAIRSORT);
+        pairs_to_keys_kernel<<<grid, 256, 0, ctx->stream>>>(pairs_out, count, nullptr, nb, k0);
         SQ_LAUNCH_CHECK();
         bool in_alt = false;
         SQ_TRY(sq_radix_sort_u64(ctx, k0, k1, count, nullptr, 0, 2 * nb, &in_alt, tmp, sq_radix_tmp_bytes(count)));
-        keys_to_pairs_kernel<<<grid, 256, 0, ctx->stream>>>(in_alt ? k1 : k0, count, nb, pairs_out);
+        keys_to_pairs_kernel<<<grid, 256, 0, ctx->stream>>>(in_alt ? k1 : k0, count, nullptr, nb, pairs_out);
         SQ_LAUNCH_CHECK();
     }
     return SUBQUAD_OK;
+}
+
+int band_args(int64_t n, int bands, int rows, int64_t pairs_capacity, const uint32_t *sig, const uint32_t *pairs_out)
+{
+    if (n < 0 || n >= (int64_t(1) << 31) || bands < 1 || rows < 1 || rows > 8 || bands * rows > 512 ||
+        pairs_capacity < 0)
+        return SUBQUAD_ERR_ARG;
+    if (n >= 2 && (!sig || (pairs_capacity > 0 && !pairs_out))) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(sig) % 16 || reinterpret_cast<uintptr_t>(pairs_out) % 8) return SUBQUAD_ERR_ARG;
+    return SUBQUAD_OK;
+}
+
+}  // namespace
+
+extern "C" int subquad_band_candidates(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows,
+                                       int32_t bucket_cap, uint32_t *pairs_out, int64_t pairs_capacity,
+                                       int64_t *num_pairs_out)
+{
+    SQ_ENTER(ctx);
+    if (!num_pairs_out) return SUBQUAD_ERR_ARG;
+    *num_pairs_out = 0;
+    SQ_TRY(band_args(n, bands, rows, pairs_capacity, sig, pairs_out));
+    if (n < 2) return subquad_check(ctx);
+    return band_run(ctx, sig, n, bands, rows, bucket_cap, nullptr, pairs_out, pairs_capacity, num_pairs_out, nullptr);
+}
+
+extern "C" int subquad_band_candidates_async(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows,
+                                             int32_t bucket_cap, const int32_t *donor, uint32_t *pairs_out,
+                                             int64_t pairs_capacity, uint64_t *d_num_pairs)
+{
+    SQ_ENTER(ctx);
+    if (!d_num_pairs) return SUBQUAD_ERR_ARG;
+    SQ_TRY(band_args(n, bands, rows, pairs_capacity, sig, pairs_out));
+    if (n < 2) {
+        SQ_TRY_CUDA(cudaMemsetAsync(d_num_pairs, 0, sizeof(uint64_t), ctx->stream));
+        return SUBQUAD_OK;
+    }
+    return band_run(ctx, sig, n, bands, rows, bucket_cap, donor, pairs_out, pairs_capacity, nullptr,
+                    reinterpret_cast<unsigned long long *>(d_num_pairs));
 }

@@ -92,6 +92,64 @@ extern "C" int subquad_create(subquad_ctx **out, int device, void *cuda_stream)
     return SUBQUAD_OK;
 }
 
+cudaEvent_t sq_prof_event(subquad_ctx *ctx)
+{
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+static void prof_recycle(subquad_ctx *ctx)
+{
+    for (auto &r : ctx->prof_records) {
+        ctx->prof_pool.push_back(r.start);
+        ctx->prof_pool.push_back(r.stop);
+    }
+    ctx->prof_records.clear();
+}
+
+extern "C" int subquad_profile_enable(subquad_ctx *ctx, int on)
+{
+    SQ_ENTER(ctx);
+    ctx->prof_on = on != 0;
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_profile_reset(subquad_ctx *ctx)
+{
+    SQ_ENTER(ctx);
+    SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    prof_recycle(ctx);
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_profile_read(subquad_ctx *ctx, int kernel, double *total_ms, int64_t *launches)
+{
+    SQ_ENTER(ctx);
+    if (!total_ms || !launches || kernel < 0 || kernel >= SUBQUAD_PROF_COUNT) return SUBQUAD_ERR_ARG;
+    SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    double t = 0.0;
+    int64_t c = 0;
+    for (auto &r : ctx->prof_records) {
+        if (r.kernel != kernel) continue;
+        float ms = 0.f;
+        SQ_TRY_CUDA(cudaEventElapsedTime(&ms, r.start, r.stop));
+        t += ms;
+        ++c;
+    }
+    *total_ms = t;
+    *launches = c;
+    return SUBQUAD_OK;
+}
+
 extern "C" int subquad_destroy(subquad_ctx *ctx)
 {
     if (!ctx) return SUBQUAD_OK;
@@ -99,6 +157,9 @@ extern "C" int subquad_destroy(subquad_ctx *ctx)
         SqDeviceGuard guard(ctx);
         if (guard.ok) {
             cudaStreamSynchronize(ctx->stream);
+            prof_recycle(ctx);
+            for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+            ctx->prof_pool.clear();
             cudaFree(ctx->scratch);
             cudaFree(ctx->d_table);
             cudaFree(ctx->d_err);
@@ -128,6 +189,7 @@ extern "C" int subquad_check(subquad_ctx *ctx)
     SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));
     if (err & SQ_DEVERR_INPUT) return SUBQUAD_ERR_INPUT;
     if (err & SQ_DEVERR_TIMEOUT) return SUBQUAD_ERR_TIMEOUT;
+    if (err & SQ_DEVERR_CAPACITY) return SUBQUAD_ERR_CAPACITY;
     return SUBQUAD_OK;
 }
 

@@ -82,11 +82,14 @@ struct PairInputs {
 
 template <int WORDS, int CPL>
 __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
-    const uint32_t *__restrict__ pairs, int64_t m, const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc,
-    const uint64_t *__restrict__ packed, const float *__restrict__ emb, int d, const float *__restrict__ params,
-    int hidden, float *__restrict__ fused, float *__restrict__ alpha_out)
+    const uint32_t *__restrict__ pairs, int64_t m_max, const unsigned long long *__restrict__ d_m,
+    const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc, const uint64_t *__restrict__ packed,
+    const float *__restrict__ emb, int d, const float *__restrict__ params, int hidden, float *__restrict__ fused,
+    float *__restrict__ alpha_out)
 {
     __shared__ float s_par[5 * kMaxHidden + 1];
+    int64_t m = m_max;
+    if (d_m) m = (int64_t)*d_m < m_max ? (int64_t)*d_m : m_max;
     for (int q = threadIdx.x; q < 5 * hidden + 1; q += blockDim.x) s_par[q] = params[q];
     __syncthreads();
     const float *W1 = s_par, *b1 = s_par + 3 * hidden, *w2 = s_par + 4 * hidden;
@@ -137,12 +140,13 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
 template <int WORDS>
 int launch_forward(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
                    const int32_t *self_scores, const void *packed, const float *emb, int d, const float *gate_params,
-                   int hidden, float *fused_out, float *alpha_out)
+                   int hidden, float *fused_out, float *alpha_out, const unsigned long long *d_m = nullptr)
 {
     const int cpl = (d / 4 + kTppF - 1) / kTppF;  // float4 chunks per lane
+    SqProfScope prof(ctx, SUBQUAD_PROF_FUSE);
 #define SQ_FWD(C)                                                                                                  \
     fuse_forward_kernel<WORDS, C><<<grid, kFuseThreads, 0, ctx->stream>>>(                                         \
-        pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d, gate_params, hidden, fused_out, alpha_out)
+        pairs, m, d_m, sw, self_scores, (const uint64_t *)packed, emb, d, gate_params, hidden, fused_out, alpha_out)
     if (cpl <= 1) SQ_FWD(1);
     else if (cpl <= 2) SQ_FWD(2);
     else if (cpl <= 4) SQ_FWD(4);
@@ -542,4 +546,26 @@ extern "C" int subquad_fuse_backward_params_noalloc(subquad_ctx *ctx, const uint
     reduce_partials_kernel<<<1, 352, 0, ctx->stream>>>(partials, (int)grid, P, grad_params);
     SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
+}
+
+extern "C" int subquad_fuse_forward_async(subquad_ctx *ctx, const uint32_t *pairs, const uint64_t *d_m, int64_t m_max,
+                                          const int32_t *sw, const int32_t *self_scores, const void *packed,
+                                          int pack_stride, const float *emb, int d, const float *gate_params,
+                                          int hidden, float *fused_out, float *alpha_out)
+{
+    SQ_ENTER(ctx);
+    if (!d_m || m_max < 0 || d < 4 || d > 1024 || d % 4 || hidden < 1 || hidden > kMaxHidden) return SUBQUAD_ERR_ARG;
+    if (pack_stride != 16 && pack_stride != 32) return SUBQUAD_ERR_ARG;
+    if (m_max == 0) return SUBQUAD_OK;
+    if (!pairs || !sw || !self_scores || !packed || !emb || !gate_params || !fused_out) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(emb) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8 ||
+        reinterpret_cast<uintptr_t>(packed) % 16)
+        return SUBQUAD_ERR_ARG;
+    const unsigned grid = sq_grid(ctx, (m_max + 7) / 8 * 32, kFuseThreads, 8);
+    const auto *dm = reinterpret_cast<const unsigned long long *>(d_m);
+    if (pack_stride == 16)
+        return launch_forward<2>(ctx, grid, pairs, m_max, sw, self_scores, packed, emb, d, gate_params, hidden,
+                                 fused_out, alpha_out, dm);
+    return launch_forward<4>(ctx, grid, pairs, m_max, sw, self_scores, packed, emb, d, gate_params, hidden, fused_out,
+                             alpha_out, dm);
 }

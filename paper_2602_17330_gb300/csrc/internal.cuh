@@ -11,6 +11,14 @@
 enum : uint32_t {
     SQ_DEVERR_INPUT = 1u,
     SQ_DEVERR_TIMEOUT = 2u,
+    SQ_DEVERR_CAPACITY = 4u,
+};
+
+#include <vector>
+
+struct SqProfRecord {
+    int kernel;
+    cudaEvent_t start, stop;
 };
 
 struct subquad_ctx {
@@ -28,6 +36,36 @@ struct subquad_ctx {
     size_t scratch_cap = 0;
     int64_t launches = 0;  // kernels launched through this context
     int tune[SUBQUAD_TUNE_COUNT];  // tuning knobs, see subquad_set_tuning
+    bool prof_on = false;          // per-kernel event timing (subquad_profile_*)
+    std::vector<SqProfRecord> prof_records;
+    std::vector<cudaEvent_t> prof_pool;
+};
+
+// Opt-in per-kernel timing: events recorded on the context stream around one
+// launch (or launch sequence) tagged with a SUBQUAD_PROF_* id.
+cudaEvent_t sq_prof_event(subquad_ctx *ctx);
+struct SqProfScope {
+    subquad_ctx *ctx;
+    int kernel;
+    cudaEvent_t stop = nullptr;
+    SqProfScope(subquad_ctx *c, int k) : ctx(c), kernel(k)
+    {
+        if (!ctx->prof_on) return;
+        cudaEvent_t start = sq_prof_event(ctx);
+        stop = sq_prof_event(ctx);
+        if (!start || !stop) {
+            stop = nullptr;
+            return;
+        }
+        cudaEventRecord(start, ctx->stream);
+        ctx->prof_records.push_back({kernel, start, stop});
+    }
+    void finish()
+    {
+        if (stop) cudaEventRecord(stop, ctx->stream);
+        stop = nullptr;
+    }
+    ~SqProfScope() { finish(); }
 };
 
 // Last CUDA error seen by the library on this thread (for diagnostics).
@@ -126,3 +164,7 @@ int sq_radix_sort_u32(subquad_ctx *ctx, uint32_t *keys, uint32_t *vals, uint32_t
 int sq_radix_sort_u64(subquad_ctx *ctx, uint64_t *keys, uint64_t *keys_alt, int64_t count, const uint32_t *d_count,
                       int begin_bit, int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes);
 size_t sq_radix_tmp_bytes(int64_t count);
+
+// Lane-replicated alignment score table for the context's matrix and gap_open
+// (align.cu); shared by the alignment and the brute-force retrieval kernels.
+int sq_ensure_align_table(subquad_ctx *ctx, int gap_open);

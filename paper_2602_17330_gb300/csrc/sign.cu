@@ -130,6 +130,7 @@ extern "C" int subquad_sign(subquad_ctx *ctx, const void *packed, int pack_strid
     if (reinterpret_cast<uintptr_t>(packed) % 16 || reinterpret_cast<uintptr_t>(sig_out) % 16) return SUBQUAD_ERR_ARG;
     const size_t smem = (size_t)bands * rows * sizeof(uint2);
     unsigned grid = sq_grid(ctx, n, 256, 8);
+    SqProfScope prof(ctx, SUBQUAD_PROF_SIGN);
     if (pack_stride == 16)
         sign_kernel<2><<<grid, 256, smem, ctx->stream>>>((const uint64_t *)packed, n, k, bands, rows, a, b, sig_out);
     else

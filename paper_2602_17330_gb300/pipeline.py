@@ -108,3 +108,66 @@ def cells_of(lens: np.ndarray, pairs: np.ndarray) -> int:
     if pairs.shape[0] == 0:
         return 0
     return int((lens[pairs[:, 0]].astype(np.int64) * lens[pairs[:, 1]].astype(np.int64)).sum())
+
+
+class BatchedPipeline:
+    """Many repertoires in one pass with no host synchronisation: pack ->
+    sign -> donor-confined banding -> length-binned self-scores and alignment
+    -> fusion, every count kept on the device, so the whole pass can be
+    captured once as a CUDA graph and replayed.  The pair buffer has a fixed
+    capacity; an overflow is reported by ``ctx.check()``."""
+
+    def __init__(self, ctx, cfg: Workload, n: int, capacity: int):
+        torch = ctx.torch
+        self.ctx, self.cfg, self.n, self.capacity = ctx, cfg, n, capacity
+        dev = ctx.device
+        self.packed = torch.empty((n, cfg.pack_stride), dtype=torch.uint8, device=dev)
+        self.sig = torch.empty((cfg.bands, n, cfg.rows), dtype=torch.int32, device=dev)
+        self.pairs = torch.empty((capacity, 2), dtype=torch.int32, device=dev)
+        self.num_pairs = torch.zeros((1,), dtype=torch.int64, device=dev)
+        self.self_sc = torch.empty((n,), dtype=torch.int32, device=dev)
+        self.sw = torch.empty((capacity,), dtype=torch.int32, device=dev)
+        self.fused = torch.empty((capacity,), dtype=torch.float32, device=dev)
+        self.graph = None
+
+    def step(self, x):
+        """Queue one pass on the context's stream (no host synchronisation)."""
+        from . import subquad
+
+        ctx, cfg, n = self.ctx, self.cfg, self.n
+        lib, P = subquad.lib(), subquad._ptr
+        subquad._check(lib.subquad_pack(ctx.handle, P(x["codes"]), int(x["codes"].shape[1]), P(x["lens"]), n,
+                                        cfg.pack_stride, P(self.packed)), "subquad_pack")
+        subquad._check(lib.subquad_sign(ctx.handle, P(self.packed), cfg.pack_stride, n, cfg.k, cfg.bands, cfg.rows,
+                                        P(x["a"]), P(x["b"]), P(self.sig)), "subquad_sign")
+        ctx.band_candidates_async(self.sig, n, cfg.bands, cfg.rows, cfg.bucket_cap, self.pairs, self.num_pairs,
+                                  donor=x.get("donor"))
+        ctx.self_scores(self.packed, cfg.gap_open, cfg.gap_extend, out=self.self_sc, binned=True)
+        ctx.align_score_binned_async(self.packed, self.pairs, self.num_pairs, self.sw, cfg.gap_open, cfg.gap_extend)
+        ctx.fuse_forward_async(self.pairs, self.num_pairs, self.sw, self.self_sc, self.packed, x["emb"], x["params"],
+                               cfg.hidden, self.fused)
+
+    def capture(self, x):
+        """Run one pass eagerly (reserves scratch, builds tables), then capture
+        the pass as a CUDA graph on the context's stream."""
+        torch = self.ctx.torch
+        with torch.cuda.stream(self.ctx.stream):
+            self.step(x)
+        self.ctx.stream.synchronize()
+        self.ctx.check()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.ctx.stream):
+            self.step(x)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def result(self):
+        """(pairs, sw, fused, self) of the last pass as numpy, trimmed to |C|."""
+        self.ctx.stream.synchronize()
+        self.ctx.check()
+        m = int(self.num_pairs.item())
+        return dict(pairs=self.pairs[:m].cpu().numpy().view(np.uint32), sw=self.sw[:m].cpu().numpy(),
+                    fused=self.fused[:m].cpu().numpy(), self=self.self_sc.cpu().numpy(), m=m)

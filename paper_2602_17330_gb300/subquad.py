@@ -28,6 +28,9 @@ SUBQUAD_ERR_TIMEOUT = -4
 SUBQUAD_ERR_NOMEM = -5
 SUBQUAD_ERR_INPUT = -6
 
+PROF_NAMES = ["sign", "band", "band_insert", "band_sort", "band_emit", "band_pairsort", "align", "align_bin", "self",
+              "fuse"]
+
 TUNE_ALIGN_SHAPE = 0
 TUNE_BAND_L2_MB = 1
 
@@ -45,6 +48,9 @@ SIGNATURES = {
     "subquad_check": (_c.c_int, [_P]),
     "subquad_scratch_bytes": (_I64, [_P]),
     "subquad_launch_count": (_I64, [_P]),
+    "subquad_profile_enable": (_c.c_int, [_P, _c.c_int]),
+    "subquad_profile_reset": (_c.c_int, [_P]),
+    "subquad_profile_read": (_c.c_int, [_P, _c.c_int, _c.POINTER(_c.c_double), _c.POINTER(_I64)]),
     "subquad_set_tuning": (_c.c_int, [_P, _c.c_int, _c.c_int]),
     "subquad_get_tuning": (_c.c_int, [_P, _c.c_int, _c.POINTER(_c.c_int)]),
     "subquad_default_matrix": (_c.c_int, [_P]),
@@ -54,11 +60,19 @@ SIGNATURES = {
     "subquad_sign": (_c.c_int, [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _c.c_int, _P, _P, _P]),
     "subquad_band_candidates": (_c.c_int, [_P, _P, _I64, _c.c_int, _c.c_int, _c.c_int32, _P, _I64,
                                            _c.POINTER(_I64)]),
+    "subquad_band_candidates_async": (_c.c_int, [_P, _P, _I64, _c.c_int, _c.c_int, _c.c_int32, _P, _P, _I64, _P]),
+    "subquad_align_score_binned_async": (_c.c_int, [_P, _P, _c.c_int, _P, _P, _I64, _c.c_int, _c.c_int, _P]),
+    "subquad_fuse_forward_async": (_c.c_int, [_P, _P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P, _c.c_int,
+                                              _P, _P]),
     "subquad_align_score": (_c.c_int, [_P, _P, _c.c_int, _P, _I64, _c.c_int, _c.c_int, _P]),
     "subquad_self_scores": (_c.c_int, [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _P]),
     "subquad_align_score_binned": (_c.c_int, [_P, _P, _c.c_int, _P, _I64, _c.c_int, _c.c_int, _P]),
     "subquad_self_scores_binned": (_c.c_int, [_P, _P, _c.c_int, _I64, _c.c_int, _c.c_int, _P]),
     "subquad_fuse_forward": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P, _c.c_int, _P, _P]),
+    "subquad_topk_candidates": (_c.c_int, [_P, _P, _P, _I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _c.c_int, _P,
+                                           _P]),
+    "subquad_topk_bruteforce": (_c.c_int, [_P, _P, _c.c_int, _I64, _P, _c.c_int, _c.c_int, _P, _I64, _c.c_int, _P,
+                                           _P]),
     "subquad_pair_labels": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "subquad_pair_weights": (_c.c_int, [_P, _P, _I64, _c.c_int, _P]),
     "subquad_bce_loss": (_c.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
@@ -163,6 +177,21 @@ class Context:
     def launch_count(self) -> int:
         return int(lib().subquad_launch_count(self.handle))
 
+    def profile(self, on: bool = True):
+        _check(lib().subquad_profile_enable(self.handle, 1 if on else 0), "subquad_profile_enable")
+
+    def profile_reset(self):
+        _check(lib().subquad_profile_reset(self.handle), "subquad_profile_reset")
+
+    def profile_read(self) -> dict:
+        """{kernel tag: (total ms, launches)} since the last reset."""
+        out = {}
+        for k, name in enumerate(PROF_NAMES):
+            t, c = ctypes.c_double(0.0), _I64(0)
+            _check(lib().subquad_profile_read(self.handle, k, ctypes.byref(t), ctypes.byref(c)), "subquad_profile_read")
+            out[name] = (float(t.value), int(c.value))
+        return out
+
     def set_tuning(self, key: int, value: int):
         _check(lib().subquad_set_tuning(self.handle, key, value), "subquad_set_tuning")
 
@@ -230,6 +259,25 @@ class Context:
         _check(st, "subquad_band_candidates")
         return out[: int(count.value)]
 
+    # -- batched, graph-capturable forms (counts stay on the device) ----------
+    def band_candidates_async(self, sig, n: int, bands: int, rows: int, bucket_cap: int, pairs_out, d_num_pairs,
+                              donor=None):
+        """Writes |C| to the device tensor d_num_pairs (int64 [1]); no sync."""
+        _check(lib().subquad_band_candidates_async(self.handle, _ptr(sig), n, bands, rows, bucket_cap, _ptr(donor),
+                                                   _ptr(pairs_out), int(pairs_out.shape[0]), _ptr(d_num_pairs)),
+               "subquad_band_candidates_async")
+
+    def align_score_binned_async(self, packed, pairs, d_m, out, gap_open: int = 10, gap_extend: int = 1):
+        _check(lib().subquad_align_score_binned_async(self.handle, _ptr(packed), int(packed.shape[1]), _ptr(pairs),
+                                                      _ptr(d_m), int(pairs.shape[0]), gap_open, gap_extend,
+                                                      _ptr(out)), "subquad_align_score_binned_async")
+
+    def fuse_forward_async(self, pairs, d_m, sw, self_sc, packed, emb, params, hidden: int, out, alpha=None):
+        _check(lib().subquad_fuse_forward_async(self.handle, _ptr(pairs), _ptr(d_m), int(pairs.shape[0]), _ptr(sw),
+                                                _ptr(self_sc), _ptr(packed), int(packed.shape[1]), _ptr(emb),
+                                                int(emb.shape[1]), _ptr(params), hidden, _ptr(out), _ptr(alpha)),
+               "subquad_fuse_forward_async")
+
     def align_score(self, packed, pairs, gap_open: int = 10, gap_extend: int = 1, out=None, binned: bool = False):
         """binned=False: subquad_align_score (pairs in input order);
         binned=True: subquad_align_score_binned (length-binned work list)."""
@@ -264,6 +312,36 @@ class Context:
                                           _ptr(out), _ptr(alpha) if want_alpha else None), "subquad_fuse_forward")
         return (out, alpha) if want_alpha else out
 
+
+    # -- cross-donor retrieval -----------------------------------------------
+    def topk_candidates(self, pairs, scores, n: int, donor, queries, k: int, index=None):
+        """-> (top_id uint32-as-int32 [nq, k], top_score int32 [nq, k])."""
+        torch = self.torch
+        m = int(pairs.shape[0])
+        donor = self._dev(donor, torch.int32)
+        queries = self._dev(queries, torch.int32)
+        nq = int(queries.shape[0])
+        index = self.pair_index(pairs, n) if index is None else index
+        ids = self._empty((nq, k), torch.int32)
+        sc = self._empty((nq, k), torch.int32)
+        _check(lib().subquad_topk_candidates(self.handle, _ptr(pairs), _ptr(scores), m, n, _ptr(donor),
+                                             _ptr(index["perm_i"]), _ptr(index["off_i"]), _ptr(index["perm_j"]),
+                                             _ptr(index["off_j"]), _ptr(queries), nq, k, _ptr(ids), _ptr(sc)),
+               "subquad_topk_candidates")
+        return ids, sc
+
+    def topk_bruteforce(self, packed, donor, queries, k: int, gap_open: int = 10, gap_extend: int = 1):
+        torch = self.torch
+        n = int(packed.shape[0])
+        donor = self._dev(donor, torch.int32)
+        queries = self._dev(queries, torch.int32)
+        nq = int(queries.shape[0])
+        ids = self._empty((nq, k), torch.int32)
+        sc = self._empty((nq, k), torch.int32)
+        _check(lib().subquad_topk_bruteforce(self.handle, _ptr(packed), int(packed.shape[1]), n, _ptr(donor),
+                                             gap_open, gap_extend, _ptr(queries), nq, k, _ptr(ids), _ptr(sc)),
+               "subquad_topk_bruteforce")
+        return ids, sc
 
     # -- gate training ---------------------------------------------------------
     def pair_labels(self, pairs, family, subgroup):
@@ -396,3 +474,23 @@ def subquad_fuse_backward_params_noalloc(ctx: Context, *a, **k):
 
 def subquad_adam_step(ctx: Context, *a, **k):
     return ctx.adam_step(*a, **k)
+
+
+def subquad_topk_candidates(ctx: Context, *a, **k):
+    return ctx.topk_candidates(*a, **k)
+
+
+def subquad_topk_bruteforce(ctx: Context, *a, **k):
+    return ctx.topk_bruteforce(*a, **k)
+
+
+def subquad_band_candidates_async(ctx: Context, *a, **k):
+    return ctx.band_candidates_async(*a, **k)
+
+
+def subquad_align_score_binned_async(ctx: Context, *a, **k):
+    return ctx.align_score_binned_async(*a, **k)
+
+
+def subquad_fuse_forward_async(ctx: Context, *a, **k):
+    return ctx.fuse_forward_async(*a, **k)

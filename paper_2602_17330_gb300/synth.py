@@ -274,3 +274,57 @@ def zipf_repertoire(n: int = 10_000_000, seed: int = 0, hi: int = 50_000) -> Rep
     sizes = zipf_family_sizes(n // 2, 1.2, 2, hi, rng_for(seed, "sizes"))
     return make_repertoire(n, seed=seed, len_min=6, len_max=24, tail_frac=0.02,
                            tail_range=(25, 30), family_sizes=sizes)
+
+
+def pooled_repertoire(n_donors: int = 64, size_lo: int = 50_000, size_hi: int = 2_000_000, n_public: int = 500,
+                      public_lo: float = 1e-4, public_hi: float = 1e-2, seed: int = 0,
+                      family_size: int = 25) -> Repertoire:
+    """Many donors pooled into one repertoire (``donor`` gives each sequence's
+    donor).  Donor sizes are log-uniform on [size_lo, size_hi]; every donor has
+    its own residue frequencies and private families (families of
+    ``family_size`` covering half of its private sequences), and shares
+    ``n_public`` public families: each donor's total public fraction f_d is
+    log-uniform on [public_lo, public_hi] and its public members are spread
+    uniformly over the public families (each a 1-3 substitution variant of the
+    family's seed).  Family ids: public families 0..n_public-1, private ones
+    after them."""
+    r = rng_for(seed, "donors")
+    sizes = np.exp(r.uniform(np.log(size_lo), np.log(size_hi), n_donors)).astype(np.int64)
+    fracs = np.exp(r.uniform(np.log(public_lo), np.log(public_hi), n_donors))
+    rp = rng_for(seed, "public")
+    pub_freq = rp.dirichlet(np.full(20, 2.0))
+    pub_lens = _draw_lengths(rp, n_public, 8, 24, 0.0, (25, 30))
+    pub_codes = _draw_sequences(rp, pub_freq, pub_lens)
+    codes, lens, family, subgroup, donor = [], [], [], [], []
+    next_family = n_public
+    for d in range(n_donors):
+        n_d = int(sizes[d])
+        n_pub = min(n_d, int(round(fracs[d] * n_d)))
+        n_priv = n_d - n_pub
+        n_fam = max(1, int(round(0.5 * n_priv / family_size)))
+        rep = make_repertoire(n_priv, n_fam, seed=int(seed) * 100_003 + d + 1)
+        rd = rng_for(int(seed) * 100_003 + d + 1, "public")
+        pf = rd.integers(0, n_public, n_pub)
+        pc = pub_codes[pf].copy()
+        pl = pub_lens[pf].copy()
+        _substitute(rd, pub_freq, pc, pl)
+        fam = np.where(rep.family >= 0, rep.family + next_family, -1).astype(np.int32)
+        next_family += n_fam
+        c = np.concatenate([rep.codes, pc])
+        l = np.concatenate([rep.lens, pl])
+        f = np.concatenate([fam, pf.astype(np.int32)])
+        perm = rd.permutation(n_d)
+        codes.append(c[perm])
+        lens.append(l[perm])
+        family.append(f[perm])
+        subgroup.append(np.zeros(n_d, dtype=np.int32))
+        donor.append(np.full(n_d, d, dtype=np.int32))
+    return Repertoire(codes=np.ascontiguousarray(np.concatenate(codes)), lens=np.ascontiguousarray(np.concatenate(lens)),
+                      family=np.ascontiguousarray(np.concatenate(family)),
+                      subgroup=np.ascontiguousarray(np.concatenate(subgroup)), freq=pub_freq,
+                      donor=np.ascontiguousarray(np.concatenate(donor)))
+
+
+def sample_queries(n: int, count: int, seed: int = 0) -> np.ndarray:
+    """`count` distinct sequence ids drawn without replacement (uint32)."""
+    return np.sort(rng_for(seed, "queries").choice(n, size=min(count, n), replace=False)).astype(np.uint32)
