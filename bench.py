@@ -302,7 +302,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # algorithmic work per step of each tagged kernel: (bound, amount, unit, what)
     algo = {
         "sign": ("alu", 6.0 * hash_evals, "ops", "6 integer ops per hash evaluation"),
-        "band_insert": ("hbm", 4.0 * cfg.hashes * cfg.n, "bytes", "signatures read once"),
+        "band_partition": ("hbm", 4.0 * cfg.hashes * cfg.n + 8.0 * cfg.bands * cfg.n, "bytes",
+                           "signatures read once, (fingerprint, id) records written once"),
+        "band_group": ("hbm", 8.0 * cfg.bands * cfg.n, "bytes", "records read once"),
         "band_emit": ("hbm", 8.0 * m, "bytes", "unique pairs written once"),
         "band_pairsort": ("hbm", 16.0 * m, "bytes", "pairs read and written once"),
         "align": ("alu", SW_OPS_PER_CELL * cells, "ops", f"{SW_OPS_PER_CELL} int32 ops per DP cell"),
@@ -311,8 +313,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "fuse": ("hbm", 16.0 * m + cfg.n * (4.0 * cfg.d + 4 + cfg.pack_stride), "bytes",
                  "16 B per pair + each embedding row, self-score and record once"),
     }
-    kernel_names = {"sign": "sign_kernel", "band_insert": "band_insert_kernel + band_filter_kernel",
-                    "band_emit": "band chunking + band_emit_kernel", "band_pairsort": "pair radix sort",
+    kernel_names = {"sign": "sign_kernel", "band_partition": "part_hist_kernel + scan + part_scatter_kernel",
+                    "band_group": "part_group_kernel",
+                    "band_emit": "chunk pair-count scan + band_emit_kernel", "band_pairsort": "pair radix sort",
                     "align": "align_binned_kernel" if cfg.binned else "align_plain_kernel",
                     "align_bin": "bin_count/offsets/scatter", "self": "self-score alignment kernel",
                     "fuse": "fuse_forward_kernel"}

@@ -82,9 +82,10 @@ int64_t subquad_launch_count(const subquad_ctx *ctx);
  * effect for later calls and never change results.
  *   SUBQUAD_TUNE_ALIGN_SHAPE: batched alignment launch shape, 0 = 256 threads
  *     x 2 blocks per SM, 1 = 128 threads x 3 blocks per SM (default 1);
- *   SUBQUAD_TUNE_BAND_L2_MB: L2 share in MB for the banding hash tables; bands
- *     are inserted in groups whose tables fit it (default 48). */
-enum { SUBQUAD_TUNE_ALIGN_SHAPE = 0, SUBQUAD_TUNE_BAND_L2_MB = 1, SUBQUAD_TUNE_COUNT = 2 };
+ *   SUBQUAD_TUNE_BAND_PART_LOG2: log2 of the target number of (band, sequence)
+ *     keys per hash partition of the banding stage, 6..16 (default 10); each
+ *     partition is grouped by one CTA in shared memory. */
+enum { SUBQUAD_TUNE_ALIGN_SHAPE = 0, SUBQUAD_TUNE_BAND_PART_LOG2 = 1, SUBQUAD_TUNE_COUNT = 2 };
 int subquad_set_tuning(subquad_ctx *ctx, int key, int value);
 int subquad_get_tuning(const subquad_ctx *ctx, int key, int *value);
 
@@ -96,8 +97,8 @@ int subquad_get_tuning(const subquad_ctx *ctx, int key, int *value);
 enum {
     SUBQUAD_PROF_SIGN = 0,          /* sign_kernel */
     SUBQUAD_PROF_BAND = 1,          /* the whole banding stage of one call */
-    SUBQUAD_PROF_BAND_INSERT = 2,   /* hash insert + singleton filter, per band group */
-    SUBQUAD_PROF_BAND_SORT = 3,     /* sort of the kept keys */
+    SUBQUAD_PROF_BAND_PARTITION = 2, /* key hashing + stable hash partition, per band group */
+    SUBQUAD_PROF_BAND_GROUP = 3,     /* shared-memory grouping into buckets and chunks */
     SUBQUAD_PROF_BAND_EMIT = 4,     /* chunking + pair emission */
     SUBQUAD_PROF_BAND_PAIRSORT = 5, /* final sort of the pairs */
     SUBQUAD_PROF_ALIGN = 6,         /* align_plain_kernel or align_binned_kernel (pairs) */

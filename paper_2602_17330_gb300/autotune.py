@@ -3,8 +3,8 @@
 Each knob changes only how work is mapped onto the GB300 (never a result):
 * TUNE_ALIGN_SHAPE -- batched Smith-Waterman launch shape (256 threads x 2
   blocks per SM with 128 registers, or 128 x 3 with 168 registers);
-* TUNE_BAND_L2_MB -- L2 share given to the banding hash tables, which sets
-  how many bands are inserted per group.
+* TUNE_BAND_PART_LOG2 -- log2 of the target keys per hash partition of the
+  banding stage (each partition is grouped by one CTA in shared memory).
 
 ``autotune`` times every candidate on the caller's own workload with CUDA
 events on the context's stream, keeps the fastest, and caches the choice per
@@ -22,7 +22,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning.json")
 
 CANDIDATES = {
     subquad.TUNE_ALIGN_SHAPE: (0, 1),
-    subquad.TUNE_BAND_L2_MB: (8, 16, 32, 48, 64),
+    subquad.TUNE_BAND_PART_LOG2: (9, 10, 11),
 }
 
 
@@ -78,7 +78,7 @@ def autotune(ctx, packed, pairs, sig=None, n: int = 0, bands: int = 0, rows: int
     choice[knob] = min(timings[knob], key=timings[knob].get)
     ctx.set_tuning(knob, choice[knob])
     if sig is not None and n > 1:
-        knob = subquad.TUNE_BAND_L2_MB
+        knob = subquad.TUNE_BAND_PART_LOG2
         timings[knob] = {}
         buf = ctx.torch.empty((max(int(pairs.shape[0]), 1), 2), dtype=ctx.torch.int32, device=ctx.device)
         for v in CANDIDATES[knob]:

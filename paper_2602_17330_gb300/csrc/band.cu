@@ -1,35 +1,31 @@
 // (a2) LSH banding, candidate emission and deduplication (Algorithm 1,
 // preprocessing: "build MinHash index; generate candidate list CAND").
 //
-// Bands are inserted in groups whose hash tables fit a share of L2:
-//  1. insert every (band, sequence) key -- the exact R-tuple -- into a
-//     per-band open-addressing table whose slots hold the id of the first
-//     inserter; equal keys meet at one slot, so the slot index is an exact
-//     bucket id; count the members of every bucket;
-//  2. keep only members of buckets with >= 2 members (on the 1M-sequence
-//     donor about 10% of the keys) and radix-sort them by (bucket, id): each
-//     bucket becomes one contiguous run with its members in ascending id order
-//     (the contiguous bucket blocks of the paper's index);
-//  3. run starts by a max-scan of head positions; rank in bucket = position -
-//     run start; chunk = rank / cap; every kept element records, per band, the
-//     sorted position of its chunk head (its chunk id G[i][b]; singletons keep
-//     a sentinel that matches nothing);
-//  4. chunks with >= 2 members are compacted and their pair counts scanned;
-//  5. each warp takes 32 consecutive pair indices, finds their chunks, decodes
-//     (u, v) and keeps pair (i, j) only if no earlier band already puts i and j
-//     in one chunk (first-band ownership), so every pair of C is emitted once;
-//  6. after all groups: read back |C| (the call's only host synchronisation),
-//     then radix-sort the pairs into lexicographic order.
-// Element counts produced on the device (kept keys, chunks, raw pairs) are
-// consumed on the device: the kernels after them are sized for the upper
-// bound and read the actual count.
+//  1. every (band, sequence) key -- the exact R-tuple, plus the donor in a
+//     batch of donors -- is hashed to a 32-bit fingerprint and a partition
+//     digit; a per-tile histogram, a scan and a stable scatter lay the records
+//     (fingerprint, id) of each partition out contiguously in id order;
+//  2. one CTA per partition (about 1024 records) groups equal keys in a
+//     shared-memory hash table (fingerprint match confirmed on the exact
+//     keys); buckets of >= 2 members get contiguous kept positions, their
+//     chunks (runs of cap members in id order; the whole bucket when it is
+//     within cap) go to a chunk list, and each member records its chunk id
+//     G[i][b] for the band (singletons keep a sentinel that matches nothing);
+//  3. the chunk pair counts are scanned; each warp takes 32 consecutive pair
+//     indices, finds their chunks, decodes (u, v) and keeps pair (i, j) only
+//     if no earlier band already puts i and j in one chunk (first-band
+//     ownership), so every pair of C is emitted once;
+//  4. read back |C| (the synchronous form's only host synchronisation), then
+//     radix-sort the pairs into lexicographic order.
+// Counts produced on the device (chunks, raw pairs) are consumed on the
+// device: the kernels after them are sized for the upper bound and read the
+// actual count.
 #include <algorithm>
 
 #include "internal.cuh"
 
 namespace {
 
-constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr uint32_t kNoChunk = 0xffffffffu;  // chunk id of a singleton (matches nothing)
 
 __device__ __forceinline__ uint32_t mix32(uint32_t h)
@@ -93,15 +89,6 @@ __device__ __forceinline__ unsigned long long block_append(bool flag, unsigned l
     return pos;
 }
 
-// Step 1: exact bucket id (= table slot) per (band, sequence).  A slot holds
-// the id of its first inserter (whose key it stands for) in bits 0..30; bit 31
-// is set, by a plain store, as soon as a second member arrives.  Only the
-// first member of a bucket uses an atomic (the claiming CAS), so a bucket of
-// hundreds of members adds no contended atomics.  blockIdx.y = band in group.
-constexpr uint32_t kShared = 0x80000000u;
-
-constexpr int kInsIlp = 4;  // elements per thread in the singleton filter
-
 __device__ __forceinline__ uint32_t key_hash(const uint32_t k[8], int rows)
 {
     uint32_t h = 0x9e3779b9u ^ (uint32_t)rows;
@@ -111,8 +98,6 @@ __device__ __forceinline__ uint32_t key_hash(const uint32_t k[8], int rows)
     return h;
 }
 
-// Probe from `slot` until the element's key is claimed or found (the slow path
-// after a first probe that hit another key).
 // Equal keys: the same R-tuple and, in a batch of donors, the same donor.
 __device__ __forceinline__ bool same_key(const uint32_t *band_sig, int rows, uint32_t owner, const uint32_t k[8],
                                          const int32_t *donor, int32_t my_donor)
@@ -120,147 +105,647 @@ __device__ __forceinline__ bool same_key(const uint32_t *band_sig, int rows, uin
     return key_equal(band_sig + (int64_t)owner * rows, rows, k) && (!donor || donor[owner] == my_donor);
 }
 
-__device__ __forceinline__ uint32_t probe_from(uint32_t *tab, uint32_t slot, uint32_t smask, const uint32_t k[8],
-                                               uint32_t i, const uint32_t *band_sig, int rows, const int32_t *donor,
-                                               int32_t my_donor, uint32_t *err)
-{
-    for (uint32_t probe = 0; probe <= smask; ++probe) {
-        uint32_t cur = tab[slot];
-        if (cur == kEmpty) {
-            cur = atomicCAS(&tab[slot], kEmpty, i);
-            if (cur == kEmpty) return slot;
-        }
-        if (same_key(band_sig, rows, cur & ~kShared, k, donor, my_donor)) {
-            if (!(cur & kShared)) tab[slot] = cur | kShared;
-            return slot;
-        }
-        slot = (slot + 1) & smask;
-    }
-    atomicOr(err, SQ_DEVERR_TIMEOUT);  // unreachable: the table is at most half full
-    return 0;
-}
+// Steps 1-2: stable hash partition of the (band, sequence) keys.
+//
+// Every key gets a 32-bit fingerprint fp (a hash of the R-tuple and, in a
+// batch of donors, the donor) and a partition digit (pbits of an independent
+// second hash).
+// A per-tile digit histogram, an exclusive scan of the digit-major histogram
+// and a stable scatter place the records (fp << 32 | id) of every partition
+// contiguously, in ascending id order.  Equal keys have equal fingerprints and
+// so land in one partition.
+constexpr int kPartThreads = 256;
+constexpr int kPartItems = 16;
+constexpr int kPartTile = kPartThreads * kPartItems;
+constexpr int kPartMaxBits = 10;
 
-__global__ void __launch_bounds__(256) band_insert_kernel(const uint32_t *__restrict__ sig, int64_t n, int rows,
-                                                          int band0, int log_s, const int32_t *__restrict__ donor,
-                                                          uint32_t *__restrict__ table, uint32_t *__restrict__ slot_of,
-                                                          uint32_t *err)
-{
-    const int gb = blockIdx.y;
-    const uint32_t smask = (1u << log_s) - 1u;
-    const uint32_t *band_sig = sig + (int64_t)(band0 + gb) * n * rows;
-    uint32_t *tab = table + ((int64_t)gb << log_s);
-    uint32_t *slots = slot_of + (int64_t)gb * n;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t k[8];
-        load_key(band_sig + i * rows, rows, k);
-        const int32_t dn = donor ? donor[i] : 0;
-        const uint32_t home = mix32(key_hash(k, rows) ^ (uint32_t)dn) & smask;
-        slots[i] = probe_from(tab, home, smask, k, (uint32_t)i, band_sig, rows, donor, dn, err);
-    }
-}
-
-// Step 1b: keep the members of buckets with >= 2 members (singletons can form
-// no pair), as keys ((band << log_s | slot) << nbits) | id, appended in any
-// order -- the sort that follows orders them by band, bucket, then id.  A
-// member is kept if its bucket's slot is flagged shared.
-__global__ void __launch_bounds__(256) band_filter_kernel(const uint32_t *__restrict__ slot_of,
-                                                          const uint32_t *__restrict__ table, int64_t n, int band0,
-                                                          int log_s, int nbits, uint64_t *__restrict__ keys,
-                                                          unsigned long long *__restrict__ d_kept)
-{
-    __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_warp[32];
-    const int gb = blockIdx.y;
-    const uint32_t *tab = table + ((int64_t)gb << log_s);
-    const uint32_t *slots = slot_of + (int64_t)gb * n;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x * kInsIlp;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kInsIlp + threadIdx.x;
-         base - threadIdx.x < n; base += step) {
-        uint32_t slot[kInsIlp];
-        bool keep[kInsIlp];
-#pragma unroll
-        for (int q = 0; q < kInsIlp; ++q) {
-            const int64_t i = base + (int64_t)q * blockDim.x;
-            slot[q] = i < n ? slots[i] : 0u;
-        }
-#pragma unroll
-        for (int q = 0; q < kInsIlp; ++q) {
-            const int64_t i = base + (int64_t)q * blockDim.x;
-            keep[q] = i < n && (tab[slot[q]] & kShared) != 0u;
-        }
-#pragma unroll
-        for (int q = 0; q < kInsIlp; ++q) {
-            const int64_t i = base + (int64_t)q * blockDim.x;
-            const unsigned long long pos = block_append(keep[q], d_kept, &s_base, s_warp);
-            if (keep[q]) keys[pos] = ((((uint64_t)(band0 + gb) << log_s) | slot[q]) << nbits) | (uint64_t)i;
-        }
-    }
-}
-
-__device__ __forceinline__ int64_t dev_count(int64_t count_max, const uint32_t *d_count)
-{
-    const int64_t c = (int64_t)*d_count;
-    return c < count_max ? c : count_max;
-}
-
-// Step 3a: head positions of runs of equal buckets (0 elsewhere), for a max-scan.
-__global__ void band_heads_kernel(const uint64_t *__restrict__ keys, int nbits, int64_t count_max,
-                                  const uint32_t *__restrict__ d_count, uint32_t *__restrict__ head_pos)
-{
-    const int64_t count = dev_count(count_max, d_count);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-        head_pos[e] = (e == 0 || (keys[e] >> nbits) != (keys[e - 1] >> nbits)) ? (uint32_t)e : 0u;
-}
-
-struct ChunkInfo {
-    uint32_t head;  // sorted position of the element's chunk head
-    bool is_head, is_last;
+struct KeyHash {
+    uint32_t fp, digit;
 };
 
-__device__ __forceinline__ ChunkInfo chunk_info(const uint32_t *__restrict__ run_start, int64_t count, int64_t e,
-                                                int cap)
+// Two independent 32-bit hashes of the key: the fingerprint (one chain of
+// mixes) and the partition digit (a second chain with another seed), so two
+// distinct keys share a partition and a fingerprint with probability about
+// 2^-(32 + pbits).
+__device__ __forceinline__ KeyHash hash_key(const uint32_t k[8], int rows, int32_t dn, int pbits)
 {
-    ChunkInfo c;
-    const uint32_t rs = run_start[e];
-    const uint32_t rank = (uint32_t)e - rs;
-    c.head = cap > 0 ? rs + (rank / (uint32_t)cap) * (uint32_t)cap : rs;
-    c.is_head = (uint32_t)e == c.head;
-    c.is_last = e + 1 == count || run_start[e + 1] != rs || (cap > 0 && (rank + 1) % (uint32_t)cap == 0);
-    return c;
+    KeyHash h;
+    h.fp = mix32(key_hash(k, rows) ^ (uint32_t)dn);
+    uint32_t g = 0x85ebca6bu ^ (uint32_t)rows ^ ((uint32_t)dn * 0x27d4eb2fu);
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+        if (r < rows) g = mix32(g ^ k[r] ^ 0x165667b1u);
+    h.digit = pbits ? mix32(g) >> (32 - pbits) : 0u;
+    return h;
 }
 
-// Step 3b: chunk ids per (sequence, band) and flags of chunks with >= 2 members.
-__global__ void band_chunks_kernel(const uint64_t *__restrict__ keys, int nbits, const uint32_t *__restrict__ run_start,
-                                   int64_t count_max, const uint32_t *__restrict__ d_count, int cap, int log_s,
-                                   int band0, int bands, uint32_t *__restrict__ chunk_of, uint32_t *__restrict__ flags)
+// fd[gb * n + i] = (digit << 32 | fingerprint) of key (band0 + gb, i);
+// hist[(gb * P + digit) * ntiles + tile] = members of the digit in the tile
+__global__ void __launch_bounds__(kPartThreads) part_hist_kernel(const uint32_t *__restrict__ sig, int64_t n, int rows,
+                                                                 int band0, int pbits, const int32_t *__restrict__ donor,
+                                                                 int64_t ntiles, uint32_t *__restrict__ hist,
+                                                                 uint64_t *__restrict__ fd)
 {
-    const int64_t count = dev_count(count_max, d_count);
-    const uint64_t idmask = (1ull << nbits) - 1ull;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-        ChunkInfo c = chunk_info(run_start, count, e, cap);
-        const uint64_t k = keys[e];
-        const int b = (int)((k >> nbits) >> log_s);
-        chunk_of[(int64_t)(k & idmask) * bands + b] = c.head;
-        flags[e] = (c.is_head && !c.is_last) ? 1u : 0u;
+    extern __shared__ uint32_t s_hist[];
+    const int P = 1 << pbits, gb = blockIdx.y;
+    for (int q = threadIdx.x; q < P; q += blockDim.x) s_hist[q] = 0;
+    __syncthreads();
+    const uint32_t *band_sig = sig + (int64_t)(band0 + gb) * n * rows;
+    const int64_t tile = blockIdx.x;
+    // all loads first (independent, so they are in flight together), then the counts
+    uint32_t dg[kPartItems];
+#pragma unroll
+    for (int r = 0; r < kPartItems; ++r) {
+        const int64_t i = tile * kPartTile + r * kPartThreads + threadIdx.x;
+        dg[r] = 0x80000000u;
+        if (i < n) {
+            uint32_t k[8];
+            load_key(band_sig + i * rows, rows, k);
+            const KeyHash h = hash_key(k, rows, donor ? donor[i] : 0, pbits);
+            dg[r] = h.digit;
+            fd[(int64_t)gb * n + i] = ((uint64_t)h.digit << 32) | h.fp;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kPartItems; ++r)
+        if (dg[r] < 0x80000000u) atomicAdd(&s_hist[dg[r]], 1u);
+    __syncthreads();
+    for (int q = threadIdx.x; q < P; q += blockDim.x) hist[((int64_t)gb * P + q) * ntiles + tile] = s_hist[q];
+}
+
+// Stable scatter: warp w of a tile owns ids [tile*4096 + w*512, +512) in
+// rounds of 32, so digit-major ranks follow ascending id.
+__global__ void __launch_bounds__(kPartThreads, 3) part_scatter_kernel(const uint64_t *__restrict__ fd, int64_t n,
+                                                                    int pbits, int64_t ntiles,
+                                                                    const uint32_t *__restrict__ offs,
+                                                                    uint64_t *__restrict__ recs)
+{
+    extern __shared__ uint32_t s_wcnt[];  // [warps][P]
+    const int P = 1 << pbits, gb = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < (kPartThreads / 32) * P; q += blockDim.x) s_wcnt[q] = 0;
+    __syncthreads();
+    const uint64_t *band_fd = fd + (int64_t)gb * n;
+    const int64_t tile = blockIdx.x;
+    const int64_t wbase = tile * kPartTile + warp * 32 * kPartItems;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t *wcnt = s_wcnt + warp * P;
+    // dr[r]: digit in the low 16 bits (P = invalid), rank within the warp's
+    // digit run in the high 16 bits (< 32 * kPartItems)
+    uint32_t fp[kPartItems], dr[kPartItems];
+#pragma unroll
+    for (int r = 0; r < kPartItems; ++r) {
+        const int64_t i = wbase + r * 32 + lane;
+        const uint64_t v = i < n ? band_fd[i] : ((uint64_t)P << 32);
+        fp[r] = (uint32_t)v;
+        dr[r] = (uint32_t)(v >> 32);
+    }
+#pragma unroll
+    for (int r = 0; r < kPartItems; ++r) {
+        const uint32_t d = dr[r];
+        const bool valid = d < (uint32_t)P;
+        // lanes with the same digit: one ballot per digit bit (bit pbits marks invalid lanes)
+        uint32_t peers = 0xffffffffu;
+        for (int bit = 0; bit <= pbits; ++bit) {
+            const uint32_t m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? m : ~m;
+        }
+        const uint32_t before = __popc(peers & lt);
+        const uint32_t base = valid ? wcnt[d] : 0u;
+        __syncwarp();
+        if (valid && before == 0) wcnt[d] = base + __popc(peers);
+        __syncwarp();
+        dr[r] = d | ((base + before) << 16);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < P; d += blockDim.x) {
+        uint32_t run = offs[((int64_t)gb * P + d) * ntiles + tile];
+#pragma unroll
+        for (int w = 0; w < kPartThreads / 32; ++w) {
+            const uint32_t c = s_wcnt[w * P + d];
+            s_wcnt[w * P + d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kPartItems; ++r) {
+        const int64_t i = wbase + r * 32 + lane;
+        if (i < n) recs[wcnt[dr[r] & 0xffffu] + (dr[r] >> 16)] = ((uint64_t)fp[r] << 32) | (uint32_t)i;
     }
 }
 
-// Step 4: compacted chunk heads, sizes and pair counts.
-__global__ void band_chunk_list_kernel(const uint32_t *__restrict__ run_start, const uint32_t *__restrict__ flags,
-                                       const uint32_t *__restrict__ cidx, int64_t count_max,
-                                       const uint32_t *__restrict__ d_count, int cap, uint32_t *__restrict__ heads,
-                                       uint32_t *__restrict__ sizes, uint64_t *__restrict__ npairs)
+// Steps 3-4: one CTA per partition groups its records in a shared-memory
+// hash table keyed by fingerprint; a fingerprint match is confirmed by
+// comparing the two exact keys (and donors), so distinct keys never merge.
+// Per bucket of c >= 2 members the CTA reserves c contiguous kept positions
+// and writes its chunks (c members, or runs of cap members in id order when
+// c > cap) to the chunk list; every kept member records its chunk head as its
+// chunk id for the band.  Buckets within cap are filled in any order (one
+// chunk, order irrelevant); buckets above cap are filled by one warp walking
+// the records in id order, so chunk m holds ranks [m*cap, (m+1)*cap).
+// A partition holding more than kGrpDistinct distinct keys is split by
+// further fingerprint bits into sub-ranges processed one after another.
+constexpr int kGrpThreads = 256;
+constexpr int kGrpSlots = 4096;
+constexpr int kGrpDistinct = 3072;
+constexpr int kGrpFast = 3072;       // partitions up to this size are grouped with records in shared memory
+constexpr int kGrpFastSlots = 4096;  // their table (load <= 3/4)
+constexpr int kGrpVerify = 1024;     // deferred key comparisons held in shared memory
+constexpr uint32_t kFastEmpty = 0xffffffffu;
+// fast-path layout: tab u32[4096] | cnt u32[4096] | rec u64[3072] | slot u16[3072] | keys u16[1536] | vlist uint2[1024]
+constexpr size_t kGrpFastSmem = (size_t)kGrpFastSlots * 8 + (size_t)kGrpFast * 8 + (size_t)kGrpFast * 2 +
+                                (size_t)kGrpFast + (size_t)kGrpVerify * 8;
+// exact-path layout: tab u64[4096] | cnt u32[4096]
+constexpr size_t kGrpExactSmem = (size_t)kGrpSlots * (sizeof(unsigned long long) + sizeof(uint32_t));
+constexpr size_t kGrpSmem = kGrpFastSmem > kGrpExactSmem ? kGrpFastSmem : kGrpExactSmem;
+static_assert(kGrpFast * 4 <= kGrpFastSlots * 3, "a fast-path table is never more than 3/4 full");
+static_assert(kGrpFast <= 4096, "record indices fit the 12 low bits of a fast-path table entry");
+constexpr int kGrpStack = 48;
+constexpr int kGrpMaxLevel = 20;  // sub-ranges select fingerprint bits 12..31
+constexpr uint64_t kGrpEmpty = ~0ull;
+
+__device__ __forceinline__ uint64_t block_exclusive_u64(uint64_t v, uint64_t *total, uint64_t *s_warp)
 {
-    const int64_t count = dev_count(count_max, d_count);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-        if (flags[e]) heads[cidx[e]] = (uint32_t)e;
-        ChunkInfo c = chunk_info(run_start, count, e, cap);
-        if (c.is_last && !c.is_head) {
-            const uint32_t s = (uint32_t)e - c.head + 1;
-            const uint32_t ci = cidx[c.head];
-            sizes[ci] = s;
-            npairs[ci] = (uint64_t)s * (s - 1) / 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t run = 0;
+        for (int w = 0; w < nw; ++w) {
+            const uint64_t c = s_warp[w];
+            s_warp[w] = run;
+            run += c;
         }
+        s_warp[32] = run;
+    }
+    __syncthreads();
+    const uint64_t res = s_warp[warp] + inc - v;
+    *total = s_warp[32];
+    __syncthreads();
+    return res;
+}
+
+struct GroupOut {
+    uint32_t *kept_ids;
+    unsigned long long *d_kept;
+    uint32_t *d_nchunks;
+    uint32_t *heads, *sizes, *cband;
+    uint64_t *npairs;
+    uint32_t *chunk_of;
+    uint32_t *rslot;
+};
+
+struct GroupShared {
+    unsigned long long *tab;  // (fp << 32 | owner id) while inserting; (kept offset << 32 | count) after
+    uint32_t *cnt;            // member counts, then fill cursors
+    uint64_t *scan;           // [33]
+    uint32_t *distinct, *overflow, *big;
+    unsigned long long *kbase;
+    uint32_t *cbase;
+};
+
+// Slot of the record's key in the table, claiming an empty slot for a new
+// key.  Table entries hold (fingerprint, owner id); a fingerprint match is
+// confirmed on the exact keys.  Returns kGrpSlots if the table is declared
+// overflowed (more than kGrpDistinct keys) before the key is placed.
+__device__ __forceinline__ uint32_t find_or_claim(const GroupShared &g, uint32_t fp, uint32_t id,
+                                                  const uint32_t *band_sig, int rows, const int32_t *donor)
+{
+    uint32_t slot = fp & (kGrpSlots - 1);
+    bool have = false;
+    uint32_t key[8];
+    int32_t dn = 0;
+    for (int probe = 0; probe < kGrpSlots; ++probe) {
+        if (*(volatile uint32_t *)g.overflow) return kGrpSlots;
+        unsigned long long e = g.tab[slot];
+        if (e == kGrpEmpty) {
+            const unsigned long long mine = ((unsigned long long)fp << 32) | id;
+            e = atomicCAS(&g.tab[slot], kGrpEmpty, mine);
+            if (e == kGrpEmpty) {
+                if (atomicAdd(g.distinct, 1u) >= (uint32_t)kGrpDistinct) *g.overflow = 1;
+                return slot;
+            }
+        }
+        if ((uint32_t)(e >> 32) == fp) {
+            if (!have) {
+                load_key(band_sig + (int64_t)id * rows, rows, key);
+                dn = donor ? donor[id] : 0;
+                have = true;
+            }
+            if (same_key(band_sig, rows, (uint32_t)e, key, donor, dn)) return slot;
+        }
+        slot = (slot + 1) & (kGrpSlots - 1);
+    }
+    return kGrpSlots;
+}
+
+// Bucket offsets (kept members and chunks of >= 2 members per slot), one
+// reservation of kept positions and chunk-list entries per table, chunk list
+// entries, and the table rewritten to (kept offset << 32 | count).  Sets
+// *g.big if a bucket exceeds the cap.  Ends with the block synchronised.
+__device__ __forceinline__ void bucket_phase(const GroupShared &g, int cap, int b, const GroupOut &o)
+{
+    constexpr int kPer = kGrpSlots / kGrpThreads;
+    uint32_t c[kPer];
+    uint64_t mine = 0;
+    bool big = false;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        c[j] = g.cnt[j * kGrpThreads + threadIdx.x];
+        if (c[j] >= 2) {
+            uint32_t nch = 1;
+            if (cap > 0 && c[j] > (uint32_t)cap) {
+                nch = (cap >= 2 ? c[j] / (uint32_t)cap : 0u) + ((c[j] % (uint32_t)cap) >= 2 ? 1u : 0u);
+                big = true;
+            }
+            mine += ((uint64_t)c[j] << 32) | nch;
+        }
+    }
+    uint64_t total;
+    const uint64_t excl = block_exclusive_u64(mine, &total, g.scan);
+    if (big) *g.big = 1;
+    if (threadIdx.x == 0) {
+        *g.kbase = (total >> 32) ? atomicAdd(o.d_kept, (unsigned long long)(total >> 32)) : 0ull;
+        *g.cbase = (uint32_t)total ? atomicAdd(o.d_nchunks, (uint32_t)total) : 0u;
+    }
+    __syncthreads();
+    uint32_t koff = (uint32_t)(excl >> 32), coff = (uint32_t)excl;
+    const uint64_t kbase = *g.kbase;
+    const uint32_t cbase = *g.cbase;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int slot = j * kGrpThreads + threadIdx.x;
+        if (c[j] >= 2) {
+            const uint32_t head = (uint32_t)(kbase + koff);
+            const uint32_t step = (cap > 0 && c[j] > (uint32_t)cap) ? (uint32_t)cap : c[j];
+            for (uint32_t m0 = 0; m0 < c[j]; m0 += step) {
+                const uint32_t sz = min(step, c[j] - m0);
+                if (sz < 2) continue;
+                o.heads[cbase + coff] = head + m0;
+                o.sizes[cbase + coff] = sz;
+                o.cband[cbase + coff] = (uint32_t)b;
+                o.npairs[cbase + coff] = (uint64_t)sz * (sz - 1) / 2;
+                ++coff;
+            }
+            g.tab[slot] = ((unsigned long long)koff << 32) | c[j];
+            koff += c[j];
+        } else {
+            g.tab[slot] = c[j];  // 0 or 1 member: nothing kept
+        }
+        g.cnt[slot] = 0;  // becomes the fill cursor
+    }
+    __syncthreads();
+}
+
+// Kept position of a member of a bucket within the cap (any order).
+__device__ __forceinline__ void place_any(const GroupShared &g, uint32_t slot, uint32_t id, int cap, int b, int bands,
+                                          const GroupOut &o)
+{
+    const unsigned long long e = g.tab[slot];
+    const uint32_t cc = (uint32_t)e;
+    if (cc < 2 || (cap > 0 && cc > (uint32_t)cap)) return;
+    const uint32_t r = atomicAdd(&g.cnt[slot], 1u);
+    const uint64_t head = *g.kbase + (e >> 32);
+    o.kept_ids[head + r] = id;
+    o.chunk_of[(int64_t)id * bands + b] = (uint32_t)head;
+}
+
+// Members of buckets above the cap, ranked in id order by one warp walking
+// the records in order (records of a partition are in ascending id order).
+template <typename SlotOf>
+__device__ __forceinline__ void place_in_order(const GroupShared &g, const uint64_t *prec, int64_t cnt, uint32_t kmask,
+                                               uint32_t k, SlotOf slot_of, int cap, int b, int bands,
+                                               const GroupOut &o)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int64_t q0 = 0; q0 < cnt; q0 += 32) {
+        const int64_t q = q0 + lane;
+        uint32_t slot = 0, id = 0;
+        bool mine = false;
+        if (q < cnt) {
+            const uint64_t rec = prec[q];
+            id = (uint32_t)rec;
+            if ((((uint32_t)(rec >> 32) >> 12) & kmask) == k) {
+                slot = slot_of(q);
+                const uint32_t cc = (uint32_t)g.tab[slot];
+                mine = cc >= 2 && cap > 0 && cc > (uint32_t)cap;
+            }
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, mine ? slot : (0x80000000u | lane));
+        const uint32_t before = __popc(peers & lt);
+        const uint32_t base = mine ? g.cnt[slot] : 0u;
+        __syncwarp();
+        if (mine && before == 0) g.cnt[slot] = base + __popc(peers);
+        __syncwarp();
+        if (mine) {
+            const uint32_t r = base + before;
+            const uint64_t head = *g.kbase + (g.tab[slot] >> 32);
+            o.kept_ids[head + r] = id;
+            o.chunk_of[(int64_t)id * bands + b] = (uint32_t)(head + (r / (uint32_t)cap) * (uint32_t)cap);
+        }
+    }
+}
+
+// Fast path for a partition of at most kGrpFast records: records staged in
+// shared memory, one table of about 3-6 cnt slots (u32 entries: the upper 20
+// fingerprint bits and the owner's record index; the full fingerprint is
+// compared through the staged record).  Records are grouped by fingerprint;
+// every member that is not its bucket's owner then compares its exact key
+// with the owner's (a deferred list processed by the whole block, so the loads
+// overlap).  Returns false, with nothing written, if two distinct keys share
+// a fingerprint: the caller then runs the exact path.
+__device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, uint32_t cnt,
+                                        const uint32_t *__restrict__ band_sig, int rows,
+                                        const int32_t *__restrict__ donor, int cap, int b, int bands,
+                                        const GroupOut &o, unsigned long long *s_dyn, uint64_t *s_scan,
+                                        uint32_t &s_nk, uint32_t &s_nv, uint32_t &s_clash, uint32_t &s_big,
+                                        unsigned long long &s_kbase, uint32_t &s_cbase)
+{
+    uint32_t *tab = reinterpret_cast<uint32_t *>(s_dyn);
+    uint32_t *cntv = tab + kGrpFastSlots;
+    uint64_t *srec = reinterpret_cast<uint64_t *>(cntv + kGrpFastSlots);
+    uint16_t *sslot = reinterpret_cast<uint16_t *>(srec + kGrpFast);
+    uint16_t *keys = sslot + kGrpFast;
+    uint2 *vlist = reinterpret_cast<uint2 *>(keys + kGrpFast / 2);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lt = (1u << lane) - 1u;
+    // a power of two >= 3 cnt (load <= 1/3; linear probing then stays short
+    // for every lane of a warp), at most kGrpFastSlots
+    uint32_t tslots = 256;
+    while (tslots < 3 * cnt && tslots < (uint32_t)kGrpFastSlots) tslots <<= 1;
+
+#pragma unroll 4
+    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) srec[q] = prec[q];
+    for (uint32_t q = threadIdx.x; q < tslots; q += blockDim.x) {
+        tab[q] = kFastEmpty;
+        cntv[q] = 0;
+    }
+    if (threadIdx.x == 0) {
+        s_nk = 0;
+        s_nv = 0;
+        s_clash = 0;
+        s_big = 0;
+    }
+    __syncthreads();
+    bool clash = false;
+    // insert; warp-uniform trip count so the ballots see the whole warp
+    for (uint32_t q0 = warp * 32; q0 < cnt; q0 += blockDim.x) {
+        const uint32_t q = q0 + lane;
+        const bool valid = q < cnt;
+        uint32_t owner = q;
+        if (valid) {
+            const uint32_t fp = (uint32_t)(srec[q] >> 32);
+            const uint32_t mine = (fp & ~0xfffu) | q;
+            uint32_t sl = fp >> (32 - __ffs(tslots) + 1);
+#pragma unroll 1
+            for (uint32_t probe = 0; probe < tslots; ++probe) {
+                uint32_t e = tab[sl];
+                if (e == kFastEmpty) {
+                    e = atomicCAS(&tab[sl], kFastEmpty, mine);
+                    if (e == kFastEmpty) break;
+                }
+                if (((e ^ fp) & ~0xfffu) == 0 && (uint32_t)(srec[e & 0xfffu] >> 32) == fp) {
+                    owner = e & 0xfffu;
+                    break;
+                }
+                sl = (sl + 1) & (tslots - 1);
+            }
+            sslot[q] = (uint16_t)sl;
+            atomicAdd(&cntv[sl], 1u);
+        }
+        const bool need = valid && owner != q;
+        const uint32_t m = __ballot_sync(0xffffffffu, need);
+        uint32_t base = 0;
+        if (lane == 0 && m) base = atomicAdd(&s_nv, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (need) {
+            const uint32_t v = base + __popc(m & lt);
+            if (v < (uint32_t)kGrpVerify) {
+                vlist[v] = make_uint2(q, owner);
+            } else {
+                const uint32_t id = (uint32_t)srec[q];
+                uint32_t key[8];
+                load_key(band_sig + (int64_t)id * rows, rows, key);
+                clash = clash || !same_key(band_sig, rows, (uint32_t)srec[owner], key, donor, donor ? donor[id] : 0);
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t nv = min(s_nv, (uint32_t)kGrpVerify);
+    for (uint32_t t = threadIdx.x; t < nv; t += blockDim.x) {
+        const uint2 pr = vlist[t];
+        const uint32_t id = (uint32_t)srec[pr.x];
+        uint32_t key[8];
+        load_key(band_sig + (int64_t)id * rows, rows, key);
+        clash = clash || !same_key(band_sig, rows, (uint32_t)srec[pr.y], key, donor, donor ? donor[id] : 0);
+    }
+    // buckets of >= 2 members listed (warp-aggregated appends); other slots marked
+    for (uint32_t t0 = 0; t0 < tslots; t0 += blockDim.x) {
+        const uint32_t sl = t0 + threadIdx.x;
+        const bool kept = cntv[sl] >= 2;
+        if (!kept) tab[sl] = kFastEmpty;
+        const uint32_t m = __ballot_sync(0xffffffffu, kept);
+        uint32_t base = 0;
+        if (lane == 0 && m) base = atomicAdd(&s_nk, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (kept) keys[base + __popc(m & lt)] = (uint16_t)sl;
+    }
+    if (clash) s_clash = 1;
+    __syncthreads();
+    if (s_clash) return false;  // uniform: read after the barrier
+
+    // kept offsets and chunk counts over the listed buckets
+    const uint32_t nk = s_nk;
+    uint64_t sum = 0;
+    bool big = false;
+    for (uint32_t t = threadIdx.x; t < nk; t += blockDim.x) {
+        const uint32_t c = cntv[keys[t]];
+        uint32_t nch = 1;
+        if (cap > 0 && c > (uint32_t)cap) {
+            nch = (cap >= 2 ? c / (uint32_t)cap : 0u) + ((c % (uint32_t)cap) >= 2 ? 1u : 0u);
+            big = true;
+        }
+        sum += ((uint64_t)c << 32) | nch;
+    }
+    uint64_t total;
+    const uint64_t excl = block_exclusive_u64(sum, &total, s_scan);
+    if (big) s_big = 1;
+    if (threadIdx.x == 0) {
+        s_kbase = (total >> 32) ? atomicAdd(o.d_kept, (unsigned long long)(total >> 32)) : 0ull;
+        s_cbase = (uint32_t)total ? atomicAdd(o.d_nchunks, (uint32_t)total) : 0u;
+    }
+    __syncthreads();
+    const uint64_t kbase = s_kbase;
+    {
+        uint32_t koff = (uint32_t)(excl >> 32), coff = (uint32_t)excl;
+        const uint32_t cbase = s_cbase;
+        for (uint32_t t = threadIdx.x; t < nk; t += blockDim.x) {
+            const uint32_t sl = keys[t];
+            const uint32_t c = cntv[sl];
+            const uint32_t head = (uint32_t)(kbase + koff);
+            const uint32_t step = (cap > 0 && c > (uint32_t)cap) ? (uint32_t)cap : c;
+            for (uint32_t m0 = 0; m0 < c; m0 += step) {
+                const uint32_t sz = min(step, c - m0);
+                if (sz < 2) continue;
+                o.heads[cbase + coff] = head + m0;
+                o.sizes[cbase + coff] = sz;
+                o.cband[cbase + coff] = (uint32_t)b;
+                o.npairs[cbase + coff] = (uint64_t)sz * (sz - 1) / 2;
+                ++coff;
+            }
+            tab[sl] = (koff << 16) | c;  // koff, c < 2^12
+            koff += c;
+            cntv[sl] = 0;  // becomes the fill cursor
+        }
+    }
+    __syncthreads();
+    // members of buckets within the cap: any order
+    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const uint32_t sl = sslot[q];
+        const uint32_t e = tab[sl];
+        if (e == kFastEmpty) continue;
+        const uint32_t c = e & 0xffffu;
+        if (cap > 0 && c > (uint32_t)cap) continue;
+        const uint32_t r = atomicAdd(&cntv[sl], 1u);
+        const uint64_t head = kbase + (e >> 16);
+        const uint32_t id = (uint32_t)srec[q];
+        o.kept_ids[head + r] = id;
+        o.chunk_of[(int64_t)id * bands + b] = (uint32_t)head;
+    }
+    // members of buckets above the cap: ranks in id order (one warp, records in order)
+    if (s_big && warp == 0) {
+        for (uint32_t q0 = 0; q0 < cnt; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            uint32_t sl = 0, e = kFastEmpty;
+            if (q < cnt) {
+                sl = sslot[q];
+                e = tab[sl];
+            }
+            const bool mine = e != kFastEmpty && cap > 0 && (e & 0xffffu) > (uint32_t)cap;
+            const uint32_t peers = __match_any_sync(0xffffffffu, mine ? sl : (0x80000000u | lane));
+            const uint32_t before = __popc(peers & lt);
+            const uint32_t basec = mine ? cntv[sl] : 0u;
+            __syncwarp();
+            if (mine && before == 0) cntv[sl] = basec + __popc(peers);
+            __syncwarp();
+            if (mine) {
+                const uint32_t r = basec + before;
+                const uint64_t head = kbase + (e >> 16);
+                const uint32_t id = (uint32_t)srec[q];
+                o.kept_ids[head + r] = id;
+                o.chunk_of[(int64_t)id * bands + b] = (uint32_t)(head + (r / (uint32_t)cap) * (uint32_t)cap);
+            }
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kGrpThreads, 3) part_group_kernel(
+    const uint64_t *__restrict__ recs, const uint32_t *__restrict__ offs, int64_t ntiles, int64_t total_recs,
+    int pbits, int band0, int bands, const uint32_t *__restrict__ sig, int64_t n, int rows,
+    const int32_t *__restrict__ donor, int cap, GroupOut o, uint32_t *err)
+{
+    extern __shared__ unsigned long long s_dyn[];
+    __shared__ uint64_t s_scan[33];
+    __shared__ uint32_t s_stack[kGrpStack][2];
+    __shared__ int s_top;
+    __shared__ uint32_t s_distinct, s_overflow, s_big, s_nv;
+    __shared__ unsigned long long s_kbase;
+    __shared__ uint32_t s_cbase;
+    GroupShared g;
+    g.tab = s_dyn;
+    g.cnt = reinterpret_cast<uint32_t *>(s_dyn + kGrpSlots);
+    g.scan = s_scan;
+    g.distinct = &s_distinct;
+    g.overflow = &s_overflow;
+    g.big = &s_big;
+    g.kbase = &s_kbase;
+    g.cbase = &s_cbase;
+
+    const int64_t p = blockIdx.x;
+    const int gb = (int)(p >> pbits), b = band0 + gb;
+    const int64_t start = offs[p * ntiles];
+    const int64_t end = p + 1 < (int64_t)gridDim.x ? (int64_t)offs[(p + 1) * ntiles] : total_recs;
+    const int64_t cnt = end - start;
+    if (cnt < 2) return;
+    const uint32_t *band_sig = sig + (int64_t)b * n * rows;
+    const uint64_t *prec = recs + start;
+
+    if (cnt <= kGrpFast &&
+        group_fast(prec, (uint32_t)cnt, band_sig, rows, donor, cap, b, bands, o, s_dyn, s_scan, s_distinct, s_nv,
+                   s_overflow, s_big, s_kbase, s_cbase))
+        return;
+
+    // Large partition (or a fingerprint clash): records streamed from global
+    // memory, every fingerprint match confirmed on the exact keys before it
+    // joins a bucket; the partition is split into fingerprint sub-ranges (a stack of (level, k): the records
+    // with ((fp >> 12) mod 2^level) == k) while one holds too many keys.
+    uint32_t *rslot = o.rslot + start;
+    if (threadIdx.x == 0) {
+        s_stack[0][0] = 0;
+        s_stack[0][1] = 0;
+        s_top = 1;
+    }
+    for (;;) {
+        __syncthreads();
+        const int top = s_top;
+        if (top == 0) break;
+        const uint32_t level = s_stack[top - 1][0], k = s_stack[top - 1][1];
+        const uint32_t kmask = (1u << level) - 1u;
+        __syncthreads();  // every thread has read the node before it is popped
+        for (int q = threadIdx.x; q < kGrpSlots; q += blockDim.x) {
+            g.tab[q] = kGrpEmpty;
+            g.cnt[q] = 0;
+        }
+        if (threadIdx.x == 0) {
+            s_top = top - 1;
+            s_distinct = 0;
+            s_overflow = 0;
+            s_big = 0;
+        }
+        __syncthreads();
+        for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const uint64_t rec = prec[q];
+            const uint32_t fp = (uint32_t)(rec >> 32);
+            if (((fp >> 12) & kmask) != k) continue;
+            const uint32_t sl = find_or_claim(g, fp, (uint32_t)rec, band_sig, rows, donor);
+            if (sl < (uint32_t)kGrpSlots) {
+                rslot[q] = sl;
+                atomicAdd(&g.cnt[sl], 1u);
+            } else {
+                s_overflow = 1;
+            }
+        }
+        __syncthreads();
+        if (s_overflow) {
+            if (threadIdx.x == 0) {
+                if (level + 1 > (uint32_t)kGrpMaxLevel || s_top + 2 > kGrpStack) {
+                    atomicOr(err, SQ_DEVERR_CAPACITY);
+                } else {
+                    s_stack[s_top][0] = level + 1;
+                    s_stack[s_top][1] = k + (1u << level);
+                    s_stack[s_top + 1][0] = level + 1;
+                    s_stack[s_top + 1][1] = k;
+                    s_top += 2;
+                }
+            }
+            continue;
+        }
+        bucket_phase(g, cap, b, o);
+        for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const uint64_t rec = prec[q];
+            if ((((uint32_t)(rec >> 32) >> 12) & kmask) != k) continue;
+            place_any(g, rslot[q], (uint32_t)rec, cap, b, bands, o);
+        }
+        if (s_big && threadIdx.x < 32)
+            place_in_order(g, prec, cnt, kmask, k, [&](int64_t q) { return rslot[q]; }, cap, b, bands, o);
     }
 }
 
@@ -280,66 +765,305 @@ __device__ __forceinline__ void decode_pair(uint64_t t, uint32_t s, uint32_t &u,
     v = (uint32_t)(ue + 1 + (int64_t)(t - row_start(ue)));
 }
 
-// Step 5: owned pairs of this band group, appended to out.
+// Chunk holding the first raw pair of every group of 32 (one binary search
+// per group, all in parallel).
+__device__ __forceinline__ uint32_t chunk_of_raw(const uint64_t *__restrict__ poff, uint32_t nc, uint64_t q)
+{
+    uint32_t lo = 0, hi = nc;  // largest c with poff[c] <= q (every chunk has >= 1 pair)
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (poff[mid] <= q) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void band_warp_chunk_kernel(const uint64_t *__restrict__ poff, const uint32_t *__restrict__ d_nchunks,
+                                       const uint64_t *__restrict__ d_total, uint32_t *__restrict__ wchunk,
+                                       int64_t wmax)
+{
+    const uint32_t nc = *d_nchunks;
+    const uint64_t groups = min((*d_total + 31) / 32, (uint64_t)wmax);
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < groups;
+         w += (uint64_t)gridDim.x * blockDim.x)
+        wchunk[w] = chunk_of_raw(poff, nc, w * 32);
+}
+
+// Step 5: owned pairs, appended to out.  Each warp takes 32 consecutive raw
+// pair indices; their chunks are c0 (looked up) plus the chunks starting
+// inside the group (one load per lane and a warp OR of start positions); each
+// lane decodes its (u, v) and keeps pair (i, j) only if no earlier band
+// already puts i and j in one chunk (first-band ownership), so every pair of
+// C is emitted exactly once.
 __global__ void __launch_bounds__(256) band_emit_kernel(
-    const uint64_t *__restrict__ keys, int nbits, const uint32_t *__restrict__ heads,
-    const uint32_t *__restrict__ sizes, const uint64_t *__restrict__ poff, const uint32_t *__restrict__ d_nchunks,
-    const uint64_t *__restrict__ d_total, int log_s, int band0, int bands, const uint32_t *__restrict__ chunk_of,
-    uint32_t *__restrict__ out, int64_t capacity, unsigned long long *__restrict__ d_count, uint32_t *err)
+    const uint32_t *__restrict__ kept_ids, const uint32_t *__restrict__ heads, const uint32_t *__restrict__ sizes,
+    const uint32_t *__restrict__ cband, const uint64_t *__restrict__ poff, const uint32_t *__restrict__ wchunk,
+    int64_t wmax, const uint32_t *__restrict__ d_nchunks, const uint64_t *__restrict__ d_total, int bands,
+    const uint32_t *__restrict__ chunk_of, uint32_t *__restrict__ out, int64_t capacity,
+    unsigned long long *__restrict__ d_count, uint32_t *__restrict__ deg, uint32_t *err)
 {
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_warp[32];
     const uint32_t nc = *d_nchunks;
     const uint64_t total = *d_total;
-    const int lane = threadIdx.x & 31;
+    const uint32_t lane = threadIdx.x & 31;
     // block-uniform trip count (block_append synchronises the block)
     for (uint64_t b0 = (uint64_t)blockIdx.x * blockDim.x; b0 < total; b0 += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t q0 = b0 + (threadIdx.x & ~31u);
-        // chunk of q0: largest c with poff[c] <= q0 (every chunk has >= 1 pair)
-        uint32_t c0 = 0;
-        if (lane == 0 && q0 < total) {
-            uint32_t lo = 0, hi = nc;
-            while (hi - lo > 1) {
-                uint32_t mid = (lo + hi) >> 1;
-                if (poff[mid] <= q0) lo = mid;
-                else hi = mid;
-            }
-            c0 = lo;
-        }
-        c0 = __shfl_sync(0xffffffffu, c0, 0);
         const uint64_t q = q0 + lane;
+        uint32_t c0 = 0, starts = 0;
+        if (q0 < total) {
+            c0 = q0 / 32 < (uint64_t)wmax ? wchunk[q0 / 32] : chunk_of_raw(poff, nc, q0);
+            const uint32_t c = c0 + 1 + lane;
+            if (c < nc) {
+                const uint64_t d = poff[c] - q0;  // >= 1: chunk c starts after q0
+                if (d < 32) starts = 1u << d;
+            }
+        }
+        starts = __reduce_or_sync(0xffffffffu, starts);
         bool owned = false;
         uint32_t i = 0, j = 0;
         if (q < total) {
-            uint32_t lo = c0, hi = min(nc, c0 + (uint32_t)lane + 1);
-            while (hi - lo > 1) {
-                uint32_t mid = (lo + hi) >> 1;
-                if (poff[mid] <= q) lo = mid;
-                else hi = mid;
-            }
-            const uint32_t h = heads[lo], s = sizes[lo];
+            const uint32_t cl = c0 + __popc(starts & ((2u << lane) - 1u));
+            const uint32_t h = heads[cl], s = sizes[cl];
+            const int b = (int)cband[cl];
             uint32_t u, v;
-            decode_pair(q - poff[lo], s, u, v);
+            decode_pair(q - poff[cl], s, u, v);
             if (u >= v || v >= s) {  // cannot happen for a consistent chunk list
                 atomicOr(err, SQ_DEVERR_TIMEOUT);
                 u = 0;
                 v = 1;
             }
-            const uint64_t idmask = (1ull << nbits) - 1ull;
-            i = (uint32_t)(keys[h + u] & idmask);
-            j = (uint32_t)(keys[h + v] & idmask);
-            const int b = (int)((keys[h] >> nbits) >> log_s);
+            i = kept_ids[h + u];
+            j = kept_ids[h + v];
+            if (i > j) {
+                const uint32_t t = i;
+                i = j;
+                j = t;
+            }
             owned = true;
             const uint32_t *gi = chunk_of + (int64_t)i * bands;
             const uint32_t *gj = chunk_of + (int64_t)j * bands;
-            for (int bb = 0; bb < b; ++bb)
-                if (gi[bb] == gj[bb] && gi[bb] != kNoChunk) {
-                    owned = false;
-                    break;
-                }
+            for (int bb = 0; bb < b; ++bb) {
+                const uint32_t x = gi[bb], y = gj[bb];
+                owned = owned && !(x == y && x != kNoChunk);
+            }
         }
         const unsigned long long pos = block_append(owned, d_count, &s_base, s_warp);
-        if (owned && pos < (unsigned long long)capacity) reinterpret_cast<uint2 *>(out)[pos] = make_uint2(i, j);
+        if (owned && pos < (unsigned long long)capacity) {
+            reinterpret_cast<uint2 *>(out)[pos] = make_uint2(i, j);
+            if (deg) atomicAdd(&deg[i], 1u);
+        }
+    }
+}
+
+// Lexicographic order of the emitted pairs (synchronous form): a counting
+// pass by first member i (degrees counted by the emitter, scanned into row
+// offsets), a scatter of the second members into their rows, and a sort of
+// every row: in registers for rows of at most kRowSmall partners, in shared
+// memory (one CTA per row) up to kRowMid.  Longer rows (possible only with
+// very large buckets) take the global radix sort instead.
+constexpr int kRowSmall = 32;
+constexpr int kRowWarp = 1024;  // rows up to this size: one warp, registers
+constexpr int kRowMid = 8192;   // rows up to this size: one CTA, shared memory
+constexpr int kRowThreads = 256;
+
+__device__ __forceinline__ uint64_t row_end(const uint32_t *rowoff, int64_t n, uint64_t m, int64_t i)
+{
+    return i + 1 < n ? rowoff[i + 1] : m;
+}
+
+// rows of more than kRowSmall partners: those up to kRowWarp listed from the
+// front of `mid`, those up to kRowMid from the back, the longer ones counted
+__global__ void __launch_bounds__(kRowThreads) rows_classify_kernel(const uint32_t *__restrict__ rowoff, int64_t n,
+                                                                    const unsigned long long *__restrict__ d_m,
+                                                                    uint32_t *__restrict__ mid,
+                                                                    unsigned long long *__restrict__ d_warp,
+                                                                    unsigned long long *__restrict__ d_cta,
+                                                                    unsigned long long *__restrict__ d_long)
+{
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_warp[32];
+    const uint64_t m = *d_m;
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n; b0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = b0 + threadIdx.x;
+        uint64_t d = 0;
+        if (i < n) d = row_end(rowoff, n, m, i) - rowoff[i];
+        if (d > (uint64_t)kRowMid) atomicAdd(d_long, 1ull);
+        const bool is_warp = d > (uint64_t)kRowSmall && d <= (uint64_t)kRowWarp;
+        const bool is_cta = d > (uint64_t)kRowWarp && d <= (uint64_t)kRowMid;
+        const unsigned long long pw = block_append(is_warp, d_warp, &s_base, s_warp);
+        if (is_warp) mid[pw] = (uint32_t)i;
+        const unsigned long long pc = block_append(is_cta, d_cta, &s_base, s_warp);
+        if (is_cta) mid[n - 1 - (int64_t)pc] = (uint32_t)i;
+    }
+}
+
+__global__ void pairs_scatter_kernel(const uint32_t *__restrict__ pairs, int64_t m, const uint32_t *__restrict__ rowoff,
+                                     uint32_t *__restrict__ fill, uint32_t *__restrict__ col)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
+        col[rowoff[ij.x] + atomicSub(&fill[ij.x], 1u) - 1u] = ij.y;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void bitonic_regs(uint32_t (&v)[N])
+{
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                const int b = a ^ j;
+                if (b > a) {
+                    const uint32_t lo = min(v[a], v[b]), hi = max(v[a], v[b]);
+                    const bool asc = (a & k) == 0;
+                    v[a] = asc ? lo : hi;
+                    v[b] = asc ? hi : lo;
+                }
+            }
+}
+
+template <int N>
+__device__ __forceinline__ void sort_row_regs(const uint32_t *__restrict__ col, uint64_t r0, uint32_t d, uint32_t i,
+                                              uint32_t *__restrict__ out)
+{
+    uint32_t v[N];
+#pragma unroll
+    for (int t = 0; t < N; ++t) v[t] = (uint32_t)t < d ? col[r0 + t] : 0xffffffffu;
+    bitonic_regs<N>(v);
+#pragma unroll
+    for (int t = 0; t < N; ++t)
+        if ((uint32_t)t < d) reinterpret_cast<uint2 *>(out)[r0 + t] = make_uint2(i, v[t]);
+}
+
+__global__ void __launch_bounds__(kRowThreads) rows_sort_small_kernel(const uint32_t *__restrict__ rowoff, int64_t n,
+                                                                      const unsigned long long *__restrict__ d_m,
+                                                                      const uint32_t *__restrict__ col,
+                                                                      uint32_t *__restrict__ out)
+{
+    const uint64_t m = *d_m;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t r0 = rowoff[i];
+        const uint64_t d = row_end(rowoff, n, m, i) - r0;
+        if (d == 0 || d > (uint64_t)kRowSmall) continue;
+        if (d == 1) reinterpret_cast<uint2 *>(out)[r0] = make_uint2((uint32_t)i, col[r0]);
+        else if (d <= 4) sort_row_regs<4>(col, r0, (uint32_t)d, (uint32_t)i, out);
+        else if (d <= 8) sort_row_regs<8>(col, r0, (uint32_t)d, (uint32_t)i, out);
+        else if (d <= 16) sort_row_regs<16>(col, r0, (uint32_t)d, (uint32_t)i, out);
+        else sort_row_regs<32>(col, r0, (uint32_t)d, (uint32_t)i, out);
+    }
+}
+
+// One warp per row of 33..kRowWarp partners: E values per lane in striped
+// order (element a = e * 32 + lane), bitonic network over 32 E elements with
+// register exchanges for distances >= 32 and lane shuffles below.
+template <int E>
+__device__ __forceinline__ void sort_row_warp(const uint32_t *__restrict__ col, uint64_t r0, uint32_t d, uint32_t i,
+                                              uint32_t *__restrict__ out)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t a = e * 32 + lane;
+        v[e] = a < d ? col[r0 + a] : 0xffffffffu;
+    }
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int jr = j >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int e2 = e ^ jr;
+                    if (e2 > e) {
+                        const bool asc = ((e * 32 + lane) & k) == 0;
+                        const uint32_t lo = min(v[e], v[e2]), hi = max(v[e], v[e2]);
+                        v[e] = asc ? lo : hi;
+                        v[e2] = asc ? hi : lo;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t y = __shfl_xor_sync(0xffffffffu, v[e], j);
+                    const bool asc = ((e * 32 + lane) & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    v[e] = (lower == asc) ? min(v[e], y) : max(v[e], y);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t a = e * 32 + lane;
+        if (a < d) reinterpret_cast<uint2 *>(out)[r0 + a] = make_uint2(i, v[e]);
+    }
+}
+
+__global__ void __launch_bounds__(kRowThreads) rows_sort_warp_kernel(const uint32_t *__restrict__ rowoff, int64_t n,
+                                                                     const unsigned long long *__restrict__ d_m,
+                                                                     const uint32_t *__restrict__ mid,
+                                                                     const unsigned long long *__restrict__ d_warp,
+                                                                     const uint32_t *__restrict__ col,
+                                                                     uint32_t *__restrict__ out)
+{
+    const uint64_t m = *d_m, nrows = *d_warp;
+    const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t wstep = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t r = w0; r < nrows; r += wstep) {
+        const uint32_t i = mid[r];
+        const uint64_t r0 = rowoff[i];
+        const uint32_t d = (uint32_t)(row_end(rowoff, n, m, i) - r0);
+        if (d <= 64) sort_row_warp<2>(col, r0, d, i, out);
+        else if (d <= 128) sort_row_warp<4>(col, r0, d, i, out);
+        else if (d <= 256) sort_row_warp<8>(col, r0, d, i, out);
+        else if (d <= 512) sort_row_warp<16>(col, r0, d, i, out);
+        else sort_row_warp<32>(col, r0, d, i, out);
+    }
+}
+
+// one CTA per row of kRowWarp+1..kRowMid partners (listed from the back of
+// `mid`): bitonic sort of the row, padded to a power of two, in shared memory
+__global__ void __launch_bounds__(kRowThreads) rows_sort_mid_kernel(const uint32_t *__restrict__ rowoff, int64_t n,
+                                                                    const unsigned long long *__restrict__ d_m,
+                                                                    const uint32_t *__restrict__ mid,
+                                                                    const unsigned long long *__restrict__ d_mid,
+                                                                    const uint32_t *__restrict__ col,
+                                                                    uint32_t *__restrict__ out)
+{
+    __shared__ uint32_t s[kRowMid];
+    const uint64_t m = *d_m, nmid = *d_mid;
+    for (uint64_t r = blockIdx.x; r < nmid; r += gridDim.x) {
+        const uint32_t i = mid[n - 1 - (int64_t)r];
+        const uint64_t r0 = rowoff[i];
+        const uint32_t d = (uint32_t)(row_end(rowoff, n, m, i) - r0);
+        uint32_t P2 = 64;
+        while (P2 < d) P2 <<= 1;
+        for (uint32_t t = threadIdx.x; t < P2; t += blockDim.x) s[t] = t < d ? col[r0 + t] : 0xffffffffu;
+        __syncthreads();
+        for (uint32_t k = 2; k <= P2; k <<= 1)
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                const uint32_t lj = 31 - __clz(j);
+                for (uint32_t t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
+                    const uint32_t a = ((t >> lj) << (lj + 1)) + (t & (j - 1)), b = a + j;
+                    const uint32_t x = s[a], y = s[b];
+                    const bool asc = (a & k) == 0;
+                    if (asc ? x > y : x < y) {
+                        s[a] = y;
+                        s[b] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        for (uint32_t t = threadIdx.x; t < d; t += blockDim.x)
+            reinterpret_cast<uint2 *>(out)[r0 + t] = make_uint2(i, s[t]);
+        __syncthreads();
     }
 }
 
@@ -422,39 +1146,48 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
     const int cap = (bucket_cap <= 0 || bucket_cap >= n) ? 0 : bucket_cap;
     SqProfScope prof(ctx, SUBQUAD_PROF_BAND);
 
-    // Table of S >= 2n 32-bit slots per band.  Bands are inserted in groups
-    // whose tables fit a share of L2 (the random probes then stay on chip);
-    // the kept keys of all bands are sorted and chunked together.
-    const int log_s = bits_for((uint64_t)(2 * n - 1));
-    const int64_t S = int64_t(1) << log_s;
-    const int nbits = bits_for((uint64_t)(n - 1));
-    const int key_bits = nbits + log_s + bits_for((uint64_t)(bands - 1));
-    if (key_bits > 64) return SUBQUAD_ERR_ARG;
-    const int64_t l2_budget = (int64_t)ctx->tune[SUBQUAD_TUNE_BAND_L2_MB] << 20;
-    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(bands, l2_budget / (S * 4)));
-    const int64_t mg = (int64_t)G * n;       // elements per insert group
-    const int64_t mall = (int64_t)bands * n;  // upper bound of kept keys
+    // Partitions of at most 2^part_log2 records on average (the tuning knob;
+    // default 1024): P = 2^pbits per band.  Bands are partitioned in groups
+    // of at most 2^28 records (bounding the record buffers); kept members,
+    // chunk ids and the chunk list span all bands.
+    const int part_log2 = ctx->tune[SUBQUAD_TUNE_BAND_PART_LOG2];
+    int pbits = 0;
+    while ((n >> pbits) > (int64_t(1) << part_log2) && pbits < kPartMaxBits) ++pbits;
+    const int64_t P = int64_t(1) << pbits;
+    const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(bands, (int64_t(1) << 28) / n));
+    const int64_t mg = (int64_t)G * n;        // records per group
+    const int64_t mall = (int64_t)bands * n;  // upper bound of kept members
+    const int64_t hlen = (int64_t)G * P * ntiles;
     const int nb = bits_for((uint64_t)(n - 1));
     const int64_t final_cap = std::max<int64_t>(pairs_capacity, 1);
+    const size_t tmp_bytes =
+        std::max(std::max(sq_scan_tmp_bytes(hlen), sq_scan_tmp_bytes(mall / 2 + 1)), sq_scan_tmp_bytes(n));
+    // start chunks of the first 4 * bands * n raw pairs, in groups of 32
+    // (later groups, if any, search for their start chunk)
+    const int64_t wmax = mall / 8 + 64;
 
     auto layout = [&](SqArena &a) {
         struct L {
-            uint32_t *chunk_of, *table, *slot_of, *run_start, *flags, *cidx, *heads, *sizes;
-            uint64_t *k0, *k1, *npairs, *p0, *p1;
+            uint32_t *chunk_of, *kept, *rslot, *offs, *heads, *sizes, *cband, *wchunk, *deg, *rowoff, *mid;
+            uint64_t *recs, *fd, *npairs, *p0, *p1;
             void *tmp, *ptmp;
         } l;
         l.chunk_of = a.take<uint32_t>((size_t)n * bands);
-        l.table = a.take<uint32_t>((size_t)G * S);
-        l.slot_of = a.take<uint32_t>(mg);
-        l.k0 = a.take<uint64_t>(mall);
-        l.k1 = a.take<uint64_t>(mall);
-        l.run_start = a.take<uint32_t>(mall);
-        l.flags = a.take<uint32_t>(mall);
-        l.cidx = a.take<uint32_t>(mall);
-        l.heads = a.take<uint32_t>(mall);
-        l.sizes = a.take<uint32_t>(mall);
-        l.npairs = a.take<uint64_t>(mall);
-        l.tmp = a.take<char>(std::max(sq_radix_tmp_bytes(mall), sq_scan_tmp_bytes(mall)));
+        l.kept = a.take<uint32_t>(mall);
+        l.recs = a.take<uint64_t>(mg);
+        l.fd = a.take<uint64_t>(mg);
+        l.rslot = a.take<uint32_t>(mg);
+        l.offs = a.take<uint32_t>(hlen);
+        l.heads = a.take<uint32_t>(mall / 2 + 1);
+        l.sizes = a.take<uint32_t>(mall / 2 + 1);
+        l.cband = a.take<uint32_t>(mall / 2 + 1);
+        l.npairs = a.take<uint64_t>(mall / 2 + 1);
+        l.wchunk = a.take<uint32_t>(wmax);
+        l.deg = async ? nullptr : a.take<uint32_t>(n);
+        l.rowoff = async ? nullptr : a.take<uint32_t>(n);
+        l.mid = async ? nullptr : a.take<uint32_t>(n);
+        l.tmp = a.take<char>(tmp_bytes);
         // the asynchronous form sorts the pairs in its own scratch (sized by the capacity)
         l.p0 = async ? a.take<uint64_t>(final_cap) : nullptr;
         l.p1 = async ? a.take<uint64_t>(final_cap) : nullptr;
@@ -466,68 +1199,53 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
     SQ_TRY(sq_scratch_reserve(ctx, measure.off));
     SqArena arena(ctx->scratch);
     auto L = layout(arena);
-    const size_t tmp_bytes = std::max(sq_radix_tmp_bytes(mall), sq_scan_tmp_bytes(mall));
 
     unsigned long long *d_count = reinterpret_cast<unsigned long long *>(ctx->d_small);
     uint32_t *d_nchunks = reinterpret_cast<uint32_t *>(ctx->d_small + 1);
     uint64_t *d_total = ctx->d_small + 2;
-    unsigned long long *d_kept64 = reinterpret_cast<unsigned long long *>(ctx->d_small + 3);
-    const uint32_t *d_kept = reinterpret_cast<const uint32_t *>(ctx->d_small + 3);  // low word (< 2^32 keys)
+    unsigned long long *d_kept = reinterpret_cast<unsigned long long *>(ctx->d_small + 3);
     unsigned long long *d_clamped = reinterpret_cast<unsigned long long *>(ctx->d_small + 4);
     SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 8 * sizeof(uint64_t), ctx->stream));
     SQ_TRY_CUDA(cudaMemsetAsync(L.chunk_of, 0xff, (size_t)n * bands * sizeof(uint32_t), ctx->stream));
+    if (!async) SQ_TRY_CUDA(cudaMemsetAsync(L.deg, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
 
+    GroupOut go{L.kept, d_kept, d_nchunks, L.heads, L.sizes, L.cband, L.npairs, L.chunk_of, L.rslot};
     for (int band0 = 0; band0 < bands; band0 += G) {
         const int gb = std::min(G, bands - band0);
-        const dim3 grid(sq_grid(ctx, n, 256, (8 + gb - 1) / gb), gb);
-        const dim3 fgrid(sq_grid(ctx, (n + kInsIlp - 1) / kInsIlp, 256, (8 + gb - 1) / gb), gb);
-        SqProfScope prof_ins(ctx, SUBQUAD_PROF_BAND_INSERT);
-        SQ_TRY_CUDA(cudaMemsetAsync(L.table, 0xff, (size_t)gb * S * sizeof(uint32_t), ctx->stream));
-        band_insert_kernel<<<grid, 256, 0, ctx->stream>>>(sig, n, rows, band0, log_s, donor, L.table, L.slot_of,
-                                                          ctx->d_err);
-        SQ_LAUNCH_CHECK();
-        band_filter_kernel<<<fgrid, 256, 0, ctx->stream>>>(L.slot_of, L.table, n, band0, log_s, nbits, L.k0, d_kept64);
+        const int64_t recs = (int64_t)gb * n;
+        const int64_t hl = (int64_t)gb * P * ntiles;
+        const dim3 grid((unsigned)ntiles, gb);
+        {
+            SqProfScope prof_ins(ctx, SUBQUAD_PROF_BAND_PARTITION);
+            part_hist_kernel<<<grid, kPartThreads, P * sizeof(uint32_t), ctx->stream>>>(sig, n, rows, band0, pbits,
+                                                                                      donor, ntiles, L.offs, L.fd);
+            SQ_LAUNCH_CHECK();
+            SQ_TRY(sq_scan_u32(ctx, L.offs, L.offs, hl, nullptr, false, false, nullptr, L.tmp, tmp_bytes));
+            part_scatter_kernel<<<grid, kPartThreads, (kPartThreads / 32) * P * sizeof(uint32_t), ctx->stream>>>(
+                L.fd, n, pbits, ntiles, L.offs, L.recs);
+            SQ_LAUNCH_CHECK();
+        }
+        SqProfScope prof_grp(ctx, SUBQUAD_PROF_BAND_GROUP);
+        SQ_TRY_CUDA(cudaFuncSetAttribute(part_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGrpSmem));
+        part_group_kernel<<<(unsigned)(gb * P), kGrpThreads, kGrpSmem, ctx->stream>>>(
+            L.recs, L.offs, ntiles, recs, pbits, band0, bands, sig, n, rows, donor, cap, go, ctx->d_err);
         SQ_LAUNCH_CHECK();
     }
     {
-        // synchronous form: read the kept count back so the sort and scans
-        // below launch grids for the kept keys (~10% of bands*n)
-        int64_t kept = mall;
-        const uint32_t *dk = d_kept;
-        if (!async) {
-            SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 3, ctx->d_small + 3, sizeof(uint64_t),
-                                        cudaMemcpyDeviceToHost, ctx->stream));
-            SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
-            kept = std::min<int64_t>((int64_t)ctx->h_pinned[3], mall);
-            dk = nullptr;
-        }
-        const unsigned grid = sq_grid(ctx, std::max<int64_t>(kept, 1), 256, 8);
-        bool in_alt = false;
-        {
-            SqProfScope prof_sort(ctx, SUBQUAD_PROF_BAND_SORT);
-            SQ_TRY(sq_radix_sort_u64(ctx, L.k0, L.k1, kept, dk, 0, key_bits, &in_alt, L.tmp, tmp_bytes));
-        }
         SqProfScope prof_emit(ctx, SUBQUAD_PROF_BAND_EMIT);
-        const uint64_t *K = in_alt ? L.k1 : L.k0;
-        band_heads_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, kept, d_kept, L.run_start);
-        SQ_LAUNCH_CHECK();
-        SQ_TRY(sq_scan_u32(ctx, L.run_start, L.run_start, kept, dk, true, true, nullptr, L.tmp, tmp_bytes));
-        band_chunks_kernel<<<grid, 256, 0, ctx->stream>>>(K, nbits, L.run_start, kept, d_kept, cap, log_s, 0, bands,
-                                                          L.chunk_of, L.flags);
-        SQ_LAUNCH_CHECK();
-        SQ_TRY(sq_scan_u32(ctx, L.flags, L.cidx, kept, dk, false, false, d_nchunks, L.tmp, tmp_bytes));
-        band_chunk_list_kernel<<<grid, 256, 0, ctx->stream>>>(L.run_start, L.flags, L.cidx, kept, d_kept, cap,
-                                                              L.heads, L.sizes, L.npairs);
-        SQ_LAUNCH_CHECK();
         // pair counts -> offsets.  Only the first nchunks entries are written;
         // an exclusive prefix at entry c depends on entries < c only, so the
         // unwritten tail never reaches a used offset.
-        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, kept, dk, nullptr, L.tmp, tmp_bytes));
+        const int64_t cmax = mall / 2 + 1;
+        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, cmax, d_nchunks, nullptr, L.tmp, tmp_bytes));
         band_total_kernel<<<1, 1, 0, ctx->stream>>>(L.npairs, L.sizes, d_nchunks, d_total);
         SQ_LAUNCH_CHECK();
+        band_warp_chunk_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(L.npairs, d_nchunks, d_total,
+                                                                                    L.wchunk, wmax);
+        SQ_LAUNCH_CHECK();
         band_emit_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(
-            K, nbits, L.heads, L.sizes, L.npairs, d_nchunks, d_total, log_s, 0, bands, L.chunk_of, pairs_out,
-            pairs_capacity, d_count, ctx->d_err);
+            L.kept, L.heads, L.sizes, L.cband, L.npairs, L.wchunk, wmax, d_nchunks, d_total, bands, L.chunk_of, pairs_out,
+            pairs_capacity, d_count, L.deg, ctx->d_err);
         SQ_LAUNCH_CHECK();
     }
     if (async) {
@@ -546,14 +1264,47 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
         }
         return SUBQUAD_OK;
     }
+    // row offsets of the pairs by first member, and the row classes
+    unsigned long long *d_mid = reinterpret_cast<unsigned long long *>(ctx->d_small + 5);
+    unsigned long long *d_long = reinterpret_cast<unsigned long long *>(ctx->d_small + 6);
+    unsigned long long *d_wrows = reinterpret_cast<unsigned long long *>(ctx->d_small + 7);
+    const unsigned rgrid = sq_grid(ctx, n, kRowThreads, 8);
+    {
+        SqProfScope prof_ps(ctx, SUBQUAD_PROF_BAND_PAIRSORT);
+        SQ_TRY(sq_scan_u32(ctx, L.deg, L.rowoff, n, nullptr, false, false, nullptr, L.tmp, tmp_bytes));
+        rows_classify_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_count, L.mid, d_wrows, d_mid,
+                                                                     d_long);
+        SQ_LAUNCH_CHECK();
+    }
     SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_small, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
     SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->d_small + 6, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                ctx->stream));
     SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
     const int64_t count = (int64_t)ctx->h_pinned[0];
     const uint32_t err = (uint32_t)(ctx->h_pinned[1] & 0xffffffffu);
+    const uint64_t long_rows = ctx->h_pinned[2];
     *num_pairs_out = count;
     if (err) return subquad_check(ctx);
     if (count > pairs_capacity) return SUBQUAD_ERR_CAPACITY;
+    if (count > 1 && long_rows == 0 && count <= 2 * mg && count < (int64_t(1) << 32)) {
+        // the record buffer is free after the emission: it holds the row columns
+        uint32_t *col = reinterpret_cast<uint32_t *>(L.recs);
+        SqProfScope prof_ps(ctx, SUBQUAD_PROF_BAND_PAIRSORT);
+        pairs_scatter_kernel<<<sq_grid(ctx, count, 256, 8), 256, 0, ctx->stream>>>(pairs_out, count, L.rowoff, L.deg,
+                                                                                   col);
+        SQ_LAUNCH_CHECK();
+        rows_sort_small_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_count, col, pairs_out);
+        SQ_LAUNCH_CHECK();
+        rows_sort_warp_kernel<<<(unsigned)ctx->num_sms * 8, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_count,
+                                                                                          L.mid, d_wrows, col,
+                                                                                          pairs_out);
+        SQ_LAUNCH_CHECK();
+        rows_sort_mid_kernel<<<(unsigned)ctx->num_sms * 4, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_count, L.mid,
+                                                                                         d_mid, col, pairs_out);
+        SQ_LAUNCH_CHECK();
+        return SUBQUAD_OK;
+    }
     if (count > 1) {
         SqArena a2(nullptr);
         a2.take<uint64_t>(count);
@@ -579,7 +1330,7 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
 int band_args(int64_t n, int bands, int rows, int64_t pairs_capacity, const uint32_t *sig, const uint32_t *pairs_out)
 {
     if (n < 0 || n >= (int64_t(1) << 31) || bands < 1 || rows < 1 || rows > 8 || bands * rows > 512 ||
-        pairs_capacity < 0)
+        pairs_capacity < 0 || (int64_t)bands * n >= (int64_t)0xffffffffLL)
         return SUBQUAD_ERR_ARG;
     if (n >= 2 && (!sig || (pairs_capacity > 0 && !pairs_out))) return SUBQUAD_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(sig) % 16 || reinterpret_cast<uintptr_t>(pairs_out) % 8) return SUBQUAD_ERR_ARG;

@@ -28,11 +28,11 @@ SUBQUAD_ERR_TIMEOUT = -4
 SUBQUAD_ERR_NOMEM = -5
 SUBQUAD_ERR_INPUT = -6
 
-PROF_NAMES = ["sign", "band", "band_insert", "band_sort", "band_emit", "band_pairsort", "align", "align_bin", "self",
+PROF_NAMES = ["sign", "band", "band_partition", "band_group", "band_emit", "band_pairsort", "align", "align_bin", "self",
               "fuse"]
 
 TUNE_ALIGN_SHAPE = 0
-TUNE_BAND_L2_MB = 1
+TUNE_BAND_PART_LOG2 = 1
 
 _c = ctypes
 _P = _c.c_void_p

@@ -181,6 +181,73 @@ def test_candidates_degenerate_inputs(ctx, torch):
     assert got.shape[0] == 5 * 45
 
 
+@pytest.mark.parametrize("cap", [0, 4])
+def test_candidates_split_partitions(ctx, torch, oracle_mod, cap):
+    """A partition target of 2^16 keys puts all 20k keys of a band in one
+    partition, more distinct keys than one shared-memory table holds: the
+    partition is split into fingerprint sub-ranges; the result is unchanged."""
+    from paper_2602_17330_gb300 import subquad
+
+    rep = synth.donor_repertoire(20_000, seed=4)
+    a, b = synth.hash_coefficients(64, seed=4)
+    _, sig = gpu_sig(ctx, torch, rep, 3, a, b, 16, 4, 16)
+    want = oracle_mod.candidates(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), 16, 4, cap)
+    old = ctx.get_tuning(subquad.TUNE_BAND_PART_LOG2)
+    try:
+        for part_log2 in (16, 6):
+            ctx.set_tuning(subquad.TUNE_BAND_PART_LOG2, part_log2)
+            got = to_np(ctx.band_candidates(sig, rep.n, 16, 4, cap)).view(np.uint32)
+            assert got.shape == want.shape and (got == want).all()
+    finally:
+        ctx.set_tuning(subquad.TUNE_BAND_PART_LOG2, old)
+
+
+def _mix32(h):
+    h &= 0xFFFFFFFF
+    h ^= h >> 16
+    h = (h * 0x7FEB352D) & 0xFFFFFFFF
+    h ^= h >> 15
+    h = (h * 0x846CA68B) & 0xFFFFFFFF
+    h ^= h >> 16
+    return h
+
+
+def test_candidates_fingerprint_clash(ctx, torch, oracle_mod):
+    """White-box: distinct 2-row keys built to share the library's 32-bit key
+    fingerprint (a chain of 32-bit mixes) must stay in separate buckets.  With
+    at most 1024 keys per band (the default partition target) every band is a
+    single partition, so the equal fingerprints meet in one table."""
+    rng = np.random.default_rng(77)
+    n, bands, rows = 1000, 2, 2
+    sig = rng.integers(0, 40, (n, bands * rows)).astype(np.uint32)
+    c0 = 0x9E3779B9 ^ rows
+    groups = []
+    for g in range(6):
+        k0, k1 = 1000 + 2 * g, 5000 + g
+        k0b = 1001 + 2 * g
+        k1b = _mix32(c0 ^ k0) ^ k1 ^ _mix32(c0 ^ k0b)  # same fingerprint, different key
+        groups.append(((k0, k1), (k0b, k1b)))
+    ids = rng.permutation(n)[:6 * 9]
+    for g, ((a0, a1), (b0, b1)) in enumerate(groups):
+        for t, i in enumerate(ids[9 * g:9 * g + 9]):
+            sig[i, 0:2] = (a0, a1) if t < 5 else (b0, b1)
+    for cap in (0, 3):
+        got = gpu_candidates_from_sig(ctx, torch, sig, bands, rows, cap)
+        want = oracle_mod.candidates(sig, bands, rows, cap)
+        assert got.shape == want.shape and (got == want).all()
+
+
+@pytest.mark.parametrize("n,cap", [(20_000, 64), (20_000, 1), (3_000, 1_200), (2_500, 0)])
+def test_candidates_one_giant_bucket(ctx, torch, oracle_mod, n, cap):
+    """Every sequence has the same key in every band: one bucket of n members
+    per band, chunked by rank in id order when it exceeds the cap."""
+    rng = np.random.default_rng(n + cap)
+    sig = np.repeat(rng.integers(0, 1 << 31, (1, 2 * 2)).astype(np.uint32), n, axis=0)
+    got = gpu_candidates_from_sig(ctx, torch, sig, 2, 2, cap)
+    want = oracle_mod.candidates(sig, 2, 2, cap)
+    assert got.shape == want.shape and (got == want).all()
+
+
 # --------------------------------------------------------------------------
 # (a3) alignment
 # --------------------------------------------------------------------------
@@ -276,7 +343,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(ctx, torch, oracle_mod):
     res = autotune.autotune(ctx, packed, pairs, sig=sig, n=rep.n, bands=16, rows=4, bucket_cap=2048, reps=2,
                             use_cache=False)
     assert int(res["choice"][str(subquad.TUNE_ALIGN_SHAPE)]) in (0, 1)
-    assert int(res["choice"][str(subquad.TUNE_BAND_L2_MB)]) in autotune.CANDIDATES[subquad.TUNE_BAND_L2_MB]
+    assert int(res["choice"][str(subquad.TUNE_BAND_PART_LOG2)]) in autotune.CANDIDATES[subquad.TUNE_BAND_PART_LOG2]
     pairs2 = to_np(ctx.band_candidates(sig, rep.n, 16, 4, 2048)).view(np.uint32)
     want = oracle_mod.candidates(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), 16, 4, 2048)
     assert (pairs2 == want).all()
