@@ -249,17 +249,18 @@ __global__ void __launch_bounds__(kPartThreads, 3) part_scatter_kernel(const uin
 constexpr int kGrpThreads = 256;
 constexpr int kGrpSlots = 4096;
 constexpr int kGrpDistinct = 3072;
-constexpr int kGrpFast = 3072;       // partitions up to this size are grouped with records in shared memory
-constexpr int kGrpFastSlots = 4096;  // their table (load <= 3/4)
-constexpr int kGrpVerify = 1024;     // deferred key comparisons held in shared memory
+constexpr int kGrpFast = 2048;       // partitions up to this size are grouped with records in shared memory
+constexpr int kGrpFastSlots = 4096;  // their table (load <= 1/2)
+constexpr int kGrpVerify = 160;      // deferred key comparisons held in shared memory (more: compared at once)
 constexpr uint32_t kFastEmpty = 0xffffffffu;
-// fast-path layout: tab u32[4096] | cnt u32[4096] | rec u64[3072] | slot u16[3072] | keys u16[1536] | vlist uint2[1024]
+// fast-path layout: tab u32[4096] | cnt u32[4096] | rec u64[2048] | slot u16[2048] | keys u16[1024] | vlist uint2[160]
+// (under 56 KB, so four CTAs share an SM)
 constexpr size_t kGrpFastSmem = (size_t)kGrpFastSlots * 8 + (size_t)kGrpFast * 8 + (size_t)kGrpFast * 2 +
                                 (size_t)kGrpFast + (size_t)kGrpVerify * 8;
 // exact-path layout: tab u64[4096] | cnt u32[4096]
 constexpr size_t kGrpExactSmem = (size_t)kGrpSlots * (sizeof(unsigned long long) + sizeof(uint32_t));
 constexpr size_t kGrpSmem = kGrpFastSmem > kGrpExactSmem ? kGrpFastSmem : kGrpExactSmem;
-static_assert(kGrpFast * 4 <= kGrpFastSlots * 3, "a fast-path table is never more than 3/4 full");
+static_assert(kGrpFast * 2 <= kGrpFastSlots, "a fast-path table is never more than half full");
 static_assert(kGrpFast <= 4096, "record indices fit the 12 low bits of a fast-path table entry");
 constexpr int kGrpStack = 48;
 constexpr int kGrpMaxLevel = 20;  // sub-ranges select fingerprint bits 12..31
@@ -299,8 +300,16 @@ struct GroupOut {
     uint32_t *heads, *sizes, *cband;
     uint64_t *npairs;
     uint32_t *chunk_of;
+    uint32_t *kept_mask;  // bit b (b < 32): the sequence is in a chunk of >= 2 members in band b
     uint32_t *rslot;
 };
+
+// Records that member id has chunk `head` in band b.
+__device__ __forceinline__ void set_chunk(const GroupOut &o, uint32_t id, int b, int bands, uint32_t head)
+{
+    o.chunk_of[(int64_t)id * bands + b] = head;
+    if (b < 32) atomicOr(&o.kept_mask[id], 1u << b);
+}
 
 struct GroupShared {
     unsigned long long *tab;  // (fp << 32 | owner id) while inserting; (kept offset << 32 | count) after
@@ -414,7 +423,7 @@ __device__ __forceinline__ void place_any(const GroupShared &g, uint32_t slot, u
     const uint32_t r = atomicAdd(&g.cnt[slot], 1u);
     const uint64_t head = *g.kbase + (e >> 32);
     o.kept_ids[head + r] = id;
-    o.chunk_of[(int64_t)id * bands + b] = (uint32_t)head;
+    set_chunk(o, id, b, bands, (uint32_t)head);
 }
 
 // Members of buckets above the cap, ranked in id order by one warp walking
@@ -449,7 +458,7 @@ __device__ __forceinline__ void place_in_order(const GroupShared &g, const uint6
             const uint32_t r = base + before;
             const uint64_t head = *g.kbase + (g.tab[slot] >> 32);
             o.kept_ids[head + r] = id;
-            o.chunk_of[(int64_t)id * bands + b] = (uint32_t)(head + (r / (uint32_t)cap) * (uint32_t)cap);
+            set_chunk(o, id, b, bands, (uint32_t)(head + (r / (uint32_t)cap) * (uint32_t)cap));
         }
     }
 }
@@ -617,7 +626,7 @@ __device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, ui
         const uint64_t head = kbase + (e >> 16);
         const uint32_t id = (uint32_t)srec[q];
         o.kept_ids[head + r] = id;
-        o.chunk_of[(int64_t)id * bands + b] = (uint32_t)head;
+        set_chunk(o, id, b, bands, (uint32_t)head);
     }
     // members of buckets above the cap: ranks in id order (one warp, records in order)
     if (s_big && warp == 0) {
@@ -640,14 +649,14 @@ __device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, ui
                 const uint64_t head = kbase + (e >> 16);
                 const uint32_t id = (uint32_t)srec[q];
                 o.kept_ids[head + r] = id;
-                o.chunk_of[(int64_t)id * bands + b] = (uint32_t)(head + (r / (uint32_t)cap) * (uint32_t)cap);
+                set_chunk(o, id, b, bands, (uint32_t)(head + (r / (uint32_t)cap) * (uint32_t)cap));
             }
         }
     }
     return true;
 }
 
-__global__ void __launch_bounds__(kGrpThreads, 3) part_group_kernel(
+__global__ void __launch_bounds__(kGrpThreads, 4) part_group_kernel(
     const uint64_t *__restrict__ recs, const uint32_t *__restrict__ offs, int64_t ntiles, int64_t total_recs,
     int pbits, int band0, int bands, const uint32_t *__restrict__ sig, int64_t n, int rows,
     const int32_t *__restrict__ donor, int cap, GroupOut o, uint32_t *err)
@@ -799,7 +808,8 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
     const uint32_t *__restrict__ kept_ids, const uint32_t *__restrict__ heads, const uint32_t *__restrict__ sizes,
     const uint32_t *__restrict__ cband, const uint64_t *__restrict__ poff, const uint32_t *__restrict__ wchunk,
     int64_t wmax, const uint32_t *__restrict__ d_nchunks, const uint64_t *__restrict__ d_total, int bands,
-    const uint32_t *__restrict__ chunk_of, uint32_t *__restrict__ out, int64_t capacity,
+    const uint32_t *__restrict__ chunk_of, const uint32_t *__restrict__ kept_mask, uint32_t *__restrict__ out,
+    int64_t capacity,
     unsigned long long *__restrict__ d_count, uint32_t *__restrict__ deg, uint32_t *err)
 {
     __shared__ unsigned long long s_base;
@@ -844,7 +854,14 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
             owned = true;
             const uint32_t *gi = chunk_of + (int64_t)i * bands;
             const uint32_t *gj = chunk_of + (int64_t)j * bands;
-            for (int bb = 0; bb < b; ++bb) {
+            // earlier bands where both are in some chunk (mask), then their chunk ids
+            uint32_t common = kept_mask[i] & kept_mask[j] & (b >= 32 ? 0xffffffffu : ((1u << b) - 1u));
+            while (common) {
+                const int bb = __ffs(common) - 1;
+                common &= common - 1u;
+                owned = owned && gi[bb] != gj[bb];
+            }
+            for (int bb = 32; bb < b; ++bb) {
                 const uint32_t x = gi[bb], y = gj[bb];
                 owned = owned && !(x == y && x != kNoChunk);
             }
@@ -1169,11 +1186,12 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
 
     auto layout = [&](SqArena &a) {
         struct L {
-            uint32_t *chunk_of, *kept, *rslot, *offs, *heads, *sizes, *cband, *wchunk, *deg, *rowoff, *mid;
+            uint32_t *chunk_of, *kept_mask, *kept, *rslot, *offs, *heads, *sizes, *cband, *wchunk, *deg, *rowoff, *mid;
             uint64_t *recs, *fd, *npairs, *p0, *p1;
             void *tmp, *ptmp;
         } l;
         l.chunk_of = a.take<uint32_t>((size_t)n * bands);
+        l.kept_mask = a.take<uint32_t>(n);
         l.kept = a.take<uint32_t>(mall);
         l.recs = a.take<uint64_t>(mg);
         l.fd = a.take<uint64_t>(mg);
@@ -1207,9 +1225,10 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
     unsigned long long *d_clamped = reinterpret_cast<unsigned long long *>(ctx->d_small + 4);
     SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 8 * sizeof(uint64_t), ctx->stream));
     SQ_TRY_CUDA(cudaMemsetAsync(L.chunk_of, 0xff, (size_t)n * bands * sizeof(uint32_t), ctx->stream));
+    SQ_TRY_CUDA(cudaMemsetAsync(L.kept_mask, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
     if (!async) SQ_TRY_CUDA(cudaMemsetAsync(L.deg, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
 
-    GroupOut go{L.kept, d_kept, d_nchunks, L.heads, L.sizes, L.cband, L.npairs, L.chunk_of, L.rslot};
+    GroupOut go{L.kept, d_kept, d_nchunks, L.heads, L.sizes, L.cband, L.npairs, L.chunk_of, L.kept_mask, L.rslot};
     for (int band0 = 0; band0 < bands; band0 += G) {
         const int gb = std::min(G, bands - band0);
         const int64_t recs = (int64_t)gb * n;
@@ -1244,7 +1263,8 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
                                                                                     L.wchunk, wmax);
         SQ_LAUNCH_CHECK();
         band_emit_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(
-            L.kept, L.heads, L.sizes, L.cband, L.npairs, L.wchunk, wmax, d_nchunks, d_total, bands, L.chunk_of, pairs_out,
+            L.kept, L.heads, L.sizes, L.cband, L.npairs, L.wchunk, wmax, d_nchunks, d_total, bands, L.chunk_of,
+            L.kept_mask, pairs_out,
             pairs_capacity, d_count, L.deg, ctx->d_err);
         SQ_LAUNCH_CHECK();
     }
