@@ -1,7 +1,7 @@
 // Device-wide scan and stable LSD radix sort used by the banding stage.
 //
-// Scan: reduce-then-scan over tiles of 4096 elements (256 threads x 16), with
-// the tile totals scanned by a single CTA.  Radix sort: 8-bit digits; per pass
+// Scan: one pass over tiles of 4096 elements (256 threads x 16) with
+// decoupled look-back between tiles.  Radix sort: 8-bit digits; per pass
 // a digit histogram per tile (warp-aggregated shared-memory counts), a scan of
 // the digit-major histogram, and a stable scatter in which each warp ranks its
 // 256 elements round by round with __match_any_sync so equal digits keep their
@@ -87,70 +87,104 @@ __device__ __forceinline__ void load_tile(const T *in, int64_t base, int64_t cou
     __syncthreads();
 }
 
+// Single-pass scan with decoupled look-back: each CTA takes the next tile
+// index from a counter (so every lower tile belongs to a CTA already
+// running), publishes its tile total, then warp 0 reads the status words of
+// the 32 preceding tiles at a time: a tile that has published its inclusive
+// prefix ends the walk, tiles with only a total are added and the window
+// moves back.  Status word: flag in bits 62..63, value below (values and
+// totals stay under 2^62).  Spins on an unpublished tile are bounded;
+// running out sets the TIMEOUT error bit instead of waiting forever.
+constexpr unsigned long long kScanFlagAgg = 1ull << 62;
+constexpr unsigned long long kScanFlagPre = 2ull << 62;
+constexpr unsigned long long kScanValue = (1ull << 62) - 1ull;
+constexpr long long kScanSpinLimit = 1ll << 22;
+
 template <typename T, bool MAX>
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T *__restrict__ in, int64_t count_max,
-                                                                   const uint32_t *__restrict__ d_count,
-                                                                   T *__restrict__ tile_sums)
+__device__ __forceinline__ T warp_reduce(T v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = op<T, MAX>(v, __shfl_xor_sync(0xffffffffu, v, d));
+    return v;
+}
+
+template <typename T, bool MAX>
+__global__ void __launch_bounds__(kScanThreads) scan_onepass_kernel(const T *__restrict__ in, T *__restrict__ out,
+                                                                    int64_t count_max,
+                                                                    const uint32_t *__restrict__ d_count,
+                                                                    bool inclusive, unsigned long long *status,
+                                                                    uint32_t *tile_counter, T *total_out,
+                                                                    uint32_t *err)
 {
     __shared__ T s_buf[kScanTilePadded];
+    __shared__ uint32_t s_tile;
+    __shared__ T s_prefix;
     const int64_t count = eff_count(count_max, d_count);
-    if ((int64_t)blockIdx.x * kScanTile >= count) {
-        if (threadIdx.x == 0) tile_sums[blockIdx.x] = T(0);
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int64_t base = t * kScanTile;
+    if (base >= count) {
+        if (t == 0 && threadIdx.x == 0 && total_out) *total_out = T(0);  // empty input
         return;
     }
-    T items[kScanItems];
-    load_tile(in, (int64_t)blockIdx.x * kScanTile, count, s_buf, items);
-    T acc = items[0];
-#pragma unroll
-    for (int q = 1; q < kScanItems; ++q) acc = op<T, MAX>(acc, items[q]);
-    T total;
-    block_exclusive<T, MAX>(acc, &total);
-    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
-}
-
-// Single CTA: exclusive scan of the tile totals in place; writes the grand
-// total to *total_out when given.
-template <typename T, bool MAX>
-__global__ void __launch_bounds__(1024) scan_tiles_kernel(T *__restrict__ sums, int64_t ntiles, T *total_out)
-{
-    T carry = T(0);
-    for (int64_t base = 0; base < ntiles; base += blockDim.x) {
-        int64_t g = base + threadIdx.x;
-        T v = g < ntiles ? sums[g] : T(0);
-        T total;
-        T exc = block_exclusive<T, MAX>(v, &total);
-        if (g < ntiles) sums[g] = op<T, MAX>(carry, exc);
-        carry = op<T, MAX>(carry, total);
-    }
-    if (threadIdx.x == 0 && total_out) *total_out = carry;
-}
-
-template <typename T, bool MAX>
-__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const T *__restrict__ in, T *__restrict__ out,
-                                                                  int64_t count_max,
-                                                                  const uint32_t *__restrict__ d_count,
-                                                                  const T *__restrict__ tile_prefix, bool inclusive)
-{
-    __shared__ T s_buf[kScanTilePadded];
-    const int64_t count = eff_count(count_max, d_count);
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    if (base >= count) return;
     T items[kScanItems];
     load_tile(in, base, count, s_buf, items);
     T acc = items[0];
 #pragma unroll
     for (int q = 1; q < kScanItems; ++q) acc = op<T, MAX>(acc, items[q]);
     T total;
-    T run = op<T, MAX>(tile_prefix[blockIdx.x], block_exclusive<T, MAX>(acc, &total));
+    const T excl = block_exclusive<T, MAX>(acc, &total);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        T prefix = T(0);
+        if (t == 0) {
+            if (lane == 0) atomicExch(&status[0], kScanFlagPre | (unsigned long long)total);
+        } else {
+            if (lane == 0) atomicExch(&status[t], kScanFlagAgg | (unsigned long long)total);
+            T run = T(0);
+            int64_t j = t - 1;
+            long long spins = 0;
+            for (;;) {
+                const int64_t idx = j - lane;
+                unsigned long long v = kScanFlagPre;
+                if (idx >= 0) v = *(volatile unsigned long long *)&status[idx];
+                while (__any_sync(0xffffffffu, (v >> 62) == 0)) {
+                    if ((v >> 62) == 0) v = *(volatile unsigned long long *)&status[idx];
+                    if (++spins > kScanSpinLimit) {
+                        if (lane == 0) atomicOr(err, SQ_DEVERR_TIMEOUT);
+                        v = kScanFlagPre;  // give up: the error bit is set
+                    }
+                }
+                const uint32_t pmask = __ballot_sync(0xffffffffu, (v & kScanFlagPre) != 0);
+                const T val = (T)(v & kScanValue);
+                if (pmask) {
+                    const int k = __ffs(pmask) - 1;  // nearest tile with its inclusive prefix
+                    run = op<T, MAX>(run, warp_reduce<T, MAX>(lane <= k ? val : T(0)));
+                    break;
+                }
+                run = op<T, MAX>(run, warp_reduce<T, MAX>(val));
+                j -= 32;
+            }
+            prefix = run;
+            if (lane == 0) atomicExch(&status[t], kScanFlagPre | (unsigned long long)op<T, MAX>(prefix, total));
+        }
+        if (lane == 0) {
+            s_prefix = prefix;
+            if (total_out && base + kScanTile >= count) *total_out = op<T, MAX>(prefix, total);
+        }
+    }
+    __syncthreads();
+    T run = op<T, MAX>(s_prefix, excl);
 #pragma unroll
     for (int q = 0; q < kScanItems; ++q) {
-        T next = op<T, MAX>(run, items[q]);
+        const T next = op<T, MAX>(run, items[q]);
         s_buf[pad(threadIdx.x * kScanItems + q)] = inclusive ? next : run;
         run = next;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < kScanTile; q += kScanThreads) {
-        int64_t g = base + q;
+        const int64_t g = base + q;
         if (g < count) out[g] = s_buf[pad(q)];
     }
 }
@@ -163,15 +197,14 @@ int scan_impl(subquad_ctx *ctx, const T *in, T *out, int64_t count, const uint32
         if (total_out) SQ_TRY_CUDA(cudaMemsetAsync(total_out, 0, sizeof(T), ctx->stream));
         return SUBQUAD_OK;
     }
-    int64_t ntiles = (count + kScanTile - 1) / kScanTile;
-    if ((size_t)ntiles * sizeof(T) > tmp_bytes) return SUBQUAD_ERR_ARG;
-    T *sums = static_cast<T *>(tmp);
-    scan_reduce_kernel<T, MAX><<<(unsigned)ntiles, kScanThreads, 0, ctx->stream>>>(in, count, d_count, sums);
-    SQ_LAUNCH_CHECK();
-    scan_tiles_kernel<T, MAX><<<1, 1024, 0, ctx->stream>>>(sums, ntiles, total_out);
-    SQ_LAUNCH_CHECK();
-    scan_apply_kernel<T, MAX><<<(unsigned)ntiles, kScanThreads, 0, ctx->stream>>>(in, out, count, d_count, sums,
-                                                                                    inclusive);
+    const int64_t ntiles = (count + kScanTile - 1) / kScanTile;
+    const size_t need = (size_t)(ntiles + 1) * sizeof(unsigned long long);
+    if (need > tmp_bytes) return SUBQUAD_ERR_ARG;
+    unsigned long long *status = static_cast<unsigned long long *>(tmp);
+    uint32_t *counter = reinterpret_cast<uint32_t *>(status + ntiles);
+    SQ_TRY_CUDA(cudaMemsetAsync(tmp, 0, need, ctx->stream));
+    scan_onepass_kernel<T, MAX><<<(unsigned)ntiles, kScanThreads, 0, ctx->stream>>>(
+        in, out, count, d_count, inclusive, status, counter, total_out, ctx->d_err);
     SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
 }
@@ -281,13 +314,13 @@ int radix_impl(subquad_ctx *ctx, K *keys, uint32_t *vals, K *keys_alt, uint32_t 
     if (count >= (int64_t(1) << 32)) return SUBQUAD_ERR_ARG;
     const int64_t ntiles = (count + kSortTile - 1) / kSortTile;
     const int64_t hist_len = ntiles * kRadix;
-    const int64_t scan_tiles = (hist_len + kScanTile - 1) / kScanTile;
-    size_t need = (size_t)hist_len * sizeof(uint32_t) * 2 + (size_t)scan_tiles * sizeof(uint32_t) + 1024;
+    const size_t scan_bytes = sq_scan_tmp_bytes(hist_len);
+    size_t need = (size_t)hist_len * sizeof(uint32_t) * 2 + scan_bytes + 1024;
     if (need > tmp_bytes) return SUBQUAD_ERR_ARG;
     SqArena arena(tmp);
     uint32_t *hist = arena.take<uint32_t>(hist_len);
     uint32_t *offs = arena.take<uint32_t>(hist_len);
-    uint32_t *scan_tmp = arena.take<uint32_t>(scan_tiles);
+    char *scan_tmp = arena.take<char>(scan_bytes);
     K *src_k = keys, *dst_k = keys_alt;
     uint32_t *src_v = vals, *dst_v = vals_alt;
     bool in_alt = false;
@@ -296,7 +329,7 @@ int radix_impl(subquad_ctx *ctx, K *keys, uint32_t *vals, K *keys_alt, uint32_t 
                                                                                 ntiles);
         SQ_LAUNCH_CHECK();
         SQ_TRY((scan_impl<uint32_t, false>(ctx, hist, offs, hist_len, nullptr, false, nullptr, scan_tmp,
-                                           (size_t)scan_tiles * sizeof(uint32_t))));
+                                           scan_bytes)));
         radix_scatter_kernel<K, HAS_VAL><<<(unsigned)ntiles, kSortThreads, 0, ctx->stream>>>(
             src_k, src_v, dst_k, dst_v, count, d_count, shift, offs, ntiles);
         SQ_LAUNCH_CHECK();
@@ -488,15 +521,14 @@ int onesweep_u64(subquad_ctx *ctx, uint64_t *keys, uint64_t *keys_alt, int64_t c
 
 size_t sq_scan_tmp_bytes(int64_t count)
 {
-    return (size_t)((count + kScanTile - 1) / kScanTile + 1) * sizeof(uint64_t) + 256;
+    return (size_t)((count + kScanTile - 1) / kScanTile + 2) * sizeof(uint64_t) + 256;
 }
 
 size_t sq_radix_tmp_bytes(int64_t count)
 {
     int64_t ntiles = (count + kSortTile - 1) / kSortTile;
     int64_t hist_len = ntiles * kRadix;
-    int64_t scan_tiles = (hist_len + kScanTile - 1) / kScanTile;
-    const size_t classic = (size_t)hist_len * sizeof(uint32_t) * 2 + (size_t)scan_tiles * sizeof(uint32_t) + 4096;
+    const size_t classic = (size_t)hist_len * sizeof(uint32_t) * 2 + sq_scan_tmp_bytes(hist_len) + 4096;
     const int64_t os_tiles = (count + kOsTile - 1) / kOsTile;
     const size_t onesweep = (size_t)kOsMaxPasses * (os_tiles + 1) * kRadix * sizeof(uint32_t) + 4096;
     return classic > onesweep ? classic : onesweep;
