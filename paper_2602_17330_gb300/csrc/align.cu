@@ -373,30 +373,55 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
         E[p] = 0u;
         HM[p] = neg_o;
     }
-    uint32_t best = 0u;
+    // Two target columns per iteration, the second one row behind the first:
+    // column j's row p and column j+1's row p-1 are independent, so each step
+    // carries two dependency chains (F -> max -> H -> H-o) instead of one.  A
+    // column beyond the target's length scores every cell with the padding
+    // residue and can never raise the maximum.
+    uint32_t bestA = 0u, bestB = 0u;
     TargetStream<WORDS> sP(tP), sQ(tQ);
     const int Lt = max(LtP, LtQ);
-    for (int j = 0; j < Lt; ++j) {
+    for (int j = 0; j < Lt; j += 2) {
+        const uint32_t aP = sP.next(), aQ = sQ.next();
         const uint32_t bP = sP.next(), bQ = sQ.next();
-        const char *colP = s_tab + (j < LtP ? bP : 20u) * (kLanes * 4);
-        const char *colQ = s_tab + (j < LtQ ? bQ : 20u) * (kLanes * 4);
-        uint32_t hm_diag = neg_o, hm_up = neg_o, F = 0u;
+        const char *colAP = s_tab + (j < LtP ? aP : 20u) * (kLanes * 4);
+        const char *colAQ = s_tab + (j < LtQ ? aQ : 20u) * (kLanes * 4);
+        const char *colBP = s_tab + (j + 1 < LtP ? bP : 20u) * (kLanes * 4);
+        const char *colBQ = s_tab + (j + 1 < LtQ ? bQ : 20u) * (kLanes * 4);
+        uint32_t dA = neg_o, upA = neg_o, FA = 0u;
+        uint32_t dB = neg_o, upB = neg_o, FB = 0u;
 #pragma unroll
-        for (int p = 0; p < NQ; ++p) {
-            const uint32_t lo = *reinterpret_cast<const uint32_t *>(colP + qoffP[p]);
-            const uint32_t hi = *reinterpret_cast<const uint32_t *>(colQ + qoffQ[p]);
-            const uint32_t s_o = __byte_perm(lo, hi, 0x5410);
-            const uint32_t e_new = __viaddmax_s16x2_relu(E[p], neg_e, HM[p]);
-            F = __viaddmax_s16x2_relu(F, neg_e, hm_up);
-            const uint32_t h = __viaddmax_s16x2_relu(hm_diag, s_o, __vmaxs2(e_new, F));
-            hm_diag = HM[p];
-            HM[p] = __vadd2(h, neg_o);
-            hm_up = HM[p];
-            E[p] = e_new;
-            best = __vmaxs2(best, h);
+        for (int p = 0; p <= NQ; ++p) {
+            if (p < NQ) {  // column j, row p
+                const uint32_t lo = *reinterpret_cast<const uint32_t *>(colAP + qoffP[p]);
+                const uint32_t hi = *reinterpret_cast<const uint32_t *>(colAQ + qoffQ[p]);
+                const uint32_t s_o = __byte_perm(lo, hi, 0x5410);
+                const uint32_t e_new = __viaddmax_s16x2_relu(E[p], neg_e, HM[p]);
+                FA = __viaddmax_s16x2_relu(FA, neg_e, upA);
+                const uint32_t h = __viaddmax_s16x2_relu(dA, s_o, __vmaxs2(e_new, FA));
+                dA = HM[p];
+                HM[p] = __vadd2(h, neg_o);
+                upA = HM[p];
+                E[p] = e_new;
+                bestA = __vmaxs2(bestA, h);
+            }
+            if (p >= 1) {  // column j + 1, row p - 1
+                const int r = p >= 1 ? p - 1 : 0;
+                const uint32_t lo = *reinterpret_cast<const uint32_t *>(colBP + qoffP[r]);
+                const uint32_t hi = *reinterpret_cast<const uint32_t *>(colBQ + qoffQ[r]);
+                const uint32_t s_o = __byte_perm(lo, hi, 0x5410);
+                const uint32_t e_new = __viaddmax_s16x2_relu(E[r], neg_e, HM[r]);
+                FB = __viaddmax_s16x2_relu(FB, neg_e, upB);
+                const uint32_t h = __viaddmax_s16x2_relu(dB, s_o, __vmaxs2(e_new, FB));
+                dB = HM[r];
+                HM[r] = __vadd2(h, neg_o);
+                upB = HM[r];
+                E[r] = e_new;
+                bestB = __vmaxs2(bestB, h);
+            }
         }
     }
-    return best;
+    return __vmaxs2(bestA, bestB);
 }
 
 template <int WORDS, bool SELF>
@@ -441,6 +466,42 @@ struct BinnedShape {
     static constexpr int blocks = CFG == 0 ? 2 : 3;
 };
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Sequence ids (i, j) of work-list entry q and the pair index it came from.
+template <bool SELF>
+__device__ __forceinline__ uint4 entry_ids(const uint32_t *__restrict__ order, const uint32_t *__restrict__ pairs,
+                                           int64_t q, int64_t m)
+{
+    if (q >= m) return make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t p = order[q];
+    if (SELF) return make_uint4(p, p, p, 1u);
+    const uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
+    return make_uint4(ij.x, ij.y, p, 1u);
+}
+
+template <int WORDS>
+__device__ __forceinline__ void orient(Rec<WORDS> &A, int &La, Rec<WORDS> &B, int &Lb, bool symmetric)
+{
+    constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
+    La = min(A.len(), MAXLEN);
+    Lb = min(B.len(), MAXLEN);
+    if (symmetric && Lb < La) {
+        const Rec<WORDS> T = A;
+        A = B;
+        B = T;
+        const int tl = La;
+        La = Lb;
+        Lb = tl;
+    }
+}
+
 template <int WORDS, bool SELF, int CFG>
 __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::blocks)
     align_binned_kernel(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs,
@@ -457,24 +518,58 @@ __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::b
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // each warp takes 64 consecutive entries of the bin-ordered list: entry
-    // base + lane in the low halves, base + 32 + lane in the high halves
-    for (int64_t base = warp * 64; base < m; base += nwarps * 64) {
-        const int64_t qP = base + lane, qQ = base + 32 + lane;
-        const bool vP = qP < m, vQ = qQ < m;
+    const int64_t stride = nwarps * 64;
+    // Per thread, a double buffer of its two entries' four records in shared
+    // memory (after the table).  Each warp takes 64 consecutive entries of the
+    // bin-ordered list per iteration (entry base + lane in the low halves,
+    // base + 32 + lane in the high halves); the records of iteration k+1 are
+    // copied with cp.async while iteration k computes, and the ids of
+    // iteration k+2 are loaded meanwhile.  A thread reads only what it copied.
+    Rec<WORDS> *buf = reinterpret_cast<Rec<WORDS> *>(s_tab_words + kTabWords) + threadIdx.x * 8;
+    auto issue = [&](int slot, uint4 idP, uint4 idQ) {
+        Rec<WORDS> *d = buf + slot * 4;
+        if (idP.w) {
+#pragma unroll
+            for (int c = 0; c < WORDS / 2; ++c) {
+                cp_async16(reinterpret_cast<char *>(d + 0) + 16 * c, packed + (int64_t)idP.x * WORDS + 2 * c);
+                cp_async16(reinterpret_cast<char *>(d + 1) + 16 * c, packed + (int64_t)idP.y * WORDS + 2 * c);
+            }
+        }
+        if (idQ.w) {
+#pragma unroll
+            for (int c = 0; c < WORDS / 2; ++c) {
+                cp_async16(reinterpret_cast<char *>(d + 2) + 16 * c, packed + (int64_t)idQ.x * WORDS + 2 * c);
+                cp_async16(reinterpret_cast<char *>(d + 3) + 16 * c, packed + (int64_t)idQ.y * WORDS + 2 * c);
+            }
+        }
+        cp_async_commit();
+    };
+    int64_t base = warp * 64;
+    uint4 curP = entry_ids<SELF>(order, pairs, base + lane, m), curQ = entry_ids<SELF>(order, pairs, base + 32 + lane, m);
+    issue(0, curP, curQ);
+    uint4 nxtP = entry_ids<SELF>(order, pairs, base + stride + lane, m);
+    uint4 nxtQ = entry_ids<SELF>(order, pairs, base + stride + 32 + lane, m);
+    for (int k = 0; base < m; ++k, base += stride) {
+        issue((k + 1) & 1, nxtP, nxtQ);  // empty group past the end
+        const uint4 farP = entry_ids<SELF>(order, pairs, base + 2 * stride + lane, m);
+        const uint4 farQ = entry_ids<SELF>(order, pairs, base + 2 * stride + 32 + lane, m);
+        cp_async_wait1();  // this iteration's records have landed
+        const bool vP = curP.w != 0, vQ = curQ.w != 0;
+        const Rec<WORDS> *r = buf + (k & 1) * 4;
         Rec<WORDS> AP, BP, AQ, BQ;
         int LaP = 0, LbP = 0, LaQ = 0, LbQ = 0;
-        uint32_t pP = 0, pQ = 0;
         if (vP) {
-            pP = order[qP];
-            load_oriented<WORDS, SELF>(packed, pairs, pP, symmetric, AP, LaP, BP, LbP);
+            AP = r[0];
+            BP = r[1];
+            orient<WORDS>(AP, LaP, BP, LbP, symmetric);
         } else {
-            AP.w[0] = AP.w[1] = BP.w[0] = BP.w[1] = 0;
-            if (WORDS == 4) AP.w[2 % WORDS] = BP.w[2 % WORDS] = 0;
+#pragma unroll
+            for (int w = 0; w < WORDS; ++w) AP.w[w] = BP.w[w] = 0;
         }
         if (vQ) {
-            pQ = order[qQ];
-            load_oriented<WORDS, SELF>(packed, pairs, pQ, symmetric, AQ, LaQ, BQ, LbQ);
+            AQ = r[2];
+            BQ = r[3];
+            orient<WORDS>(AQ, LaQ, BQ, LbQ, symmetric);
         } else {
             AQ = AP;
             BQ = BP;
@@ -482,23 +577,28 @@ __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::b
             LbQ = LbP;
         }
         const int wmax = __reduce_max_sync(0xffffffffu, max(LaP, LaQ));
-        if (!vP) continue;
-        uint32_t sc;
-        switch ((wmax + 1) >> 1) {
+        if (vP) {
+            uint32_t sc;
+            switch ((wmax + 1) >> 1) {
 #define SQ_CASE(H)                                                                                                 \
     case H:                                                                                                        \
         sc = sw_pair2<WORDS, (H < 1 ? 2 : (2 * H <= MAXLEN ? 2 * H : MAXLEN))>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ,  \
                                                                               s_tab, lane, o, e);                   \
         break;
-            SQ_CASE(0) SQ_CASE(1) SQ_CASE(2) SQ_CASE(3) SQ_CASE(4) SQ_CASE(5) SQ_CASE(6) SQ_CASE(7) SQ_CASE(8)
-            SQ_CASE(9) SQ_CASE(10) SQ_CASE(11) SQ_CASE(12)
+                SQ_CASE(0) SQ_CASE(1) SQ_CASE(2) SQ_CASE(3) SQ_CASE(4) SQ_CASE(5) SQ_CASE(6) SQ_CASE(7) SQ_CASE(8)
+                SQ_CASE(9) SQ_CASE(10) SQ_CASE(11) SQ_CASE(12)
 #undef SQ_CASE
-        default:
-            sc = sw_pair2<WORDS, MAXLEN>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e);
-            break;
+            default:
+                sc = sw_pair2<WORDS, MAXLEN>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e);
+                break;
+            }
+            out[curP.z] = (int32_t)(sc & 0xffffu);
+            if (vQ) out[curQ.z] = (int32_t)(sc >> 16);
         }
-        out[pP] = (int32_t)(sc & 0xffffu);
-        if (vQ) out[pQ] = (int32_t)(sc >> 16);
+        curP = nxtP;
+        curQ = nxtQ;
+        nxtP = farP;
+        nxtQ = farQ;
     }
 }
 
@@ -531,10 +631,10 @@ int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const u
     SQ_LAUNCH_CHECK();
     prof_bin.finish();
     SqProfScope prof(ctx, SELF ? SUBQUAD_PROF_SELF : SUBQUAD_PROF_ALIGN);
-    const size_t smem = sizeof(int32_t) * kTabWords;
 #define SQ_BINNED(W, C)                                                                                            \
     do {                                                                                                           \
         auto k = align_binned_kernel<W, SELF, C>;                                                                  \
+        const size_t smem = sizeof(int32_t) * kTabWords + sizeof(uint64_t) * W * 8 * BinnedShape<C>::threads;      \
         static bool attr_set[64] = {};                                                                             \
         const int dev_slot = ctx->device & 63;                                                                     \
         if (!attr_set[dev_slot]) {                                                                                 \
