@@ -309,7 +309,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "band_pairsort": ("hbm", 16.0 * m, "bytes", "pairs read and written once"),
         "align": ("alu", SW_OPS_PER_CELL * cells, "ops", f"{SW_OPS_PER_CELL} int32 ops per DP cell"),
         "align_bin": ("hbm", 12.0 * m, "bytes", "pair list read, order written"),
-        "self": ("alu", SW_OPS_PER_CELL * self_cells, "ops", f"{SW_OPS_PER_CELL} int32 ops per DP cell"),
+        "self": ("hbm", (cfg.pack_stride + 4.0) * cfg.n, "bytes",
+                 "record read, score written once (diagonal sum: the matrix is diagonally dominant)"),
         "fuse": ("hbm", 16.0 * m + cfg.n * (4.0 * cfg.d + 4 + cfg.pack_stride), "bytes",
                  "16 B per pair + each embedding row, self-score and record once"),
     }
@@ -317,7 +318,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     "band_group": "part_group_kernel",
                     "band_emit": "chunk pair-count scan + band_emit_kernel", "band_pairsort": "pair radix sort",
                     "align": "align_binned_kernel" if cfg.binned else "align_plain_kernel",
-                    "align_bin": "bin_count/offsets/scatter", "self": "self-score alignment kernel",
+                    "align_bin": "bin_count/offsets/scatter", "self": "self_diag_kernel",
                     "fuse": "fuse_forward_kernel"}
     stage_roof = {}
     for name, (bound, amount, unit, what) in algo.items():

@@ -675,6 +675,55 @@ extern "C" int subquad_align_score(subquad_ctx *ctx, const void *packed, int pac
     return launch_align<false>(ctx, packed, pack_stride, pairs, m, gap_open, gap_extend, scores_out);
 }
 
+namespace {
+
+struct DiagScores {
+    int8_t d[20];
+};
+
+// Self-scores when the matrix is diagonally dominant (see subquad_ctx): the
+// sum of the diagonal entries over the residues, one thread per sequence.
+template <int WORDS>
+__global__ void self_diag_kernel(const uint64_t *__restrict__ packed, int64_t n, DiagScores diag,
+                                 int32_t *__restrict__ out)
+{
+    constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
+    __shared__ int32_t s_d[32];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int a = 0; a < 20; ++a) s_d[a] = diag.d[a];
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Rec<WORDS> r;
+        r.load(packed, i);
+        const int L = min(r.len(), MAXLEN);
+        int32_t s = 0;
+#pragma unroll
+        for (int p = 0; p < MAXLEN; ++p) {
+            const uint32_t c = min((uint32_t)(r.w[p / 12] >> (5 * (p % 12))) & 31u, 19u);
+            s += p < L ? s_d[c] : 0;
+        }
+        out[i] = s;
+    }
+}
+
+int launch_self_diag(subquad_ctx *ctx, const void *packed, int pack_stride, int64_t n, int32_t *out)
+{
+    DiagScores d;
+    for (int a = 0; a < 20; ++a) d.d[a] = ctx->h_matrix[21 * a];
+    const unsigned grid = sq_grid(ctx, n, 256, 8);
+    SqProfScope prof(ctx, SUBQUAD_PROF_SELF);
+    if (pack_stride == 16)
+        self_diag_kernel<2><<<grid, 256, 0, ctx->stream>>>(static_cast<const uint64_t *>(packed), n, d, out);
+    else
+        self_diag_kernel<4><<<grid, 256, 0, ctx->stream>>>(static_cast<const uint64_t *>(packed), n, d, out);
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
+}
+
+}  // namespace
+
 extern "C" int subquad_self_scores(subquad_ctx *ctx, const void *packed, int pack_stride, int64_t n, int gap_open,
                                    int gap_extend, int32_t *self_out)
 {
@@ -684,6 +733,7 @@ extern "C" int subquad_self_scores(subquad_ctx *ctx, const void *packed, int pac
     if (n == 0) return SUBQUAD_OK;
     if (!packed || !self_out) return SUBQUAD_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(packed) % 16) return SUBQUAD_ERR_ARG;
+    if (ctx->self_is_diagonal) return launch_self_diag(ctx, packed, pack_stride, n, self_out);
     SQ_TRY(ensure_table(ctx, gap_open));
     return launch_align<true>(ctx, packed, pack_stride, nullptr, n, gap_open, gap_extend, self_out);
 }
@@ -711,6 +761,7 @@ extern "C" int subquad_self_scores_binned(subquad_ctx *ctx, const void *packed, 
     if (n == 0) return SUBQUAD_OK;
     if (!packed || !self_out) return SUBQUAD_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(packed) % 16) return SUBQUAD_ERR_ARG;
+    if (ctx->self_is_diagonal) return launch_self_diag(ctx, packed, pack_stride, n, self_out);
     SQ_TRY(ensure_table(ctx, gap_open));
     return launch_binned<true>(ctx, packed, pack_stride, nullptr, n, gap_open, gap_extend, self_out);
 }

@@ -71,7 +71,7 @@ extern "C" int subquad_create(subquad_ctx **out, int device, void *cuda_stream)
     ctx->device = device;
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     memcpy(ctx->h_matrix, kBlosum62, sizeof(kBlosum62));
-    ctx->matrix_symmetric = true;
+    sq_update_matrix_flags(ctx);
     for (int k = 0; k < SUBQUAD_TUNE_COUNT; ++k) ctx->tune[k] = 0;
     ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE] = 1;
     ctx->tune[SUBQUAD_TUNE_BAND_PART_LOG2] = 10;
@@ -238,12 +238,24 @@ extern "C" int subquad_set_matrix(subquad_ctx *ctx, const int8_t *matrix)
     for (int k = 0; k < 400; ++k)
         if (src[k] < -64 || src[k] > 63) return SUBQUAD_ERR_ARG;
     memcpy(ctx->h_matrix, src, 400);
-    bool sym = true;
-    for (int a = 0; a < 20; ++a)
-        for (int b = 0; b < 20; ++b) sym = sym && ctx->h_matrix[20 * a + b] == ctx->h_matrix[20 * b + a];
-    ctx->matrix_symmetric = sym;
+    sq_update_matrix_flags(ctx);
     ctx->table_gap_open = -1;  // rebuild the device table on next use
     return SUBQUAD_OK;
+}
+
+void sq_update_matrix_flags(subquad_ctx *ctx)
+{
+    const int8_t *m = ctx->h_matrix;
+    bool sym = true, diag = true;
+    for (int a = 0; a < 20; ++a) {
+        diag = diag && m[21 * a] > 0;
+        for (int b = 0; b < 20; ++b) {
+            sym = sym && m[20 * a + b] == m[20 * b + a];
+            diag = diag && 2 * (int)m[20 * a + b] <= (int)m[21 * a] + (int)m[21 * b];
+        }
+    }
+    ctx->matrix_symmetric = sym;
+    ctx->self_is_diagonal = diag;
 }
 
 extern "C" int subquad_pack_stride(int max_len)

@@ -27,6 +27,11 @@ struct subquad_ctx {
     int num_sms = 0;
     int8_t h_matrix[400];   // scoring matrix, row = first sequence's residue
     bool matrix_symmetric = true;
+    // Self-alignment shortcut: true when every diagonal entry is positive and
+    // 2 M(a, b) <= M(a, a) + M(b, b) for all a, b; then (with gap costs >= 0)
+    // the best local alignment of a sequence with itself is the ungapped
+    // identity alignment, whose score is the sum of the diagonal entries.
+    bool self_is_diagonal = true;
     int32_t *d_table = nullptr;  // lane-replicated alignment table (see align.cu)
     int table_gap_open = -1;     // gap-open folded into d_table (-1: not built)
     uint32_t *d_err = nullptr;   // sticky device error word
@@ -167,4 +172,5 @@ size_t sq_radix_tmp_bytes(int64_t count);
 
 // Lane-replicated alignment score table for the context's matrix and gap_open
 // (align.cu); shared by the alignment and the brute-force retrieval kernels.
+void sq_update_matrix_flags(subquad_ctx *ctx);
 int sq_ensure_align_table(subquad_ctx *ctx, int gap_open);

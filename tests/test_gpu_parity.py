@@ -312,6 +312,27 @@ def test_align_custom_matrices(ctx, torch, oracle_mod):
     assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)).all()
 
 
+@pytest.mark.parametrize("binned", [False, True])
+def test_self_scores_both_paths(ctx, torch, oracle_mod, binned):
+    """Self-scores through the diagonal-sum path (BLOSUM62, a diagonally
+    dominant custom matrix) and the dynamic programme (a matrix that is not)."""
+    rep = synth.zipf_repertoire(3000, seed=8, hi=100)
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 32)
+    rng = np.random.default_rng(3)
+    dom = rng.integers(-5, 3, (20, 20)).astype(np.int32)
+    np.fill_diagonal(dom, rng.integers(3, 12, 20))
+    bad = dom.copy()
+    bad[0, 1] = bad[1, 0] = 30
+    try:
+        for M in (None, dom, bad):
+            ctx.set_matrix(None if M is None else M.ravel())
+            for o, e in ((10, 1), (0, 0)):
+                got = to_np(ctx.self_scores(packed, o, e, binned=binned))
+                assert (got == oracle_mod.self_scores(rep.codes, rep.lens, o, e, M)).all()
+    finally:
+        ctx.set_matrix(None)
+
+
 @pytest.mark.parametrize("shape", [0, 1])
 @pytest.mark.parametrize("stride,maker", [(16, "donor"), (32, "zipf")])
 def test_align_binned_launch_shapes(ctx, torch, oracle_mod, shape, stride, maker):

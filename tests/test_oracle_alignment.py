@@ -163,3 +163,22 @@ def test_self_score_is_diagonal_sum_and_bounds(oracle_mod):
     assert (s_ij == s_ji).all()
     assert (s_ij >= 0).all()
     assert (s_ij <= np.minimum(self_sc[pairs[:, 0]], self_sc[pairs[:, 1]])).all()
+
+
+def test_self_score_shortcut_condition(oracle_mod):
+    """The library scores a sequence against itself as the sum of its diagonal
+    entries when every diagonal entry is positive and 2 M(a,b) <= M(a,a) +
+    M(b,b) (then no alignment beats the ungapped identity alignment).
+    BLOSUM62 satisfies it; a matrix that breaks it has self-scores above the
+    diagonal sum, computed here by the full dynamic programme."""
+    M = oracle_mod.blosum62().astype(np.int64)
+    d = np.diag(M)
+    assert (d > 0).all() and (2 * M <= d[:, None] + d[None, :]).all()
+    bad = np.full((20, 20), -4, dtype=np.int32)
+    np.fill_diagonal(bad, 1)
+    bad[0, 1] = bad[1, 0] = 10  # A-C far above the diagonal
+    codes = np.zeros((1, 32), dtype=np.uint8)
+    codes[0, :6] = [0, 1, 0, 1, 0, 1]  # ACACAC
+    lens = np.array([6], dtype=np.uint8)
+    sc = oracle_mod.self_scores(codes, lens, 10, 1, bad)
+    assert sc[0] > 6  # the shifted alignment A-C, C-A, ... wins
