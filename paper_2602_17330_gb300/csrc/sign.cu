@@ -13,16 +13,15 @@ namespace {
 
 constexpr uint32_t kP31 = 0x7fffffffu;
 
-// min(best, (a*x + b) mod P) for x < 20^6, a, b < 2^31.  v = a*x + b < 2^57,
-// r = (v mod 2^31) + (v >> 31) < P + 2^26 < 2P, so one conditional subtract
-// finishes the reduction; min3 over (r, r - P) picks it (r - P wraps above r
-// when r < P).
-__device__ __forceinline__ uint32_t hash_min(uint32_t best, uint32_t a, uint32_t b, uint32_t x)
+// min(best, (a*x + b) mod P) for x < 20^6, given a2 = 2a and b2 = 2b with
+// a, b < P.  w = a2*x + b2 = 2v for v = a*x + b < 2^57, so the high word of w
+// is v >> 31 and the low word shifted right by one is v mod 2^31; their sum
+// r < P + 2^26 < 2P, so one conditional subtract finishes the reduction, and
+// min3 over (r, r - P) picks it (r - P wraps above r when r < P).
+__device__ __forceinline__ uint32_t hash_min(uint32_t best, uint32_t a2, uint32_t b2, uint32_t x)
 {
-    uint64_t v = (uint64_t)a * x + b;
-    uint32_t lo = (uint32_t)v & kP31;
-    uint32_t hi = (uint32_t)(v >> 31);
-    uint32_t r = lo + hi;
+    const uint64_t w = (uint64_t)a2 * x + b2;
+    const uint32_t r = (uint32_t)(w >> 32) + ((uint32_t)w >> 1);
     return min(best, min(r, r - kP31));
 }
 
@@ -82,7 +81,8 @@ __global__ void __launch_bounds__(256) sign_kernel(const uint64_t *__restrict__ 
 {
     extern __shared__ uint2 s_ab[];
     const int H = bands * rows;
-    for (int t = threadIdx.x; t < H; t += blockDim.x) s_ab[t] = make_uint2(a[t], b[t]);
+    // coefficients reduced mod P (same hash) and doubled for hash_min
+    for (int t = threadIdx.x; t < H; t += blockDim.x) s_ab[t] = make_uint2(2u * (a[t] % kP31), 2u * (b[t] % kP31));
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // the loop trip count is uniform per warp so the warp-level dispatch is safe
