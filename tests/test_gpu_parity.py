@@ -237,6 +237,29 @@ def test_candidates_fingerprint_clash(ctx, torch, oracle_mod):
         assert got.shape == want.shape and (got == want).all()
 
 
+@pytest.mark.parametrize("cap", [0, 3])
+def test_candidates_every_key_twice(ctx, torch, oracle_mod, cap):
+    """Every key occurs exactly twice, so none is filtered out; with a
+    partition target of 2^16 records a band is one partition with 10,000
+    distinct keys, more than one shared-memory table holds: the exact path
+    splits it into fingerprint sub-ranges."""
+    from paper_2602_17330_gb300 import subquad
+
+    rng = np.random.default_rng(21)
+    n, bands, rows = 20_000, 3, 4
+    half = rng.integers(0, 1 << 31, (n // 2, bands * rows)).astype(np.uint32)
+    sig = np.concatenate([half, half])[rng.permutation(n)]
+    want = oracle_mod.candidates(sig, bands, rows, cap)
+    old = ctx.get_tuning(subquad.TUNE_BAND_PART_LOG2)
+    try:
+        for part_log2 in (16, 10, 6):
+            ctx.set_tuning(subquad.TUNE_BAND_PART_LOG2, part_log2)
+            got = gpu_candidates_from_sig(ctx, torch, sig, bands, rows, cap)
+            assert got.shape == want.shape and (got == want).all()
+    finally:
+        ctx.set_tuning(subquad.TUNE_BAND_PART_LOG2, old)
+
+
 @pytest.mark.parametrize("n,cap", [(20_000, 64), (20_000, 1), (3_000, 1_200), (2_500, 0)])
 def test_candidates_one_giant_bucket(ctx, torch, oracle_mod, n, cap):
     """Every sequence has the same key in every band: one bucket of n members
