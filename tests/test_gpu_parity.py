@@ -239,10 +239,10 @@ def test_candidates_fingerprint_clash(ctx, torch, oracle_mod):
 
 @pytest.mark.parametrize("cap", [0, 3])
 def test_candidates_every_key_twice(ctx, torch, oracle_mod, cap):
-    """Every key occurs exactly twice, so none is filtered out; with a
-    partition target of 2^16 records a band is one partition with 10,000
-    distinct keys, more than one shared-memory table holds: the exact path
-    splits it into fingerprint sub-ranges."""
+    """Every key occurs exactly twice (every key is kept); with a partition
+    target of 2^16 keys a band is one partition with 10,000 distinct keys,
+    more than one shared-memory table holds: the exact path splits it into
+    fingerprint sub-ranges."""
     from paper_2602_17330_gb300 import subquad
 
     rng = np.random.default_rng(21)
