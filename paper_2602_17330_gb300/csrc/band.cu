@@ -15,8 +15,11 @@
 //     indices, finds their chunks, decodes (u, v) and keeps pair (i, j) only
 //     if no earlier band already puts i and j in one chunk (first-band
 //     ownership), so every pair of C is emitted once;
-//  4. read back |C| (the synchronous form's only host synchronisation), then
-//     radix-sort the pairs into lexicographic order.
+//  4. lexicographic order: degrees counted by the emitter give row offsets,
+//     the second members are scattered into their rows and every row is
+//     sorted (registers, a warp, a CTA, or in place in global memory);
+//     the synchronous form then reads back |C| (its only host
+//     synchronisation).
 // Counts produced on the device (chunks, raw pairs) are consumed on the
 // device: the kernels after them are sized for the upper bound and read the
 // actual count.
@@ -874,12 +877,12 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
     }
 }
 
-// Lexicographic order of the emitted pairs (synchronous form): a counting
-// pass by first member i (degrees counted by the emitter, scanned into row
-// offsets), a scatter of the second members into their rows, and a sort of
-// every row: in registers for rows of at most kRowSmall partners, in shared
-// memory (one CTA per row) up to kRowMid.  Longer rows (possible only with
-// very large buckets) take the global radix sort instead.
+// Lexicographic order of the emitted pairs: a counting pass by first member
+// i (degrees counted by the emitter, scanned into row offsets), a scatter of
+// the second members into their rows, and a sort of every row: in registers
+// for rows of at most kRowSmall partners, by one warp up to kRowWarp, by one
+// CTA in shared memory up to kRowMid, in place in global memory beyond.
+// Every count stays on the device.
 constexpr int kRowSmall = 32;
 constexpr int kRowWarp = 1024;  // rows up to this size: one warp, registers
 constexpr int kRowMid = 8192;   // rows up to this size: one CTA, shared memory
@@ -891,12 +894,13 @@ __device__ __forceinline__ uint64_t row_end(const uint32_t *rowoff, int64_t n, u
 }
 
 // rows of more than kRowSmall partners: those up to kRowWarp listed from the
-// front of `mid`, those up to kRowMid from the back, the longer ones counted
+// front of `mid`, those up to kRowMid from the back, the longer ones in `lng`
 __global__ void __launch_bounds__(kRowThreads) rows_classify_kernel(const uint32_t *__restrict__ rowoff, int64_t n,
                                                                     const unsigned long long *__restrict__ d_m,
                                                                     uint32_t *__restrict__ mid,
                                                                     unsigned long long *__restrict__ d_warp,
                                                                     unsigned long long *__restrict__ d_cta,
+                                                                    uint32_t *__restrict__ lng,
                                                                     unsigned long long *__restrict__ d_long)
 {
     __shared__ unsigned long long s_base;
@@ -906,7 +910,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_classify_kernel(const uint32
         const int64_t i = b0 + threadIdx.x;
         uint64_t d = 0;
         if (i < n) d = row_end(rowoff, n, m, i) - rowoff[i];
-        if (d > (uint64_t)kRowMid) atomicAdd(d_long, 1ull);
+        if (d > (uint64_t)kRowMid) lng[atomicAdd(d_long, 1ull)] = (uint32_t)i;
         const bool is_warp = d > (uint64_t)kRowSmall && d <= (uint64_t)kRowWarp;
         const bool is_cta = d > (uint64_t)kRowWarp && d <= (uint64_t)kRowMid;
         const unsigned long long pw = block_append(is_warp, d_warp, &s_base, s_warp);
@@ -916,9 +920,11 @@ __global__ void __launch_bounds__(kRowThreads) rows_classify_kernel(const uint32
     }
 }
 
-__global__ void pairs_scatter_kernel(const uint32_t *__restrict__ pairs, int64_t m, const uint32_t *__restrict__ rowoff,
-                                     uint32_t *__restrict__ fill, uint32_t *__restrict__ col)
+__global__ void pairs_scatter_kernel(const uint32_t *__restrict__ pairs, const unsigned long long *__restrict__ d_m,
+                                     const uint32_t *__restrict__ rowoff, uint32_t *__restrict__ fill,
+                                     uint32_t *__restrict__ col)
 {
+    const int64_t m = (int64_t)*d_m;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
         const uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
         col[rowoff[ij.x] + atomicSub(&fill[ij.x], 1u) - 1u] = ij.y;
@@ -1097,51 +1103,56 @@ __global__ void band_total_kernel(const uint64_t *__restrict__ poff, const uint3
     *d_total = total;
 }
 
-__device__ __forceinline__ int64_t count_or(int64_t m, const unsigned long long *d_m)
+// One CTA per row of more than kRowMid partners, sorted in place in global
+// memory by a bitonic network whose comparators all put the smaller value at
+// the lower index (a "flip" step, then half-cleaners), so positions past the
+// row's end act as +infinity and are never touched.
+__global__ void __launch_bounds__(1024) rows_sort_long_kernel(const uint32_t *__restrict__ rowoff, int64_t n,
+                                                              const unsigned long long *__restrict__ d_m,
+                                                              const uint32_t *__restrict__ lng,
+                                                              const unsigned long long *__restrict__ d_long,
+                                                              uint32_t *__restrict__ col, uint32_t *__restrict__ out)
 {
-    if (!d_m) return m;
-    const int64_t c = (int64_t)*d_m;
-    return c < m ? c : m;
-}
-
-__global__ void pairs_to_keys_kernel(const uint32_t *__restrict__ pairs, int64_t m_max,
-                                     const unsigned long long *__restrict__ d_m, int nbits, uint64_t *__restrict__ keys)
-{
-    const int64_t m = count_or(m_max, d_m);
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
-        uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
-        keys[p] = ((uint64_t)ij.x << nbits) | ij.y;
+    const uint64_t m = *d_m, nl = *d_long;
+    for (uint64_t r = blockIdx.x; r < nl; r += gridDim.x) {
+        const uint32_t i = lng[r];
+        const uint64_t r0 = rowoff[i];
+        const uint64_t d = row_end(rowoff, n, m, i) - r0;
+        uint32_t *v = col + r0;
+        uint64_t P2 = 2;
+        while (P2 < d) P2 <<= 1;
+        for (uint64_t k = 2; k <= P2; k <<= 1) {
+            for (uint64_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint64_t t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
+                    const uint64_t a = (t / j) * 2 * j + (t % j);
+                    const uint64_t b = j == (k >> 1) ? (a | (k - 1)) - (a & (k - 1)) : a + j;  // flip, then half-cleaners
+                    if (b < d) {
+                        const uint32_t x = v[a], y = v[b];
+                        if (x > y) {
+                            v[a] = y;
+                            v[b] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint64_t t = threadIdx.x; t < d; t += blockDim.x)
+            reinterpret_cast<uint2 *>(out)[r0 + t] = make_uint2(i, v[t]);
+        __syncthreads();
     }
 }
 
-__global__ void keys_to_pairs_kernel(const uint64_t *__restrict__ keys, int64_t m_max,
-                                     const unsigned long long *__restrict__ d_m, int nbits,
-                                     uint32_t *__restrict__ pairs)
-{
-    const int64_t m = count_or(m_max, d_m);
-    const uint64_t mask = (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1ull);
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t k = keys[p];
-        reinterpret_cast<uint2 *>(pairs)[p] = make_uint2((uint32_t)(k >> nbits), (uint32_t)(k & mask));
-    }
-}
-
-// Async finish: publish |C|, flag an overflow, clamp the count used below.
+// Finish: publish |C| (asynchronous form: with the sticky CAPACITY bit on an
+// overflow), clamp the count of written pairs used by the sort.
 __global__ void band_finish_kernel(const unsigned long long *__restrict__ d_count, int64_t capacity,
                                    unsigned long long *__restrict__ d_out, unsigned long long *__restrict__ d_clamped,
                                    uint32_t *err)
 {
     const unsigned long long c = *d_count;
     if (d_out) *d_out = c;
-    if (c > (unsigned long long)capacity) atomicOr(err, SQ_DEVERR_CAPACITY);
+    if (d_out && c > (unsigned long long)capacity) atomicOr(err, SQ_DEVERR_CAPACITY);
     *d_clamped = c < (unsigned long long)capacity ? c : (unsigned long long)capacity;
-}
-
-int bits_for(uint64_t v)  // number of bits needed to hold values 0..v
-{
-    int b = 1;
-    while (b < 64 && (v >> b) != 0) ++b;
-    return b;
 }
 
 }  // namespace
@@ -1176,7 +1187,6 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
     const int64_t mg = (int64_t)G * n;        // records per group
     const int64_t mall = (int64_t)bands * n;  // upper bound of kept members
     const int64_t hlen = (int64_t)G * P * ntiles;
-    const int nb = bits_for((uint64_t)(n - 1));
     const int64_t final_cap = std::max<int64_t>(pairs_capacity, 1);
     const size_t tmp_bytes =
         std::max(std::max(sq_scan_tmp_bytes(hlen), sq_scan_tmp_bytes(mall / 2 + 1)), sq_scan_tmp_bytes(n));
@@ -1187,8 +1197,9 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
     auto layout = [&](SqArena &a) {
         struct L {
             uint32_t *chunk_of, *kept_mask, *kept, *rslot, *offs, *heads, *sizes, *cband, *wchunk, *deg, *rowoff, *mid;
-            uint64_t *recs, *fd, *npairs, *p0, *p1;
-            void *tmp, *ptmp;
+            uint32_t *lng, *col;
+            uint64_t *recs, *fd, *npairs;
+            void *tmp;
         } l;
         l.chunk_of = a.take<uint32_t>((size_t)n * bands);
         l.kept_mask = a.take<uint32_t>(n);
@@ -1202,14 +1213,13 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
         l.cband = a.take<uint32_t>(mall / 2 + 1);
         l.npairs = a.take<uint64_t>(mall / 2 + 1);
         l.wchunk = a.take<uint32_t>(wmax);
-        l.deg = async ? nullptr : a.take<uint32_t>(n);
-        l.rowoff = async ? nullptr : a.take<uint32_t>(n);
-        l.mid = async ? nullptr : a.take<uint32_t>(n);
+        l.deg = a.take<uint32_t>(n);
+        l.rowoff = a.take<uint32_t>(n);
+        l.mid = a.take<uint32_t>(n);
+        l.lng = a.take<uint32_t>((final_cap >> 13) + 1);
+        // row columns: in the record buffer (free after the emission) when it is large enough
+        l.col = final_cap <= 2 * mg ? reinterpret_cast<uint32_t *>(l.recs) : a.take<uint32_t>(final_cap);
         l.tmp = a.take<char>(tmp_bytes);
-        // the asynchronous form sorts the pairs in its own scratch (sized by the capacity)
-        l.p0 = async ? a.take<uint64_t>(final_cap) : nullptr;
-        l.p1 = async ? a.take<uint64_t>(final_cap) : nullptr;
-        l.ptmp = async ? a.take<char>(sq_radix_tmp_bytes(final_cap)) : nullptr;
         return l;
     };
     SqArena measure(nullptr);
@@ -1226,7 +1236,7 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
     SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 8 * sizeof(uint64_t), ctx->stream));
     SQ_TRY_CUDA(cudaMemsetAsync(L.chunk_of, 0xff, (size_t)n * bands * sizeof(uint32_t), ctx->stream));
     SQ_TRY_CUDA(cudaMemsetAsync(L.kept_mask, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
-    if (!async) SQ_TRY_CUDA(cudaMemsetAsync(L.deg, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
+    SQ_TRY_CUDA(cudaMemsetAsync(L.deg, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
 
     GroupOut go{L.kept, d_kept, d_nchunks, L.heads, L.sizes, L.cband, L.npairs, L.chunk_of, L.kept_mask, L.rslot};
     for (int band0 = 0; band0 < bands; band0 += G) {
@@ -1268,89 +1278,56 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
             pairs_capacity, d_count, L.deg, ctx->d_err);
         SQ_LAUNCH_CHECK();
     }
-    if (async) {
-        band_finish_kernel<<<1, 1, 0, ctx->stream>>>(d_count, pairs_capacity, d_num_pairs, d_clamped, ctx->d_err);
-        SQ_LAUNCH_CHECK();
-        if (pairs_capacity > 1) {
-            const unsigned grid = sq_grid(ctx, pairs_capacity, 256, 8);
-            pairs_to_keys_kernel<<<grid, 256, 0, ctx->stream>>>(pairs_out, pairs_capacity, d_clamped, nb, L.p0);
-            SQ_LAUNCH_CHECK();
-            bool in_alt = false;
-            SQ_TRY(sq_radix_sort_u64(ctx, L.p0, L.p1, pairs_capacity, reinterpret_cast<const uint32_t *>(d_clamped),
-                                     0, 2 * nb, &in_alt, L.ptmp, sq_radix_tmp_bytes(final_cap)));
-            keys_to_pairs_kernel<<<grid, 256, 0, ctx->stream>>>(in_alt ? L.p1 : L.p0, pairs_capacity, d_clamped, nb,
-                                                                pairs_out);
-            SQ_LAUNCH_CHECK();
-        }
-        return SUBQUAD_OK;
-    }
-    // row offsets of the pairs by first member, and the row classes
-    unsigned long long *d_mid = reinterpret_cast<unsigned long long *>(ctx->d_small + 5);
-    unsigned long long *d_long = reinterpret_cast<unsigned long long *>(ctx->d_small + 6);
-    unsigned long long *d_wrows = reinterpret_cast<unsigned long long *>(ctx->d_small + 7);
-    const unsigned rgrid = sq_grid(ctx, n, kRowThreads, 8);
+    // |C| published (asynchronous form), an overflow flagged, the count of
+    // written pairs clamped to the capacity for the sort below
+    band_finish_kernel<<<1, 1, 0, ctx->stream>>>(d_count, pairs_capacity, async ? d_num_pairs : nullptr, d_clamped,
+                                                 ctx->d_err);
+    SQ_LAUNCH_CHECK();
     {
+        // lexicographic order: row offsets by first member, row classes, the
+        // second members scattered into their rows, every row sorted
         SqProfScope prof_ps(ctx, SUBQUAD_PROF_BAND_PAIRSORT);
+        unsigned long long *d_mid = reinterpret_cast<unsigned long long *>(ctx->d_small + 5);
+        unsigned long long *d_long = reinterpret_cast<unsigned long long *>(ctx->d_small + 6);
+        unsigned long long *d_wrows = reinterpret_cast<unsigned long long *>(ctx->d_small + 7);
+        const unsigned rgrid = sq_grid(ctx, n, kRowThreads, 8);
         SQ_TRY(sq_scan_u32(ctx, L.deg, L.rowoff, n, nullptr, false, false, nullptr, L.tmp, tmp_bytes));
-        rows_classify_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_count, L.mid, d_wrows, d_mid,
-                                                                     d_long);
+        rows_classify_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_clamped, L.mid, d_wrows, d_mid,
+                                                                     L.lng, d_long);
+        SQ_LAUNCH_CHECK();
+        pairs_scatter_kernel<<<sq_grid(ctx, final_cap, 256, 8), 256, 0, ctx->stream>>>(pairs_out, d_clamped,
+                                                                                      L.rowoff, L.deg, L.col);
+        SQ_LAUNCH_CHECK();
+        rows_sort_small_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_clamped, L.col, pairs_out);
+        SQ_LAUNCH_CHECK();
+        rows_sort_warp_kernel<<<(unsigned)ctx->num_sms * 8, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_clamped,
+                                                                                          L.mid, d_wrows, L.col,
+                                                                                          pairs_out);
+        SQ_LAUNCH_CHECK();
+        rows_sort_mid_kernel<<<(unsigned)ctx->num_sms * 4, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_clamped,
+                                                                                         L.mid, d_mid, L.col,
+                                                                                         pairs_out);
+        SQ_LAUNCH_CHECK();
+        rows_sort_long_kernel<<<(unsigned)ctx->num_sms, 1024, 0, ctx->stream>>>(L.rowoff, n, d_clamped, L.lng, d_long,
+                                                                               L.col, pairs_out);
         SQ_LAUNCH_CHECK();
     }
+    if (async) return SUBQUAD_OK;
     SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_small, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
     SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
-    SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->d_small + 6, sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                                ctx->stream));
     SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
     const int64_t count = (int64_t)ctx->h_pinned[0];
     const uint32_t err = (uint32_t)(ctx->h_pinned[1] & 0xffffffffu);
-    const uint64_t long_rows = ctx->h_pinned[2];
     *num_pairs_out = count;
     if (err) return subquad_check(ctx);
-    if (count > pairs_capacity) return SUBQUAD_ERR_CAPACITY;
-    if (count > 1 && long_rows == 0 && count <= 2 * mg && count < (int64_t(1) << 32)) {
-        // the record buffer is free after the emission: it holds the row columns
-        uint32_t *col = reinterpret_cast<uint32_t *>(L.recs);
-        SqProfScope prof_ps(ctx, SUBQUAD_PROF_BAND_PAIRSORT);
-        pairs_scatter_kernel<<<sq_grid(ctx, count, 256, 8), 256, 0, ctx->stream>>>(pairs_out, count, L.rowoff, L.deg,
-                                                                                   col);
-        SQ_LAUNCH_CHECK();
-        rows_sort_small_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_count, col, pairs_out);
-        SQ_LAUNCH_CHECK();
-        rows_sort_warp_kernel<<<(unsigned)ctx->num_sms * 8, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_count,
-                                                                                          L.mid, d_wrows, col,
-                                                                                          pairs_out);
-        SQ_LAUNCH_CHECK();
-        rows_sort_mid_kernel<<<(unsigned)ctx->num_sms * 4, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_count, L.mid,
-                                                                                         d_mid, col, pairs_out);
-        SQ_LAUNCH_CHECK();
-        return SUBQUAD_OK;
-    }
-    if (count > 1) {
-        SqArena a2(nullptr);
-        a2.take<uint64_t>(count);
-        a2.take<uint64_t>(count);
-        a2.take<char>(sq_radix_tmp_bytes(count));
-        SQ_TRY(sq_scratch_reserve(ctx, a2.off));
-        SqArena a3(ctx->scratch);
-        uint64_t *k0 = a3.take<uint64_t>(count);
-        uint64_t *k1 = a3.take<uint64_t>(count);
-        void *tmp = a3.take<char>(sq_radix_tmp_bytes(count));
-        const unsigned grid = sq_grid(ctx, count, 256, 8);
-        SqProfScope prof_ps(ctx, SUBQUAD_PROF_BAND_PAIRSORT);
-        pairs_to_keys_kernel<<<grid, 256, 0, ctx->stream>>>(pairs_out, count, nullptr, nb, k0);
-        SQ_LAUNCH_CHECK();
-        bool in_alt = false;
-        SQ_TRY(sq_radix_sort_u64(ctx, k0, k1, count, nullptr, 0, 2 * nb, &in_alt, tmp, sq_radix_tmp_bytes(count)));
-        keys_to_pairs_kernel<<<grid, 256, 0, ctx->stream>>>(in_alt ? k1 : k0, count, nullptr, nb, pairs_out);
-        SQ_LAUNCH_CHECK();
-    }
+    if (count > pairs_capacity) return SUBQUAD_ERR_CAPACITY;  // the status reports it (no sticky bit)
     return SUBQUAD_OK;
 }
 
 int band_args(int64_t n, int bands, int rows, int64_t pairs_capacity, const uint32_t *sig, const uint32_t *pairs_out)
 {
     if (n < 0 || n >= (int64_t(1) << 31) || bands < 1 || rows < 1 || rows > 8 || bands * rows > 512 ||
-        pairs_capacity < 0 || (int64_t)bands * n >= (int64_t)0xffffffffLL)
+        pairs_capacity < 0 || pairs_capacity >= (int64_t)0xffffffffLL || (int64_t)bands * n >= (int64_t)0xffffffffLL)
         return SUBQUAD_ERR_ARG;
     if (n >= 2 && (!sig || (pairs_capacity > 0 && !pairs_out))) return SUBQUAD_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(sig) % 16 || reinterpret_cast<uintptr_t>(pairs_out) % 8) return SUBQUAD_ERR_ARG;

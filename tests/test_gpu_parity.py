@@ -260,6 +260,22 @@ def test_candidates_every_key_twice(ctx, torch, oracle_mod, cap):
         ctx.set_tuning(subquad.TUNE_BAND_PART_LOG2, old)
 
 
+def test_candidates_row_longer_than_shared_memory(ctx, torch, oracle_mod):
+    """Sequence 0 shares a chunk with 19 different sequences in each of 512
+    one-row bands: its row has 9,728 partners, more than one CTA sorts in
+    shared memory, so the row is sorted in place in global memory."""
+    rng = np.random.default_rng(33)
+    bands, rows, per = 512, 1, 19
+    n = 1 + bands * per
+    sig = rng.integers(0, 1 << 31, (n, bands)).astype(np.uint32)
+    for b in range(bands):
+        sig[1 + per * b: 1 + per * (b + 1), b] = sig[0, b]
+    got = gpu_candidates_from_sig(ctx, torch, sig, bands, rows, per + 1)
+    want = oracle_mod.candidates(sig, bands, rows, per + 1)
+    assert (want[:, 0] == 0).sum() == bands * per
+    assert got.shape == want.shape and (got == want).all()
+
+
 @pytest.mark.parametrize("n,cap", [(20_000, 64), (20_000, 1), (3_000, 1_200), (2_500, 0)])
 def test_candidates_one_giant_bucket(ctx, torch, oracle_mod, n, cap):
     """Every sequence has the same key in every band: one bucket of n members
