@@ -52,6 +52,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shapes")
+    p.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     p.add_argument("--cpu-sample-n", type=int, default=500_000, help="oracle sample for the cpu_baseline key")
     p.add_argument("--ref-sample-n", type=int, default=200_000, help="oracle sample per step of --impl reference")
     return p.parse_args()
@@ -202,11 +203,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     stream = torch.cuda.Stream(device=dev)
     ctx = subquad.Context(local_rank, stream=stream)
-    pipe = pipeline.Pipeline(ctx, cfg)
+    pipe = pipeline.Pipeline(ctx, cfg)  # synchronous form: e2e and the plain/batched comparison
+    # the timed step: every count stays on the device, no host synchronisation
+    step_pipe = pipeline.BatchedPipeline(ctx, cfg, cfg.n, capacity=8 * cfg.n)
     with torch.cuda.stream(stream):
         x = pipe.upload(rep, a, b, emb, params)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
         for _ in range(max(args.warmup, 1)):
+            step_pipe.step(x)
             out = pipe.forward(x)
     stream.synchronize()
     ctx.check()
@@ -219,9 +223,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                        rows=cfg.rows, bucket_cap=cfg.bucket_cap, gap_open=cfg.gap_open,
                                        gap_extend=cfg.gap_extend, reps=3, use_cache=False)
         out = pipe.forward(x)
+        step_pipe.step(x)
     stream.synchronize()
+    ctx.check()
     pairs_np = out["pairs"].cpu().numpy().view(np.uint32)
     m = int(pairs_np.shape[0])
+    if int(step_pipe.num_pairs.item()) != m:
+        raise RuntimeError("the device-count step and the synchronous step disagree on |C|")
     cells = pipeline.cells_of(rep.lens, pairs_np)
 
     stage_names = ["pack", "sign", "band", "self", "align", "fuse"]
@@ -245,7 +253,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 e.record(stream)
                 ev[name] = e
 
-            pipe.forward(x, marks=mark)
+            step_pipe.step(x, marks=mark)
             steps.append(ev)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
@@ -289,6 +297,28 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 times.append((e0, e1))
             stream.synchronize()
             sw_ms["binned" if binned else "plain"] = statistics.mean(a.elapsed_time(b) for a, b in times)
+
+    # the same step replayed as one CUDA graph (captured after the timed
+    # region; profiler off): no launch or host cost between kernels
+    graph = None
+    if not args.no_graph:
+        step_pipe.capture(x)
+        times = []
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step_pipe.replay()
+                e1.record(stream)
+                times.append((e0, e1))
+        stream.synchronize()
+        ctx.check()
+        if int(step_pipe.num_pairs.item()) != m:
+            raise RuntimeError("graph replay produced a different |C|")
+        g_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in times)
+        graph = {"value": m / (g_ms / 1e3) * world, "unit": UNIT, "ms_per_step": g_ms,
+                 "note": "the timed step captured once as a CUDA graph and replayed"}
 
     # roofline of the dominant kernel, from the library's live per-kernel event
     # timings over the timed region (same stream as the launches)
@@ -369,6 +399,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "sw_gcups_plain": cells / (sw_ms["plain"] / 1e3) / 1e9,
             "sw_gcups_binned": cells / (sw_ms["binned"] / 1e3) / 1e9,
             "stages_ms": stage_ms, "kernel_rooflines": stage_roof, "wall_s": wall, "autotune": tuning["choice"],
+            "graph": graph,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

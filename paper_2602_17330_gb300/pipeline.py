@@ -130,22 +130,31 @@ class BatchedPipeline:
         self.fused = torch.empty((capacity,), dtype=torch.float32, device=dev)
         self.graph = None
 
-    def step(self, x):
-        """Queue one pass on the context's stream (no host synchronisation)."""
+    def step(self, x, marks=None):
+        """Queue one pass on the context's stream (no host synchronisation).
+        ``marks``, when given, is called with each stage name after the stage
+        is queued."""
         from . import subquad
 
         ctx, cfg, n = self.ctx, self.cfg, self.n
+        mark = marks or (lambda name: None)
         lib, P = subquad.lib(), subquad._ptr
         subquad._check(lib.subquad_pack(ctx.handle, P(x["codes"]), int(x["codes"].shape[1]), P(x["lens"]), n,
                                         cfg.pack_stride, P(self.packed)), "subquad_pack")
+        mark("pack")
         subquad._check(lib.subquad_sign(ctx.handle, P(self.packed), cfg.pack_stride, n, cfg.k, cfg.bands, cfg.rows,
                                         P(x["a"]), P(x["b"]), P(self.sig)), "subquad_sign")
+        mark("sign")
         ctx.band_candidates_async(self.sig, n, cfg.bands, cfg.rows, cfg.bucket_cap, self.pairs, self.num_pairs,
                                   donor=x.get("donor"))
+        mark("band")
         ctx.self_scores(self.packed, cfg.gap_open, cfg.gap_extend, out=self.self_sc, binned=True)
+        mark("self")
         ctx.align_score_binned_async(self.packed, self.pairs, self.num_pairs, self.sw, cfg.gap_open, cfg.gap_extend)
+        mark("align")
         ctx.fuse_forward_async(self.pairs, self.num_pairs, self.sw, self.self_sc, self.packed, x["emb"], x["params"],
                                cfg.hidden, self.fused)
+        mark("fuse")
 
     def capture(self, x):
         """Run one pass eagerly (reserves scratch, builds tables), then capture
