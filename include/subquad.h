@@ -83,7 +83,7 @@ int64_t subquad_launch_count(const subquad_ctx *ctx);
  *   SUBQUAD_TUNE_ALIGN_SHAPE: batched alignment launch shape, 0 = 256 threads
  *     x 2 blocks per SM, 1 = 128 threads x 3 blocks per SM (default 1);
  *   SUBQUAD_TUNE_BAND_PART_LOG2: log2 of the target number of (band, sequence)
- *     keys per hash partition of the banding stage, 6..16 (default 10); each
+ *     keys per hash partition of the banding stage, 6..16 (default 11); each
  *     partition is grouped by one CTA in shared memory. */
 enum { SUBQUAD_TUNE_ALIGN_SHAPE = 0, SUBQUAD_TUNE_BAND_PART_LOG2 = 1, SUBQUAD_TUNE_COUNT = 2 };
 int subquad_set_tuning(subquad_ctx *ctx, int key, int value);

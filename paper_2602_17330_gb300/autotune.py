@@ -22,7 +22,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning.json")
 
 CANDIDATES = {
     subquad.TUNE_ALIGN_SHAPE: (0, 1),
-    subquad.TUNE_BAND_PART_LOG2: (9, 10, 11),
+    subquad.TUNE_BAND_PART_LOG2: (10, 11),
 }
 
 

@@ -5,7 +5,7 @@
 //     batch of donors -- is hashed to a 32-bit fingerprint and a partition
 //     digit; a per-tile histogram, a scan and a stable scatter lay the records
 //     (fingerprint, id) of each partition out contiguously in id order;
-//  2. one CTA per partition (about 1024 records) groups equal keys in a
+//  2. one CTA per partition (about 2048 records) groups equal keys in a
 //     shared-memory hash table (fingerprint match confirmed on the exact
 //     keys); buckets of >= 2 members get contiguous kept positions, their
 //     chunks (runs of cap members in id order; the whole bucket when it is
@@ -252,18 +252,24 @@ __global__ void __launch_bounds__(kPartThreads, 3) part_scatter_kernel(const uin
 constexpr int kGrpThreads = 256;
 constexpr int kGrpSlots = 4096;
 constexpr int kGrpDistinct = 3072;
-constexpr int kGrpFast = 2048;       // partitions up to this size are grouped with records in shared memory
-constexpr int kGrpFastSlots = 4096;  // their table (load <= 1/2)
+constexpr int kGrpFast = 3072;       // partitions up to this size are grouped with records in shared memory
+constexpr int kGrpFastSurv = 1024;   // ... when at most this many records pass the filter
+constexpr int kGrpFastSlots = 2048;  // their table (load <= 1/2)
 constexpr int kGrpVerify = 160;      // deferred key comparisons held in shared memory (more: compared at once)
+constexpr int kGrpBloomWords = 512;  // 16384-bit filter bitmaps (two), aliased on the table
 constexpr uint32_t kFastEmpty = 0xffffffffu;
-// fast-path layout: tab u32[4096] | cnt u32[4096] | rec u64[2048] | slot u16[2048] | keys u16[1024] | vlist uint2[160]
-// (under 56 KB, so four CTAs share an SM)
-constexpr size_t kGrpFastSmem = (size_t)kGrpFastSlots * 8 + (size_t)kGrpFast * 8 + (size_t)kGrpFast * 2 +
-                                (size_t)kGrpFast + (size_t)kGrpVerify * 8;
+constexpr uint16_t kNoSlot = 0xffffu;
+// fast-path layout: tab u32[2048] | cnt u32[2048] | rec u64[3072] | slot u16[3072] | surv u16[3072] |
+//                   keys u16[1024] | vlist uint2[160]  (under 56 KB: four CTAs per SM)
+constexpr size_t kGrpFastSmem = (size_t)kGrpFastSlots * 8 + (size_t)kGrpFast * 8 + (size_t)kGrpFast * 4 +
+                                (size_t)kGrpFastSurv * 2 + (size_t)kGrpVerify * 8;
 // exact-path layout: tab u64[4096] | cnt u32[4096]
 constexpr size_t kGrpExactSmem = (size_t)kGrpSlots * (sizeof(unsigned long long) + sizeof(uint32_t));
 constexpr size_t kGrpSmem = kGrpFastSmem > kGrpExactSmem ? kGrpFastSmem : kGrpExactSmem;
-static_assert(kGrpFast * 2 <= kGrpFastSlots, "a fast-path table is never more than half full");
+static_assert(kGrpFastSurv * 2 <= kGrpFastSlots, "a fast-path table is never more than half full");
+static_assert(2 * kGrpBloomWords <= 2 * kGrpFastSlots, "the filter bitmaps fit in the table");
+static_assert(kGrpFast <= 4096, "record indices fit the 12 low bits of a fast-path table entry");
+static_assert(kGrpFastSmem <= 56 * 1024, "four fast-path CTAs share an SM");
 static_assert(kGrpFast <= 4096, "record indices fit the 12 low bits of a fast-path table entry");
 constexpr int kGrpStack = 48;
 constexpr int kGrpMaxLevel = 20;  // sub-ranges select fingerprint bits 12..31
@@ -466,14 +472,18 @@ __device__ __forceinline__ void place_in_order(const GroupShared &g, const uint6
     }
 }
 
-// Fast path for a partition of at most kGrpFast records: records staged in
-// shared memory, one table of about 3-6 cnt slots (u32 entries: the upper 20
-// fingerprint bits and the owner's record index; the full fingerprint is
-// compared through the staged record).  Records are grouped by fingerprint;
-// every member that is not its bucket's owner then compares its exact key
-// with the owner's (a deferred list processed by the whole block, so the loads
-// overlap).  Returns false, with nothing written, if two distinct keys share
-// a fingerprint: the caller then runs the exact path.
+// Fast path for a partition of at most kGrpFast records, staged in shared
+// memory.  A two-bitmap filter on fingerprint bits first drops the records
+// whose key certainly occurs once (a record passes when another record set
+// its bit before it, or it set a bit another record hits later); the
+// passing records (about 15% on a donor repertoire, at most kGrpFastSurv)
+// are grouped in a table of at least 2x their number (u32 entries: the upper
+// 20 fingerprint bits and the owner's record index; the full fingerprint is
+// compared through the staged record).  Every member that is not its
+// bucket's owner then compares its exact key with the owner's (a deferred
+// list processed by the whole block, so the loads overlap).  Returns false,
+// with nothing written, if two distinct keys share a fingerprint or too many
+// records pass: the caller then runs the exact path.
 __device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, uint32_t cnt,
                                         const uint32_t *__restrict__ band_sig, int rows,
                                         const int32_t *__restrict__ donor, int cap, int b, int bands,
@@ -485,37 +495,68 @@ __device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, ui
     uint32_t *cntv = tab + kGrpFastSlots;
     uint64_t *srec = reinterpret_cast<uint64_t *>(cntv + kGrpFastSlots);
     uint16_t *sslot = reinterpret_cast<uint16_t *>(srec + kGrpFast);
-    uint16_t *keys = sslot + kGrpFast;
-    uint2 *vlist = reinterpret_cast<uint2 *>(keys + kGrpFast / 2);
+    uint16_t *surv = sslot + kGrpFast;
+    uint16_t *keys = surv + kGrpFast;
+    uint2 *vlist = reinterpret_cast<uint2 *>(keys + kGrpFastSurv);
+    uint32_t *bloom1 = tab, *bloom2 = tab + kGrpBloomWords;
+    __shared__ uint32_t s_ns;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lt = (1u << lane) - 1u;
-    // a power of two >= 3 cnt (load <= 1/3; linear probing then stays short
-    // for every lane of a warp), at most kGrpFastSlots
-    uint32_t tslots = 256;
-    while (tslots < 3 * cnt && tslots < (uint32_t)kGrpFastSlots) tslots <<= 1;
 
 #pragma unroll 4
     for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) srec[q] = prec[q];
-    for (uint32_t q = threadIdx.x; q < tslots; q += blockDim.x) {
-        tab[q] = kFastEmpty;
-        cntv[q] = 0;
-    }
+    for (uint32_t q = threadIdx.x; q < 2 * kGrpBloomWords; q += blockDim.x) tab[q] = 0u;
     if (threadIdx.x == 0) {
+        s_ns = 0;
         s_nk = 0;
         s_nv = 0;
         s_clash = 0;
         s_big = 0;
     }
     __syncthreads();
-    bool clash = false;
-    // insert; warp-uniform trip count so the ballots see the whole warp
+    // filter: equal keys have equal fingerprints, hence equal bits
+    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const uint32_t bi = (uint32_t)(srec[q] >> 32) & (32u * kGrpBloomWords - 1u);
+        const uint32_t bit = 1u << (bi & 31);
+        if (atomicOr(&bloom1[bi >> 5], bit) & bit) atomicOr(&bloom2[bi >> 5], bit);
+    }
+    __syncthreads();
     for (uint32_t q0 = warp * 32; q0 < cnt; q0 += blockDim.x) {
         const uint32_t q = q0 + lane;
-        const bool valid = q < cnt;
+        bool pass = false;
+        if (q < cnt) {
+            const uint32_t bi = (uint32_t)(srec[q] >> 32) & (32u * kGrpBloomWords - 1u);
+            pass = (bloom2[bi >> 5] >> (bi & 31)) & 1u;
+            sslot[q] = kNoSlot;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, pass);
+        uint32_t base = 0;
+        if (lane == 0 && m) base = atomicAdd(&s_ns, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const uint32_t at = base + __popc(m & lt);
+        if (pass && at < (uint32_t)kGrpFast) surv[at] = (uint16_t)q;
+    }
+    __syncthreads();
+    const uint32_t ns = s_ns;
+    if (ns > (uint32_t)kGrpFastSurv) return false;  // uniform: too many keys repeat
+    uint32_t tslots = 64;
+    while (tslots < 2 * ns) tslots <<= 1;
+    const int tshift = 33 - __ffs(tslots);
+    for (uint32_t q = threadIdx.x; q < tslots; q += blockDim.x) {
+        tab[q] = kFastEmpty;
+        cntv[q] = 0;
+    }
+    __syncthreads();
+    bool clash = false;
+    // insert the passing records; warp-uniform trip count so the ballots see the whole warp
+    for (uint32_t t0 = warp * 32; t0 < ns; t0 += blockDim.x) {
+        const uint32_t t = t0 + lane;
+        const bool valid = t < ns;
+        const uint32_t q = valid ? surv[t] : 0u;
         uint32_t owner = q;
         if (valid) {
             const uint32_t fp = (uint32_t)(srec[q] >> 32);
             const uint32_t mine = (fp & ~0xfffu) | q;
-            uint32_t sl = fp >> (32 - __ffs(tslots) + 1);
+            uint32_t sl = fp >> tshift;
 #pragma unroll 1
             for (uint32_t probe = 0; probe < tslots; ++probe) {
                 uint32_t e = tab[sl];
@@ -558,11 +599,14 @@ __device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, ui
         load_key(band_sig + (int64_t)id * rows, rows, key);
         clash = clash || !same_key(band_sig, rows, (uint32_t)srec[pr.y], key, donor, donor ? donor[id] : 0);
     }
-    // buckets of >= 2 members listed (warp-aggregated appends); other slots marked
+    // buckets of >= 2 members listed (warp-aggregated appends); every other
+    // slot's entry becomes its member count (0 or 1)
     for (uint32_t t0 = 0; t0 < tslots; t0 += blockDim.x) {
         const uint32_t sl = t0 + threadIdx.x;
-        const bool kept = cntv[sl] >= 2;
-        if (!kept) tab[sl] = kFastEmpty;
+        const bool in = sl < tslots;
+        const uint32_t c = in ? cntv[sl] : 0u;
+        const bool kept = c >= 2;
+        if (in && !kept) tab[sl] = c;
         const uint32_t m = __ballot_sync(0xffffffffu, kept);
         uint32_t base = 0;
         if (lane == 0 && m) base = atomicAdd(&s_nk, (uint32_t)__popc(m));
@@ -619,13 +663,12 @@ __device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, ui
     }
     __syncthreads();
     // members of buckets within the cap: any order
-    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const uint32_t sl = sslot[q];
-        const uint32_t e = tab[sl];
-        if (e == kFastEmpty) continue;
+    for (uint32_t t = threadIdx.x; t < ns; t += blockDim.x) {
+        const uint32_t q = surv[t];
+        const uint32_t e = tab[sslot[q]];
         const uint32_t c = e & 0xffffu;
-        if (cap > 0 && c > (uint32_t)cap) continue;
-        const uint32_t r = atomicAdd(&cntv[sl], 1u);
+        if (c < 2 || e == kFastEmpty || (cap > 0 && c > (uint32_t)cap)) continue;
+        const uint32_t r = atomicAdd(&cntv[sslot[q]], 1u);
         const uint64_t head = kbase + (e >> 16);
         const uint32_t id = (uint32_t)srec[q];
         o.kept_ids[head + r] = id;
@@ -636,11 +679,11 @@ __device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, ui
         for (uint32_t q0 = 0; q0 < cnt; q0 += 32) {
             const uint32_t q = q0 + lane;
             uint32_t sl = 0, e = kFastEmpty;
-            if (q < cnt) {
+            if (q < cnt && sslot[q] != kNoSlot) {
                 sl = sslot[q];
                 e = tab[sl];
             }
-            const bool mine = e != kFastEmpty && cap > 0 && (e & 0xffffu) > (uint32_t)cap;
+            const bool mine = e != kFastEmpty && (e & 0xffffu) >= 2 && cap > 0 && (e & 0xffffu) > (uint32_t)cap;
             const uint32_t peers = __match_any_sync(0xffffffffu, mine ? sl : (0x80000000u | lane));
             const uint32_t before = __popc(peers & lt);
             const uint32_t basec = mine ? cntv[sl] : 0u;
@@ -1175,7 +1218,7 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
     SqProfScope prof(ctx, SUBQUAD_PROF_BAND);
 
     // Partitions of at most 2^part_log2 records on average (the tuning knob;
-    // default 1024): P = 2^pbits per band.  Bands are partitioned in groups
+    // default 2048): P = 2^pbits per band.  Bands are partitioned in groups
     // of at most 2^28 records (bounding the record buffers); kept members,
     // chunk ids and the chunk list span all bands.
     const int part_log2 = ctx->tune[SUBQUAD_TUNE_BAND_PART_LOG2];

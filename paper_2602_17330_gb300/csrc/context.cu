@@ -74,7 +74,7 @@ extern "C" int subquad_create(subquad_ctx **out, int device, void *cuda_stream)
     sq_update_matrix_flags(ctx);
     for (int k = 0; k < SUBQUAD_TUNE_COUNT; ++k) ctx->tune[k] = 0;
     ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE] = 1;
-    ctx->tune[SUBQUAD_TUNE_BAND_PART_LOG2] = 10;
+    ctx->tune[SUBQUAD_TUNE_BAND_PART_LOG2] = 11;
     SqDeviceGuard guard(ctx);
     cudaError_t e = guard.ok ? cudaSuccess : cudaErrorInvalidDevice;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
