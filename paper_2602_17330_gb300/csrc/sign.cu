@@ -7,6 +7,8 @@
 // (a_t x + b_t) mod (2^31 - 1) exactly with one 32x32->64 multiply-add and a
 // Mersenne fold, keeps the running minimum, and stores each band's R minima as
 // one vector store into the band-major output sig[b][i][r].
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace {
@@ -74,46 +76,87 @@ __device__ __forceinline__ void sign_one(const uint64_t *__restrict__ w, int L, 
     }
 }
 
+// One CTA handles tiles of kSignTile consecutive sequences: it counting-sorts
+// the tile by k-mer count in shared memory, so each warp takes 32 sequences
+// of (nearly) equal count and the per-warp k-mer count NK wastes almost no
+// evaluations; signatures are written back at the sequences' own ids (a tile
+// covers one contiguous id range).
+constexpr int kSignThreads = 256;
+constexpr int kSignPer = 1;
+constexpr int kSignTile = kSignThreads * kSignPer;
+
 template <int WORDS>
-__global__ void __launch_bounds__(256) sign_kernel(const uint64_t *__restrict__ packed, int64_t n, int k, int bands,
-                                                   int rows, const uint32_t *__restrict__ a,
-                                                   const uint32_t *__restrict__ b, uint32_t *__restrict__ sig)
+__global__ void __launch_bounds__(kSignThreads) sign_kernel(const uint64_t *__restrict__ packed, int64_t n, int k,
+                                                            int bands, int rows, const uint32_t *__restrict__ a,
+                                                            const uint32_t *__restrict__ b, uint32_t *__restrict__ sig)
 {
     extern __shared__ uint2 s_ab[];
+    __shared__ uint32_t s_cnt[32];
+    __shared__ uint16_t s_order[kSignTile];
     const int H = bands * rows;
     // coefficients reduced mod P (same hash) and doubled for hash_min
     for (int t = threadIdx.x; t < H; t += blockDim.x) s_ab[t] = make_uint2(2u * (a[t] % kP31), 2u * (b[t] % kP31));
-    __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // the loop trip count is uniform per warp so the warp-level dispatch is safe
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        const bool valid = i < n;
-        uint64_t w[WORDS];
+    for (int64_t base = (int64_t)blockIdx.x * kSignTile; base < n; base += (int64_t)gridDim.x * kSignTile) {
+        if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0;
+        __syncthreads();
+        uint32_t bin[kSignPer];
 #pragma unroll
-        for (int q = 0; q < WORDS; ++q) w[q] = 0;
-        if (valid) {
-            const ulonglong2 *rec = reinterpret_cast<const ulonglong2 *>(packed + i * WORDS);
-            ulonglong2 r0 = rec[0];
-            w[0] = r0.x;
-            w[1] = r0.y;
-            if (WORDS == 4) {
-                ulonglong2 r1 = rec[1];
-                w[2 % WORDS] = r1.x;
-                w[3 % WORDS] = r1.y;
+        for (int r = 0; r < kSignPer; ++r) {
+            const int64_t i = base + r * kSignThreads + threadIdx.x;
+            bin[r] = 31;  // past the end: sorted last
+            if (i < n) {
+                const ulonglong2 w01 = reinterpret_cast<const ulonglong2 *>(packed + i * WORDS)[0];
+                bin[r] = (uint32_t)max(sq_record_len(w01.x, w01.y) - k + 1, 0);
+            }
+            atomicAdd(&s_cnt[bin[r]], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const uint32_t c = s_cnt[threadIdx.x];
+            uint32_t inc = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+                if ((int)threadIdx.x >= d) inc += o;
+            }
+            s_cnt[threadIdx.x] = inc - c;  // exclusive
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSignPer; ++r) s_order[atomicAdd(&s_cnt[bin[r]], 1u)] = (uint16_t)(r * kSignThreads + threadIdx.x);
+        __syncthreads();
+#pragma unroll 1
+        for (int r = 0; r < kSignPer; ++r) {
+            const int64_t i = base + s_order[r * kSignThreads + threadIdx.x];
+            const bool valid = i < n;
+            uint64_t w[WORDS];
+#pragma unroll
+            for (int q = 0; q < WORDS; ++q) w[q] = 0;
+            if (valid) {
+                const ulonglong2 *rec = reinterpret_cast<const ulonglong2 *>(packed + i * WORDS);
+                const ulonglong2 r0 = rec[0];
+                w[0] = r0.x;
+                w[1] = r0.y;
+                if (WORDS == 4) {
+                    const ulonglong2 r1 = rec[1];
+                    w[2 % WORDS] = r1.x;
+                    w[3 % WORDS] = r1.y;
+                }
+            }
+            const int L = sq_record_len(w[0], w[1]);
+            const int nk = valid ? L - k + 1 : 0;
+            const int wmax = __reduce_max_sync(0xffffffffu, nk > 0 ? nk : 0);
+            if (valid) {
+                if (wmax <= 4) sign_one<WORDS, 4>(w, L, k, i, n, bands, rows, s_ab, sig);
+                else if (wmax <= 8) sign_one<WORDS, 8>(w, L, k, i, n, bands, rows, s_ab, sig);
+                else if (wmax <= 12) sign_one<WORDS, 12>(w, L, k, i, n, bands, rows, s_ab, sig);
+                else if (wmax <= 16) sign_one<WORDS, 16>(w, L, k, i, n, bands, rows, s_ab, sig);
+                else if (wmax <= 20) sign_one<WORDS, 20>(w, L, k, i, n, bands, rows, s_ab, sig);
+                else if (wmax <= 24) sign_one<WORDS, 24>(w, L, k, i, n, bands, rows, s_ab, sig);
+                else sign_one<WORDS, (WORDS == 2 ? 24 : 30)>(w, L, k, i, n, bands, rows, s_ab, sig);
             }
         }
-        const int L = sq_record_len(w[0], w[1]);
-        const int nk = valid ? L - k + 1 : 0;
-        const int wmax = __reduce_max_sync(0xffffffffu, nk > 0 ? nk : 0);
-        if (!valid) continue;
-        if (wmax <= 4) sign_one<WORDS, 4>(w, L, k, i, n, bands, rows, s_ab, sig);
-        else if (wmax <= 8) sign_one<WORDS, 8>(w, L, k, i, n, bands, rows, s_ab, sig);
-        else if (wmax <= 12) sign_one<WORDS, 12>(w, L, k, i, n, bands, rows, s_ab, sig);
-        else if (wmax <= 16) sign_one<WORDS, 16>(w, L, k, i, n, bands, rows, s_ab, sig);
-        else if (wmax <= 20) sign_one<WORDS, 20>(w, L, k, i, n, bands, rows, s_ab, sig);
-        else if (wmax <= 24) sign_one<WORDS, 24>(w, L, k, i, n, bands, rows, s_ab, sig);
-        else sign_one<WORDS, (WORDS == 2 ? 24 : 30)>(w, L, k, i, n, bands, rows, s_ab, sig);
+        __syncthreads();  // s_order and s_cnt are reused by the next tile
     }
 }
 
@@ -129,12 +172,12 @@ extern "C" int subquad_sign(subquad_ctx *ctx, const void *packed, int pack_strid
     if (!packed || !a || !b || !sig_out) return SUBQUAD_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(packed) % 16 || reinterpret_cast<uintptr_t>(sig_out) % 16) return SUBQUAD_ERR_ARG;
     const size_t smem = (size_t)bands * rows * sizeof(uint2);
-    unsigned grid = sq_grid(ctx, n, 256, 8);
+    unsigned grid = (unsigned)std::min<int64_t>((n + kSignTile - 1) / kSignTile, int64_t(1) << 30);
     SqProfScope prof(ctx, SUBQUAD_PROF_SIGN);
     if (pack_stride == 16)
-        sign_kernel<2><<<grid, 256, smem, ctx->stream>>>((const uint64_t *)packed, n, k, bands, rows, a, b, sig_out);
+        sign_kernel<2><<<grid, kSignThreads, smem, ctx->stream>>>((const uint64_t *)packed, n, k, bands, rows, a, b, sig_out);
     else
-        sign_kernel<4><<<grid, 256, smem, ctx->stream>>>((const uint64_t *)packed, n, k, bands, rows, a, b, sig_out);
+        sign_kernel<4><<<grid, kSignThreads, smem, ctx->stream>>>((const uint64_t *)packed, n, k, bands, rows, a, b, sig_out);
     SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
 }
