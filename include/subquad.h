@@ -193,6 +193,31 @@ int subquad_band_candidates_async(subquad_ctx *ctx, const uint32_t *sig, int64_t
                                   int32_t bucket_cap, const int32_t *donor, uint32_t *pairs_out,
                                   int64_t pairs_capacity, uint64_t *d_num_pairs);
 
+/* Streamed form, for candidate sets larger than one buffer (the hardware-
+ * aware batching of Eq. batch applied to the candidate list itself).
+ * subquad_band_stream_create groups the keys once (same arguments and
+ * semantics as subquad_band_candidates_async; donor may be NULL) and keeps
+ * the chunk structure in the stream's own device memory (owned by the
+ * stream, about 20 bytes per (sequence, band) plus 12 per sequence);
+ * *total_raw_out (host, nullable) receives the number of raw pairs, an upper
+ * bound of |C|.  It SYNCHRONISES the stream.  Each subquad_band_stream_next
+ * call writes to pairs_out (device uint32 [capacity][2], capacity >= 32) the
+ * pairs of C found among the next floor(capacity/32)*32 raw pairs, sorted
+ * lexicographically; *num_pairs_out (host) receives their number (it may be
+ * 0) and *done (host) becomes 1 once the raw pairs are exhausted.  The
+ * batches partition C: every pair of C is returned by exactly one call.  It
+ * SYNCHRONISES the stream.  subquad_band_stream_reset restarts the
+ * sequence; subquad_band_stream_destroy frees the stream (NULL is a no-op).
+ * The context's scratch is used between calls; the stream stays valid. */
+typedef struct subquad_band_stream subquad_band_stream;
+int subquad_band_stream_create(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows,
+                               int32_t bucket_cap, const int32_t *donor, subquad_band_stream **out,
+                               uint64_t *total_raw_out);
+int subquad_band_stream_next(subquad_ctx *ctx, subquad_band_stream *stream, uint32_t *pairs_out,
+                             int64_t capacity, int64_t *num_pairs_out, int *done);
+int subquad_band_stream_reset(subquad_band_stream *stream);
+void subquad_band_stream_destroy(subquad_band_stream *stream);
+
 /* ------------------------------------------------------------------------ */
 /* (a3) Affine-gap local alignment -- the alignment channel computed for     */
 /* every candidate pair in Algorithm 1's affinity loop.  The paper's own GPU  */

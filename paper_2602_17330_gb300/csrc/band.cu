@@ -24,6 +24,7 @@
 // device: the kernels after them are sized for the upper bound and read the
 // actual count.
 #include <algorithm>
+#include <new>
 
 #include "internal.cuh"
 
@@ -854,17 +855,17 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
     const uint32_t *__restrict__ kept_ids, const uint32_t *__restrict__ heads, const uint32_t *__restrict__ sizes,
     const uint32_t *__restrict__ cband, const uint64_t *__restrict__ poff, const uint32_t *__restrict__ wchunk,
     int64_t wmax, const uint32_t *__restrict__ d_nchunks, const uint64_t *__restrict__ d_total, int bands,
-    const uint32_t *__restrict__ chunk_of, const uint32_t *__restrict__ kept_mask, uint32_t *__restrict__ out,
-    int64_t capacity,
-    unsigned long long *__restrict__ d_count, uint32_t *__restrict__ deg, uint32_t *err)
+    const uint32_t *__restrict__ chunk_of, const uint32_t *__restrict__ kept_mask, uint64_t raw0, uint64_t raw1,
+    uint32_t *__restrict__ out, int64_t capacity, unsigned long long *__restrict__ d_count,
+    uint32_t *__restrict__ deg, uint32_t *err)
 {
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_warp[32];
     const uint32_t nc = *d_nchunks;
-    const uint64_t total = *d_total;
+    const uint64_t total = min(*d_total, raw1);  // raw pairs [raw0, total) of this call; raw0 % 32 == 0
     const uint32_t lane = threadIdx.x & 31;
     // block-uniform trip count (block_append synchronises the block)
-    for (uint64_t b0 = (uint64_t)blockIdx.x * blockDim.x; b0 < total; b0 += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t b0 = raw0 + (uint64_t)blockIdx.x * blockDim.x; b0 < total; b0 += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t q0 = b0 + (threadIdx.x & ~31u);
         const uint64_t q = q0 + lane;
         uint32_t c0 = 0, starts = 0;
@@ -927,7 +928,7 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
 // CTA in shared memory up to kRowMid, in place in global memory beyond.
 // Every count stays on the device.
 constexpr int kRowSmall = 32;
-constexpr int kRowWarp = 1024;  // rows up to this size: one warp, registers
+constexpr int kRowWarp = 256;   // rows up to this size: one warp, registers
 constexpr int kRowMid = 8192;   // rows up to this size: one CTA, shared memory
 constexpr int kRowThreads = 256;
 
@@ -1209,6 +1210,197 @@ namespace {
 // the actual counts, |C| goes to *d_num_pairs and an overflow of the capacity
 // sets the sticky CAPACITY error -- so the call can be captured in a graph once
 // a call of the same shape has reserved the scratch.
+// The chunk structure of one banding (device arrays): per (sequence, band)
+// chunk ids and kept-band masks, kept members, the chunk list with its
+// scanned pair counts, the start chunk of every 32nd raw pair, and the
+// device counts (chunks, raw pairs, kept members).
+struct BandIndex {
+    int64_t n = 0, mall = 0, cmax = 0, wmax = 0;
+    int bands = 0;
+    uint32_t *chunk_of, *kept_mask, *kept, *heads, *sizes, *cband, *wchunk;
+    uint64_t *poff;
+    uint64_t *counters;  // [0] chunks (low word), [1] raw pairs, [2] kept members
+};
+
+BandIndex take_index(SqArena &a, int64_t n, int bands)
+{
+    BandIndex I;
+    I.n = n;
+    I.bands = bands;
+    I.mall = (int64_t)bands * n;
+    I.cmax = I.mall / 2 + 1;  // chunks of >= 2 members
+    I.wmax = I.mall / 8 + 64;  // start chunks of the first 4 * bands * n raw pairs
+    I.chunk_of = a.take<uint32_t>((size_t)n * bands);
+    I.kept_mask = a.take<uint32_t>(n);
+    I.kept = a.take<uint32_t>(I.mall);
+    I.heads = a.take<uint32_t>(I.cmax);
+    I.sizes = a.take<uint32_t>(I.cmax);
+    I.cband = a.take<uint32_t>(I.cmax);
+    I.poff = a.take<uint64_t>(I.cmax);
+    I.wchunk = a.take<uint32_t>(I.wmax);
+    I.counters = a.take<uint64_t>(4);
+    return I;
+}
+
+struct GroupScratch {
+    int pbits = 0, G = 0;
+    int64_t P = 0, ntiles = 0, mg = 0, hlen = 0;
+    uint64_t *recs, *fd;
+    uint32_t *rslot, *offs;
+    void *tmp;
+    size_t tmp_bytes = 0;
+};
+
+GroupScratch plan_group(subquad_ctx *ctx, int64_t n, int bands)
+{
+    GroupScratch S;
+    // Partitions of at most 2^part_log2 keys on average (the tuning knob;
+    // default 2048): P = 2^pbits per band.  Bands are partitioned in groups
+    // of at most 2^28 keys (bounding the record buffers); kept members,
+    // chunk ids and the chunk list span all bands.
+    const int part_log2 = ctx->tune[SUBQUAD_TUNE_BAND_PART_LOG2];
+    while ((n >> S.pbits) > (int64_t(1) << part_log2) && S.pbits < kPartMaxBits) ++S.pbits;
+    S.P = int64_t(1) << S.pbits;
+    S.ntiles = (n + kPartTile - 1) / kPartTile;
+    S.G = (int)std::max<int64_t>(1, std::min<int64_t>(bands, (int64_t(1) << 28) / n));
+    S.mg = (int64_t)S.G * n;
+    S.hlen = (int64_t)S.G * S.P * S.ntiles;
+    S.tmp_bytes = std::max(sq_scan_tmp_bytes(S.hlen), sq_scan_tmp_bytes((int64_t)bands * n / 2 + 1));
+    return S;
+}
+
+void take_group(SqArena &a, GroupScratch &S)
+{
+    S.recs = a.take<uint64_t>(S.mg);
+    S.fd = a.take<uint64_t>(S.mg);
+    S.rslot = a.take<uint32_t>(S.mg);
+    S.offs = a.take<uint32_t>(S.hlen);
+    S.tmp = a.take<char>(S.tmp_bytes);
+}
+
+// Steps 1-3: partition, group, chunk list, pair offsets, start chunks.
+int band_index_build(subquad_ctx *ctx, const uint32_t *sig, int rows, int cap, const int32_t *donor,
+                     const BandIndex &I, const GroupScratch &S)
+{
+    const int64_t n = I.n;
+    const int bands = I.bands;
+    uint32_t *d_nchunks = reinterpret_cast<uint32_t *>(I.counters);
+    uint64_t *d_total = I.counters + 1;
+    unsigned long long *d_kept = reinterpret_cast<unsigned long long *>(I.counters + 2);
+    SQ_TRY_CUDA(cudaMemsetAsync(I.counters, 0, 4 * sizeof(uint64_t), ctx->stream));
+    SQ_TRY_CUDA(cudaMemsetAsync(I.chunk_of, 0xff, (size_t)n * bands * sizeof(uint32_t), ctx->stream));
+    SQ_TRY_CUDA(cudaMemsetAsync(I.kept_mask, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
+    GroupOut go{I.kept, d_kept, d_nchunks, I.heads, I.sizes, I.cband, I.poff, I.chunk_of, I.kept_mask, S.rslot};
+    for (int band0 = 0; band0 < bands; band0 += S.G) {
+        const int gb = std::min(S.G, bands - band0);
+        const int64_t recs = (int64_t)gb * n;
+        const int64_t hl = (int64_t)gb * S.P * S.ntiles;
+        const dim3 grid((unsigned)S.ntiles, gb);
+        {
+            SqProfScope prof_ins(ctx, SUBQUAD_PROF_BAND_PARTITION);
+            part_hist_kernel<<<grid, kPartThreads, S.P * sizeof(uint32_t), ctx->stream>>>(
+                sig, n, rows, band0, S.pbits, donor, S.ntiles, S.offs, S.fd);
+            SQ_LAUNCH_CHECK();
+            SQ_TRY(sq_scan_u32(ctx, S.offs, S.offs, hl, nullptr, false, false, nullptr, S.tmp, S.tmp_bytes));
+            part_scatter_kernel<<<grid, kPartThreads, (kPartThreads / 32) * S.P * sizeof(uint32_t), ctx->stream>>>(
+                S.fd, n, S.pbits, S.ntiles, S.offs, S.recs);
+            SQ_LAUNCH_CHECK();
+        }
+        SqProfScope prof_grp(ctx, SUBQUAD_PROF_BAND_GROUP);
+        SQ_TRY_CUDA(cudaFuncSetAttribute(part_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGrpSmem));
+        part_group_kernel<<<(unsigned)(gb * S.P), kGrpThreads, kGrpSmem, ctx->stream>>>(
+            S.recs, S.offs, S.ntiles, recs, S.pbits, band0, bands, sig, n, rows, donor, cap, go, ctx->d_err);
+        SQ_LAUNCH_CHECK();
+    }
+    SqProfScope prof_emit(ctx, SUBQUAD_PROF_BAND_EMIT);
+    // pair counts -> offsets.  Only the first nchunks entries are written;
+    // an exclusive prefix at entry c depends on entries < c only, so the
+    // unwritten tail never reaches a used offset.
+    SQ_TRY(sq_scan_u64(ctx, I.poff, I.poff, I.cmax, d_nchunks, nullptr, S.tmp, S.tmp_bytes));
+    band_total_kernel<<<1, 1, 0, ctx->stream>>>(I.poff, I.sizes, d_nchunks, d_total);
+    SQ_LAUNCH_CHECK();
+    band_warp_chunk_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(I.poff, d_nchunks, d_total, I.wchunk,
+                                                                                I.wmax);
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
+}
+
+struct EmitScratch {
+    uint32_t *deg, *rowoff, *mid, *lng, *col;
+    void *tmp;
+    size_t tmp_bytes = 0;
+};
+
+void take_emit(SqArena &a, EmitScratch &E, int64_t n, int64_t capacity, uint32_t *col_alias, int64_t alias_words)
+{
+    E.deg = a.take<uint32_t>(n);
+    E.rowoff = a.take<uint32_t>(n);
+    E.mid = a.take<uint32_t>(n);
+    E.lng = a.take<uint32_t>((capacity >> 13) + 1);
+    // row columns: in a free buffer of the caller when it is large enough
+    E.col = capacity <= alias_words ? col_alias : a.take<uint32_t>(capacity);
+    E.tmp_bytes = sq_scan_tmp_bytes(n);
+    E.tmp = a.take<char>(E.tmp_bytes);
+}
+
+// Step 4: the owned pairs among raw pairs [raw0, raw1) (raw0 % 32 == 0),
+// appended to pairs_out (at most capacity written; d_count receives the
+// owned count) and sorted lexicographically.  d_publish, when given, receives
+// the owned count with the sticky CAPACITY bit on an overflow.
+int band_emit_sorted(subquad_ctx *ctx, const BandIndex &I, uint64_t raw0, uint64_t raw1, uint32_t *pairs_out,
+                     int64_t capacity, unsigned long long *d_publish, const EmitScratch &E)
+{
+    const int64_t n = I.n;
+    const int64_t cap1 = std::max<int64_t>(capacity, 1);
+    unsigned long long *d_count = reinterpret_cast<unsigned long long *>(ctx->d_small);
+    unsigned long long *d_clamped = reinterpret_cast<unsigned long long *>(ctx->d_small + 4);
+    unsigned long long *d_mid = reinterpret_cast<unsigned long long *>(ctx->d_small + 5);
+    unsigned long long *d_long = reinterpret_cast<unsigned long long *>(ctx->d_small + 6);
+    unsigned long long *d_wrows = reinterpret_cast<unsigned long long *>(ctx->d_small + 7);
+    SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 8 * sizeof(uint64_t), ctx->stream));
+    SQ_TRY_CUDA(cudaMemsetAsync(E.deg, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
+    {
+        SqProfScope prof_emit(ctx, SUBQUAD_PROF_BAND_EMIT);
+        band_emit_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(
+            I.kept, I.heads, I.sizes, I.cband, I.poff, I.wchunk, I.wmax, reinterpret_cast<const uint32_t *>(I.counters),
+            I.counters + 1, I.bands, I.chunk_of, I.kept_mask, raw0, raw1, pairs_out, capacity, d_count, E.deg,
+            ctx->d_err);
+        SQ_LAUNCH_CHECK();
+    }
+    // the owned count published, an overflow flagged, the count of written
+    // pairs clamped to the capacity for the sort below
+    band_finish_kernel<<<1, 1, 0, ctx->stream>>>(d_count, capacity, d_publish, d_clamped, ctx->d_err);
+    SQ_LAUNCH_CHECK();
+    // lexicographic order: row offsets by first member, row classes, the
+    // second members scattered into their rows, every row sorted
+    SqProfScope prof_ps(ctx, SUBQUAD_PROF_BAND_PAIRSORT);
+    const unsigned rgrid = sq_grid(ctx, n, kRowThreads, 8);
+    SQ_TRY(sq_scan_u32(ctx, E.deg, E.rowoff, n, nullptr, false, false, nullptr, E.tmp, E.tmp_bytes));
+    rows_classify_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.mid, d_wrows, d_mid, E.lng,
+                                                                 d_long);
+    SQ_LAUNCH_CHECK();
+    pairs_scatter_kernel<<<sq_grid(ctx, cap1, 256, 8), 256, 0, ctx->stream>>>(pairs_out, d_clamped, E.rowoff, E.deg,
+                                                                              E.col);
+    SQ_LAUNCH_CHECK();
+    rows_sort_small_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.col, pairs_out);
+    SQ_LAUNCH_CHECK();
+    rows_sort_warp_kernel<<<(unsigned)ctx->num_sms * 8, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.mid,
+                                                                                      d_wrows, E.col, pairs_out);
+    SQ_LAUNCH_CHECK();
+    rows_sort_mid_kernel<<<(unsigned)ctx->num_sms * 4, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.mid,
+                                                                                     d_mid, E.col, pairs_out);
+    SQ_LAUNCH_CHECK();
+    rows_sort_long_kernel<<<(unsigned)ctx->num_sms, 1024, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.lng, d_long,
+                                                                           E.col, pairs_out);
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
+}
+
+// Synchronous form (d_num_pairs == nullptr): reads back |C| once at the end.
+// Asynchronous form: no host synchronisation -- |C| goes to *d_num_pairs and
+// an overflow of the capacity sets the sticky CAPACITY error -- so the call
+// can be captured in a graph once a call of the same shape has reserved the
+// scratch.
 int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows, int32_t bucket_cap,
              const int32_t *donor, uint32_t *pairs_out, int64_t pairs_capacity, int64_t *num_pairs_out,
              unsigned long long *d_num_pairs)
@@ -1216,145 +1408,25 @@ int band_run(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int ro
     const bool async = d_num_pairs != nullptr;
     const int cap = (bucket_cap <= 0 || bucket_cap >= n) ? 0 : bucket_cap;
     SqProfScope prof(ctx, SUBQUAD_PROF_BAND);
-
-    // Partitions of at most 2^part_log2 records on average (the tuning knob;
-    // default 2048): P = 2^pbits per band.  Bands are partitioned in groups
-    // of at most 2^28 records (bounding the record buffers); kept members,
-    // chunk ids and the chunk list span all bands.
-    const int part_log2 = ctx->tune[SUBQUAD_TUNE_BAND_PART_LOG2];
-    int pbits = 0;
-    while ((n >> pbits) > (int64_t(1) << part_log2) && pbits < kPartMaxBits) ++pbits;
-    const int64_t P = int64_t(1) << pbits;
-    const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
-    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(bands, (int64_t(1) << 28) / n));
-    const int64_t mg = (int64_t)G * n;        // records per group
-    const int64_t mall = (int64_t)bands * n;  // upper bound of kept members
-    const int64_t hlen = (int64_t)G * P * ntiles;
-    const int64_t final_cap = std::max<int64_t>(pairs_capacity, 1);
-    const size_t tmp_bytes =
-        std::max(std::max(sq_scan_tmp_bytes(hlen), sq_scan_tmp_bytes(mall / 2 + 1)), sq_scan_tmp_bytes(n));
-    // start chunks of the first 4 * bands * n raw pairs, in groups of 32
-    // (later groups, if any, search for their start chunk)
-    const int64_t wmax = mall / 8 + 64;
-
-    auto layout = [&](SqArena &a) {
-        struct L {
-            uint32_t *chunk_of, *kept_mask, *kept, *rslot, *offs, *heads, *sizes, *cband, *wchunk, *deg, *rowoff, *mid;
-            uint32_t *lng, *col;
-            uint64_t *recs, *fd, *npairs;
-            void *tmp;
-        } l;
-        l.chunk_of = a.take<uint32_t>((size_t)n * bands);
-        l.kept_mask = a.take<uint32_t>(n);
-        l.kept = a.take<uint32_t>(mall);
-        l.recs = a.take<uint64_t>(mg);
-        l.fd = a.take<uint64_t>(mg);
-        l.rslot = a.take<uint32_t>(mg);
-        l.offs = a.take<uint32_t>(hlen);
-        l.heads = a.take<uint32_t>(mall / 2 + 1);
-        l.sizes = a.take<uint32_t>(mall / 2 + 1);
-        l.cband = a.take<uint32_t>(mall / 2 + 1);
-        l.npairs = a.take<uint64_t>(mall / 2 + 1);
-        l.wchunk = a.take<uint32_t>(wmax);
-        l.deg = a.take<uint32_t>(n);
-        l.rowoff = a.take<uint32_t>(n);
-        l.mid = a.take<uint32_t>(n);
-        l.lng = a.take<uint32_t>((final_cap >> 13) + 1);
-        // row columns: in the record buffer (free after the emission) when it is large enough
-        l.col = final_cap <= 2 * mg ? reinterpret_cast<uint32_t *>(l.recs) : a.take<uint32_t>(final_cap);
-        l.tmp = a.take<char>(tmp_bytes);
-        return l;
+    GroupScratch S = plan_group(ctx, n, bands);
+    const int64_t cap1 = std::max<int64_t>(pairs_capacity, 1);
+    auto layout = [&](SqArena &a, BandIndex &I, EmitScratch &E) {
+        I = take_index(a, n, bands);
+        take_group(a, S);
+        // the record buffer is free after the grouping: it holds the row columns when large enough
+        take_emit(a, E, n, cap1, reinterpret_cast<uint32_t *>(S.recs), 2 * S.mg);
     };
-    SqArena measure(nullptr);
-    layout(measure);
-    SQ_TRY(sq_scratch_reserve(ctx, measure.off));
+    BandIndex I;
+    EmitScratch E;
+    {
+        SqArena measure(nullptr);
+        layout(measure, I, E);
+        SQ_TRY(sq_scratch_reserve(ctx, measure.off));
+    }
     SqArena arena(ctx->scratch);
-    auto L = layout(arena);
-
-    unsigned long long *d_count = reinterpret_cast<unsigned long long *>(ctx->d_small);
-    uint32_t *d_nchunks = reinterpret_cast<uint32_t *>(ctx->d_small + 1);
-    uint64_t *d_total = ctx->d_small + 2;
-    unsigned long long *d_kept = reinterpret_cast<unsigned long long *>(ctx->d_small + 3);
-    unsigned long long *d_clamped = reinterpret_cast<unsigned long long *>(ctx->d_small + 4);
-    SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 8 * sizeof(uint64_t), ctx->stream));
-    SQ_TRY_CUDA(cudaMemsetAsync(L.chunk_of, 0xff, (size_t)n * bands * sizeof(uint32_t), ctx->stream));
-    SQ_TRY_CUDA(cudaMemsetAsync(L.kept_mask, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
-    SQ_TRY_CUDA(cudaMemsetAsync(L.deg, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
-
-    GroupOut go{L.kept, d_kept, d_nchunks, L.heads, L.sizes, L.cband, L.npairs, L.chunk_of, L.kept_mask, L.rslot};
-    for (int band0 = 0; band0 < bands; band0 += G) {
-        const int gb = std::min(G, bands - band0);
-        const int64_t recs = (int64_t)gb * n;
-        const int64_t hl = (int64_t)gb * P * ntiles;
-        const dim3 grid((unsigned)ntiles, gb);
-        {
-            SqProfScope prof_ins(ctx, SUBQUAD_PROF_BAND_PARTITION);
-            part_hist_kernel<<<grid, kPartThreads, P * sizeof(uint32_t), ctx->stream>>>(sig, n, rows, band0, pbits,
-                                                                                      donor, ntiles, L.offs, L.fd);
-            SQ_LAUNCH_CHECK();
-            SQ_TRY(sq_scan_u32(ctx, L.offs, L.offs, hl, nullptr, false, false, nullptr, L.tmp, tmp_bytes));
-            part_scatter_kernel<<<grid, kPartThreads, (kPartThreads / 32) * P * sizeof(uint32_t), ctx->stream>>>(
-                L.fd, n, pbits, ntiles, L.offs, L.recs);
-            SQ_LAUNCH_CHECK();
-        }
-        SqProfScope prof_grp(ctx, SUBQUAD_PROF_BAND_GROUP);
-        SQ_TRY_CUDA(cudaFuncSetAttribute(part_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGrpSmem));
-        part_group_kernel<<<(unsigned)(gb * P), kGrpThreads, kGrpSmem, ctx->stream>>>(
-            L.recs, L.offs, ntiles, recs, pbits, band0, bands, sig, n, rows, donor, cap, go, ctx->d_err);
-        SQ_LAUNCH_CHECK();
-    }
-    {
-        SqProfScope prof_emit(ctx, SUBQUAD_PROF_BAND_EMIT);
-        // pair counts -> offsets.  Only the first nchunks entries are written;
-        // an exclusive prefix at entry c depends on entries < c only, so the
-        // unwritten tail never reaches a used offset.
-        const int64_t cmax = mall / 2 + 1;
-        SQ_TRY(sq_scan_u64(ctx, L.npairs, L.npairs, cmax, d_nchunks, nullptr, L.tmp, tmp_bytes));
-        band_total_kernel<<<1, 1, 0, ctx->stream>>>(L.npairs, L.sizes, d_nchunks, d_total);
-        SQ_LAUNCH_CHECK();
-        band_warp_chunk_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(L.npairs, d_nchunks, d_total,
-                                                                                    L.wchunk, wmax);
-        SQ_LAUNCH_CHECK();
-        band_emit_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(
-            L.kept, L.heads, L.sizes, L.cband, L.npairs, L.wchunk, wmax, d_nchunks, d_total, bands, L.chunk_of,
-            L.kept_mask, pairs_out,
-            pairs_capacity, d_count, L.deg, ctx->d_err);
-        SQ_LAUNCH_CHECK();
-    }
-    // |C| published (asynchronous form), an overflow flagged, the count of
-    // written pairs clamped to the capacity for the sort below
-    band_finish_kernel<<<1, 1, 0, ctx->stream>>>(d_count, pairs_capacity, async ? d_num_pairs : nullptr, d_clamped,
-                                                 ctx->d_err);
-    SQ_LAUNCH_CHECK();
-    {
-        // lexicographic order: row offsets by first member, row classes, the
-        // second members scattered into their rows, every row sorted
-        SqProfScope prof_ps(ctx, SUBQUAD_PROF_BAND_PAIRSORT);
-        unsigned long long *d_mid = reinterpret_cast<unsigned long long *>(ctx->d_small + 5);
-        unsigned long long *d_long = reinterpret_cast<unsigned long long *>(ctx->d_small + 6);
-        unsigned long long *d_wrows = reinterpret_cast<unsigned long long *>(ctx->d_small + 7);
-        const unsigned rgrid = sq_grid(ctx, n, kRowThreads, 8);
-        SQ_TRY(sq_scan_u32(ctx, L.deg, L.rowoff, n, nullptr, false, false, nullptr, L.tmp, tmp_bytes));
-        rows_classify_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_clamped, L.mid, d_wrows, d_mid,
-                                                                     L.lng, d_long);
-        SQ_LAUNCH_CHECK();
-        pairs_scatter_kernel<<<sq_grid(ctx, final_cap, 256, 8), 256, 0, ctx->stream>>>(pairs_out, d_clamped,
-                                                                                      L.rowoff, L.deg, L.col);
-        SQ_LAUNCH_CHECK();
-        rows_sort_small_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_clamped, L.col, pairs_out);
-        SQ_LAUNCH_CHECK();
-        rows_sort_warp_kernel<<<(unsigned)ctx->num_sms * 8, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_clamped,
-                                                                                          L.mid, d_wrows, L.col,
-                                                                                          pairs_out);
-        SQ_LAUNCH_CHECK();
-        rows_sort_mid_kernel<<<(unsigned)ctx->num_sms * 4, kRowThreads, 0, ctx->stream>>>(L.rowoff, n, d_clamped,
-                                                                                         L.mid, d_mid, L.col,
-                                                                                         pairs_out);
-        SQ_LAUNCH_CHECK();
-        rows_sort_long_kernel<<<(unsigned)ctx->num_sms, 1024, 0, ctx->stream>>>(L.rowoff, n, d_clamped, L.lng, d_long,
-                                                                               L.col, pairs_out);
-        SQ_LAUNCH_CHECK();
-    }
+    layout(arena, I, E);
+    SQ_TRY(band_index_build(ctx, sig, rows, cap, donor, I, S));
+    SQ_TRY(band_emit_sorted(ctx, I, 0, ~0ull, pairs_out, pairs_capacity, async ? d_num_pairs : nullptr, E));
     if (async) return SUBQUAD_OK;
     SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_small, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
     SQ_TRY_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1404,4 +1476,135 @@ extern "C" int subquad_band_candidates_async(subquad_ctx *ctx, const uint32_t *s
     }
     return band_run(ctx, sig, n, bands, rows, bucket_cap, donor, pairs_out, pairs_capacity, nullptr,
                     reinterpret_cast<unsigned long long *>(d_num_pairs));
+}
+
+// ---------------------------------------------------------------------------
+// Streamed candidates: the chunk structure is built once and kept in the
+// stream's own device memory; every call emits, in lexicographic order, the
+// owned pairs among the next block of raw pairs (at most `capacity` of them,
+// so the batch always fits).  Ownership is decided against all bands, so the
+// batches partition C: every pair of C comes out exactly once.
+// ---------------------------------------------------------------------------
+struct subquad_band_stream {
+    int device = 0;
+    void *mem = nullptr;
+    BandIndex index;
+    uint64_t next = 0, total = 0;
+};
+
+extern "C" int subquad_band_stream_create(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows,
+                                          int32_t bucket_cap, const int32_t *donor, subquad_band_stream **out,
+                                          uint64_t *total_raw_out)
+{
+    SQ_ENTER(ctx);
+    if (!out) return SUBQUAD_ERR_ARG;
+    *out = nullptr;
+    if (total_raw_out) *total_raw_out = 0;
+    SQ_TRY(band_args(n, bands, rows, 0, sig, nullptr));
+    auto *st = new (std::nothrow) subquad_band_stream;
+    if (!st) return SUBQUAD_ERR_NOMEM;
+    st->device = ctx->device;
+    if (n >= 2) {
+        SqArena m(nullptr);
+        take_index(m, n, bands);
+        if (cudaMalloc(&st->mem, m.off) != cudaSuccess) {
+            cudaGetLastError();
+            delete st;
+            return SUBQUAD_ERR_NOMEM;
+        }
+        SqArena a(st->mem);
+        st->index = take_index(a, n, bands);
+        GroupScratch S = plan_group(ctx, n, bands);
+        {
+            SqArena measure(nullptr);
+            take_group(measure, S);
+            const int rc = sq_scratch_reserve(ctx, measure.off);
+            if (rc != SUBQUAD_OK) {
+                cudaFree(st->mem);
+                delete st;
+                return rc;
+            }
+        }
+        SqArena arena(ctx->scratch);
+        take_group(arena, S);
+        const int cap = (bucket_cap <= 0 || bucket_cap >= n) ? 0 : bucket_cap;
+        int rc = band_index_build(ctx, sig, rows, cap, donor, st->index, S);
+        uint64_t total = 0;
+        if (rc == SUBQUAD_OK) {
+            // (subquad_check reuses the first staging word: read the total first)
+            rc = cudaMemcpyAsync(ctx->h_pinned + 2, st->index.counters + 1, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                 ctx->stream) == cudaSuccess &&
+                         cudaStreamSynchronize(ctx->stream) == cudaSuccess
+                     ? SUBQUAD_OK
+                     : SUBQUAD_ERR_CUDA;
+            total = ctx->h_pinned[2];
+            if (rc == SUBQUAD_OK) rc = subquad_check(ctx);
+        }
+        if (rc != SUBQUAD_OK) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(st->mem);
+            delete st;
+            return rc;
+        }
+        st->total = total;
+    }
+    if (total_raw_out) *total_raw_out = st->total;
+    *out = st;
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_band_stream_next(subquad_ctx *ctx, subquad_band_stream *st, uint32_t *pairs_out,
+                                        int64_t capacity, int64_t *num_pairs_out, int *done)
+{
+    SQ_ENTER(ctx);
+    if (!st || !num_pairs_out || !done) return SUBQUAD_ERR_ARG;
+    *num_pairs_out = 0;
+    *done = 0;
+    if (st->device != ctx->device || capacity < 32 || capacity >= (int64_t)0xffffffffLL || !pairs_out ||
+        reinterpret_cast<uintptr_t>(pairs_out) % 8)
+        return SUBQUAD_ERR_ARG;
+    if (st->next >= st->total) {
+        *done = 1;
+        return SUBQUAD_OK;
+    }
+    const uint64_t batch = (uint64_t)capacity & ~31ull;  // owned <= raw: the batch fits
+    const BandIndex &I = st->index;
+    EmitScratch E;
+    {
+        SqArena measure(nullptr);
+        take_emit(measure, E, I.n, capacity, nullptr, 0);
+        SQ_TRY(sq_scratch_reserve(ctx, measure.off));
+    }
+    SqArena arena(ctx->scratch);
+    take_emit(arena, E, I.n, capacity, nullptr, 0);
+    SQ_TRY(band_emit_sorted(ctx, I, st->next, st->next + batch, pairs_out, capacity, nullptr, E));
+    SQ_TRY_CUDA(
+        cudaMemcpyAsync(ctx->h_pinned + 2, ctx->d_small, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int64_t count = (int64_t)ctx->h_pinned[2];  // read before subquad_check reuses the staging words
+    SQ_TRY(subquad_check(ctx));
+    *num_pairs_out = count;
+    st->next += batch;
+    *done = st->next >= st->total ? 1 : 0;
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_band_stream_reset(subquad_band_stream *st)
+{
+    if (!st) return SUBQUAD_ERR_ARG;
+    st->next = 0;
+    return SUBQUAD_OK;
+}
+
+extern "C" void subquad_band_stream_destroy(subquad_band_stream *st)
+{
+    if (!st) return;
+    if (st->mem) {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        cudaSetDevice(st->device);
+        cudaFree(st->mem);
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    delete st;
 }

@@ -61,6 +61,11 @@ SIGNATURES = {
     "subquad_band_candidates": (_c.c_int, [_P, _P, _I64, _c.c_int, _c.c_int, _c.c_int32, _P, _I64,
                                            _c.POINTER(_I64)]),
     "subquad_band_candidates_async": (_c.c_int, [_P, _P, _I64, _c.c_int, _c.c_int, _c.c_int32, _P, _P, _I64, _P]),
+    "subquad_band_stream_create": (_c.c_int, [_P, _P, _I64, _c.c_int, _c.c_int, _c.c_int32, _P, _c.POINTER(_P),
+                                              _c.POINTER(_c.c_uint64)]),
+    "subquad_band_stream_next": (_c.c_int, [_P, _P, _P, _I64, _c.POINTER(_I64), _c.POINTER(_c.c_int)]),
+    "subquad_band_stream_reset": (_c.c_int, [_P]),
+    "subquad_band_stream_destroy": (None, [_P]),
     "subquad_align_score_binned_async": (_c.c_int, [_P, _P, _c.c_int, _P, _P, _I64, _c.c_int, _c.c_int, _P]),
     "subquad_fuse_forward_async": (_c.c_int, [_P, _P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P, _c.c_int,
                                               _P, _P]),
@@ -266,6 +271,29 @@ class Context:
         _check(lib().subquad_band_candidates_async(self.handle, _ptr(sig), n, bands, rows, bucket_cap, _ptr(donor),
                                                    _ptr(pairs_out), int(pairs_out.shape[0]), _ptr(d_num_pairs)),
                "subquad_band_candidates_async")
+
+    def band_stream(self, sig, n: int, bands: int, rows: int, bucket_cap: int = 0, donor=None,
+                    capacity: int = 1 << 22):
+        """Streamed candidates: yields int32 [k, 2] device tensors (each sorted
+        lexicographically; together exactly the pairs of
+        band_candidates_async).  A buffer of ``capacity`` pairs is reused:
+        consume (or copy) each batch before asking for the next."""
+        torch = self.torch
+        handle = _P()
+        total = _c.c_uint64(0)
+        _check(lib().subquad_band_stream_create(self.handle, _ptr(sig), n, bands, rows, bucket_cap, _ptr(donor),
+                                                _c.byref(handle), _c.byref(total)), "subquad_band_stream_create")
+        buf = self._empty((capacity, 2), torch.int32)
+        try:
+            done = _c.c_int(0)
+            while not done.value:
+                count = _I64(0)
+                _check(lib().subquad_band_stream_next(self.handle, handle, _ptr(buf), capacity, _c.byref(count),
+                                                      _c.byref(done)), "subquad_band_stream_next")
+                if count.value:
+                    yield buf[:count.value]
+        finally:
+            lib().subquad_band_stream_destroy(handle)
 
     def align_score_binned_async(self, packed, pairs, d_m, out, gap_open: int = 10, gap_extend: int = 1):
         _check(lib().subquad_align_score_binned_async(self.handle, _ptr(packed), int(packed.shape[1]), _ptr(pairs),
