@@ -37,6 +37,10 @@ TINY = Workload("tiny_1k", 1000)
 # one donor of 1,000,000 sequences, 20,000 families of 25, 50 rare subgroups,
 # the same hashing with buckets capped at 2,048
 DONOR_1M = Workload("donor_1m", 1_000_000, bucket_cap=2048)
+# 10,000,000 sequences of lengths 6-30 with Zipf(1.2) family sizes up to
+# 50,000 (ragged buckets, no cap), 128 hashes in 32 bands of 4: a candidate set
+# of ~1e10 pairs, processed as a stream of batches
+ZIPF_10M = Workload("zipf_10m", 10_000_000, bands=32, rows=4, pack_stride=32)
 
 
 class Pipeline:
@@ -180,3 +184,81 @@ class BatchedPipeline:
         m = int(self.num_pairs.item())
         return dict(pairs=self.pairs[:m].cpu().numpy().view(np.uint32), sw=self.sw[:m].cpu().numpy(),
                     fused=self.fused[:m].cpu().numpy(), self=self.self_sc.cpu().numpy(), m=m)
+
+
+class StreamedPipeline:
+    """Candidate sets larger than one buffer: pack, sign and self-scores once,
+    the band index once, then the candidates in batches of at most
+    ``batch_capacity`` pairs, each aligned (length-binned) and fused.  Each
+    batch is handed to the caller as device tensors (pairs, sw, fused) valid
+    until the next batch; together the batches hold every candidate pair
+    exactly once."""
+
+    def __init__(self, ctx, cfg: Workload, n: int, batch_capacity: int):
+        torch = ctx.torch
+        self.ctx, self.cfg, self.n, self.capacity = ctx, cfg, n, batch_capacity
+        dev = ctx.device
+        self.packed = torch.empty((n, cfg.pack_stride), dtype=torch.uint8, device=dev)
+        self.sig = torch.empty((cfg.bands, n, cfg.rows), dtype=torch.int32, device=dev)
+        self.self_sc = torch.empty((n,), dtype=torch.int32, device=dev)
+        self.pairs = torch.empty((batch_capacity, 2), dtype=torch.int32, device=dev)
+        self.sw = torch.empty((batch_capacity,), dtype=torch.int32, device=dev)
+        self.fused = torch.empty((batch_capacity,), dtype=torch.float32, device=dev)
+        self.stream = None
+        self.total_raw = 0
+
+    def prepare(self, x, marks=None):
+        """Pack, sign, self-scores and the band index (synchronises once).
+        Returns the number of raw pairs (an upper bound of |C|)."""
+        import ctypes
+
+        from . import subquad
+
+        ctx, cfg, n = self.ctx, self.cfg, self.n
+        mark = marks or (lambda name: None)
+        lib, P = subquad.lib(), subquad._ptr
+        self.close()
+        subquad._check(lib.subquad_pack(ctx.handle, P(x["codes"]), int(x["codes"].shape[1]), P(x["lens"]), n,
+                                        cfg.pack_stride, P(self.packed)), "subquad_pack")
+        subquad._check(lib.subquad_sign(ctx.handle, P(self.packed), cfg.pack_stride, n, cfg.k, cfg.bands, cfg.rows,
+                                        P(x["a"]), P(x["b"]), P(self.sig)), "subquad_sign")
+        mark("sign")
+        ctx.self_scores(self.packed, cfg.gap_open, cfg.gap_extend, out=self.self_sc, binned=True)
+        handle, total = ctypes.c_void_p(), ctypes.c_uint64(0)
+        subquad._check(lib.subquad_band_stream_create(ctx.handle, P(self.sig), n, cfg.bands, cfg.rows,
+                                                      cfg.bucket_cap, P(x.get("donor")), ctypes.byref(handle),
+                                                      ctypes.byref(total)), "subquad_band_stream_create")
+        self.stream, self.total_raw = handle, int(total.value)
+        mark("index")
+        return self.total_raw
+
+    def batches(self, x, max_batches=None):
+        """Yields (pairs, sw, fused) for each non-empty batch."""
+        import ctypes
+
+        from . import subquad
+
+        ctx, cfg = self.ctx, self.cfg
+        lib = subquad.lib()
+        done, k = ctypes.c_int(0), 0
+        while not done.value and (max_batches is None or k < max_batches):
+            count = ctypes.c_int64(0)
+            subquad._check(lib.subquad_band_stream_next(ctx.handle, self.stream, subquad._ptr(self.pairs),
+                                                        self.capacity, ctypes.byref(count), ctypes.byref(done)),
+                           "subquad_band_stream_next")
+            k += 1
+            m = int(count.value)
+            if m == 0:
+                continue
+            pairs = self.pairs[:m]
+            sw = ctx.align_score(self.packed, pairs, cfg.gap_open, cfg.gap_extend, out=self.sw[:m], binned=True)
+            fused = ctx.fuse_forward(pairs, sw, self.self_sc, self.packed, x["emb"], x["params"], cfg.hidden,
+                                     out=self.fused[:m])
+            yield pairs, sw, fused
+
+    def close(self):
+        if self.stream is not None:
+            from . import subquad
+
+            subquad.lib().subquad_band_stream_destroy(self.stream)
+            self.stream = None

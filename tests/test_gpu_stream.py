@@ -97,3 +97,42 @@ def test_stream_argument_checks(ctx, torch):
     finally:
         lib.subquad_band_stream_destroy(h)
     lib.subquad_band_stream_destroy(None)
+
+
+def test_streamed_pipeline_matches_one_pass(ctx, torch, oracle_mod):
+    """Zipf families (ragged buckets, no cap), lengths 6-30, 32 bands of 4:
+    the streamed pipeline's batches, put together, carry the same pairs,
+    scores and fused values as one unbatched pass."""
+    from paper_2602_17330_gb300 import pipeline
+
+    cfg = pipeline.Workload("zipf_small", 30_000, bands=32, rows=4, pack_stride=32)
+    rep = synth.zipf_repertoire(cfg.n, seed=3, hi=400)
+    a, b = synth.hash_coefficients(cfg.hashes, seed=3)
+    emb = synth.unit_embeddings(rep.n, cfg.d, seed=3)
+    params = synth.gate_parameters(cfg.hidden, seed=3)
+    one = pipeline.Pipeline(ctx, cfg)
+    x = one.upload(rep, a, b, emb, params)
+    ref = one.forward(x)
+    want_pairs = to_np(ref["pairs"]).view(np.uint32)
+    want_sw, want_f = to_np(ref["sw"]), to_np(ref["fused"])
+    sp = pipeline.StreamedPipeline(ctx, cfg, rep.n, batch_capacity=40_000)
+    total = sp.prepare(x)
+    assert total >= want_pairs.shape[0]
+    got_p, got_s, got_f, nb = [], [], [], 0
+    for pairs, sw, fused in sp.batches(x):
+        got_p.append(to_np(pairs).view(np.uint32).copy())
+        got_s.append(to_np(sw).copy())
+        got_f.append(to_np(fused).copy())
+        nb += 1
+    sp.close()
+    ctx.check()
+    assert nb > 3
+    gp, gs, gf = np.concatenate(got_p), np.concatenate(got_s), np.concatenate(got_f)
+    key = gp[:, 0].astype(np.uint64) << np.uint64(32) | gp[:, 1].astype(np.uint64)
+    order = np.argsort(key)
+    assert (gp[order] == want_pairs).all()
+    assert (gs[order] == want_sw).all()
+    assert np.allclose(gf[order], want_f, rtol=1e-6, atol=1e-7)
+    # the candidate set itself against the oracle
+    want = oracle_mod.candidates(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), 32, 4, 0)
+    assert want.shape == want_pairs.shape and (want == want_pairs).all()
