@@ -57,6 +57,8 @@ def parse_args():
                    help="sequences of the streamed Zipf workload (0: skip the streamed measurement)")
     p.add_argument("--stream-batches", type=int, default=16, help="candidate batches timed in the streamed run")
     p.add_argument("--stream-capacity", type=int, default=8_000_000, help="pairs per streamed batch")
+    p.add_argument("--no-train", action="store_true", help="skip the gate-training measurement")
+    p.add_argument("--no-topk", action="store_true", help="skip the cross-donor top-k measurement")
     p.add_argument("--cpu-sample-n", type=int, default=500_000, help="oracle sample for the cpu_baseline key")
     p.add_argument("--ref-sample-n", type=int, default=200_000, help="oracle sample per step of --impl reference")
     return p.parse_args()
@@ -324,9 +326,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         graph = {"value": m / (g_ms / 1e3) * world, "unit": UNIT, "ms_per_step": g_ms,
                  "note": "the timed step captured once as a CUDA graph and replayed"}
 
-    stream_res = None
-    if args.stream_n > 0 and rank == 0 and world == 1:
-        stream_res = run_stream(args, ctx, stream, dev, flush)
+    stream_res = train_res = topk_res = None
+    if rank == 0 and world == 1:
+        if not args.no_train:
+            train_res = run_train(args, ctx, stream, rep, step_pipe, m)
+        if not args.no_topk:
+            topk_res = run_topk(args, ctx, stream)
+        if args.stream_n > 0:
+            stream_res = run_stream(args, ctx, stream, dev, flush)
 
     # roofline of the dominant kernel, from the library's live per-kernel event
     # timings over the timed region (same stream as the launches)
@@ -407,10 +414,112 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "sw_gcups_plain": cells / (sw_ms["plain"] / 1e3) / 1e9,
             "sw_gcups_binned": cells / (sw_ms["binned"] / 1e3) / 1e9,
             "stages_ms": stage_ms, "kernel_rooflines": stage_roof, "wall_s": wall, "autotune": tuning["choice"],
-            "graph": graph, "stream": stream_res,
+            "graph": graph, "train": train_res, "topk": topk_res, "stream": stream_res,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
+
+
+def run_train(args, ctx, stream, rep, step_pipe, m):
+    """Gate training on the 1M donor's candidate list: the first 4,000,000
+    pairs, family-correlated embeddings (d = 128, trained), gate 3-32-1;
+    one step = fused forward + weighted BCE + adjoint (parameters and
+    embeddings) + Adam, full batch, all on the device."""
+    import numpy as np
+    import torch
+
+    from paper_2602_17330_gb300 import synth
+    from paper_2602_17330_gb300.train import GateTrainer
+
+    d, hidden, mt = 128, 32, min(4_000_000, m)
+    with torch.cuda.stream(stream):
+        pairs = step_pipe.pairs[:mt]
+        sw = step_pipe.sw[:mt]
+        emb = torch.from_numpy(synth.family_embeddings(rep.family, d, seed=1)).to(ctx.device)
+        params = torch.from_numpy(synth.gate_parameters(hidden, seed=1)).to(ctx.device)
+        label, group = ctx.pair_labels(pairs, torch.from_numpy(rep.family), torch.from_numpy(rep.subgroup))
+        weight = ctx.pair_weights(group, int(rep.subgroup.max()) + 1)
+        tr = GateTrainer(ctx, pairs, sw, step_pipe.self_sc, step_pipe.packed, emb, params, hidden, label, weight)
+        for _ in range(3):
+            tr.step()
+        stream.synchronize()
+        loss0 = float(tr.loss.item())
+        steps = 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            tr.step()
+        e1.record(stream)
+        stream.synchronize()
+    ctx.check()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": f"first {mt:,} candidate pairs of the 1M donor, d={d} (trained), gate 3-{hidden}-1, "
+                        "weighted BCE, Adam lr 1e-3, full batch",
+            "ms_per_step": ms, "pairs_per_s": mt / (ms / 1e3), "loss_first": loss0, "loss_last": float(tr.loss.item())}
+
+
+def run_topk(args, ctx, stream):
+    """Cross-donor top-50 retrieval on pooled donors (16 donors of 50k-200k
+    sequences, 500 public families at 0.01-1% per donor): banding over the
+    pooled sequences, batched alignment, top-50 of other-donor candidates for
+    100,000 queries; recall@50 (ties counted) against the exhaustive top-50
+    for 1,000 public-family queries."""
+    import numpy as np
+    import torch
+
+    from paper_2602_17330_gb300 import pipeline, synth
+
+    rep = synth.pooled_repertoire(16, 50_000, 200_000, seed=5)
+    cfg = pipeline.Workload("pooled", rep.n)
+    a, b = synth.hash_coefficients(cfg.hashes, seed=5)
+    bp = pipeline.BatchedPipeline(ctx, cfg, rep.n, capacity=8 * rep.n)
+    with torch.cuda.stream(stream):
+        x = {"codes": torch.from_numpy(rep.codes).to(ctx.device), "lens": torch.from_numpy(rep.lens).to(ctx.device),
+             "a": torch.from_numpy(a.view(np.int32)).to(ctx.device), "b": torch.from_numpy(b.view(np.int32)).to(ctx.device),
+             "emb": torch.from_numpy(synth.unit_embeddings(rep.n, cfg.d, seed=5)).to(ctx.device),
+             "params": torch.from_numpy(synth.gate_parameters(cfg.hidden, seed=5)).to(ctx.device)}
+        bp.step(x)  # banding over the pooled donors (no donor confinement: cross-donor pairs are the point)
+        x["donor"] = torch.from_numpy(rep.donor).to(ctx.device)
+        stream.synchronize()
+        ctx.check()
+        mq = int(bp.num_pairs.item())
+        pairs, scores = bp.pairs[:mq], bp.sw[:mq]
+        queries = torch.from_numpy(synth.sample_queries(rep.n, 100_000, seed=5).view(np.int32)).to(ctx.device)
+        index = ctx.pair_index(pairs, rep.n)
+        ctx.topk_candidates(pairs, scores, rep.n, x["donor"], queries, 50, index=index)  # warm
+        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        e0.record(stream)
+        index = ctx.pair_index(pairs, rep.n)
+        e1.record(stream)
+        ids, sc = ctx.topk_candidates(pairs, scores, rep.n, x["donor"], queries, 50, index=index)
+        e2.record(stream)
+        # recall on 1,000 queries drawn from the public families (the sequences
+        # that have relatives in other donors)
+        public = np.flatnonzero((rep.family >= 0) & (rep.family < 500))
+        rq = np.sort(np.random.default_rng(5).choice(public, size=min(1000, public.size), replace=False))
+        sub = torch.from_numpy(rq.astype(np.int32)).to(ctx.device)
+        ids_p, sc_p = ctx.topk_candidates(pairs, scores, rep.n, x["donor"], sub, 50, index=index)
+        e2b = torch.cuda.Event(enable_timing=True)
+        e2b.record(stream)
+        _, sc_b = ctx.topk_bruteforce(bp.packed, x["donor"], sub, 50)
+        e3.record(stream)
+        stream.synchronize()
+    ctx.check()
+    got = sc_p.cpu().numpy()
+    best = sc_b.cpu().numpy()
+    thr = best[:, 49]  # 50th-best exhaustive score (-1: fewer than 50 other-donor sequences)
+    hit = ((got >= thr[:, None]) & (got >= 0)).sum(1)
+    recall = float(np.minimum(hit, 50).mean() / 50.0)
+    with_cand = float((sc[:, 0] >= 0).float().mean().item())
+    return {"workload": f"{rep.n:,} sequences pooled from 16 donors (50k-200k each), 500 public families; "
+                        f"{mq:,} candidate pairs over the pooled donors; 100,000 queries, k = 50",
+            "pair_index_ms": e0.elapsed_time(e1), "topk_ms": e1.elapsed_time(e2),
+            "queries_per_s": 100_000 / (e1.elapsed_time(e2) / 1e3),
+            "bruteforce_1000_queries_ms": e2b.elapsed_time(e3),
+            "queries_with_cross_donor_candidates": with_cand,
+            "recall_at_50_public_queries": recall,
+            "recall_note": "tie-aware recall@50 of the candidate route against the exhaustive top-50 (other donors), "
+                           "on 1,000 queries drawn from public-family members"}
 
 
 def run_stream(args, ctx, stream, dev, flush):
