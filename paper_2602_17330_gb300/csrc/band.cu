@@ -929,7 +929,7 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
 // Every count stays on the device.
 constexpr int kRowSmall = 32;
 constexpr int kRowWarp = 256;   // rows up to this size: one warp, registers
-constexpr int kRowMid = 8192;   // rows up to this size: one CTA, shared memory
+constexpr int kRowMid = 8192;   // rows up to this size: one CTA, radix sort in shared memory
 constexpr int kRowThreads = 256;
 
 __device__ __forceinline__ uint64_t row_end(const uint32_t *rowoff, int64_t n, uint64_t m, int64_t i)
@@ -1095,8 +1095,14 @@ __global__ void __launch_bounds__(kRowThreads) rows_sort_warp_kernel(const uint3
     }
 }
 
-// one CTA per row of kRowWarp+1..kRowMid partners (listed from the back of
-// `mid`): bitonic sort of the row, padded to a power of two, in shared memory
+// One CTA per row of kRowWarp+1..kRowMid partners (listed from the back of
+// `mid`): LSD radix sort in shared memory of the keys v - (i + 1) < n, 8-bit
+// digits, as many passes as n needs.  Each pass: every warp counts the digits
+// of its contiguous slice, one scan over (digit, warp) gives stable bases,
+// then every warp scatters its slice in order, ranking equal digits within a
+// round of 32 by one ballot per digit bit.
+constexpr int kRadixWarps = kRowThreads / 32;
+
 __global__ void __launch_bounds__(kRowThreads) rows_sort_mid_kernel(const uint32_t *__restrict__ rowoff, int64_t n,
                                                                     const unsigned long long *__restrict__ d_m,
                                                                     const uint32_t *__restrict__ mid,
@@ -1104,32 +1110,85 @@ __global__ void __launch_bounds__(kRowThreads) rows_sort_mid_kernel(const uint32
                                                                     const uint32_t *__restrict__ col,
                                                                     uint32_t *__restrict__ out)
 {
-    __shared__ uint32_t s[kRowMid];
+    extern __shared__ uint32_t s_rs[];  // [2][kRowMid] keys, then [kRadixWarps][256] counts
+    uint32_t *bufA = s_rs, *bufB = s_rs + kRowMid, *wcnt = s_rs + 2 * kRowMid;
+    __shared__ uint32_t s_dtot[256];
     const uint64_t m = *d_m, nmid = *d_mid;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lt = (1u << lane) - 1u;
     for (uint64_t r = blockIdx.x; r < nmid; r += gridDim.x) {
         const uint32_t i = mid[n - 1 - (int64_t)r];
         const uint64_t r0 = rowoff[i];
         const uint32_t d = (uint32_t)(row_end(rowoff, n, m, i) - r0);
-        uint32_t P2 = 64;
-        while (P2 < d) P2 <<= 1;
-        for (uint32_t t = threadIdx.x; t < P2; t += blockDim.x) s[t] = t < d ? col[r0 + t] : 0xffffffffu;
-        __syncthreads();
-        for (uint32_t k = 2; k <= P2; k <<= 1)
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                const uint32_t lj = 31 - __clz(j);
-                for (uint32_t t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
-                    const uint32_t a = ((t >> lj) << (lj + 1)) + (t & (j - 1)), b = a + j;
-                    const uint32_t x = s[a], y = s[b];
-                    const bool asc = (a & k) == 0;
-                    if (asc ? x > y : x < y) {
-                        s[a] = y;
-                        s[b] = x;
+        const uint32_t lo = i + 1;  // every partner is above i
+        const uint32_t range = (uint32_t)n - lo;
+        const int nbits = range > 1 ? 32 - __clz(range - 1) : 1;
+        for (uint32_t t = threadIdx.x; t < d; t += blockDim.x) bufA[t] = col[r0 + t] - lo;
+        // warp slices of whole rounds of 32
+        const uint32_t slice = ((d + kRadixWarps * 32 - 1) / (kRadixWarps * 32)) * 32;
+        const uint32_t s0 = warp * slice, s1 = min(d, s0 + slice);
+        for (int shift = 0; shift < nbits; shift += 8) {
+            for (uint32_t t = threadIdx.x; t < kRadixWarps * 256; t += blockDim.x) wcnt[t] = 0;
+            __syncthreads();
+            uint32_t *wc = wcnt + warp * 256;
+            for (uint32_t t = s0 + lane; t < s1; t += 32) atomicAdd(&wc[(bufA[t] >> shift) & 255u], 1u);
+            __syncthreads();
+            {
+                // thread = digit: exclusive over warps, then over digits
+                const uint32_t dg = threadIdx.x;
+                uint32_t run = 0;
+#pragma unroll
+                for (int w = 0; w < kRadixWarps; ++w) {
+                    const uint32_t c = wcnt[w * 256 + dg];
+                    wcnt[w * 256 + dg] = run;
+                    run += c;
+                }
+                s_dtot[dg] = run;
+                __syncthreads();
+                if (warp == 0) {
+                    uint32_t carry = 0;
+                    for (int base = 0; base < 256; base += 32) {
+                        const uint32_t v = s_dtot[base + lane];
+                        uint32_t inc = v;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                            if ((int)lane >= o) inc += y;
+                        }
+                        s_dtot[base + lane] = carry + inc - v;
+                        carry += __shfl_sync(0xffffffffu, inc, 31);
                     }
                 }
                 __syncthreads();
+                const uint32_t dbase = s_dtot[dg];
+#pragma unroll
+                for (int w = 0; w < kRadixWarps; ++w) wcnt[w * 256 + dg] += dbase;
             }
+            __syncthreads();
+            for (uint32_t t0 = s0; t0 < s1; t0 += 32) {
+                const uint32_t t = t0 + lane;
+                const bool valid = t < s1;
+                const uint32_t key = valid ? bufA[t] : 0u;
+                const uint32_t dgt = valid ? (key >> shift) & 255u : 256u;
+                uint32_t peers = 0xffffffffu;
+#pragma unroll
+                for (int bit = 0; bit < 9; ++bit) {
+                    const uint32_t mb = __ballot_sync(0xffffffffu, (dgt >> bit) & 1u);
+                    peers &= ((dgt >> bit) & 1u) ? mb : ~mb;
+                }
+                const uint32_t before = __popc(peers & lt);
+                const uint32_t base = valid ? wc[dgt] : 0u;
+                __syncwarp();
+                if (valid && before == 0) wc[dgt] = base + __popc(peers);
+                __syncwarp();
+                if (valid) bufB[base + before] = key;
+            }
+            __syncthreads();
+            uint32_t *tmp = bufA;
+            bufA = bufB;
+            bufB = tmp;
+        }
         for (uint32_t t = threadIdx.x; t < d; t += blockDim.x)
-            reinterpret_cast<uint2 *>(out)[r0 + t] = make_uint2(i, s[t]);
+            reinterpret_cast<uint2 *>(out)[r0 + t] = make_uint2(i, bufA[t] + lo);
         __syncthreads();
     }
 }
@@ -1387,8 +1446,11 @@ int band_emit_sorted(subquad_ctx *ctx, const BandIndex &I, uint64_t raw0, uint64
     rows_sort_warp_kernel<<<(unsigned)ctx->num_sms * 8, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.mid,
                                                                                       d_wrows, E.col, pairs_out);
     SQ_LAUNCH_CHECK();
-    rows_sort_mid_kernel<<<(unsigned)ctx->num_sms * 4, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.mid,
-                                                                                     d_mid, E.col, pairs_out);
+    constexpr size_t kRadixSmem = (2 * (size_t)kRowMid + (size_t)kRadixWarps * 256) * sizeof(uint32_t);
+    SQ_TRY_CUDA(cudaFuncSetAttribute(rows_sort_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRadixSmem));
+    rows_sort_mid_kernel<<<(unsigned)ctx->num_sms * 3, kRowThreads, kRadixSmem, ctx->stream>>>(
+        E.rowoff, n, d_clamped, E.mid, d_mid, E.col, pairs_out);
     SQ_LAUNCH_CHECK();
     rows_sort_long_kernel<<<(unsigned)ctx->num_sms, 1024, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.lng, d_long,
                                                                            E.col, pairs_out);
