@@ -361,7 +361,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     }
     kernel_names = {"sign": "sign_kernel", "band_partition": "part_hist_kernel + scan + part_scatter_kernel",
                     "band_group": "part_group_kernel",
-                    "band_emit": "chunk pair-count scan + band_emit_kernel", "band_pairsort": "pair radix sort",
+                    "band_emit": "chunk pair-count scan + band_emit_kernel", "band_pairsort": "row counting + per-row sorts (registers, warp, CTA radix)",
                     "align": "align_binned_kernel" if cfg.binned else "align_plain_kernel",
                     "align_bin": "bin_count/offsets/scatter", "self": "self_diag_kernel",
                     "fuse": "fuse_forward_kernel"}

@@ -165,9 +165,6 @@ size_t sq_scan_tmp_bytes(int64_t count);
 int sq_radix_sort_u32(subquad_ctx *ctx, uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       int64_t count, const uint32_t *d_count, int begin_bit, int end_bit, bool *result_in_alt,
                       void *tmp, size_t tmp_bytes);
-// Stable LSD radix sort of uint64 keys on bits [begin_bit, end_bit).
-int sq_radix_sort_u64(subquad_ctx *ctx, uint64_t *keys, uint64_t *keys_alt, int64_t count, const uint32_t *d_count,
-                      int begin_bit, int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes);
 size_t sq_radix_tmp_bytes(int64_t count);
 
 // Lane-replicated alignment score table for the context's matrix and gap_open

@@ -1,4 +1,5 @@
-// Device-wide scan and stable LSD radix sort used by the banding stage.
+// Device-wide scan (banding, binning) and stable LSD radix sort (pair index of
+// the gate training).
 //
 // Scan: one pass over tiles of 4096 elements (256 threads x 16) with
 // decoupled look-back between tiles.  Radix sort: 8-bit digits; per pass
@@ -345,178 +346,6 @@ int radix_impl(subquad_ctx *ctx, K *keys, uint32_t *vals, K *keys_alt, uint32_t 
     return SUBQUAD_OK;
 }
 
-// ---------------------------------------------------------------------------
-// One-sweep LSD radix sort of uint64 keys (host-known count).
-//   1. one pass over the keys builds the digit histograms of every pass;
-//   2. one block scans them into per-pass digit bases;
-//   3. per pass, one kernel: each block takes the next tile from an atomic
-//      counter (so every earlier tile is owned by a running block), ranks its
-//      keys per digit with warp match, publishes its per-digit counts, looks
-//      back over earlier tiles' published counts (a tile that has its full
-//      prefix ends the walk) to get its exclusive prefix per digit, publishes
-//      its own inclusive prefix and scatters.  Each pass reads and writes the
-//      keys once.  Spins on an unpublished tile are bounded; running out sets
-//      the TIMEOUT error bit instead of waiting forever.
-// ---------------------------------------------------------------------------
-constexpr int kOsThreads = 256;
-constexpr int kOsItems = 16;  // per thread
-constexpr int kOsTile = kOsThreads * kOsItems;
-constexpr uint32_t kOsAgg = 1u << 30;     // status: tile count published
-constexpr uint32_t kOsPrefix = 2u << 30;  // status: inclusive prefix published
-constexpr uint32_t kOsValue = (1u << 30) - 1u;
-constexpr int kOsMaxPasses = 8;
-constexpr long long kOsSpinLimit = 1ll << 24;
-
-__global__ void __launch_bounds__(kOsThreads) onesweep_hist_kernel(const uint64_t *__restrict__ keys, int64_t count,
-                                                                   int begin_bit, int passes,
-                                                                   uint32_t *__restrict__ hist)
-{
-    __shared__ uint32_t s_hist[kOsMaxPasses][kRadix];
-    for (int q = threadIdx.x; q < kOsMaxPasses * kRadix; q += blockDim.x) (&s_hist[0][0])[q] = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < count; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = base + threadIdx.x;
-        const bool valid = g < count;
-        const uint64_t k = valid ? keys[g] : 0ull;
-        for (int ps = 0; ps < passes; ++ps) {
-            const uint32_t d = valid ? (uint32_t)(k >> (begin_bit + 8 * ps)) & 0xffu : 0xffffu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_hist[ps][d], (uint32_t)__popc(peers));
-        }
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < passes * kRadix; q += blockDim.x) {
-        const uint32_t v = (&s_hist[0][0])[q];
-        if (v) atomicAdd(&hist[q], v);
-    }
-}
-
-__global__ void __launch_bounds__(kRadix) onesweep_bases_kernel(uint32_t *__restrict__ hist, int passes)
-{
-    for (int ps = 0; ps < passes; ++ps) {
-        uint32_t *h = hist + ps * kRadix;
-        uint32_t total;
-        const uint32_t v = h[threadIdx.x];
-        const uint32_t exc = block_exclusive<uint32_t, false>(v, &total);
-        h[threadIdx.x] = exc;
-        __syncthreads();
-    }
-}
-
-__global__ void __launch_bounds__(kOsThreads) onesweep_pass_kernel(const uint64_t *__restrict__ keys_in,
-                                                                   uint64_t *__restrict__ keys_out, int64_t count,
-                                                                   int shift, const uint32_t *__restrict__ bases,
-                                                                   uint32_t *__restrict__ status,
-                                                                   uint32_t *__restrict__ tile_counter, uint32_t *err)
-{
-    __shared__ uint32_t s_wcnt[kOsThreads / 32][kRadix];
-    __shared__ uint32_t s_excl[kRadix];
-    __shared__ uint32_t s_tile;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
-    for (int q = threadIdx.x; q < (kOsThreads / 32) * kRadix; q += blockDim.x) (&s_wcnt[0][0])[q] = 0;
-    __syncthreads();
-    const uint32_t t = s_tile;
-    const int64_t wbase = (int64_t)t * kOsTile + warp * 32 * kOsItems;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    uint64_t key[kOsItems];
-    uint32_t dig[kOsItems], rank[kOsItems];
-#pragma unroll
-    for (int r = 0; r < kOsItems; ++r) {
-        const int64_t g = wbase + r * 32 + lane;
-        const bool valid = g < count;
-        key[r] = valid ? keys_in[g] : 0ull;
-        dig[r] = valid ? (uint32_t)(key[r] >> shift) & 0xffu : 0xffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
-        const uint32_t before = __popc(peers & lt_mask);
-        const uint32_t base = valid ? s_wcnt[warp][dig[r]] : 0u;
-        rank[r] = base + before;
-        __syncwarp();
-        if (valid && before == 0) s_wcnt[warp][dig[r]] = base + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    // thread d: exclusive prefix over warps, tile count, publish, look back
-    {
-        const int d = threadIdx.x;
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < kOsThreads / 32; ++w) {
-            const uint32_t c = s_wcnt[w][d];
-            s_wcnt[w][d] = run;
-            run += c;
-        }
-        uint32_t *mine = status + (size_t)t * kRadix + d;
-        uint32_t excl = 0;
-        if (t == 0) {
-            atomicExch(mine, kOsPrefix | run);
-        } else {
-            atomicExch(mine, kOsAgg | run);
-            long long spins = 0;
-            for (int64_t j = (int64_t)t - 1; j >= 0;) {
-                const uint32_t v = *(volatile const uint32_t *)(status + (size_t)j * kRadix + d);
-                if (v & kOsPrefix) {
-                    excl += v & kOsValue;
-                    break;
-                }
-                if (v & kOsAgg) {
-                    excl += v & kOsValue;
-                    --j;
-                    continue;
-                }
-                if (++spins > kOsSpinLimit) {
-                    atomicOr(err, SQ_DEVERR_TIMEOUT);
-                    break;
-                }
-            }
-            atomicExch(mine, kOsPrefix | (excl + run));
-        }
-        s_excl[d] = bases[d] + excl;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kOsItems; ++r) {
-        if (dig[r] < (uint32_t)kRadix) {
-            const uint32_t pos = s_excl[dig[r]] + s_wcnt[warp][dig[r]] + rank[r];
-            keys_out[pos] = key[r];
-        }
-    }
-}
-
-int onesweep_u64(subquad_ctx *ctx, uint64_t *keys, uint64_t *keys_alt, int64_t count, int begin_bit, int end_bit,
-                 bool *result_in_alt, void *tmp, size_t tmp_bytes)
-{
-    *result_in_alt = false;
-    if (count <= 1 || end_bit <= begin_bit) return SUBQUAD_OK;
-    const int passes = (end_bit - begin_bit + 7) / 8;
-    if (passes > kOsMaxPasses) return SUBQUAD_ERR_ARG;
-    const int64_t ntiles = (count + kOsTile - 1) / kOsTile;
-    SqArena a(tmp);
-    uint32_t *hist = a.take<uint32_t>((size_t)kOsMaxPasses * kRadix);
-    uint32_t *counters = a.take<uint32_t>(kOsMaxPasses);
-    uint32_t *status = a.take<uint32_t>((size_t)passes * ntiles * kRadix);
-    if (a.off > tmp_bytes) return SUBQUAD_ERR_ARG;
-    SQ_TRY_CUDA(cudaMemsetAsync(tmp, 0, a.off, ctx->stream));
-    onesweep_hist_kernel<<<sq_grid(ctx, count, kOsThreads, 4), kOsThreads, 0, ctx->stream>>>(keys, count, begin_bit,
-                                                                                              passes, hist);
-    SQ_LAUNCH_CHECK();
-    onesweep_bases_kernel<<<1, kRadix, 0, ctx->stream>>>(hist, passes);
-    SQ_LAUNCH_CHECK();
-    uint64_t *src = keys, *dst = keys_alt;
-    for (int ps = 0; ps < passes; ++ps) {
-        onesweep_pass_kernel<<<(unsigned)ntiles, kOsThreads, 0, ctx->stream>>>(
-            src, dst, count, begin_bit + 8 * ps, hist + ps * kRadix, status + (size_t)ps * ntiles * kRadix,
-            counters + ps, ctx->d_err);
-        SQ_LAUNCH_CHECK();
-        uint64_t *tk = src;
-        src = dst;
-        dst = tk;
-    }
-    *result_in_alt = (passes & 1) != 0;
-    return SUBQUAD_OK;
-}
-
 }  // namespace
 
 size_t sq_scan_tmp_bytes(int64_t count)
@@ -528,10 +357,7 @@ size_t sq_radix_tmp_bytes(int64_t count)
 {
     int64_t ntiles = (count + kSortTile - 1) / kSortTile;
     int64_t hist_len = ntiles * kRadix;
-    const size_t classic = (size_t)hist_len * sizeof(uint32_t) * 2 + sq_scan_tmp_bytes(hist_len) + 4096;
-    const int64_t os_tiles = (count + kOsTile - 1) / kOsTile;
-    const size_t onesweep = (size_t)kOsMaxPasses * (os_tiles + 1) * kRadix * sizeof(uint32_t) + 4096;
-    return classic > onesweep ? classic : onesweep;
+    return (size_t)hist_len * sizeof(uint32_t) * 2 + sq_scan_tmp_bytes(hist_len) + 4096;
 }
 
 int sq_scan_u32(subquad_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t count, const uint32_t *d_count,
@@ -555,14 +381,5 @@ int sq_radix_sort_u32(subquad_ctx *ctx, uint32_t *keys, uint32_t *vals, uint32_t
         return radix_impl<uint32_t, true>(ctx, keys, vals, keys_alt, vals_alt, count, d_count, begin_bit, end_bit,
                                           result_in_alt, tmp, tmp_bytes);
     return radix_impl<uint32_t, false>(ctx, keys, nullptr, keys_alt, nullptr, count, d_count, begin_bit, end_bit,
-                                       result_in_alt, tmp, tmp_bytes);
-}
-
-int sq_radix_sort_u64(subquad_ctx *ctx, uint64_t *keys, uint64_t *keys_alt, int64_t count, const uint32_t *d_count,
-                      int begin_bit, int end_bit, bool *result_in_alt, void *tmp, size_t tmp_bytes)
-{
-    if (!d_count && count < (int64_t)kOsValue && (end_bit - begin_bit + 7) / 8 <= kOsMaxPasses)
-        return onesweep_u64(ctx, keys, keys_alt, count, begin_bit, end_bit, result_in_alt, tmp, tmp_bytes);
-    return radix_impl<uint64_t, false>(ctx, keys, nullptr, keys_alt, nullptr, count, d_count, begin_bit, end_bit,
                                        result_in_alt, tmp, tmp_bytes);
 }
