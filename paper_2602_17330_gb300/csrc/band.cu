@@ -845,6 +845,24 @@ __global__ void band_warp_chunk_kernel(const uint64_t *__restrict__ poff, const 
         wchunk[w] = chunk_of_raw(poff, nc, w * 32);
 }
 
+// Lanes of the warp holding the same value as their neighbours form runs;
+// run_of returns the lane mask of the calling lane's run and its first lane.
+// Every lane of the warp must call it.
+struct RunOf {
+    uint32_t mask, first;
+};
+__device__ __forceinline__ RunOf run_of(uint32_t key, uint32_t lane)
+{
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+    const uint32_t upto = (2u << lane) - 1u;  // lanes 0..lane (all lanes for lane 31)
+    const uint32_t first = 31u - __clz(heads & upto);
+    const uint32_t later = heads & ~upto;
+    const uint32_t end = later ? (uint32_t)__ffs(later) - 1u : 32u;
+    const uint32_t mask = (end == 32u ? 0xffffffffu : ((1u << end) - 1u)) & ~((1u << first) - 1u);
+    return {mask, first};
+}
+
 // Step 5: owned pairs, appended to out.  Each warp takes 32 consecutive raw
 // pair indices; their chunks are c0 (looked up) plus the chunks starting
 // inside the group (one load per lane and a warp OR of start positions); each
@@ -914,9 +932,14 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
             }
         }
         const unsigned long long pos = block_append(owned, d_count, &s_base, s_warp);
-        if (owned && pos < (unsigned long long)capacity) {
-            reinterpret_cast<uint2 *>(out)[pos] = make_uint2(i, j);
-            if (deg) atomicAdd(&deg[i], 1u);
+        const bool written = owned && pos < (unsigned long long)capacity;
+        if (written) reinterpret_cast<uint2 *>(out)[pos] = make_uint2(i, j);
+        if (deg) {
+            // one count per run of equal first members (a chunk's pairs come
+            // in runs sharing i): the run's first written lane adds them all
+            const RunOf r = run_of(q < total ? i : 0xffffffffu, lane);
+            const uint32_t mine = __ballot_sync(0xffffffffu, written) & r.mask;
+            if (written && lane == (uint32_t)__ffs(mine) - 1u) atomicAdd(&deg[i], (uint32_t)__popc(mine));
         }
     }
 }
@@ -969,9 +992,19 @@ __global__ void pairs_scatter_kernel(const uint32_t *__restrict__ pairs, const u
                                      uint32_t *__restrict__ col)
 {
     const int64_t m = (int64_t)*d_m;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
-        const uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
-        col[rowoff[ij.x] + atomicSub(&fill[ij.x], 1u) - 1u] = ij.y;
+    const uint32_t lane = threadIdx.x & 31;
+    // warp-uniform trip count; a run of equal first members takes its slots
+    // with one atomic (positions old-1, old-2, ... in lane order)
+    for (int64_t pb = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); pb < m;
+         pb += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = pb + lane;
+        const bool valid = p < m;
+        const uint2 ij = valid ? reinterpret_cast<const uint2 *>(pairs)[p] : make_uint2(0xffffffffu, 0u);
+        const RunOf r = run_of(ij.x, lane);
+        uint32_t top = 0;
+        if (valid && lane == r.first) top = atomicSub(&fill[ij.x], (uint32_t)__popc(r.mask));
+        top = __shfl_sync(0xffffffffu, top, r.first);
+        if (valid) col[rowoff[ij.x] + top - 1u - (lane - r.first)] = ij.y;
     }
 }
 
