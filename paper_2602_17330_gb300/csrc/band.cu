@@ -946,9 +946,11 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
 
 // Lexicographic order of the emitted pairs: a counting pass by first member
 // i (degrees counted by the emitter, scanned into row offsets), a scatter of
-// the second members into their rows, and a sort of every row: in registers
-// for rows of at most kRowSmall partners, by one warp up to kRowWarp, by one
-// CTA in shared memory up to kRowMid, in place in global memory beyond.
+// the second members into their rows, and a sort of every row, the rows
+// listed by size class first: by one thread in registers for rows of at most
+// kRowSmall partners (four classes, so the lanes of a warp sort rows of one
+// size), by one warp up to kRowWarp, by one CTA in shared memory up to
+// kRowMid, in place in global memory beyond.
 // Every count stays on the device.
 constexpr int kRowSmall = 32;
 constexpr int kRowWarp = 256;   // rows up to this size: one warp, registers
@@ -960,30 +962,91 @@ __device__ __forceinline__ uint64_t row_end(const uint32_t *rowoff, int64_t n, u
     return i + 1 < n ? rowoff[i + 1] : m;
 }
 
-// rows of more than kRowSmall partners: those up to kRowWarp listed from the
-// front of `mid`, those up to kRowMid from the back, the longer ones in `lng`
+// Row classes by partner count d: 2..4, 5..8, 9..16, 17..32 (sorted by one
+// thread per row in registers), 33..kRowWarp (one warp), kRowWarp+1..kRowMid
+// (one CTA), longer (in place in global memory).  Each class is listed so a
+// warp of a sorting kernel takes rows of one class only.
+constexpr int kRowClasses = 7;
+enum { kClsS4 = 0, kClsS8, kClsS16, kClsS32, kClsWarp, kClsCta, kClsLong };
+
+__device__ __forceinline__ int row_class(uint64_t d)
+{
+    if (d <= 1) return -1;
+    if (d <= 4) return kClsS4;
+    if (d <= 8) return kClsS8;
+    if (d <= 16) return kClsS16;
+    if (d <= (uint64_t)kRowSmall) return kClsS32;
+    if (d <= (uint64_t)kRowWarp) return kClsWarp;
+    if (d <= (uint64_t)kRowMid) return kClsCta;
+    return kClsLong;
+}
+
+// Positions of the block's threads in per-class lists: one ballot per class
+// per warp, one atomic per class per block (cls < 0: no list).
+__device__ __forceinline__ unsigned long long block_append_class(int cls, unsigned long long *counters,
+                                                                 unsigned long long *s_base,
+                                                                 uint32_t (*s_wc)[32])
+{
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t rank = 0;
+#pragma unroll
+    for (int c = 0; c < kRowClasses; ++c) {
+        const uint32_t mk = __ballot_sync(0xffffffffu, cls == c);
+        if (cls == c) rank = __popc(mk & ((1u << lane) - 1u));
+        if (lane == 0) s_wc[c][warp] = __popc(mk);
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)kRowClasses) {
+        const int c = threadIdx.x;
+        uint32_t run = 0;
+        for (uint32_t w = 0; w < nw; ++w) {
+            const uint32_t t = s_wc[c][w];
+            s_wc[c][w] = run;
+            run += t;
+        }
+        s_base[c] = run ? atomicAdd(&counters[c], (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long pos = cls >= 0 ? s_base[cls] + s_wc[cls][warp] + rank : 0ull;
+    __syncthreads();
+    return pos;
+}
+
+// Lists: classes S4/S8 from the front/back of sa, S16/S32 of sb, Warp/Cta
+// of mid, Long in lng.  Rows of one partner are written out here (the row
+// columns are in place).
 __global__ void __launch_bounds__(kRowThreads) rows_classify_kernel(const uint32_t *__restrict__ rowoff, int64_t n,
                                                                     const unsigned long long *__restrict__ d_m,
+                                                                    const uint32_t *__restrict__ col,
+                                                                    uint32_t *__restrict__ out,
+                                                                    uint32_t *__restrict__ sa, uint32_t *__restrict__ sb,
                                                                     uint32_t *__restrict__ mid,
-                                                                    unsigned long long *__restrict__ d_warp,
-                                                                    unsigned long long *__restrict__ d_cta,
                                                                     uint32_t *__restrict__ lng,
-                                                                    unsigned long long *__restrict__ d_long)
+                                                                    unsigned long long *__restrict__ d_cls)
 {
-    __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_warp[32];
+    __shared__ unsigned long long s_base[kRowClasses];
+    __shared__ uint32_t s_wc[kRowClasses][32];
     const uint64_t m = *d_m;
     for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n; b0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = b0 + threadIdx.x;
-        uint64_t d = 0;
-        if (i < n) d = row_end(rowoff, n, m, i) - rowoff[i];
-        if (d > (uint64_t)kRowMid) lng[atomicAdd(d_long, 1ull)] = (uint32_t)i;
-        const bool is_warp = d > (uint64_t)kRowSmall && d <= (uint64_t)kRowWarp;
-        const bool is_cta = d > (uint64_t)kRowWarp && d <= (uint64_t)kRowMid;
-        const unsigned long long pw = block_append(is_warp, d_warp, &s_base, s_warp);
-        if (is_warp) mid[pw] = (uint32_t)i;
-        const unsigned long long pc = block_append(is_cta, d_cta, &s_base, s_warp);
-        if (is_cta) mid[n - 1 - (int64_t)pc] = (uint32_t)i;
+        uint64_t d = 0, r0 = 0;
+        if (i < n) {
+            r0 = rowoff[i];
+            d = row_end(rowoff, n, m, i) - r0;
+        }
+        if (d == 1) reinterpret_cast<uint2 *>(out)[r0] = make_uint2((uint32_t)i, col[r0]);
+        const int cls = row_class(d);
+        const unsigned long long pos = block_append_class(cls, d_cls, s_base, s_wc);
+        switch (cls) {
+        case kClsS4: sa[pos] = (uint32_t)i; break;
+        case kClsS8: sa[n - 1 - (int64_t)pos] = (uint32_t)i; break;
+        case kClsS16: sb[pos] = (uint32_t)i; break;
+        case kClsS32: sb[n - 1 - (int64_t)pos] = (uint32_t)i; break;
+        case kClsWarp: mid[pos] = (uint32_t)i; break;
+        case kClsCta: mid[n - 1 - (int64_t)pos] = (uint32_t)i; break;
+        case kClsLong: lng[pos] = (uint32_t)i; break;
+        default: break;
+        }
     }
 }
 
@@ -1040,21 +1103,27 @@ __device__ __forceinline__ void sort_row_regs(const uint32_t *__restrict__ col, 
         if ((uint32_t)t < d) reinterpret_cast<uint2 *>(out)[r0 + t] = make_uint2(i, v[t]);
 }
 
+// One thread per row of 2..32 partners; the four class lists are walked in
+// turn so the lanes of a warp (nearly always) sort rows of one class.
 __global__ void __launch_bounds__(kRowThreads) rows_sort_small_kernel(const uint32_t *__restrict__ rowoff, int64_t n,
                                                                       const unsigned long long *__restrict__ d_m,
+                                                                      const uint32_t *__restrict__ sa,
+                                                                      const uint32_t *__restrict__ sb,
+                                                                      const unsigned long long *__restrict__ d_cls,
                                                                       const uint32_t *__restrict__ col,
                                                                       uint32_t *__restrict__ out)
 {
     const uint64_t m = *d_m;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t e0 = d_cls[kClsS4], e1 = e0 + d_cls[kClsS8], e2 = e1 + d_cls[kClsS16], e3 = e2 + d_cls[kClsS32];
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < e3; v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = v < e0 ? sa[v] : v < e1 ? sa[n - 1 - (int64_t)(v - e0)]
+                         : v < e2 ? sb[v - e1] : sb[n - 1 - (int64_t)(v - e2)];
         const uint64_t r0 = rowoff[i];
-        const uint64_t d = row_end(rowoff, n, m, i) - r0;
-        if (d == 0 || d > (uint64_t)kRowSmall) continue;
-        if (d == 1) reinterpret_cast<uint2 *>(out)[r0] = make_uint2((uint32_t)i, col[r0]);
-        else if (d <= 4) sort_row_regs<4>(col, r0, (uint32_t)d, (uint32_t)i, out);
-        else if (d <= 8) sort_row_regs<8>(col, r0, (uint32_t)d, (uint32_t)i, out);
-        else if (d <= 16) sort_row_regs<16>(col, r0, (uint32_t)d, (uint32_t)i, out);
-        else sort_row_regs<32>(col, r0, (uint32_t)d, (uint32_t)i, out);
+        const uint32_t d = (uint32_t)(row_end(rowoff, n, m, i) - r0);
+        if (v < e0) sort_row_regs<4>(col, r0, d, i, out);
+        else if (v < e1) sort_row_regs<8>(col, r0, d, i, out);
+        else if (v < e2) sort_row_regs<16>(col, r0, d, i, out);
+        else sort_row_regs<32>(col, r0, d, i, out);
     }
 }
 
@@ -1418,7 +1487,7 @@ int band_index_build(subquad_ctx *ctx, const uint32_t *sig, int rows, int cap, c
 }
 
 struct EmitScratch {
-    uint32_t *deg, *rowoff, *mid, *lng, *col;
+    uint32_t *deg, *rowoff, *sa, *sb, *mid, *lng, *col;
     void *tmp;
     size_t tmp_bytes = 0;
 };
@@ -1427,6 +1496,8 @@ void take_emit(SqArena &a, EmitScratch &E, int64_t n, int64_t capacity, uint32_t
 {
     E.deg = a.take<uint32_t>(n);
     E.rowoff = a.take<uint32_t>(n);
+    E.sa = a.take<uint32_t>(n);
+    E.sb = a.take<uint32_t>(n);
     E.mid = a.take<uint32_t>(n);
     E.lng = a.take<uint32_t>((capacity >> 13) + 1);
     // row columns: in a free buffer of the caller when it is large enough
@@ -1446,10 +1517,8 @@ int band_emit_sorted(subquad_ctx *ctx, const BandIndex &I, uint64_t raw0, uint64
     const int64_t cap1 = std::max<int64_t>(capacity, 1);
     unsigned long long *d_count = reinterpret_cast<unsigned long long *>(ctx->d_small);
     unsigned long long *d_clamped = reinterpret_cast<unsigned long long *>(ctx->d_small + 4);
-    unsigned long long *d_mid = reinterpret_cast<unsigned long long *>(ctx->d_small + 5);
-    unsigned long long *d_long = reinterpret_cast<unsigned long long *>(ctx->d_small + 6);
-    unsigned long long *d_wrows = reinterpret_cast<unsigned long long *>(ctx->d_small + 7);
-    SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 8 * sizeof(uint64_t), ctx->stream));
+    unsigned long long *d_cls = reinterpret_cast<unsigned long long *>(ctx->d_small + 8);  // kRowClasses counters
+    SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_small, 0, 16 * sizeof(uint64_t), ctx->stream));
     SQ_TRY_CUDA(cudaMemsetAsync(E.deg, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
     {
         SqProfScope prof_emit(ctx, SUBQUAD_PROF_BAND_EMIT);
@@ -1463,29 +1532,30 @@ int band_emit_sorted(subquad_ctx *ctx, const BandIndex &I, uint64_t raw0, uint64
     // pairs clamped to the capacity for the sort below
     band_finish_kernel<<<1, 1, 0, ctx->stream>>>(d_count, capacity, d_publish, d_clamped, ctx->d_err);
     SQ_LAUNCH_CHECK();
-    // lexicographic order: row offsets by first member, row classes, the
-    // second members scattered into their rows, every row sorted
+    // lexicographic order: row offsets by first member, the second members
+    // scattered into their rows, row class lists, every row sorted
     SqProfScope prof_ps(ctx, SUBQUAD_PROF_BAND_PAIRSORT);
     const unsigned rgrid = sq_grid(ctx, n, kRowThreads, 8);
     SQ_TRY(sq_scan_u32(ctx, E.deg, E.rowoff, n, nullptr, false, false, nullptr, E.tmp, E.tmp_bytes));
-    rows_classify_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.mid, d_wrows, d_mid, E.lng,
-                                                                 d_long);
-    SQ_LAUNCH_CHECK();
     pairs_scatter_kernel<<<sq_grid(ctx, cap1, 256, 8), 256, 0, ctx->stream>>>(pairs_out, d_clamped, E.rowoff, E.deg,
                                                                               E.col);
     SQ_LAUNCH_CHECK();
-    rows_sort_small_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.col, pairs_out);
+    rows_classify_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.col, pairs_out, E.sa, E.sb,
+                                                                 E.mid, E.lng, d_cls);
     SQ_LAUNCH_CHECK();
-    rows_sort_warp_kernel<<<(unsigned)ctx->num_sms * 8, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.mid,
-                                                                                      d_wrows, E.col, pairs_out);
+    rows_sort_small_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.sa, E.sb, d_cls, E.col,
+                                                                   pairs_out);
+    SQ_LAUNCH_CHECK();
+    rows_sort_warp_kernel<<<(unsigned)ctx->num_sms * 8, kRowThreads, 0, ctx->stream>>>(
+        E.rowoff, n, d_clamped, E.mid, d_cls + kClsWarp, E.col, pairs_out);
     SQ_LAUNCH_CHECK();
     constexpr size_t kRadixSmem = (2 * (size_t)kRowMid + (size_t)kRadixWarps * 256) * sizeof(uint32_t);
     SQ_TRY_CUDA(cudaFuncSetAttribute(rows_sort_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kRadixSmem));
     rows_sort_mid_kernel<<<(unsigned)ctx->num_sms * 3, kRowThreads, kRadixSmem, ctx->stream>>>(
-        E.rowoff, n, d_clamped, E.mid, d_mid, E.col, pairs_out);
+        E.rowoff, n, d_clamped, E.mid, d_cls + kClsCta, E.col, pairs_out);
     SQ_LAUNCH_CHECK();
-    rows_sort_long_kernel<<<(unsigned)ctx->num_sms, 1024, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.lng, d_long,
+    rows_sort_long_kernel<<<(unsigned)ctx->num_sms, 1024, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.lng, d_cls + kClsLong,
                                                                            E.col, pairs_out);
     SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;

@@ -79,7 +79,7 @@ extern "C" int subquad_create(subquad_ctx **out, int device, void *cuda_stream)
     cudaError_t e = guard.ok ? cudaSuccess : cudaErrorInvalidDevice;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, 256);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_small, 8 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_small, 16 * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 8 * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, 256, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

@@ -36,7 +36,7 @@ struct subquad_ctx {
     int table_gap_open = -1;     // gap-open folded into d_table (-1: not built)
     uint32_t *d_err = nullptr;   // sticky device error word
     uint64_t *h_pinned = nullptr;  // pinned host staging, 8 words
-    uint64_t *d_small = nullptr;   // small device scalars (counters), 8 words
+    uint64_t *d_small = nullptr;   // small device scalars (counters), 16 words
     void *scratch = nullptr;
     size_t scratch_cap = 0;
     int64_t launches = 0;  // kernels launched through this context
