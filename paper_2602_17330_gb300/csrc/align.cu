@@ -395,7 +395,7 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
             if (p < NQ) {  // column j, row p
                 const uint32_t lo = *reinterpret_cast<const uint32_t *>(colAP + qoffP[p]);
                 const uint32_t hi = *reinterpret_cast<const uint32_t *>(colAQ + qoffQ[p]);
-                const uint32_t s_o = __byte_perm(lo, hi, 0x5410);
+                const uint32_t s_o = (lo & 0x0000ffffu) | (hi & 0xffff0000u);
                 const uint32_t e_new = __viaddmax_s16x2_relu(E[p], neg_e, HM[p]);
                 FA = __viaddmax_s16x2_relu(FA, neg_e, upA);
                 const uint32_t h = __viaddmax_s16x2_relu(dA, s_o, __vmaxs2(e_new, FA));
@@ -409,7 +409,7 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
                 const int r = p >= 1 ? p - 1 : 0;
                 const uint32_t lo = *reinterpret_cast<const uint32_t *>(colBP + qoffP[r]);
                 const uint32_t hi = *reinterpret_cast<const uint32_t *>(colBQ + qoffQ[r]);
-                const uint32_t s_o = __byte_perm(lo, hi, 0x5410);
+                const uint32_t s_o = (lo & 0x0000ffffu) | (hi & 0xffff0000u);
                 const uint32_t e_new = __viaddmax_s16x2_relu(E[r], neg_e, HM[r]);
                 FB = __viaddmax_s16x2_relu(FB, neg_e, upB);
                 const uint32_t h = __viaddmax_s16x2_relu(dB, s_o, __vmaxs2(e_new, FB));
@@ -510,8 +510,17 @@ __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::b
 {
     extern __shared__ int32_t s_tab_words[];
     const int64_t m = items(m_max, d_m);
-    for (int q = threadIdx.x; q < kTabWords / 4; q += blockDim.x)
-        reinterpret_cast<int4 *>(s_tab_words)[q] = reinterpret_cast<const int4 *>(table)[q];
+    // each staged word holds its 16-bit score in both halves, so the two
+    // pairs' scores combine with one bitwise select (low half of the first
+    // word, high half of the second)
+    for (int q = threadIdx.x; q < kTabWords / 4; q += blockDim.x) {
+        int4 v = reinterpret_cast<const int4 *>(table)[q];
+        v.x = (int32_t)(((uint32_t)v.x & 0xffffu) * 0x10001u);
+        v.y = (int32_t)(((uint32_t)v.y & 0xffffu) * 0x10001u);
+        v.z = (int32_t)(((uint32_t)v.z & 0xffffu) * 0x10001u);
+        v.w = (int32_t)(((uint32_t)v.w & 0xffffu) * 0x10001u);
+        reinterpret_cast<int4 *>(s_tab_words)[q] = v;
+    }
     __syncthreads();
     const char *s_tab = reinterpret_cast<const char *>(s_tab_words);
     constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
