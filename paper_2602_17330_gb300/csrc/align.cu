@@ -274,21 +274,33 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const uint64_t *__restri
         if (s_hist[b]) atomicAdd(&counts[b], s_hist[b]);
 }
 
-__global__ void __launch_bounds__(1024) bin_offsets_kernel(uint32_t *__restrict__ counts)
+// Exclusive scan of the kBins counts (one thread per bin, 32 warps).
+__global__ void __launch_bounds__(kBins) bin_offsets_kernel(uint32_t *__restrict__ counts)
 {
-    __shared__ uint32_t s[kBins];
-    s[threadIdx.x] = counts[threadIdx.x];
+    static_assert(kBins == 32 * 32, "one warp per 32 bins, 32 warps");
+    __shared__ uint32_t s_w[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t v = counts[threadIdx.x];
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[warp] = inc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int b = 0; b < kBins; ++b) {
-            const uint32_t c = s[b];
-            s[b] = run;
-            run += c;
+    if (warp == 0) {
+        const uint32_t w = s_w[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if ((int)lane >= o) wi += y;
         }
+        s_w[lane] = wi - w;
     }
     __syncthreads();
-    counts[threadIdx.x] = s[threadIdx.x];
+    counts[threadIdx.x] = s_w[warp] + inc - v;
 }
 
 // Same block ranges as bin_count_kernel: the block reserves one slice of each
@@ -325,7 +337,7 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(const uint16_t *__rest
 }
 
 // Two pairs per thread in packed 16-bit halves (pair P low, pair Q high).  Per
-// cell: two table lookups packed with one byte permute, then
+// cell: two table lookups combined with one bitwise select, then
 //   E = max(E - e, H(i,j-1) - o, 0)   F = max(F - e, H(i-1,j) - o, 0)  (DPX add-max-relu)
 //   H = max((H(i-1,j-1) - o) + (M + o), max(E, F), 0)                  (packed max, DPX add-max-relu)
 // Every intermediate lies in [-1064, 2953] for |M| <= 64, o, e <= 1000 and

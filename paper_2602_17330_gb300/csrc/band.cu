@@ -3,8 +3,8 @@
 //
 //  1. every (band, sequence) key -- the exact R-tuple, plus the donor in a
 //     batch of donors -- is hashed to a 32-bit fingerprint and a partition
-//     digit; a per-tile histogram, a scan and a stable scatter lay the records
-//     (fingerprint, id) of each partition out contiguously in id order;
+//     digit; a per-tile histogram, a scan and a scatter lay the records
+//     (fingerprint, id) of each partition out contiguously;
 //  2. one CTA per partition (about 2048 records) groups equal keys in a
 //     shared-memory hash table (fingerprint match confirmed on the exact
 //     keys); buckets of >= 2 members get contiguous kept positions, their
@@ -109,15 +109,15 @@ __device__ __forceinline__ bool same_key(const uint32_t *band_sig, int rows, uin
     return key_equal(band_sig + (int64_t)owner * rows, rows, k) && (!donor || donor[owner] == my_donor);
 }
 
-// Steps 1-2: stable hash partition of the (band, sequence) keys.
+// Steps 1-2: hash partition of the (band, sequence) keys.
 //
 // Every key gets a 32-bit fingerprint fp (a hash of the R-tuple and, in a
 // batch of donors, the donor) and a partition digit (pbits of an independent
 // second hash).
 // A per-tile digit histogram, an exclusive scan of the digit-major histogram
-// and a stable scatter place the records (fp << 32 | id) of every partition
-// contiguously, in ascending id order.  Equal keys have equal fingerprints and
-// so land in one partition.
+// and a scatter place the records (fp << 32 | id) of every partition
+// contiguously (tile by tile; within a tile in any order).  Equal keys have
+// equal fingerprints and so land in one partition.
 constexpr int kPartThreads = 256;
 constexpr int kPartItems = 16;
 constexpr int kPartTile = kPartThreads * kPartItems;
@@ -177,65 +177,39 @@ __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(const uint32_t 
     for (int q = threadIdx.x; q < P; q += blockDim.x) hist[((int64_t)gb * P + q) * ntiles + tile] = s_hist[q];
 }
 
-// Stable scatter: warp w of a tile owns ids [tile*4096 + w*512, +512) in
-// rounds of 32, so digit-major ranks follow ascending id.
-__global__ void __launch_bounds__(kPartThreads, 3) part_scatter_kernel(const uint64_t *__restrict__ fd, int64_t n,
+// Scatter: the tile's slice of every partition starts at the scanned offset;
+// each record takes the next position of its digit (shared-memory atomic), so
+// a partition's records come tile by tile, in any order within a tile.  All
+// positions are taken before any record is stored: the stores then leave as
+// one burst per thread, which keeps the partial-sector writes of neighbouring
+// runs together in L2.
+__global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const uint64_t *__restrict__ fd, int64_t n,
                                                                     int pbits, int64_t ntiles,
                                                                     const uint32_t *__restrict__ offs,
                                                                     uint64_t *__restrict__ recs)
 {
-    extern __shared__ uint32_t s_wcnt[];  // [warps][P]
+    extern __shared__ uint32_t s_pos[];  // [P]
     const int P = 1 << pbits, gb = blockIdx.y;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = threadIdx.x; q < (kPartThreads / 32) * P; q += blockDim.x) s_wcnt[q] = 0;
-    __syncthreads();
-    const uint64_t *band_fd = fd + (int64_t)gb * n;
     const int64_t tile = blockIdx.x;
-    const int64_t wbase = tile * kPartTile + warp * 32 * kPartItems;
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t *wcnt = s_wcnt + warp * P;
-    // dr[r]: digit in the low 16 bits (P = invalid), rank within the warp's
-    // digit run in the high 16 bits (< 32 * kPartItems)
-    uint32_t fp[kPartItems], dr[kPartItems];
+    for (int q = threadIdx.x; q < P; q += blockDim.x) s_pos[q] = offs[((int64_t)gb * P + q) * ntiles + tile];
+    const uint64_t *band_fd = fd + (int64_t)gb * n;
+    uint64_t v[kPartItems];
+    uint32_t pos[kPartItems];
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
-        const int64_t i = wbase + r * 32 + lane;
-        const uint64_t v = i < n ? band_fd[i] : ((uint64_t)P << 32);
-        fp[r] = (uint32_t)v;
-        dr[r] = (uint32_t)(v >> 32);
-    }
-#pragma unroll
-    for (int r = 0; r < kPartItems; ++r) {
-        const uint32_t d = dr[r];
-        const bool valid = d < (uint32_t)P;
-        // lanes with the same digit: one ballot per digit bit (bit pbits marks invalid lanes)
-        uint32_t peers = 0xffffffffu;
-        for (int bit = 0; bit <= pbits; ++bit) {
-            const uint32_t m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-            peers &= ((d >> bit) & 1u) ? m : ~m;
-        }
-        const uint32_t before = __popc(peers & lt);
-        const uint32_t base = valid ? wcnt[d] : 0u;
-        __syncwarp();
-        if (valid && before == 0) wcnt[d] = base + __popc(peers);
-        __syncwarp();
-        dr[r] = d | ((base + before) << 16);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < P; d += blockDim.x) {
-        uint32_t run = offs[((int64_t)gb * P + d) * ntiles + tile];
-#pragma unroll
-        for (int w = 0; w < kPartThreads / 32; ++w) {
-            const uint32_t c = s_wcnt[w * P + d];
-            s_wcnt[w * P + d] = run;
-            run += c;
-        }
+        const int64_t i = tile * kPartTile + r * kPartThreads + threadIdx.x;
+        v[r] = i < n ? band_fd[i] : ~0ull;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
-        const int64_t i = wbase + r * 32 + lane;
-        if (i < n) recs[wcnt[dr[r] & 0xffffu] + (dr[r] >> 16)] = ((uint64_t)fp[r] << 32) | (uint32_t)i;
+        const int64_t i = tile * kPartTile + r * kPartThreads + threadIdx.x;
+        pos[r] = i < n ? atomicAdd(&s_pos[(uint32_t)(v[r] >> 32)], 1u) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kPartItems; ++r) {
+        const int64_t i = tile * kPartTile + r * kPartThreads + threadIdx.x;
+        if (i < n) recs[pos[r]] = (v[r] << 32) | (uint32_t)i;
     }
 }
 
@@ -245,9 +219,9 @@ __global__ void __launch_bounds__(kPartThreads, 3) part_scatter_kernel(const uin
 // Per bucket of c >= 2 members the CTA reserves c contiguous kept positions
 // and writes its chunks (c members, or runs of cap members in id order when
 // c > cap) to the chunk list; every kept member records its chunk head as its
-// chunk id for the band.  Buckets within cap are filled in any order (one
-// chunk, order irrelevant); buckets above cap are filled by one warp walking
-// the records in id order, so chunk m holds ranks [m*cap, (m+1)*cap).
+// chunk id for the band.  Members are placed in any order; a bucket above
+// the cap is then sorted by id in place, so chunk m holds ranks
+// [m*cap, (m+1)*cap) (order_bucket).
 // A partition holding more than kGrpDistinct distinct keys is split by
 // further fingerprint bits into sub-ranges processed one after another.
 constexpr int kGrpThreads = 256;
@@ -423,54 +397,50 @@ __device__ __forceinline__ void bucket_phase(const GroupShared &g, int cap, int 
     __syncthreads();
 }
 
-// Kept position of a member of a bucket within the cap (any order).
+// Kept position of a member of a bucket (any order).  A member of a bucket
+// within the cap records the bucket's single chunk; chunk ids of the members
+// of a bucket above the cap follow once the bucket is ordered (order_bucket).
 __device__ __forceinline__ void place_any(const GroupShared &g, uint32_t slot, uint32_t id, int cap, int b, int bands,
                                           const GroupOut &o)
 {
     const unsigned long long e = g.tab[slot];
     const uint32_t cc = (uint32_t)e;
-    if (cc < 2 || (cap > 0 && cc > (uint32_t)cap)) return;
+    if (cc < 2) return;
     const uint32_t r = atomicAdd(&g.cnt[slot], 1u);
     const uint64_t head = *g.kbase + (e >> 32);
     o.kept_ids[head + r] = id;
+    if (cap > 0 && cc > (uint32_t)cap) return;
     set_chunk(o, id, b, bands, (uint32_t)head);
 }
 
-// Members of buckets above the cap, ranked in id order by one warp walking
-// the records in order (records of a partition are in ascending id order).
-template <typename SlotOf>
-__device__ __forceinline__ void place_in_order(const GroupShared &g, const uint64_t *prec, int64_t cnt, uint32_t kmask,
-                                               uint32_t k, SlotOf slot_of, int cap, int b, int bands,
-                                               const GroupOut &o)
+// A bucket above the cap: its c kept members (at v, kept position head) are
+// sorted by id in place -- an all-ascending bitonic network over the next
+// power of two, positions >= c acting as +infinity that never move -- and the
+// member of rank r records chunk head + (r / cap) * cap, so chunk m holds
+// ranks [m*cap, (m+1)*cap).  Called by every thread of the block.
+__device__ void order_bucket(uint32_t *v, uint32_t c, uint32_t head, int cap, int b, int bands, const GroupOut &o)
 {
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
-    for (int64_t q0 = 0; q0 < cnt; q0 += 32) {
-        const int64_t q = q0 + lane;
-        uint32_t slot = 0, id = 0;
-        bool mine = false;
-        if (q < cnt) {
-            const uint64_t rec = prec[q];
-            id = (uint32_t)rec;
-            if ((((uint32_t)(rec >> 32) >> 12) & kmask) == k) {
-                slot = slot_of(q);
-                const uint32_t cc = (uint32_t)g.tab[slot];
-                mine = cc >= 2 && cap > 0 && cc > (uint32_t)cap;
+    uint64_t P2 = 2;
+    while (P2 < c) P2 <<= 1;
+    for (uint64_t k = 2; k <= P2; k <<= 1) {
+        for (uint64_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint64_t t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
+                const uint64_t a = (t / j) * 2 * j + (t % j);
+                const uint64_t bb = j == (k >> 1) ? (a | (k - 1)) - (a & (k - 1)) : a + j;  // flip, then half-cleaners
+                if (bb < c) {
+                    const uint32_t x = v[a], y = v[bb];
+                    if (x > y) {
+                        v[a] = y;
+                        v[bb] = x;
+                    }
+                }
             }
-        }
-        const uint32_t peers = __match_any_sync(0xffffffffu, mine ? slot : (0x80000000u | lane));
-        const uint32_t before = __popc(peers & lt);
-        const uint32_t base = mine ? g.cnt[slot] : 0u;
-        __syncwarp();
-        if (mine && before == 0) g.cnt[slot] = base + __popc(peers);
-        __syncwarp();
-        if (mine) {
-            const uint32_t r = base + before;
-            const uint64_t head = *g.kbase + (g.tab[slot] >> 32);
-            o.kept_ids[head + r] = id;
-            set_chunk(o, id, b, bands, (uint32_t)(head + (r / (uint32_t)cap) * (uint32_t)cap));
+            __syncthreads();
         }
     }
+    for (uint32_t r = threadIdx.x; r < c; r += blockDim.x)
+        set_chunk(o, v[r], b, bands, head + (r / (uint32_t)cap) * (uint32_t)cap);
+    __syncthreads();
 }
 
 // Fast path for a partition of at most kGrpFast records, staged in shared
@@ -663,41 +633,34 @@ __device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, ui
         }
     }
     __syncthreads();
-    // members of buckets within the cap: any order
+    // kept positions in any order; members of buckets within the cap record
+    // their chunk now, those of buckets above it once the bucket is ordered
     for (uint32_t t = threadIdx.x; t < ns; t += blockDim.x) {
         const uint32_t q = surv[t];
         const uint32_t e = tab[sslot[q]];
         const uint32_t c = e & 0xffffu;
-        if (c < 2 || e == kFastEmpty || (cap > 0 && c > (uint32_t)cap)) continue;
+        if (c < 2 || e == kFastEmpty) continue;
         const uint32_t r = atomicAdd(&cntv[sslot[q]], 1u);
         const uint64_t head = kbase + (e >> 16);
         const uint32_t id = (uint32_t)srec[q];
         o.kept_ids[head + r] = id;
+        if (cap > 0 && c > (uint32_t)cap) continue;
         set_chunk(o, id, b, bands, (uint32_t)head);
     }
-    // members of buckets above the cap: ranks in id order (one warp, records in order)
-    if (s_big && warp == 0) {
-        for (uint32_t q0 = 0; q0 < cnt; q0 += 32) {
-            const uint32_t q = q0 + lane;
-            uint32_t sl = 0, e = kFastEmpty;
-            if (q < cnt && sslot[q] != kNoSlot) {
-                sl = sslot[q];
-                e = tab[sl];
-            }
-            const bool mine = e != kFastEmpty && (e & 0xffffu) >= 2 && cap > 0 && (e & 0xffffu) > (uint32_t)cap;
-            const uint32_t peers = __match_any_sync(0xffffffffu, mine ? sl : (0x80000000u | lane));
-            const uint32_t before = __popc(peers & lt);
-            const uint32_t basec = mine ? cntv[sl] : 0u;
-            __syncwarp();
-            if (mine && before == 0) cntv[sl] = basec + __popc(peers);
-            __syncwarp();
-            if (mine) {
-                const uint32_t r = basec + before;
-                const uint64_t head = kbase + (e >> 16);
-                const uint32_t id = (uint32_t)srec[q];
-                o.kept_ids[head + r] = id;
-                set_chunk(o, id, b, bands, (uint32_t)(head + (r / (uint32_t)cap) * (uint32_t)cap));
-            }
+    if (s_big) {  // uniform: set before a barrier
+        // the buckets above the cap, listed (surv is free), then ordered one by one
+        if (threadIdx.x == 0) s_ns = 0;
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < nk; t += blockDim.x) {
+            const uint32_t c = tab[keys[t]] & 0xffffu;
+            if (c > (uint32_t)cap) surv[atomicAdd(&s_ns, 1u)] = keys[t];
+        }
+        __syncthreads();
+        const uint32_t nbig = s_ns;
+        for (uint32_t k = 0; k < nbig; ++k) {
+            const uint32_t e = tab[surv[k]];
+            const uint32_t head = (uint32_t)(kbase + (e >> 16));
+            order_bucket(o.kept_ids + head, e & 0xffffu, head, cap, b, bands, o);
         }
     }
     return true;
@@ -800,8 +763,23 @@ __global__ void __launch_bounds__(kGrpThreads, 4) part_group_kernel(
             if ((((uint32_t)(rec >> 32) >> 12) & kmask) != k) continue;
             place_any(g, rslot[q], (uint32_t)rec, cap, b, bands, o);
         }
-        if (s_big && threadIdx.x < 32)
-            place_in_order(g, prec, cnt, kmask, k, [&](int64_t q) { return rslot[q]; }, cap, b, bands, o);
+        if (s_big) {  // uniform: set before the barrier that ends bucket_phase
+            // the buckets above the cap, listed in the free cursor array, then ordered one by one
+            __syncthreads();
+            if (threadIdx.x == 0) s_distinct = 0;
+            __syncthreads();
+            for (int q = threadIdx.x; q < kGrpSlots; q += blockDim.x) {
+                const uint32_t c = (uint32_t)g.tab[q];
+                if (c >= 2 && c > (uint32_t)cap) g.cnt[atomicAdd(&s_distinct, 1u)] = (uint32_t)q;
+            }
+            __syncthreads();
+            const uint32_t nbig = s_distinct;
+            for (uint32_t t = 0; t < nbig; ++t) {
+                const unsigned long long e = g.tab[g.cnt[t]];
+                const uint32_t head = (uint32_t)(*g.kbase + (e >> 32));
+                order_bucket(o.kept_ids + head, (uint32_t)e, head, cap, b, bands, o);
+            }
+        }
     }
 }
 
@@ -1463,8 +1441,8 @@ int band_index_build(subquad_ctx *ctx, const uint32_t *sig, int rows, int cap, c
                 sig, n, rows, band0, S.pbits, donor, S.ntiles, S.offs, S.fd);
             SQ_LAUNCH_CHECK();
             SQ_TRY(sq_scan_u32(ctx, S.offs, S.offs, hl, nullptr, false, false, nullptr, S.tmp, S.tmp_bytes));
-            part_scatter_kernel<<<grid, kPartThreads, (kPartThreads / 32) * S.P * sizeof(uint32_t), ctx->stream>>>(
-                S.fd, n, S.pbits, S.ntiles, S.offs, S.recs);
+            part_scatter_kernel<<<grid, kPartThreads, S.P * sizeof(uint32_t), ctx->stream>>>(S.fd, n, S.pbits,
+                                                                                              S.ntiles, S.offs, S.recs);
             SQ_LAUNCH_CHECK();
         }
         SqProfScope prof_grp(ctx, SUBQUAD_PROF_BAND_GROUP);
