@@ -93,15 +93,6 @@ __device__ __forceinline__ unsigned long long block_append(bool flag, unsigned l
     return pos;
 }
 
-__device__ __forceinline__ uint32_t key_hash(const uint32_t k[8], int rows)
-{
-    uint32_t h = 0x9e3779b9u ^ (uint32_t)rows;
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-        if (r < rows) h = mix32(h ^ k[r]);
-    return h;
-}
-
 // Equal keys: the same R-tuple and, in a batch of donors, the same donor.
 __device__ __forceinline__ bool same_key(const uint32_t *band_sig, int rows, uint32_t owner, const uint32_t k[8],
                                          const int32_t *donor, int32_t my_donor)
@@ -127,19 +118,28 @@ struct KeyHash {
     uint32_t fp, digit;
 };
 
-// Two independent 32-bit hashes of the key: the fingerprint (one chain of
-// mixes) and the partition digit (a second chain with another seed), so two
-// distinct keys share a partition and a fingerprint with probability about
-// 2^-(32 + pbits).
+// Two 32-bit hashes of the key: every word is pre-mixed (w ^ w >> 16, a
+// bijection, so the low bits depend on the high ones), the words are summed
+// in two polynomials mod 2^32 (Horner with two different odd multipliers)
+// and each sum is finished by mix32: the fingerprint and the partition digit.
+// Distinct keys share a partition and a fingerprint with probability about
+// 2^-(32 + pbits) (a shared fingerprint is caught by the exact-key check).
+constexpr uint32_t kFpMul = 0x9e3779b1u;
+constexpr uint32_t kDigitMul = 0x85ebca77u;
+
 __device__ __forceinline__ KeyHash hash_key(const uint32_t k[8], int rows, int32_t dn, int pbits)
 {
-    KeyHash h;
-    h.fp = mix32(key_hash(k, rows) ^ (uint32_t)dn);
-    uint32_t g = 0x85ebca6bu ^ (uint32_t)rows ^ ((uint32_t)dn * 0x27d4eb2fu);
+    uint32_t a = 0x7f4a7c15u ^ (uint32_t)rows, g = 0x165667b1u ^ (uint32_t)rows;
 #pragma unroll
     for (int r = 0; r < 8; ++r)
-        if (r < rows) g = mix32(g ^ k[r] ^ 0x165667b1u);
-    h.digit = pbits ? mix32(g) >> (32 - pbits) : 0u;
+        if (r < rows) {
+            const uint32_t w = k[r] ^ (k[r] >> 16);
+            a = (a + w) * kFpMul;
+            g = (g + w) * kDigitMul;
+        }
+    KeyHash h;
+    h.fp = mix32(a ^ (uint32_t)dn);
+    h.digit = pbits ? mix32(g ^ ((uint32_t)dn * 0x27d4eb2fu)) >> (32 - pbits) : 0u;
     return h;
 }
 

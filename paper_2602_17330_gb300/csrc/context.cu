@@ -4,6 +4,8 @@
 
 #include <new>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
@@ -306,6 +308,70 @@ __global__ void pack_kernel(const uint8_t *__restrict__ codes, int code_stride, 
     }
 }
 
+// The same packing for code rows of a multiple of 4 bytes (codes 4-byte
+// aligned): each block stages its 256 rows with coalesced 32-bit loads into
+// shared memory (row pitch of an odd number of words, so the per-thread row
+// reads hit distinct banks), then every thread packs its row from there.
+constexpr int kPackRows = 256;
+constexpr int kPackMaxStrideWords = 16;  // code rows of up to 64 bytes take the staged path
+
+template <int WORDS>
+__global__ void __launch_bounds__(kPackRows) pack_staged_kernel(const uint32_t *__restrict__ codes, int stride_words,
+                                                                const uint8_t *__restrict__ lens, int64_t n,
+                                                                uint64_t *__restrict__ out, uint32_t *err)
+{
+    __shared__ uint32_t s_rows[kPackRows * (kPackMaxStrideWords + 1)];
+    const int max_len = WORDS == 2 ? 24 : 30;
+    const int pitch = stride_words | 1;  // odd
+    for (int64_t r0 = (int64_t)blockIdx.x * kPackRows; r0 < n; r0 += (int64_t)gridDim.x * kPackRows) {
+        const int rows = (int)(n - r0 < kPackRows ? n - r0 : kPackRows);
+        const uint32_t *src = codes + r0 * stride_words;
+        for (int w = threadIdx.x; w < rows * stride_words; w += blockDim.x) {
+            const int row = w / stride_words, col = w - row * stride_words;
+            s_rows[row * pitch + col] = src[w];
+        }
+        __syncthreads();
+        const int t = threadIdx.x;
+        if (t < rows) {
+            const int64_t i = r0 + t;
+            int L = lens[i];
+            bool bad = L < 1 || L > max_len || L > 4 * stride_words;
+            uint64_t w[WORDS];
+#pragma unroll
+            for (int k = 0; k < WORDS; ++k) w[k] = 0;
+            const uint32_t *row = s_rows + t * pitch;
+            const int Lc = min(min(L, max_len), 4 * stride_words);
+            for (int q = 0; q * 4 < Lc; ++q) {
+                const uint32_t word = row[q];
+#pragma unroll
+                for (int bpos = 0; bpos < 4; ++bpos) {
+                    const int p = 4 * q + bpos;
+                    if (p < Lc) {
+                        const uint32_t c = (word >> (8 * bpos)) & 0xffu;
+                        bad |= c >= 20u;
+                        const uint64_t v = (uint64_t)(c & 31u) << (5 * (p % 12));
+#pragma unroll
+                        for (int k = 0; k < WORDS; ++k)
+                            if (p / 12 == k) w[k] |= v;
+                    }
+                }
+            }
+            if (bad) {
+                atomicOr(err, SQ_DEVERR_INPUT);
+#pragma unroll
+                for (int k = 0; k < WORDS; ++k) w[k] = 0;
+                L = 0;
+            }
+            w[0] |= (uint64_t)(L & 15) << 60;
+            w[1] |= (uint64_t)(L >> 4) << 60;
+            uint64_t *dst = out + i * WORDS;
+            reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(w[0], w[1]);
+            if (WORDS == 4) reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(w[2 % WORDS], w[3 % WORDS]);
+        }
+        __syncthreads();
+    }
+}
+
 extern "C" int subquad_pack(subquad_ctx *ctx, const uint8_t *codes, int code_stride, const uint8_t *lens, int64_t n,
                             int pack_stride, void *packed_out)
 {
@@ -315,10 +381,22 @@ extern "C" int subquad_pack(subquad_ctx *ctx, const uint8_t *codes, int code_str
     if (reinterpret_cast<uintptr_t>(packed_out) % 16) return SUBQUAD_ERR_ARG;
     if (n == 0) return SUBQUAD_OK;
     unsigned grid = sq_grid(ctx, n, 256);
-    if (pack_stride == 16)
+    const bool staged = code_stride % 4 == 0 && code_stride / 4 <= kPackMaxStrideWords &&
+                        reinterpret_cast<uintptr_t>(codes) % 4 == 0;
+    if (staged) {
+        const unsigned sgrid = (unsigned)std::min<int64_t>((n + kPackRows - 1) / kPackRows, (int64_t)ctx->num_sms * 8);
+        const uint32_t *cw = reinterpret_cast<const uint32_t *>(codes);
+        if (pack_stride == 16)
+            pack_staged_kernel<2><<<sgrid, kPackRows, 0, ctx->stream>>>(cw, code_stride / 4, lens, n,
+                                                                        (uint64_t *)packed_out, ctx->d_err);
+        else
+            pack_staged_kernel<4><<<sgrid, kPackRows, 0, ctx->stream>>>(cw, code_stride / 4, lens, n,
+                                                                        (uint64_t *)packed_out, ctx->d_err);
+    } else if (pack_stride == 16) {
         pack_kernel<2><<<grid, 256, 0, ctx->stream>>>(codes, code_stride, lens, n, (uint64_t *)packed_out, ctx->d_err);
-    else
+    } else {
         pack_kernel<4><<<grid, 256, 0, ctx->stream>>>(codes, code_stride, lens, n, (uint64_t *)packed_out, ctx->d_err);
+    }
     SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
 }

@@ -57,6 +57,31 @@ def assert_fused_close(got, want):
 # (a1) signatures
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("stride", [16, 32])
+def test_pack_staged_and_byte_paths_agree(ctx, torch, stride):
+    """Code rows of 32 bytes take the shared-memory staged packer, rows of 33
+    bytes the per-byte one; both must give the same records, and the records
+    must decode to the input (5-bit codes, length in the top nibbles of words
+    0 and 1).  n spans several grid strides and a ragged last block."""
+    rng = np.random.default_rng(5 + stride)
+    n = 311_373
+    max_len = 24 if stride == 16 else 30
+    lens = rng.integers(1, max_len + 1, n).astype(np.uint8)
+    codes32 = rng.integers(0, 20, (n, 32)).astype(np.uint8)
+    codes33 = np.zeros((n, 33), np.uint8)
+    codes33[:, :32] = codes32
+    a = to_np(ctx.pack(torch.from_numpy(codes32), torch.from_numpy(lens), stride))
+    b = to_np(ctx.pack(torch.from_numpy(codes33), torch.from_numpy(lens), stride))
+    assert (a == b).all()
+    w = np.ascontiguousarray(a).view(np.uint64).reshape(n, stride // 8)
+    L = (w[:, 0] >> np.uint64(60)) | ((w[:, 1] >> np.uint64(60)) << np.uint64(4))
+    assert (L.astype(np.int64) == lens).all()
+    for p in range(max_len):
+        code = (w[:, p // 12] >> np.uint64(5 * (p % 12))) & np.uint64(31)
+        mask = p < lens
+        assert (code[mask].astype(np.int64) == codes32[mask, p]).all()
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 6])
 def test_sign_bitexact_tiny(ctx, torch, oracle_mod, k):
     rep = synth.tiny_repertoire()
@@ -202,30 +227,29 @@ def test_candidates_split_partitions(ctx, torch, oracle_mod, cap):
         ctx.set_tuning(subquad.TUNE_BAND_PART_LOG2, old)
 
 
-def _mix32(h):
-    h &= 0xFFFFFFFF
-    h ^= h >> 16
-    h = (h * 0x7FEB352D) & 0xFFFFFFFF
-    h ^= h >> 15
-    h = (h * 0x846CA68B) & 0xFFFFFFFF
-    h ^= h >> 16
-    return h
+FP_MUL = 0x9E3779B1  # the library's fingerprint multiplier
+
+
+def _premix(w):
+    return (w ^ (w >> 16)) & 0xFFFFFFFF  # its own inverse
 
 
 def test_candidates_fingerprint_clash(ctx, torch, oracle_mod):
     """White-box: distinct 2-row keys built to share the library's 32-bit key
-    fingerprint (a chain of 32-bit mixes) must stay in separate buckets.  With
-    at most 1024 keys per band (the default partition target) every band is a
+    fingerprint (words pre-mixed by w ^ w >> 16, summed by Horner with an odd
+    multiplier mod 2^32, then mixed) must stay in separate buckets.  With at
+    most 1024 keys per band (the default partition target) every band is a
     single partition, so the equal fingerprints meet in one table."""
     rng = np.random.default_rng(77)
     n, bands, rows = 1000, 2, 2
     sig = rng.integers(0, 40, (n, bands * rows)).astype(np.uint32)
-    c0 = 0x9E3779B9 ^ rows
     groups = []
     for g in range(6):
         k0, k1 = 1000 + 2 * g, 5000 + g
         k0b = 1001 + 2 * g
-        k1b = _mix32(c0 ^ k0) ^ k1 ^ _mix32(c0 ^ k0b)  # same fingerprint, different key
+        # (s + p(k0)) M + p(k1) == (s + p(k0b)) M + p(k1b)  (mod 2^32)
+        k1b = _premix((_premix(k1) + (_premix(k0) - _premix(k0b)) * FP_MUL) & 0xFFFFFFFF)
+        assert (k0b, k1b) != (k0, k1)
         groups.append(((k0, k1), (k0b, k1b)))
     ids = rng.permutation(n)[:6 * 9]
     for g, ((a0, a1), (b0, b1)) in enumerate(groups):
