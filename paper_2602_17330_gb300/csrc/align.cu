@@ -232,16 +232,11 @@ __device__ __forceinline__ uint32_t bin_of_item(const uint64_t *__restrict__ pac
     return (uint32_t)(Lq * 32 + Lt);
 }
 
-// Warp-aggregated shared-memory add: the peers with the same bin add once.
-__device__ __forceinline__ uint32_t warp_smem_add(uint32_t *s_arr, uint32_t bin, bool valid)
+// Shared-memory add of one item to its bin; returns the item's position
+// among the bin's adds (any order).
+__device__ __forceinline__ uint32_t smem_bin_add(uint32_t *s_arr, uint32_t bin, bool valid)
 {
-    const uint32_t key = valid ? bin : 0xffffffffu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, key);
-    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (valid && lane == leader) base = atomicAdd(&s_arr[bin], (uint32_t)__popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    return base + __popc(peers & ((1u << lane) - 1u));
+    return valid ? atomicAdd(&s_arr[bin], 1u) : 0u;
 }
 
 // Each block histograms one contiguous range of items in shared memory and
@@ -267,7 +262,7 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const uint64_t *__restri
             bin = bin_of_item<WORDS, SELF>(packed, pairs, p, symmetric);
             bin_of[p] = (uint16_t)bin;
         }
-        warp_smem_add(s_hist, bin, valid);
+        smem_bin_add(s_hist, bin, valid);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kBins; b += blockDim.x)
@@ -319,7 +314,7 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(const uint16_t *__rest
     for (int64_t base = lo; base < hi; base += blockDim.x) {
         const int64_t p = base + threadIdx.x;
         const bool valid = p < hi;
-        warp_smem_add(s_cnt, valid ? bin_of[p] : 0u, valid);
+        smem_bin_add(s_cnt, valid ? bin_of[p] : 0u, valid);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kBins; b += blockDim.x) {
@@ -331,7 +326,7 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(const uint16_t *__rest
         const int64_t p = base + threadIdx.x;
         const bool valid = p < hi;
         const uint32_t bin = valid ? bin_of[p] : 0u;
-        const uint32_t r = warp_smem_add(s_cnt, bin, valid);
+        const uint32_t r = smem_bin_add(s_cnt, bin, valid);
         if (valid) order[s_base[bin] + r] = (uint32_t)p;
     }
 }
