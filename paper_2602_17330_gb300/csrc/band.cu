@@ -847,6 +847,44 @@ __device__ __forceinline__ RunOf run_of(uint32_t key, uint32_t lane)
 // lane decodes its (u, v) and keeps pair (i, j) only if no earlier band
 // already puts i and j in one chunk (first-band ownership), so every pair of
 // C is emitted exactly once.
+// Positions of up to two appends per thread in one block-wide reservation:
+// the block's f0 appends first (in thread order), then its f1 appends, so the
+// output keeps the order of each span.  Every thread of the block must call it.
+__device__ __forceinline__ void block_append2(bool f0, bool f1, unsigned long long *counter,
+                                              unsigned long long *s_base, uint32_t *s_warp,
+                                              unsigned long long &p0, unsigned long long &p1)
+{
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t c = (uint32_t)f0 | ((uint32_t)f1 << 16);  // two counters of < 2^16 (blockDim <= 1024)
+    uint32_t inc = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= (uint32_t)d) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (uint32_t w = 0; w < nw; ++w) {
+            const uint32_t t = s_warp[w];
+            s_warp[w] = run;
+            run += t;
+        }
+        const uint32_t n0 = run & 0xffffu, n1 = run >> 16;
+        s_warp[nw] = n0;
+        *s_base = n0 + n1 ? atomicAdd(counter, (unsigned long long)(n0 + n1)) : 0ull;
+    }
+    __syncthreads();
+    const uint32_t excl = s_warp[warp] + inc - c;
+    p0 = *s_base + (excl & 0xffffu);
+    p1 = *s_base + s_warp[nw] + (excl >> 16);
+    __syncthreads();
+}
+
+// Each block iteration takes two spans of blockDim raw pairs, so every thread
+// carries two independent chains of dependent loads (chunk -> chunk entry ->
+// member ids -> masks and chunk ids) in flight.
 __global__ void __launch_bounds__(256) band_emit_kernel(
     const uint32_t *__restrict__ kept_ids, const uint32_t *__restrict__ heads, const uint32_t *__restrict__ sizes,
     const uint32_t *__restrict__ cband, const uint64_t *__restrict__ poff, const uint32_t *__restrict__ wchunk,
@@ -855,69 +893,99 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
     uint32_t *__restrict__ out, int64_t capacity, unsigned long long *__restrict__ d_count,
     uint32_t *__restrict__ deg, uint32_t *err)
 {
+    constexpr int H = 2;
     __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_warp[33];
     const uint32_t nc = *d_nchunks;
     const uint64_t total = min(*d_total, raw1);  // raw pairs [raw0, total) of this call; raw0 % 32 == 0
     const uint32_t lane = threadIdx.x & 31;
-    // block-uniform trip count (block_append synchronises the block)
-    for (uint64_t b0 = raw0 + (uint64_t)blockIdx.x * blockDim.x; b0 < total; b0 += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t q0 = b0 + (threadIdx.x & ~31u);
-        const uint64_t q = q0 + lane;
-        uint32_t c0 = 0, starts = 0;
-        if (q0 < total) {
-            c0 = q0 / 32 < (uint64_t)wmax ? wchunk[q0 / 32] : chunk_of_raw(poff, nc, q0);
-            const uint32_t c = c0 + 1 + lane;
-            if (c < nc) {
-                const uint64_t d = poff[c] - q0;  // >= 1: chunk c starts after q0
-                if (d < 32) starts = 1u << d;
+    // block-uniform trip count (block_append2 synchronises the block)
+    for (uint64_t b0 = raw0 + (uint64_t)blockIdx.x * blockDim.x * H; b0 < total;
+         b0 += (uint64_t)gridDim.x * blockDim.x * H) {
+        uint64_t q0[H], q[H];
+        uint32_t c0[H], starts[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            q0[h] = b0 + (uint64_t)h * blockDim.x + (threadIdx.x & ~31u);
+            q[h] = q0[h] + lane;
+            c0[h] = 0;
+            starts[h] = 0;
+            if (q0[h] < total) {
+                c0[h] = q0[h] / 32 < (uint64_t)wmax ? wchunk[q0[h] / 32] : chunk_of_raw(poff, nc, q0[h]);
+                const uint32_t c = c0[h] + 1 + lane;
+                if (c < nc) {
+                    const uint64_t d = poff[c] - q0[h];  // >= 1: chunk c starts after q0
+                    if (d < 32) starts[h] = 1u << d;
+                }
             }
         }
-        starts = __reduce_or_sync(0xffffffffu, starts);
-        bool owned = false;
-        uint32_t i = 0, j = 0;
-        if (q < total) {
-            const uint32_t cl = c0 + __popc(starts & ((2u << lane) - 1u));
-            const uint32_t h = heads[cl], s = sizes[cl];
-            const int b = (int)cband[cl];
-            uint32_t u, v;
-            decode_pair(q - poff[cl], s, u, v);
-            if (u >= v || v >= s) {  // cannot happen for a consistent chunk list
-                atomicOr(err, SQ_DEVERR_TIMEOUT);
-                u = 0;
-                v = 1;
+        bool owned[H];
+        uint32_t i[H], j[H], b[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            starts[h] = __reduce_or_sync(0xffffffffu, starts[h]);
+            owned[h] = false;
+            i[h] = j[h] = b[h] = 0;
+            if (q[h] < total) {
+                const uint32_t cl = c0[h] + __popc(starts[h] & ((2u << lane) - 1u));
+                const uint32_t hd = heads[cl], sz = sizes[cl];
+                b[h] = cband[cl];
+                uint32_t u, v;
+                decode_pair(q[h] - poff[cl], sz, u, v);
+                if (u >= v || v >= sz) {  // cannot happen for a consistent chunk list
+                    atomicOr(err, SQ_DEVERR_TIMEOUT);
+                    u = 0;
+                    v = 1;
+                }
+                i[h] = kept_ids[hd + u];
+                j[h] = kept_ids[hd + v];
+                owned[h] = true;
             }
-            i = kept_ids[h + u];
-            j = kept_ids[h + v];
-            if (i > j) {
-                const uint32_t t = i;
-                i = j;
-                j = t;
+        }
+        uint32_t common[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            if (i[h] > j[h]) {
+                const uint32_t t = i[h];
+                i[h] = j[h];
+                j[h] = t;
             }
-            owned = true;
-            const uint32_t *gi = chunk_of + (int64_t)i * bands;
-            const uint32_t *gj = chunk_of + (int64_t)j * bands;
             // earlier bands where both are in some chunk (mask), then their chunk ids
-            uint32_t common = kept_mask[i] & kept_mask[j] & (b >= 32 ? 0xffffffffu : ((1u << b) - 1u));
-            while (common) {
-                const int bb = __ffs(common) - 1;
-                common &= common - 1u;
-                owned = owned && gi[bb] != gj[bb];
+            common[h] = owned[h] ? kept_mask[i[h]] & kept_mask[j[h]] &
+                                       (b[h] >= 32 ? 0xffffffffu : ((1u << b[h]) - 1u))
+                                 : 0u;
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            if (!owned[h]) continue;
+            const uint32_t *gi = chunk_of + (int64_t)i[h] * bands;
+            const uint32_t *gj = chunk_of + (int64_t)j[h] * bands;
+            while (common[h]) {
+                const int bb = __ffs(common[h]) - 1;
+                common[h] &= common[h] - 1u;
+                if (gi[bb] == gj[bb]) {
+                    owned[h] = false;
+                    break;
+                }
             }
-            for (int bb = 32; bb < b; ++bb) {
+            for (int bb = 32; owned[h] && bb < (int)b[h]; ++bb) {
                 const uint32_t x = gi[bb], y = gj[bb];
-                owned = owned && !(x == y && x != kNoChunk);
+                if (x == y && x != kNoChunk) owned[h] = false;
             }
         }
-        const unsigned long long pos = block_append(owned, d_count, &s_base, s_warp);
-        const bool written = owned && pos < (unsigned long long)capacity;
-        if (written) reinterpret_cast<uint2 *>(out)[pos] = make_uint2(i, j);
-        if (deg) {
-            // one count per run of equal first members (a chunk's pairs come
-            // in runs sharing i): the run's first written lane adds them all
-            const RunOf r = run_of(q < total ? i : 0xffffffffu, lane);
-            const uint32_t mine = __ballot_sync(0xffffffffu, written) & r.mask;
-            if (written && lane == (uint32_t)__ffs(mine) - 1u) atomicAdd(&deg[i], (uint32_t)__popc(mine));
+        unsigned long long pos[H];
+        block_append2(owned[0], owned[1], d_count, &s_base, s_warp, pos[0], pos[1]);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const bool written = owned[h] && pos[h] < (unsigned long long)capacity;
+            if (written) reinterpret_cast<uint2 *>(out)[pos[h]] = make_uint2(i[h], j[h]);
+            if (deg) {
+                // one count per run of equal first members (a chunk's pairs come
+                // in runs sharing i): the run's first written lane adds them all
+                const RunOf r = run_of(q[h] < total ? i[h] : 0xffffffffu, lane);
+                const uint32_t mine = __ballot_sync(0xffffffffu, written) & r.mask;
+                if (written && lane == (uint32_t)__ffs(mine) - 1u) atomicAdd(&deg[i[h]], (uint32_t)__popc(mine));
+            }
         }
     }
 }
