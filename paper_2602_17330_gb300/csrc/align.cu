@@ -254,15 +254,23 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const uint64_t *__restri
     __syncthreads();
     const int64_t per = (m + gridDim.x - 1) / gridDim.x;
     const int64_t lo = (int64_t)blockIdx.x * per, hi = min(m, lo + per);
-    for (int64_t base = lo; base < hi; base += blockDim.x) {
-        const int64_t p = base + threadIdx.x;
-        const bool valid = p < hi;
-        uint32_t bin = 0;
-        if (valid) {
-            bin = bin_of_item<WORDS, SELF>(packed, pairs, p, symmetric);
-            bin_of[p] = (uint16_t)bin;
+    // four items per thread and iteration: their record gathers in flight together
+    constexpr int H = 4;
+    for (int64_t base = lo; base < hi; base += (int64_t)blockDim.x * H) {
+        uint32_t bin[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int64_t p = base + h * (int64_t)blockDim.x + threadIdx.x;
+            bin[h] = p < hi ? bin_of_item<WORDS, SELF>(packed, pairs, p, symmetric) : kBins;
         }
-        smem_bin_add(s_hist, bin, valid);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int64_t p = base + h * (int64_t)blockDim.x + threadIdx.x;
+            if (bin[h] < (uint32_t)kBins) {
+                bin_of[p] = (uint16_t)bin[h];
+                smem_bin_add(s_hist, bin[h], true);
+            }
+        }
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kBins; b += blockDim.x)
@@ -311,10 +319,17 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(const uint16_t *__rest
     __syncthreads();
     const int64_t per = (m + gridDim.x - 1) / gridDim.x;
     const int64_t lo = (int64_t)blockIdx.x * per, hi = min(m, lo + per);
-    for (int64_t base = lo; base < hi; base += blockDim.x) {
-        const int64_t p = base + threadIdx.x;
-        const bool valid = p < hi;
-        smem_bin_add(s_cnt, valid ? bin_of[p] : 0u, valid);
+    constexpr int H = 4;
+    for (int64_t base = lo; base < hi; base += (int64_t)blockDim.x * H) {
+        uint32_t bin[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int64_t p = base + h * (int64_t)blockDim.x + threadIdx.x;
+            bin[h] = p < hi ? bin_of[p] : (uint32_t)kBins;
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+            if (bin[h] < (uint32_t)kBins) smem_bin_add(s_cnt, bin[h], true);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kBins; b += blockDim.x) {
@@ -322,12 +337,18 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(const uint16_t *__rest
         s_cnt[b] = 0;
     }
     __syncthreads();
-    for (int64_t base = lo; base < hi; base += blockDim.x) {
-        const int64_t p = base + threadIdx.x;
-        const bool valid = p < hi;
-        const uint32_t bin = valid ? bin_of[p] : 0u;
-        const uint32_t r = smem_bin_add(s_cnt, bin, valid);
-        if (valid) order[s_base[bin] + r] = (uint32_t)p;
+    for (int64_t base = lo; base < hi; base += (int64_t)blockDim.x * H) {
+        uint32_t bin[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int64_t p = base + h * (int64_t)blockDim.x + threadIdx.x;
+            bin[h] = p < hi ? bin_of[p] : (uint32_t)kBins;
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int64_t p = base + h * (int64_t)blockDim.x + threadIdx.x;
+            if (bin[h] < (uint32_t)kBins) order[s_base[bin[h]] + smem_bin_add(s_cnt, bin[h], true)] = (uint32_t)p;
+        }
     }
 }
 

@@ -1100,20 +1100,37 @@ __global__ void pairs_scatter_kernel(const uint32_t *__restrict__ pairs, const u
                                      const uint32_t *__restrict__ rowoff, uint32_t *__restrict__ fill,
                                      uint32_t *__restrict__ col)
 {
+    constexpr int H = 4;  // groups of 32 pairs per warp and iteration, their loads in flight together
     const int64_t m = (int64_t)*d_m;
     const uint32_t lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // warp-uniform trip count; a run of equal first members takes its slots
     // with one atomic (positions old-1, old-2, ... in lane order)
-    for (int64_t pb = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); pb < m;
-         pb += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = pb + lane;
-        const bool valid = p < m;
-        const uint2 ij = valid ? reinterpret_cast<const uint2 *>(pairs)[p] : make_uint2(0xffffffffu, 0u);
-        const RunOf r = run_of(ij.x, lane);
-        uint32_t top = 0;
-        if (valid && lane == r.first) top = atomicSub(&fill[ij.x], (uint32_t)__popc(r.mask));
-        top = __shfl_sync(0xffffffffu, top, r.first);
-        if (valid) col[rowoff[ij.x] + top - 1u - (lane - r.first)] = ij.y;
+    for (int64_t pb = warp * 32 * H; pb < m; pb += nwarps * 32 * H) {
+        uint2 ij[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int64_t p = pb + h * 32 + lane;
+            ij[h] = p < m ? reinterpret_cast<const uint2 *>(pairs)[p] : make_uint2(0xffffffffu, 0u);
+        }
+        uint32_t top[H], first[H], off[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const RunOf r = run_of(ij[h].x, lane);
+            first[h] = r.first;
+            top[h] = 0;
+            off[h] = 0;
+            if (ij[h].x != 0xffffffffu) {
+                if (lane == r.first) top[h] = atomicSub(&fill[ij[h].x], (uint32_t)__popc(r.mask));
+                off[h] = rowoff[ij[h].x];
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const uint32_t t = __shfl_sync(0xffffffffu, top[h], first[h]);
+            if (ij[h].x != 0xffffffffu) col[off[h] + t - 1u - (lane - first[h])] = ij[h].y;
+        }
     }
 }
 
