@@ -1,12 +1,14 @@
 // Device-wide scan (banding, binning) and stable LSD radix sort (pair index of
 // the gate training).
 //
-// Scan: one pass over tiles of 4096 elements (256 threads x 16) with
-// decoupled look-back between tiles.  Radix sort: 8-bit digits; per pass
+// Scan: reduce-then-scan over at most two chunks per SM, each chunk scanned
+// in tiles of 4096 elements (256 threads x 16).  Radix sort: 8-bit digits; per pass
 // a digit histogram per tile (warp-aggregated shared-memory counts), a scan of
 // the digit-major histogram, and a stable scatter in which each warp ranks its
 // 256 elements round by round with __match_any_sync so equal digits keep their
 // input order.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace {
@@ -88,106 +90,94 @@ __device__ __forceinline__ void load_tile(const T *in, int64_t base, int64_t cou
     __syncthreads();
 }
 
-// Single-pass scan with decoupled look-back: each CTA takes the next tile
-// index from a counter (so every lower tile belongs to a CTA already
-// running), publishes its tile total, then warp 0 reads the status words of
-// the 32 preceding tiles at a time: a tile that has published its inclusive
-// prefix ends the walk, tiles with only a total are added and the window
-// moves back.  Status word: flag in bits 62..63, value below (values and
-// totals stay under 2^62).  Spins on an unpublished tile are bounded;
-// running out sets the TIMEOUT error bit instead of waiting forever.
-constexpr unsigned long long kScanFlagAgg = 1ull << 62;
-constexpr unsigned long long kScanFlagPre = 2ull << 62;
-constexpr unsigned long long kScanValue = (1ull << 62) - 1ull;
-constexpr long long kScanSpinLimit = 1ll << 22;
-
+// Reduce-then-scan over G contiguous chunks (whole tiles of kScanTile
+// elements; G at most two per SM): one kernel reduces every chunk, a second
+// one gives each chunk its prefix (the reduction of the chunk totals before
+// it) and scans the chunk tile by tile with a running carry.  Two passes over
+// the input, one over the output, and no waiting between CTAs.
 template <typename T, bool MAX>
-__device__ __forceinline__ T warp_reduce(T v)
+__device__ __forceinline__ T block_reduce(T v, T *s_warp)
 {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v = op<T, MAX>(v, __shfl_xor_sync(0xffffffffu, v, d));
-    return v;
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    T r = T(0);
+    for (int w = 0; w < nw; ++w) r = op<T, MAX>(r, s_warp[w]);
+    __syncthreads();
+    return r;
+}
+
+// Chunk [lo, hi) of chunk b: chunks are whole tiles, the last one ragged.
+__device__ __forceinline__ void scan_chunk(int64_t count, int64_t b, int64_t G, int64_t &lo, int64_t &hi)
+{
+    const int64_t tiles = (count + kScanTile - 1) / kScanTile;
+    const int64_t per = (tiles + G - 1) / G;
+    lo = min(count, b * per * kScanTile);
+    hi = min(count, lo + per * kScanTile);
 }
 
 template <typename T, bool MAX>
-__global__ void __launch_bounds__(kScanThreads) scan_onepass_kernel(const T *__restrict__ in, T *__restrict__ out,
-                                                                    int64_t count_max,
-                                                                    const uint32_t *__restrict__ d_count,
-                                                                    bool inclusive, unsigned long long *status,
-                                                                    uint32_t *tile_counter, T *total_out,
-                                                                    uint32_t *err)
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T *__restrict__ in, int64_t count_max,
+                                                                   const uint32_t *__restrict__ d_count,
+                                                                   T *__restrict__ partial)
+{
+    __shared__ T s_warp[32];
+    const int64_t count = eff_count(count_max, d_count);
+    int64_t lo, hi;
+    scan_chunk(count, blockIdx.x, gridDim.x, lo, hi);
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    int64_t g = lo + threadIdx.x;
+    for (; g + 3 * kScanThreads < hi; g += 4 * kScanThreads) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = op<T, MAX>(acc[u], in[g + u * kScanThreads]);
+    }
+    for (; g < hi; g += kScanThreads) acc[0] = op<T, MAX>(acc[0], in[g]);
+    const T r = block_reduce<T, MAX>(op<T, MAX>(op<T, MAX>(acc[0], acc[1]), op<T, MAX>(acc[2], acc[3])), s_warp);
+    if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
+template <typename T, bool MAX>
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const T *__restrict__ in, T *__restrict__ out,
+                                                                  int64_t count_max,
+                                                                  const uint32_t *__restrict__ d_count,
+                                                                  bool inclusive, const T *__restrict__ partial,
+                                                                  T *total_out)
 {
     __shared__ T s_buf[kScanTilePadded];
-    __shared__ uint32_t s_tile;
-    __shared__ T s_prefix;
+    __shared__ T s_warp[32];
     const int64_t count = eff_count(count_max, d_count);
-    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
-    __syncthreads();
-    const int64_t t = s_tile;
-    const int64_t base = t * kScanTile;
-    if (base >= count) {
-        if (t == 0 && threadIdx.x == 0 && total_out) *total_out = T(0);  // empty input
-        return;
-    }
-    T items[kScanItems];
-    load_tile(in, base, count, s_buf, items);
-    T acc = items[0];
+    int64_t lo, hi;
+    scan_chunk(count, blockIdx.x, gridDim.x, lo, hi);
+    // prefix of this chunk: the chunk totals before it
+    T pre = T(0);
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += kScanThreads) pre = op<T, MAX>(pre, partial[k]);
+    T carry = block_reduce<T, MAX>(pre, s_warp);
+    for (int64_t base = lo; base < hi; base += kScanTile) {
+        T items[kScanItems];
+        load_tile(in, base, hi, s_buf, items);
+        T acc = items[0];
 #pragma unroll
-    for (int q = 1; q < kScanItems; ++q) acc = op<T, MAX>(acc, items[q]);
-    T total;
-    const T excl = block_exclusive<T, MAX>(acc, &total);
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        T prefix = T(0);
-        if (t == 0) {
-            if (lane == 0) atomicExch(&status[0], kScanFlagPre | (unsigned long long)total);
-        } else {
-            if (lane == 0) atomicExch(&status[t], kScanFlagAgg | (unsigned long long)total);
-            T run = T(0);
-            int64_t j = t - 1;
-            long long spins = 0;
-            for (;;) {
-                const int64_t idx = j - lane;
-                unsigned long long v = kScanFlagPre;
-                if (idx >= 0) v = *(volatile unsigned long long *)&status[idx];
-                while (__any_sync(0xffffffffu, (v >> 62) == 0)) {
-                    if ((v >> 62) == 0) v = *(volatile unsigned long long *)&status[idx];
-                    if (++spins > kScanSpinLimit) {
-                        if (lane == 0) atomicOr(err, SQ_DEVERR_TIMEOUT);
-                        v = kScanFlagPre;  // give up: the error bit is set
-                    }
-                }
-                const uint32_t pmask = __ballot_sync(0xffffffffu, (v & kScanFlagPre) != 0);
-                const T val = (T)(v & kScanValue);
-                if (pmask) {
-                    const int k = __ffs(pmask) - 1;  // nearest tile with its inclusive prefix
-                    run = op<T, MAX>(run, warp_reduce<T, MAX>(lane <= k ? val : T(0)));
-                    break;
-                }
-                run = op<T, MAX>(run, warp_reduce<T, MAX>(val));
-                j -= 32;
-            }
-            prefix = run;
-            if (lane == 0) atomicExch(&status[t], kScanFlagPre | (unsigned long long)op<T, MAX>(prefix, total));
-        }
-        if (lane == 0) {
-            s_prefix = prefix;
-            if (total_out && base + kScanTile >= count) *total_out = op<T, MAX>(prefix, total);
-        }
-    }
-    __syncthreads();
-    T run = op<T, MAX>(s_prefix, excl);
+        for (int q = 1; q < kScanItems; ++q) acc = op<T, MAX>(acc, items[q]);
+        T total;
+        const T excl = block_exclusive<T, MAX>(acc, &total);
+        T run = op<T, MAX>(carry, excl);
 #pragma unroll
-    for (int q = 0; q < kScanItems; ++q) {
-        const T next = op<T, MAX>(run, items[q]);
-        s_buf[pad(threadIdx.x * kScanItems + q)] = inclusive ? next : run;
-        run = next;
+        for (int q = 0; q < kScanItems; ++q) {
+            const T next = op<T, MAX>(run, items[q]);
+            s_buf[pad(threadIdx.x * kScanItems + q)] = inclusive ? next : run;
+            run = next;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < kScanTile; q += kScanThreads) {
+            const int64_t g = base + q;
+            if (g < hi) out[g] = s_buf[pad(q)];
+        }
+        __syncthreads();
+        carry = op<T, MAX>(carry, total);
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < kScanTile; q += kScanThreads) {
-        const int64_t g = base + q;
-        if (g < count) out[g] = s_buf[pad(q)];
-    }
+    if (total_out && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) *total_out = carry;
 }
 
 template <typename T, bool MAX>
@@ -199,13 +189,13 @@ int scan_impl(subquad_ctx *ctx, const T *in, T *out, int64_t count, const uint32
         return SUBQUAD_OK;
     }
     const int64_t ntiles = (count + kScanTile - 1) / kScanTile;
-    const size_t need = (size_t)(ntiles + 1) * sizeof(unsigned long long);
-    if (need > tmp_bytes) return SUBQUAD_ERR_ARG;
-    unsigned long long *status = static_cast<unsigned long long *>(tmp);
-    uint32_t *counter = reinterpret_cast<uint32_t *>(status + ntiles);
-    SQ_TRY_CUDA(cudaMemsetAsync(tmp, 0, need, ctx->stream));
-    scan_onepass_kernel<T, MAX><<<(unsigned)ntiles, kScanThreads, 0, ctx->stream>>>(
-        in, out, count, d_count, inclusive, status, counter, total_out, ctx->d_err);
+    const int64_t G = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 2);
+    if ((size_t)G * sizeof(T) > tmp_bytes) return SUBQUAD_ERR_ARG;
+    T *partial = static_cast<T *>(tmp);
+    scan_reduce_kernel<T, MAX><<<(unsigned)G, kScanThreads, 0, ctx->stream>>>(in, count, d_count, partial);
+    SQ_LAUNCH_CHECK();
+    scan_apply_kernel<T, MAX><<<(unsigned)G, kScanThreads, 0, ctx->stream>>>(in, out, count, d_count, inclusive,
+                                                                            partial, total_out);
     SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
 }
