@@ -98,6 +98,20 @@ def traffic_for(kernel: str):
     return entry["dram_bytes_per_launch"] if digest == entry.get("source_sha256") else None
 
 
+def whole_job(total_ms: float, units: float, world: int, device) -> tuple[float, float]:
+    """(time of the slowest rank, units of all ranks): whole-job throughput is
+    units / time.  One process per GPU; device is this rank's (CPU for gloo)."""
+    if world <= 1:
+        return total_ms, units
+    import torch
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
@@ -305,21 +319,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     clocks = sampler.stop() if sampler else None
 
     # whole job: units over all ranks / max time over ranks
-    def whole_job(ms_list):
-        total_ms = sum(ms_list)
-        if world > 1:
-            t = torch.tensor([total_ms, float(m) * args.steps], dtype=torch.float64, device=dev)
-            tmax = t.clone()
-            torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-            torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-            return float(tmax[0]), float(t[1])
-        return total_ms, float(m) * args.steps
-
-    e_max_ms, e_units = whole_job(step_ms)
+    e_max_ms, e_units = whole_job(sum(step_ms), float(m) * args.steps, world, dev)
     eager = {"value": e_units / (e_max_ms / 1e3), "unit": UNIT, "ms_per_step": e_max_ms / args.steps,
              "note": "the same step launched kernel by kernel from the host, per-stage events between stages"}
     if graph_ms is not None:
-        max_ms, total_units = whole_job(graph_ms)
+        max_ms, total_units = whole_job(sum(graph_ms), float(m) * args.steps, world, dev)
         timed_mode = "cuda graph replay"
     else:
         max_ms, total_units = e_max_ms, e_units
@@ -690,13 +694,7 @@ def run_e2e(args, pipe, rep, a, b, emb, params, stream, dev, world):
     e1.record(cout)
     torch.cuda.synchronize(dev)
     ctx.check()
-    total = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([total], dtype=torch.float64, device=dev)
-        uu = torch.tensor([units], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(uu, op=torch.distributed.ReduceOp.SUM)
-        total, units = float(tt), float(uu)
+    total, units = whole_job(e0.elapsed_time(e1), units, world, dev)
     return {"value": units / (total / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(max(d2h)), "ms_per_step": total / args.steps,
             "overlap": "input copies, device-count compute and result copies of neighbouring steps on separate "
