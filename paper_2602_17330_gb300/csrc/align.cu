@@ -616,18 +616,37 @@ __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::b
         const int wmax = __reduce_max_sync(0xffffffffu, max(LaP, LaQ));
         if (vP) {
             uint32_t sc;
-            switch ((wmax + 1) >> 1) {
+            // rows: the warp's longest query, exactly for the pair lists' common
+            // lengths (7..24 with 16-byte records), else rounded up to even
+            constexpr bool kExact = WORDS == 2 && !SELF;
+            if (kExact && wmax >= 7) {
+                switch (wmax) {
+#define SQ_EXACT(N)                                                                                                \
+    case N:                                                                                                        \
+        sc = sw_pair2<WORDS, (N <= MAXLEN ? N : MAXLEN)>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e);      \
+        break;
+                    SQ_EXACT(7) SQ_EXACT(8) SQ_EXACT(9) SQ_EXACT(10) SQ_EXACT(11) SQ_EXACT(12) SQ_EXACT(13)
+                    SQ_EXACT(14) SQ_EXACT(15) SQ_EXACT(16) SQ_EXACT(17) SQ_EXACT(18) SQ_EXACT(19) SQ_EXACT(20)
+                    SQ_EXACT(21) SQ_EXACT(22) SQ_EXACT(23)
+#undef SQ_EXACT
+                default:
+                    sc = sw_pair2<WORDS, MAXLEN>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e);
+                    break;
+                }
+            } else {
+                switch ((wmax + 1) >> 1) {
 #define SQ_CASE(H)                                                                                                 \
     case H:                                                                                                        \
         sc = sw_pair2<WORDS, (H < 1 ? 2 : (2 * H <= MAXLEN ? 2 * H : MAXLEN))>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ,  \
                                                                               s_tab, lane, o, e);                   \
         break;
-                SQ_CASE(0) SQ_CASE(1) SQ_CASE(2) SQ_CASE(3) SQ_CASE(4) SQ_CASE(5) SQ_CASE(6) SQ_CASE(7) SQ_CASE(8)
-                SQ_CASE(9) SQ_CASE(10) SQ_CASE(11) SQ_CASE(12)
+                    SQ_CASE(0) SQ_CASE(1) SQ_CASE(2) SQ_CASE(3) SQ_CASE(4) SQ_CASE(5) SQ_CASE(6) SQ_CASE(7)
+                    SQ_CASE(8) SQ_CASE(9) SQ_CASE(10) SQ_CASE(11) SQ_CASE(12)
 #undef SQ_CASE
-            default:
-                sc = sw_pair2<WORDS, MAXLEN>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e);
-                break;
+                default:
+                    sc = sw_pair2<WORDS, MAXLEN>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e);
+                    break;
+                }
             }
             out[curP.z] = (int32_t)(sc & 0xffffu);
             if (vQ) out[curQ.z] = (int32_t)(sc >> 16);
