@@ -300,6 +300,25 @@ def test_candidates_row_longer_than_shared_memory(ctx, torch, oracle_mod):
     assert got.shape == want.shape and (got == want).all()
 
 
+@pytest.mark.parametrize("n,nbig,size,cap", [(3_000, 3, 300, 64), (20_000, 40, 500, 64), (20_000, 40, 500, 499)])
+def test_candidates_several_buckets_above_cap(ctx, torch, oracle_mod, n, nbig, size, cap):
+    """Several buckets above the cap in one partition: with 900 repeated keys
+    among 3,000 (one partition) the shared-memory fast path sorts three
+    buckets one after another; with 40 buckets of 500 among 20,000 (16
+    partitions of ~1,250 records, too many repeats for the fast path) the
+    exact path does.  Chunks must hold ranks [m cap, (m+1) cap) in id order."""
+    rng = np.random.default_rng(n + nbig + cap)
+    bands, rows = 3, 2
+    sig = rng.integers(0, 1 << 31, (n, bands * rows)).astype(np.uint32)  # singletons
+    for b in range(bands):
+        ids = rng.permutation(n)[:nbig * size]
+        for g in range(nbig):
+            sig[ids[g * size:(g + 1) * size], b * rows:(b + 1) * rows] = rng.integers(0, 1 << 31, rows)
+    got = gpu_candidates_from_sig(ctx, torch, sig, bands, rows, cap)
+    want = oracle_mod.candidates(sig, bands, rows, cap)
+    assert got.shape == want.shape and (got == want).all()
+
+
 @pytest.mark.parametrize("n,cap", [(20_000, 64), (20_000, 1), (3_000, 1_200), (2_500, 0)])
 def test_candidates_one_giant_bucket(ctx, torch, oracle_mod, n, cap):
     """Every sequence has the same key in every band: one bucket of n members
