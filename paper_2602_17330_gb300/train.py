@@ -80,3 +80,27 @@ class GateTrainer:
         if self.train_emb:
             st.update(emb=self.emb, m1e=self.m1e, m2e=self.m2e)
         return st
+
+    def checkpoint(self) -> dict:
+        """Host copies of everything the next step reads (step count, gate
+        parameters, embeddings, Adam moments)."""
+        return {k: (v.detach().cpu().clone() if torch.is_tensor(v) else v) for k, v in self.state().items()}
+
+    def restore(self, ckpt: dict) -> None:
+        """Continue from a checkpoint: the steps after it reproduce those of
+        the uninterrupted run bit for bit (every kernel is deterministic)."""
+        st = self.state()
+        if set(ckpt) != set(st):
+            raise ValueError("checkpoint does not match this trainer (embedding training on/off)")
+        for k, v in st.items():
+            if torch.is_tensor(v):
+                if tuple(ckpt[k].shape) != tuple(v.shape):
+                    raise ValueError(f"checkpoint tensor {k} has shape {tuple(ckpt[k].shape)}, expected {tuple(v.shape)}")
+                v.copy_(ckpt[k].to(v.device))
+        self.t = int(ckpt["t"])
+
+    def save(self, path: str) -> None:
+        torch.save(self.checkpoint(), path)
+
+    def load(self, path: str) -> None:
+        self.restore(torch.load(path, map_location="cpu"))

@@ -187,3 +187,43 @@ def test_autograd_function_matches_direct_calls(ctx, torch, case):
     gp, ge = ctx.fuse_backward(case["pairs"], case["sw"], case["self"], case["packed"], case["emb_t"],
                                case["params_t"], case["hidden"], wts.contiguous())
     assert torch.equal(params.grad, gp) and torch.equal(emb.grad, ge)
+
+
+@pytest.mark.parametrize("train_emb", [True, False])
+def test_resume_from_checkpoint_is_bit_identical(ctx, torch, case, tmp_path, train_emb):
+    """Six steps in one run against three steps, a checkpoint written to disk,
+    a fresh trainer restored from it and three more steps: parameters,
+    embeddings, Adam moments and the last loss agree bit for bit."""
+    from paper_2602_17330_gb300 import train
+
+    rep = case["rep"]
+    label, group = ctx.pair_labels(case["pairs"], torch.from_numpy(rep.family), torch.from_numpy(rep.subgroup))
+    weight = ctx.pair_weights(group, 51)
+
+    def trainer():
+        return train.GateTrainer(ctx, case["pairs"], case["sw"], case["self"], case["packed"], case["emb_t"],
+                                 case["params_t"], case["hidden"], label, weight, lr=1e-3, train_emb=train_emb)
+
+    full = trainer()
+    for _ in range(6):
+        loss_full = full.step().clone()
+    first = trainer()
+    for _ in range(3):
+        first.step()
+    path = str(tmp_path / "gate.ckpt")
+    first.save(path)
+    resumed = trainer()
+    resumed.load(path)
+    assert resumed.t == 3
+    for _ in range(3):
+        loss_resumed = resumed.step().clone()
+    a, b = full.state(), resumed.state()
+    assert a["t"] == b["t"] == 6
+    for k in a:
+        if torch.is_tensor(a[k]):
+            assert torch.equal(a[k], b[k]), k
+    assert torch.equal(loss_full, loss_resumed)
+    other = train.GateTrainer(ctx, case["pairs"], case["sw"], case["self"], case["packed"], case["emb_t"],
+                              case["params_t"], case["hidden"], label, weight, lr=1e-3, train_emb=not train_emb)
+    with pytest.raises(ValueError):
+        other.restore(first.checkpoint())
