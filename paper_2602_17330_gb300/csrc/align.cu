@@ -452,39 +452,6 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
     return __vmaxs2(bestA, bestB);
 }
 
-template <int WORDS, bool SELF>
-__device__ __forceinline__ void load_oriented(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs,
-                                              uint32_t p, bool symmetric, Rec<WORDS> &A, int &La, Rec<WORDS> &B,
-                                              int &Lb)
-{
-    constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
-    uint32_t i, j;
-    if (SELF) {
-        i = j = p;
-    } else {
-        const uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
-        i = ij.x;
-        j = ij.y;
-    }
-    A.load(packed, i);
-    La = min(A.len(), MAXLEN);
-    if (SELF) {
-        B = A;
-        Lb = La;
-    } else {
-        B.load(packed, j);
-        Lb = min(B.len(), MAXLEN);
-    }
-    if (symmetric && Lb < La) {
-        const Rec<WORDS> T = A;
-        A = B;
-        B = T;
-        const int tl = La;
-        La = Lb;
-        Lb = tl;
-    }
-}
-
 // Launch shapes of the batched kernel: 0 = 256 threads, 2 blocks per SM (128
 // registers); 1 = 128 threads, 3 blocks per SM (168 registers, no spills up
 // to 24 rows).  Chosen by the context's tuning (see subquad_set_tuning).

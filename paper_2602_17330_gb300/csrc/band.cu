@@ -68,31 +68,6 @@ __device__ __forceinline__ bool key_equal(const uint32_t *__restrict__ p, int ro
     return eq;
 }
 
-// Block-wide exclusive position of each flagged thread in an append buffer:
-// one global atomic per block instead of one per warp, so a single hot counter
-// is touched 8x less often.
-__device__ __forceinline__ unsigned long long block_append(bool flag, unsigned long long *counter,
-                                                           unsigned long long *s_base, uint32_t *s_warp)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t mask = __ballot_sync(0xffffffffu, flag);
-    if (lane == 0) s_warp[warp] = __popc(mask);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int w = 0; w < nw; ++w) {
-            const uint32_t c = s_warp[w];
-            s_warp[w] = run;
-            run += c;
-        }
-        *s_base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
-    }
-    __syncthreads();
-    const unsigned long long pos = *s_base + s_warp[warp] + __popc(mask & ((1u << lane) - 1u));
-    __syncthreads();
-    return pos;
-}
-
 // Equal keys: the same R-tuple and, in a batch of donors, the same donor.
 __device__ __forceinline__ bool same_key(const uint32_t *band_sig, int rows, uint32_t owner, const uint32_t k[8],
                                          const int32_t *donor, int32_t my_donor)

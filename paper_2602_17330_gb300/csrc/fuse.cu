@@ -36,13 +36,6 @@ __device__ __forceinline__ float quad_sum(float v)
     return v;
 }
 
-template <int WORDS>
-__device__ __forceinline__ int record_len(const uint64_t *__restrict__ packed, uint32_t i)
-{
-    ulonglong2 r = reinterpret_cast<const ulonglong2 *>(packed + (int64_t)i * WORDS)[0];
-    return sq_record_len(r.x, r.y);
-}
-
 // Per-pair inputs of the fusion, all loads issued together so one round trip
 // to memory (after the pair indices) covers the embedding rows, the alignment
 // score, both self-scores and both lengths.
