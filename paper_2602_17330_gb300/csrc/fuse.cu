@@ -80,13 +80,20 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
     const float *__restrict__ emb, int d, const float *__restrict__ params, int hidden, float *__restrict__ fused,
     float *__restrict__ alpha_out)
 {
-    __shared__ float s_par[5 * kMaxHidden + 1];
+    // hidden unit k as one 16-byte word (W1[k][0..2], b1[k]) and w2[k]: two
+    // shared-memory loads per unit instead of five
+    __shared__ float4 s_unit[kMaxHidden];
+    __shared__ float s_w2[kMaxHidden];
+    __shared__ float s_b2;
     int64_t m = m_max;
     if (d_m) m = (int64_t)*d_m < m_max ? (int64_t)*d_m : m_max;
-    for (int q = threadIdx.x; q < 5 * hidden + 1; q += blockDim.x) s_par[q] = params[q];
+    for (int k = threadIdx.x; k < hidden; k += blockDim.x) {
+        s_unit[k] = make_float4(params[3 * k], params[3 * k + 1], params[3 * k + 2], params[3 * hidden + k]);
+        s_w2[k] = params[4 * hidden + k];
+    }
+    if (threadIdx.x == 0) s_b2 = params[5 * hidden];
     __syncthreads();
-    const float *W1 = s_par, *b1 = s_par + 3 * hidden, *w2 = s_par + 4 * hidden;
-    const float b2 = s_par[5 * hidden];
+    const float b2 = s_b2;
     constexpr int kPairsPerWarp = 32 / kTppF;
     const int sub = threadIdx.x & (kTppF - 1);
     const int slot = (threadIdx.x & 31) / kTppF;
@@ -118,8 +125,9 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
         const float delta = fabsf((float)(in.len_i - in.len_j));
         float acc = 0.f;
         for (int k = sub; k < hidden; k += kTppF) {
-            float z = fmaf(W1[3 * k], s, fmaf(W1[3 * k + 1], c, fmaf(W1[3 * k + 2], delta, b1[k])));
-            acc = fmaf(w2[k], fmaxf(z, 0.f), acc);
+            const float4 u = s_unit[k];
+            float z = fmaf(u.x, s, fmaf(u.y, c, fmaf(u.z, delta, u.w)));
+            acc = fmaf(s_w2[k], fmaxf(z, 0.f), acc);
         }
         const float g = quad_sum(acc) + b2;
         if (valid && sub == 0) {
