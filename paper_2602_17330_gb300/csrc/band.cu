@@ -448,8 +448,6 @@ __device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, ui
     __shared__ uint32_t s_ns;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lt = (1u << lane) - 1u;
 
-#pragma unroll 4
-    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) srec[q] = prec[q];
     for (uint32_t q = threadIdx.x; q < 2 * kGrpBloomWords; q += blockDim.x) tab[q] = 0u;
     if (threadIdx.x == 0) {
         s_ns = 0;
@@ -459,11 +457,25 @@ __device__ __forceinline__ bool group_fast(const uint64_t *__restrict__ prec, ui
         s_big = 0;
     }
     __syncthreads();
-    // filter: equal keys have equal fingerprints, hence equal bits
-    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const uint32_t bi = (uint32_t)(srec[q] >> 32) & (32u * kGrpBloomWords - 1u);
-        const uint32_t bit = 1u << (bi & 31);
-        if (atomicOr(&bloom1[bi >> 5], bit) & bit) atomicOr(&bloom2[bi >> 5], bit);
+    // records staged and entered in the filter in one pass: equal keys have
+    // equal fingerprints, hence equal bits
+    for (uint32_t q0 = threadIdx.x; q0 < cnt; q0 += 4 * blockDim.x) {
+        uint64_t rec[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t q = q0 + u * blockDim.x;
+            rec[u] = q < cnt ? prec[q] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t q = q0 + u * blockDim.x;
+            if (q < cnt) {
+                srec[q] = rec[u];
+                const uint32_t bi = (uint32_t)(rec[u] >> 32) & (32u * kGrpBloomWords - 1u);
+                const uint32_t bit = 1u << (bi & 31);
+                if (atomicOr(&bloom1[bi >> 5], bit) & bit) atomicOr(&bloom2[bi >> 5], bit);
+            }
+        }
     }
     __syncthreads();
     for (uint32_t q0 = warp * 32; q0 < cnt; q0 += blockDim.x) {
