@@ -97,7 +97,7 @@ int subquad_get_tuning(const subquad_ctx *ctx, int key, int *value);
 enum {
     SUBQUAD_PROF_SIGN = 0,          /* sign_kernel */
     SUBQUAD_PROF_BAND = 1,          /* the whole banding stage of one call */
-    SUBQUAD_PROF_BAND_PARTITION = 2, /* key hashing + stable hash partition, per band group */
+    SUBQUAD_PROF_BAND_PARTITION = 2, /* key hashing + hash partition (per-tile counts, scan, scatter), per band group */
     SUBQUAD_PROF_BAND_GROUP = 3,     /* shared-memory grouping into buckets and chunks */
     SUBQUAD_PROF_BAND_EMIT = 4,     /* chunking + pair emission */
     SUBQUAD_PROF_BAND_PAIRSORT = 5, /* final sort of the pairs */
