@@ -51,6 +51,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=1_000_000, help="sequences per donor (default: the 1M donor)")
+    p.add_argument("--seed", type=int, default=0, help="data seed (rank r uses seed + r): repertoire and embeddings")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shapes")
@@ -194,10 +195,10 @@ def run_reference(args, rank: int, world: int):
         return
     n = args.ref_sample_n
     for _ in range(args.warmup):
-        oracle_step(n)
+        oracle_step(n, seed=args.seed)
     tot_pairs, tot_s = 0, 0.0
     for _ in range(args.steps):
-        p, s = oracle_step(n)
+        p, s = oracle_step(n, seed=args.seed)
         tot_pairs += p
         tot_s += s
     value = tot_pairs / tot_s
@@ -232,9 +233,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     dev = torch.device("cuda", local_rank)
     cfg = workload_of(args.n)
 
-    rep = synth.donor_repertoire(cfg.n, seed=rank)
+    rep = synth.donor_repertoire(cfg.n, seed=args.seed + rank)
     a, b = synth.hash_coefficients(cfg.hashes, seed=0)
-    emb = synth.unit_embeddings(rep.n, cfg.d, seed=rank)
+    emb = synth.unit_embeddings(rep.n, cfg.d, seed=args.seed + rank)
     params = synth.gate_parameters(cfg.hidden, seed=0)
 
     stream = torch.cuda.Stream(device=dev)
@@ -428,7 +429,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_s = args.cpu_sample_n
-        p_s, sec = oracle_step(n_s)
+        p_s, sec = oracle_step(n_s, seed=args.seed)
         cpu = {"value": p_s / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"single-threaded oracle, full pipeline on a {n_s:,}-sequence donor from the same "
                          f"generator ({p_s:,} pairs, {sec:.1f} s)"}
@@ -439,7 +440,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32/f32", "data": "synthetic",
             "config": {"workload": workload_desc(cfg),
-                       "n": cfg.n, "pairs_per_step": m, "cells_per_step": cells, "l2": "flushed between steps",
+                       "n": cfg.n, "seed": args.seed, "pairs_per_step": m, "cells_per_step": cells,
+                       "l2": "flushed between steps",
                        "sw_kernel": ("length-binned" if cfg.binned else "plain") + " (one pair per thread)"},
             "sw_gcups": gcups, "sw_frac_of_int_peak": gcups * SW_OPS_PER_CELL / alu_peak,
             "sw_gcups_plain": cells / (sw_ms["plain"] / 1e3) / 1e9,

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "subquad.h"
@@ -49,12 +50,27 @@ struct subquad_ctx {
 // Opt-in per-kernel timing: events recorded on the context stream around one
 // launch (or launch sequence) tagged with a SUBQUAD_PROF_* id.
 cudaEvent_t sq_prof_event(subquad_ctx *ctx);
+// Name of a profiled kernel tag (NVTX range and diagnostics).
+inline const char *sq_prof_name(int k)
+{
+    static const char *const names[SUBQUAD_PROF_COUNT] = {"subquad.sign", "subquad.band", "subquad.band_partition",
+                                                          "subquad.band_group", "subquad.band_emit",
+                                                          "subquad.band_pairsort", "subquad.align",
+                                                          "subquad.align_bin", "subquad.self", "subquad.fuse"};
+    return k >= 0 && k < SUBQUAD_PROF_COUNT ? names[k] : "subquad";
+}
+
+// Every tagged region is an NVTX range (free unless a tool is attached);
+// with the context's profiler on it is also timed by events on its stream.
 struct SqProfScope {
     subquad_ctx *ctx;
     int kernel;
     cudaEvent_t stop = nullptr;
+    bool ranged = false;
     SqProfScope(subquad_ctx *c, int k) : ctx(c), kernel(k)
     {
+        nvtxRangePushA(sq_prof_name(k));
+        ranged = true;
         if (!ctx->prof_on) return;
         cudaEvent_t start = sq_prof_event(ctx);
         stop = sq_prof_event(ctx);
@@ -69,6 +85,8 @@ struct SqProfScope {
     {
         if (stop) cudaEventRecord(stop, ctx->stream);
         stop = nullptr;
+        if (ranged) nvtxRangePop();
+        ranged = false;
     }
     ~SqProfScope() { finish(); }
 };

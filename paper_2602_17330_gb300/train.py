@@ -100,7 +100,75 @@ class GateTrainer:
         self.t = int(ckpt["t"])
 
     def save(self, path: str) -> None:
-        torch.save(self.checkpoint(), path)
+        write_checkpoint(path, self.checkpoint())
 
     def load(self, path: str) -> None:
-        self.restore(torch.load(path, map_location="cpu"))
+        self.restore(read_checkpoint(path))
+
+
+# Checkpoint file: magic, format version, step count, tensor count; per tensor
+# its name, dtype code and shape; the raw little-endian payloads; and a SHA-256
+# of everything before it, checked on reading.
+_MAGIC = b"SQGATE01"
+_DTYPES = {torch.float32: 0, torch.int32: 1}
+_CODES = {v: k for k, v in _DTYPES.items()}
+
+
+def write_checkpoint(path: str, ckpt: dict) -> None:
+    import hashlib
+    import struct
+
+    names = sorted(k for k, v in ckpt.items() if torch.is_tensor(v))
+    head = bytearray(_MAGIC)
+    head += struct.pack("<qq", int(ckpt["t"]), len(names))
+    body = bytearray()
+    for k in names:
+        v = ckpt[k].detach().cpu().contiguous()
+        if v.dtype not in _DTYPES:
+            raise ValueError(f"checkpoint tensor {k}: unsupported dtype {v.dtype}")
+        nb = k.encode()
+        head += struct.pack("<H", len(nb)) + nb + struct.pack("<BB", _DTYPES[v.dtype], v.dim())
+        head += struct.pack(f"<{v.dim()}q", *v.shape)
+        body += v.numpy().tobytes()
+    data = bytes(head + body)
+    with open(path, "wb") as fh:
+        fh.write(data + hashlib.sha256(data).digest())
+
+
+def read_checkpoint(path: str) -> dict:
+    import hashlib
+    import struct
+
+    import numpy as np
+
+    with open(path, "rb") as fh:
+        raw = fh.read()
+    if len(raw) < len(_MAGIC) + 16 + 32 or raw[:len(_MAGIC)] != _MAGIC:
+        raise ValueError("not a gate checkpoint")
+    data, digest = raw[:-32], raw[-32:]
+    if hashlib.sha256(data).digest() != digest:
+        raise ValueError("gate checkpoint checksum mismatch")
+    off = len(_MAGIC)
+    t, count = struct.unpack_from("<qq", data, off)
+    off += 16
+    specs = []
+    for _ in range(count):
+        (ln,) = struct.unpack_from("<H", data, off)
+        off += 2
+        name = data[off:off + ln].decode()
+        off += ln
+        code, dim = struct.unpack_from("<BB", data, off)
+        off += 2
+        shape = struct.unpack_from(f"<{dim}q", data, off)
+        off += 8 * dim
+        specs.append((name, _CODES[code], shape))
+    out = {"t": int(t)}
+    for name, dt, shape in specs:
+        npdt = np.float32 if dt == torch.float32 else np.int32
+        nbytes = int(np.prod(shape, dtype=np.int64)) * 4
+        out[name] = torch.from_numpy(np.frombuffer(data, dtype=npdt, count=nbytes // 4, offset=off).copy()).reshape(
+            shape)
+        off += nbytes
+    if off != len(data):
+        raise ValueError("gate checkpoint has trailing bytes")
+    return out
