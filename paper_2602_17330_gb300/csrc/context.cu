@@ -326,9 +326,23 @@ __global__ void __launch_bounds__(kPackRows) pack_staged_kernel(const uint32_t *
     for (int64_t r0 = (int64_t)blockIdx.x * kPackRows; r0 < n; r0 += (int64_t)gridDim.x * kPackRows) {
         const int rows = (int)(n - r0 < kPackRows ? n - r0 : kPackRows);
         const uint32_t *src = codes + r0 * stride_words;
-        for (int w = threadIdx.x; w < rows * stride_words; w += blockDim.x) {
-            const int row = w / stride_words, col = w - row * stride_words;
-            s_rows[row * pitch + col] = src[w];
+        const int words = rows * stride_words;
+        if ((stride_words & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            // 16-byte loads (a multiple of 4 words per row keeps them inside one row)
+            for (int w = 4 * threadIdx.x; w < words; w += 4 * blockDim.x) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(src + w);
+                const int row = w / stride_words, col = w - row * stride_words;
+                uint32_t *d = s_rows + row * pitch + col;
+                d[0] = v.x;
+                d[1] = v.y;
+                d[2] = v.z;
+                d[3] = v.w;
+            }
+        } else {
+            for (int w = threadIdx.x; w < words; w += blockDim.x) {
+                const int row = w / stride_words, col = w - row * stride_words;
+                s_rows[row * pitch + col] = src[w];
+            }
         }
         __syncthreads();
         const int t = threadIdx.x;
