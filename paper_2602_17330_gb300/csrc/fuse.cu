@@ -100,11 +100,17 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int d4 = d >> 2;
-    // the trip count is uniform per warp, so full-warp shuffles are safe
-    for (int64_t pbase = warp * kPairsPerWarp; pbase < m; pbase += nwarps * kPairsPerWarp) {
+    // the trip count is uniform per warp, so full-warp shuffles are safe; the
+    // next iteration's pair is loaded one iteration ahead
+    const int64_t pstep = nwarps * kPairsPerWarp;
+    uint2 ij_next = warp * kPairsPerWarp + slot < m
+                        ? __ldg(reinterpret_cast<const uint2 *>(pairs) + warp * kPairsPerWarp + slot)
+                        : make_uint2(0, 0);
+    for (int64_t pbase = warp * kPairsPerWarp; pbase < m; pbase += pstep) {
         const int64_t p = pbase + slot;
         const bool valid = p < m;
-        const uint2 ij = valid ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p) : make_uint2(0, 0);
+        const uint2 ij = valid ? ij_next : make_uint2(0, 0);
+        ij_next = p + pstep < m ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p + pstep) : make_uint2(0, 0);
         PairInputs<WORDS, CPL, kTppF> in;
         in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
         float dot = 0.f, sii = 0.f, sjj = 0.f;
