@@ -211,20 +211,20 @@ __device__ __forceinline__ int64_t items(int64_t m_max, const unsigned long long
     return c < m_max ? c : m_max;
 }
 
-// Bin of a work item: (query length, target length) after orientation.
-template <int WORDS, bool SELF>
-__device__ __forceinline__ uint32_t bin_of_item(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs,
-                                                int64_t p, bool symmetric)
+// Sequence ids of work item p, and its bin: (query length, target length)
+// after orientation.
+template <bool SELF>
+__device__ __forceinline__ uint2 ids_of_item(const uint32_t *__restrict__ pairs, int64_t p)
+{
+    if (SELF) return make_uint2((uint32_t)p, (uint32_t)p);
+    return reinterpret_cast<const uint2 *>(pairs)[p];
+}
+
+template <int WORDS>
+__device__ __forceinline__ uint32_t bin_of_ids(const uint64_t *__restrict__ packed, uint2 ij, bool symmetric)
 {
     constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
-    uint32_t i, j;
-    if (SELF) {
-        i = j = (uint32_t)p;
-    } else {
-        const uint2 ij = reinterpret_cast<const uint2 *>(pairs)[p];
-        i = ij.x;
-        j = ij.y;
-    }
+    const uint32_t i = ij.x, j = ij.y;
     const ulonglong2 ri = reinterpret_cast<const ulonglong2 *>(packed + (int64_t)i * WORDS)[0];
     const ulonglong2 rj = reinterpret_cast<const ulonglong2 *>(packed + (int64_t)j * WORDS)[0];
     const int La = min(sq_record_len(ri.x, ri.y), MAXLEN), Lb = min(sq_record_len(rj.x, rj.y), MAXLEN);
@@ -254,14 +254,28 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const uint64_t *__restri
     __syncthreads();
     const int64_t per = (m + gridDim.x - 1) / gridDim.x;
     const int64_t lo = (int64_t)blockIdx.x * per, hi = min(m, lo + per);
-    // four items per thread and iteration: their record gathers in flight together
+    // four items per thread and iteration (their record gathers in flight
+    // together); the next iteration's ids are loaded one iteration ahead
     constexpr int H = 4;
+    uint2 nxt[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int64_t p = lo + h * (int64_t)blockDim.x + threadIdx.x;
+        nxt[h] = p < hi ? ids_of_item<SELF>(pairs, p) : make_uint2(0, 0);
+    }
     for (int64_t base = lo; base < hi; base += (int64_t)blockDim.x * H) {
+        uint2 cur[H];
         uint32_t bin[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) {
+            cur[h] = nxt[h];
+            const int64_t pn = base + (int64_t)blockDim.x * H + h * (int64_t)blockDim.x + threadIdx.x;
+            nxt[h] = pn < hi ? ids_of_item<SELF>(pairs, pn) : make_uint2(0, 0);
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
             const int64_t p = base + h * (int64_t)blockDim.x + threadIdx.x;
-            bin[h] = p < hi ? bin_of_item<WORDS, SELF>(packed, pairs, p, symmetric) : kBins;
+            bin[h] = p < hi ? bin_of_ids<WORDS>(packed, cur[h], symmetric) : kBins;
         }
 #pragma unroll
         for (int h = 0; h < H; ++h) {

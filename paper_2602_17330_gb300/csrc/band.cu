@@ -1094,12 +1094,20 @@ __global__ void pairs_scatter_kernel(const uint32_t *__restrict__ pairs, const u
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // warp-uniform trip count; a run of equal first members takes its slots
     // with one atomic (positions old-1, old-2, ... in lane order)
+    // (the next iteration's pairs are loaded one iteration ahead)
+    uint2 nxt[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int64_t p = warp * 32 * H + h * 32 + lane;
+        nxt[h] = p < m ? reinterpret_cast<const uint2 *>(pairs)[p] : make_uint2(0xffffffffu, 0u);
+    }
     for (int64_t pb = warp * 32 * H; pb < m; pb += nwarps * 32 * H) {
         uint2 ij[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) {
-            const int64_t p = pb + h * 32 + lane;
-            ij[h] = p < m ? reinterpret_cast<const uint2 *>(pairs)[p] : make_uint2(0xffffffffu, 0u);
+            ij[h] = nxt[h];
+            const int64_t p = pb + nwarps * 32 * H + h * 32 + lane;
+            nxt[h] = p < m ? reinterpret_cast<const uint2 *>(pairs)[p] : make_uint2(0xffffffffu, 0u);
         }
         uint32_t top[H], first[H], off[H];
 #pragma unroll
