@@ -828,12 +828,6 @@ __device__ __forceinline__ RunOf run_of(uint32_t key, uint32_t lane)
     return {mask, first};
 }
 
-// Step 5: owned pairs, appended to out.  Each warp takes 32 consecutive raw
-// pair indices; their chunks are c0 (looked up) plus the chunks starting
-// inside the group (one load per lane and a warp OR of start positions); each
-// lane decodes its (u, v) and keeps pair (i, j) only if no earlier band
-// already puts i and j in one chunk (first-band ownership), so every pair of
-// C is emitted exactly once.
 // Positions of up to two appends per thread in one block-wide reservation:
 // the block's f0 appends first (in thread order), then its f1 appends, so the
 // output keeps the order of each span.  Every thread of the block must call it.
@@ -869,6 +863,12 @@ __device__ __forceinline__ void block_append2(bool f0, bool f1, unsigned long lo
     __syncthreads();
 }
 
+// Step 5: owned pairs, appended to out.  Each warp takes 32 consecutive raw
+// pair indices; their chunks are c0 (looked up) plus the chunks starting
+// inside the group (one load per lane and a warp OR of start positions); each
+// lane decodes its (u, v) and keeps pair (i, j) only if no earlier band
+// already puts i and j in one chunk (first-band ownership), so every pair of
+// C is emitted exactly once.
 // Each block iteration takes two spans of blockDim raw pairs, so every thread
 // carries two independent chains of dependent loads (chunk -> chunk entry ->
 // member ids -> masks and chunk ids) in flight.
