@@ -24,6 +24,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -33,14 +35,14 @@ UNIT = "pairs/s"
 # Smith-Waterman algorithmic int32 operations per DP cell: H-diagonal + score,
 # max3-with-0, H - open, E add-max, F add-max, running best max.
 SW_OPS_PER_CELL = 6
-# Integer lane operations per SM per clock on sm_103a: the fastest integer
-# issue rate measured by `python -m paper_2602_17330_gb300.peak` (2-input add
-# and min/max at 128; 3-input add, multiply-add and every DPX operation at 64;
-# summary in profiles/alu_peak_gb300.md).  Times 152 SMs and the 2070 MHz
-# maximum SM clock gives the integer roof.
-INT_LANE_OPS_PER_SM_CLK = 128.0
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
+# The integer roof: 128 integer lane operations per SM per clock (the issue
+# width of an sm_103a SM) x SM count x max SM clock, the last two read from the
+# device at run time.  profiles/int_issue_peak.json holds the measured rates
+# (`python -m paper_2602_17330_gb300.peak --json ...` on a GB300: 2-input add
+# and min/max issue at ~125-127 lane-ops/SM/clk; 3-input add, multiply-add and
+# every DPX operation at 64).
+INT_PEAK_FILE = os.path.join(ROOT, "profiles", "int_issue_peak.json")
+INT_LANE_OPS_NOMINAL = 128.0  # 4 sub-partitions x 32 lanes of integer issue per clock
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -76,8 +78,39 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def alu_peak_gops():
-    return INT_LANE_OPS_PER_SM_CLK * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+def int_lane_ops_per_sm_clk():
+    """(rate, source): the nominal integer issue rate of an sm_103a SM (128
+    lanes), with the fastest measured rate from the committed probe beside it."""
+    if os.path.exists(INT_PEAK_FILE):
+        with open(INT_PEAK_FILE) as fh:
+            d = json.load(fh)
+        meas = max(v for k, v in d["ops"].items() if k in ("iadd (2-input)", "imax", "__vmaxs2"))
+        return INT_LANE_OPS_NOMINAL, (f"128 lane-ops/SM/clk (measured fastest integer issue {meas:.1f}: "
+                                      f"{d['command']}, {d['date']})")
+    return INT_LANE_OPS_NOMINAL, "128 lane-ops/SM/clk (4 x 32 integer lanes)"
+
+
+def device_sm_clock(device_index: int):
+    """(SM count, max SM clock in MHz) of the device, read at run time."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits", "-i",
+                              str(device_index)], capture_output=True, text=True, timeout=20).stdout.strip()
+        mhz = float(out.splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(path):
+            with open(path) as fh:
+                mhz = float(json.load(fh).get("sm_max_mhz", 0.0)) or None
+    return sms, mhz
+
+
+def alu_peak_gops(sms: int, mhz: float):
+    rate, src = int_lane_ops_per_sm_clk()
+    return rate * sms * mhz * 1e6 / 1e9, f"{src} x {sms} SMs x {mhz:.0f} MHz"
 
 
 def traffic_for(kernel: str):
@@ -157,9 +190,12 @@ class ClockSampler:
 # CPU baseline / reference arm: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
 
-def oracle_step(n_sample: int, seed: int = 0):
+def oracle_step(n_sample: int, seed: int = 0, threads: int = 1):
     """One pass of the oracle over a donor repertoire of n_sample sequences
-    (same generator, families of 25, same hashing).  Returns (pairs, seconds)."""
+    (same generator, families of 25, same hashing).  threads > 1 runs the
+    signatures, alignments and fusion over that many host threads (the
+    oracle's threaded runners; the banding stays single-threaded).  Returns
+    (pairs, seconds)."""
     import oracle
     from paper_2602_17330_gb300 import pipeline, synth
 
@@ -168,13 +204,37 @@ def oracle_step(n_sample: int, seed: int = 0):
     a, b = synth.hash_coefficients(cfg.hashes, seed=0)
     emb = synth.unit_embeddings(rep.n, cfg.d, seed=seed)
     params = synth.gate_parameters(cfg.hidden, seed=0)
+    idx = np.arange(rep.n, dtype=np.uint32)
     t0 = time.perf_counter()
-    sig = oracle.sign(rep.codes, rep.lens, cfg.k, a, b)
-    pairs = oracle.candidates(sig, cfg.bands, cfg.rows, cfg.bucket_cap)
-    self_sc = oracle.self_scores(rep.codes, rep.lens, cfg.gap_open, cfg.gap_extend)
-    sw = oracle.sw_pairs(rep.codes, rep.lens, pairs, cfg.gap_open, cfg.gap_extend)
-    oracle.fuse_forward(pairs, sw, self_sc, rep.lens, emb, params, cfg.hidden)
+    if threads > 1:
+        sig = oracle.sign_mt(rep.codes, rep.lens, cfg.k, a, b, threads)
+        pairs = oracle.candidates(sig, cfg.bands, cfg.rows, cfg.bucket_cap)
+        self_sc = oracle.sw_pairs_mt(rep.codes, rep.lens, np.stack([idx, idx], 1), threads, cfg.gap_open,
+                                     cfg.gap_extend)
+        sw = oracle.sw_pairs_mt(rep.codes, rep.lens, pairs, threads, cfg.gap_open, cfg.gap_extend)
+        oracle.fuse_forward_mt(pairs, sw, self_sc, rep.lens, emb, params, cfg.hidden, threads)
+    else:
+        sig = oracle.sign(rep.codes, rep.lens, cfg.k, a, b)
+        pairs = oracle.candidates(sig, cfg.bands, cfg.rows, cfg.bucket_cap)
+        self_sc = oracle.self_scores(rep.codes, rep.lens, cfg.gap_open, cfg.gap_extend)
+        sw = oracle.sw_pairs(rep.codes, rep.lens, pairs, cfg.gap_open, cfg.gap_extend)
+        oracle.fuse_forward(pairs, sw, self_sc, rep.lens, emb, params, cfg.hidden)
     return pairs.shape[0], time.perf_counter() - t0
+
+
+def host_cpu() -> str:
+    """CPU model of the host, for the baseline's record."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
 
 
 def workload_of(n: int):
@@ -373,7 +433,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # roofline of the dominant kernel, from the library's live per-kernel event
     # timings over the timed region (same stream as the launches)
     hbm_peak, peak_kind = measured_peaks()
-    alu_peak = alu_peak_gops()
+    alu_peak, alu_src = alu_peak_gops(*device_sm_clock(local_rank))
     align_s = stage_ms["align"] / 1e3
     gcups = cells / align_s / 1e9
     L = rep.lens.astype(np.int64)
@@ -417,7 +477,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     d = stage_roof[dom]
     roof = {"kernel": d["kernel"], "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
             "unit": d["unit"], "frac": d["frac"], "traffic": traffic_for(dom),
-            "peak_source": ("integer issue 128 lane-ops/SM/clk (measured) x 152 SMs x 2070 MHz" if d["bound"] == "alu"
+            "peak_source": (alu_src if d["bound"] == "alu"
                             else f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"),
             "algorithmic": d["algorithmic"]}
 
@@ -428,11 +488,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
         n_s = args.cpu_sample_n
         p_s, sec = oracle_step(n_s, seed=args.seed)
+        threads = oracle.host_threads()
+        p_n, sec_n = oracle_step(n_s, seed=args.seed, threads=threads)
         cpu = {"value": p_s / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"single-threaded oracle, full pipeline on a {n_s:,}-sequence donor from the same "
-                         f"generator ({p_s:,} pairs, {sec:.1f} s)"}
+                         f"generator ({p_s:,} pairs, {sec:.1f} s)",
+               "host_cpu": host_cpu(),
+               "n_core": {"value": p_n / sec_n, "unit": UNIT, "cores": threads, "kind": "oracle",
+                          "sample": f"the same oracle routines over {threads} host threads (signatures, alignments "
+                                    f"and fusion split by index range; banding single-threaded) on the same "
+                                    f"donor ({p_n:,} pairs, {sec_n:.1f} s)"}}
 
     if rank == 0:
         line = {

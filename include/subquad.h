@@ -17,10 +17,10 @@
  * - Return value: SUBQUAD_OK (0) or a negative subquad_status.  No call aborts
  *   the process.  Argument errors are detected on the host before any work is
  *   queued.  Errors found by kernels (an invalid residue code or length in
- *   subquad_pack, an exhausted iteration bound) are recorded in a sticky
- *   device-side word and reported by the next synchronising call
- *   (subquad_band_candidates, subquad_check) as SUBQUAD_ERR_INPUT or
- *   SUBQUAD_ERR_TIMEOUT.
+ *   subquad_pack, an exhausted iteration bound, an internal consistency check
+ *   that failed) are recorded in a sticky device-side word and reported by
+ *   the next synchronising call (subquad_band_candidates, subquad_check) as
+ *   SUBQUAD_ERR_INPUT, SUBQUAD_ERR_TIMEOUT or SUBQUAD_ERR_INTERNAL.
  * - Residue codes are 0..19 in the order ACDEFGHIKLMNPQRSTVWY.
  * - A pair list is uint32 [m][2], pair p = (pairs[2p], pairs[2p+1]).
  * - One context per host thread / stream; a context is not thread-safe.
@@ -44,7 +44,8 @@ typedef enum {
     SUBQUAD_ERR_CUDA = -3,     /* a CUDA runtime call failed */
     SUBQUAD_ERR_TIMEOUT = -4,  /* a bounded device-side loop ran out of iterations */
     SUBQUAD_ERR_NOMEM = -5,    /* scratch allocation failed */
-    SUBQUAD_ERR_INPUT = -6     /* input data invalid (residue code >= 20, length out of range) */
+    SUBQUAD_ERR_INPUT = -6,    /* input data invalid (residue code >= 20, length out of range) */
+    SUBQUAD_ERR_INTERNAL = -7  /* a kernel's internal consistency check failed (a library defect, not bad input) */
 } subquad_status;
 
 /* Human-readable text for a status code (static storage). */
@@ -363,7 +364,11 @@ int subquad_fuse_backward(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, co
  * The call allocates nothing: its block partials live in one 2 MiB
  * file-scope device array that every GPU loading the library keeps until the
  * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress), so make it before any stream capture.  It
+ * address (cudaGetSymbolAddress), so make it before any stream capture.  The
+ * address is cached per device for the life of the process: after a
+ * cudaDeviceReset (or any teardown of the device's primary context) the
+ * cached address is stale, so do not use this entry point again in that
+ * process.  It
  * returns SUBQUAD_ERR_ARG when (4 x SMs) x (5 hidden + 1) doubles exceed
  * 2 MiB (on a 152-SM GB300 every hidden <= 64 fits).  All calls share the
  * array, which keeps the last call's contents (each call overwrites every

@@ -37,7 +37,8 @@ def build(force: bool = False) -> str:
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+            subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_POSIX_C_SOURCE=200809L", "-Wall", "-fPIC", "-pthread",
+                                   "-shared", "-o", tmp, _SRC, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -67,6 +68,9 @@ def _load():
     lib.oracle_fuse_backward.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, F32P, c.c_int,
                                          F64P, F64P, opt_f64]
     lib.oracle_fuse_backward.restype = c.c_int
+    lib.oracle_fuse_backward_scale.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, F32P, c.c_int,
+                                               F64P, F64P, opt_f64]
+    lib.oracle_fuse_backward_scale.restype = c.c_int
     lib.oracle_pair_labels.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, I32P]
     lib.oracle_pair_labels.restype = None
     lib.oracle_pair_weights.argtypes = [I32P, c.c_int64, c.c_int, F64P]
@@ -78,6 +82,13 @@ def _load():
     lib.oracle_adam.restype = None
     lib.oracle_topk.argtypes = [U32P, I32P, c.c_int64, I32P, U32P, c.c_int64, c.c_int, U32P, I32P]
     lib.oracle_topk.restype = c.c_int
+    lib.oracle_sign_mt.argtypes = [U8P, c.c_int, U8P, c.c_int64, c.c_int, c.c_int, U32P, U32P, U32P, c.c_int]
+    lib.oracle_sign_mt.restype = c.c_int
+    lib.oracle_sw_pairs_mt.argtypes = [U8P, c.c_int, U8P, U32P, c.c_int64, I32P, c.c_int, c.c_int, I32P, c.c_int]
+    lib.oracle_sw_pairs_mt.restype = c.c_int
+    lib.oracle_fuse_forward_mt.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, F32P, c.c_int, F64P,
+                                           c.c_int]
+    lib.oracle_fuse_forward_mt.restype = c.c_int
     _lib = lib
     return lib
 
@@ -207,6 +218,24 @@ def fuse_backward(pairs, sw_scores, self_sc, lens, emb, params, hidden: int, dL_
     return gp, ge
 
 
+def fuse_backward_scale(pairs, sw_scores, self_sc, lens, emb, params, hidden: int, dL_dfused,
+                        with_emb: bool = True):
+    """Rounding scale of the adjoint: (FP64 [P], FP64 [n, d] or None), the
+    summed magnitude of every pair's contribution to each gradient entry, with
+    cancelling factors taken as magnitude + 1.  A float32 gradient lies within
+    a fixed multiple of unit roundoff times this scale of the exact one."""
+    p = _pairs(pairs)
+    emb = _c(emb, np.float32)
+    sc = np.zeros(5 * hidden + 1, dtype=np.float64)
+    se = np.zeros(emb.shape, dtype=np.float64) if with_emb else None
+    rc = _load().oracle_fuse_backward_scale(p, p.shape[0], _c(sw_scores, np.int32), _c(self_sc, np.int32),
+                                            _c(lens, np.uint8), emb, emb.shape[1], _c(params, np.float32), hidden,
+                                            _c(dL_dfused, np.float64), sc, _ptr(se))
+    if rc != 0:
+        raise MemoryError("oracle_fuse_backward_scale failed")
+    return sc, se
+
+
 # --------------------------------------------------------------------------
 # Gate training objective and optimiser
 # --------------------------------------------------------------------------
@@ -256,3 +285,49 @@ def topk(pairs, scores, donor, queries, k: int):
     if _load().oracle_topk(p, _c(scores, np.int32), p.shape[0], _c(donor, np.int32), q, q.shape[0], k, ids, sc):
         raise MemoryError("oracle_topk failed")
     return ids, sc
+
+
+# --------------------------------------------------------------------------
+# All host cores: the same routines over contiguous index ranges in threads
+# (identical results; the CPU baseline's N-core figure)
+# --------------------------------------------------------------------------
+
+def host_threads() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def sign_mt(codes, lens, k: int, a, b, threads: int) -> np.ndarray:
+    codes = _c(codes, np.uint8)
+    lens = _c(lens, np.uint8)
+    a = _c(a, np.uint32)
+    b = _c(b, np.uint32)
+    n, H = lens.shape[0], a.shape[0]
+    if n and int(lens.min()) < k:
+        raise ValueError("every sequence needs at least one k-mer")
+    sig = np.zeros((n, H), dtype=np.uint32)
+    if _load().oracle_sign_mt(codes, codes.shape[1], lens, n, k, H, a, b, sig, threads):
+        raise MemoryError("oracle_sign_mt failed")
+    return sig
+
+
+def sw_pairs_mt(codes, lens, pairs, threads: int, gap_open: int = 10, gap_extend: int = 1, matrix=None):
+    codes = _c(codes, np.uint8)
+    lens = _c(lens, np.uint8)
+    p = _pairs(pairs)
+    M = blosum62() if matrix is None else _c(matrix, np.int32)
+    out = np.zeros(p.shape[0], dtype=np.int32)
+    if _load().oracle_sw_pairs_mt(codes, codes.shape[1], lens, p, p.shape[0], _c(M.reshape(-1), np.int32), gap_open,
+                                  gap_extend, out, threads):
+        raise MemoryError("oracle_sw_pairs_mt failed")
+    return out
+
+
+def fuse_forward_mt(pairs, sw_scores, self_sc, lens, emb, params, hidden: int, threads: int) -> np.ndarray:
+    p = _pairs(pairs)
+    emb = _c(emb, np.float32)
+    out = np.zeros(p.shape[0], dtype=np.float64)
+    if _load().oracle_fuse_forward_mt(p, p.shape[0], _c(sw_scores, np.int32), _c(self_sc, np.int32),
+                                      _c(lens, np.uint8), emb, emb.shape[1], _c(params, np.float32), hidden, out,
+                                      threads):
+        raise MemoryError("oracle_fuse_forward_mt failed")
+    return out

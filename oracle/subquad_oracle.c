@@ -222,7 +222,7 @@ int64_t oracle_candidates(const uint32_t *sig /* [n][H] */, int64_t n, int H, in
 int32_t oracle_sw(const uint8_t *a, int La, const uint8_t *b, int Lb, const int32_t *M /* [20][20] */,
                   int o, int e)
 {
-    static int32_t Hm[SW_MAXL + 1][SW_MAXL + 1], Em[SW_MAXL + 1][SW_MAXL + 1], Fm[SW_MAXL + 1][SW_MAXL + 1];
+    int32_t Hm[SW_MAXL + 1][SW_MAXL + 1], Em[SW_MAXL + 1][SW_MAXL + 1], Fm[SW_MAXL + 1][SW_MAXL + 1];
     if (La > SW_MAXL || Lb > SW_MAXL || La < 0 || Lb < 0) return -1;
     int32_t best = 0;
     for (int i = 0; i <= La; ++i) {
@@ -374,6 +374,60 @@ int oracle_fuse_backward(const uint32_t *pairs, int64_t m, const int32_t *sw, co
     return 0;
 }
 
+/* Rounding scale of the adjoint (no counterpart in the paper; used only to
+ * state the FP32 tolerance of the GPU gradients).  For each parameter q,
+ * scale[q] accumulates over pairs the contribution of pair p to
+ * grad_params[q] evaluated on operand magnitudes, the quantity that bounds the
+ * rounding error of a floating-point evaluation: every factor in absolute
+ * value; a difference a - b by |a| + |b| (the channel difference s - c'); a
+ * sum by the sum of its terms' magnitudes (the pre-activation z); the cosine
+ * by 1 (its dot product's rounding error is relative to |e_i||e_j|); and the
+ * ReLU taken as open for every pair (a pre-activation near zero may round to
+ * either side).  scale_emb (nullable, [n][d]) does the same for grad_emb.  A
+ * float32 evaluation of the chain differs from the exact gradient by at most
+ * a small multiple of unit roundoff times this scale.  Both accumulate
+ * (caller zeroes).                                                          */
+int oracle_fuse_backward_scale(const uint32_t *pairs, int64_t m, const int32_t *sw, const int32_t *self,
+                               const uint8_t *lens, const float *emb, int d, const float *params, int h,
+                               const double *dL_dfused, double *scale, double *scale_emb)
+{
+    double *z = (double *)malloc((size_t)(h > 0 ? h : 1) * sizeof(double));
+    if (!z) return -1;
+    const float *W1 = params, *b1 = params + 3 * h, *w2 = params + 4 * h;
+    double *sW1 = scale, *sb1 = scale + 3 * h, *sw2 = scale + 4 * h, *sb2 = scale + 5 * h;
+    for (int64_t p = 0; p < m; ++p) {
+        fuse_state st;
+        fuse_pair(pairs, p, sw, self, lens, emb, d, params, h, z, &st);
+        double dA = fabs(dL_dfused[p]);
+        double diff = fabs(st.s) + 0.5 * (1.0 + fabs(st.c));
+        double d_g = dA * diff * st.alpha * (1.0 - st.alpha);
+        double d_c = dA * (1.0 - st.alpha) * 0.5;
+        sb2[0] += d_g;
+        for (int k = 0; k < h; ++k) {
+            double zmag = fabs((double)W1[3 * k]) * st.s + fabs((double)W1[3 * k + 1]) +
+                          fabs((double)W1[3 * k + 2]) * st.delta + fabs((double)b1[k]);
+            sw2[k] += d_g * zmag;
+            double d_z = d_g * fabs((double)w2[k]);
+            sW1[3 * k] += d_z * st.s;
+            sW1[3 * k + 1] += d_z;
+            sW1[3 * k + 2] += d_z * st.delta;
+            sb1[k] += d_z;
+            d_c += d_z * fabs((double)W1[3 * k + 1]);
+        }
+        if (scale_emb && st.ni > 0.0 && st.nj > 0.0) {
+            uint32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+            const float *ei = emb + (int64_t)i * d, *ej = emb + (int64_t)j * d;
+            double inv = 1.0 / (st.ni * st.nj);
+            for (int k = 0; k < d; ++k) {
+                scale_emb[(int64_t)i * d + k] += d_c * (fabs((double)ej[k]) * inv + fabs((double)ei[k]) / (st.ni * st.ni));
+                scale_emb[(int64_t)j * d + k] += d_c * (fabs((double)ei[k]) * inv + fabs((double)ej[k]) / (st.nj * st.nj));
+            }
+        }
+    }
+    free(z);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Training objective for the gate (reading: weighted binary cross-entropy of
  * the fused score against family-match labels; weight of a pair = inverse
@@ -499,4 +553,137 @@ int oracle_topk(const uint32_t *pairs, const int32_t *scores, int64_t m, const i
     }
     free(buf);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Multi-threaded runners (the CPU baseline over all host cores; no new
+ * arithmetic).  Each splits its index range into `threads` contiguous pieces
+ * and calls the single-threaded routine above on each piece in its own POSIX
+ * thread; results land in the same places, so the output is identical to the
+ * single-threaded call.  Signatures are split by sequence, alignments and
+ * fusion by pair.                                                           */
+/* ------------------------------------------------------------------------- */
+#include <pthread.h>
+
+typedef struct {
+    int kind; /* 0 sign, 1 sw, 2 fuse forward */
+    int64_t lo, hi;
+    /* sign */
+    const uint8_t *codes;
+    int code_stride;
+    const uint8_t *lens;
+    int k, H;
+    const uint32_t *a, *b;
+    uint32_t *sig;
+    /* sw */
+    const uint32_t *pairs;
+    const int32_t *M;
+    int o, e;
+    int32_t *scores;
+    /* fuse */
+    const int32_t *sw, *self;
+    const float *emb, *params;
+    int d, h;
+    double *fused;
+    int rc;
+} mt_job;
+
+static void *mt_run(void *arg)
+{
+    mt_job *j = (mt_job *)arg;
+    int64_t n = j->hi - j->lo;
+    if (n <= 0) return NULL;
+    if (j->kind == 0)
+        oracle_sign(j->codes + j->lo * (int64_t)j->code_stride, j->code_stride, j->lens + j->lo, n, j->k, j->H, j->a,
+                    j->b, j->sig + j->lo * (int64_t)j->H);
+    else if (j->kind == 1)
+        oracle_sw_pairs(j->codes, j->code_stride, j->lens, j->pairs + 2 * j->lo, n, j->M, j->o, j->e,
+                        j->scores + j->lo);
+    else
+        j->rc = oracle_fuse_forward(j->pairs + 2 * j->lo, n, j->sw + j->lo, j->self, j->lens, j->emb, j->d, j->params,
+                                    j->h, j->fused + j->lo, NULL, NULL, NULL);
+    return NULL;
+}
+
+static int mt_launch(mt_job *proto, int64_t count, int threads)
+{
+    if (threads < 1) threads = 1;
+    if (threads > 1024) threads = 1024;
+    mt_job *jobs = (mt_job *)calloc((size_t)threads, sizeof(mt_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    int rc = 0;
+    if (!jobs || !tid) {
+        free(jobs);
+        free(tid);
+        return -1;
+    }
+    for (int t = 0; t < threads; ++t) {
+        jobs[t] = *proto;
+        jobs[t].lo = count * t / threads;
+        jobs[t].hi = count * (t + 1) / threads;
+        if (pthread_create(&tid[t], NULL, mt_run, &jobs[t]) != 0) {
+            mt_run(&jobs[t]); /* run inline if a thread cannot be started */
+            tid[t] = 0;
+        }
+    }
+    for (int t = 0; t < threads; ++t) {
+        if (tid[t]) pthread_join(tid[t], NULL);
+        if (jobs[t].rc) rc = jobs[t].rc;
+    }
+    free(jobs);
+    free(tid);
+    return rc;
+}
+
+int oracle_sign_mt(const uint8_t *codes, int code_stride, const uint8_t *lens, int64_t n, int k, int H,
+                   const uint32_t *a, const uint32_t *b, uint32_t *sig, int threads)
+{
+    mt_job j;
+    memset(&j, 0, sizeof(j));
+    j.kind = 0;
+    j.codes = codes;
+    j.code_stride = code_stride;
+    j.lens = lens;
+    j.k = k;
+    j.H = H;
+    j.a = a;
+    j.b = b;
+    j.sig = sig;
+    return mt_launch(&j, n, threads);
+}
+
+int oracle_sw_pairs_mt(const uint8_t *codes, int code_stride, const uint8_t *lens, const uint32_t *pairs, int64_t m,
+                       const int32_t *M, int o, int e, int32_t *scores, int threads)
+{
+    mt_job j;
+    memset(&j, 0, sizeof(j));
+    j.kind = 1;
+    j.codes = codes;
+    j.code_stride = code_stride;
+    j.lens = lens;
+    j.pairs = pairs;
+    j.M = M;
+    j.o = o;
+    j.e = e;
+    j.scores = scores;
+    return mt_launch(&j, m, threads);
+}
+
+int oracle_fuse_forward_mt(const uint32_t *pairs, int64_t m, const int32_t *sw, const int32_t *self,
+                           const uint8_t *lens, const float *emb, int d, const float *params, int h, double *fused,
+                           int threads)
+{
+    mt_job j;
+    memset(&j, 0, sizeof(j));
+    j.kind = 2;
+    j.pairs = pairs;
+    j.sw = sw;
+    j.self = self;
+    j.lens = lens;
+    j.emb = emb;
+    j.d = d;
+    j.params = params;
+    j.h = h;
+    j.fused = fused;
+    return mt_launch(&j, m, threads);
 }

@@ -19,6 +19,8 @@
 //   H = max(t, E, F, 0)                       (DPX max3-relu)
 #include <string.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace {
@@ -672,11 +674,20 @@ int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const u
     do {                                                                                                           \
         auto k = align_binned_kernel<W, SELF, C>;                                                                  \
         const size_t smem = sizeof(int32_t) * kTabWords + sizeof(uint64_t) * W * 8 * BinnedShape<C>::threads;      \
+        static std::mutex attr_mutex;                                                                              \
         static bool attr_set[64] = {};                                                                             \
-        const int dev_slot = ctx->device & 63;                                                                     \
-        if (!attr_set[dev_slot]) {                                                                                 \
+        const bool slot_ok = ctx->device >= 0 && ctx->device < 64;                                                 \
+        bool need_attr;                                                                                            \
+        {                                                                                                          \
+            std::lock_guard<std::mutex> lock(attr_mutex);                                                          \
+            need_attr = !slot_ok || !attr_set[ctx->device];                                                        \
+        }                                                                                                          \
+        if (need_attr) { /* racing first launches both set it: harmless */                                         \
             SQ_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));         \
-            attr_set[dev_slot] = true;                                                                             \
+            if (slot_ok) {                                                                                         \
+                std::lock_guard<std::mutex> lock(attr_mutex);                                                      \
+                attr_set[ctx->device] = true;                                                                      \
+            }                                                                                                      \
         }                                                                                                          \
         const unsigned grid = sq_grid(ctx, (m + 1) / 2, BinnedShape<C>::threads, BinnedShape<C>::blocks);         \
         k<<<grid, BinnedShape<C>::threads, smem, ctx->stream>>>(pk, pairs, order, m, d_m, ctx->d_table, o, e,      \

@@ -920,7 +920,7 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
                 uint32_t u, v;
                 decode_pair(q[h] - poff[cl], sz, u, v);
                 if (u >= v || v >= sz) {  // cannot happen for a consistent chunk list
-                    atomicOr(err, SQ_DEVERR_TIMEOUT);
+                    atomicOr(err, SQ_DEVERR_INTERNAL);
                     u = 0;
                     v = 1;
                 }

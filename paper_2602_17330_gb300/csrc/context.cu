@@ -48,6 +48,7 @@ extern "C" const char *subquad_strerror(int status)
     case SUBQUAD_ERR_TIMEOUT: return "device loop exceeded its iteration bound";
     case SUBQUAD_ERR_NOMEM: return "scratch allocation failed";
     case SUBQUAD_ERR_INPUT: return "invalid input data (residue code or length)";
+    case SUBQUAD_ERR_INTERNAL: return "internal consistency check failed in a kernel";
     default: return "unknown status";
     }
 }
@@ -191,6 +192,7 @@ extern "C" int subquad_check(subquad_ctx *ctx)
     SQ_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));
     if (err & SQ_DEVERR_INPUT) return SUBQUAD_ERR_INPUT;
     if (err & SQ_DEVERR_TIMEOUT) return SUBQUAD_ERR_TIMEOUT;
+    if (err & SQ_DEVERR_INTERNAL) return SUBQUAD_ERR_INTERNAL;
     if (err & SQ_DEVERR_CAPACITY) return SUBQUAD_ERR_CAPACITY;
     return SUBQUAD_OK;
 }

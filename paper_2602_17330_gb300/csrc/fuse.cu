@@ -504,7 +504,8 @@ double *g_static_ptr[kMaxDevices] = {};
 
 // Device address of g_static_partials on `device` (which must be current):
 // the host-side symbol is only a stand-in, so the address is looked up once
-// per device and cached.
+// per device and cached for the life of the process (a device reset, which
+// reloads the module, would leave the cached address stale).
 int static_partials(int device, double **out)
 {
     if (device < 0 || device >= kMaxDevices) return SUBQUAD_ERR_ARG;

@@ -13,6 +13,7 @@ enum : uint32_t {
     SQ_DEVERR_INPUT = 1u,
     SQ_DEVERR_TIMEOUT = 2u,
     SQ_DEVERR_CAPACITY = 4u,
+    SQ_DEVERR_INTERNAL = 8u,  // a consistency check inside a kernel failed
 };
 
 #include <vector>

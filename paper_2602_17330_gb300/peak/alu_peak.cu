@@ -58,6 +58,9 @@ __global__ void __launch_bounds__(kThreads) probe(int *out, long long *rec, int 
                                                       __int_as_float(v[(c + 2) & 7])));  // two fp32 max
             if (OP == 20) v[c] = __vmaxs2(__vmaxs2(v[c], v[(c + 1) & 7]), v[(c + 2) & 7]);  // two packed maxes
             if (OP == 21) v[c] = v[c] + v[(c + 1) & 7];                                  // 2-input add
+            if (OP == 22) v[c] = __viaddmin_s16x2(v[c], b, a + it);                        // packed 16-bit add-min
+            if (OP == 23) v[c] = __vimin3_s16x2(v[c], a, b + it);                          // packed 16-bit min3
+            if (OP == 24) v[c] = __vmins2(v[c], a + it);                                   // packed 16-bit min
         }
     }
     long long t1 = clock64();
@@ -191,6 +194,9 @@ int main()
     run<19>(sms, per_sm, out, rec, "fmaxf(fmaxf(a,b),c)");
     run<20>(sms, per_sm, out, rec, "__vmaxs2(__vmaxs2(a,b),c)");
     run<21>(sms, per_sm, out, rec, "iadd (2-input)");
+    run<22>(sms, per_sm, out, rec, "__viaddmin_s16x2");
+    run<23>(sms, per_sm, out, rec, "__vimin3_s16x2");
+    run<24>(sms, per_sm, out, rec, "__vmins2");
     lds_probe(sms, out, rec);
     CK(cudaFree(out));
     CK(cudaFree(rec));

@@ -27,6 +27,7 @@ SUBQUAD_ERR_CUDA = -3
 SUBQUAD_ERR_TIMEOUT = -4
 SUBQUAD_ERR_NOMEM = -5
 SUBQUAD_ERR_INPUT = -6
+SUBQUAD_ERR_INTERNAL = -7
 
 PROF_NAMES = ["sign", "band", "band_partition", "band_group", "band_emit", "band_pairsort", "align", "align_bin", "self",
               "fuse"]

@@ -187,3 +187,68 @@ def test_topk_against_brute_force(oracle_mod):
         cand.sort()
         want = cand[:k] + [(1, 0xFFFFFFFF)] * (k - len(cand[:k]))
         assert [(-int(s), int(x)) for s, x in zip(sc[qi], ids[qi])] == want
+
+
+# Tolerance of a float32 adjoint against the FP64 oracle, per gradient entry:
+#   |g - g*| <= max(GRAD_RTOL |g*|, GRAD_KAPPA * scale),
+# where scale is the oracle's rounding scale of that entry (every pair's term
+# evaluated on operand magnitudes, see oracle_fuse_backward_scale).  Where the
+# terms do not cancel, GRAD_RTOL |g*| is the larger and the relative 1e-4
+# applies; where they cancel to below GRAD_KAPPA * scale / GRAD_RTOL, float32
+# cannot deliver 1e-4 of the result and the floor is the rounding error a
+# correct float32 evaluation may carry.  GRAD_KAPPA = 2^-18 = 64 unit
+# roundoffs; a float32 evaluation of the chain measures below 0.2 u * scale
+# (the test below), while the first-order worst case with every rounding
+# aligned is a few hundred u at h = 64 and length differences near 20.
+GRAD_RTOL = 1e-4
+GRAD_KAPPA = 2.0 ** -18
+
+
+def float32_adjoint(C, sw, self_sc, lens, emb, params, h, dL):
+    """The adjoint's parameter gradient with every per-pair quantity rounded to
+    float32 (numpy), the per-pair terms summed in float64."""
+    f32 = np.float32
+    i, j = C[:, 0].astype(np.int64), C[:, 1].astype(np.int64)
+    s = sw.astype(f32) / np.sqrt(self_sc[i].astype(f32) * self_sc[j].astype(f32))
+    ei, ej = emb[i], emb[j]
+    dot = (ei * ej).sum(1, dtype=f32)
+    c = dot / np.sqrt((ei * ei).sum(1, dtype=f32) * (ej * ej).sum(1, dtype=f32))
+    delta = np.abs(lens[i].astype(f32) - lens[j].astype(f32))
+    W1 = params[: 3 * h].reshape(h, 3)
+    b1, w2, b2 = params[3 * h: 4 * h], params[4 * h: 5 * h], params[5 * h]
+    z = (W1[:, 0][None] * s[:, None] + W1[:, 1][None] * c[:, None] + W1[:, 2][None] * delta[:, None]
+         + b1[None]).astype(f32)
+    g = (np.maximum(z, f32(0)) * w2[None]).sum(1, dtype=f32) + b2
+    a = f32(1) / (f32(1) + np.exp(-g))
+    d_g = dL.astype(f32) * (s - f32(0.5) * (f32(1) + c)) * a * (f32(1) - a)
+    dz = np.where(z > 0, d_g[:, None] * w2[None], f32(0)).astype(f32)
+    out = np.zeros(5 * h + 1)
+    out[0:3 * h:3] = (dz * s[:, None]).astype(np.float64).sum(0)
+    out[1:3 * h:3] = (dz * c[:, None]).astype(np.float64).sum(0)
+    out[2:3 * h:3] = (dz * delta[:, None]).astype(np.float64).sum(0)
+    out[3 * h:4 * h] = dz.astype(np.float64).sum(0)
+    out[4 * h:5 * h] = (d_g[:, None] * np.maximum(z, f32(0))).astype(np.float64).sum(0)
+    out[5 * h] = d_g.astype(np.float64).sum()
+    return out
+
+
+@pytest.mark.parametrize("d,h", [(24, 8), (128, 32)])
+def test_gradient_rounding_scale_bounds_float32_chain(oracle_mod, small, d, h):
+    """The scale bounds the exact gradient (triangle inequality), and a float32
+    evaluation of the chain lies within GRAD_KAPPA * scale of the FP64
+    gradient even when the per-pair upstream gradients have random signs (the
+    sum then cancels to far below its terms)."""
+    rep = small["rep"]
+    emb = synth.family_embeddings(rep.family, d, seed=4) * np.float32(1.7)
+    params = synth.gate_parameters(h, seed=4)
+    dL = np.random.default_rng(4).standard_normal(small["C"].shape[0])
+    gp, _ = oracle_mod.fuse_backward(small["C"], small["sw"], small["self"], rep.lens, emb, params, h, dL,
+                                     with_emb=False)
+    scale, se = oracle_mod.fuse_backward_scale(small["C"], small["sw"], small["self"], rep.lens, emb, params, h, dL)
+    assert (np.abs(gp) <= scale * (1 + 1e-12)).all()
+    _, ge = oracle_mod.fuse_backward(small["C"], small["sw"], small["self"], rep.lens, emb, params, h, dL)
+    assert (np.abs(ge) <= se * (1 + 1e-12) + 1e-300).all()
+    g32 = float32_adjoint(small["C"], small["sw"], small["self"], rep.lens, emb, params, h, dL.astype(np.float32))
+    err = np.abs(g32 - gp)
+    assert (err <= GRAD_KAPPA * scale).all(), float((err / scale).max())
+    assert (err <= 2.0 ** -22 * scale).all(), "float32 chain error above 0.25 u * scale"

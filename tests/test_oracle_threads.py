@@ -1,0 +1,26 @@
+"""The oracle's multi-threaded runners (the CPU baseline over all host cores)
+split index ranges over threads and call the single-threaded routines, so
+their results must equal the single-threaded calls exactly."""
+import numpy as np
+import pytest
+
+from paper_2602_17330_gb300 import synth
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_threaded_runners_equal_single_thread(oracle_mod, threads):
+    rep = synth.donor_repertoire(6_000, seed=3)
+    a, b = synth.hash_coefficients(64, seed=3)
+    sig = oracle_mod.sign(rep.codes, rep.lens, 3, a, b)
+    assert (oracle_mod.sign_mt(rep.codes, rep.lens, 3, a, b, threads) == sig).all()
+    C = oracle_mod.candidates(sig, 16, 4, 2048)
+    sw = oracle_mod.sw_pairs(rep.codes, rep.lens, C)
+    assert (oracle_mod.sw_pairs_mt(rep.codes, rep.lens, C, threads) == sw).all()
+    self_sc = oracle_mod.self_scores(rep.codes, rep.lens)
+    emb = synth.unit_embeddings(rep.n, 64, seed=3)
+    params = synth.gate_parameters(16, seed=3)
+    want = oracle_mod.fuse_forward(C, sw, self_sc, rep.lens, emb, params, 16)["fused"]
+    assert (oracle_mod.fuse_forward_mt(C, sw, self_sc, rep.lens, emb, params, 16, threads) == want).all()
+    # fewer items than threads
+    few = C[:2]
+    assert (oracle_mod.sw_pairs_mt(rep.codes, rep.lens, few, threads) == sw[:2]).all()

@@ -18,13 +18,13 @@ from paper_2602_17330_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def _close(got, want, scale, rel=1e-4, floor=1e-6):
-    err = np.abs(got.astype(np.float64) - want.astype(np.float64))
-    return bool((err <= rel * np.abs(want) + floor * scale).all())
-
-
 @pytest.mark.parametrize("d,hidden", [(64, 16), (128, 32)])
 def test_noalloc_matches_allocating_backward_twice(d, hidden):
+    """Two calls in a row, the second on a shorter pair list and another
+    upstream gradient, so a block partial left over from the first call would
+    change the second result.  The entry point runs the same kernels with the
+    same fixed grid and reduction order as subquad_fuse_backward, so each
+    result must equal the allocating entry point's bit for bit."""
     import torch
 
     from paper_2602_17330_gb300 import _build, subquad
@@ -41,15 +41,14 @@ def test_noalloc_matches_allocating_backward_twice(d, hidden):
         self_sc = ctx.self_scores(packed)
         emb = torch.from_numpy(synth.family_embeddings(rep.family, d, seed=21)).cuda()
         params = torch.from_numpy(synth.gate_parameters(hidden, seed=21)).cuda()
-        m = int(pairs.shape[0])
-        dL = torch.from_numpy((np.random.default_rng(21).standard_normal(m) / m).astype(np.float32)).cuda()
-        want = ctx.fuse_backward(pairs, sw, self_sc, packed, emb, params, hidden, dL, want_emb=False)
-        want_np = want.cpu().numpy()
-        scale = float(dL.abs().sum()) * 20.0
-        scratch_before = ctx.scratch_bytes()
+        m_all = int(pairs.shape[0])
         lib = subquad.lib()
         P = ctypes.c_void_p
-        for call in range(2):
+        for call, (m, seed) in enumerate([(m_all, 21), (m_all - 12_345, 22)]):
+            dL = torch.from_numpy((np.random.default_rng(seed).standard_normal(m) / m).astype(np.float32)).cuda()
+            want = ctx.fuse_backward(pairs[:m], sw[:m], self_sc, packed, emb, params, hidden, dL, want_emb=False)
+            want_np = want.cpu().numpy()
+            scratch_before = ctx.scratch_bytes()
             out = torch.full((5 * hidden + 1,), float("nan"), dtype=torch.float32, device="cuda")
             st = lib.subquad_fuse_backward_params_noalloc(
                 ctx.handle, P(pairs.data_ptr()), m, P(sw.data_ptr()), P(self_sc.data_ptr()), P(packed.data_ptr()),
@@ -58,6 +57,5 @@ def test_noalloc_matches_allocating_backward_twice(d, hidden):
             assert st == 0, subquad.lib().subquad_strerror(st)
             ctx.check()
             got = out.cpu().numpy()
-            assert np.isfinite(got).all(), f"call {call}: output not written"
-            assert _close(got, want_np, scale), f"call {call}: differs from subquad_fuse_backward"
-        assert ctx.scratch_bytes() == scratch_before, "the call grew the context scratch"
+            assert np.array_equal(got, want_np), f"call {call}: differs from subquad_fuse_backward"
+            assert ctx.scratch_bytes() == scratch_before, "the call grew the context scratch"
