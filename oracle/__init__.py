@@ -71,6 +71,12 @@ def _load():
     lib.oracle_fuse_backward_scale.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, F32P, c.c_int,
                                                F64P, F64P, opt_f64]
     lib.oracle_fuse_backward_scale.restype = c.c_int
+    lib.oracle_fuse_forward_mc.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, opt_f64, c.c_int, F32P,
+                                           c.c_int, c.c_int, F64P, opt_f64, opt_f64]
+    lib.oracle_fuse_forward_mc.restype = c.c_int
+    lib.oracle_fuse_backward_mc.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, opt_f64, c.c_int,
+                                            F32P, c.c_int, c.c_int, F64P, F64P, opt_f64]
+    lib.oracle_fuse_backward_mc.restype = c.c_int
     lib.oracle_pair_labels.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, I32P]
     lib.oracle_pair_labels.restype = None
     lib.oracle_pair_weights.argtypes = [I32P, c.c_int64, c.c_int, F64P]
@@ -234,6 +240,47 @@ def fuse_backward_scale(pairs, sw_scores, self_sc, lens, emb, params, hidden: in
     if rc != 0:
         raise MemoryError("oracle_fuse_backward_scale failed")
     return sc, se
+
+
+def mc_param_count(hidden: int, channels: int) -> int:
+    """Parameters of the M-channel gate: W1 [h][M+1], b1 [h], W2 [M-1][h], b2 [M-1]."""
+    return (channels + 1) * hidden + hidden + (channels - 1) * hidden + (channels - 1)
+
+
+def fuse_forward_mc(pairs, sw_scores, self_sc, lens, emb, sig, params, hidden: int, channels: int):
+    """M-channel fusion (M = 2 or 3).  sig: uint32 [n, H] sequence-major (used
+    for M = 3).  Returns dict of FP64 arrays: fused [m], weights [m, M],
+    jaccard [m] (0 for M = 2)."""
+    p = _pairs(pairs)
+    m = p.shape[0]
+    emb = _c(emb, np.float32)
+    sig_c = None if sig is None else _c(sig, np.uint32)
+    H = 0 if sig_c is None else sig_c.shape[1]
+    out = {"fused": np.zeros(m), "weights": np.zeros((m, channels)), "jaccard": np.zeros(m)}
+    rc = _load().oracle_fuse_forward_mc(p, m, _c(sw_scores, np.int32), _c(self_sc, np.int32), _c(lens, np.uint8),
+                                        emb, emb.shape[1], _ptr(sig_c), H, _c(params, np.float32), hidden, channels,
+                                        out["fused"], _ptr(out["weights"]), _ptr(out["jaccard"]))
+    if rc != 0:
+        raise ValueError("oracle_fuse_forward_mc failed")
+    return out
+
+
+def fuse_backward_mc(pairs, sw_scores, self_sc, lens, emb, sig, params, hidden: int, channels: int, dL_dfused,
+                     with_emb: bool = True):
+    """Returns (grad_params FP64 [P], grad_emb FP64 [n, d] or None)."""
+    p = _pairs(pairs)
+    emb = _c(emb, np.float32)
+    sig_c = None if sig is None else _c(sig, np.uint32)
+    H = 0 if sig_c is None else sig_c.shape[1]
+    gp = np.zeros(mc_param_count(hidden, channels), dtype=np.float64)
+    ge = np.zeros(emb.shape, dtype=np.float64) if with_emb else None
+    rc = _load().oracle_fuse_backward_mc(p, p.shape[0], _c(sw_scores, np.int32), _c(self_sc, np.int32),
+                                         _c(lens, np.uint8), emb, emb.shape[1], _ptr(sig_c), H,
+                                         _c(params, np.float32), hidden, channels, _c(dL_dfused, np.float64), gp,
+                                         _ptr(ge))
+    if rc != 0:
+        raise ValueError("oracle_fuse_backward_mc failed")
+    return gp, ge
 
 
 # --------------------------------------------------------------------------

@@ -429,6 +429,158 @@ int oracle_fuse_backward_scale(const uint32_t *pairs, int64_t m, const int32_t *
 }
 
 /* ------------------------------------------------------------------------- */
+/* M-channel gated fusion (Eq. wm with M > 2 channels, Eq. afused; Eq. alpha's
+ * sigmoid is the M = 2 case).  Channels, in order:
+ *   a^(1) = s  (normalised alignment, as above),
+ *   a^(2) = c' = (1 + c)/2  (embedding cosine, as above),
+ *   a^(3) = J  (MinHash estimate of the k-mer Jaccard index: the fraction of
+ *               the H hash rows on which the two signatures agree; M = 3).
+ * Reading: one two-layer MLP scores all channels from the features
+ * f = [s, c, |L_i - L_j|, J] (J only for M = 3); its M - 1 outputs are the
+ * logits of channels 1, 3, ..., and channel 2 keeps the fixed logit 0 (the
+ * reference channel), so M = 2 is exactly the gate above.
+ *   z = W1 f + b1 (h),  u = ReLU(z),  g^(1) = W2[0] . u + b2[0],  g^(2) = 0,
+ *   g^(3) = W2[1] . u + b2[1];  w = softmax(g);  fused = sum_m w_m a^(m).
+ * params (float32): W1 [h][F] row-major (F = M + 1), b1 [h], W2 [M-1][h]
+ * row-major, b2 [M-1]; for M = 2 this is the layout of the two-channel gate.
+ * sig: uint32 [n][H] sequence-major (the layout of oracle_sign).
+ * Pins: softmax weights against a library softmax, weights sum to one,
+ * M = 2 equals the two-channel gate, J against the exact agreement count,
+ * channel limits (one dominant logit gives that channel's affinity).        */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double a[3], f[4], g[3], w[3], fused, c, ni, nj;
+} mc_state;
+
+static void fuse_pair_mc(const uint32_t *pairs, int64_t p, const int32_t *sw, const int32_t *self,
+                         const uint8_t *lens, const float *emb, int d, const uint32_t *sig, int H, const float *params,
+                         int h, int M, double *z /* [h] */, mc_state *st)
+{
+    uint32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+    const float *ei = emb + (int64_t)i * d, *ej = emb + (int64_t)j * d;
+    double prod = (double)self[i] * (double)self[j];
+    double s = prod > 0.0 ? (double)sw[p] / sqrt(prod) : 0.0;
+    double dot = 0.0, sii = 0.0, sjj = 0.0;
+    for (int k = 0; k < d; ++k) {
+        dot += (double)ei[k] * (double)ej[k];
+        sii += (double)ei[k] * (double)ei[k];
+        sjj += (double)ej[k] * (double)ej[k];
+    }
+    st->ni = sqrt(sii);
+    st->nj = sqrt(sjj);
+    st->c = (st->ni > 0.0 && st->nj > 0.0) ? dot / (st->ni * st->nj) : 0.0;
+    int F = M + 1;
+    st->f[0] = s;
+    st->f[1] = st->c;
+    st->f[2] = fabs((double)lens[i] - (double)lens[j]);
+    st->a[0] = s;
+    st->a[1] = 0.5 * (1.0 + st->c);
+    if (M == 3) {
+        int agree = 0;
+        for (int t = 0; t < H; ++t) agree += sig[(int64_t)i * H + t] == sig[(int64_t)j * H + t];
+        st->a[2] = (double)agree / (double)H;
+        st->f[3] = st->a[2];
+    }
+    const float *W1 = params, *b1 = params + F * h, *W2 = params + (F + 1) * h, *b2 = params + (F + M) * h;
+    for (int k = 0; k < h; ++k) {
+        double acc = (double)b1[k];
+        for (int q = 0; q < F; ++q) acc += (double)W1[F * k + q] * st->f[q];
+        z[k] = acc;
+    }
+    /* logits: channel 1 <- output 0, channel 2 <- 0, channel 3 <- output 1 */
+    st->g[1] = 0.0;
+    for (int r = 0; r < M - 1; ++r) {
+        double acc = (double)b2[r];
+        for (int k = 0; k < h; ++k) acc += (double)W2[r * h + k] * (z[k] > 0.0 ? z[k] : 0.0);
+        st->g[r == 0 ? 0 : 2] = acc;
+    }
+    double mx = st->g[0];
+    for (int q = 1; q < M; ++q)
+        if (st->g[q] > mx) mx = st->g[q];
+    double den = 0.0;
+    for (int q = 0; q < M; ++q) den += exp(st->g[q] - mx);
+    st->fused = 0.0;
+    for (int q = 0; q < M; ++q) {
+        st->w[q] = exp(st->g[q] - mx) / den;
+        st->fused += st->w[q] * st->a[q];
+    }
+}
+
+int oracle_fuse_forward_mc(const uint32_t *pairs, int64_t m, const int32_t *sw, const int32_t *self,
+                           const uint8_t *lens, const float *emb, int d, const uint32_t *sig, int H,
+                           const float *params, int h, int M, double *fused, double *weights /* [m][M], nullable */,
+                           double *jacc /* [m], nullable */)
+{
+    if (M < 2 || M > 3 || (M == 3 && (!sig || H < 1))) return -2;
+    double *z = (double *)malloc((size_t)(h > 0 ? h : 1) * sizeof(double));
+    if (!z) return -1;
+    for (int64_t p = 0; p < m; ++p) {
+        mc_state st;
+        fuse_pair_mc(pairs, p, sw, self, lens, emb, d, sig, H, params, h, M, z, &st);
+        fused[p] = st.fused;
+        if (weights)
+            for (int q = 0; q < M; ++q) weights[p * M + q] = st.w[q];
+        if (jacc) jacc[p] = M == 3 ? st.a[2] : 0.0;
+    }
+    free(z);
+    return 0;
+}
+
+/* Adjoint of the M-channel fusion.  With fused = sum_m w_m a_m and w the
+ * softmax of g, d fused / d g_k = w_k (a_k - fused); the logits' gradients
+ * flow through W2, the ReLU (subgradient 0 at 0) and W1 to the parameters,
+ * and with the channel c' = (1 + c)/2 and the feature c into the cosine and
+ * the embeddings.  J is integer-derived and not differentiated.
+ * grad_params (layout of params) and grad_emb (nullable, [n][d]) accumulate.
+ * Pin: central finite differences of forward + loss in a test.              */
+int oracle_fuse_backward_mc(const uint32_t *pairs, int64_t m, const int32_t *sw, const int32_t *self,
+                            const uint8_t *lens, const float *emb, int d, const uint32_t *sig, int H,
+                            const float *params, int h, int M, const double *dL_dfused, double *grad_params,
+                            double *grad_emb)
+{
+    if (M < 2 || M > 3 || (M == 3 && (!sig || H < 1))) return -2;
+    double *z = (double *)malloc((size_t)(h > 0 ? h : 1) * sizeof(double));
+    if (!z) return -1;
+    int F = M + 1;
+    const float *W1 = params, *W2 = params + (F + 1) * h;
+    double *gW1 = grad_params, *gb1 = grad_params + F * h, *gW2 = grad_params + (F + 1) * h,
+           *gb2 = grad_params + (F + M) * h;
+    for (int64_t p = 0; p < m; ++p) {
+        mc_state st;
+        fuse_pair_mc(pairs, p, sw, self, lens, emb, d, sig, H, params, h, M, z, &st);
+        double dA = dL_dfused[p];
+        double d_out[2]; /* gradient of MLP output r (logit of channel 1, then 3) */
+        d_out[0] = dA * st.w[0] * (st.a[0] - st.fused);
+        d_out[1] = M == 3 ? dA * st.w[2] * (st.a[2] - st.fused) : 0.0;
+        double d_c = dA * st.w[1] * 0.5; /* through the channel c' */
+        for (int r = 0; r < M - 1; ++r) gb2[r] += d_out[r];
+        for (int k = 0; k < h; ++k) {
+            double u = z[k] > 0.0 ? z[k] : 0.0;
+            double du = 0.0;
+            for (int r = 0; r < M - 1; ++r) {
+                gW2[r * h + k] += d_out[r] * u;
+                du += d_out[r] * (double)W2[r * h + k];
+            }
+            double d_z = z[k] > 0.0 ? du : 0.0;
+            for (int q = 0; q < F; ++q) gW1[F * k + q] += d_z * st.f[q];
+            gb1[k] += d_z;
+            d_c += d_z * (double)W1[F * k + 1];
+        }
+        if (grad_emb && st.ni > 0.0 && st.nj > 0.0) {
+            uint32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+            const float *ei = emb + (int64_t)i * d, *ej = emb + (int64_t)j * d;
+            double inv = 1.0 / (st.ni * st.nj);
+            for (int k = 0; k < d; ++k) {
+                grad_emb[(int64_t)i * d + k] += d_c * ((double)ej[k] * inv - st.c * (double)ei[k] / (st.ni * st.ni));
+                grad_emb[(int64_t)j * d + k] += d_c * ((double)ei[k] * inv - st.c * (double)ej[k] / (st.nj * st.nj));
+            }
+        }
+    }
+    free(z);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Training objective for the gate (reading: weighted binary cross-entropy of
  * the fused score against family-match labels; weight of a pair = inverse
  * frequency of its subgroup among the batch's pairs, normalised so the weights

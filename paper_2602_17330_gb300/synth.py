@@ -251,6 +251,21 @@ def gate_param_count(hidden: int) -> int:
     return 3 * hidden + hidden + hidden + 1
 
 
+def gate_parameters_mc(hidden: int, channels: int, seed: int = 0) -> np.ndarray:
+    """Flat float32 parameters of the M-channel gate: [W1 (hidden x (M+1),
+    row-major), b1 (hidden), W2 ((M-1) x hidden, row-major), b2 (M-1)], each
+    layer uniform on +-1/sqrt(fan_in).  For M = 2 this equals gate_parameters."""
+    if channels == 2:
+        return gate_parameters(hidden, seed)
+    r = rng_for(seed, "gate")
+    F = channels + 1
+    w1 = r.uniform(-1.0, 1.0, (hidden, F)) / np.sqrt(F)
+    b1 = r.uniform(-1.0, 1.0, hidden) / np.sqrt(F)
+    w2 = r.uniform(-1.0, 1.0, (channels - 1, hidden)) / np.sqrt(hidden)
+    b2 = r.uniform(-1.0, 1.0, channels - 1) / np.sqrt(hidden)
+    return np.concatenate([w1.ravel(), b1, w2.ravel(), b2]).astype(np.float32)
+
+
 # ---------------------------------------------------------------------------
 # The five workloads, by what they are
 # ---------------------------------------------------------------------------
