@@ -387,6 +387,46 @@ int subquad_fuse_backward_params_noalloc(subquad_ctx *ctx, const uint32_t *pairs
 int subquad_adam_step(subquad_ctx *ctx, float *param, const float *grad, float *m1, float *m2, int64_t count, int t,
                       float lr, float beta1, float beta2, float eps);
 
+/* ------------------------------------------------------------------------ */
+/* M-channel gated fusion -- Eq. wm with M > 2 channels and Eq. afused (the  */
+/* two-channel gate above is its M = 2 case).                                */
+/* ------------------------------------------------------------------------ */
+
+/* Channels: a1 = s = S_ij / sqrt(S_ii S_jj), a2 = c' = (1 + cos(e_i, e_j)) / 2
+ * and, for channels == 3, a3 = J = the fraction of the bands*rows MinHash rows
+ * on which the signatures of i and j agree (the sketch's estimate of their
+ * k-mer Jaccard index).  One gate MLP scores the channels from the features
+ * f = [s, c, |L_i - L_j|, J] (J only for M = 3): z = W1 f + b1, u = ReLU(z),
+ * its M - 1 outputs W2 u + b2 are the logits of channels 1 and 3 and channel 2
+ * keeps logit 0; w = softmax of the M logits; fused = sum_m w_m a_m.
+ * gate_params: device float [(2M+1) hidden + M - 1] = W1 [hidden][M+1]
+ * row-major, b1 [hidden], W2 [M-1][hidden] row-major, b2 [M-1] (for M = 2
+ * exactly the layout of subquad_fuse_forward).  sig: device uint32
+ * [bands][n][rows] as written by subquad_sign (16-byte aligned when rows ==
+ * 4; ignored for M = 2).  weights_out: device float [m][M] or NULL.  Other
+ * arguments as subquad_fuse_forward; channels is 2 or 3, 1 <= rows <= 8,
+ * bands*rows <= 512. */
+int subquad_fuse_forward_mc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                            const int32_t *self_scores, const void *packed, int pack_stride, const float *emb, int d,
+                            const uint32_t *sig, int64_t n, int bands, int rows, const float *gate_params, int hidden,
+                            int channels, float *fused_out, float *weights_out);
+
+/* Adjoint of subquad_fuse_forward_mc for dL/dfused (device float [m]):
+ * d fused / d g_k = w_k (a_k - fused) for the MLP's outputs, then W2, the ReLU
+ * (subgradient 0 at 0) and W1; the cosine receives w_2 / 2 through the
+ * channel c' and the W1 column of c through the feature.  J is integer-derived
+ * and not differentiated.  grad_params (device float, layout of gate_params)
+ * and, when not NULL, grad_emb (device float [n][d], needs the pair index of
+ * subquad_pair_index) are overwritten.  Reductions as subquad_fuse_backward
+ * (compensated FP32 per lane, FP64 across lanes and blocks in a fixed order):
+ * bitwise reproducible. */
+int subquad_fuse_backward_mc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                             const int32_t *self_scores, const void *packed, int pack_stride, const float *emb,
+                             int64_t n, int d, const uint32_t *sig, int bands, int rows, const float *gate_params,
+                             int hidden, int channels, const float *dL_dfused, const uint32_t *perm_i,
+                             const uint32_t *off_i, const uint32_t *perm_j, const uint32_t *off_j, float *grad_params,
+                             float *grad_emb);
+
 /* subquad_fuse_forward for a pair count held on the device (*d_m, at most
  * m_max pairs): the graph-capturable form. */
 int subquad_fuse_forward_async(subquad_ctx *ctx, const uint32_t *pairs, const uint64_t *d_m, int64_t m_max,

@@ -77,6 +77,9 @@ def _load():
     lib.oracle_fuse_backward_mc.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, opt_f64, c.c_int,
                                             F32P, c.c_int, c.c_int, F64P, F64P, opt_f64]
     lib.oracle_fuse_backward_mc.restype = c.c_int
+    lib.oracle_fuse_backward_mc_scale.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, opt_f64, c.c_int,
+                                                  F32P, c.c_int, c.c_int, F64P, F64P, opt_f64]
+    lib.oracle_fuse_backward_mc_scale.restype = c.c_int
     lib.oracle_pair_labels.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, I32P]
     lib.oracle_pair_labels.restype = None
     lib.oracle_pair_weights.argtypes = [I32P, c.c_int64, c.c_int, F64P]
@@ -281,6 +284,24 @@ def fuse_backward_mc(pairs, sw_scores, self_sc, lens, emb, sig, params, hidden: 
     if rc != 0:
         raise ValueError("oracle_fuse_backward_mc failed")
     return gp, ge
+
+
+def fuse_backward_mc_scale(pairs, sw_scores, self_sc, lens, emb, sig, params, hidden: int, channels: int,
+                           dL_dfused, with_emb: bool = True):
+    """Rounding scale of the M-channel adjoint: (FP64 [P], FP64 [n, d] or None)."""
+    p = _pairs(pairs)
+    emb = _c(emb, np.float32)
+    sig_c = None if sig is None else _c(sig, np.uint32)
+    H = 0 if sig_c is None else sig_c.shape[1]
+    sc = np.zeros(mc_param_count(hidden, channels), dtype=np.float64)
+    se = np.zeros(emb.shape, dtype=np.float64) if with_emb else None
+    rc = _load().oracle_fuse_backward_mc_scale(p, p.shape[0], _c(sw_scores, np.int32), _c(self_sc, np.int32),
+                                               _c(lens, np.uint8), emb, emb.shape[1], _ptr(sig_c), H,
+                                               _c(params, np.float32), hidden, channels, _c(dL_dfused, np.float64),
+                                               sc, _ptr(se))
+    if rc != 0:
+        raise ValueError("oracle_fuse_backward_mc_scale failed")
+    return sc, se
 
 
 # --------------------------------------------------------------------------

@@ -580,6 +580,59 @@ int oracle_fuse_backward_mc(const uint32_t *pairs, int64_t m, const int32_t *sw,
     return 0;
 }
 
+/* Rounding scale of the M-channel adjoint (test infrastructure, as
+ * oracle_fuse_backward_scale): every pair's contribution evaluated on operand
+ * magnitudes -- factors in absolute value, a difference a - b as |a| + |b|,
+ * sums as the sum of their terms' magnitudes, the cosine as 1, the ReLU open.
+ * scale (layout of params) and scale_emb (nullable) accumulate.             */
+int oracle_fuse_backward_mc_scale(const uint32_t *pairs, int64_t m, const int32_t *sw, const int32_t *self,
+                                  const uint8_t *lens, const float *emb, int d, const uint32_t *sig, int H,
+                                  const float *params, int h, int M, const double *dL_dfused, double *scale,
+                                  double *scale_emb)
+{
+    if (M < 2 || M > 3 || (M == 3 && (!sig || H < 1))) return -2;
+    double *z = (double *)malloc((size_t)(h > 0 ? h : 1) * sizeof(double));
+    if (!z) return -1;
+    int F = M + 1;
+    const float *W1 = params, *b1 = params + F * h, *W2 = params + (F + 1) * h;
+    double *sW1 = scale, *sb1 = scale + F * h, *sW2 = scale + (F + 1) * h, *sb2 = scale + (F + M) * h;
+    for (int64_t p = 0; p < m; ++p) {
+        mc_state st;
+        fuse_pair_mc(pairs, p, sw, self, lens, emb, d, sig, H, params, h, M, z, &st);
+        double dA = fabs(dL_dfused[p]);
+        double fmag[4] = {st.f[0], 1.0, st.f[2], M == 3 ? st.f[3] : 0.0};
+        double amag = fabs(st.a[0]) + fabs(st.a[1]) + (M == 3 ? fabs(st.a[2]) : 0.0); /* bounds |fused| */
+        double d_out[2];
+        d_out[0] = dA * st.w[0] * (fabs(st.a[0]) + amag);
+        d_out[1] = M == 3 ? dA * st.w[2] * (fabs(st.a[2]) + amag) : 0.0;
+        double d_c = dA * st.w[1] * 0.5;
+        for (int r = 0; r < M - 1; ++r) sb2[r] += d_out[r];
+        for (int k = 0; k < h; ++k) {
+            double zmag = fabs((double)b1[k]);
+            for (int q = 0; q < F; ++q) zmag += fabs((double)W1[F * k + q]) * fmag[q];
+            double du = 0.0;
+            for (int r = 0; r < M - 1; ++r) {
+                sW2[r * h + k] += d_out[r] * zmag;
+                du += d_out[r] * fabs((double)W2[r * h + k]);
+            }
+            for (int q = 0; q < F; ++q) sW1[F * k + q] += du * fmag[q];
+            sb1[k] += du;
+            d_c += du * fabs((double)W1[F * k + 1]);
+        }
+        if (scale_emb && st.ni > 0.0 && st.nj > 0.0) {
+            uint32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+            const float *ei = emb + (int64_t)i * d, *ej = emb + (int64_t)j * d;
+            double inv = 1.0 / (st.ni * st.nj);
+            for (int k = 0; k < d; ++k) {
+                scale_emb[(int64_t)i * d + k] += d_c * (fabs((double)ej[k]) * inv + fabs((double)ei[k]) / (st.ni * st.ni));
+                scale_emb[(int64_t)j * d + k] += d_c * (fabs((double)ei[k]) * inv + fabs((double)ej[k]) / (st.nj * st.nj));
+            }
+        }
+    }
+    free(z);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Training objective for the gate (reading: weighted binary cross-entropy of
  * the fused score against family-match labels; weight of a pair = inverse

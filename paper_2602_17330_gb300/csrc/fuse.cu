@@ -577,3 +577,429 @@ extern "C" int subquad_fuse_forward_async(subquad_ctx *ctx, const uint32_t *pair
     return launch_forward<4>(ctx, grid, pairs, m_max, sw, self_scores, packed, emb, d, gate_params, hidden, fused_out,
                              alpha_out, dm);
 }
+
+// ---------------------------------------------------------------------------
+// M-channel fusion (Eq. wm with M > 2, Eq. afused): channels s, c' = (1+c)/2
+// and, for M = 3, J = the fraction of the H MinHash rows on which the two
+// signatures agree (the sketch's estimate of the k-mer Jaccard index).  One
+// gate MLP scores the channels from f = [s, c, |dL|, J]: its M - 1 outputs
+// are the logits of channels 1 and 3, channel 2 keeps logit 0, and the
+// weights are the softmax of the logits.  Parameters: W1 [h][M+1], b1 [h],
+// W2 [M-1][h], b2 [M-1] (for M = 2 the layout of the two-channel gate).
+// The forward uses four lanes per pair like the two-channel kernel; the
+// signature rows of a band are one 16-byte vector per sequence when rows ==
+// 4 (the library's layout [band][n][rows]), so lane q compares bands q,
+// q + 4, ... with one vector load per member.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Agreeing signature rows of sequences i and j, summed over the hashes this
+// lane owns (hash t of band t / rows, row t % rows; lanes stride by `lanes`).
+template <int LANES>
+__device__ __forceinline__ int sig_agree(const uint32_t *__restrict__ sig, int64_t n, int bands, int rows, uint32_t i,
+                                         uint32_t j, int sub, bool valid)
+{
+    int agree = 0;
+    if (!valid) return 0;
+    if (rows == 4) {
+        const uint4 *sv = reinterpret_cast<const uint4 *>(sig);
+        for (int b = sub; b < bands; b += LANES) {
+            const uint4 x = __ldg(sv + (int64_t)b * n + i), y = __ldg(sv + (int64_t)b * n + j);
+            agree += (x.x == y.x) + (x.y == y.y) + (x.z == y.z) + (x.w == y.w);
+        }
+    } else {
+        const int H = bands * rows;
+        for (int t = sub; t < H; t += LANES) {
+            const int b = t / rows, r = t - b * rows;
+            const int64_t base = (int64_t)b * n * rows + r;
+            agree += __ldg(sig + base + (int64_t)i * rows) == __ldg(sig + base + (int64_t)j * rows);
+        }
+    }
+    return agree;
+}
+
+// Parameter offsets of the M-channel gate.
+struct McLayout {
+    int F, W1, b1, W2, b2, P;
+    __host__ __device__ McLayout(int M, int h)
+        : F(M + 1), W1(0), b1((M + 1) * h), W2((M + 2) * h), b2((2 * M + 1) * h), P((2 * M + 1) * h + M - 1)
+    {
+    }
+};
+
+template <int M, int WORDS, int CPL>
+__global__ void __launch_bounds__(kFuseThreads) fuse_forward_mc_kernel(
+    const uint32_t *__restrict__ pairs, int64_t m, const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc,
+    const uint64_t *__restrict__ packed, const float *__restrict__ emb, int d, const uint32_t *__restrict__ sig,
+    int64_t n, int bands, int rows, const float *__restrict__ params, int hidden, float *__restrict__ fused,
+    float *__restrict__ weights)
+{
+    constexpr int F = M + 1;
+    __shared__ float s_w1[kMaxHidden * F];
+    __shared__ float s_b1[kMaxHidden];
+    __shared__ float s_w2[(M - 1) * kMaxHidden];
+    __shared__ float s_b2[M - 1];
+    const McLayout L(M, hidden);
+    for (int q = threadIdx.x; q < hidden * F; q += blockDim.x) s_w1[q] = params[L.W1 + q];
+    for (int q = threadIdx.x; q < hidden; q += blockDim.x) s_b1[q] = params[L.b1 + q];
+    for (int q = threadIdx.x; q < (M - 1) * hidden; q += blockDim.x) s_w2[q] = params[L.W2 + q];
+    if (threadIdx.x < M - 1) s_b2[threadIdx.x] = params[L.b2 + threadIdx.x];
+    __syncthreads();
+    const int H = bands * rows;
+    constexpr int kPairsPerWarp = 32 / kTppF;
+    const int sub = threadIdx.x & (kTppF - 1);
+    const int slot = (threadIdx.x & 31) / kTppF;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int d4 = d >> 2;
+    for (int64_t pbase = warp * kPairsPerWarp; pbase < m; pbase += nwarps * kPairsPerWarp) {
+        const int64_t p = pbase + slot;
+        const bool valid = p < m;
+        const uint2 ij = valid ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p) : make_uint2(0, 0);
+        PairInputs<WORDS, CPL, kTppF> in;
+        in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
+        int agree = M == 3 ? sig_agree<kTppF>(sig, n, bands, rows, ij.x, ij.y, sub, valid) : 0;
+        float dot = 0.f, sii = 0.f, sjj = 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const float4 a = in.a[c], b = in.b[c];
+            dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, dot))));
+            sii = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, sii))));
+            sjj = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, sjj))));
+        }
+        dot = quad_sum(dot);
+        sii = quad_sum(sii);
+        sjj = quad_sum(sjj);
+        if (M == 3) {
+            agree += __shfl_xor_sync(0xffffffffu, agree, 2, kTppF);
+            agree += __shfl_xor_sync(0xffffffffu, agree, 1, kTppF);
+        }
+        const float prod = (float)in.self_i * (float)in.self_j;
+        const float s = prod > 0.f ? (float)in.sw * rsqrtf(prod) : 0.f;
+        const float nn = sii * sjj;
+        const float c = nn > 0.f ? dot * rsqrtf(nn) : 0.f;
+        const float delta = fabsf((float)(in.len_i - in.len_j));
+        const float J = M == 3 ? (float)agree / (float)H : 0.f;
+        float acc0 = 0.f, acc1 = 0.f;
+        for (int k = sub; k < hidden; k += kTppF) {
+            const float *w = s_w1 + k * F;
+            float z = fmaf(w[0], s, fmaf(w[1], c, fmaf(w[2], delta, s_b1[k])));
+            if (M == 3) z = fmaf(w[3], J, z);
+            const float u = fmaxf(z, 0.f);
+            acc0 = fmaf(s_w2[k], u, acc0);
+            if (M == 3) acc1 = fmaf(s_w2[hidden + k], u, acc1);
+        }
+        const float g1 = quad_sum(acc0) + s_b2[0];
+        const float g3 = M == 3 ? quad_sum(acc1) + s_b2[M - 2] : 0.f;
+        if (valid && sub == 0) {
+            const float cp = 0.5f * (1.f + c);
+            const float mx = M == 3 ? fmaxf(fmaxf(g1, 0.f), g3) : fmaxf(g1, 0.f);
+            const float e1 = __expf(g1 - mx), e2 = __expf(-mx), e3 = M == 3 ? __expf(g3 - mx) : 0.f;
+            const float inv = __fdividef(1.f, e1 + e2 + e3);
+            const float w1 = e1 * inv, w2 = e2 * inv, w3 = e3 * inv;
+            fused[p] = M == 3 ? fmaf(w1, s, fmaf(w2, cp, w3 * J)) : fmaf(w1, s, w2 * cp);
+            if (weights) {
+                weights[p * M] = w1;
+                weights[p * M + 1] = w2;
+                if (M == 3) weights[p * M + 2] = w3;
+            }
+        }
+    }
+}
+
+// Adjoint of the M-channel fusion: sixteen lanes per pair as in the
+// two-channel adjoint; d fused / d g_k = w_k (a_k - fused) for the two MLP
+// outputs, then W2, the ReLU and W1; the cosine receives w_2 / 2 from the
+// channel c' and W1[k][1] dz_k from the feature c.
+template <int M, int WORDS, int CPL, int HPL>
+__global__ void __launch_bounds__(kFuseThreads) fuse_backward_mc_kernel(
+    const uint32_t *__restrict__ pairs, int64_t m, const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc,
+    const uint64_t *__restrict__ packed, const float *__restrict__ emb, int d, const uint32_t *__restrict__ sig,
+    int64_t n, int bands, int rows, const float *__restrict__ params, int hidden, const float *__restrict__ dL,
+    float4 *__restrict__ coef, double *__restrict__ partials)
+{
+    constexpr int F = M + 1;
+    __shared__ float s_par[(2 * M + 1) * kMaxHidden + M - 1];
+    extern __shared__ double s_red[];  // [kGroups][P]
+    const McLayout L(M, hidden);
+    const int P = L.P;
+    for (int q = threadIdx.x; q < P; q += blockDim.x) s_par[q] = params[q];
+    __syncthreads();
+    const float *W1 = s_par + L.W1, *b1 = s_par + L.b1, *W2 = s_par + L.W2, *b2 = s_par + L.b2;
+    const int H = bands * rows;
+    const int sub = threadIdx.x & (kTpp - 1);
+    const int half = (threadIdx.x >> 4) & 1;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int d4 = d >> 2;
+    Kahan gW1[HPL][F], gb1[HPL], gW2[HPL][M - 1], gb2[M - 1];
+    for (int64_t pbase = warp * 2; pbase < m; pbase += nwarps * 2) {
+        const int64_t p = pbase + half;
+        const bool valid = p < m;
+        const uint2 ij = valid ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p) : make_uint2(0, 0);
+        PairInputs<WORDS, CPL> in;
+        in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
+        const float dA = valid ? __ldg(dL + p) : 0.f;
+        int agree = M == 3 ? sig_agree<kTpp>(sig, n, bands, rows, ij.x, ij.y, sub, valid) : 0;
+        float dot = 0.f, sii = 0.f, sjj = 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const float4 a = in.a[c], b = in.b[c];
+            dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w))) + dot;
+            sii = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, a.w * a.w))) + sii;
+            sjj = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, b.w * b.w))) + sjj;
+        }
+        dot = group_sum(dot);
+        sii = group_sum(sii);
+        sjj = group_sum(sjj);
+        if (M == 3) {
+#pragma unroll
+            for (int o = kTpp / 2; o > 0; o >>= 1) agree += __shfl_xor_sync(0xffffffffu, agree, o, kTpp);
+        }
+        const float prod = (float)in.self_i * (float)in.self_j;
+        const float s = prod > 0.f ? (float)in.sw / sqrtf(prod) : 0.f;
+        const float nn = sii * sjj;
+        const float c = nn > 0.f ? dot / sqrtf(nn) : 0.f;
+        const float f[4] = {s, c, fabsf((float)(in.len_i - in.len_j)), M == 3 ? (float)agree / (float)H : 0.f};
+        float z[HPL];
+        float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+        for (int hh = 0; hh < HPL; ++hh) {
+            const int k = sub + hh * kTpp;
+            z[hh] = 0.f;
+            if (k < hidden) {
+                float t = b1[k];
+#pragma unroll
+                for (int q = F - 1; q >= 0; --q) t = fmaf(W1[k * F + q], f[q], t);
+                z[hh] = t;
+                const float u = fmaxf(t, 0.f);
+                acc0 = fmaf(W2[k], u, acc0);
+                if (M == 3) acc1 = fmaf(W2[hidden + k], u, acc1);
+            }
+        }
+        const float g1 = group_sum(acc0) + b2[0];
+        const float g3 = M == 3 ? group_sum(acc1) + b2[M - 2] : 0.f;
+        const float mx = M == 3 ? fmaxf(fmaxf(g1, 0.f), g3) : fmaxf(g1, 0.f);
+        const float e1 = expf(g1 - mx), e2 = expf(-mx), e3 = M == 3 ? expf(g3 - mx) : 0.f;
+        const float den = e1 + e2 + e3;
+        const float w1 = e1 / den, w2 = e2 / den, w3 = e3 / den;
+        const float cp = 0.5f * (1.f + c);
+        const float fused = M == 3 ? w1 * s + w2 * cp + w3 * f[3] : w1 * s + w2 * cp;
+        const float d0 = dA * w1 * (s - fused);
+        const float d1 = M == 3 ? dA * w3 * (f[3] - fused) : 0.f;
+        float dc = 0.f;
+#pragma unroll
+        for (int hh = 0; hh < HPL; ++hh) {
+            const int k = sub + hh * kTpp;
+            if (k < hidden && valid) {
+                const float u = fmaxf(z[hh], 0.f);
+                gW2[hh][0].add(d0 * u);
+                float du = d0 * W2[k];
+                if (M == 3) {
+                    gW2[hh][M - 2].add(d1 * u);
+                    du = fmaf(d1, W2[hidden + k], du);
+                }
+                const float dz = z[hh] > 0.f ? du : 0.f;
+#pragma unroll
+                for (int q = 0; q < F; ++q) gW1[hh][q].add(dz * f[q]);
+                gb1[hh].add(dz);
+                dc = fmaf(dz, W1[k * F + 1], dc);
+            }
+        }
+        dc = group_sum(dc) + dA * w2 * 0.5f;
+        if (sub == 0 && valid) {
+            gb2[0].add(d0);
+            if (M == 3) gb2[M - 2].add(d1);
+            if (coef) {
+                const float ni = sqrtf(sii), nj = sqrtf(sjj);
+                float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ni > 0.f && nj > 0.f) {
+                    cf.x = dc / (ni * nj);
+                    cf.y = -dc * c / sii;
+                    cf.z = -dc * c / sjj;
+                }
+                coef[p] = cf;
+            }
+        }
+    }
+    const int grp = threadIdx.x / kTpp;
+    double *mine = s_red + (size_t)grp * P;
+#pragma unroll
+    for (int hh = 0; hh < HPL; ++hh) {
+        const int k = sub + hh * kTpp;
+        if (k < hidden) {
+#pragma unroll
+            for (int q = 0; q < F; ++q) mine[L.W1 + k * F + q] = gW1[hh][q].value();
+            mine[L.b1 + k] = gb1[hh].value();
+#pragma unroll
+            for (int r = 0; r < M - 1; ++r) mine[L.W2 + r * hidden + k] = gW2[hh][r].value();
+        }
+    }
+    if (sub == 0)
+        for (int r = 0; r < M - 1; ++r) mine[L.b2 + r] = gb2[r].value();
+    __syncthreads();
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+        double t = 0.0;
+        for (int gi = 0; gi < kGroups; ++gi) t += s_red[(size_t)gi * P + q];
+        partials[(int64_t)blockIdx.x * P + q] = t;
+    }
+}
+
+template <int M, int WORDS>
+int launch_forward_mc(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                      const int32_t *self_scores, const void *packed, const float *emb, int d, const uint32_t *sig,
+                      int64_t n, int bands, int rows, const float *params, int hidden, float *fused, float *weights)
+{
+    const int cpl = (d / 4 + kTppF - 1) / kTppF;
+    SqProfScope prof(ctx, SUBQUAD_PROF_FUSE);
+#define SQ_FWDMC(C)                                                                                                \
+    fuse_forward_mc_kernel<M, WORDS, C><<<grid, kFuseThreads, 0, ctx->stream>>>(                                   \
+        pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d, sig, n, bands, rows, params, hidden, fused, weights)
+    if (cpl <= 1) SQ_FWDMC(1);
+    else if (cpl <= 2) SQ_FWDMC(2);
+    else if (cpl <= 4) SQ_FWDMC(4);
+    else if (cpl <= 8) SQ_FWDMC(8);
+    else if (cpl <= 16) SQ_FWDMC(16);
+    else if (cpl <= 32) SQ_FWDMC(32);
+    else SQ_FWDMC(64);
+#undef SQ_FWDMC
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
+}
+
+template <int M, int WORDS, int CPL>
+int launch_backward_mc_cpl(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                           const int32_t *self_scores, const void *packed, const float *emb, int d,
+                           const uint32_t *sig, int64_t n, int bands, int rows, const float *params, int hidden,
+                           const float *dL, float4 *coef, double *partials)
+{
+    const int hpl = (hidden + kTpp - 1) / kTpp;
+    const size_t smem = sizeof(double) * kGroups * McLayout(M, hidden).P;
+#define SQ_BWDMC(HH)                                                                                               \
+    do {                                                                                                           \
+        auto kern = fuse_backward_mc_kernel<M, WORDS, CPL, HH>;                                                    \
+        SQ_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));           \
+        kern<<<grid, kFuseThreads, smem, ctx->stream>>>(pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d,  \
+                                                        sig, n, bands, rows, params, hidden, dL, coef, partials);  \
+    } while (0)
+    if (hpl <= 1) SQ_BWDMC(1);
+    else if (hpl <= 2) SQ_BWDMC(2);
+    else SQ_BWDMC(4);
+#undef SQ_BWDMC
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
+}
+
+template <int M, int WORDS>
+int launch_backward_mc(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                       const int32_t *self_scores, const void *packed, const float *emb, int d, const uint32_t *sig,
+                       int64_t n, int bands, int rows, const float *params, int hidden, const float *dL, float4 *coef,
+                       double *partials)
+{
+    const int cpl = (d / 4 + kTpp - 1) / kTpp;
+#define SQ_BMC(C)                                                                                                  \
+    return launch_backward_mc_cpl<M, WORDS, C>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, sig, n, bands, \
+                                               rows, params, hidden, dL, coef, partials)
+    if (cpl <= 1) SQ_BMC(1);
+    if (cpl <= 2) SQ_BMC(2);
+    if (cpl <= 4) SQ_BMC(4);
+    if (cpl <= 8) SQ_BMC(8);
+    SQ_BMC(16);
+#undef SQ_BMC
+}
+
+int check_mc_args(int64_t m, int64_t n, int d, int hidden, int channels, int pack_stride, const uint32_t *sig,
+                  int bands, int rows)
+{
+    if (m < 0 || n < 0 || d < 4 || d > 1024 || d % 4 || hidden < 1 || hidden > kMaxHidden) return SUBQUAD_ERR_ARG;
+    if (channels != 2 && channels != 3) return SUBQUAD_ERR_ARG;
+    if (pack_stride != 16 && pack_stride != 32) return SUBQUAD_ERR_ARG;
+    if (channels == 3) {
+        if (!sig || bands < 1 || rows < 1 || rows > 8 || bands * rows > 512 || n < 1) return SUBQUAD_ERR_ARG;
+        if (rows == 4 && reinterpret_cast<uintptr_t>(sig) % 16) return SUBQUAD_ERR_ARG;
+        if (reinterpret_cast<uintptr_t>(sig) % 4) return SUBQUAD_ERR_ARG;
+    }
+    return SUBQUAD_OK;
+}
+
+}  // namespace
+
+extern "C" int subquad_fuse_forward_mc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                                       const int32_t *self_scores, const void *packed, int pack_stride,
+                                       const float *emb, int d, const uint32_t *sig, int64_t n, int bands, int rows,
+                                       const float *gate_params, int hidden, int channels, float *fused_out,
+                                       float *weights_out)
+{
+    SQ_ENTER(ctx);
+    SQ_TRY(check_mc_args(m, channels == 3 ? n : 0, d, hidden, channels, pack_stride, sig, bands, rows));
+    if (m == 0) return SUBQUAD_OK;
+    if (!pairs || !sw || !self_scores || !packed || !emb || !gate_params || !fused_out) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(emb) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8 ||
+        reinterpret_cast<uintptr_t>(packed) % 16)
+        return SUBQUAD_ERR_ARG;
+    const unsigned grid = sq_grid(ctx, (m + 7) / 8 * 32, kFuseThreads, 8);
+#define SQ_MCF(MM, W)                                                                                              \
+    return launch_forward_mc<MM, W>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, sig, n, bands, rows,      \
+                                    gate_params, hidden, fused_out, weights_out)
+    if (channels == 2) {
+        if (pack_stride == 16) SQ_MCF(2, 2);
+        SQ_MCF(2, 4);
+    }
+    if (pack_stride == 16) SQ_MCF(3, 2);
+    SQ_MCF(3, 4);
+#undef SQ_MCF
+}
+
+extern "C" int subquad_fuse_backward_mc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                                        const int32_t *self_scores, const void *packed, int pack_stride,
+                                        const float *emb, int64_t n, int d, const uint32_t *sig, int bands, int rows,
+                                        const float *gate_params, int hidden, int channels, const float *dL_dfused,
+                                        const uint32_t *perm_i, const uint32_t *off_i, const uint32_t *perm_j,
+                                        const uint32_t *off_j, float *grad_params, float *grad_emb)
+{
+    SQ_ENTER(ctx);
+    SQ_TRY(check_mc_args(m, n, d, hidden, channels, pack_stride, sig, bands, rows));
+    if (!grad_params || !gate_params) return SUBQUAD_ERR_ARG;
+    if (m > 0 && (!pairs || !sw || !self_scores || !packed || !emb || !dL_dfused)) return SUBQUAD_ERR_ARG;
+    if (grad_emb && (!perm_i || !off_i || !perm_j || !off_j || !emb)) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(emb) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8 ||
+        reinterpret_cast<uintptr_t>(packed) % 16 || reinterpret_cast<uintptr_t>(grad_emb) % 16)
+        return SUBQUAD_ERR_ARG;
+    const int P = McLayout(channels, hidden).P;
+    const unsigned grid = (unsigned)ctx->num_sms * 4;  // fixed: the reduction order does not depend on m
+    SqArena measure(nullptr);
+    measure.take<double>((size_t)grid * P);
+    if (grad_emb) measure.take<float4>((size_t)m);
+    SQ_TRY(sq_scratch_reserve(ctx, measure.off));
+    SqArena arena(ctx->scratch);
+    double *partials = arena.take<double>((size_t)grid * P);
+    float4 *coef = grad_emb ? arena.take<float4>((size_t)m) : nullptr;
+#define SQ_MCB(MM, W)                                                                                              \
+    SQ_TRY((launch_backward_mc<MM, W>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, sig, n, bands, rows,    \
+                                      gate_params, hidden, dL_dfused, coef, partials)))
+    if (channels == 2) {
+        if (pack_stride == 16) SQ_MCB(2, 2);
+        else SQ_MCB(2, 4);
+    } else {
+        if (pack_stride == 16) SQ_MCB(3, 2);
+        else SQ_MCB(3, 4);
+    }
+#undef SQ_MCB
+    reduce_partials_kernel<<<1, 352, 0, ctx->stream>>>(partials, (int)grid, P, grad_params);
+    SQ_LAUNCH_CHECK();
+    if (grad_emb && n > 0) {
+        const int cpl = (d / 4 + kTpp - 1) / kTpp;
+        const unsigned g2 = sq_grid(ctx, n * kTpp, kFuseThreads, 8);
+#define SQ_EMB(C)                                                                                                  \
+    emb_grad_kernel<C><<<g2, kFuseThreads, 0, ctx->stream>>>(pairs, coef, emb, n, d, perm_i, off_i, perm_j, off_j,  \
+                                                            grad_emb)
+        if (cpl <= 1) SQ_EMB(1);
+        else if (cpl <= 2) SQ_EMB(2);
+        else if (cpl <= 4) SQ_EMB(4);
+        else if (cpl <= 8) SQ_EMB(8);
+        else SQ_EMB(16);
+#undef SQ_EMB
+        SQ_LAUNCH_CHECK();
+    }
+    return SUBQUAD_OK;
+}

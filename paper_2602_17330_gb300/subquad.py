@@ -87,6 +87,10 @@ SIGNATURES = {
                                          _P, _P, _P, _P, _P, _P]),
     "subquad_fuse_backward_params_noalloc": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P,
                                                         _c.c_int, _P, _P]),
+    "subquad_fuse_forward_mc": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P, _I64, _c.c_int,
+                                           _c.c_int, _P, _c.c_int, _c.c_int, _P, _P]),
+    "subquad_fuse_backward_mc": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _I64, _c.c_int, _P, _c.c_int,
+                                            _c.c_int, _P, _c.c_int, _c.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "subquad_adam_step": (_c.c_int, [_P, _P, _P, _P, _P, _I64, _c.c_int, _c.c_float, _c.c_float, _c.c_float,
                                      _c.c_float]),
 }
@@ -438,6 +442,42 @@ class Context:
             int(emb.shape[1]), _ptr(params), hidden, _ptr(dL), _ptr(out)), "subquad_fuse_backward_params_noalloc")
         return out
 
+    def fuse_forward_mc(self, pairs, sw, self_sc, packed, emb, sig, params, hidden: int, channels: int,
+                        want_weights: bool = False, out=None):
+        """M-channel fusion (channels 2 or 3); sig is the int32 [bands, n, rows]
+        tensor of sign() (unused for 2 channels)."""
+        torch = self.torch
+        m = int(pairs.shape[0])
+        emb = self._dev(emb, torch.float32)
+        params = self._dev(params, torch.float32)
+        out = self._empty((m,), torch.float32) if out is None else out
+        w = self._empty((m, channels), torch.float32) if want_weights else None
+        bands, n, rows = (int(x) for x in sig.shape) if sig is not None else (0, int(emb.shape[0]), 0)
+        _check(lib().subquad_fuse_forward_mc(self.handle, _ptr(pairs), m, _ptr(sw), _ptr(self_sc), _ptr(packed),
+                                             int(packed.shape[1]), _ptr(emb), int(emb.shape[1]), _ptr(sig), n, bands,
+                                             rows, _ptr(params), hidden, channels, _ptr(out), _ptr(w)),
+               "subquad_fuse_forward_mc")
+        return (out, w) if want_weights else out
+
+    def fuse_backward_mc(self, pairs, sw, self_sc, packed, emb, sig, params, hidden: int, channels: int, dL,
+                         index=None, grad_params=None, grad_emb=None, want_emb: bool = True):
+        torch = self.torch
+        m = int(pairs.shape[0])
+        n, d = int(emb.shape[0]), int(emb.shape[1])
+        grad_params = torch.empty_like(params) if grad_params is None else grad_params
+        if want_emb:
+            if index is None:
+                index = self.pair_index(pairs, n)
+            grad_emb = self._empty((n, d), torch.float32) if grad_emb is None else grad_emb
+        ix = index or {}
+        bands, rows = (int(sig.shape[0]), int(sig.shape[2])) if sig is not None else (0, 0)
+        _check(lib().subquad_fuse_backward_mc(
+            self.handle, _ptr(pairs), m, _ptr(sw), _ptr(self_sc), _ptr(packed), int(packed.shape[1]), _ptr(emb), n, d,
+            _ptr(sig), bands, rows, _ptr(params), hidden, channels, _ptr(dL), _ptr(ix.get("perm_i")),
+            _ptr(ix.get("off_i")), _ptr(ix.get("perm_j")), _ptr(ix.get("off_j")), _ptr(grad_params),
+            _ptr(grad_emb) if want_emb else None), "subquad_fuse_backward_mc")
+        return (grad_params, grad_emb) if want_emb else grad_params
+
     def adam_step(self, param, grad, m1, m2, t: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
                   eps: float = 1e-8):
         _check(lib().subquad_adam_step(self.handle, _ptr(param), _ptr(grad), _ptr(m1), _ptr(m2), int(param.numel()),
@@ -499,6 +539,14 @@ def subquad_fuse_backward(ctx: Context, *a, **k):
 
 def subquad_fuse_backward_params_noalloc(ctx: Context, *a, **k):
     return ctx.fuse_backward_params_noalloc(*a, **k)
+
+
+def subquad_fuse_forward_mc(ctx: Context, *a, **k):
+    return ctx.fuse_forward_mc(*a, **k)
+
+
+def subquad_fuse_backward_mc(ctx: Context, *a, **k):
+    return ctx.fuse_backward_mc(*a, **k)
 
 
 def subquad_adam_step(ctx: Context, *a, **k):

@@ -149,3 +149,17 @@ def test_backward_matches_central_differences(oracle_mod, small, M):
         num = (loss_of(oracle_mod, d, params, up, y, w, h, M) - loss_of(oracle_mod, d, params, dn, y, w, h, M)) / (
             float(up[i, c]) - float(dn[i, c]))
         assert abs(num - ge[i, c]) <= 1e-4 * abs(ge[i, c]) + 1e-9, (i, c, num, ge[i, c])
+
+
+def test_mc_rounding_scale_bounds_the_gradient(oracle_mod, small):
+    """The M-channel rounding scale bounds every gradient entry (each pair
+    term is bounded by its operand-magnitude evaluation)."""
+    d = small
+    h = 6
+    for M in (2, 3):
+        params = synth.gate_parameters_mc(h, M, seed=6)
+        dL = np.random.default_rng(6).standard_normal(d["C"].shape[0])
+        args = (d["C"], d["sw"], d["self"], d["rep"].lens, d["emb"], d["sig"], params, h, M, dL)
+        gp, ge = oracle_mod.fuse_backward_mc(*args)
+        sc, se = oracle_mod.fuse_backward_mc_scale(*args)
+        assert (np.abs(gp) <= sc * (1 + 1e-12)).all() and (np.abs(ge) <= se * (1 + 1e-12) + 1e-300).all()
