@@ -80,6 +80,12 @@ def _load():
     lib.oracle_fuse_backward_mc_scale.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, opt_f64, c.c_int,
                                                   F32P, c.c_int, c.c_int, F64P, F64P, opt_f64]
     lib.oracle_fuse_backward_mc_scale.restype = c.c_int
+    lib.oracle_edit.argtypes = [U8P, c.c_int, U8P, c.c_int, c.c_int, U8P]
+    lib.oracle_edit.restype = c.c_int32
+    lib.oracle_edit_pairs.argtypes = [U8P, c.c_int, U8P, U32P, c.c_int64, c.c_int, U8P, I32P]
+    lib.oracle_edit_pairs.restype = None
+    lib.oracle_default_edit_costs.argtypes = [U8P]
+    lib.oracle_default_edit_costs.restype = None
     lib.oracle_pair_labels.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, I32P]
     lib.oracle_pair_labels.restype = None
     lib.oracle_pair_weights.argtypes = [I32P, c.c_int64, c.c_int, F64P]
@@ -193,6 +199,34 @@ def self_scores(codes, lens, gap_open: int = 10, gap_extend: int = 1, matrix=Non
     n = _c(lens, np.uint8).shape[0]
     idx = np.arange(n, dtype=np.uint32)
     return sw_pairs(codes, lens, np.stack([idx, idx], axis=1), gap_open, gap_extend, matrix)
+
+
+# --------------------------------------------------------------------------
+# Edit distance (the GPU appendix's edit-distance kernel)
+# --------------------------------------------------------------------------
+
+def default_edit_costs() -> np.ndarray:
+    """uint8 [20, 20]: 0 on the diagonal, 1 where BLOSUM62 > 0, else 2."""
+    out = np.zeros(400, dtype=np.uint8)
+    _load().oracle_default_edit_costs(out)
+    return out.reshape(20, 20)
+
+
+def edit(a_codes, b_codes, indel: int = 2, sub=None) -> int:
+    S = default_edit_costs() if sub is None else _c(sub, np.uint8)
+    a = _c(a_codes, np.uint8)
+    b = _c(b_codes, np.uint8)
+    return int(_load().oracle_edit(a, a.shape[0], b, b.shape[0], indel, _c(S.reshape(-1), np.uint8)))
+
+
+def edit_pairs(codes, lens, pairs, indel: int = 2, sub=None) -> np.ndarray:
+    codes = _c(codes, np.uint8)
+    lens = _c(lens, np.uint8)
+    p = _pairs(pairs)
+    S = default_edit_costs() if sub is None else _c(sub, np.uint8)
+    out = np.zeros(p.shape[0], dtype=np.int32)
+    _load().oracle_edit_pairs(codes, codes.shape[1], lens, p, p.shape[0], indel, _c(S.reshape(-1), np.uint8), out)
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -261,6 +261,60 @@ void oracle_sw_pairs(const uint8_t *codes, int code_stride, const uint8_t *lens,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Edit distance (the GPU appendix's edit-distance kernel, Eq. d_{x,y}):
+ *   d(x, y) = min( d(x-1, y) + del, d(x, y-1) + ins,
+ *                  d(x-1, y-1) + [a_x != b_y] sub(a_x, b_y) ),
+ * d(0, 0) = 0, d(x, 0) = x del, d(0, y) = y ins; the distance is d(La, Lb).
+ * Reading: insertion and deletion cost the same `indel`; the substitution cost
+ * is a caller-supplied 20 x 20 table (zero on the diagonal); the default
+ * "biochemical similarity" costs, in half units with indel = 2, are 1 for a
+ * conservative substitution (BLOSUM62 entry > 0) and 2 otherwise -- so in the
+ * paper's units an indel costs 1, a dissimilar substitution 1 and a similar
+ * one 1/2.
+ * Pins: hand-worked distances (tests/golden), brute-force enumeration of edit
+ * scripts on short strings, Hamming distance when indels are prohibitive,
+ * indel (La + Lb - 2 LCS) when substitutions are, metric axioms.           */
+/* ------------------------------------------------------------------------- */
+#define ED_MAXL 64
+
+int32_t oracle_edit(const uint8_t *a, int La, const uint8_t *b, int Lb, int indel, const uint8_t *sub /* [20][20] */)
+{
+    int32_t D[ED_MAXL + 1][ED_MAXL + 1];
+    if (La < 0 || Lb < 0 || La > ED_MAXL || Lb > ED_MAXL) return -1;
+    for (int x = 0; x <= La; ++x) D[x][0] = x * indel;
+    for (int y = 0; y <= Lb; ++y) D[0][y] = y * indel;
+    for (int x = 1; x <= La; ++x)
+        for (int y = 1; y <= Lb; ++y) {
+            int32_t best = D[x - 1][y] + indel;                         /* delete a_x */
+            if (D[x][y - 1] + indel < best) best = D[x][y - 1] + indel; /* insert b_y */
+            int32_t diag = D[x - 1][y - 1] + (a[x - 1] != b[y - 1] ? (int32_t)sub[20 * a[x - 1] + b[y - 1]] : 0);
+            if (diag < best) best = diag;
+            D[x][y] = best;
+        }
+    return D[La][Lb];
+}
+
+void oracle_edit_pairs(const uint8_t *codes, int code_stride, const uint8_t *lens, const uint32_t *pairs, int64_t m,
+                       int indel, const uint8_t *sub, int32_t *dist)
+{
+    for (int64_t p = 0; p < m; ++p) {
+        uint32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+        dist[p] = oracle_edit(codes + (int64_t)i * code_stride, lens[i], codes + (int64_t)j * code_stride, lens[j],
+                              indel, sub);
+    }
+}
+
+/* The default substitution costs above (half units): 0 on the diagonal, 1
+ * where BLOSUM62 > 0, 2 elsewhere.                                          */
+void oracle_default_edit_costs(uint8_t *out /* [20][20] */)
+{
+    int32_t M[400];
+    oracle_blosum62(M);
+    for (int a = 0; a < 20; ++a)
+        for (int b = 0; b < 20; ++b) out[20 * a + b] = (uint8_t)(a == b ? 0 : (M[20 * a + b] > 0 ? 1 : 2));
+}
+
+/* ------------------------------------------------------------------------- */
 /* Per-pair gated fusion (Eq. alpha, Eq. wm, Eq. afused) with M = 2 channels:
  * a^(1) = s = S_ij / sqrt(S_ii S_jj) (normalised alignment, reading: geometric
  * mean of self-scores), a^(2) = c' = (1 + c)/2 with c the embedding cosine
