@@ -35,6 +35,9 @@ UNIT = "pairs/s"
 # Smith-Waterman algorithmic int32 operations per DP cell: H-diagonal + score,
 # max3-with-0, H - open, E add-max, F add-max, running best max.
 SW_OPS_PER_CELL = 6
+# Edit-distance algorithmic int32 operations per DP cell: diagonal + substitution,
+# left + insertion and its min, up + deletion and its min.
+ED_OPS_PER_CELL = 5
 # The integer roof: 128 integer lane operations per SM per clock (the issue
 # width of an sm_103a SM) x SM count x max SM clock, the last two read from the
 # device at run time.  profiles/int_issue_peak.json holds the measured rates
@@ -420,6 +423,19 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 times.append((e0, e1))
             stream.synchronize()
             sw_ms["binned" if binned else "plain"] = statistics.mean(a.elapsed_time(b) for a, b in times)
+        # edit distance (the paper's own DP) on the same pairs, same scheduler
+        ctx.set_edit_costs()
+        ed_out = torch.empty((m,), dtype=torch.int32, device=dev)
+        times = []
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.edit_distance(out["packed"], out["pairs"], out=ed_out)
+            e1.record(stream)
+            times.append((e0, e1))
+        stream.synchronize()
+        sw_ms["edit"] = statistics.mean(a.elapsed_time(b) for a, b in times)
 
     stream_res = train_res = topk_res = None
     if rank == 0 and world == 1:
@@ -515,6 +531,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "sw_gcups": gcups, "sw_frac_of_int_peak": gcups * SW_OPS_PER_CELL / alu_peak,
             "sw_gcups_plain": cells / (sw_ms["plain"] / 1e3) / 1e9,
             "sw_gcups_binned": cells / (sw_ms["binned"] / 1e3) / 1e9,
+            "edit": {"gcups": cells / (sw_ms["edit"] / 1e3) / 1e9, "ms": sw_ms["edit"],
+                     "frac_of_int_peak": cells * ED_OPS_PER_CELL / (sw_ms["edit"] / 1e3) / 1e9 / alu_peak,
+                     "note": f"edit distance of every candidate pair (length binning + edit_binned_kernel), "
+                             f"{ED_OPS_PER_CELL} int32 ops per DP cell, default biochemical costs"},
             "stages_ms": stage_ms, "kernel_rooflines": stage_roof, "wall_s": wall, "autotune": tuning["choice"],
             "timed_mode": timed_mode, "eager": eager, "train": train_res, "topk": topk_res, "stream": stream_res,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,

@@ -106,7 +106,8 @@ enum {
     SUBQUAD_PROF_ALIGN_BIN = 7,     /* length binning of the work list */
     SUBQUAD_PROF_SELF = 8,          /* self-score alignment kernel */
     SUBQUAD_PROF_FUSE = 9,          /* fuse_forward_kernel */
-    SUBQUAD_PROF_COUNT = 10
+    SUBQUAD_PROF_EDIT = 10,         /* edit_binned_kernel */
+    SUBQUAD_PROF_COUNT = 11
 };
 int subquad_profile_enable(subquad_ctx *ctx, int on);
 int subquad_profile_reset(subquad_ctx *ctx);
@@ -257,6 +258,40 @@ int subquad_self_scores_binned(subquad_ctx *ctx, const void *packed, int pack_st
 int subquad_align_score_binned_async(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs,
                                      const uint64_t *d_m, int64_t m_max, int gap_open, int gap_extend,
                                      int32_t *scores_out);
+
+/* ------------------------------------------------------------------------ */
+/* Edit distance -- the paper's own GPU similarity kernel (GPU appendix,     */
+/* edit-distance recurrence), a second alignment mode on the length-binned    */
+/* scheduler.                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Host-only, needs no GPU: the default substitution costs, uint8 [20][20] in
+ * code order, in half units (with the default indel cost 2): 0 on the
+ * diagonal, 1 for a conservative substitution (BLOSUM62 entry > 0), 2
+ * otherwise -- the reading of "substitution costs based on biochemical
+ * similarity" with insertion and deletion costing one unit. */
+int subquad_default_edit_costs(uint8_t *out);
+
+/* Costs of later subquad_edit_distance calls: indel (0..255) for an
+ * insertion or a deletion, sub (host uint8 [20][20], symmetric, zero on the
+ * diagonal; NULL = the defaults) for a substitution.  A new context starts
+ * with indel 2 and the defaults.  Host-only; the device table is rebuilt on
+ * the next call (which then synchronises the stream once). */
+int subquad_set_edit_costs(subquad_ctx *ctx, int indel, const uint8_t *sub);
+
+/* dist_out[p] = D(La, Lb) for pairs[p] = (a, b) under
+ *   D(x, y) = min(D(x-1, y) + indel, D(x, y-1) + indel,
+ *                 D(x-1, y-1) + sub(a_x, b_y)),  D(x, 0) = x indel, D(0, y) = y indel,
+ * the context's costs.  packed: device records; pairs: device uint32 [m][2];
+ * dist_out: device int32 [m].  Pairs are binned by length into a work list
+ * in context scratch (as subquad_align_score_binned). */
+int subquad_edit_distance(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs, int64_t m,
+                          int32_t *dist_out);
+
+/* subquad_edit_distance for a pair count held on the device (*d_m, at most
+ * m_max pairs): the graph-capturable form. */
+int subquad_edit_distance_async(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs,
+                                const uint64_t *d_m, int64_t m_max, int32_t *dist_out);
 
 /* ------------------------------------------------------------------------ */
 /* (a4) Per-pair gated fusion -- Eq. alpha, Eq. wm and Eq. afused with two   */

@@ -641,9 +641,12 @@ __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::b
     }
 }
 
+// Length-binned work list of m items in context scratch: *order_out lists the
+// item indices grouped by (query length, target length) bin.  The bins are
+// the scheduler shared by the batched alignment and edit-distance kernels.
 template <bool SELF>
-int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs, int64_t m, int o,
-                  int e, int32_t *out, const unsigned long long *d_m = nullptr)
+int build_work_list(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs, int64_t m,
+                    const unsigned long long *d_m, bool symmetric, uint32_t **order_out)
 {
     if (m >= (int64_t(1) << 32)) return SUBQUAD_ERR_ARG;
     SqArena measure(nullptr);
@@ -660,15 +663,25 @@ int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const u
     const unsigned g = sq_grid(ctx, m, 256, 8);
     const uint64_t *pk = static_cast<const uint64_t *>(packed);
     if (pack_stride == 16)
-        bin_count_kernel<2, SELF><<<g, 256, 0, ctx->stream>>>(pk, pairs, m, d_m, ctx->matrix_symmetric, bin_of, counts);
+        bin_count_kernel<2, SELF><<<g, 256, 0, ctx->stream>>>(pk, pairs, m, d_m, symmetric, bin_of, counts);
     else
-        bin_count_kernel<4, SELF><<<g, 256, 0, ctx->stream>>>(pk, pairs, m, d_m, ctx->matrix_symmetric, bin_of, counts);
+        bin_count_kernel<4, SELF><<<g, 256, 0, ctx->stream>>>(pk, pairs, m, d_m, symmetric, bin_of, counts);
     SQ_LAUNCH_CHECK();
     bin_offsets_kernel<<<1, kBins, 0, ctx->stream>>>(counts);
     SQ_LAUNCH_CHECK();
     bin_scatter_kernel<<<g, 256, 0, ctx->stream>>>(bin_of, m, d_m, counts, order);
     SQ_LAUNCH_CHECK();
-    prof_bin.finish();
+    *order_out = order;
+    return SUBQUAD_OK;
+}
+
+template <bool SELF>
+int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs, int64_t m, int o,
+                  int e, int32_t *out, const unsigned long long *d_m = nullptr)
+{
+    uint32_t *order = nullptr;
+    SQ_TRY(build_work_list<SELF>(ctx, packed, pack_stride, pairs, m, d_m, ctx->matrix_symmetric, &order));
+    const uint64_t *pk = static_cast<const uint64_t *>(packed);
     SqProfScope prof(ctx, SELF ? SUBQUAD_PROF_SELF : SUBQUAD_PROF_ALIGN);
 #define SQ_BINNED(W, C)                                                                                            \
     do {                                                                                                           \
@@ -828,4 +841,242 @@ extern "C" int subquad_align_score_binned_async(subquad_ctx *ctx, const void *pa
     SQ_TRY(ensure_table(ctx, gap_open));
     return launch_binned<false>(ctx, packed, pack_stride, pairs, m_max, gap_open, gap_extend, scores_out,
                                 reinterpret_cast<const unsigned long long *>(d_m));
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Edit distance (the GPU appendix's edit-distance recurrence) as a second
+// alignment mode on the same length-binned scheduler:
+//   D(x, y) = min(D(x-1, y) + indel, D(x, y-1) + indel,
+//                 D(x-1, y-1) + sub(a_x, b_y)),   D(x, 0) = x indel,
+//   D(0, y) = y indel,  distance = D(La, Lb),
+// with the context's costs (sub symmetric, zero on the diagonal).  Two pairs
+// per thread in packed 16-bit halves, the shorter sequence unrolled down the
+// rows at the warp's common height, the longer streamed through the columns.
+// Rows below a pair's query and columns right of its target are made
+// transparent: a move down into a padding row and a move right into a padding
+// column cost 0, and the padding residue's substitution cost is indel against
+// a real residue and 0 against itself; every path to the bottom-right corner
+// of the padded grid then costs at least D(La, Lb) and one costs exactly that,
+// so the corner holds the distance.  Per cell (DPX):
+//   t = D(x-1, y-1) + sub;  m = min(D(x, y-1) + h_y, t);  D = min(D(x-1, y) + v_x, m).
+// Every value is at most 60 x 255 < 2^15, so 16-bit lanes are exact.
+// ---------------------------------------------------------------------------
+constexpr int kEdRows = 21;  // 20 residues + the padding residue
+constexpr int kEdWords = kEdRows * kEdRows * kLanes;
+
+int ensure_edit_table(subquad_ctx *ctx)
+{
+    if (ctx->d_edit_table && ctx->edit_table_valid) return SUBQUAD_OK;
+    static thread_local uint32_t host[kEdWords];
+    for (int a = 0; a < kEdRows; ++a)
+        for (int b = 0; b < kEdRows; ++b) {
+            uint32_t v;
+            if (a < 20 && b < 20) v = ctx->h_edit_sub[20 * a + b];
+            else if (a == 20 && b == 20) v = 0;
+            else v = (uint32_t)ctx->edit_indel;
+            for (int l = 0; l < kLanes; ++l) host[(a * kEdRows + b) * kLanes + l] = v * 0x10001u;
+        }
+    if (!ctx->d_edit_table) SQ_TRY_CUDA(cudaMalloc(&ctx->d_edit_table, sizeof(uint32_t) * kEdWords));
+    SQ_TRY_CUDA(cudaStreamSynchronize(ctx->stream));  // earlier work may still read the old table
+    SQ_TRY_CUDA(cudaMemcpy(ctx->d_edit_table, host, sizeof(uint32_t) * kEdWords, cudaMemcpyHostToDevice));
+    ctx->edit_table_valid = true;
+    return SUBQUAD_OK;
+}
+
+template <int WORDS, int NQ>
+__device__ __forceinline__ uint32_t ed_pair2(const Rec<WORDS> &qP, int LqP, const Rec<WORDS> &tP, int LtP,
+                                             const Rec<WORDS> &qQ, int LqQ, const Rec<WORDS> &tQ, int LtQ,
+                                             const char *__restrict__ s_tab, int lane, int indel)
+{
+    uint32_t qoffP[NQ], qoffQ[NQ], D[NQ], vc[NQ];
+    uint32_t acc = 0u;
+#pragma unroll
+    for (int p = 0; p < NQ; ++p) {
+        uint32_t cp = (uint32_t)(qP.w[p / 12] >> (5 * (p % 12))) & 31u;
+        uint32_t cq = (uint32_t)(qQ.w[p / 12] >> (5 * (p % 12))) & 31u;
+        cp = p < LqP ? min(cp, 19u) : 20u;
+        cq = p < LqQ ? min(cq, 19u) : 20u;
+        qoffP[p] = (cp * kEdRows * kLanes + (uint32_t)lane) * 4u;
+        qoffQ[p] = (cq * kEdRows * kLanes + (uint32_t)lane) * 4u;
+        vc[p] = pack2(p < LqP ? indel : 0, p < LqQ ? indel : 0);
+        acc = __vadd2(acc, vc[p]);
+        D[p] = acc;  // D(p + 1, 0)
+    }
+    TargetStream<WORDS> sP(tP), sQ(tQ);
+    const int Lt = max(LtP, LtQ);
+    uint32_t top = 0u;  // D(0, y)
+    for (int j = 0; j < Lt; ++j) {
+        const uint32_t aP = sP.next(), aQ = sQ.next();
+        const char *colP = s_tab + (j < LtP ? aP : 20u) * (kLanes * 4);
+        const char *colQ = s_tab + (j < LtQ ? aQ : 20u) * (kLanes * 4);
+        const uint32_t hc = pack2(j < LtP ? indel : 0, j < LtQ ? indel : 0);
+        uint32_t diag = top;
+        top = __vadd2(top, hc);
+        uint32_t up = top;
+#pragma unroll
+        for (int p = 0; p < NQ; ++p) {
+            const uint32_t lo = *reinterpret_cast<const uint32_t *>(colP + qoffP[p]);
+            const uint32_t hi = *reinterpret_cast<const uint32_t *>(colQ + qoffQ[p]);
+            const uint32_t sub = (lo & 0x0000ffffu) | (hi & 0xffff0000u);
+            const uint32_t t = __vadd2(diag, sub);
+            const uint32_t mleft = __viaddmin_s16x2(D[p], hc, t);
+            const uint32_t d = __viaddmin_s16x2(up, vc[p], mleft);
+            diag = D[p];
+            D[p] = d;
+            up = d;
+        }
+    }
+    return NQ > 0 ? D[NQ - 1] : top;
+}
+
+template <int WORDS, int CFG>
+__global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::blocks)
+    edit_binned_kernel(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs,
+                       const uint32_t *__restrict__ order, int64_t m_max, const unsigned long long *__restrict__ d_m,
+                       const uint32_t *__restrict__ table, int indel, int32_t *__restrict__ out)
+{
+    extern __shared__ int32_t s_tab_words[];
+    const int64_t m = items(m_max, d_m);
+    for (int q = threadIdx.x; q < kEdWords / 4; q += blockDim.x)
+        reinterpret_cast<int4 *>(s_tab_words)[q] = reinterpret_cast<const int4 *>(table)[q];
+    __syncthreads();
+    const char *s_tab = reinterpret_cast<const char *>(s_tab_words);
+    constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t stride = nwarps * 64;
+    // the record double buffer of the batched alignment kernel (see there)
+    Rec<WORDS> *buf = reinterpret_cast<Rec<WORDS> *>(s_tab_words + kEdWords) + threadIdx.x * 8;
+    auto issue = [&](int slot, uint4 idP, uint4 idQ) {
+        Rec<WORDS> *dst = buf + slot * 4;
+        if (idP.w) {
+#pragma unroll
+            for (int c = 0; c < WORDS / 2; ++c) {
+                cp_async16(reinterpret_cast<char *>(dst + 0) + 16 * c, packed + (int64_t)idP.x * WORDS + 2 * c);
+                cp_async16(reinterpret_cast<char *>(dst + 1) + 16 * c, packed + (int64_t)idP.y * WORDS + 2 * c);
+            }
+        }
+        if (idQ.w) {
+#pragma unroll
+            for (int c = 0; c < WORDS / 2; ++c) {
+                cp_async16(reinterpret_cast<char *>(dst + 2) + 16 * c, packed + (int64_t)idQ.x * WORDS + 2 * c);
+                cp_async16(reinterpret_cast<char *>(dst + 3) + 16 * c, packed + (int64_t)idQ.y * WORDS + 2 * c);
+            }
+        }
+        cp_async_commit();
+    };
+    int64_t base = warp * 64;
+    uint4 curP = entry_ids<false>(order, pairs, base + lane, m), curQ = entry_ids<false>(order, pairs, base + 32 + lane, m);
+    issue(0, curP, curQ);
+    uint4 nxtP = entry_ids<false>(order, pairs, base + stride + lane, m);
+    uint4 nxtQ = entry_ids<false>(order, pairs, base + stride + 32 + lane, m);
+    for (int k = 0; base < m; ++k, base += stride) {
+        issue((k + 1) & 1, nxtP, nxtQ);
+        const uint4 farP = entry_ids<false>(order, pairs, base + 2 * stride + lane, m);
+        const uint4 farQ = entry_ids<false>(order, pairs, base + 2 * stride + 32 + lane, m);
+        cp_async_wait1();
+        const bool vP = curP.w != 0, vQ = curQ.w != 0;
+        const Rec<WORDS> *r = buf + (k & 1) * 4;
+        Rec<WORDS> AP, BP, AQ, BQ;
+        int LaP = 0, LbP = 0, LaQ = 0, LbQ = 0;
+        if (vP) {
+            AP = r[0];
+            BP = r[1];
+            orient<WORDS>(AP, LaP, BP, LbP, true);
+        } else {
+#pragma unroll
+            for (int w = 0; w < WORDS; ++w) AP.w[w] = BP.w[w] = 0;
+        }
+        if (vQ) {
+            AQ = r[2];
+            BQ = r[3];
+            orient<WORDS>(AQ, LaQ, BQ, LbQ, true);
+        } else {
+            AQ = AP;
+            BQ = BP;
+            LaQ = LaP;
+            LbQ = LbP;
+        }
+        const int wmax = __reduce_max_sync(0xffffffffu, max(LaP, LaQ));
+        if (vP) {
+            uint32_t dist;
+            switch ((wmax + 1) >> 1) {
+#define SQ_ED(H)                                                                                                   \
+    case H:                                                                                                        \
+        dist = ed_pair2<WORDS, (H < 1 ? 2 : (2 * H <= MAXLEN ? 2 * H : MAXLEN))>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, \
+                                                                                s_tab, lane, indel);               \
+        break;
+                SQ_ED(0) SQ_ED(1) SQ_ED(2) SQ_ED(3) SQ_ED(4) SQ_ED(5) SQ_ED(6) SQ_ED(7) SQ_ED(8) SQ_ED(9) SQ_ED(10)
+                SQ_ED(11) SQ_ED(12)
+#undef SQ_ED
+            default:
+                dist = ed_pair2<WORDS, MAXLEN>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, indel);
+                break;
+            }
+            out[curP.z] = (int32_t)(dist & 0xffffu);
+            if (vQ) out[curQ.z] = (int32_t)(dist >> 16);
+        }
+        curP = nxtP;
+        curQ = nxtQ;
+        nxtP = farP;
+        nxtQ = farQ;
+    }
+}
+
+int launch_edit(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs, int64_t m,
+                int32_t *out, const unsigned long long *d_m)
+{
+    SQ_TRY(ensure_edit_table(ctx));
+    uint32_t *order = nullptr;
+    SQ_TRY(build_work_list<false>(ctx, packed, pack_stride, pairs, m, d_m, true, &order));
+    const uint64_t *pk = static_cast<const uint64_t *>(packed);
+    SqProfScope prof(ctx, SUBQUAD_PROF_EDIT);
+#define SQ_EDL(W, C)                                                                                               \
+    do {                                                                                                           \
+        auto k = edit_binned_kernel<W, C>;                                                                         \
+        const size_t smem = sizeof(uint32_t) * kEdWords + sizeof(uint64_t) * W * 8 * BinnedShape<C>::threads;      \
+        SQ_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));             \
+        const unsigned grid = sq_grid(ctx, (m + 1) / 2, BinnedShape<C>::threads, BinnedShape<C>::blocks);         \
+        k<<<grid, BinnedShape<C>::threads, smem, ctx->stream>>>(pk, pairs, order, m, d_m, ctx->d_edit_table,       \
+                                                               ctx->edit_indel, out);                             \
+    } while (0)
+    const int cfg = ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE];
+    if (pack_stride == 16) {
+        if (cfg == 0) SQ_EDL(2, 0);
+        else SQ_EDL(2, 1);
+    } else {
+        if (cfg == 0) SQ_EDL(4, 0);
+        else SQ_EDL(4, 1);
+    }
+#undef SQ_EDL
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
+}
+
+}  // namespace
+
+extern "C" int subquad_edit_distance(subquad_ctx *ctx, const void *packed, int pack_stride, const uint32_t *pairs,
+                                     int64_t m, int32_t *dist_out)
+{
+    SQ_ENTER(ctx);
+    if (m < 0 || (pack_stride != 16 && pack_stride != 32)) return SUBQUAD_ERR_ARG;
+    if (m == 0) return SUBQUAD_OK;
+    if (!packed || !pairs || !dist_out) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(packed) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8) return SUBQUAD_ERR_ARG;
+    return launch_edit(ctx, packed, pack_stride, pairs, m, dist_out, nullptr);
+}
+
+extern "C" int subquad_edit_distance_async(subquad_ctx *ctx, const void *packed, int pack_stride,
+                                           const uint32_t *pairs, const uint64_t *d_m, int64_t m_max,
+                                           int32_t *dist_out)
+{
+    SQ_ENTER(ctx);
+    if (!d_m || m_max < 0 || (pack_stride != 16 && pack_stride != 32)) return SUBQUAD_ERR_ARG;
+    if (m_max == 0) return SUBQUAD_OK;
+    if (!packed || !pairs || !dist_out) return SUBQUAD_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(packed) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8) return SUBQUAD_ERR_ARG;
+    return launch_edit(ctx, packed, pack_stride, pairs, m_max, dist_out, reinterpret_cast<const unsigned long long *>(d_m));
 }

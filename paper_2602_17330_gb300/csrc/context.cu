@@ -75,6 +75,8 @@ extern "C" int subquad_create(subquad_ctx **out, int device, void *cuda_stream)
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     memcpy(ctx->h_matrix, kBlosum62, sizeof(kBlosum62));
     sq_update_matrix_flags(ctx);
+    sq_default_edit_costs(ctx->h_edit_sub);
+    ctx->edit_indel = 2;
     for (int k = 0; k < SUBQUAD_TUNE_COUNT; ++k) ctx->tune[k] = 0;
     ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE] = 1;
     ctx->tune[SUBQUAD_TUNE_BAND_PART_LOG2] = 11;
@@ -165,6 +167,7 @@ extern "C" int subquad_destroy(subquad_ctx *ctx)
             ctx->prof_pool.clear();
             cudaFree(ctx->scratch);
             cudaFree(ctx->d_table);
+            cudaFree(ctx->d_edit_table);
             cudaFree(ctx->d_err);
             cudaFree(ctx->d_small);
             cudaFreeHost(ctx->h_pinned);
@@ -244,6 +247,37 @@ extern "C" int subquad_set_matrix(subquad_ctx *ctx, const int8_t *matrix)
     memcpy(ctx->h_matrix, src, 400);
     sq_update_matrix_flags(ctx);
     ctx->table_gap_open = -1;  // rebuild the device table on next use
+    return SUBQUAD_OK;
+}
+
+void sq_default_edit_costs(uint8_t *out)
+{
+    for (int a = 0; a < 20; ++a)
+        for (int b = 0; b < 20; ++b) out[20 * a + b] = (uint8_t)(a == b ? 0 : (kBlosum62[a][b] > 0 ? 1 : 2));
+}
+
+extern "C" int subquad_default_edit_costs(uint8_t *out)
+{
+    if (!out) return SUBQUAD_ERR_ARG;
+    sq_default_edit_costs(out);
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_set_edit_costs(subquad_ctx *ctx, int indel, const uint8_t *sub)
+{
+    SQ_ENTER(ctx);
+    if (indel < 0 || indel > 255) return SUBQUAD_ERR_ARG;
+    uint8_t costs[400];
+    if (sub) memcpy(costs, sub, 400);
+    else sq_default_edit_costs(costs);
+    for (int a = 0; a < 20; ++a) {
+        if (costs[21 * a] != 0) return SUBQUAD_ERR_ARG;
+        for (int b = 0; b < 20; ++b)
+            if (costs[20 * a + b] != costs[20 * b + a]) return SUBQUAD_ERR_ARG;
+    }
+    memcpy(ctx->h_edit_sub, costs, 400);
+    ctx->edit_indel = indel;
+    ctx->edit_table_valid = false;
     return SUBQUAD_OK;
 }
 

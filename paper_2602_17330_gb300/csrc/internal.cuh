@@ -36,6 +36,12 @@ struct subquad_ctx {
     bool self_is_diagonal = true;
     int32_t *d_table = nullptr;  // lane-replicated alignment table (see align.cu)
     int table_gap_open = -1;     // gap-open folded into d_table (-1: not built)
+    // edit-distance costs (subquad_set_edit_costs) and their lane-replicated
+    // device table (built on first use after a change)
+    uint8_t h_edit_sub[400];
+    int edit_indel = 2;
+    uint32_t *d_edit_table = nullptr;
+    bool edit_table_valid = false;
     uint32_t *d_err = nullptr;   // sticky device error word
     uint64_t *h_pinned = nullptr;  // pinned host staging, 8 words
     uint64_t *d_small = nullptr;   // small device scalars (counters), 16 words
@@ -57,7 +63,8 @@ inline const char *sq_prof_name(int k)
     static const char *const names[SUBQUAD_PROF_COUNT] = {"subquad.sign", "subquad.band", "subquad.band_partition",
                                                           "subquad.band_group", "subquad.band_emit",
                                                           "subquad.band_pairsort", "subquad.align",
-                                                          "subquad.align_bin", "subquad.self", "subquad.fuse"};
+                                                          "subquad.align_bin", "subquad.self", "subquad.fuse",
+                                                          "subquad.edit"};
     return k >= 0 && k < SUBQUAD_PROF_COUNT ? names[k] : "subquad";
 }
 
@@ -189,4 +196,7 @@ size_t sq_radix_tmp_bytes(int64_t count);
 // Lane-replicated alignment score table for the context's matrix and gap_open
 // (align.cu); shared by the alignment and the brute-force retrieval kernels.
 void sq_update_matrix_flags(subquad_ctx *ctx);
+// Default edit-distance substitution costs from the built-in BLOSUM62 (half
+// units): 0 on the diagonal, 1 where the score is positive, else 2.
+void sq_default_edit_costs(uint8_t *out);
 int sq_ensure_align_table(subquad_ctx *ctx, int gap_open);

@@ -30,7 +30,7 @@ SUBQUAD_ERR_INPUT = -6
 SUBQUAD_ERR_INTERNAL = -7
 
 PROF_NAMES = ["sign", "band", "band_partition", "band_group", "band_emit", "band_pairsort", "align", "align_bin", "self",
-              "fuse"]
+              "fuse", "edit"]
 
 TUNE_ALIGN_SHAPE = 0
 TUNE_BAND_PART_LOG2 = 1
@@ -91,6 +91,10 @@ SIGNATURES = {
                                            _c.c_int, _P, _c.c_int, _c.c_int, _P, _P]),
     "subquad_fuse_backward_mc": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _I64, _c.c_int, _P, _c.c_int,
                                             _c.c_int, _P, _c.c_int, _c.c_int, _P, _P, _P, _P, _P, _P, _P]),
+    "subquad_default_edit_costs": (_c.c_int, [_P]),
+    "subquad_set_edit_costs": (_c.c_int, [_P, _c.c_int, _P]),
+    "subquad_edit_distance": (_c.c_int, [_P, _P, _c.c_int, _P, _I64, _P]),
+    "subquad_edit_distance_async": (_c.c_int, [_P, _P, _c.c_int, _P, _P, _I64, _P]),
     "subquad_adam_step": (_c.c_int, [_P, _P, _P, _P, _P, _I64, _c.c_int, _c.c_float, _c.c_float, _c.c_float,
                                      _c.c_float]),
 }
@@ -130,6 +134,14 @@ def default_matrix():
     """The library's built-in BLOSUM62 as a list of 400 ints (host-only)."""
     buf = (ctypes.c_int8 * 400)()
     _check(lib().subquad_default_matrix(ctypes.cast(buf, _P)), "subquad_default_matrix")
+    return list(buf)
+
+
+def default_edit_costs():
+    """The library's default edit-distance substitution costs (400 ints, half
+    units; host-only)."""
+    buf = (ctypes.c_uint8 * 400)()
+    _check(lib().subquad_default_edit_costs(ctypes.cast(buf, _P)), "subquad_default_edit_costs")
     return list(buf)
 
 
@@ -216,6 +228,13 @@ class Context:
             return
         buf = (ctypes.c_int8 * 400)(*[int(v) for v in list(matrix)])
         _check(lib().subquad_set_matrix(self.handle, ctypes.cast(buf, _P)), "subquad_set_matrix")
+
+    def set_edit_costs(self, indel: int = 2, sub=None):
+        buf = None
+        if sub is not None:
+            buf = (ctypes.c_uint8 * 400)(*[int(v) for v in list(sub)])
+        _check(lib().subquad_set_edit_costs(self.handle, indel, None if buf is None else ctypes.cast(buf, _P)),
+               "subquad_set_edit_costs")
 
     # -- helpers ---------------------------------------------------------------
     def _dev(self, t, dtype):
@@ -321,6 +340,20 @@ class Context:
         _check(getattr(lib(), name)(self.handle, _ptr(packed), int(packed.shape[1]), _ptr(pairs), m, gap_open,
                                     gap_extend, _ptr(out)), name)
         return out
+
+    def edit_distance(self, packed, pairs, out=None):
+        """subquad_edit_distance: int32 [m] distances under the context's costs."""
+        torch = self.torch
+        m = int(pairs.shape[0])
+        out = self._empty((m,), torch.int32) if out is None else out
+        _check(lib().subquad_edit_distance(self.handle, _ptr(packed), int(packed.shape[1]), _ptr(pairs), m, _ptr(out)),
+               "subquad_edit_distance")
+        return out
+
+    def edit_distance_async(self, packed, pairs, d_m, out):
+        _check(lib().subquad_edit_distance_async(self.handle, _ptr(packed), int(packed.shape[1]), _ptr(pairs),
+                                                 _ptr(d_m), int(pairs.shape[0]), _ptr(out)),
+               "subquad_edit_distance_async")
 
     def self_scores(self, packed, gap_open: int = 10, gap_extend: int = 1, out=None, binned: bool = False):
         torch = self.torch
@@ -547,6 +580,14 @@ def subquad_fuse_forward_mc(ctx: Context, *a, **k):
 
 def subquad_fuse_backward_mc(ctx: Context, *a, **k):
     return ctx.fuse_backward_mc(*a, **k)
+
+
+def subquad_edit_distance(ctx: Context, *a, **k):
+    return ctx.edit_distance(*a, **k)
+
+
+def subquad_edit_distance_async(ctx: Context, *a, **k):
+    return ctx.edit_distance_async(*a, **k)
 
 
 def subquad_adam_step(ctx: Context, *a, **k):

@@ -61,3 +61,10 @@ def test_create_without_gpu_fails_cleanly(libmod):
     h = ctypes.c_void_p()
     st = libmod.lib().subquad_create(ctypes.byref(h), 0, None)
     assert st != 0 and not h.value
+
+
+def test_default_edit_costs_match_oracle(libmod, oracle_mod):
+    """The library derives its default edit costs from its own BLOSUM62 table;
+    they must equal the oracle's, derived from the independently typed one."""
+    lib_costs = np.array(libmod.default_edit_costs(), dtype=np.uint8).reshape(20, 20)
+    assert (lib_costs == oracle_mod.default_edit_costs()).all()
