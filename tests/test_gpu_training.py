@@ -99,7 +99,7 @@ def grads_close(got, want, scale, what):
     floor = GRAD_KAPPA * scale
     bound = np.maximum(rel_bound, floor)
     ratio = err / np.maximum(bound, 1e-300)
-    checked_rel = rel_bound >= floor
+    checked_rel = (rel_bound >= floor) & (want != 0)
     worst_rel = float((err[checked_rel] / np.abs(want[checked_rel])).max()) if checked_rel.any() else 0.0
     print(f"\n{what}: worst err / (u scale) = {float((err / np.maximum(scale, 1e-300)).max()) / 2.0 ** -24:.3f}, "
           f"{int(checked_rel.sum())}/{err.size} entries at rel {GRAD_RTOL:g} (worst rel {worst_rel:.2e})")
