@@ -462,6 +462,64 @@ int subquad_fuse_backward_mc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m,
                              const uint32_t *off_i, const uint32_t *perm_j, const uint32_t *off_j, float *grad_params,
                              float *grad_emb);
 
+/* ------------------------------------------------------------------------ */
+/* Graph construction and RMT-based thresholding (the graph-construction     */
+/* section; Algorithm 1's graph step): A_ij = fused score on the candidate    */
+/* pairs, thresholded by its eigenvalue spectrum into the sparse graph G.     */
+/* ------------------------------------------------------------------------ */
+
+/* Connected components of the graph on n vertices whose edges are the pairs
+ * with weights[p] >= tau (compared in double precision).  labels_out (device
+ * uint32 [n]) receives each vertex's component label, the smallest vertex id
+ * of its component; sizes_out (device uint32 [n], nullable) receives at
+ * index v the size of the component labelled v (0 for non-labels).  pairs:
+ * device uint32 [m][2], ids < n < 2^31; weights: device float [m].  Also the
+ * clusters of the repertoire distance (subquad_cluster_js). */
+int subquad_graph_components(subquad_ctx *ctx, const uint32_t *pairs, const float *weights, int64_t m, int64_t n,
+                             double tau, uint32_t *labels_out, uint32_t *sizes_out);
+
+/* The threshold scan.  For each taus[t] (host, strictly increasing, in
+ * order): A_t keeps the entries >= taus[t]; it is block-diagonal over its
+ * components, so its spectrum is the union of the components' spectra
+ * (components of one vertex are left out).  When every component has at
+ * most s_max vertices (2 <= s_max <= 64) the spectrum is computed (FP64
+ * Jacobi per component), sorted, levels within 1e-9 of their predecessor are
+ * dropped as degenerate, and r_mean[t] = mean over consecutive spacings of
+ * min(d_k, d_{k+1}) / max(d_k, d_{k+1}) (num_ratios[t] terms, num_levels[t]
+ * levels).  The scan stops at the first t with max_comp[t] <= s_max and
+ * r_mean[t] <= r_mid (the caller's level-statistics boundary between the
+ * localized, Poisson regime (2 ln 2 - 1) and the random-matrix, GOE regime
+ * (4 - 2 sqrt 3); their midpoint is the reading used by the package), and
+ * *tau_star (host) = that threshold, else the last one.  Per-threshold
+ * outputs (host arrays [num_taus], nullable): r_mean (NaN when not
+ * evaluated), num_ratios, num_levels, max_comp (-1 when not reached).
+ * SYNCHRONISES the stream (a few times per threshold); uses context scratch
+ * of about 600 bytes per vertex. */
+int subquad_rmt_threshold(subquad_ctx *ctx, const uint32_t *pairs, const float *weights, int64_t m, int64_t n,
+                          const double *taus, int num_taus, int s_max, double r_mid, double *tau_star, double *r_mean,
+                          int64_t *num_ratios, int64_t *num_levels, int32_t *max_comp);
+
+/* G: the pairs with weights >= tau, in input order, to pairs_out (device
+ * uint32 [m][2]) and weights_out (device float [m], nullable); their number
+ * to the device word *d_count.  No host synchronisation. */
+int subquad_graph_prune(subquad_ctx *ctx, const uint32_t *pairs, const float *weights, int64_t m, double tau,
+                        uint32_t *pairs_out, float *weights_out, uint64_t *d_count);
+
+/* Cluster-mass Jensen-Shannon repertoire distance (appendix on repertoire-
+ * level distances): with p_d(k) = |cluster k n donor d| / |donor d|,
+ * dist_out[a][b] = sqrt(JS(p_a || p_b)), JS = 1/2 KL(p_a || M) + 1/2 KL(p_b
+ * || M), M = (p_a + p_b) / 2, natural log (so distances lie in [0,
+ * sqrt(ln 2)]).  labels: device uint32 [n] cluster label of every sequence
+ * (any ids < 2^31; e.g. subquad_graph_components of the pruned graph over the
+ * pooled repertoires, so cluster k is the same cluster for every donor);
+ * donor: device int32 [n] in [0, num_donors) (others set SUBQUAD_ERR_INPUT in
+ * the sticky error); dist_out: device double [num_donors][num_donors],
+ * symmetric, zero diagonal, NaN in the rows and columns of donors without
+ * sequences.  1 <= num_donors <= 4096.  The per-pair terms are added with
+ * FP64 atomics (summation order, and so the last bits, may vary). */
+int subquad_cluster_js(subquad_ctx *ctx, const uint32_t *labels, const int32_t *donor, int64_t n, int num_donors,
+                       double *dist_out);
+
 /* subquad_fuse_forward for a pair count held on the device (*d_m, at most
  * m_max pairs): the graph-capturable form. */
 int subquad_fuse_forward_async(subquad_ctx *ctx, const uint32_t *pairs, const uint64_t *d_m, int64_t m_max,
