@@ -63,10 +63,16 @@ def parse_args():
     p.add_argument("--no-graph", action="store_true", help="time the eager steps instead of CUDA-graph replays")
     p.add_argument("--stream-n", type=int, default=10_000_000,
                    help="sequences of the streamed Zipf workload (0: skip the streamed measurement)")
-    p.add_argument("--stream-batches", type=int, default=16, help="candidate batches timed in the streamed run")
+    p.add_argument("--stream-batches", type=int, default=0,
+                   help="candidate batches timed in the streamed run (0: the whole candidate set)")
     p.add_argument("--stream-capacity", type=int, default=8_000_000, help="pairs per streamed batch")
     p.add_argument("--no-train", action="store_true", help="skip the gate-training measurement")
     p.add_argument("--no-topk", action="store_true", help="skip the cross-donor top-k measurement")
+    p.add_argument("--no-graph", action="store_true", help="skip the graph / RMT threshold / JS distance measurement")
+    p.add_argument("--configs", action="store_true",
+                   help="also run the long checks at their stated sizes: the 64-donor batch (about 4e7 sequences, "
+                        "recall@50 on 10,000 queries against brute force) and 100 gate-training steps beside the "
+                        "oracle's FP64 trajectory")
     p.add_argument("--cpu-sample-n", type=int, default=500_000, help="oracle sample for the cpu_baseline key")
     p.add_argument("--ref-sample-n", type=int, default=200_000, help="oracle sample per step of --impl reference")
     return p.parse_args()
@@ -437,14 +443,19 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         stream.synchronize()
         sw_ms["edit"] = statistics.mean(a.elapsed_time(b) for a, b in times)
 
-    stream_res = train_res = topk_res = None
+    stream_res = train_res = topk_res = graph_res = configs = None
     if rank == 0 and world == 1:
         if not args.no_train:
             train_res = run_train(args, ctx, stream, rep, step_pipe, m)
         if not args.no_topk:
             topk_res = run_topk(args, ctx, stream)
+        if not args.no_graph:
+            graph_res = graph_step(ctx, stream, step_pipe.pairs[:m], step_pipe.fused[:m], cfg.n)
         if args.stream_n > 0:
             stream_res = run_stream(args, ctx, stream, dev, flush)
+        if args.configs:
+            configs = {"config4_trajectory": run_config4_trajectory(args, ctx, stream, rep, step_pipe, m),
+                       "config5_full": run_config5(args, ctx, stream, flush)}
 
     # roofline of the dominant kernel, from the library's live per-kernel event
     # timings over the timed region (same stream as the launches)
@@ -537,6 +548,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                              f"{ED_OPS_PER_CELL} int32 ops per DP cell, default biochemical costs"},
             "stages_ms": stage_ms, "kernel_rooflines": stage_roof, "wall_s": wall, "autotune": tuning["choice"],
             "timed_mode": timed_mode, "eager": eager, "train": train_res, "topk": topk_res, "stream": stream_res,
+            "graph": graph_res, "configs": configs,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -546,14 +558,14 @@ def run_train(args, ctx, stream, rep, step_pipe, m):
     """Gate training on the 1M donor's candidate list: the first 4,000,000
     pairs, family-correlated embeddings (d = 128, trained), gate 3-32-1;
     one step = fused forward + weighted BCE + adjoint (parameters and
-    embeddings) + Adam, full batch, all on the device."""
-    import numpy as np
+    embeddings) + Adam, full batch, all on the device; 100 timed steps."""
     import torch
 
     from paper_2602_17330_gb300 import synth
     from paper_2602_17330_gb300.train import GateTrainer
 
     d, hidden, mt = 128, 32, min(4_000_000, m)
+    steps = 100
     with torch.cuda.stream(stream):
         pairs = step_pipe.pairs[:mt]
         sw = step_pipe.sw[:mt]
@@ -561,23 +573,23 @@ def run_train(args, ctx, stream, rep, step_pipe, m):
         params = torch.from_numpy(synth.gate_parameters(hidden, seed=1)).to(ctx.device)
         label, group = ctx.pair_labels(pairs, torch.from_numpy(rep.family), torch.from_numpy(rep.subgroup))
         weight = ctx.pair_weights(group, int(rep.subgroup.max()) + 1)
-        tr = GateTrainer(ctx, pairs, sw, step_pipe.self_sc, step_pipe.packed, emb, params, hidden, label, weight)
-        for _ in range(3):
-            tr.step()
-        stream.synchronize()
-        loss0 = float(tr.loss.item())
-        steps = 10
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            tr.step()
-        e1.record(stream)
-        stream.synchronize()
+        for warm in range(2):  # warm-up trainer (scratch, tables), then the timed one from the same start
+            tr = GateTrainer(ctx, pairs, sw, step_pipe.self_sc, step_pipe.packed, emb, params, hidden, label, weight)
+            losses = torch.empty((steps,), dtype=torch.float32, device=ctx.device)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(steps if warm else 3):
+                losses[k:k + 1].copy_(tr.step())
+            e1.record(stream)
+            stream.synchronize()
     ctx.check()
     ms = e0.elapsed_time(e1) / steps
+    lv = losses.cpu().numpy()
     return {"workload": f"first {mt:,} candidate pairs of the 1M donor, d={d} (trained), gate 3-{hidden}-1, "
                         "weighted BCE, Adam lr 1e-3, full batch",
-            "ms_per_step": ms, "pairs_per_s": mt / (ms / 1e3), "loss_first": loss0, "loss_last": float(tr.loss.item())}
+            "steps": steps, "ms_per_step": ms, "pairs_per_s": mt / (ms / 1e3),
+            "loss_step_1": float(lv[0]), "loss_step_10": float(lv[9]), "loss_step_100": float(lv[99])}
 
 
 def run_topk(args, ctx, stream):
@@ -627,6 +639,7 @@ def run_topk(args, ctx, stream):
         e3.record(stream)
         stream.synchronize()
     ctx.check()
+    g = graph_step(ctx, stream, pairs, bp.fused[:mq], rep.n, donor=x["donor"], num_donors=16)
     got = sc_p.cpu().numpy()
     best = sc_b.cpu().numpy()
     thr = best[:, 49]  # 50th-best exhaustive score (-1: fewer than 50 other-donor sequences)
@@ -639,7 +652,7 @@ def run_topk(args, ctx, stream):
             "queries_per_s": 100_000 / (e1.elapsed_time(e2) / 1e3),
             "bruteforce_1000_queries_ms": e2b.elapsed_time(e3),
             "queries_with_cross_donor_candidates": with_cand,
-            "recall_at_50_public_queries": recall,
+            "recall_at_50_public_queries": recall, "graph_and_js": g,
             "recall_note": "tie-aware recall@50 of the candidate route against the exhaustive top-50 (other donors), "
                            "on 1,000 queries drawn from public-family members"}
 
@@ -647,9 +660,10 @@ def run_topk(args, ctx, stream):
 def run_stream(args, ctx, stream, dev, flush):
     """The streamed form on the 10M-sequence Zipf workload (lengths 6-30, 32
     bands of 4, no cap): pack, sign, self-scores and the band index once,
-    then the first K candidate batches, each emitted in order, aligned and
-    fused.  Reports the index time, the batch throughput in candidate pairs
-    per second, and the raw-pair total (an upper bound of |C|)."""
+    then every candidate batch (by default the whole candidate set C), each
+    emitted in order, aligned and fused.  Reports |C|, its DP cells, the index
+    time, the total time, pairs per second and GCUPS of the alignment
+    kernels (their launches timed by the library's event profiler)."""
     import numpy as np
     import torch
 
@@ -663,34 +677,226 @@ def run_stream(args, ctx, stream, dev, flush):
     emb = synth.unit_embeddings(rep.n, cfg.d, seed=0)
     params = synth.gate_parameters(cfg.hidden, seed=0)
     sp = pipeline.StreamedPipeline(ctx, cfg, cfg.n, args.stream_capacity)
+    max_batches = args.stream_batches if args.stream_batches > 0 else None
     with torch.cuda.stream(stream):
         x = pipeline.Pipeline(ctx, cfg).upload(rep, a, b, emb, params)
+        lens_t = x["lens"].to(torch.int64)
         del emb
         sp.prepare(x)  # warm-up: reserves scratch
         for _ in sp.batches(x, max_batches=2):
             pass
         stream.synchronize()
         flush.zero_()
+        cells = torch.zeros((), dtype=torch.int64, device=dev)
+        ctx.profile(True)
+        ctx.profile_reset()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         total_raw = sp.prepare(x)
         e1.record(stream)
-        pairs = 0
-        for p_, _, _ in sp.batches(x, max_batches=args.stream_batches):
+        pairs, nb = 0, 0
+        for p_, _, _ in sp.batches(x, max_batches=max_batches):
             pairs += int(p_.shape[0])
+            nb += 1
+            pl = p_.to(torch.int64)
+            cells += (lens_t[pl[:, 0]] * lens_t[pl[:, 1]]).sum()
         e2.record(stream)
         stream.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
     ctx.check()
     sp.close()
     prep_ms, batch_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
-    rate = pairs / (batch_ms / 1e3)
+    cells = int(cells.item())
+    align_ms = prof["align"][0] + prof["align_bin"][0]
     return {"workload": f"{cfg.name}: {cfg.n:,} sequences, lengths 6-30, Zipf(1.2) families up to 50,000, "
                         f"{cfg.hashes} hashes in {cfg.bands}x{cfg.rows} bands, no cap",
-            "index_ms": prep_ms, "batches": args.stream_batches, "batch_capacity": args.stream_capacity,
-            "pairs": pairs, "batches_ms": batch_ms, "value": rate, "unit": UNIT,
-            "raw_pairs_total": total_raw,
+            "whole_candidate_set": max_batches is None, "candidate_pairs": pairs, "cells": cells,
+            "raw_pairs_total": total_raw, "batches": nb, "batch_capacity": args.stream_capacity,
+            "index_ms": prep_ms, "batches_ms": batch_ms, "total_ms": prep_ms + batch_ms,
+            "value": pairs / (batch_ms / 1e3), "unit": UNIT,
+            "sw_gcups": cells / (align_ms / 1e3) / 1e9 if align_ms > 0 else None,
             "note": "pack, sign, self-scores and the band index once; then candidate batches emitted in order, "
-                    "aligned and fused (each batch synchronises once for its count)"}
+                    "aligned (length-binned) and fused; each batch synchronises once for its count; cells summed "
+                    "on the device per batch; GCUPS over the profiled binning + alignment launches"}
+
+
+GRAPH_TAUS = [round(0.40 + 0.02 * k, 2) for k in range(26)]  # 0.40, 0.42, ..., 0.90
+
+
+def graph_step(ctx, stream, pairs, fused, n, donor=None, num_donors=0):
+    """Graph construction of Algorithm 1 on the fused candidate graph: the
+    RMT threshold scan (level statistics of the block-diagonal thresholded
+    matrix), the pruned graph G, its connected components as clusters and,
+    given donors, their cluster-mass Jensen-Shannon distances."""
+    import numpy as np
+    import torch
+
+    with torch.cuda.stream(stream):
+        stream.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = ctx.rmt_threshold(pairs, fused, n, GRAPH_TAUS, 64)
+        t1 = time.perf_counter()
+        e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e1.record(stream)
+        gp, gw = ctx.graph_prune(pairs, fused, res["tau_star"])
+        labels, sizes = ctx.graph_components(gp, gw, n, res["tau_star"], want_sizes=True)
+        e2.record(stream)
+        js = None
+        if donor is not None:
+            js = ctx.cluster_js(labels, donor, num_donors)
+        e3.record(stream)
+        stream.synchronize()
+    ctx.check()
+    sz = sizes.cpu().numpy()
+    lab = labels.cpu().numpy()
+    roots = np.flatnonzero(lab == np.arange(n))
+    clusters = int((sz[roots] >= 2).sum())
+    k = GRAPH_TAUS.index(res["tau_star"])
+    out = {"tau_star": res["tau_star"], "thresholds_scanned": int(sum(1 for c in res["max_comp"] if c >= 0)),
+           "r_at_tau_star": res["r_mean"][k], "levels_at_tau_star": res["num_levels"][k],
+           "max_component_at_tau_star": res["max_comp"][k], "edges_in": int(pairs.shape[0]),
+           "edges_kept": int(gp.shape[0]), "clusters_ge2": clusters,
+           "scan_ms": 1e3 * (t1 - t0), "scan_gpu_ms": e0.elapsed_time(e1), "prune_components_ms": e1.elapsed_time(e2),
+           "first_evaluable_tau": next((t for t, c in zip(GRAPH_TAUS, res["max_comp"]) if 0 <= c <= 64), None)}
+    if js is not None:
+        D = js.cpu().numpy()
+        off = D[~np.eye(num_donors, dtype=bool)]
+        out.update(js_ms=e2.elapsed_time(e3), js_mean=float(np.nanmean(off)), js_min=float(np.nanmin(off)),
+                   js_max=float(np.nanmax(off)))
+    return out
+
+
+def run_config5(args, ctx, stream, flush):
+    """The many-repertoire batch at its stated size: 64 donors of log-uniform
+    sizes in 5e4..2e6, 500 public families; one batched pass (pack, sign,
+    banding over the pooled donors, length-binned alignment, fusion), then the
+    top-50 other-donor matches of 100,000 queries, recall@50 (ties counted)
+    against the exhaustive GPU top-50 on a 10,000-query subsample of them, and
+    the donors' cluster-mass JS distances."""
+    import numpy as np
+    import torch
+
+    from paper_2602_17330_gb300 import pipeline, synth
+
+    t_gen = time.perf_counter()
+    rep = synth.pooled_repertoire(64, 50_000, 2_000_000, seed=5)
+    t_gen = time.perf_counter() - t_gen
+    cfg = pipeline.Workload("pooled_64", rep.n, bucket_cap=2048)
+    a, b = synth.hash_coefficients(cfg.hashes, seed=5)
+    bp = pipeline.BatchedPipeline(ctx, cfg, rep.n, capacity=8 * rep.n)
+    with torch.cuda.stream(stream):
+        x = {"codes": torch.from_numpy(rep.codes).to(ctx.device), "lens": torch.from_numpy(rep.lens).to(ctx.device),
+             "a": torch.from_numpy(a.view(np.int32)).to(ctx.device),
+             "b": torch.from_numpy(b.view(np.int32)).to(ctx.device),
+             "emb": torch.from_numpy(synth.unit_embeddings(rep.n, cfg.d, seed=5)).to(ctx.device),
+             "params": torch.from_numpy(synth.gate_parameters(cfg.hidden, seed=5)).to(ctx.device)}
+        bp.step(x)  # warm-up (scratch)
+        stream.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bp.step(x)
+        e1.record(stream)
+        stream.synchronize()
+        ctx.check()
+        mq = int(bp.num_pairs.item())
+        pairs, scores = bp.pairs[:mq], bp.sw[:mq]
+        donor = torch.from_numpy(rep.donor).to(ctx.device)
+        q_np = synth.sample_queries(rep.n, 100_000, seed=5)
+        queries = torch.from_numpy(q_np.view(np.int32)).to(ctx.device)
+        e2, e3, e4, e5 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        e2.record(stream)
+        index = ctx.pair_index(pairs, rep.n)
+        ids, sc = ctx.topk_candidates(pairs, scores, rep.n, donor, queries, 50, index=index)
+        e3.record(stream)
+        sub_idx = np.sort(np.random.default_rng(5).choice(q_np.size, 10_000, replace=False))
+        sub = torch.from_numpy(q_np[sub_idx].view(np.int32)).to(ctx.device)
+        e4.record(stream)
+        _, sc_b = ctx.topk_bruteforce(bp.packed, donor, sub, 50)
+        e5.record(stream)
+        stream.synchronize()
+    ctx.check()
+    got = sc.cpu().numpy()[sub_idx]
+    best = sc_b.cpu().numpy()
+    thr = best[:, 49]
+    hit = ((got >= thr[:, None]) & (got >= 0)).sum(1)
+    recall = float(np.minimum(hit, 50).mean() / 50.0)
+    public = (rep.family[q_np[sub_idx]] >= 0) & (rep.family[q_np[sub_idx]] < 500)
+    rec_pub = float(np.minimum(hit[public], 50).mean() / 50.0) if public.any() else None
+    cells = pipeline.cells_of(rep.lens, pairs.cpu().numpy().view(np.uint32))
+    g = graph_step(ctx, stream, pairs, bp.fused[:mq], rep.n, donor=donor, num_donors=64)
+    return {"workload": f"{rep.n:,} sequences pooled from 64 donors (log-uniform 5e4-2e6), 500 public families "
+                        "(total public fraction log-uniform 1e-4..1e-2 per donor); 64 hashes in 16x4 bands, cap 2048",
+            "generate_s": t_gen, "candidate_pairs": mq, "cells": cells, "pass_ms": e0.elapsed_time(e1),
+            "pairs_per_s": mq / (e0.elapsed_time(e1) / 1e3),
+            "topk_100k_queries_ms": e2.elapsed_time(e3), "bruteforce_10k_queries_ms": e4.elapsed_time(e5),
+            "recall_at_50": recall, "recall_at_50_public_queries": rec_pub, "public_queries_in_sample": int(public.sum()),
+            "queries_with_cross_donor_candidates": float((got[:, 0] >= 0).mean()), "graph": g,
+            "recall_note": "tie-aware recall@50 of the candidate route against the exhaustive top-50 among other "
+                           "donors' sequences, on a seeded 10,000-query subsample of the 100,000 queries"}
+
+
+def run_config4_trajectory(args, ctx, stream, rep, step_pipe, m):
+    """100 full-batch Adam steps of the gate (3-32-1) on the first 4,000,000
+    candidate pairs with d = 128 family-correlated embeddings held fixed, on
+    the GPU and, beside it, in the FP64 oracle (its threaded forward and
+    parameter adjoint, its Adam) from the same start; the loss at steps 1, 10
+    and 100 on both, the drift, and the largest parameter difference."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2602_17330_gb300 import synth
+    from paper_2602_17330_gb300.train import GateTrainer
+
+    d, hidden, mt, steps = 128, 32, min(4_000_000, m), 100
+    res = step_pipe.result()
+    pairs_np, sw_np, self_np = res["pairs"][:mt], res["sw"][:mt], res["self"]
+    emb = synth.family_embeddings(rep.family, d, seed=1)
+    params0 = synth.gate_parameters(hidden, seed=1)
+    with torch.cuda.stream(stream):
+        pairs = step_pipe.pairs[:mt]
+        label, group = ctx.pair_labels(pairs, torch.from_numpy(rep.family), torch.from_numpy(rep.subgroup))
+        ng = int(rep.subgroup.max()) + 1
+        weight = ctx.pair_weights(group, ng)
+        tr = GateTrainer(ctx, pairs, step_pipe.sw[:mt], step_pipe.self_sc, step_pipe.packed,
+                         torch.from_numpy(emb).to(ctx.device), torch.from_numpy(params0).to(ctx.device), hidden,
+                         label, weight, train_emb=False)
+        losses = torch.empty((steps,), dtype=torch.float32, device=ctx.device)
+        for k in range(steps):
+            losses[k:k + 1].copy_(tr.step())
+        stream.synchronize()
+    ctx.check()
+    gpu_loss = losses.cpu().numpy().astype(np.float64)
+    gpu_params = tr.params.cpu().numpy().astype(np.float64)
+    threads = oracle.host_threads()
+    y, g = oracle.pair_labels(pairs_np, rep.family, rep.subgroup)
+    w = oracle.pair_weights(g, ng)
+    p = params0.astype(np.float64)
+    m1, m2 = np.zeros_like(p), np.zeros_like(p)
+    ora_loss = []
+    t0 = time.perf_counter()
+    for t in range(1, steps + 1):
+        fused = oracle.fuse_forward_mt(pairs_np, sw_np, self_np, rep.lens, emb, p.astype(np.float32), hidden, threads)
+        loss, dL = oracle.bce_loss(fused, y, w)
+        ora_loss.append(loss)
+        grad = oracle.fuse_backward_params_mt(pairs_np, sw_np, self_np, rep.lens, emb, p.astype(np.float32), hidden,
+                                              dL, threads)
+        oracle.adam_step(p, grad, m1, m2, t)
+    ora_s = time.perf_counter() - t0
+    ora_loss = np.array(ora_loss)
+    rel = np.abs(gpu_loss - ora_loss) / np.abs(ora_loss)
+    return {"workload": f"first {mt:,} candidate pairs of the 1M donor, d={d} (fixed), gate 3-{hidden}-1 trained, "
+                        "weighted BCE, Adam lr 1e-3, 100 full-batch steps",
+            "gpu_loss": {"1": gpu_loss[0], "10": gpu_loss[9], "100": gpu_loss[99]},
+            "oracle_loss": {"1": ora_loss[0], "10": ora_loss[9], "100": ora_loss[99]},
+            "loss_rel_drift": {"1": rel[0], "10": rel[9], "100": rel[99], "max": float(rel.max())},
+            "max_param_abs_diff_after_100": float(np.abs(gpu_params - p).max()),
+            "oracle_s": ora_s, "oracle_threads": threads,
+            "note": "the oracle's parameters are rounded to float32 for each forward, like the GPU's"}
 
 
 def run_e2e(args, pipe, rep, a, b, emb, params, stream, dev, world):

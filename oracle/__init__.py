@@ -104,6 +104,9 @@ def _load():
     lib.oracle_fuse_forward_mt.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, F32P, c.c_int, F64P,
                                            c.c_int]
     lib.oracle_fuse_forward_mt.restype = c.c_int
+    lib.oracle_fuse_backward_params_mt.argtypes = [U32P, c.c_int64, I32P, I32P, U8P, F32P, c.c_int, F32P, c.c_int,
+                                                   F64P, F64P, c.c_int]
+    lib.oracle_fuse_backward_params_mt.restype = c.c_int
     _lib = lib
     return lib
 
@@ -433,3 +436,15 @@ def fuse_forward_mt(pairs, sw_scores, self_sc, lens, emb, params, hidden: int, t
                                       threads):
         raise MemoryError("oracle_fuse_forward_mt failed")
     return out
+
+
+def fuse_backward_params_mt(pairs, sw_scores, self_sc, lens, emb, params, hidden: int, dL_dfused, threads: int):
+    """Parameter gradient of the fusion adjoint (FP64 [5 h + 1]) over threads."""
+    p = _pairs(pairs)
+    emb = _c(emb, np.float32)
+    gp = np.zeros(5 * hidden + 1, dtype=np.float64)
+    if _load().oracle_fuse_backward_params_mt(p, p.shape[0], _c(sw_scores, np.int32), _c(self_sc, np.int32),
+                                              _c(lens, np.uint8), emb, emb.shape[1], _c(params, np.float32), hidden,
+                                              _c(dL_dfused, np.float64), gp, threads):
+        raise MemoryError("oracle_fuse_backward_params_mt failed")
+    return gp

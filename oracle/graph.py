@@ -89,16 +89,22 @@ def threshold_spectrum(n: int, pairs, weights, tau: float, s_max: int) -> dict:
     if not out["evaluable"]:
         out.update(levels=None, r_mean=float("nan"), n_r=0)
         return out
-    keep = w >= tau
+    keep = np.flatnonzero(w >= tau)
+    edge_comp = lab[p[keep, 0]]
+    by_comp = keep[np.argsort(edge_comp, kind="stable")]
+    bounds = np.searchsorted(np.sort(edge_comp), active)
+    ends = np.searchsorted(np.sort(edge_comp), active, side="right")
+    vorder = np.argsort(lab, kind="stable")
+    vstart = np.searchsorted(lab[vorder], active)
     levels = []
-    for c in active:
-        verts = np.flatnonzero(lab == c)
+    for c, e0, e1, v0 in zip(active, bounds, ends, vstart):
+        verts = vorder[v0:v0 + sizes[c]]
         local = {int(v): k for k, v in enumerate(verts)}
         M = np.zeros((verts.size, verts.size))
-        sel = keep & (lab[p[:, 0]] == c)
-        for (i, j), x in zip(p[sel], w[sel]):
-            M[local[int(i)], local[int(j)]] = x
-            M[local[int(j)], local[int(i)]] = x
+        for q in by_comp[e0:e1]:
+            i, j = int(p[q, 0]), int(p[q, 1])
+            M[local[i], local[j]] = w[q]
+            M[local[j], local[i]] = w[q]
         levels.append(np.linalg.eigvalsh(M))
     lv = np.sort(np.concatenate(levels)) if levels else np.zeros(0)
     r, nr = r_statistic(lv)

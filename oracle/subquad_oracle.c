@@ -825,7 +825,7 @@ int oracle_topk(const uint32_t *pairs, const int32_t *scores, int64_t m, const i
 #include <pthread.h>
 
 typedef struct {
-    int kind; /* 0 sign, 1 sw, 2 fuse forward */
+    int kind; /* 0 sign, 1 sw, 2 fuse forward, 3 fuse backward (parameters only) */
     int64_t lo, hi;
     /* sign */
     const uint8_t *codes;
@@ -844,6 +844,8 @@ typedef struct {
     const float *emb, *params;
     int d, h;
     double *fused;
+    const double *dL;
+    double *grad; /* kind 3: this thread's own parameter-gradient partial */
     int rc;
 } mt_job;
 
@@ -858,9 +860,12 @@ static void *mt_run(void *arg)
     else if (j->kind == 1)
         oracle_sw_pairs(j->codes, j->code_stride, j->lens, j->pairs + 2 * j->lo, n, j->M, j->o, j->e,
                         j->scores + j->lo);
-    else
+    else if (j->kind == 2)
         j->rc = oracle_fuse_forward(j->pairs + 2 * j->lo, n, j->sw + j->lo, j->self, j->lens, j->emb, j->d, j->params,
                                     j->h, j->fused + j->lo, NULL, NULL, NULL);
+    else
+        j->rc = oracle_fuse_backward(j->pairs + 2 * j->lo, n, j->sw + j->lo, j->self, j->lens, j->emb, j->d, j->params,
+                                     j->h, j->dL + j->lo, j->grad, NULL);
     return NULL;
 }
 
@@ -880,6 +885,7 @@ static int mt_launch(mt_job *proto, int64_t count, int threads)
         jobs[t] = *proto;
         jobs[t].lo = count * t / threads;
         jobs[t].hi = count * (t + 1) / threads;
+        if (proto->kind == 3) jobs[t].grad = proto->grad + (int64_t)t * (5 * proto->h + 1);
         if (pthread_create(&tid[t], NULL, mt_run, &jobs[t]) != 0) {
             mt_run(&jobs[t]); /* run inline if a thread cannot be started */
             tid[t] = 0;
@@ -945,4 +951,38 @@ int oracle_fuse_forward_mt(const uint32_t *pairs, int64_t m, const int32_t *sw, 
     j.h = h;
     j.fused = fused;
     return mt_launch(&j, m, threads);
+}
+
+/* Parameter gradient of the fusion adjoint over `threads` threads: thread t
+ * accumulates its pair range into its own partial (the single-threaded
+ * routine above); the partials are then added in thread order.  Summation
+ * order differs from the single-threaded call (results agree to FP64
+ * rounding).  grad_params accumulates (caller zeroes).                      */
+int oracle_fuse_backward_params_mt(const uint32_t *pairs, int64_t m, const int32_t *sw, const int32_t *self,
+                                   const uint8_t *lens, const float *emb, int d, const float *params, int h,
+                                   const double *dL_dfused, double *grad_params, int threads)
+{
+    if (threads < 1) threads = 1;
+    if (threads > 1024) threads = 1024;
+    int P = 5 * h + 1;
+    double *part = (double *)calloc((size_t)threads * (size_t)P, sizeof(double));
+    if (!part) return -1;
+    mt_job j;
+    memset(&j, 0, sizeof(j));
+    j.kind = 3;
+    j.pairs = pairs;
+    j.sw = sw;
+    j.self = self;
+    j.lens = lens;
+    j.emb = emb;
+    j.d = d;
+    j.params = params;
+    j.h = h;
+    j.dL = dL_dfused;
+    j.grad = part;
+    int rc = mt_launch(&j, m, threads);
+    for (int t = 0; t < threads; ++t)
+        for (int q = 0; q < P; ++q) grad_params[q] += part[(int64_t)t * P + q];
+    free(part);
+    return rc;
 }

@@ -24,3 +24,18 @@ def test_threaded_runners_equal_single_thread(oracle_mod, threads):
     # fewer items than threads
     few = C[:2]
     assert (oracle_mod.sw_pairs_mt(rep.codes, rep.lens, few, threads) == sw[:2]).all()
+
+
+def test_threaded_parameter_gradient(oracle_mod):
+    rep = synth.donor_repertoire(6_000, seed=4)
+    a, b = synth.hash_coefficients(64, seed=4)
+    C = oracle_mod.candidates(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), 16, 4, 2048)
+    sw = oracle_mod.sw_pairs(rep.codes, rep.lens, C)
+    self_sc = oracle_mod.self_scores(rep.codes, rep.lens)
+    emb = synth.family_embeddings(rep.family, 32, seed=4)
+    params = synth.gate_parameters(8, seed=4)
+    dL = np.random.default_rng(4).standard_normal(C.shape[0])
+    want, _ = oracle_mod.fuse_backward(C, sw, self_sc, rep.lens, emb, params, 8, dL, with_emb=False)
+    for threads in (1, 5):
+        got = oracle_mod.fuse_backward_params_mt(C, sw, self_sc, rep.lens, emb, params, 8, dL, threads)
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-15)
