@@ -68,7 +68,8 @@ def parse_args():
     p.add_argument("--stream-capacity", type=int, default=8_000_000, help="pairs per streamed batch")
     p.add_argument("--no-train", action="store_true", help="skip the gate-training measurement")
     p.add_argument("--no-topk", action="store_true", help="skip the cross-donor top-k measurement")
-    p.add_argument("--no-graph", action="store_true", help="skip the graph / RMT threshold / JS distance measurement")
+    p.add_argument("--no-graph-step", action="store_true",
+                   help="skip the graph construction / RMT threshold / JS distance measurement")
     p.add_argument("--configs", action="store_true",
                    help="also run the long checks at their stated sizes: the 64-donor batch (about 4e7 sequences, "
                         "recall@50 on 10,000 queries against brute force) and 100 gate-training steps beside the "
@@ -449,7 +450,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             train_res = run_train(args, ctx, stream, rep, step_pipe, m)
         if not args.no_topk:
             topk_res = run_topk(args, ctx, stream)
-        if not args.no_graph:
+        if not args.no_graph_step:
             graph_res = graph_step(ctx, stream, step_pipe.pairs[:m], step_pipe.fused[:m], cfg.n)
         if args.stream_n > 0:
             stream_res = run_stream(args, ctx, stream, dev, flush)
