@@ -328,7 +328,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if not args.no_autotune:
             tuning = autotune.autotune(ctx, out["packed"], out["pairs"], sig=out["sig"], n=cfg.n, bands=cfg.bands,
                                        rows=cfg.rows, bucket_cap=cfg.bucket_cap, gap_open=cfg.gap_open,
-                                       gap_extend=cfg.gap_extend, reps=3, use_cache=False)
+                                       gap_extend=cfg.gap_extend, reps=3, use_cache=False,
+                                       fuse=(out["sw"], out["self"], x["emb"], x["params"], cfg.hidden))
         out = pipe.forward(x)
         step_pipe.step(x)
     stream.synchronize()
@@ -881,16 +882,24 @@ def run_config4_trajectory(args, ctx, stream, rep, step_pipe, m):
     from paper_2602_17330_gb300.train import GateTrainer
 
     d, hidden, mt, steps = 128, 32, min(4_000_000, m), 100
-    res = step_pipe.result()
-    pairs_np, sw_np, self_np = res["pairs"][:mt], res["sw"][:mt], res["self"]
+    threads = oracle.host_threads()
+    # the trajectory's inputs (pair list, alignment scores) from the oracle side
+    a, b = synth.hash_coefficients(64, seed=0)
+    sig = oracle.sign_mt(rep.codes, rep.lens, 3, a, b, threads)
+    pairs_np = oracle.candidates(sig, 16, 4, 2048)[:mt]
+    del sig
+    sw_np = oracle.sw_pairs_mt(rep.codes, rep.lens, pairs_np, threads)
+    idx = np.arange(rep.n, dtype=np.uint32)
+    self_np = oracle.sw_pairs_mt(rep.codes, rep.lens, np.stack([idx, idx], 1), threads)
     emb = synth.family_embeddings(rep.family, d, seed=1)
     params0 = synth.gate_parameters(hidden, seed=1)
     with torch.cuda.stream(stream):
-        pairs = step_pipe.pairs[:mt]
+        pairs = torch.from_numpy(pairs_np.view(np.int32)).to(ctx.device)
         label, group = ctx.pair_labels(pairs, torch.from_numpy(rep.family), torch.from_numpy(rep.subgroup))
         ng = int(rep.subgroup.max()) + 1
         weight = ctx.pair_weights(group, ng)
-        tr = GateTrainer(ctx, pairs, step_pipe.sw[:mt], step_pipe.self_sc, step_pipe.packed,
+        tr = GateTrainer(ctx, pairs, torch.from_numpy(sw_np).to(ctx.device), torch.from_numpy(self_np).to(ctx.device),
+                         step_pipe.packed,
                          torch.from_numpy(emb).to(ctx.device), torch.from_numpy(params0).to(ctx.device), hidden,
                          label, weight, train_emb=False)
         losses = torch.empty((steps,), dtype=torch.float32, device=ctx.device)
@@ -900,7 +909,6 @@ def run_config4_trajectory(args, ctx, stream, rep, step_pipe, m):
     ctx.check()
     gpu_loss = losses.cpu().numpy().astype(np.float64)
     gpu_params = tr.params.cpu().numpy().astype(np.float64)
-    threads = oracle.host_threads()
     y, g = oracle.pair_labels(pairs_np, rep.family, rep.subgroup)
     w = oracle.pair_weights(g, ng)
     p = params0.astype(np.float64)

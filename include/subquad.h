@@ -85,8 +85,15 @@ int64_t subquad_launch_count(const subquad_ctx *ctx);
  *     x 2 blocks per SM, 1 = 128 threads x 3 blocks per SM (default 1);
  *   SUBQUAD_TUNE_BAND_PART_LOG2: log2 of the target number of (band, sequence)
  *     keys per hash partition of the banding stage, 6..16 (default 11); each
- *     partition is grouped by one CTA in shared memory. */
-enum { SUBQUAD_TUNE_ALIGN_SHAPE = 0, SUBQUAD_TUNE_BAND_PART_LOG2 = 1, SUBQUAD_TUNE_COUNT = 2 };
+ *     partition is grouped by one CTA in shared memory;
+ *   SUBQUAD_TUNE_FUSE_LANES: lanes per pair of the two-channel fusion forward,
+ *     4 or 8 (default 4). */
+enum {
+    SUBQUAD_TUNE_ALIGN_SHAPE = 0,
+    SUBQUAD_TUNE_BAND_PART_LOG2 = 1,
+    SUBQUAD_TUNE_FUSE_LANES = 2,
+    SUBQUAD_TUNE_COUNT = 3
+};
 int subquad_set_tuning(subquad_ctx *ctx, int key, int value);
 int subquad_get_tuning(const subquad_ctx *ctx, int key, int *value);
 

@@ -4,7 +4,8 @@ Each knob changes only how work is mapped onto the GB300 (never a result):
 * TUNE_ALIGN_SHAPE -- batched Smith-Waterman launch shape (256 threads x 2
   blocks per SM with 128 registers, or 128 x 3 with 168 registers);
 * TUNE_BAND_PART_LOG2 -- log2 of the target keys per hash partition of the
-  banding stage (each partition is grouped by one CTA in shared memory).
+  banding stage (each partition is grouped by one CTA in shared memory);
+* TUNE_FUSE_LANES -- lanes per pair of the fusion forward (4 or 8).
 
 ``autotune`` times every candidate on the caller's own workload with CUDA
 events on the context's stream, keeps the fastest, and caches the choice per
@@ -23,6 +24,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning.json")
 CANDIDATES = {
     subquad.TUNE_ALIGN_SHAPE: (0, 1),
     subquad.TUNE_BAND_PART_LOG2: (10, 11),
+    subquad.TUNE_FUSE_LANES: (4, 8),
 }
 
 
@@ -60,8 +62,10 @@ def load_cached(ctx, shape: str) -> dict | None:
 
 
 def autotune(ctx, packed, pairs, sig=None, n: int = 0, bands: int = 0, rows: int = 0, bucket_cap: int = 0,
-             gap_open: int = 10, gap_extend: int = 1, reps: int = 5, shape: str = "", use_cache: bool = True) -> dict:
-    """Pick the fastest setting of every knob on this workload; returns
+             gap_open: int = 10, gap_extend: int = 1, reps: int = 5, shape: str = "", use_cache: bool = True,
+             fuse=None) -> dict:
+    """Pick the fastest setting of every knob on this workload (the fusion
+    knob when ``fuse`` = (sw, self_scores, emb, params, hidden) is given); returns
     {"choice": {knob: value}, "timings_ms": {knob: {value: ms}}}."""
     if use_cache and shape:
         cached = load_cached(ctx, shape)
@@ -85,6 +89,17 @@ def autotune(ctx, packed, pairs, sig=None, n: int = 0, bands: int = 0, rows: int
             ctx.set_tuning(knob, v)
             timings[knob][v] = _time(ctx, lambda: ctx.band_candidates(sig, n, bands, rows, bucket_cap, out=buf),
                                      max(2, reps // 2))
+        choice[knob] = min(timings[knob], key=timings[knob].get)
+        ctx.set_tuning(knob, choice[knob])
+    if fuse is not None:
+        sw, self_sc, emb, params, hidden = fuse
+        knob = subquad.TUNE_FUSE_LANES
+        timings[knob] = {}
+        out_f = ctx.torch.empty((int(pairs.shape[0]),), dtype=ctx.torch.float32, device=ctx.device)
+        for v in CANDIDATES[knob]:
+            ctx.set_tuning(knob, v)
+            timings[knob][v] = _time(ctx, lambda: ctx.fuse_forward(pairs, sw, self_sc, packed, emb, params, hidden,
+                                                                   out=out_f), reps)
         choice[knob] = min(timings[knob], key=timings[knob].get)
         ctx.set_tuning(knob, choice[knob])
     result = {"choice": {str(k): v for k, v in choice.items()},

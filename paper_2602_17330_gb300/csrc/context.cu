@@ -80,6 +80,7 @@ extern "C" int subquad_create(subquad_ctx **out, int device, void *cuda_stream)
     for (int k = 0; k < SUBQUAD_TUNE_COUNT; ++k) ctx->tune[k] = 0;
     ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE] = 1;
     ctx->tune[SUBQUAD_TUNE_BAND_PART_LOG2] = 11;
+    ctx->tune[SUBQUAD_TUNE_FUSE_LANES] = 4;
     SqDeviceGuard guard(ctx);
     cudaError_t e = guard.ok ? cudaSuccess : cudaErrorInvalidDevice;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -227,6 +228,7 @@ extern "C" int subquad_set_tuning(subquad_ctx *ctx, int key, int value)
     if (!ctx || key < 0 || key >= SUBQUAD_TUNE_COUNT) return SUBQUAD_ERR_ARG;
     if (key == SUBQUAD_TUNE_ALIGN_SHAPE && (value < 0 || value > 1)) return SUBQUAD_ERR_ARG;
     if (key == SUBQUAD_TUNE_BAND_PART_LOG2 && (value < 6 || value > 16)) return SUBQUAD_ERR_ARG;
+    if (key == SUBQUAD_TUNE_FUSE_LANES && value != 4 && value != 8) return SUBQUAD_ERR_ARG;
     ctx->tune[key] = value;
     return SUBQUAD_OK;
 }

@@ -27,12 +27,21 @@ __device__ __forceinline__ float group_sum(float v)
     return v;
 }
 
-constexpr int kTppF = 4;  // lanes per pair in the forward kernel
+constexpr int kTppF = 4;  // lanes per pair in the forward kernels (default)
 
 __device__ __forceinline__ float quad_sum(float v)
 {
     v += __shfl_xor_sync(0xffffffffu, v, 2, kTppF);
     v += __shfl_xor_sync(0xffffffffu, v, 1, kTppF);
+    return v;
+}
+
+// Sum over the T lanes of one pair (T a power of two <= 32).
+template <int T>
+__device__ __forceinline__ float lanes_sum(float v)
+{
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, T);
     return v;
 }
 
@@ -73,7 +82,7 @@ struct PairInputs {
     }
 };
 
-template <int WORDS, int CPL>
+template <int WORDS, int CPL, int TPPF>
 __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
     const uint32_t *__restrict__ pairs, int64_t m_max, const unsigned long long *__restrict__ d_m,
     const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc, const uint64_t *__restrict__ packed,
@@ -94,9 +103,9 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
     if (threadIdx.x == 0) s_b2 = params[5 * hidden];
     __syncthreads();
     const float b2 = s_b2;
-    constexpr int kPairsPerWarp = 32 / kTppF;
-    const int sub = threadIdx.x & (kTppF - 1);
-    const int slot = (threadIdx.x & 31) / kTppF;
+    constexpr int kPairsPerWarp = 32 / TPPF;
+    const int sub = threadIdx.x & (TPPF - 1);
+    const int slot = (threadIdx.x & 31) / TPPF;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int d4 = d >> 2;
@@ -111,7 +120,7 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
         const bool valid = p < m;
         const uint2 ij = valid ? ij_next : make_uint2(0, 0);
         ij_next = p + pstep < m ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p + pstep) : make_uint2(0, 0);
-        PairInputs<WORDS, CPL, kTppF> in;
+        PairInputs<WORDS, CPL, TPPF> in;
         in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
         float dot = 0.f, sii = 0.f, sjj = 0.f;
 #pragma unroll
@@ -121,21 +130,21 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
             sii = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, sii))));
             sjj = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, sjj))));
         }
-        dot = quad_sum(dot);
-        sii = quad_sum(sii);
-        sjj = quad_sum(sjj);
+        dot = lanes_sum<TPPF>(dot);
+        sii = lanes_sum<TPPF>(sii);
+        sjj = lanes_sum<TPPF>(sjj);
         const float prod = (float)in.self_i * (float)in.self_j;
         const float s = prod > 0.f ? (float)in.sw * rsqrtf(prod) : 0.f;
         const float nn = sii * sjj;
         const float c = nn > 0.f ? dot * rsqrtf(nn) : 0.f;
         const float delta = fabsf((float)(in.len_i - in.len_j));
         float acc = 0.f;
-        for (int k = sub; k < hidden; k += kTppF) {
+        for (int k = sub; k < hidden; k += TPPF) {
             const float4 u = s_unit[k];
             float z = fmaf(u.x, s, fmaf(u.y, c, fmaf(u.z, delta, u.w)));
             acc = fmaf(s_w2[k], fmaxf(z, 0.f), acc);
         }
-        const float g = quad_sum(acc) + b2;
+        const float g = lanes_sum<TPPF>(acc) + b2;
         if (valid && sub == 0) {
             const float a = __fdividef(1.f, 1.f + __expf(-g));
             fused[p] = fmaf(a, s - 0.5f * (1.f + c), 0.5f * (1.f + c));
@@ -144,15 +153,14 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
     }
 }
 
-template <int WORDS>
-int launch_forward(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
-                   const int32_t *self_scores, const void *packed, const float *emb, int d, const float *gate_params,
-                   int hidden, float *fused_out, float *alpha_out, const unsigned long long *d_m = nullptr)
+template <int WORDS, int TPPF>
+int launch_forward_t(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                     const int32_t *self_scores, const void *packed, const float *emb, int d, const float *gate_params,
+                     int hidden, float *fused_out, float *alpha_out, const unsigned long long *d_m)
 {
-    const int cpl = (d / 4 + kTppF - 1) / kTppF;  // float4 chunks per lane
-    SqProfScope prof(ctx, SUBQUAD_PROF_FUSE);
+    const int cpl = (d / 4 + TPPF - 1) / TPPF;  // float4 chunks per lane
 #define SQ_FWD(C)                                                                                                  \
-    fuse_forward_kernel<WORDS, C><<<grid, kFuseThreads, 0, ctx->stream>>>(                                         \
+    fuse_forward_kernel<WORDS, C, TPPF><<<grid, kFuseThreads, 0, ctx->stream>>>(                                   \
         pairs, m, d_m, sw, self_scores, (const uint64_t *)packed, emb, d, gate_params, hidden, fused_out, alpha_out)
     if (cpl <= 1) SQ_FWD(1);
     else if (cpl <= 2) SQ_FWD(2);
@@ -164,6 +172,22 @@ int launch_forward(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64
 #undef SQ_FWD
     SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
+}
+
+// Lanes per pair from the context's tuning: 4 (eight pairs per warp; each lane
+// load covers half a 128-byte line of a row) or 8 (four pairs per warp; a
+// pair's eight lanes read a whole line per load).
+template <int WORDS>
+int launch_forward(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
+                   const int32_t *self_scores, const void *packed, const float *emb, int d, const float *gate_params,
+                   int hidden, float *fused_out, float *alpha_out, const unsigned long long *d_m = nullptr)
+{
+    SqProfScope prof(ctx, SUBQUAD_PROF_FUSE);
+    if (ctx->tune[SUBQUAD_TUNE_FUSE_LANES] == 8)
+        return launch_forward_t<WORDS, 8>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden,
+                                          fused_out, alpha_out, d_m);
+    return launch_forward_t<WORDS, 4>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden,
+                                      fused_out, alpha_out, d_m);
 }
 
 

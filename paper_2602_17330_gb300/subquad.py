@@ -34,6 +34,7 @@ PROF_NAMES = ["sign", "band", "band_partition", "band_group", "band_emit", "band
 
 TUNE_ALIGN_SHAPE = 0
 TUNE_BAND_PART_LOG2 = 1
+TUNE_FUSE_LANES = 2
 
 _c = ctypes
 _P = _c.c_void_p

@@ -477,11 +477,14 @@ def test_fuse_forward_within_tolerance(ctx, torch, oracle_mod, d, hidden, scale)
         emb = np.ascontiguousarray(emb * rng.uniform(0.2, 5.0, (rep.n, 1)).astype(np.float32))
     params = synth.gate_parameters(hidden, seed=hidden)
     tp = torch.from_numpy(pairs.view(np.int32)).to(ctx.device)
-    sw = ctx.align_score(packed, tp)
-    self_sc = ctx.self_scores(packed)
+    # both sides take the oracle's alignment scores (inputs of this step)
+    sw_o = oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)
+    self_o = oracle_mod.self_scores(rep.codes, rep.lens)
+    sw = torch.from_numpy(sw_o).to(ctx.device)
+    self_sc = torch.from_numpy(self_o).to(ctx.device)
     fused, alpha = ctx.fuse_forward(tp, sw, self_sc, packed, torch.from_numpy(emb), torch.from_numpy(params), hidden,
                                     want_alpha=True)
-    want = oracle_mod.fuse_forward(pairs, to_np(sw), to_np(self_sc), rep.lens, emb, params, hidden)
+    want = oracle_mod.fuse_forward(pairs, sw_o, self_o, rep.lens, emb, params, hidden)
     assert_fused_close(to_np(fused), want["fused"])
     assert_fused_close(to_np(alpha), want["alpha"])
 
@@ -501,7 +504,10 @@ def donor_1m(ctx, torch, oracle_mod):
     params = synth.gate_parameters(cfg.hidden, seed=0)
     run = pipeline.Pipeline(ctx, cfg)
     out = run.forward_numpy(rep, a, b, emb, params)
-    return dict(rep=rep, a=a, b=b, emb=emb, params=params, out=out, cfg=cfg)
+    threads = oracle_mod.host_threads()
+    sig_o = oracle_mod.sign_mt(rep.codes, rep.lens, 3, a, b, threads)
+    pairs_o = oracle_mod.candidates(sig_o, cfg.bands, cfg.rows, cfg.bucket_cap)
+    return dict(rep=rep, a=a, b=b, emb=emb, params=params, out=out, cfg=cfg, sig_o=sig_o, pairs_o=pairs_o)
 
 
 def test_full_size_signatures_sampled(donor_1m, oracle_mod):
@@ -515,8 +521,7 @@ def test_full_size_signatures_sampled(donor_1m, oracle_mod):
 
 def test_full_size_candidates_exact(donor_1m, oracle_mod):
     d = donor_1m
-    sig = oracle_mod.sign(d["rep"].codes, d["rep"].lens, 3, d["a"], d["b"])
-    want = oracle_mod.candidates(sig, d["cfg"].bands, d["cfg"].rows, d["cfg"].bucket_cap)
+    want = d["pairs_o"]
     got = d["out"]["pairs"]
     assert got.shape == want.shape and (got == want).all()
 
@@ -525,13 +530,15 @@ def test_full_size_scores_and_fusion_sampled(donor_1m, oracle_mod):
     d = donor_1m
     rep, out = d["rep"], d["out"]
     rng = np.random.default_rng(1)
-    sel = np.sort(rng.choice(out["pairs"].shape[0], 30_000, replace=False))
-    pairs = out["pairs"][sel]
-    assert (out["sw"][sel] == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)).all()
+    # the GPU's pair list equals the oracle's (test_full_size_candidates_exact);
+    # the sample and every oracle input below come from the oracle side
+    assert (out["pairs"] == d["pairs_o"]).all()
+    sel = np.sort(rng.choice(d["pairs_o"].shape[0], 30_000, replace=False))
+    pairs = d["pairs_o"][sel]
+    sw_o = oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)
+    assert (out["sw"][sel] == sw_o).all()
     assert (out["sw_plain"][sel] == out["sw"][sel]).all()
-    seqs = np.unique(pairs.ravel())
-    want_self = oracle_mod.sw_pairs(rep.codes, rep.lens, np.stack([seqs, seqs], 1))
-    assert (out["self"][seqs] == want_self).all()
-    want = oracle_mod.fuse_forward(pairs, out["sw"][sel], out["self"], rep.lens, d["emb"], d["params"],
-                                   d["cfg"].hidden)
+    self_o = oracle_mod.self_scores(rep.codes, rep.lens)
+    assert (out["self"] == self_o).all()
+    want = oracle_mod.fuse_forward(pairs, sw_o, self_o, rep.lens, d["emb"], d["params"], d["cfg"].hidden)
     assert_fused_close(out["fused"][sel], want["fused"])

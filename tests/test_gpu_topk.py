@@ -31,14 +31,17 @@ def to_np(t):
 
 
 @pytest.fixture(scope="module")
-def pooled(ctx, torch):
+def pooled(ctx, torch, oracle_mod):
+    """Pooled donors with the oracle's candidate list and scores (the inputs
+    of the retrieval step), uploaded for the GPU."""
     rep = synth.pooled_repertoire(8, 300, 3000, n_public=40, public_lo=0.3, public_hi=0.6, seed=3)
     a, b = synth.hash_coefficients(64, seed=3)
     packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 16)
-    sig = ctx.sign(packed, rep.n, 3, torch.from_numpy(a.view(np.int32)), torch.from_numpy(b.view(np.int32)), 16, 4)
-    pairs = ctx.band_candidates(sig, rep.n, 16, 4, 0)
-    scores = ctx.align_score(packed, pairs, binned=True)
-    return dict(rep=rep, packed=packed, pairs=pairs, scores=scores)
+    pairs_o = oracle_mod.candidates(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), 16, 4, 0)
+    scores_o = oracle_mod.sw_pairs(rep.codes, rep.lens, pairs_o)
+    pairs = torch.from_numpy(pairs_o.view(np.int32)).to(ctx.device)
+    scores = torch.from_numpy(scores_o).to(ctx.device)
+    return dict(rep=rep, packed=packed, pairs=pairs, scores=scores, pairs_o=pairs_o, scores_o=scores_o)
 
 
 @pytest.mark.parametrize("k", [1, 5, 50, 200])
@@ -48,8 +51,7 @@ def test_topk_candidates_against_oracle(ctx, torch, oracle_mod, pooled, k):
     ids, sc = ctx.topk_candidates(pooled["pairs"], pooled["scores"], rep.n, torch.from_numpy(rep.donor),
                                   torch.from_numpy(queries.view(np.int32)), k)
     ctx.check()
-    want_ids, want_sc = oracle_mod.topk(to_np(pooled["pairs"]).view(np.uint32), to_np(pooled["scores"]), rep.donor,
-                                        queries, k)
+    want_ids, want_sc = oracle_mod.topk(pooled["pairs_o"], pooled["scores_o"], rep.donor, queries, k)
     assert (to_np(ids).view(np.uint32) == want_ids).all()
     assert (to_np(sc) == want_sc).all()
     assert (want_sc[:, 0] >= 0).mean() > 0.1  # a good share of queries have cross-donor candidates
