@@ -2,7 +2,8 @@
 
 Each knob changes only how work is mapped onto the GB300 (never a result):
 * TUNE_ALIGN_SHAPE -- batched Smith-Waterman launch shape (256 threads x 2
-  blocks per SM with 128 registers, or 128 x 3 with 168 registers);
+  blocks per SM with 128 registers, 128 x 3 with 168 registers, or one block
+  of 384 threads per SM with split score tables);
 * TUNE_BAND_PART_LOG2 -- log2 of the target keys per hash partition of the
   banding stage (each partition is grouped by one CTA in shared memory);
 * TUNE_FUSE_LANES -- lanes per pair of the fusion forward (4 or 8).
@@ -22,7 +23,7 @@ from . import subquad
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning.json")
 
 CANDIDATES = {
-    subquad.TUNE_ALIGN_SHAPE: (0, 1),
+    subquad.TUNE_ALIGN_SHAPE: (0, 1, 2),
     subquad.TUNE_BAND_PART_LOG2: (10, 11),
     subquad.TUNE_FUSE_LANES: (4, 8),
 }

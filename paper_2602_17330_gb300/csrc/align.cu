@@ -399,10 +399,16 @@ struct TargetStream {
     }
 };
 
-template <int WORDS, int NQ>
+// SPLIT (launch shape 2): the table is staged twice, scores in the low half
+// of each word (zero above) and in the high half (zero below); a pair of
+// lookups combines with one integer multiply-add by the runtime constant
+// `unit` (= 1), and the lookup addresses are formed the same way, so this
+// arithmetic runs on the FMA pipe and leaves the ALU pipe (where the DPX and
+// packed max operations run) to the recurrence.
+template <int WORDS, int NQ, bool SPLIT = false>
 __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, const Rec<WORDS> &tP, int LtP,
                                              const Rec<WORDS> &qQ, int LqQ, const Rec<WORDS> &tQ, int LtQ,
-                                             const char *__restrict__ s_tab, int lane, int o, int e)
+                                             const char *__restrict__ s_tab, int lane, int o, int e, uint32_t unit = 1)
 {
     uint32_t qoffP[NQ], qoffQ[NQ], E[NQ], HM[NQ];
     const uint32_t neg_o = pack2(-o, -o), neg_e = pack2(-e, -e);
@@ -428,18 +434,27 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
     for (int j = 0; j < Lt; j += 2) {
         const uint32_t aP = sP.next(), aQ = sQ.next();
         const uint32_t bP = sP.next(), bQ = sQ.next();
-        const char *colAP = s_tab + (j < LtP ? aP : 20u) * (kLanes * 4);
-        const char *colAQ = s_tab + (j < LtQ ? aQ : 20u) * (kLanes * 4);
-        const char *colBP = s_tab + (j + 1 < LtP ? bP : 20u) * (kLanes * 4);
-        const char *colBQ = s_tab + (j + 1 < LtQ ? bQ : 20u) * (kLanes * 4);
+        const uint32_t offAP = (j < LtP ? aP : 20u) * (kLanes * 4);
+        const uint32_t offAQ = (j < LtQ ? aQ : 20u) * (kLanes * 4) + (SPLIT ? kTabWords * 4u : 0u);
+        const uint32_t offBP = (j + 1 < LtP ? bP : 20u) * (kLanes * 4);
+        const uint32_t offBQ = (j + 1 < LtQ ? bQ : 20u) * (kLanes * 4) + (SPLIT ? kTabWords * 4u : 0u);
+        const char *colAP = s_tab + offAP, *colAQ = s_tab + offAQ;
+        const char *colBP = s_tab + offBP, *colBQ = s_tab + offBQ;
         uint32_t dA = neg_o, upA = neg_o, FA = 0u;
         uint32_t dB = neg_o, upB = neg_o, FB = 0u;
 #pragma unroll
         for (int p = 0; p <= NQ; ++p) {
             if (p < NQ) {  // column j, row p
-                const uint32_t lo = *reinterpret_cast<const uint32_t *>(colAP + qoffP[p]);
-                const uint32_t hi = *reinterpret_cast<const uint32_t *>(colAQ + qoffQ[p]);
-                const uint32_t s_o = (lo & 0x0000ffffu) | (hi & 0xffff0000u);
+                uint32_t s_o;
+                if (SPLIT) {
+                    const uint32_t lo = *reinterpret_cast<const uint32_t *>(s_tab + (qoffP[p] * unit + offAP));
+                    const uint32_t hi = *reinterpret_cast<const uint32_t *>(s_tab + (qoffQ[p] * unit + offAQ));
+                    s_o = hi * unit + lo;
+                } else {
+                    const uint32_t lo = *reinterpret_cast<const uint32_t *>(colAP + qoffP[p]);
+                    const uint32_t hi = *reinterpret_cast<const uint32_t *>(colAQ + qoffQ[p]);
+                    s_o = (lo & 0x0000ffffu) | (hi & 0xffff0000u);
+                }
                 const uint32_t e_new = __viaddmax_s16x2_relu(E[p], neg_e, HM[p]);
                 FA = __viaddmax_s16x2_relu(FA, neg_e, upA);
                 const uint32_t h = __viaddmax_s16x2_relu(dA, s_o, __vmaxs2(e_new, FA));
@@ -451,9 +466,16 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
             }
             if (p >= 1) {  // column j + 1, row p - 1
                 const int r = p >= 1 ? p - 1 : 0;
-                const uint32_t lo = *reinterpret_cast<const uint32_t *>(colBP + qoffP[r]);
-                const uint32_t hi = *reinterpret_cast<const uint32_t *>(colBQ + qoffQ[r]);
-                const uint32_t s_o = (lo & 0x0000ffffu) | (hi & 0xffff0000u);
+                uint32_t s_o;
+                if (SPLIT) {
+                    const uint32_t lo = *reinterpret_cast<const uint32_t *>(s_tab + (qoffP[r] * unit + offBP));
+                    const uint32_t hi = *reinterpret_cast<const uint32_t *>(s_tab + (qoffQ[r] * unit + offBQ));
+                    s_o = hi * unit + lo;
+                } else {
+                    const uint32_t lo = *reinterpret_cast<const uint32_t *>(colBP + qoffP[r]);
+                    const uint32_t hi = *reinterpret_cast<const uint32_t *>(colBQ + qoffQ[r]);
+                    s_o = (lo & 0x0000ffffu) | (hi & 0xffff0000u);
+                }
                 const uint32_t e_new = __viaddmax_s16x2_relu(E[r], neg_e, HM[r]);
                 FB = __viaddmax_s16x2_relu(FB, neg_e, upB);
                 const uint32_t h = __viaddmax_s16x2_relu(dB, s_o, __vmaxs2(e_new, FB));
@@ -470,11 +492,15 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
 
 // Launch shapes of the batched kernel: 0 = 256 threads, 2 blocks per SM (128
 // registers); 1 = 128 threads, 3 blocks per SM (168 registers, no spills up
-// to 24 rows).  Chosen by the context's tuning (see subquad_set_tuning).
+// to 24 rows); 2 = one block of 384 threads per SM (168 registers) sharing
+// the two staged tables of the split lookup.  Chosen by the context's tuning
+// (see subquad_set_tuning).
 template <int CFG>
 struct BinnedShape {
-    static constexpr int threads = CFG == 0 ? 256 : 128;
-    static constexpr int blocks = CFG == 0 ? 2 : 3;
+    static constexpr int threads = CFG == 0 ? 256 : CFG == 1 ? 128 : 384;
+    static constexpr int blocks = CFG == 0 ? 2 : CFG == 1 ? 3 : 1;
+    static constexpr bool split = CFG == 2;  // two staged tables (see sw_pair2)
+    static constexpr int tables = split ? 2 : 1;
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
@@ -517,20 +543,27 @@ template <int WORDS, bool SELF, int CFG>
 __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::blocks)
     align_binned_kernel(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs,
                         const uint32_t *__restrict__ order, int64_t m_max, const unsigned long long *__restrict__ d_m,
-                        const int32_t *__restrict__ table, int o, int e, bool symmetric, int32_t *__restrict__ out)
+                        const int32_t *__restrict__ table, int o, int e, bool symmetric, int32_t *__restrict__ out,
+                        uint32_t unit)
 {
     extern __shared__ int32_t s_tab_words[];
     const int64_t m = items(m_max, d_m);
     // each staged word holds its 16-bit score in both halves, so the two
     // pairs' scores combine with one bitwise select (low half of the first
-    // word, high half of the second)
+    // word, high half of the second); the split shape stages the low halves
+    // and the high halves as two tables instead
+    constexpr bool kSplit = BinnedShape<CFG>::split;
     for (int q = threadIdx.x; q < kTabWords / 4; q += blockDim.x) {
-        int4 v = reinterpret_cast<const int4 *>(table)[q];
-        v.x = (int32_t)(((uint32_t)v.x & 0xffffu) * 0x10001u);
-        v.y = (int32_t)(((uint32_t)v.y & 0xffffu) * 0x10001u);
-        v.z = (int32_t)(((uint32_t)v.z & 0xffffu) * 0x10001u);
-        v.w = (int32_t)(((uint32_t)v.w & 0xffffu) * 0x10001u);
-        reinterpret_cast<int4 *>(s_tab_words)[q] = v;
+        const int4 v = reinterpret_cast<const int4 *>(table)[q];
+        const uint32_t x = (uint32_t)v.x & 0xffffu, y = (uint32_t)v.y & 0xffffu, z = (uint32_t)v.z & 0xffffu,
+                       w = (uint32_t)v.w & 0xffffu;
+        if (kSplit) {
+            reinterpret_cast<uint4 *>(s_tab_words)[q] = make_uint4(x, y, z, w);
+            reinterpret_cast<uint4 *>(s_tab_words + kTabWords)[q] = make_uint4(x << 16, y << 16, z << 16, w << 16);
+        } else {
+            reinterpret_cast<uint4 *>(s_tab_words)[q] = make_uint4(x * 0x10001u, y * 0x10001u, z * 0x10001u,
+                                                                   w * 0x10001u);
+        }
     }
     __syncthreads();
     const char *s_tab = reinterpret_cast<const char *>(s_tab_words);
@@ -545,7 +578,8 @@ __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::b
     // base + 32 + lane in the high halves); the records of iteration k+1 are
     // copied with cp.async while iteration k computes, and the ids of
     // iteration k+2 are loaded meanwhile.  A thread reads only what it copied.
-    Rec<WORDS> *buf = reinterpret_cast<Rec<WORDS> *>(s_tab_words + kTabWords) + threadIdx.x * 8;
+    Rec<WORDS> *buf =
+        reinterpret_cast<Rec<WORDS> *>(s_tab_words + BinnedShape<CFG>::tables * kTabWords) + threadIdx.x * 8;
     auto issue = [&](int slot, uint4 idP, uint4 idQ) {
         Rec<WORDS> *d = buf + slot * 4;
         if (idP.w) {
@@ -606,28 +640,29 @@ __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::b
                 switch (wmax) {
 #define SQ_EXACT(N)                                                                                                \
     case N:                                                                                                        \
-        sc = sw_pair2<WORDS, (N <= MAXLEN ? N : MAXLEN)>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e);      \
+        sc = sw_pair2<WORDS, (N <= MAXLEN ? N : MAXLEN), kSplit>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, \
+                                                                e, unit);                                          \
         break;
                     SQ_EXACT(7) SQ_EXACT(8) SQ_EXACT(9) SQ_EXACT(10) SQ_EXACT(11) SQ_EXACT(12) SQ_EXACT(13)
                     SQ_EXACT(14) SQ_EXACT(15) SQ_EXACT(16) SQ_EXACT(17) SQ_EXACT(18) SQ_EXACT(19) SQ_EXACT(20)
                     SQ_EXACT(21) SQ_EXACT(22) SQ_EXACT(23)
 #undef SQ_EXACT
                 default:
-                    sc = sw_pair2<WORDS, MAXLEN>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e);
+                    sc = sw_pair2<WORDS, MAXLEN, kSplit>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e, unit);
                     break;
                 }
             } else {
                 switch ((wmax + 1) >> 1) {
 #define SQ_CASE(H)                                                                                                 \
     case H:                                                                                                        \
-        sc = sw_pair2<WORDS, (H < 1 ? 2 : (2 * H <= MAXLEN ? 2 * H : MAXLEN))>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ,  \
-                                                                              s_tab, lane, o, e);                   \
+        sc = sw_pair2<WORDS, (H < 1 ? 2 : (2 * H <= MAXLEN ? 2 * H : MAXLEN)), kSplit>(                            \
+            AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e, unit);                                          \
         break;
                     SQ_CASE(0) SQ_CASE(1) SQ_CASE(2) SQ_CASE(3) SQ_CASE(4) SQ_CASE(5) SQ_CASE(6) SQ_CASE(7)
                     SQ_CASE(8) SQ_CASE(9) SQ_CASE(10) SQ_CASE(11) SQ_CASE(12)
 #undef SQ_CASE
                 default:
-                    sc = sw_pair2<WORDS, MAXLEN>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e);
+                    sc = sw_pair2<WORDS, MAXLEN, kSplit>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, o, e, unit);
                     break;
                 }
             }
@@ -686,7 +721,8 @@ int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const u
 #define SQ_BINNED(W, C)                                                                                            \
     do {                                                                                                           \
         auto k = align_binned_kernel<W, SELF, C>;                                                                  \
-        const size_t smem = sizeof(int32_t) * kTabWords + sizeof(uint64_t) * W * 8 * BinnedShape<C>::threads;      \
+        const size_t smem = sizeof(int32_t) * kTabWords * BinnedShape<C>::tables +                                \
+                            sizeof(uint64_t) * W * 8 * BinnedShape<C>::threads;                                    \
         static std::mutex attr_mutex;                                                                              \
         static bool attr_set[64] = {};                                                                             \
         const bool slot_ok = ctx->device >= 0 && ctx->device < 64;                                                 \
@@ -704,15 +740,17 @@ int launch_binned(subquad_ctx *ctx, const void *packed, int pack_stride, const u
         }                                                                                                          \
         const unsigned grid = sq_grid(ctx, (m + 1) / 2, BinnedShape<C>::threads, BinnedShape<C>::blocks);         \
         k<<<grid, BinnedShape<C>::threads, smem, ctx->stream>>>(pk, pairs, order, m, d_m, ctx->d_table, o, e,      \
-                                                               ctx->matrix_symmetric, out);                        \
+                                                               ctx->matrix_symmetric, out, 1u);                    \
     } while (0)
     const int cfg = ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE];
     if (pack_stride == 16) {
         if (cfg == 0) SQ_BINNED(2, 0);
-        else SQ_BINNED(2, 1);
+        else if (cfg == 1) SQ_BINNED(2, 1);
+        else SQ_BINNED(2, 2);
     } else {
         if (cfg == 0) SQ_BINNED(4, 0);
-        else SQ_BINNED(4, 1);
+        else if (cfg == 1) SQ_BINNED(4, 1);
+        else SQ_BINNED(4, 2);
     }
 #undef SQ_BINNED
     SQ_LAUNCH_CHECK();

@@ -226,7 +226,7 @@ int sq_scratch_reserve(subquad_ctx *ctx, size_t bytes)
 extern "C" int subquad_set_tuning(subquad_ctx *ctx, int key, int value)
 {
     if (!ctx || key < 0 || key >= SUBQUAD_TUNE_COUNT) return SUBQUAD_ERR_ARG;
-    if (key == SUBQUAD_TUNE_ALIGN_SHAPE && (value < 0 || value > 1)) return SUBQUAD_ERR_ARG;
+    if (key == SUBQUAD_TUNE_ALIGN_SHAPE && (value < 0 || value > 2)) return SUBQUAD_ERR_ARG;
     if (key == SUBQUAD_TUNE_BAND_PART_LOG2 && (value < 6 || value > 16)) return SUBQUAD_ERR_ARG;
     if (key == SUBQUAD_TUNE_FUSE_LANES && value != 4 && value != 8) return SUBQUAD_ERR_ARG;
     ctx->tune[key] = value;

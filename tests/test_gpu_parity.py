@@ -415,7 +415,7 @@ def test_self_scores_both_paths(ctx, torch, oracle_mod, binned):
         ctx.set_matrix(None)
 
 
-@pytest.mark.parametrize("shape", [0, 1])
+@pytest.mark.parametrize("shape", [0, 1, 2])
 @pytest.mark.parametrize("stride,maker", [(16, "donor"), (32, "zipf")])
 def test_align_binned_launch_shapes(ctx, torch, oracle_mod, shape, stride, maker):
     from paper_2602_17330_gb300 import subquad
@@ -434,6 +434,29 @@ def test_align_binned_launch_shapes(ctx, torch, oracle_mod, shape, stride, maker
         ctx.set_tuning(subquad.TUNE_ALIGN_SHAPE, old)
     assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs)).all()
     assert (self_got == oracle_mod.self_scores(rep.codes, rep.lens)).all()
+
+
+@pytest.mark.parametrize("o,e", [(0, 0), (1000, 1000), (11, 1), (3, 2)])
+def test_align_split_shape_gaps_and_matrix(ctx, torch, oracle_mod, o, e):
+    """The split-table launch shape with extreme gap costs and an asymmetric
+    matrix spanning the allowed score range (negative staged values)."""
+    from paper_2602_17330_gb300 import subquad
+
+    rep = synth.zipf_repertoire(4000, seed=o + e, hi=200)
+    packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 32)
+    rng = np.random.default_rng(o + 7 * e)
+    pairs = rng.integers(0, rep.n, (9_999, 2)).astype(np.uint32)
+    tp = torch.from_numpy(pairs.view(np.int32)).to(ctx.device)
+    M = rng.integers(-64, 64, (20, 20)).astype(np.int32)
+    old = ctx.get_tuning(subquad.TUNE_ALIGN_SHAPE)
+    try:
+        ctx.set_tuning(subquad.TUNE_ALIGN_SHAPE, 2)
+        ctx.set_matrix(M.reshape(-1).tolist())
+        got = to_np(ctx.align_score(packed, tp, o, e, binned=True))
+    finally:
+        ctx.set_matrix(None)
+        ctx.set_tuning(subquad.TUNE_ALIGN_SHAPE, old)
+    assert (got == oracle_mod.sw_pairs(rep.codes, rep.lens, pairs, o, e, M)).all()
 
 
 def test_autotune_picks_a_candidate_and_keeps_results(ctx, torch, oracle_mod):
