@@ -458,6 +458,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if args.configs:
             configs = {}
             for name, fn in (("config4_trajectory", lambda: run_config4_trajectory(args, ctx, stream, rep, step_pipe, m)),
+                             ("recall_vs_band_shape", lambda: run_recall_sweep(args, ctx, stream)),
                              ("config5_full", lambda: run_config5(args, ctx, stream, flush))):
                 try:
                     configs[name] = fn()
@@ -777,6 +778,85 @@ def graph_step(ctx, stream, pairs, fused, n, donor=None, num_donors=0):
     return out
 
 
+def kmer_jaccard_of(rep, pairs, k: int = 3):
+    """Exact k-mer Jaccard index of each (i, j) in pairs (host; small lists)."""
+    import numpy as np
+
+    cache = {}
+
+    def kset(r):
+        if r not in cache:
+            c = rep.codes[r]
+            cache[r] = {tuple(c[p:p + k]) for p in range(int(rep.lens[r]) - k + 1)}
+        return cache[r]
+
+    return np.array([len(kset(int(i)) & kset(int(j))) / max(1, len(kset(int(i)) | kset(int(j)))) for i, j in pairs])
+
+
+def banding_explains(rep, queries, ids, bands: int, rows: int, sample: int = 200):
+    """The exhaustive top-k partners of `sample` queries: their exact 3-mer
+    Jaccard index J and the banding's catch probability 1 - (1 - J^rows)^bands
+    (over the hash draw); its mean is the recall the band shape can give."""
+    import numpy as np
+
+    q = queries[:sample]
+    pr = [(int(a), int(b)) for a, row in zip(q, ids[:sample]) for b in row if b != 0xFFFFFFFF]
+    J = kmer_jaccard_of(rep, pr)
+    P = 1.0 - (1.0 - J ** rows) ** bands
+    return {"pairs": len(pr), "jaccard_mean": float(J.mean()), "jaccard_p90": float(np.percentile(J, 90)),
+            "catch_probability_mean": float(P.mean())}
+
+
+def run_recall_sweep(args, ctx, stream):
+    """Recall@50 of cross-donor retrieval against the band shape, on the
+    16-donor pool (2.2M sequences, 500 public families) with the same 64 hash
+    functions grouped as 16 bands of 4 rows or 32 bands of 2 (no cap), on 1,000
+    public-family queries and 1,000 random queries, beside the banding's catch
+    probability of the exhaustive top-50 partners."""
+    import numpy as np
+    import torch
+
+    from paper_2602_17330_gb300 import pipeline, synth
+
+    rep = synth.pooled_repertoire(16, 50_000, 200_000, seed=5)
+    a, b = synth.hash_coefficients(64, seed=5)
+    public = np.flatnonzero((rep.family >= 0) & (rep.family < 500))
+    rng = np.random.default_rng(5)
+    q_pub = np.sort(rng.choice(public, size=min(1000, public.size), replace=False)).astype(np.uint32)
+    q_rnd = np.sort(rng.choice(rep.n, size=1000, replace=False)).astype(np.uint32)
+    out = {"workload": f"{rep.n:,} sequences pooled from 16 donors, 500 public families"}
+    with torch.cuda.stream(stream):
+        donor = torch.from_numpy(rep.donor).to(ctx.device)
+        codes, lens = torch.from_numpy(rep.codes).to(ctx.device), torch.from_numpy(rep.lens).to(ctx.device)
+        packed = ctx.pack(codes, lens, 16)
+        best = {}
+        for name, q in (("public", q_pub), ("random", q_rnd)):
+            ids_b, sc_b = ctx.topk_bruteforce(packed, donor, torch.from_numpy(q.view(np.int32)).to(ctx.device), 50)
+            best[name] = (ids_b.cpu().numpy().view(np.uint32), sc_b.cpu().numpy())
+        for bands, rows in ((16, 4), (32, 2)):
+            sig = ctx.sign(packed, rep.n, 3, torch.from_numpy(a.view(np.int32)).to(ctx.device),
+                           torch.from_numpy(b.view(np.int32)).to(ctx.device), bands, rows)
+            count = sum(int(bt.shape[0]) for bt in ctx.band_stream(sig, rep.n, bands, rows, 0, capacity=1 << 26))
+            res = {"candidate_pairs": count}
+            if count < 1_500_000_000:
+                pairs = ctx.band_candidates(sig, rep.n, bands, rows, 0, capacity=count + 1)
+                scores = ctx.align_score(packed, pairs, binned=True)
+                index = ctx.pair_index(pairs, rep.n)
+                for name, q in (("public", q_pub), ("random", q_rnd)):
+                    _, sc = ctx.topk_candidates(pairs, scores, rep.n, donor,
+                                                torch.from_numpy(q.view(np.int32)).to(ctx.device), 50, index=index)
+                    got = sc.cpu().numpy()
+                    thr = best[name][1][:, 49]
+                    hit = ((got >= thr[:, None]) & (got >= 0)).sum(1)
+                    res[f"recall_at_50_{name}"] = float(np.minimum(hit, 50).mean() / 50.0)
+                    res[f"explained_{name}"] = banding_explains(rep, q, best[name][0], bands, rows)
+                del pairs, scores, index
+            out[f"{bands}x{rows}"] = res
+        stream.synchronize()
+    ctx.check()
+    return out
+
+
 def run_config5(args, ctx, stream, flush):
     """The many-repertoire batch at its stated size: 64 donors of log-uniform
     sizes in 5e4..2e6, 500 public families; one batched pass (pack, sign,
@@ -843,7 +923,7 @@ def run_config5(args, ctx, stream, flush):
         sub_idx = np.sort(np.random.default_rng(5).choice(q_np.size, 10_000, replace=False))
         sub = torch.from_numpy(q_np[sub_idx].view(np.int32)).to(ctx.device)
         e4.record(stream)
-        _, sc_b = ctx.topk_bruteforce(bp.packed, donor, sub, 50)
+        ids_b, sc_b = ctx.topk_bruteforce(bp.packed, donor, sub, 50)
         e5.record(stream)
         stream.synchronize()
     ctx.check()
@@ -855,6 +935,7 @@ def run_config5(args, ctx, stream, flush):
     public = (rep.family[q_np[sub_idx]] >= 0) & (rep.family[q_np[sub_idx]] < 500)
     rec_pub = float(np.minimum(hit[public], 50).mean() / 50.0) if public.any() else None
     cells = pipeline.cells_of(rep.lens, pairs.cpu().numpy().view(np.uint32))
+    explained = banding_explains(rep, q_np[sub_idx], ids_b.cpu().numpy().view(np.uint32), cfg.bands, cfg.rows)
     g = graph_step(ctx, stream, pairs, bp.fused[:mq], rep.n, donor=donor, num_donors=64)
     return {"workload": f"{rep.n:,} sequences pooled from 64 donors (log-uniform 5e4-2e6), 500 public families "
                         "(total public fraction log-uniform 1e-4..1e-2 per donor); 64 hashes in 16x4 bands, cap 2048",
@@ -864,6 +945,7 @@ def run_config5(args, ctx, stream, flush):
             "topk_100k_queries_ms": e2.elapsed_time(e3), "bruteforce_10k_queries_ms": e4.elapsed_time(e5),
             "recall_at_50": recall, "recall_at_50_public_queries": rec_pub, "public_queries_in_sample": int(public.sum()),
             "queries_with_cross_donor_candidates": float((got[:, 0] >= 0).mean()), "graph": g,
+            "recall_explained": explained,
             "recall_note": "tie-aware recall@50 of the candidate route against the exhaustive top-50 among other "
                            "donors' sequences, on a seeded 10,000-query subsample of the 100,000 queries"}
 

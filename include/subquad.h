@@ -81,9 +81,9 @@ int64_t subquad_launch_count(const subquad_ctx *ctx);
 /* Tuning knobs (no counterpart in the paper: launch shapes chosen per device
  * by measurement, e.g. by the package's autotuner).  Host-only; they take
  * effect for later calls and never change results.
- *   SUBQUAD_TUNE_ALIGN_SHAPE: batched alignment launch shape, 0 = 256 threads
- *     x 2 blocks per SM, 1 = 128 threads x 3 blocks per SM (default 1), 2 =
- *     384 threads x 1 block per SM with split score tables;
+ *   SUBQUAD_TUNE_ALIGN_SHAPE: batched alignment and edit-distance launch
+ *     shape, 0 = 256 threads x 2 blocks per SM, 1 = 128 threads x 3 blocks per
+ *     SM, 2 = 384 threads x 1 block per SM with split score tables (default 2);
  *   SUBQUAD_TUNE_BAND_PART_LOG2: log2 of the target number of (band, sequence)
  *     keys per hash partition of the banding stage, 6..16 (default 11); each
  *     partition is grouped by one CTA in shared memory;

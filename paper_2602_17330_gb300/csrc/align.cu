@@ -923,10 +923,11 @@ int ensure_edit_table(subquad_ctx *ctx)
     return SUBQUAD_OK;
 }
 
-template <int WORDS, int NQ>
+// SPLIT: the cost table staged as low halves and high halves (see sw_pair2).
+template <int WORDS, int NQ, bool SPLIT = false>
 __device__ __forceinline__ uint32_t ed_pair2(const Rec<WORDS> &qP, int LqP, const Rec<WORDS> &tP, int LtP,
                                              const Rec<WORDS> &qQ, int LqQ, const Rec<WORDS> &tQ, int LtQ,
-                                             const char *__restrict__ s_tab, int lane, int indel)
+                                             const char *__restrict__ s_tab, int lane, int indel, uint32_t unit = 1)
 {
     uint32_t qoffP[NQ], qoffQ[NQ], D[NQ], vc[NQ];
     uint32_t acc = 0u;
@@ -947,17 +948,25 @@ __device__ __forceinline__ uint32_t ed_pair2(const Rec<WORDS> &qP, int LqP, cons
     uint32_t top = 0u;  // D(0, y)
     for (int j = 0; j < Lt; ++j) {
         const uint32_t aP = sP.next(), aQ = sQ.next();
-        const char *colP = s_tab + (j < LtP ? aP : 20u) * (kLanes * 4);
-        const char *colQ = s_tab + (j < LtQ ? aQ : 20u) * (kLanes * 4);
+        const uint32_t offP = (j < LtP ? aP : 20u) * (kLanes * 4);
+        const uint32_t offQ = (j < LtQ ? aQ : 20u) * (kLanes * 4) + (SPLIT ? kEdWords * 4u : 0u);
+        const char *colP = s_tab + offP, *colQ = s_tab + offQ;
         const uint32_t hc = pack2(j < LtP ? indel : 0, j < LtQ ? indel : 0);
         uint32_t diag = top;
         top = __vadd2(top, hc);
         uint32_t up = top;
 #pragma unroll
         for (int p = 0; p < NQ; ++p) {
-            const uint32_t lo = *reinterpret_cast<const uint32_t *>(colP + qoffP[p]);
-            const uint32_t hi = *reinterpret_cast<const uint32_t *>(colQ + qoffQ[p]);
-            const uint32_t sub = (lo & 0x0000ffffu) | (hi & 0xffff0000u);
+            uint32_t sub;
+            if (SPLIT) {
+                const uint32_t lo = *reinterpret_cast<const uint32_t *>(s_tab + (qoffP[p] * unit + offP));
+                const uint32_t hi = *reinterpret_cast<const uint32_t *>(s_tab + (qoffQ[p] * unit + offQ));
+                sub = hi * unit + lo;
+            } else {
+                const uint32_t lo = *reinterpret_cast<const uint32_t *>(colP + qoffP[p]);
+                const uint32_t hi = *reinterpret_cast<const uint32_t *>(colQ + qoffQ[p]);
+                sub = (lo & 0x0000ffffu) | (hi & 0xffff0000u);
+            }
             const uint32_t t = __vadd2(diag, sub);
             const uint32_t mleft = __viaddmin_s16x2(D[p], hc, t);
             const uint32_t d = __viaddmin_s16x2(up, vc[p], mleft);
@@ -973,12 +982,22 @@ template <int WORDS, int CFG>
 __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::blocks)
     edit_binned_kernel(const uint64_t *__restrict__ packed, const uint32_t *__restrict__ pairs,
                        const uint32_t *__restrict__ order, int64_t m_max, const unsigned long long *__restrict__ d_m,
-                       const uint32_t *__restrict__ table, int indel, int32_t *__restrict__ out)
+                       const uint32_t *__restrict__ table, int indel, int32_t *__restrict__ out, uint32_t unit)
 {
     extern __shared__ int32_t s_tab_words[];
     const int64_t m = items(m_max, d_m);
-    for (int q = threadIdx.x; q < kEdWords / 4; q += blockDim.x)
-        reinterpret_cast<int4 *>(s_tab_words)[q] = reinterpret_cast<const int4 *>(table)[q];
+    constexpr bool kSplit = BinnedShape<CFG>::split;
+    for (int q = threadIdx.x; q < kEdWords / 4; q += blockDim.x) {
+        const uint4 v = reinterpret_cast<const uint4 *>(table)[q];  // cost in both halves
+        if (kSplit) {
+            reinterpret_cast<uint4 *>(s_tab_words)[q] =
+                make_uint4(v.x & 0xffffu, v.y & 0xffffu, v.z & 0xffffu, v.w & 0xffffu);
+            reinterpret_cast<uint4 *>(s_tab_words + kEdWords)[q] =
+                make_uint4(v.x << 16, v.y << 16, v.z << 16, v.w << 16);
+        } else {
+            reinterpret_cast<uint4 *>(s_tab_words)[q] = v;
+        }
+    }
     __syncthreads();
     const char *s_tab = reinterpret_cast<const char *>(s_tab_words);
     constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
@@ -987,7 +1006,8 @@ __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::b
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t stride = nwarps * 64;
     // the record double buffer of the batched alignment kernel (see there)
-    Rec<WORDS> *buf = reinterpret_cast<Rec<WORDS> *>(s_tab_words + kEdWords) + threadIdx.x * 8;
+    Rec<WORDS> *buf =
+        reinterpret_cast<Rec<WORDS> *>(s_tab_words + BinnedShape<CFG>::tables * kEdWords) + threadIdx.x * 8;
     auto issue = [&](int slot, uint4 idP, uint4 idQ) {
         Rec<WORDS> *dst = buf + slot * 4;
         if (idP.w) {
@@ -1044,14 +1064,14 @@ __global__ void __launch_bounds__(BinnedShape<CFG>::threads, BinnedShape<CFG>::b
             switch ((wmax + 1) >> 1) {
 #define SQ_ED(H)                                                                                                   \
     case H:                                                                                                        \
-        dist = ed_pair2<WORDS, (H < 1 ? 2 : (2 * H <= MAXLEN ? 2 * H : MAXLEN))>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, \
-                                                                                s_tab, lane, indel);               \
+        dist = ed_pair2<WORDS, (H < 1 ? 2 : (2 * H <= MAXLEN ? 2 * H : MAXLEN)), kSplit>(                          \
+            AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, indel, unit);                                         \
         break;
                 SQ_ED(0) SQ_ED(1) SQ_ED(2) SQ_ED(3) SQ_ED(4) SQ_ED(5) SQ_ED(6) SQ_ED(7) SQ_ED(8) SQ_ED(9) SQ_ED(10)
                 SQ_ED(11) SQ_ED(12)
 #undef SQ_ED
             default:
-                dist = ed_pair2<WORDS, MAXLEN>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, indel);
+                dist = ed_pair2<WORDS, MAXLEN, kSplit>(AP, LaP, BP, LbP, AQ, LaQ, BQ, LbQ, s_tab, lane, indel, unit);
                 break;
             }
             out[curP.z] = (int32_t)(dist & 0xffffu);
@@ -1075,19 +1095,22 @@ int launch_edit(subquad_ctx *ctx, const void *packed, int pack_stride, const uin
 #define SQ_EDL(W, C)                                                                                               \
     do {                                                                                                           \
         auto k = edit_binned_kernel<W, C>;                                                                         \
-        const size_t smem = sizeof(uint32_t) * kEdWords + sizeof(uint64_t) * W * 8 * BinnedShape<C>::threads;      \
+        const size_t smem = sizeof(uint32_t) * kEdWords * BinnedShape<C>::tables +                                \
+                            sizeof(uint64_t) * W * 8 * BinnedShape<C>::threads;                                    \
         SQ_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));             \
         const unsigned grid = sq_grid(ctx, (m + 1) / 2, BinnedShape<C>::threads, BinnedShape<C>::blocks);         \
         k<<<grid, BinnedShape<C>::threads, smem, ctx->stream>>>(pk, pairs, order, m, d_m, ctx->d_edit_table,       \
-                                                               ctx->edit_indel, out);                             \
+                                                               ctx->edit_indel, out, 1u);                         \
     } while (0)
     const int cfg = ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE];
     if (pack_stride == 16) {
         if (cfg == 0) SQ_EDL(2, 0);
-        else SQ_EDL(2, 1);
+        else if (cfg == 1) SQ_EDL(2, 1);
+        else SQ_EDL(2, 2);
     } else {
         if (cfg == 0) SQ_EDL(4, 0);
-        else SQ_EDL(4, 1);
+        else if (cfg == 1) SQ_EDL(4, 1);
+        else SQ_EDL(4, 2);
     }
 #undef SQ_EDL
     SQ_LAUNCH_CHECK();

@@ -78,7 +78,7 @@ extern "C" int subquad_create(subquad_ctx **out, int device, void *cuda_stream)
     sq_default_edit_costs(ctx->h_edit_sub);
     ctx->edit_indel = 2;
     for (int k = 0; k < SUBQUAD_TUNE_COUNT; ++k) ctx->tune[k] = 0;
-    ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE] = 1;
+    ctx->tune[SUBQUAD_TUNE_ALIGN_SHAPE] = 2;
     ctx->tune[SUBQUAD_TUNE_BAND_PART_LOG2] = 11;
     ctx->tune[SUBQUAD_TUNE_FUSE_LANES] = 4;
     SqDeviceGuard guard(ctx);

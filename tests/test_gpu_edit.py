@@ -48,9 +48,10 @@ def test_edit_all_pairs_tiny_bitexact(ctx, torch, oracle_mod):
     assert (got == oracle_mod.edit_pairs(rep.codes, rep.lens, pairs)).all()
 
 
+@pytest.mark.parametrize("shape", [0, 1, 2])
 @pytest.mark.parametrize("m", [1, 31, 33, 64, 65, 1000, 4097])
 @pytest.mark.parametrize("stride", [16, 32])
-def test_edit_ragged_counts_and_lengths(ctx, torch, oracle_mod, m, stride):
+def test_edit_ragged_counts_and_lengths(ctx, torch, oracle_mod, m, stride, shape):
     """Random pairs of lengths 1..max (a thread's two pairs differ in both
     lengths, so the transparent padding is exercised), both record sizes."""
     rng = np.random.default_rng(m + stride)
@@ -62,8 +63,15 @@ def test_edit_ragged_counts_and_lengths(ctx, torch, oracle_mod, m, stride):
         codes[r, : lens[r]] = rng.integers(0, 20, lens[r])
     rep = synth.Repertoire(codes, lens, np.full(n, -1, np.int32), np.zeros(n, np.int32), np.ones(20) / 20)
     pairs = rng.integers(0, n, (m, 2)).astype(np.uint32)
+    from paper_2602_17330_gb300 import subquad
+
     ctx.set_edit_costs()
-    got = run(ctx, torch, rep, pairs, stride)
+    old = ctx.get_tuning(subquad.TUNE_ALIGN_SHAPE)
+    try:
+        ctx.set_tuning(subquad.TUNE_ALIGN_SHAPE, shape)
+        got = run(ctx, torch, rep, pairs, stride)
+    finally:
+        ctx.set_tuning(subquad.TUNE_ALIGN_SHAPE, old)
     assert (got == oracle_mod.edit_pairs(codes, lens, pairs)).all()
 
 
