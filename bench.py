@@ -444,6 +444,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             times.append((e0, e1))
         stream.synchronize()
         sw_ms["edit"] = statistics.mean(a.elapsed_time(b) for a, b in times)
+        # three-channel fusion (alignment, embedding cosine, MinHash Jaccard) on the same pairs
+        params3 = torch.from_numpy(synth.gate_parameters_mc(cfg.hidden, 3, seed=0)).to(dev)
+        f3 = torch.empty((m,), dtype=torch.float32, device=dev)
+        times = []
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.fuse_forward_mc(out["pairs"], out["sw"], out["self"], out["packed"], x["emb"], out["sig"], params3,
+                                cfg.hidden, 3, out=f3)
+            e1.record(stream)
+            times.append((e0, e1))
+        stream.synchronize()
+        sw_ms["fuse_mc"] = statistics.mean(a.elapsed_time(b) for a, b in times)
 
     stream_res = train_res = topk_res = graph_res = configs = None
     if rank == 0 and world == 1:
@@ -551,6 +565,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "sw_gcups": gcups, "sw_frac_of_int_peak": gcups * SW_OPS_PER_CELL / alu_peak,
             "sw_gcups_plain": cells / (sw_ms["plain"] / 1e3) / 1e9,
             "sw_gcups_binned": cells / (sw_ms["binned"] / 1e3) / 1e9,
+            "fuse_mc": {"ms": sw_ms["fuse_mc"], "pairs_per_s": m / (sw_ms["fuse_mc"] / 1e3),
+                        "hbm_frac": (16.0 * m + cfg.n * (4.0 * cfg.d + 4 + cfg.pack_stride + 4.0 * cfg.hashes))
+                        / (sw_ms["fuse_mc"] / 1e3) / 1e9 / hbm_peak,
+                        "note": "three-channel gated fusion (Eq. wm at M = 3, the MinHash Jaccard channel from the "
+                                "signatures); algorithmic bytes 16 per pair + each sequence's embedding row, "
+                                "self-score, record and signature once"},
             "edit": {"gcups": cells / (sw_ms["edit"] / 1e3) / 1e9, "ms": sw_ms["edit"],
                      "frac_of_int_peak": cells * ED_OPS_PER_CELL / (sw_ms["edit"] / 1e3) / 1e9 / alu_peak,
                      "note": f"edit distance of every candidate pair (length binning + edit_binned_kernel), "
