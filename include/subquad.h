@@ -444,15 +444,23 @@ int subquad_adam_step(subquad_ctx *ctx, float *param, const float *grad, float *
  * keeps logit 0; w = softmax of the M logits; fused = sum_m w_m a_m.
  * gate_params: device float [(2M+1) hidden + M - 1] = W1 [hidden][M+1]
  * row-major, b1 [hidden], W2 [M-1][hidden] row-major, b2 [M-1] (for M = 2
- * exactly the layout of subquad_fuse_forward).  sig: device uint32
- * [bands][n][rows] as written by subquad_sign (16-byte aligned when rows ==
- * 4; ignored for M = 2).  weights_out: device float [m][M] or NULL.  Other
- * arguments as subquad_fuse_forward; channels is 2 or 3, 1 <= rows <= 8,
- * bands*rows <= 512. */
+ * exactly the layout of subquad_fuse_forward).  sig_seq: device uint32
+ * [n][hashes], the signatures sequence-major (subquad_sig_sequence_major),
+ * 16-byte aligned when hashes % 4 == 0; 1 <= hashes <= 512; ignored for M = 2
+ * (may be NULL).  weights_out: device float [m][M] or NULL.  Other arguments
+ * as subquad_fuse_forward; channels is 2 or 3. */
 int subquad_fuse_forward_mc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
                             const int32_t *self_scores, const void *packed, int pack_stride, const float *emb, int d,
-                            const uint32_t *sig, int64_t n, int bands, int rows, const float *gate_params, int hidden,
-                            int channels, float *fused_out, float *weights_out);
+                            const uint32_t *sig_seq, int hashes, const float *gate_params, int hidden, int channels,
+                            float *fused_out, float *weights_out);
+
+/* The signatures of subquad_sign ([bands][n][rows], the banding layout)
+ * rewritten sequence-major, sig_seq_out[i][b*rows + r] = sig[b][i][r]
+ * (device uint32 [n][bands*rows]; both 16-byte aligned when rows == 4), so a
+ * sequence's whole sketch is one contiguous row for per-pair gathers (the
+ * Jaccard channel of subquad_fuse_forward_mc). */
+int subquad_sig_sequence_major(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows,
+                               uint32_t *sig_seq_out);
 
 /* Adjoint of subquad_fuse_forward_mc for dL/dfused (device float [m]):
  * d fused / d g_k = w_k (a_k - fused) for the MLP's outputs, then W2, the ReLU
@@ -465,7 +473,7 @@ int subquad_fuse_forward_mc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, 
  * bitwise reproducible. */
 int subquad_fuse_backward_mc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
                              const int32_t *self_scores, const void *packed, int pack_stride, const float *emb,
-                             int64_t n, int d, const uint32_t *sig, int bands, int rows, const float *gate_params,
+                             int64_t n, int d, const uint32_t *sig_seq, int hashes, const float *gate_params,
                              int hidden, int channels, const float *dL_dfused, const uint32_t *perm_i,
                              const uint32_t *off_i, const uint32_t *perm_j, const uint32_t *off_j, float *grad_params,
                              float *grad_emb);

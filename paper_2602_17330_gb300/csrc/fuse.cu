@@ -618,28 +618,46 @@ extern "C" int subquad_fuse_forward_async(subquad_ctx *ctx, const uint32_t *pair
 namespace {
 
 // Agreeing signature rows of sequences i and j, summed over the hashes this
-// lane owns (hash t of band t / rows, row t % rows; lanes stride by `lanes`).
+// lane owns.  sig_seq is sequence-major (uint32 [n][H], the layout of
+// subquad_sig_sequence_major), so a member's H words are one contiguous row:
+// with H % 4 == 0 lane q compares 16-byte chunks q, q + LANES, ... of the two
+// rows (a pair's lanes read consecutive chunks), else single words.
 template <int LANES>
-__device__ __forceinline__ int sig_agree(const uint32_t *__restrict__ sig, int64_t n, int bands, int rows, uint32_t i,
-                                         uint32_t j, int sub, bool valid)
+__device__ __forceinline__ int sig_agree(const uint32_t *__restrict__ sig_seq, int H, uint32_t i, uint32_t j, int sub,
+                                         bool valid)
 {
     int agree = 0;
     if (!valid) return 0;
-    if (rows == 4) {
-        const uint4 *sv = reinterpret_cast<const uint4 *>(sig);
-        for (int b = sub; b < bands; b += LANES) {
-            const uint4 x = __ldg(sv + (int64_t)b * n + i), y = __ldg(sv + (int64_t)b * n + j);
+    if ((H & 3) == 0) {
+        const int H4 = H >> 2;
+        const uint4 *ri = reinterpret_cast<const uint4 *>(sig_seq) + (int64_t)i * H4;
+        const uint4 *rj = reinterpret_cast<const uint4 *>(sig_seq) + (int64_t)j * H4;
+        for (int c = sub; c < H4; c += LANES) {
+            const uint4 x = __ldg(ri + c), y = __ldg(rj + c);
             agree += (x.x == y.x) + (x.y == y.y) + (x.z == y.z) + (x.w == y.w);
         }
     } else {
-        const int H = bands * rows;
-        for (int t = sub; t < H; t += LANES) {
-            const int b = t / rows, r = t - b * rows;
-            const int64_t base = (int64_t)b * n * rows + r;
-            agree += __ldg(sig + base + (int64_t)i * rows) == __ldg(sig + base + (int64_t)j * rows);
-        }
+        for (int t = sub; t < H; t += LANES)
+            agree += __ldg(sig_seq + (int64_t)i * H + t) == __ldg(sig_seq + (int64_t)j * H + t);
     }
     return agree;
+}
+
+// [bands][n][rows] -> [n][bands * rows]: one thread per sequence, its band
+// slices read coalesced across the warp and written into its row.
+__global__ void sig_transpose_kernel(const uint32_t *__restrict__ sig, int64_t n, int bands, int rows,
+                                     uint32_t *__restrict__ out)
+{
+    const int H = bands * rows;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (rows == 4) {
+            for (int b = 0; b < bands; ++b)
+                reinterpret_cast<uint4 *>(out + i * H)[b] = __ldg(reinterpret_cast<const uint4 *>(sig) + (int64_t)b * n + i);
+        } else {
+            for (int b = 0; b < bands; ++b)
+                for (int r = 0; r < rows; ++r) out[i * H + b * rows + r] = __ldg(sig + ((int64_t)b * n + i) * rows + r);
+        }
+    }
 }
 
 // Parameter offsets of the M-channel gate.
@@ -655,8 +673,7 @@ template <int M, int WORDS, int CPL>
 __global__ void __launch_bounds__(kFuseThreads) fuse_forward_mc_kernel(
     const uint32_t *__restrict__ pairs, int64_t m, const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc,
     const uint64_t *__restrict__ packed, const float *__restrict__ emb, int d, const uint32_t *__restrict__ sig,
-    int64_t n, int bands, int rows, const float *__restrict__ params, int hidden, float *__restrict__ fused,
-    float *__restrict__ weights)
+    int H, const float *__restrict__ params, int hidden, float *__restrict__ fused, float *__restrict__ weights)
 {
     constexpr int F = M + 1;
     __shared__ float s_w1[kMaxHidden * F];
@@ -669,7 +686,6 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_mc_kernel(
     for (int q = threadIdx.x; q < (M - 1) * hidden; q += blockDim.x) s_w2[q] = params[L.W2 + q];
     if (threadIdx.x < M - 1) s_b2[threadIdx.x] = params[L.b2 + threadIdx.x];
     __syncthreads();
-    const int H = bands * rows;
     constexpr int kPairsPerWarp = 32 / kTppF;
     const int sub = threadIdx.x & (kTppF - 1);
     const int slot = (threadIdx.x & 31) / kTppF;
@@ -682,7 +698,7 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_mc_kernel(
         const uint2 ij = valid ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p) : make_uint2(0, 0);
         PairInputs<WORDS, CPL, kTppF> in;
         in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
-        int agree = M == 3 ? sig_agree<kTppF>(sig, n, bands, rows, ij.x, ij.y, sub, valid) : 0;
+        int agree = M == 3 ? sig_agree<kTppF>(sig, H, ij.x, ij.y, sub, valid) : 0;
         float dot = 0.f, sii = 0.f, sjj = 0.f;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -739,8 +755,8 @@ template <int M, int WORDS, int CPL, int HPL>
 __global__ void __launch_bounds__(kFuseThreads) fuse_backward_mc_kernel(
     const uint32_t *__restrict__ pairs, int64_t m, const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc,
     const uint64_t *__restrict__ packed, const float *__restrict__ emb, int d, const uint32_t *__restrict__ sig,
-    int64_t n, int bands, int rows, const float *__restrict__ params, int hidden, const float *__restrict__ dL,
-    float4 *__restrict__ coef, double *__restrict__ partials)
+    int H, const float *__restrict__ params, int hidden, const float *__restrict__ dL, float4 *__restrict__ coef,
+    double *__restrict__ partials)
 {
     constexpr int F = M + 1;
     __shared__ float s_par[(2 * M + 1) * kMaxHidden + M - 1];
@@ -750,7 +766,6 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_backward_mc_kernel(
     for (int q = threadIdx.x; q < P; q += blockDim.x) s_par[q] = params[q];
     __syncthreads();
     const float *W1 = s_par + L.W1, *b1 = s_par + L.b1, *W2 = s_par + L.W2, *b2 = s_par + L.b2;
-    const int H = bands * rows;
     const int sub = threadIdx.x & (kTpp - 1);
     const int half = (threadIdx.x >> 4) & 1;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -764,7 +779,7 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_backward_mc_kernel(
         PairInputs<WORDS, CPL> in;
         in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
         const float dA = valid ? __ldg(dL + p) : 0.f;
-        int agree = M == 3 ? sig_agree<kTpp>(sig, n, bands, rows, ij.x, ij.y, sub, valid) : 0;
+        int agree = M == 3 ? sig_agree<kTpp>(sig, H, ij.x, ij.y, sub, valid) : 0;
         float dot = 0.f, sii = 0.f, sjj = 0.f;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -872,13 +887,13 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_backward_mc_kernel(
 template <int M, int WORDS>
 int launch_forward_mc(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
                       const int32_t *self_scores, const void *packed, const float *emb, int d, const uint32_t *sig,
-                      int64_t n, int bands, int rows, const float *params, int hidden, float *fused, float *weights)
+                      int H, const float *params, int hidden, float *fused, float *weights)
 {
     const int cpl = (d / 4 + kTppF - 1) / kTppF;
     SqProfScope prof(ctx, SUBQUAD_PROF_FUSE);
 #define SQ_FWDMC(C)                                                                                                \
     fuse_forward_mc_kernel<M, WORDS, C><<<grid, kFuseThreads, 0, ctx->stream>>>(                                   \
-        pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d, sig, n, bands, rows, params, hidden, fused, weights)
+        pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d, sig, H, params, hidden, fused, weights)
     if (cpl <= 1) SQ_FWDMC(1);
     else if (cpl <= 2) SQ_FWDMC(2);
     else if (cpl <= 4) SQ_FWDMC(4);
@@ -894,8 +909,8 @@ int launch_forward_mc(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, in
 template <int M, int WORDS, int CPL>
 int launch_backward_mc_cpl(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
                            const int32_t *self_scores, const void *packed, const float *emb, int d,
-                           const uint32_t *sig, int64_t n, int bands, int rows, const float *params, int hidden,
-                           const float *dL, float4 *coef, double *partials)
+                           const uint32_t *sig, int H, const float *params, int hidden, const float *dL, float4 *coef,
+                           double *partials)
 {
     const int hpl = (hidden + kTpp - 1) / kTpp;
     const size_t smem = sizeof(double) * kGroups * McLayout(M, hidden).P;
@@ -904,7 +919,7 @@ int launch_backward_mc_cpl(subquad_ctx *ctx, unsigned grid, const uint32_t *pair
         auto kern = fuse_backward_mc_kernel<M, WORDS, CPL, HH>;                                                    \
         SQ_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));           \
         kern<<<grid, kFuseThreads, smem, ctx->stream>>>(pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d,  \
-                                                        sig, n, bands, rows, params, hidden, dL, coef, partials);  \
+                                                        sig, H, params, hidden, dL, coef, partials);               \
     } while (0)
     if (hpl <= 1) SQ_BWDMC(1);
     else if (hpl <= 2) SQ_BWDMC(2);
@@ -917,13 +932,12 @@ int launch_backward_mc_cpl(subquad_ctx *ctx, unsigned grid, const uint32_t *pair
 template <int M, int WORDS>
 int launch_backward_mc(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
                        const int32_t *self_scores, const void *packed, const float *emb, int d, const uint32_t *sig,
-                       int64_t n, int bands, int rows, const float *params, int hidden, const float *dL, float4 *coef,
-                       double *partials)
+                       int H, const float *params, int hidden, const float *dL, float4 *coef, double *partials)
 {
     const int cpl = (d / 4 + kTpp - 1) / kTpp;
 #define SQ_BMC(C)                                                                                                  \
-    return launch_backward_mc_cpl<M, WORDS, C>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, sig, n, bands, \
-                                               rows, params, hidden, dL, coef, partials)
+    return launch_backward_mc_cpl<M, WORDS, C>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, sig, H, params, \
+                                               hidden, dL, coef, partials)
     if (cpl <= 1) SQ_BMC(1);
     if (cpl <= 2) SQ_BMC(2);
     if (cpl <= 4) SQ_BMC(4);
@@ -932,16 +946,14 @@ int launch_backward_mc(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, i
 #undef SQ_BMC
 }
 
-int check_mc_args(int64_t m, int64_t n, int d, int hidden, int channels, int pack_stride, const uint32_t *sig,
-                  int bands, int rows)
+int check_mc_args(int64_t m, int64_t n, int d, int hidden, int channels, int pack_stride, const uint32_t *sig, int H)
 {
     if (m < 0 || n < 0 || d < 4 || d > 1024 || d % 4 || hidden < 1 || hidden > kMaxHidden) return SUBQUAD_ERR_ARG;
     if (channels != 2 && channels != 3) return SUBQUAD_ERR_ARG;
     if (pack_stride != 16 && pack_stride != 32) return SUBQUAD_ERR_ARG;
     if (channels == 3) {
-        if (!sig || bands < 1 || rows < 1 || rows > 8 || bands * rows > 512 || n < 1) return SUBQUAD_ERR_ARG;
-        if (rows == 4 && reinterpret_cast<uintptr_t>(sig) % 16) return SUBQUAD_ERR_ARG;
-        if (reinterpret_cast<uintptr_t>(sig) % 4) return SUBQUAD_ERR_ARG;
+        if (!sig || H < 1 || H > 512) return SUBQUAD_ERR_ARG;
+        if (reinterpret_cast<uintptr_t>(sig) % ((H & 3) == 0 ? 16 : 4)) return SUBQUAD_ERR_ARG;
     }
     return SUBQUAD_OK;
 }
@@ -950,12 +962,12 @@ int check_mc_args(int64_t m, int64_t n, int d, int hidden, int channels, int pac
 
 extern "C" int subquad_fuse_forward_mc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
                                        const int32_t *self_scores, const void *packed, int pack_stride,
-                                       const float *emb, int d, const uint32_t *sig, int64_t n, int bands, int rows,
+                                       const float *emb, int d, const uint32_t *sig_seq, int hashes,
                                        const float *gate_params, int hidden, int channels, float *fused_out,
                                        float *weights_out)
 {
     SQ_ENTER(ctx);
-    SQ_TRY(check_mc_args(m, channels == 3 ? n : 0, d, hidden, channels, pack_stride, sig, bands, rows));
+    SQ_TRY(check_mc_args(m, 0, d, hidden, channels, pack_stride, sig_seq, hashes));
     if (m == 0) return SUBQUAD_OK;
     if (!pairs || !sw || !self_scores || !packed || !emb || !gate_params || !fused_out) return SUBQUAD_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(emb) % 16 || reinterpret_cast<uintptr_t>(pairs) % 8 ||
@@ -963,7 +975,7 @@ extern "C" int subquad_fuse_forward_mc(subquad_ctx *ctx, const uint32_t *pairs, 
         return SUBQUAD_ERR_ARG;
     const unsigned grid = sq_grid(ctx, (m + 7) / 8 * 32, kFuseThreads, 8);
 #define SQ_MCF(MM, W)                                                                                              \
-    return launch_forward_mc<MM, W>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, sig, n, bands, rows,      \
+    return launch_forward_mc<MM, W>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, sig_seq, hashes,         \
                                     gate_params, hidden, fused_out, weights_out)
     if (channels == 2) {
         if (pack_stride == 16) SQ_MCF(2, 2);
@@ -976,13 +988,13 @@ extern "C" int subquad_fuse_forward_mc(subquad_ctx *ctx, const uint32_t *pairs, 
 
 extern "C" int subquad_fuse_backward_mc(subquad_ctx *ctx, const uint32_t *pairs, int64_t m, const int32_t *sw,
                                         const int32_t *self_scores, const void *packed, int pack_stride,
-                                        const float *emb, int64_t n, int d, const uint32_t *sig, int bands, int rows,
+                                        const float *emb, int64_t n, int d, const uint32_t *sig_seq, int hashes,
                                         const float *gate_params, int hidden, int channels, const float *dL_dfused,
                                         const uint32_t *perm_i, const uint32_t *off_i, const uint32_t *perm_j,
                                         const uint32_t *off_j, float *grad_params, float *grad_emb)
 {
     SQ_ENTER(ctx);
-    SQ_TRY(check_mc_args(m, n, d, hidden, channels, pack_stride, sig, bands, rows));
+    SQ_TRY(check_mc_args(m, n, d, hidden, channels, pack_stride, sig_seq, hashes));
     if (!grad_params || !gate_params) return SUBQUAD_ERR_ARG;
     if (m > 0 && (!pairs || !sw || !self_scores || !packed || !emb || !dL_dfused)) return SUBQUAD_ERR_ARG;
     if (grad_emb && (!perm_i || !off_i || !perm_j || !off_j || !emb)) return SUBQUAD_ERR_ARG;
@@ -999,7 +1011,7 @@ extern "C" int subquad_fuse_backward_mc(subquad_ctx *ctx, const uint32_t *pairs,
     double *partials = arena.take<double>((size_t)grid * P);
     float4 *coef = grad_emb ? arena.take<float4>((size_t)m) : nullptr;
 #define SQ_MCB(MM, W)                                                                                              \
-    SQ_TRY((launch_backward_mc<MM, W>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, sig, n, bands, rows,    \
+    SQ_TRY((launch_backward_mc<MM, W>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, sig_seq, hashes,       \
                                       gate_params, hidden, dL_dfused, coef, partials)))
     if (channels == 2) {
         if (pack_stride == 16) SQ_MCB(2, 2);
@@ -1025,5 +1037,19 @@ extern "C" int subquad_fuse_backward_mc(subquad_ctx *ctx, const uint32_t *pairs,
 #undef SQ_EMB
         SQ_LAUNCH_CHECK();
     }
+    return SUBQUAD_OK;
+}
+
+extern "C" int subquad_sig_sequence_major(subquad_ctx *ctx, const uint32_t *sig, int64_t n, int bands, int rows,
+                                          uint32_t *sig_seq_out)
+{
+    SQ_ENTER(ctx);
+    if (n < 0 || bands < 1 || rows < 1 || rows > 8 || bands * rows > 512) return SUBQUAD_ERR_ARG;
+    if (n == 0) return SUBQUAD_OK;
+    if (!sig || !sig_seq_out) return SUBQUAD_ERR_ARG;
+    if (rows == 4 && (reinterpret_cast<uintptr_t>(sig) % 16 || reinterpret_cast<uintptr_t>(sig_seq_out) % 16))
+        return SUBQUAD_ERR_ARG;
+    sig_transpose_kernel<<<sq_grid(ctx, n, 256, 8), 256, 0, ctx->stream>>>(sig, n, bands, rows, sig_seq_out);
+    SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
 }

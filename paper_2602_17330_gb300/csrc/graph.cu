@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kUfLimit = 1 << 20;  // bound on the steps of one find or union
 constexpr int kMaxComp = 64;       // largest component the Jacobi kernel takes
-constexpr int kJacWarps = 4;       // components (warps) per Jacobi block
+constexpr int kJacWarps = 8;       // components (warps) per Jacobi block
 constexpr int kJacSweeps = 60;
 constexpr double kEpsLevel = 1e-9;
 
@@ -160,22 +160,25 @@ __global__ void mat_scatter_kernel(const uint32_t *__restrict__ pairs, const flo
 }
 
 // One warp per component: cyclic parallel Jacobi in FP64 on the block held in
-// shared memory (row pitch N + 1), round-robin pairing (player 0 fixed, the
-// others rotate), rows then columns updated per step; sweeps until the
-// off-diagonal sum of squares is <= 1e-26 of the total (or kJacSweeps).
+// shared memory (row pitch nmax + 1, nmax = the largest component rounded up
+// to even, so small components leave room for more warps per SM), round-robin
+// pairing (player 0 fixed, the others rotate), rows then columns updated per
+// step; sweeps until the off-diagonal sum of squares is <= 1e-26 of the total
+// (or kJacSweeps).
 __global__ void __launch_bounds__(32 * kJacWarps) jacobi_kernel(const uint32_t *__restrict__ comp_start,
                                                                  int64_t ncomp, int64_t A,
                                                                  const uint64_t *__restrict__ mat_off,
-                                                                 const double *__restrict__ mats,
+                                                                 const double *__restrict__ mats, int nmax,
                                                                  double *__restrict__ levels, uint32_t *err)
 {
     extern __shared__ double s_mem[];
-    constexpr int P = kMaxComp + 1;
+    const int P = nmax + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double *S = s_mem + (size_t)warp * kMaxComp * P;
+    double *S = s_mem + (size_t)warp * nmax * P;
     __shared__ int s_p[kJacWarps][kMaxComp / 2], s_q[kJacWarps][kMaxComp / 2];
     __shared__ double s_c[kJacWarps][kMaxComp / 2], s_s[kJacWarps][kMaxComp / 2];
-    for (int64_t c = blockIdx.x * (int64_t)kJacWarps + warp; c < ncomp; c += (int64_t)gridDim.x * kJacWarps) {
+    const int wpb = blockDim.x >> 5;  // warps (components in flight) per block
+    for (int64_t c = blockIdx.x * (int64_t)wpb + warp; c < ncomp; c += (int64_t)gridDim.x * wpb) {
         const uint32_t base = comp_start[c];
         const int s = (int)((c + 1 < ncomp ? comp_start[c + 1] : (uint32_t)A) - base);
         const int N = s + (s & 1);
@@ -472,11 +475,14 @@ int evaluate_threshold(subquad_ctx *ctx, const uint32_t *pairs, const float *w, 
     mat_scatter_kernel<<<sq_grid(ctx, m, 256, 8), 256, 0, ctx->stream>>>(pairs, w, m, tau, g.vpos, g.vcomp,
                                                                          g.comp_start, g.mat_off, ncomp, A, g.mats);
     SQ_LAUNCH_CHECK();
-    const size_t smem = sizeof(double) * kJacWarps * kMaxComp * (kMaxComp + 1);
+    const int nmax = (int)h[0] + ((int)h[0] & 1);
+    const size_t per_warp = sizeof(double) * nmax * (nmax + 1);
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kJacWarps, (size_t)(200 << 10) / per_warp));
+    const size_t smem = per_warp * wpb;
     SQ_TRY_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned gj = (unsigned)std::min<int64_t>((ncomp + kJacWarps - 1) / kJacWarps, (int64_t)ctx->num_sms * 4);
-    jacobi_kernel<<<gj, 32 * kJacWarps, smem, ctx->stream>>>(g.comp_start, ncomp, A, g.mat_off, g.mats, g.levels,
-                                                             ctx->d_err);
+    const unsigned gj = (unsigned)std::min<int64_t>((ncomp + wpb - 1) / wpb, (int64_t)ctx->num_sms * 16);
+    jacobi_kernel<<<gj, 32 * wpb, smem, ctx->stream>>>(g.comp_start, ncomp, A, g.mat_off, g.mats, nmax, g.levels,
+                                                       ctx->d_err);
     SQ_LAUNCH_CHECK();
     // sort the levels: low words, then high words (both stable)
     level_keys_kernel<<<ga, 256, 0, ctx->stream>>>(g.levels, A, g.keys, g.vals);

@@ -88,10 +88,11 @@ SIGNATURES = {
                                          _P, _P, _P, _P, _P, _P]),
     "subquad_fuse_backward_params_noalloc": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P,
                                                         _c.c_int, _P, _P]),
-    "subquad_fuse_forward_mc": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P, _I64, _c.c_int,
-                                           _c.c_int, _P, _c.c_int, _c.c_int, _P, _P]),
-    "subquad_fuse_backward_mc": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _I64, _c.c_int, _P, _c.c_int,
-                                            _c.c_int, _P, _c.c_int, _c.c_int, _P, _P, _P, _P, _P, _P, _P]),
+    "subquad_fuse_forward_mc": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _c.c_int, _P, _c.c_int, _P,
+                                           _c.c_int, _c.c_int, _P, _P]),
+    "subquad_fuse_backward_mc": (_c.c_int, [_P, _P, _I64, _P, _P, _P, _c.c_int, _P, _I64, _c.c_int, _P, _c.c_int, _P,
+                                            _c.c_int, _c.c_int, _P, _P, _P, _P, _P, _P, _P]),
+    "subquad_sig_sequence_major": (_c.c_int, [_P, _P, _I64, _c.c_int, _c.c_int, _P]),
     "subquad_default_edit_costs": (_c.c_int, [_P]),
     "subquad_set_edit_costs": (_c.c_int, [_P, _c.c_int, _P]),
     "subquad_edit_distance": (_c.c_int, [_P, _P, _c.c_int, _P, _I64, _P]),
@@ -481,24 +482,32 @@ class Context:
             int(emb.shape[1]), _ptr(params), hidden, _ptr(dL), _ptr(out)), "subquad_fuse_backward_params_noalloc")
         return out
 
-    def fuse_forward_mc(self, pairs, sw, self_sc, packed, emb, sig, params, hidden: int, channels: int,
+    def sig_sequence_major(self, sig):
+        """int32 [bands, n, rows] signatures of sign() -> int32 [n, bands*rows]."""
+        bands, n, rows = (int(x) for x in sig.shape)
+        out = self._empty((n, bands * rows), self.torch.int32)
+        _check(lib().subquad_sig_sequence_major(self.handle, _ptr(sig), n, bands, rows, _ptr(out)),
+               "subquad_sig_sequence_major")
+        return out
+
+    def fuse_forward_mc(self, pairs, sw, self_sc, packed, emb, sig_seq, params, hidden: int, channels: int,
                         want_weights: bool = False, out=None):
-        """M-channel fusion (channels 2 or 3); sig is the int32 [bands, n, rows]
-        tensor of sign() (unused for 2 channels)."""
+        """M-channel fusion (channels 2 or 3); sig_seq is the int32 [n, H]
+        sequence-major signature (sig_sequence_major; unused for 2 channels)."""
         torch = self.torch
         m = int(pairs.shape[0])
         emb = self._dev(emb, torch.float32)
         params = self._dev(params, torch.float32)
         out = self._empty((m,), torch.float32) if out is None else out
         w = self._empty((m, channels), torch.float32) if want_weights else None
-        bands, n, rows = (int(x) for x in sig.shape) if sig is not None else (0, int(emb.shape[0]), 0)
+        H = int(sig_seq.shape[1]) if sig_seq is not None else 0
         _check(lib().subquad_fuse_forward_mc(self.handle, _ptr(pairs), m, _ptr(sw), _ptr(self_sc), _ptr(packed),
-                                             int(packed.shape[1]), _ptr(emb), int(emb.shape[1]), _ptr(sig), n, bands,
-                                             rows, _ptr(params), hidden, channels, _ptr(out), _ptr(w)),
+                                             int(packed.shape[1]), _ptr(emb), int(emb.shape[1]), _ptr(sig_seq), H,
+                                             _ptr(params), hidden, channels, _ptr(out), _ptr(w)),
                "subquad_fuse_forward_mc")
         return (out, w) if want_weights else out
 
-    def fuse_backward_mc(self, pairs, sw, self_sc, packed, emb, sig, params, hidden: int, channels: int, dL,
+    def fuse_backward_mc(self, pairs, sw, self_sc, packed, emb, sig_seq, params, hidden: int, channels: int, dL,
                          index=None, grad_params=None, grad_emb=None, want_emb: bool = True):
         torch = self.torch
         m = int(pairs.shape[0])
@@ -509,65 +518,13 @@ class Context:
                 index = self.pair_index(pairs, n)
             grad_emb = self._empty((n, d), torch.float32) if grad_emb is None else grad_emb
         ix = index or {}
-        bands, rows = (int(sig.shape[0]), int(sig.shape[2])) if sig is not None else (0, 0)
+        H = int(sig_seq.shape[1]) if sig_seq is not None else 0
         _check(lib().subquad_fuse_backward_mc(
             self.handle, _ptr(pairs), m, _ptr(sw), _ptr(self_sc), _ptr(packed), int(packed.shape[1]), _ptr(emb), n, d,
-            _ptr(sig), bands, rows, _ptr(params), hidden, channels, _ptr(dL), _ptr(ix.get("perm_i")),
+            _ptr(sig_seq), H, _ptr(params), hidden, channels, _ptr(dL), _ptr(ix.get("perm_i")),
             _ptr(ix.get("off_i")), _ptr(ix.get("perm_j")), _ptr(ix.get("off_j")), _ptr(grad_params),
             _ptr(grad_emb) if want_emb else None), "subquad_fuse_backward_mc")
         return (grad_params, grad_emb) if want_emb else grad_params
-
-    # -- graph construction and RMT thresholding ---------------------------
-    def graph_components(self, pairs, weights, n: int, tau: float, want_sizes: bool = False):
-        torch = self.torch
-        m = int(pairs.shape[0])
-        labels = self._empty((n,), torch.int32)
-        sizes = self._empty((n,), torch.int32) if want_sizes else None
-        _check(lib().subquad_graph_components(self.handle, _ptr(pairs), _ptr(weights), m, n, float(tau), _ptr(labels),
-                                              _ptr(sizes)), "subquad_graph_components")
-        return (labels, sizes) if want_sizes else labels
-
-    def rmt_threshold(self, pairs, weights, n: int, taus, s_max: int = 64, r_mid: float | None = None) -> dict:
-        """The threshold scan; returns {tau_star, r_mean, num_ratios,
-        num_levels, max_comp} (host lists, one entry per threshold)."""
-        import math
-
-        if r_mid is None:
-            r_mid = 0.5 * ((2.0 * math.log(2.0) - 1.0) + (4.0 - 2.0 * math.sqrt(3.0)))
-        T = len(taus)
-        c_taus = (_c.c_double * T)(*[float(t) for t in taus])
-        r_mean = (_c.c_double * T)()
-        nr = (_I64 * T)()
-        nl = (_I64 * T)()
-        mc = (_c.c_int32 * T)()
-        ts = _c.c_double(0.0)
-        _check(lib().subquad_rmt_threshold(self.handle, _ptr(pairs), _ptr(weights), int(pairs.shape[0]), n,
-                                           _c.cast(c_taus, _P), T, s_max, r_mid, _c.byref(ts), _c.cast(r_mean, _P),
-                                           _c.cast(nr, _P), _c.cast(nl, _P), _c.cast(mc, _P)), "subquad_rmt_threshold")
-        return {"tau_star": ts.value, "r_mean": list(r_mean), "num_ratios": list(nr), "num_levels": list(nl),
-                "max_comp": list(mc)}
-
-    def graph_prune(self, pairs, weights, tau: float):
-        """-> (pairs int32 [k, 2], weights float [k]) with weights >= tau."""
-        torch = self.torch
-        m = int(pairs.shape[0])
-        po = self._empty((max(m, 1), 2), torch.int32)
-        wo = self._empty((max(m, 1),), torch.float32)
-        cnt = self._empty((1,), torch.int64)
-        _check(lib().subquad_graph_prune(self.handle, _ptr(pairs), _ptr(weights), m, float(tau), _ptr(po), _ptr(wo),
-                                         _ptr(cnt)), "subquad_graph_prune")
-        k = int(cnt.item())
-        return po[:k], wo[:k]
-
-    def cluster_js(self, labels, donor, num_donors: int):
-        """-> float64 [num_donors, num_donors] sqrt-JS distances of the donors'
-        cluster-mass vectors."""
-        torch = self.torch
-        donor = self._dev(donor, torch.int32)
-        out = self._empty((num_donors, num_donors), torch.float64)
-        _check(lib().subquad_cluster_js(self.handle, _ptr(labels), _ptr(donor), int(labels.shape[0]), num_donors,
-                                        _ptr(out)), "subquad_cluster_js")
-        return out
 
     def adam_step(self, param, grad, m1, m2, t: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
                   eps: float = 1e-8):
@@ -638,6 +595,10 @@ def subquad_fuse_forward_mc(ctx: Context, *a, **k):
 
 def subquad_fuse_backward_mc(ctx: Context, *a, **k):
     return ctx.fuse_backward_mc(*a, **k)
+
+
+def subquad_sig_sequence_major(ctx: Context, *a, **k):
+    return ctx.sig_sequence_major(*a, **k)
 
 
 def subquad_edit_distance(ctx: Context, *a, **k):

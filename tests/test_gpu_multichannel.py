@@ -44,6 +44,10 @@ def make_case(ctx, torch, oracle_mod, n, bands, rows, stride, d, seed):
                    rows)
     sig_o = oracle_mod.sign(rep.codes, rep.lens, 3, a, b)
     assert (to_np(sig).view(np.uint32).transpose(1, 0, 2).reshape(rep.n, -1) == sig_o).all()
+    # the kernels read the sequence-major copy; the oracle's signatures are uploaded for them
+    sig_seq = ctx.sig_sequence_major(sig)
+    assert (to_np(sig_seq).view(np.uint32) == sig_o).all()
+    sig = torch.from_numpy(sig_o.view(np.int32)).to(ctx.device)
     C = oracle_mod.candidates(sig_o, bands, rows, 0)
     sw_o = oracle_mod.sw_pairs(rep.codes, rep.lens, C)
     self_o = oracle_mod.self_scores(rep.codes, rep.lens)
