@@ -526,6 +526,58 @@ class Context:
             _ptr(grad_emb) if want_emb else None), "subquad_fuse_backward_mc")
         return (grad_params, grad_emb) if want_emb else grad_params
 
+    # -- graph construction and RMT thresholding ---------------------------
+    def graph_components(self, pairs, weights, n: int, tau: float, want_sizes: bool = False):
+        torch = self.torch
+        m = int(pairs.shape[0])
+        labels = self._empty((n,), torch.int32)
+        sizes = self._empty((n,), torch.int32) if want_sizes else None
+        _check(lib().subquad_graph_components(self.handle, _ptr(pairs), _ptr(weights), m, n, float(tau), _ptr(labels),
+                                              _ptr(sizes)), "subquad_graph_components")
+        return (labels, sizes) if want_sizes else labels
+
+    def rmt_threshold(self, pairs, weights, n: int, taus, s_max: int = 64, r_mid: float | None = None) -> dict:
+        """The threshold scan; returns {tau_star, r_mean, num_ratios,
+        num_levels, max_comp} (host lists, one entry per threshold)."""
+        import math
+
+        if r_mid is None:
+            r_mid = 0.5 * ((2.0 * math.log(2.0) - 1.0) + (4.0 - 2.0 * math.sqrt(3.0)))
+        T = len(taus)
+        c_taus = (_c.c_double * T)(*[float(t) for t in taus])
+        r_mean = (_c.c_double * T)()
+        nr = (_I64 * T)()
+        nl = (_I64 * T)()
+        mc = (_c.c_int32 * T)()
+        ts = _c.c_double(0.0)
+        _check(lib().subquad_rmt_threshold(self.handle, _ptr(pairs), _ptr(weights), int(pairs.shape[0]), n,
+                                           _c.cast(c_taus, _P), T, s_max, r_mid, _c.byref(ts), _c.cast(r_mean, _P),
+                                           _c.cast(nr, _P), _c.cast(nl, _P), _c.cast(mc, _P)), "subquad_rmt_threshold")
+        return {"tau_star": ts.value, "r_mean": list(r_mean), "num_ratios": list(nr), "num_levels": list(nl),
+                "max_comp": list(mc)}
+
+    def graph_prune(self, pairs, weights, tau: float):
+        """-> (pairs int32 [k, 2], weights float [k]) with weights >= tau."""
+        torch = self.torch
+        m = int(pairs.shape[0])
+        po = self._empty((max(m, 1), 2), torch.int32)
+        wo = self._empty((max(m, 1),), torch.float32)
+        cnt = self._empty((1,), torch.int64)
+        _check(lib().subquad_graph_prune(self.handle, _ptr(pairs), _ptr(weights), m, float(tau), _ptr(po), _ptr(wo),
+                                         _ptr(cnt)), "subquad_graph_prune")
+        k = int(cnt.item())
+        return po[:k], wo[:k]
+
+    def cluster_js(self, labels, donor, num_donors: int):
+        """-> float64 [num_donors, num_donors] sqrt-JS distances of the donors'
+        cluster-mass vectors."""
+        torch = self.torch
+        donor = self._dev(donor, torch.int32)
+        out = self._empty((num_donors, num_donors), torch.float64)
+        _check(lib().subquad_cluster_js(self.handle, _ptr(labels), _ptr(donor), int(labels.shape[0]), num_donors,
+                                        _ptr(out)), "subquad_cluster_js")
+        return out
+
     def adam_step(self, param, grad, m1, m2, t: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
                   eps: float = 1e-8):
         _check(lib().subquad_adam_step(self.handle, _ptr(param), _ptr(grad), _ptr(m1), _ptr(m2), int(param.numel()),

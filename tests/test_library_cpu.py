@@ -68,3 +68,17 @@ def test_default_edit_costs_match_oracle(libmod, oracle_mod):
     they must equal the oracle's, derived from the independently typed one."""
     lib_costs = np.array(libmod.default_edit_costs(), dtype=np.uint8).reshape(20, 20)
     assert (lib_costs == oracle_mod.default_edit_costs()).all()
+
+
+def test_every_entry_point_has_a_context_method(libmod):
+    """Each C entry point that runs on a context has a binding method (module
+    level wrappers call ctx.<name without the prefix>)."""
+    import inspect
+
+    src = inspect.getsource(libmod)
+    for name in libmod.SIGNATURES:
+        wrapper = f"def {name}(ctx: Context"
+        if wrapper in src:
+            body = src[src.index(wrapper):].split("\n")[1]
+            method = body.strip().split("ctx.")[1].split("(")[0]
+            assert hasattr(libmod.Context, method), f"{name}: Context.{method} missing"
