@@ -404,11 +404,7 @@ struct TargetStream {
 // lookups combines with one integer multiply-add by the runtime constant
 // `unit` (= 1), and the lookup addresses are formed the same way, so this
 // arithmetic runs on the FMA pipe and leaves the ALU pipe (where the DPX and
-// packed max operations run) to the recurrence.  The recurrence itself keeps
-// H, E and F biased by 2^14 per half, which turns H - o into a borrow-free
-// 32-bit add (also a multiply-add) and the floor H >= 0 into a full-rate
-// packed max: per cell 3 DPX and 3 packed max on the ALU pipe instead of 3
-// DPX, 2 packed max and a half-rate packed add.
+// packed max operations run) to the recurrence.
 template <int WORDS, int NQ, bool SPLIT = false>
 __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, const Rec<WORDS> &tP, int LtP,
                                              const Rec<WORDS> &qQ, int LqQ, const Rec<WORDS> &tQ, int LtQ,
@@ -416,15 +412,6 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
 {
     uint32_t qoffP[NQ], qoffQ[NQ], E[NQ], HM[NQ];
     const uint32_t neg_o = pack2(-o, -o), neg_e = pack2(-e, -e);
-    // SPLIT keeps H, E and F biased by kBias per half, so H - o is one plain
-    // 32-bit add that never borrows across the halves (every half stays in
-    // [kBias - 2000, kBias + 3000]) and the floor H >= 0 is a packed max with
-    // the bias; the add runs as an integer multiply-add (FMA pipe).
-    constexpr uint32_t kBias = 0x4000u;
-    const uint32_t biasP = pack2(kBias, kBias);
-    const uint32_t hm0 = SPLIT ? pack2((int32_t)kBias - o, (int32_t)kBias - o) : neg_o;  // H(0, .) - o
-    const uint32_t sub_o = ((65535u - (uint32_t)o) << 16) + (65536u - (uint32_t)o);   // h - o in both halves
-    const uint32_t e0 = SPLIT ? biasP : 0u;
 #pragma unroll
     for (int p = 0; p < NQ; ++p) {
         uint32_t cp = (uint32_t)(qP.w[p / 12] >> (5 * (p % 12))) & 31u;
@@ -433,15 +420,15 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
         cq = p < LqQ ? min(cq, 19u) : 20u;
         qoffP[p] = (cp * kTabRows * kLanes + (uint32_t)lane) * 4u;
         qoffQ[p] = (cq * kTabRows * kLanes + (uint32_t)lane) * 4u;
-        E[p] = e0;
-        HM[p] = hm0;
+        E[p] = 0u;
+        HM[p] = neg_o;
     }
     // Two target columns per iteration, the second one row behind the first:
     // column j's row p and column j+1's row p-1 are independent, so each step
     // carries two dependency chains (F -> max -> H -> H-o) instead of one.  A
     // column beyond the target's length scores every cell with the padding
     // residue and can never raise the maximum.
-    uint32_t bestA = e0, bestB = e0;
+    uint32_t bestA = 0u, bestB = 0u;
     TargetStream<WORDS> sP(tP), sQ(tQ);
     const int Lt = max(LtP, LtQ);
     for (int j = 0; j < Lt; j += 2) {
@@ -453,8 +440,8 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
         const uint32_t offBQ = (j + 1 < LtQ ? bQ : 20u) * (kLanes * 4) + (SPLIT ? kTabWords * 4u : 0u);
         const char *colAP = s_tab + offAP, *colAQ = s_tab + offAQ;
         const char *colBP = s_tab + offBP, *colBQ = s_tab + offBQ;
-        uint32_t dA = hm0, upA = hm0, FA = e0;
-        uint32_t dB = hm0, upB = hm0, FB = e0;
+        uint32_t dA = neg_o, upA = neg_o, FA = 0u;
+        uint32_t dB = neg_o, upB = neg_o, FB = 0u;
 #pragma unroll
         for (int p = 0; p <= NQ; ++p) {
             if (p < NQ) {  // column j, row p
@@ -470,10 +457,9 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
                 }
                 const uint32_t e_new = __viaddmax_s16x2_relu(E[p], neg_e, HM[p]);
                 FA = __viaddmax_s16x2_relu(FA, neg_e, upA);
-                const uint32_t h = SPLIT ? __vmaxs2(__viaddmax_s16x2(dA, s_o, __vmaxs2(e_new, FA)), biasP)
-                                         : __viaddmax_s16x2_relu(dA, s_o, __vmaxs2(e_new, FA));
+                const uint32_t h = __viaddmax_s16x2_relu(dA, s_o, __vmaxs2(e_new, FA));
                 dA = HM[p];
-                HM[p] = SPLIT ? h * unit + sub_o : __vadd2(h, neg_o);
+                HM[p] = __vadd2(h, neg_o);
                 upA = HM[p];
                 E[p] = e_new;
                 bestA = __vmaxs2(bestA, h);
@@ -492,19 +478,16 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
                 }
                 const uint32_t e_new = __viaddmax_s16x2_relu(E[r], neg_e, HM[r]);
                 FB = __viaddmax_s16x2_relu(FB, neg_e, upB);
-                const uint32_t h = SPLIT ? __vmaxs2(__viaddmax_s16x2(dB, s_o, __vmaxs2(e_new, FB)), biasP)
-                                         : __viaddmax_s16x2_relu(dB, s_o, __vmaxs2(e_new, FB));
+                const uint32_t h = __viaddmax_s16x2_relu(dB, s_o, __vmaxs2(e_new, FB));
                 dB = HM[r];
-                HM[r] = SPLIT ? h * unit + sub_o : __vadd2(h, neg_o);
+                HM[r] = __vadd2(h, neg_o);
                 upB = HM[r];
                 E[r] = e_new;
                 bestB = __vmaxs2(bestB, h);
             }
         }
     }
-    // SPLIT: both halves of the best are >= kBias, so one 32-bit subtraction
-    // removes the bias from each without a borrow
-    return SPLIT ? __vmaxs2(bestA, bestB) - biasP : __vmaxs2(bestA, bestB);
+    return __vmaxs2(bestA, bestB);
 }
 
 // Launch shapes of the batched kernel: 0 = 256 threads, 2 blocks per SM (128
