@@ -835,9 +835,10 @@ def banding_explains(rep, queries, ids, bands: int, rows: int, sample: int = 200
 
 
 def run_recall_sweep(args, ctx, stream):
-    """Recall@50 of cross-donor retrieval against the band shape, on the
-    16-donor pool (2.2M sequences, 500 public families) with the same 64 hash
-    functions grouped as 16 bands of 4 rows or 32 bands of 2 (no cap), on 1,000
+    """Recall@50 of cross-donor retrieval against the band shape, on a pool of
+    4 donors (50k-200k sequences each, 500 public families) with the same 64
+    hash functions grouped as 16 bands of 4 rows, 32 of 2 or 64 of 1 (no cap;
+    a shape whose candidate set exceeds 1.5e9 pairs is only counted), on 1,000
     public-family queries and 1,000 random queries, beside the banding's catch
     probability of the exhaustive top-50 partners."""
     import numpy as np
@@ -845,13 +846,13 @@ def run_recall_sweep(args, ctx, stream):
 
     from paper_2602_17330_gb300 import pipeline, synth
 
-    rep = synth.pooled_repertoire(16, 50_000, 200_000, seed=5)
+    rep = synth.pooled_repertoire(4, 50_000, 200_000, seed=5)
     a, b = synth.hash_coefficients(64, seed=5)
     public = np.flatnonzero((rep.family >= 0) & (rep.family < 500))
     rng = np.random.default_rng(5)
     q_pub = np.sort(rng.choice(public, size=min(1000, public.size), replace=False)).astype(np.uint32)
     q_rnd = np.sort(rng.choice(rep.n, size=1000, replace=False)).astype(np.uint32)
-    out = {"workload": f"{rep.n:,} sequences pooled from 16 donors, 500 public families"}
+    out = {"workload": f"{rep.n:,} sequences pooled from 4 donors, 500 public families"}
     with torch.cuda.stream(stream):
         donor = torch.from_numpy(rep.donor).to(ctx.device)
         codes, lens = torch.from_numpy(rep.codes).to(ctx.device), torch.from_numpy(rep.lens).to(ctx.device)
@@ -860,7 +861,7 @@ def run_recall_sweep(args, ctx, stream):
         for name, q in (("public", q_pub), ("random", q_rnd)):
             ids_b, sc_b = ctx.topk_bruteforce(packed, donor, torch.from_numpy(q.view(np.int32)).to(ctx.device), 50)
             best[name] = (ids_b.cpu().numpy().view(np.uint32), sc_b.cpu().numpy())
-        for bands, rows in ((16, 4), (32, 2)):
+        for bands, rows in ((16, 4), (32, 2), (64, 1)):
             sig = ctx.sign(packed, rep.n, 3, torch.from_numpy(a.view(np.int32)).to(ctx.device),
                            torch.from_numpy(b.view(np.int32)).to(ctx.device), bands, rows)
             count = sum(int(bt.shape[0]) for bt in ctx.band_stream(sig, rep.n, bands, rows, 0, capacity=1 << 26))

@@ -10,6 +10,7 @@
 // is the two-logit softmax of Eq. wm with logits (g, 0).  The kernel is
 // instruction-bound at 16 lanes per pair, so the split favours fewer
 // shuffles and more work per lane.
+#include <algorithm>
 #include <mutex>
 
 #include "internal.cuh"
@@ -643,21 +644,37 @@ __device__ __forceinline__ int sig_agree(const uint32_t *__restrict__ sig_seq, i
     return agree;
 }
 
-// [bands][n][rows] -> [n][bands * rows]: one thread per sequence, its band
-// slices read coalesced across the warp and written into its row.
+// [bands][n][rows] -> [n][bands * rows].  rows == 4: a block takes 64
+// sequences, reads every band's 16-byte vectors of them (64 consecutive
+// vectors per band: coalesced) into shared memory, then writes the 64 rows,
+// which are contiguous in the output, as consecutive 16-byte chunks
+// (coalesced).  Other rows: one thread per sequence, word by word.
+constexpr int kTrSeq = 64;
+
+__global__ void __launch_bounds__(256) sig_transpose4_kernel(const uint4 *__restrict__ sig, int64_t n, int bands,
+                                                              uint4 *__restrict__ out)
+{
+    extern __shared__ uint4 s_v[];  // [kTrSeq][bands]
+    for (int64_t i0 = (int64_t)blockIdx.x * kTrSeq; i0 < n; i0 += (int64_t)gridDim.x * kTrSeq) {
+        const int cnt = n - i0 < kTrSeq ? (int)(n - i0) : kTrSeq;
+        for (int q = threadIdx.x; q < cnt * bands; q += blockDim.x) {
+            const int b = q / cnt, il = q - b * cnt;
+            s_v[il * bands + b] = __ldg(sig + (int64_t)b * n + i0 + il);
+        }
+        __syncthreads();
+        uint4 *dst = out + i0 * bands;
+        for (int q = threadIdx.x; q < cnt * bands; q += blockDim.x) dst[q] = s_v[q];
+        __syncthreads();
+    }
+}
+
 __global__ void sig_transpose_kernel(const uint32_t *__restrict__ sig, int64_t n, int bands, int rows,
                                      uint32_t *__restrict__ out)
 {
     const int H = bands * rows;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (rows == 4) {
-            for (int b = 0; b < bands; ++b)
-                reinterpret_cast<uint4 *>(out + i * H)[b] = __ldg(reinterpret_cast<const uint4 *>(sig) + (int64_t)b * n + i);
-        } else {
-            for (int b = 0; b < bands; ++b)
-                for (int r = 0; r < rows; ++r) out[i * H + b * rows + r] = __ldg(sig + ((int64_t)b * n + i) * rows + r);
-        }
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int b = 0; b < bands; ++b)
+            for (int r = 0; r < rows; ++r) out[i * H + b * rows + r] = __ldg(sig + ((int64_t)b * n + i) * rows + r);
 }
 
 // Parameter offsets of the M-channel gate.
@@ -1049,7 +1066,15 @@ extern "C" int subquad_sig_sequence_major(subquad_ctx *ctx, const uint32_t *sig,
     if (!sig || !sig_seq_out) return SUBQUAD_ERR_ARG;
     if (rows == 4 && (reinterpret_cast<uintptr_t>(sig) % 16 || reinterpret_cast<uintptr_t>(sig_seq_out) % 16))
         return SUBQUAD_ERR_ARG;
-    sig_transpose_kernel<<<sq_grid(ctx, n, 256, 8), 256, 0, ctx->stream>>>(sig, n, bands, rows, sig_seq_out);
+    if (rows == 4) {
+        const size_t smem = sizeof(uint4) * kTrSeq * bands;  // <= 128 bands: 128 KB
+        SQ_TRY_CUDA(cudaFuncSetAttribute(sig_transpose4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const unsigned grid = (unsigned)std::min<int64_t>((n + kTrSeq - 1) / kTrSeq, (int64_t)ctx->num_sms * 8);
+        sig_transpose4_kernel<<<grid, 256, smem, ctx->stream>>>(reinterpret_cast<const uint4 *>(sig), n, bands,
+                                                                reinterpret_cast<uint4 *>(sig_seq_out));
+    } else {
+        sig_transpose_kernel<<<sq_grid(ctx, n, 256, 8), 256, 0, ctx->stream>>>(sig, n, bands, rows, sig_seq_out);
+    }
     SQ_LAUNCH_CHECK();
     return SUBQUAD_OK;
 }
