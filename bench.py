@@ -200,12 +200,13 @@ class ClockSampler:
 # CPU baseline / reference arm: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
 
-def oracle_step(n_sample: int, seed: int = 0, threads: int = 1):
+def oracle_step(n_sample: int, seed: int = 0, threads: int = 1, with_stages: bool = False):
     """One pass of the oracle over a donor repertoire of n_sample sequences
     (same generator, families of 25, same hashing).  threads > 1 runs the
     signatures, alignments and fusion over that many host threads (the
     oracle's threaded runners; the banding stays single-threaded).  Returns
-    (pairs, seconds)."""
+    (pairs, seconds), plus the seconds of each stage and the DP cell count
+    with with_stages."""
     import oracle
     from paper_2602_17330_gb300 import pipeline, synth
 
@@ -215,21 +216,34 @@ def oracle_step(n_sample: int, seed: int = 0, threads: int = 1):
     emb = synth.unit_embeddings(rep.n, cfg.d, seed=seed)
     params = synth.gate_parameters(cfg.hidden, seed=0)
     idx = np.arange(rep.n, dtype=np.uint32)
-    t0 = time.perf_counter()
+    marks = [time.perf_counter()]
     if threads > 1:
         sig = oracle.sign_mt(rep.codes, rep.lens, cfg.k, a, b, threads)
+        marks.append(time.perf_counter())
         pairs = oracle.candidates(sig, cfg.bands, cfg.rows, cfg.bucket_cap)
+        marks.append(time.perf_counter())
         self_sc = oracle.sw_pairs_mt(rep.codes, rep.lens, np.stack([idx, idx], 1), threads, cfg.gap_open,
                                      cfg.gap_extend)
+        marks.append(time.perf_counter())
         sw = oracle.sw_pairs_mt(rep.codes, rep.lens, pairs, threads, cfg.gap_open, cfg.gap_extend)
+        marks.append(time.perf_counter())
         oracle.fuse_forward_mt(pairs, sw, self_sc, rep.lens, emb, params, cfg.hidden, threads)
     else:
         sig = oracle.sign(rep.codes, rep.lens, cfg.k, a, b)
+        marks.append(time.perf_counter())
         pairs = oracle.candidates(sig, cfg.bands, cfg.rows, cfg.bucket_cap)
+        marks.append(time.perf_counter())
         self_sc = oracle.self_scores(rep.codes, rep.lens, cfg.gap_open, cfg.gap_extend)
+        marks.append(time.perf_counter())
         sw = oracle.sw_pairs(rep.codes, rep.lens, pairs, cfg.gap_open, cfg.gap_extend)
+        marks.append(time.perf_counter())
         oracle.fuse_forward(pairs, sw, self_sc, rep.lens, emb, params, cfg.hidden)
-    return pairs.shape[0], time.perf_counter() - t0
+    marks.append(time.perf_counter())
+    stages = {k: marks[t + 1] - marks[t] for t, k in enumerate(["sign", "band", "self", "align", "fuse"])}
+    stages["cells"] = int(pipeline.cells_of(rep.lens, pairs))
+    if not with_stages:
+        return pairs.shape[0], marks[-1] - marks[0]
+    return pairs.shape[0], marks[-1] - marks[0], stages
 
 
 def host_cpu() -> str:
@@ -547,14 +561,22 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         import oracle
 
         n_s = args.cpu_sample_n
-        p_s, sec = oracle_step(n_s, seed=args.seed)
+        p_s, sec, st1 = oracle_step(n_s, seed=args.seed, with_stages=True)
         threads = oracle.host_threads()
-        p_n, sec_n = oracle_step(n_s, seed=args.seed, threads=threads)
+        p_n, sec_n, stn = oracle_step(n_s, seed=args.seed, threads=threads, with_stages=True)
+
+        def stage_rates(st, pairs):
+            # pairs / s of each stage over the sample, alignment also in GCUPS
+            out = {k: pairs / st[k] for k in ("sign", "band", "align", "fuse") if st[k] > 0}
+            out["align_gcups"] = st["cells"] / st["align"] / 1e9 if st["align"] > 0 else None
+            out["seconds"] = {k: st[k] for k in ("sign", "band", "self", "align", "fuse")}
+            return out
         cpu = {"value": p_s / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"single-threaded oracle, full pipeline on a {n_s:,}-sequence donor from the same "
                          f"generator ({p_s:,} pairs, {sec:.1f} s)",
-               "host_cpu": host_cpu(),
+               "host_cpu": host_cpu(), "stages": stage_rates(st1, p_s),
                "n_core": {"value": p_n / sec_n, "unit": UNIT, "cores": threads, "kind": "oracle",
+                          "stages": stage_rates(stn, p_n),
                           "sample": f"the same oracle routines over {threads} host threads (signatures, alignments "
                                     f"and fusion split by index range; banding single-threaded) on the same "
                                     f"donor ({p_n:,} pairs, {sec_n:.1f} s)"}}

@@ -1507,7 +1507,11 @@ int band_index_build(subquad_ctx *ctx, const uint32_t *sig, int rows, int cap, c
     uint64_t *d_total = I.counters + 1;
     unsigned long long *d_kept = reinterpret_cast<unsigned long long *>(I.counters + 2);
     SQ_TRY_CUDA(cudaMemsetAsync(I.counters, 0, 4 * sizeof(uint64_t), ctx->stream));
-    SQ_TRY_CUDA(cudaMemsetAsync(I.chunk_of, 0xff, (size_t)n * bands * sizeof(uint32_t), ctx->stream));
+    // chunk ids of bands below 32 are read only where kept_mask says the
+    // member was placed in that band (so written); bands from 32 on are
+    // compared without a mask and start as kNoChunk
+    if (bands > 32)
+        SQ_TRY_CUDA(cudaMemsetAsync(I.chunk_of, 0xff, (size_t)n * bands * sizeof(uint32_t), ctx->stream));
     SQ_TRY_CUDA(cudaMemsetAsync(I.kept_mask, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
     GroupOut go{I.kept, d_kept, d_nchunks, I.heads, I.sizes, I.cband, I.poff, I.chunk_of, I.kept_mask, S.rslot};
     for (int band0 = 0; band0 < bands; band0 += S.G) {
@@ -1601,21 +1605,28 @@ int band_emit_sorted(subquad_ctx *ctx, const BandIndex &I, uint64_t raw0, uint64
     rows_classify_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.col, pairs_out, E.sa, E.sb,
                                                                  E.mid, E.lng, d_cls);
     SQ_LAUNCH_CHECK();
-    rows_sort_small_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.sa, E.sb, d_cls, E.col,
-                                                                   pairs_out);
-    SQ_LAUNCH_CHECK();
-    rows_sort_warp_kernel<<<(unsigned)ctx->num_sms * 8, kRowThreads, 0, ctx->stream>>>(
-        E.rowoff, n, d_clamped, E.mid, d_cls + kClsWarp, E.col, pairs_out);
-    SQ_LAUNCH_CHECK();
+    // the classes are sorted concurrently (disjoint rows): the CTA radix and
+    // in-place sorts on the context stream, the register and warp sorts on
+    // the side stream, which fill the SMs around the radix CTAs
+    SQ_TRY_CUDA(cudaEventRecord(ctx->fork, ctx->stream));
+    SQ_TRY_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
     constexpr size_t kRadixSmem = (2 * (size_t)kRowMid + (size_t)kRadixWarps * 256) * sizeof(uint32_t);
     SQ_TRY_CUDA(cudaFuncSetAttribute(rows_sort_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kRadixSmem));
     rows_sort_mid_kernel<<<(unsigned)ctx->num_sms * 3, kRowThreads, kRadixSmem, ctx->stream>>>(
         E.rowoff, n, d_clamped, E.mid, d_cls + kClsCta, E.col, pairs_out);
     SQ_LAUNCH_CHECK();
+    rows_sort_small_kernel<<<rgrid, kRowThreads, 0, ctx->side>>>(E.rowoff, n, d_clamped, E.sa, E.sb, d_cls, E.col,
+                                                                 pairs_out);
+    SQ_LAUNCH_CHECK();
+    rows_sort_warp_kernel<<<(unsigned)ctx->num_sms * 8, kRowThreads, 0, ctx->side>>>(
+        E.rowoff, n, d_clamped, E.mid, d_cls + kClsWarp, E.col, pairs_out);
+    SQ_LAUNCH_CHECK();
     rows_sort_long_kernel<<<(unsigned)ctx->num_sms, 1024, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.lng, d_cls + kClsLong,
                                                                            E.col, pairs_out);
     SQ_LAUNCH_CHECK();
+    SQ_TRY_CUDA(cudaEventRecord(ctx->join, ctx->side));
+    SQ_TRY_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->join, 0));
     return SUBQUAD_OK;
 }
 

@@ -87,6 +87,9 @@ extern "C" int subquad_create(subquad_ctx **out, int device, void *cuda_stream)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, 256);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_small, 16 * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 8 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, 256, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
@@ -172,6 +175,12 @@ extern "C" int subquad_destroy(subquad_ctx *ctx)
             cudaFree(ctx->d_err);
             cudaFree(ctx->d_small);
             cudaFreeHost(ctx->h_pinned);
+            if (ctx->side) {
+                cudaStreamSynchronize(ctx->side);
+                cudaStreamDestroy(ctx->side);
+            }
+            if (ctx->fork) cudaEventDestroy(ctx->fork);
+            if (ctx->join) cudaEventDestroy(ctx->join);
         }
     }
     delete ctx;

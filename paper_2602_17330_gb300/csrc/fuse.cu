@@ -1,10 +1,12 @@
 // (a4) Per-pair gated fusion of the alignment and embedding channels
 // (Eq. alpha, Eq. wm, Eq. afused with M = 2 channels), and its adjoint.
 //
-// Forward: four lanes own one pair (eight pairs per warp).  Each lane loads
-// d/16 float4 slices of e_i and e_j (for d = 64 a pair's two rows are read as
-// 4 x 64-byte pieces), accumulates the dot product and both squared norms,
-// and two shuffle levels finish them; each lane then evaluates hidden units
+// Forward: four lanes own one pair (eight pairs per warp).  When d % 8 == 0
+// (and d <= 128) each lane reads 32-byte chunks of e_i and e_j with 256-bit
+// loads, so a pair's four lanes read one whole 128-byte line of a row per
+// load (for d = 64, two loads per row); otherwise 16-byte chunks.  Each lane
+// accumulates the dot product and both squared norms, and two shuffle levels
+// finish them; each lane then evaluates hidden units
 // k = lane, lane + 4, ... of the gate MLP from parameters staged in shared
 // memory, and two more shuffle levels give the logit g.  alpha = sigmoid(g)
 // is the two-logit softmax of Eq. wm with logits (g, 0).  The kernel is
@@ -46,12 +48,31 @@ __device__ __forceinline__ float lanes_sum(float v)
     return v;
 }
 
+// One 32-byte load (a 256-bit vector load of the read-only path) into two
+// float4; p must be 32-byte aligned.
+__device__ __forceinline__ void ldg_v8(const float *p, float4 &lo, float4 &hi)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+        : "l"(p));
+}
+
+__device__ __forceinline__ void ldg_v8u(const uint32_t *p, uint4 &lo, uint4 &hi)
+{
+    asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+        : "l"(p));
+}
+
 // Per-pair inputs of the fusion, all loads issued together so one round trip
 // to memory (after the pair indices) covers the embedding rows, the alignment
-// score, both self-scores and both lengths.
-template <int WORDS, int CPL, int TPP = kTpp>
+// score, both self-scores and both lengths.  A lane loads CPL chunks of V
+// float4 from each row: V = 1 (16-byte loads; chunk k = float4 k) or V = 2
+// (32-byte loads, rows 32-byte aligned; chunk k = floats 8k .. 8k + 7), the
+// pair's TPP lanes taking consecutive chunks.
+template <int WORDS, int CPL, int TPP = kTpp, int V = 1>
 struct PairInputs {
-    float4 a[CPL], b[CPL];
+    float4 a[CPL * V], b[CPL * V];
     int32_t sw, self_i, self_j;
     int len_i, len_j;
 
@@ -59,14 +80,29 @@ struct PairInputs {
                                          int d, const int32_t *__restrict__ sw_in, const int32_t *__restrict__ self_sc,
                                          const uint64_t *__restrict__ packed)
     {
-        const float4 *ei = reinterpret_cast<const float4 *>(emb + (int64_t)ij.x * d);
-        const float4 *ej = reinterpret_cast<const float4 *>(emb + (int64_t)ij.y * d);
+        if (V == 2) {
+            const float *ei = emb + (int64_t)ij.x * d, *ej = emb + (int64_t)ij.y * d;
+            const int d8 = d4 >> 1;
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int k = sub + c * TPP;
-            const bool ok = valid && k < d4;
-            a[c] = ok ? __ldg(ei + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-            b[c] = ok ? __ldg(ej + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < CPL; ++c) {
+                const int k = sub + c * TPP;
+                if (valid && k < d8) {
+                    ldg_v8(ei + 8 * k, a[V * c], a[V * c + V - 1]);
+                    ldg_v8(ej + 8 * k, b[V * c], b[V * c + V - 1]);
+                } else {
+                    a[V * c] = a[V * c + V - 1] = b[V * c] = b[V * c + V - 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        } else {
+            const float4 *ei = reinterpret_cast<const float4 *>(emb + (int64_t)ij.x * d);
+            const float4 *ej = reinterpret_cast<const float4 *>(emb + (int64_t)ij.y * d);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                const int k = sub + c * TPP;
+                const bool ok = valid && k < d4;
+                a[c] = ok ? __ldg(ei + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                b[c] = ok ? __ldg(ej + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
         sw = 0;
         self_i = self_j = 0;
@@ -83,7 +119,7 @@ struct PairInputs {
     }
 };
 
-template <int WORDS, int CPL, int TPPF>
+template <int WORDS, int CPL, int TPPF, int V = 1>
 __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
     const uint32_t *__restrict__ pairs, int64_t m_max, const unsigned long long *__restrict__ d_m,
     const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc, const uint64_t *__restrict__ packed,
@@ -121,11 +157,11 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_kernel(
         const bool valid = p < m;
         const uint2 ij = valid ? ij_next : make_uint2(0, 0);
         ij_next = p + pstep < m ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p + pstep) : make_uint2(0, 0);
-        PairInputs<WORDS, CPL, TPPF> in;
+        PairInputs<WORDS, CPL, TPPF, V> in;
         in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
         float dot = 0.f, sii = 0.f, sjj = 0.f;
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
+        for (int c = 0; c < CPL * V; ++c) {
             const float4 a = in.a[c], b = in.b[c];
             dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, dot))));
             sii = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, sii))));
@@ -159,6 +195,19 @@ int launch_forward_t(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int
                      const int32_t *self_scores, const void *packed, const float *emb, int d, const float *gate_params,
                      int hidden, float *fused_out, float *alpha_out, const unsigned long long *d_m)
 {
+    if (d % 8 == 0 && d <= 8 * 4 * TPPF && reinterpret_cast<uintptr_t>(emb) % 32 == 0) {
+        // 32-byte lane loads: four lanes read a 128-byte line of a row per load
+        const int cpl8 = (d / 8 + TPPF - 1) / TPPF;
+#define SQ_FWD8(C)                                                                                                 \
+    fuse_forward_kernel<WORDS, C, TPPF, 2><<<grid, kFuseThreads, 0, ctx->stream>>>(                                \
+        pairs, m, d_m, sw, self_scores, (const uint64_t *)packed, emb, d, gate_params, hidden, fused_out, alpha_out)
+        if (cpl8 <= 1) SQ_FWD8(1);
+        else if (cpl8 <= 2) SQ_FWD8(2);
+        else SQ_FWD8(4);
+#undef SQ_FWD8
+        SQ_LAUNCH_CHECK();
+        return SUBQUAD_OK;
+    }
     const int cpl = (d / 4 + TPPF - 1) / TPPF;  // float4 chunks per lane
 #define SQ_FWD(C)                                                                                                  \
     fuse_forward_kernel<WORDS, C, TPPF><<<grid, kFuseThreads, 0, ctx->stream>>>(                                   \
@@ -175,9 +224,8 @@ int launch_forward_t(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int
     return SUBQUAD_OK;
 }
 
-// Lanes per pair from the context's tuning: 4 (eight pairs per warp; each lane
-// load covers half a 128-byte line of a row) or 8 (four pairs per warp; a
-// pair's eight lanes read a whole line per load).
+// Lanes per pair from the context's tuning: 4 (eight pairs per warp) or 8
+// (four pairs per warp).
 template <int WORDS>
 int launch_forward(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, int64_t m, const int32_t *sw,
                    const int32_t *self_scores, const void *packed, const float *emb, int d, const float *gate_params,
@@ -623,13 +671,23 @@ namespace {
 // subquad_sig_sequence_major), so a member's H words are one contiguous row:
 // with H % 4 == 0 lane q compares 16-byte chunks q, q + LANES, ... of the two
 // rows (a pair's lanes read consecutive chunks), else single words.
-template <int LANES>
+template <int LANES, int V = 1>
 __device__ __forceinline__ int sig_agree(const uint32_t *__restrict__ sig_seq, int H, uint32_t i, uint32_t j, int sub,
                                          bool valid)
 {
     int agree = 0;
     if (!valid) return 0;
-    if ((H & 3) == 0) {
+    if (V == 2) {  // H % 8 == 0, rows 32-byte aligned: 32-byte chunks, a pair's lanes read whole lines
+        const int H8 = H >> 3;
+        const uint32_t *ri = sig_seq + (int64_t)i * H, *rj = sig_seq + (int64_t)j * H;
+        for (int c = sub; c < H8; c += LANES) {
+            uint4 x0, x1, y0, y1;
+            ldg_v8u(ri + 8 * c, x0, x1);
+            ldg_v8u(rj + 8 * c, y0, y1);
+            agree += (x0.x == y0.x) + (x0.y == y0.y) + (x0.z == y0.z) + (x0.w == y0.w) + (x1.x == y1.x) +
+                     (x1.y == y1.y) + (x1.z == y1.z) + (x1.w == y1.w);
+        }
+    } else if ((H & 3) == 0) {
         const int H4 = H >> 2;
         const uint4 *ri = reinterpret_cast<const uint4 *>(sig_seq) + (int64_t)i * H4;
         const uint4 *rj = reinterpret_cast<const uint4 *>(sig_seq) + (int64_t)j * H4;
@@ -686,7 +744,7 @@ struct McLayout {
     }
 };
 
-template <int M, int WORDS, int CPL>
+template <int M, int WORDS, int CPL, int V = 1>
 __global__ void __launch_bounds__(kFuseThreads) fuse_forward_mc_kernel(
     const uint32_t *__restrict__ pairs, int64_t m, const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc,
     const uint64_t *__restrict__ packed, const float *__restrict__ emb, int d, const uint32_t *__restrict__ sig,
@@ -713,12 +771,12 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_forward_mc_kernel(
         const int64_t p = pbase + slot;
         const bool valid = p < m;
         const uint2 ij = valid ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p) : make_uint2(0, 0);
-        PairInputs<WORDS, CPL, kTppF> in;
+        PairInputs<WORDS, CPL, kTppF, V> in;
         in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
-        int agree = M == 3 ? sig_agree<kTppF>(sig, H, ij.x, ij.y, sub, valid) : 0;
+        int agree = M == 3 ? sig_agree<kTppF, V>(sig, H, ij.x, ij.y, sub, valid) : 0;
         float dot = 0.f, sii = 0.f, sjj = 0.f;
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
+        for (int c = 0; c < CPL * V; ++c) {
             const float4 a = in.a[c], b = in.b[c];
             dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, dot))));
             sii = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, sii))));
@@ -906,8 +964,22 @@ int launch_forward_mc(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, in
                       const int32_t *self_scores, const void *packed, const float *emb, int d, const uint32_t *sig,
                       int H, const float *params, int hidden, float *fused, float *weights)
 {
-    const int cpl = (d / 4 + kTppF - 1) / kTppF;
     SqProfScope prof(ctx, SUBQUAD_PROF_FUSE);
+    if (d % 8 == 0 && d <= 8 * 4 * kTppF && reinterpret_cast<uintptr_t>(emb) % 32 == 0 &&
+        (M == 2 || (H % 8 == 0 && reinterpret_cast<uintptr_t>(sig) % 32 == 0))) {
+        // 32-byte lane loads of the rows and signatures (whole lines per pair and load)
+        const int cpl8 = (d / 8 + kTppF - 1) / kTppF;
+#define SQ_FWDMC8(C)                                                                                               \
+    fuse_forward_mc_kernel<M, WORDS, C, 2><<<grid, kFuseThreads, 0, ctx->stream>>>(                                \
+        pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d, sig, H, params, hidden, fused, weights)
+        if (cpl8 <= 1) SQ_FWDMC8(1);
+        else if (cpl8 <= 2) SQ_FWDMC8(2);
+        else SQ_FWDMC8(4);
+#undef SQ_FWDMC8
+        SQ_LAUNCH_CHECK();
+        return SUBQUAD_OK;
+    }
+    const int cpl = (d / 4 + kTppF - 1) / kTppF;
 #define SQ_FWDMC(C)                                                                                                \
     fuse_forward_mc_kernel<M, WORDS, C><<<grid, kFuseThreads, 0, ctx->stream>>>(                                   \
         pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d, sig, H, params, hidden, fused, weights)

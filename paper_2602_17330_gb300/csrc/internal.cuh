@@ -26,6 +26,11 @@ struct SqProfRecord {
 struct subquad_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    // a second stream of the library's own, forked from and joined back to
+    // `stream` by events inside one call, for independent kernels that can
+    // share the GPU (graph capture records the fork as parallel branches)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     int num_sms = 0;
     int8_t h_matrix[400];   // scoring matrix, row = first sequence's residue
     bool matrix_symmetric = true;

@@ -488,13 +488,29 @@ def test_align_empty(ctx, torch):
 # (a4) fusion
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("d,hidden,scale", [(64, 16, False), (128, 32, True), (4, 1, True), (36, 64, False)])
-def test_fuse_forward_within_tolerance(ctx, torch, oracle_mod, d, hidden, scale):
+def _row_heavy_pairs(rng, n, count):
+    """Sorted pairs whose first members have long runs of partners (as in a
+    candidate list with large buckets), plus short rows and singletons."""
+    heads = rng.choice(n - 1, 40, replace=False)
+    parts = []
+    for h in heads:
+        deg = int(rng.integers(1, 400))
+        parts.append(np.stack([np.full(deg, h), rng.integers(h + 1, n, deg)], axis=1))
+    parts.append(np.sort(rng.integers(0, n, (count, 2)), axis=1))
+    pairs = np.unique(np.concatenate(parts), axis=0)
+    return pairs[pairs[:, 0] < pairs[:, 1]].astype(np.uint32)
+
+
+@pytest.mark.parametrize("lanes", [4, 8])
+@pytest.mark.parametrize("d,hidden,scale", [(64, 16, False), (128, 32, True), (4, 1, True), (36, 64, False),
+                                            (256, 17, True), (260, 16, False)])
+def test_fuse_forward_within_tolerance(ctx, torch, oracle_mod, d, hidden, scale, lanes):
+    from paper_2602_17330_gb300 import subquad
+
     rep = synth.tiny_repertoire()
     packed = ctx.pack(torch.from_numpy(rep.codes), torch.from_numpy(rep.lens), 16)
     rng = np.random.default_rng(d)
-    pairs = np.unique(np.sort(rng.integers(0, rep.n, (20_001, 2)), axis=1), axis=0)
-    pairs = pairs[pairs[:, 0] < pairs[:, 1]].astype(np.uint32)
+    pairs = _row_heavy_pairs(rng, rep.n, 20_001)
     emb = synth.family_embeddings(rep.family, d, seed=d)
     if scale:
         emb = np.ascontiguousarray(emb * rng.uniform(0.2, 5.0, (rep.n, 1)).astype(np.float32))
@@ -505,9 +521,22 @@ def test_fuse_forward_within_tolerance(ctx, torch, oracle_mod, d, hidden, scale)
     self_o = oracle_mod.self_scores(rep.codes, rep.lens)
     sw = torch.from_numpy(sw_o).to(ctx.device)
     self_sc = torch.from_numpy(self_o).to(ctx.device)
-    fused, alpha = ctx.fuse_forward(tp, sw, self_sc, packed, torch.from_numpy(emb), torch.from_numpy(params), hidden,
-                                    want_alpha=True)
+    old = ctx.get_tuning(subquad.TUNE_FUSE_LANES)
+    try:
+        ctx.set_tuning(subquad.TUNE_FUSE_LANES, lanes)
+        fused, alpha = ctx.fuse_forward(tp, sw, self_sc, packed, torch.from_numpy(emb), torch.from_numpy(params),
+                                        hidden, want_alpha=True)
+        # a ragged tail and an empty list through the same launch shape
+        tail = pairs.shape[0] - 13
+        fused_t = ctx.fuse_forward(tp[:tail], sw[:tail], self_sc, packed, torch.from_numpy(emb),
+                                   torch.from_numpy(params), hidden)
+        empty = ctx.fuse_forward(tp[:0], sw[:0], self_sc, packed, torch.from_numpy(emb), torch.from_numpy(params),
+                                 hidden)
+    finally:
+        ctx.set_tuning(subquad.TUNE_FUSE_LANES, old)
     want = oracle_mod.fuse_forward(pairs, sw_o, self_o, rep.lens, emb, params, hidden)
+    assert to_np(empty).shape[0] == 0
+    assert (to_np(fused_t) == to_np(fused)[:tail]).all()  # a pair's result does not depend on its neighbours
     assert_fused_close(to_np(fused), want["fused"])
     assert_fused_close(to_np(alpha), want["alpha"])
 
