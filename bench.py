@@ -203,8 +203,8 @@ class ClockSampler:
 def oracle_step(n_sample: int, seed: int = 0, threads: int = 1, with_stages: bool = False):
     """One pass of the oracle over a donor repertoire of n_sample sequences
     (same generator, families of 25, same hashing).  threads > 1 runs the
-    signatures, alignments and fusion over that many host threads (the
-    oracle's threaded runners; the banding stays single-threaded).  Returns
+    signatures, bands, alignments and fusion over that many host threads
+    (the oracle's threaded runners).  Returns
     (pairs, seconds), plus the seconds of each stage and the DP cell count
     with with_stages."""
     import oracle
@@ -220,7 +220,7 @@ def oracle_step(n_sample: int, seed: int = 0, threads: int = 1, with_stages: boo
     if threads > 1:
         sig = oracle.sign_mt(rep.codes, rep.lens, cfg.k, a, b, threads)
         marks.append(time.perf_counter())
-        pairs = oracle.candidates(sig, cfg.bands, cfg.rows, cfg.bucket_cap)
+        pairs = oracle.candidates_mt(sig, cfg.bands, cfg.rows, cfg.bucket_cap, threads)
         marks.append(time.perf_counter())
         self_sc = oracle.sw_pairs_mt(rep.codes, rep.lens, np.stack([idx, idx], 1), threads, cfg.gap_open,
                                      cfg.gap_extend)
@@ -579,7 +579,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                "n_core": {"value": p_n / sec_n, "unit": UNIT, "cores": threads, "kind": "oracle",
                           "stages": stage_rates(stn, p_n),
                           "sample": f"the same oracle routines over {threads} host threads (signatures, alignments "
-                                    f"and fusion split by index range; banding single-threaded) on the same "
+                                    f"and fusion split by index range, bands split by band) on the same "
                                     f"donor ({p_n:,} pairs, {sec_n:.1f} s)"}}
 
     if rank == 0:
@@ -1063,7 +1063,7 @@ def oracle_tiny_step(rep, cfg, a, b, emb, params, threads):
     t0 = time.perf_counter()
     if threads > 1:
         sig = oracle.sign_mt(rep.codes, rep.lens, cfg.k, a, b, threads)
-        pairs = oracle.candidates(sig, cfg.bands, cfg.rows, cfg.bucket_cap)
+        pairs = oracle.candidates_mt(sig, cfg.bands, cfg.rows, cfg.bucket_cap, threads)
         self_sc = oracle.sw_pairs_mt(rep.codes, rep.lens, np.stack([idx, idx], 1), threads, cfg.gap_open,
                                      cfg.gap_extend)
         sw = oracle.sw_pairs_mt(rep.codes, rep.lens, pairs, threads, cfg.gap_open, cfg.gap_extend)

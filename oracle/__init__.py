@@ -57,6 +57,8 @@ def _load():
     lib.oracle_sign.restype = None
     lib.oracle_candidates.argtypes = [U32P, c.c_int64, c.c_int, c.c_int, c.c_int, c.c_int, U32P, c.c_int64]
     lib.oracle_candidates.restype = c.c_int64
+    lib.oracle_candidates_mt.argtypes = [U32P, c.c_int64, c.c_int, c.c_int, c.c_int, c.c_int, U32P, c.c_int64, c.c_int]
+    lib.oracle_candidates_mt.restype = c.c_int64
     lib.oracle_sw.argtypes = [U8P, c.c_int, U8P, c.c_int, I32P, c.c_int, c.c_int]
     lib.oracle_sw.restype = c.c_int32
     lib.oracle_sw_pairs.argtypes = [U8P, c.c_int, U8P, U32P, c.c_int64, I32P, c.c_int, c.c_int, I32P]
@@ -170,6 +172,24 @@ def candidates(sig, bands: int, rows: int, cap: int = 0) -> np.ndarray:
         cnt = lib.oracle_candidates(sig, n, H, bands, rows, cap, out, capacity)
         if cnt < 0:
             raise MemoryError("oracle_candidates failed")
+        if cnt <= capacity:
+            return out[:cnt].copy()
+        capacity = int(cnt)
+
+
+def candidates_mt(sig, bands: int, rows: int, cap: int, threads: int) -> np.ndarray:
+    """candidates() with the bands split over `threads` host threads (the
+    same per-band routine and the same sort and deduplication: identical
+    output)."""
+    sig = _c(sig, np.uint32)
+    n, H = sig.shape
+    lib = _load()
+    capacity = max(1024, 4 * n)
+    while True:
+        out = np.zeros((capacity, 2), dtype=np.uint32)
+        cnt = lib.oracle_candidates_mt(sig, n, H, bands, rows, cap, out, capacity, int(threads))
+        if cnt < 0:
+            raise MemoryError("oracle_candidates_mt failed")
         if cnt <= capacity:
             return out[:cnt].copy()
         capacity = int(cnt)

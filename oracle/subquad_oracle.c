@@ -119,7 +119,7 @@ typedef struct {
     uint32_t id;
 } band_rec;
 
-static int g_rows; /* qsort has no context argument; single-threaded by design */
+static int g_rows; /* qsort has no context argument: set before any sort, never changed during one */
 
 static int cmp_band_rec(const void *pa, const void *pb)
 {
@@ -155,16 +155,13 @@ static int u64vec_push(u64vec *vec, uint64_t x)
     return 0;
 }
 
-/* Returns |C| (or -1 on allocation failure); writes min(|C|, out_capacity)
- * pairs, lexicographically sorted, as out[2q] = i, out[2q+1] = j. */
-int64_t oracle_candidates(const uint32_t *sig /* [n][H] */, int64_t n, int H, int bands, int rows,
-                          int cap, uint32_t *out, int64_t out_capacity)
+/* Appends the pairs (i << 32 | j) of every chunk of bands 0 .. bands-1 of
+ * sig to *all, duplicates included; g_rows must equal rows.  Returns 0, or -1
+ * on allocation failure. */
+static int band_chunk_pairs(const uint32_t *sig, int64_t n, int H, int bands, int rows, int cap, u64vec *all)
 {
-    if (rows < 1 || rows > 8 || bands * rows > H) return -1;
     band_rec *recs = (band_rec *)malloc((size_t)(n > 0 ? n : 1) * sizeof(band_rec));
-    u64vec all = {0, 0, 0};
     if (!recs) return -1;
-    g_rows = rows;
     for (int b = 0; b < bands; ++b) {
         for (int64_t i = 0; i < n; ++i) {
             memset(recs[i].key, 0, sizeof(recs[i].key));
@@ -179,10 +176,8 @@ int64_t oracle_candidates(const uint32_t *sig /* [n][H] */, int64_t n, int H, in
             for (int64_t u = s; u < e; ++u)
                 for (int64_t v = u + 1; v < e; ++v) {
                     int same_chunk = cap <= 0 || ((u - s) / cap == (v - s) / cap);
-                    if (same_chunk &&
-                        u64vec_push(&all, ((uint64_t)recs[u].id << 32) | recs[v].id) != 0) {
+                    if (same_chunk && u64vec_push(all, ((uint64_t)recs[u].id << 32) | recs[v].id) != 0) {
                         free(recs);
-                        free(all.v);
                         return -1;
                     }
                 }
@@ -190,18 +185,41 @@ int64_t oracle_candidates(const uint32_t *sig /* [n][H] */, int64_t n, int H, in
         }
     }
     free(recs);
-    if (all.len > 0) qsort(all.v, (size_t)all.len, sizeof(uint64_t), cmp_u64);
+    return 0;
+}
+
+/* The pairs of *all sorted, duplicates dropped, written to out (at most
+ * out_capacity); returns their count.  Frees all->v. */
+static int64_t sorted_unique_pairs(u64vec *all, uint32_t *out, int64_t out_capacity)
+{
+    if (all->len > 0) qsort(all->v, (size_t)all->len, sizeof(uint64_t), cmp_u64);
     int64_t count = 0;
-    for (int64_t q = 0; q < all.len; ++q) {
-        if (q > 0 && all.v[q] == all.v[q - 1]) continue;
+    for (int64_t q = 0; q < all->len; ++q) {
+        if (q > 0 && all->v[q] == all->v[q - 1]) continue;
         if (count < out_capacity) {
-            out[2 * count] = (uint32_t)(all.v[q] >> 32);
-            out[2 * count + 1] = (uint32_t)(all.v[q] & 0xffffffffu);
+            out[2 * count] = (uint32_t)(all->v[q] >> 32);
+            out[2 * count + 1] = (uint32_t)(all->v[q] & 0xffffffffu);
         }
         ++count;
     }
-    free(all.v);
+    free(all->v);
+    all->v = NULL;
     return count;
+}
+
+/* Returns |C| (or -1 on allocation failure); writes min(|C|, out_capacity)
+ * pairs, lexicographically sorted, as out[2q] = i, out[2q+1] = j. */
+int64_t oracle_candidates(const uint32_t *sig /* [n][H] */, int64_t n, int H, int bands, int rows,
+                          int cap, uint32_t *out, int64_t out_capacity)
+{
+    if (rows < 1 || rows > 8 || bands * rows > H) return -1;
+    u64vec all = {0, 0, 0};
+    g_rows = rows;
+    if (band_chunk_pairs(sig, n, H, bands, rows, cap, &all) != 0) {
+        free(all.v);
+        return -1;
+    }
+    return sorted_unique_pairs(&all, out, out_capacity);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -820,7 +838,8 @@ int oracle_topk(const uint32_t *pairs, const int32_t *scores, int64_t m, const i
  * and calls the single-threaded routine above on each piece in its own POSIX
  * thread; results land in the same places, so the output is identical to the
  * single-threaded call.  Signatures are split by sequence, alignments and
- * fusion by pair.                                                           */
+ * fusion by pair; the candidate set by band (oracle_candidates_mt, after the
+ * single-threaded per-band routine, with one final sort and deduplication). */
 /* ------------------------------------------------------------------------- */
 #include <pthread.h>
 
@@ -898,6 +917,82 @@ static int mt_launch(mt_job *proto, int64_t count, int threads)
     free(jobs);
     free(tid);
     return rc;
+}
+
+/* Candidates over `threads` threads: thread t runs band_chunk_pairs on its
+ * own contiguous range of bands into its own vector (g_rows is set once
+ * before the threads start); the vectors are concatenated, sorted and
+ * deduplicated as in oracle_candidates, so the output is identical. */
+typedef struct {
+    const uint32_t *sig;
+    int64_t n;
+    int H, b0, b1, rows, cap, rc;
+    u64vec part;
+} cand_job;
+
+static void *cand_run(void *arg)
+{
+    cand_job *j = (cand_job *)arg;
+    if (j->b1 > j->b0)
+        j->rc = band_chunk_pairs(j->sig + (int64_t)j->b0 * j->rows, j->n, j->H, j->b1 - j->b0, j->rows, j->cap,
+                                 &j->part);
+    return NULL;
+}
+
+int64_t oracle_candidates_mt(const uint32_t *sig, int64_t n, int H, int bands, int rows, int cap, uint32_t *out,
+                             int64_t out_capacity, int threads)
+{
+    if (rows < 1 || rows > 8 || bands * rows > H) return -1;
+    if (threads < 1) threads = 1;
+    if (threads > bands) threads = bands;
+    cand_job *jobs = (cand_job *)calloc((size_t)threads, sizeof(cand_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    int rc = 0;
+    if (!jobs || !tid) {
+        free(jobs);
+        free(tid);
+        return -1;
+    }
+    g_rows = rows;
+    for (int t = 0; t < threads; ++t) {
+        jobs[t].sig = sig;
+        jobs[t].n = n;
+        jobs[t].H = H;
+        jobs[t].rows = rows;
+        jobs[t].cap = cap;
+        jobs[t].b0 = (int)((int64_t)bands * t / threads);
+        jobs[t].b1 = (int)((int64_t)bands * (t + 1) / threads);
+        if (pthread_create(&tid[t], NULL, cand_run, &jobs[t]) != 0) {
+            cand_run(&jobs[t]); /* run inline if a thread cannot be started */
+            tid[t] = 0;
+        }
+    }
+    int64_t total = 0;
+    for (int t = 0; t < threads; ++t) {
+        if (tid[t]) pthread_join(tid[t], NULL);
+        if (jobs[t].rc) rc = jobs[t].rc;
+        total += jobs[t].part.len;
+    }
+    u64vec all = {0, 0, 0};
+    if (rc == 0 && total > 0) {
+        all.v = (uint64_t *)malloc((size_t)total * sizeof(uint64_t));
+        if (!all.v) rc = -1;
+    }
+    for (int t = 0; t < threads; ++t) {
+        if (rc == 0 && jobs[t].part.len > 0) {
+            memcpy(all.v + all.len, jobs[t].part.v, (size_t)jobs[t].part.len * sizeof(uint64_t));
+            all.len += jobs[t].part.len;
+        }
+        free(jobs[t].part.v);
+    }
+    free(jobs);
+    free(tid);
+    if (rc != 0) {
+        free(all.v);
+        return -1;
+    }
+    all.cap = all.len;
+    return sorted_unique_pairs(&all, out, out_capacity);
 }
 
 int oracle_sign_mt(const uint8_t *codes, int code_stride, const uint8_t *lens, int64_t n, int k, int H,

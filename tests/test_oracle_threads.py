@@ -14,6 +14,11 @@ def test_threaded_runners_equal_single_thread(oracle_mod, threads):
     sig = oracle_mod.sign(rep.codes, rep.lens, 3, a, b)
     assert (oracle_mod.sign_mt(rep.codes, rep.lens, 3, a, b, threads) == sig).all()
     C = oracle_mod.candidates(sig, 16, 4, 2048)
+    assert np.array_equal(oracle_mod.candidates_mt(sig, 16, 4, 2048, threads), C)
+    # a cap that splits buckets, no cap, and bands of other shapes
+    for bands, rows, cap in ((16, 4, 3), (32, 2, 0), (5, 3, 0)):
+        assert np.array_equal(oracle_mod.candidates_mt(sig, bands, rows, cap, threads),
+                              oracle_mod.candidates(sig, bands, rows, cap))
     sw = oracle_mod.sw_pairs(rep.codes, rep.lens, C)
     assert (oracle_mod.sw_pairs_mt(rep.codes, rep.lens, C, threads) == sw).all()
     self_sc = oracle_mod.self_scores(rep.codes, rep.lens)
