@@ -492,6 +492,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if args.configs:
             configs = {}
             for name, fn in (("config1_tiny", lambda: run_config1(args, ctx, stream)),
+                             ("seeds_1_4", lambda: run_seed_variance(args, ctx, stream, flush)),
                              ("config4_trajectory", lambda: run_config4_trajectory(args, ctx, stream, rep, step_pipe, m)),
                              ("recall_vs_band_shape", lambda: run_recall_sweep(args, ctx, stream)),
                              ("config5_full", lambda: run_config5(args, ctx, stream, flush))):
@@ -999,6 +1000,63 @@ def run_config5(args, ctx, stream, flush):
             "recall_explained": explained,
             "recall_note": "tie-aware recall@50 of the candidate route against the exhaustive top-50 among other "
                            "donors' sequences, on a seeded 10,000-query subsample of the 100,000 queries"}
+
+
+def run_seed_variance(args, ctx, stream, flush):
+    """Configs 1 and 2 again with seeds 1-4 (other repertoires, embeddings
+    and gate parameters from the same generators; the hash functions stay
+    those of seed 0): for the 1M donor |C|, DP cells and the graph-replayed
+    step time (10 replays, L2 flushed between them); for the tiny
+    repertoire |C| and its equality with the oracle's candidate set."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2602_17330_gb300 import pipeline, synth
+
+    out = {}
+    a, b = synth.hash_coefficients(64, seed=0)
+    for seed in (1, 2, 3, 4):
+        res = {}
+        tiny = synth.tiny_repertoire(seed=seed)
+        cfg1 = pipeline.TINY
+        bp1 = pipeline.BatchedPipeline(ctx, cfg1, tiny.n, capacity=tiny.n * (tiny.n - 1) // 2)
+        with torch.cuda.stream(stream):
+            x1 = pipeline.Pipeline(ctx, cfg1).upload(tiny, a, b, synth.unit_embeddings(tiny.n, cfg1.d, seed=seed),
+                                                   synth.gate_parameters(cfg1.hidden, seed=seed))
+            bp1.step(x1)
+        got = bp1.result()["pairs"]
+        want = oracle.candidates(oracle.sign(tiny.codes, tiny.lens, cfg1.k, a, b), cfg1.bands, cfg1.rows, 0)
+        res["tiny_pairs"] = int(want.shape[0])
+        res["tiny_pairs_equal_oracle"] = got.shape == want.shape and bool((got == want).all())
+        cfg = pipeline.DONOR_1M
+        rep = synth.donor_repertoire(cfg.n, seed=seed)
+        bp = pipeline.BatchedPipeline(ctx, cfg, cfg.n, capacity=8 * cfg.n)
+        with torch.cuda.stream(stream):
+            x = pipeline.Pipeline(ctx, cfg).upload(rep, a, b, synth.unit_embeddings(rep.n, cfg.d, seed=seed),
+                                                  synth.gate_parameters(cfg.hidden, seed=seed))
+        bp.capture(x)
+        ts = []
+        with torch.cuda.stream(stream):
+            for _ in range(10):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                bp.replay()
+                e1.record(stream)
+                ts.append((e0, e1))
+        stream.synchronize()
+        ctx.check()
+        m = int(bp.num_pairs.item())
+        ms = float(np.median([e0.elapsed_time(e1) for e0, e1 in ts]))
+        res.update(donor_pairs=m, donor_cells=int(pipeline.cells_of(rep.lens, bp.pairs[:m].cpu().numpy().view(np.uint32))),
+                   donor_ms_per_step=ms, donor_pairs_per_s=m / (ms / 1e3))
+        out[str(seed)] = res
+        del bp, x
+    vals = [r["donor_pairs_per_s"] for r in out.values()]
+    out["donor_pairs_per_s_mean"] = float(np.mean(vals))
+    out["donor_pairs_per_s_rel_spread"] = float((max(vals) - min(vals)) / np.mean(vals))
+    return out
 
 
 def run_config1(args, ctx, stream):

@@ -428,7 +428,7 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
     // carries two dependency chains (F -> max -> H -> H-o) instead of one.  A
     // column beyond the target's length scores every cell with the padding
     // residue and can never raise the maximum.
-    uint32_t bestA = 0u, bestB = 0u;
+    uint32_t best = 0u;
     TargetStream<WORDS> sP(tP), sQ(tQ);
     const int Lt = max(LtP, LtQ);
     for (int j = 0; j < Lt; j += 2) {
@@ -444,6 +444,7 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
         uint32_t dB = neg_o, upB = neg_o, FB = 0u;
 #pragma unroll
         for (int p = 0; p <= NQ; ++p) {
+            uint32_t hA = 0u, hB = 0u;
             if (p < NQ) {  // column j, row p
                 uint32_t s_o;
                 if (SPLIT) {
@@ -457,12 +458,11 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
                 }
                 const uint32_t e_new = __viaddmax_s16x2_relu(E[p], neg_e, HM[p]);
                 FA = __viaddmax_s16x2_relu(FA, neg_e, upA);
-                const uint32_t h = __viaddmax_s16x2_relu(dA, s_o, __vmaxs2(e_new, FA));
+                hA = __viaddmax_s16x2_relu(dA, s_o, __vmaxs2(e_new, FA));
                 dA = HM[p];
-                HM[p] = __vadd2(h, neg_o);
+                HM[p] = __vadd2(hA, neg_o);
                 upA = HM[p];
                 E[p] = e_new;
-                bestA = __vmaxs2(bestA, h);
             }
             if (p >= 1) {  // column j + 1, row p - 1
                 const int r = p >= 1 ? p - 1 : 0;
@@ -478,16 +478,18 @@ __device__ __forceinline__ uint32_t sw_pair2(const Rec<WORDS> &qP, int LqP, cons
                 }
                 const uint32_t e_new = __viaddmax_s16x2_relu(E[r], neg_e, HM[r]);
                 FB = __viaddmax_s16x2_relu(FB, neg_e, upB);
-                const uint32_t h = __viaddmax_s16x2_relu(dB, s_o, __vmaxs2(e_new, FB));
+                hB = __viaddmax_s16x2_relu(dB, s_o, __vmaxs2(e_new, FB));
                 dB = HM[r];
-                HM[r] = __vadd2(h, neg_o);
+                HM[r] = __vadd2(hB, neg_o);
                 upB = HM[r];
                 E[r] = e_new;
-                bestB = __vmaxs2(bestB, h);
             }
+            // the running maximum takes both chains' cells with one 3-input max
+            // (a cell outside its chain's range is 0 and changes nothing)
+            best = __vimax3_s16x2_relu(best, hA, hB);
         }
     }
-    return __vmaxs2(bestA, bestB);
+    return best;
 }
 
 // Launch shapes of the batched kernel: 0 = 256 threads, 2 blocks per SM (128
