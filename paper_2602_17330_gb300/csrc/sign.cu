@@ -20,17 +20,20 @@ constexpr uint32_t kP31 = 0x7fffffffu;
 // is v >> 31 and the low word shifted right by one is v mod 2^31; their sum
 // r < P + 2^26 < 2P, so one conditional subtract finishes the reduction, and
 // min3 over (r, r - P) picks it (r - P wraps above r when r < P).
-__device__ __forceinline__ uint32_t hash_min(uint32_t best, uint32_t a2, uint32_t b2, uint32_t x)
+// The low word's shift is formed as the high half of a multiply by 2^31 and
+// r - P as a multiply-add by the runtime constant unit (= 1), so both run on
+// the FMA pipe beside the minima on the ALU pipe.
+__device__ __forceinline__ uint32_t hash_min(uint32_t best, uint32_t a2, uint32_t b2, uint32_t x, uint32_t unit)
 {
     const uint64_t w = (uint64_t)a2 * x + b2;
-    const uint32_t r = (uint32_t)(w >> 32) + ((uint32_t)w >> 1);
-    return min(best, min(r, r - kP31));
+    const uint32_t r = __umulhi((uint32_t)w, 0x80000000u) + (uint32_t)(w >> 32);
+    return min(best, min(r, r * unit - kP31));
 }
 
 template <int WORDS, int NK>
 __device__ __forceinline__ void sign_one(const uint64_t *__restrict__ w, int L, int k, int64_t i, int64_t n,
                                          int bands, int rows, const uint2 *__restrict__ s_ab,
-                                         uint32_t *__restrict__ sig)
+                                         uint32_t *__restrict__ sig, uint32_t unit)
 {
     constexpr int MAXLEN = WORDS == 2 ? 24 : 30;
     uint32_t c[MAXLEN];
@@ -59,7 +62,7 @@ __device__ __forceinline__ void sign_one(const uint64_t *__restrict__ w, int L, 
                 uint2 ab = s_ab[bnd * rows + r];
                 uint32_t best = 0xffffffffu;
 #pragma unroll
-                for (int p = 0; p < NK; ++p) best = hash_min(best, ab.x, ab.y, x[p]);
+                for (int p = 0; p < NK; ++p) best = hash_min(best, ab.x, ab.y, x[p], unit);
                 out[r] = nk > 0 ? best : 0xffffffffu;
             }
         }
@@ -146,14 +149,15 @@ __global__ void __launch_bounds__(kSignThreads) sign_kernel(const uint64_t *__re
             const int L = sq_record_len(w[0], w[1]);
             const int nk = valid ? L - k + 1 : 0;
             const int wmax = __reduce_max_sync(0xffffffffu, nk > 0 ? nk : 0);
+            const uint32_t unit = blockDim.x / kSignThreads;  // 1: the kernel is launched with kSignThreads
             if (valid) {
-                if (wmax <= 4) sign_one<WORDS, 4>(w, L, k, i, n, bands, rows, s_ab, sig);
-                else if (wmax <= 8) sign_one<WORDS, 8>(w, L, k, i, n, bands, rows, s_ab, sig);
-                else if (wmax <= 12) sign_one<WORDS, 12>(w, L, k, i, n, bands, rows, s_ab, sig);
-                else if (wmax <= 16) sign_one<WORDS, 16>(w, L, k, i, n, bands, rows, s_ab, sig);
-                else if (wmax <= 20) sign_one<WORDS, 20>(w, L, k, i, n, bands, rows, s_ab, sig);
-                else if (wmax <= 24) sign_one<WORDS, 24>(w, L, k, i, n, bands, rows, s_ab, sig);
-                else sign_one<WORDS, (WORDS == 2 ? 24 : 30)>(w, L, k, i, n, bands, rows, s_ab, sig);
+                if (wmax <= 4) sign_one<WORDS, 4>(w, L, k, i, n, bands, rows, s_ab, sig, unit);
+                else if (wmax <= 8) sign_one<WORDS, 8>(w, L, k, i, n, bands, rows, s_ab, sig, unit);
+                else if (wmax <= 12) sign_one<WORDS, 12>(w, L, k, i, n, bands, rows, s_ab, sig, unit);
+                else if (wmax <= 16) sign_one<WORDS, 16>(w, L, k, i, n, bands, rows, s_ab, sig, unit);
+                else if (wmax <= 20) sign_one<WORDS, 20>(w, L, k, i, n, bands, rows, s_ab, sig, unit);
+                else if (wmax <= 24) sign_one<WORDS, 24>(w, L, k, i, n, bands, rows, s_ab, sig, unit);
+                else sign_one<WORDS, (WORDS == 2 ? 24 : 30)>(w, L, k, i, n, bands, rows, s_ab, sig, unit);
             }
         }
         __syncthreads();  // s_order and s_cnt are reused by the next tile
