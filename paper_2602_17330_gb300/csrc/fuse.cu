@@ -266,8 +266,18 @@ struct Kahan {
 
 constexpr int kGroups = kFuseThreads / kTpp;  // pair groups (half-warps) per block
 
+// The adjoint runs on a fixed grid of four blocks per SM (its reduction order
+// must not depend on m); at most two float4 chunks and two hidden units per
+// lane fit the 64 registers that keep all four resident (no spill), where 76
+// left a second, quarter-full wave of blocks.
+template <int CPL, int HPL>
+constexpr int bwd_min_blocks()
+{
+    return CPL <= 2 && HPL <= 2 ? 4 : 1;
+}
+
 template <int WORDS, int CPL, int HPL>
-__global__ void __launch_bounds__(kFuseThreads) fuse_backward_kernel(
+__global__ void __launch_bounds__(kFuseThreads, bwd_min_blocks<CPL, HPL>()) fuse_backward_kernel(
     const uint32_t *__restrict__ pairs, int64_t m, const int32_t *__restrict__ sw, const int32_t *__restrict__ self_sc,
     const uint64_t *__restrict__ packed, const float *__restrict__ emb, int d, const float *__restrict__ params,
     int hidden, const float *__restrict__ dL, float4 *__restrict__ coef, double *__restrict__ partials)
@@ -385,18 +395,30 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partials, int 
     }
 }
 
+// One half-warp per sequence v: its pairs (through the pair index, in index
+// order) are taken sixteen at a time -- each lane loads one entry's pair id,
+// pair and coefficients, so the dependent loads of sixteen pairs overlap --
+// and the partners' rows up to four at a time, then accumulated in index order, so
+// the sums are those of a sequential walk over the pairs (bitwise).  A
+// sequence in a bucket of 2,000 members has thousands of pairs; walking them
+// one dependent chain at a time made it the kernel's tail.
 template <int CPL>
 __global__ void __launch_bounds__(kFuseThreads) emb_grad_kernel(
     const uint32_t *__restrict__ pairs, const float4 *__restrict__ coef, const float *__restrict__ emb, int64_t n, int d,
     const uint32_t *__restrict__ perm_i, const uint32_t *__restrict__ off_i, const uint32_t *__restrict__ perm_j,
-    const uint32_t *__restrict__ off_j, float *__restrict__ grad_emb)
+    const uint32_t *__restrict__ off_j, float *__restrict__ grad_emb, uint32_t heavy_min)
 {
+    constexpr int kRows = CPL <= 2 ? 4 : CPL <= 4 ? 2 : 1;  // partner rows in flight per step
     const int sub = threadIdx.x & (kTpp - 1);
+    const unsigned hmask = 0xffffu << (threadIdx.x & 16);  // this half-warp's lanes
     const int d4 = d >> 2;
     const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kTpp;
     const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / kTpp;
     const uint2 *pr = reinterpret_cast<const uint2 *>(pairs);
-    for (int64_t v = grp; v < n; v += ngrp) {
+    const float4 *e4 = reinterpret_cast<const float4 *>(emb);
+    for (int64_t v = grp; v < n; v += ngrp) {  // uniform per half-warp
+        // sequences of more than heavy_min pairs are left to emb_grad_heavy_kernel
+        if ((__ldg(off_i + v + 1) - __ldg(off_i + v)) + (__ldg(off_j + v + 1) - __ldg(off_j + v)) > heavy_min) continue;
         float4 acc[CPL];
 #pragma unroll
         for (int c = 0; c < CPL; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -405,27 +427,50 @@ __global__ void __launch_bounds__(kFuseThreads) emb_grad_kernel(
             const uint32_t *perm = side == 0 ? perm_i : perm_j;
             const uint32_t *off = side == 0 ? off_i : off_j;
             const uint32_t q0 = __ldg(off + v), q1 = __ldg(off + v + 1);
-            for (uint32_t q = q0; q < q1; ++q) {
-                const uint32_t p = __ldg(perm + q);
-                const uint2 ij = __ldg(pr + p);
-                const float4 cf = __ldg(coef + p);
-                const uint32_t other = side == 0 ? ij.y : ij.x;
-                beta += side == 0 ? cf.y : cf.z;
-                const float4 *eo = reinterpret_cast<const float4 *>(emb + (int64_t)other * d);
+            for (uint32_t qb = q0; qb < q1; qb += kTpp) {
+                const int cnt = (int)min((uint32_t)kTpp, q1 - qb);
+                uint32_t other = 0;
+                float cfx = 0.f, cfb = 0.f;
+                if (sub < cnt) {
+                    const uint32_t p = __ldg(perm + qb + sub);
+                    const uint2 ij = __ldg(pr + p);
+                    const float4 cf = __ldg(coef + p);
+                    other = side == 0 ? ij.y : ij.x;
+                    cfx = cf.x;
+                    cfb = side == 0 ? cf.y : cf.z;
+                }
+                for (int t0 = 0; t0 < cnt; t0 += kRows) {
+                    float4 row[kRows][CPL];
+                    float cx[kRows], cb[kRows];
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) {
-                    const int k = sub + c * kTpp;
-                    if (k < d4) {
-                        const float4 e = __ldg(eo + k);
-                        acc[c].x = fmaf(cf.x, e.x, acc[c].x);
-                        acc[c].y = fmaf(cf.x, e.y, acc[c].y);
-                        acc[c].z = fmaf(cf.x, e.z, acc[c].z);
-                        acc[c].w = fmaf(cf.x, e.w, acc[c].w);
+                    for (int u = 0; u < kRows; ++u) {
+                        const int t = t0 + u;
+                        const uint32_t o = __shfl_sync(hmask, other, t & (kTpp - 1), kTpp);
+                        cx[u] = __shfl_sync(hmask, cfx, t & (kTpp - 1), kTpp);
+                        cb[u] = __shfl_sync(hmask, cfb, t & (kTpp - 1), kTpp);
+                        const float4 *eo = e4 + (int64_t)o * d4;
+#pragma unroll
+                        for (int c = 0; c < CPL; ++c) {
+                            const int k = sub + c * kTpp;
+                            row[u][c] = t < cnt && k < d4 ? __ldg(eo + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kRows; ++u) {
+                        if (t0 + u >= cnt) break;
+                        beta += cb[u];
+#pragma unroll
+                        for (int c = 0; c < CPL; ++c) {
+                            acc[c].x = fmaf(cx[u], row[u][c].x, acc[c].x);
+                            acc[c].y = fmaf(cx[u], row[u][c].y, acc[c].y);
+                            acc[c].z = fmaf(cx[u], row[u][c].z, acc[c].z);
+                            acc[c].w = fmaf(cx[u], row[u][c].w, acc[c].w);
+                        }
                     }
                 }
             }
         }
-        const float4 *ev = reinterpret_cast<const float4 *>(emb + v * d);
+        const float4 *ev = e4 + v * d4;
         float4 *gv = reinterpret_cast<float4 *>(grad_emb + v * d);
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -437,6 +482,157 @@ __global__ void __launch_bounds__(kFuseThreads) emb_grad_kernel(
             }
         }
     }
+}
+
+// Sequences with more than heavy_min pairs, listed (in any order: each is
+// computed on its own).
+__global__ void heavy_list_kernel(const uint32_t *__restrict__ off_i, const uint32_t *__restrict__ off_j, int64_t n,
+                                  uint32_t heavy_min, uint32_t *__restrict__ list, uint32_t *__restrict__ count)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if ((off_i[v + 1] - off_i[v]) + (off_j[v + 1] - off_j[v]) > heavy_min) list[atomicAdd(count, 1u)] = (uint32_t)v;
+}
+
+// One block per listed sequence: its D pairs (first-member side, then
+// second-member side, each in index order) are cut into 16 consecutive
+// parts, one per half-warp, each walked as in emb_grad_kernel; the 16 partial
+// rows are summed in part order in shared memory, so the result is fixed by
+// D alone.  Rows of at most 256 floats.
+template <int CPL>
+__global__ void __launch_bounds__(kFuseThreads) emb_grad_heavy_kernel(
+    const uint32_t *__restrict__ pairs, const float4 *__restrict__ coef, const float *__restrict__ emb, int d,
+    const uint32_t *__restrict__ perm_i, const uint32_t *__restrict__ off_i, const uint32_t *__restrict__ perm_j,
+    const uint32_t *__restrict__ off_j, const uint32_t *__restrict__ list, const uint32_t *__restrict__ d_count,
+    float *__restrict__ grad_emb)
+{
+    constexpr int kHalves = kFuseThreads / kTpp;
+    constexpr int kRows = CPL <= 2 ? 4 : CPL <= 4 ? 2 : 1;
+    extern __shared__ float s_part[];  // [kHalves][d + 1]: partial row, then partial beta
+    const int half = threadIdx.x / kTpp, sub = threadIdx.x & (kTpp - 1);
+    const unsigned hmask = 0xffffu << (threadIdx.x & 16);
+    const int d4 = d >> 2;
+    const uint2 *pr = reinterpret_cast<const uint2 *>(pairs);
+    const float4 *e4 = reinterpret_cast<const float4 *>(emb);
+    const uint32_t count = *d_count;
+    for (uint32_t e = blockIdx.x; e < count; e += gridDim.x) {
+        const uint32_t v = list[e];
+        const uint32_t a0 = __ldg(off_i + v), b0 = __ldg(off_j + v);
+        const uint32_t Di = __ldg(off_i + v + 1) - a0, D = Di + (__ldg(off_j + v + 1) - b0);
+        const uint32_t t0 = (uint32_t)((uint64_t)D * half / kHalves);
+        const uint32_t t1 = (uint32_t)((uint64_t)D * (half + 1) / kHalves);
+        float4 acc[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float beta = 0.f;
+        for (uint32_t tb = t0; tb < t1; tb += kTpp) {  // uniform per half-warp
+            const int cnt = (int)min((uint32_t)kTpp, t1 - tb);
+            uint32_t other = 0;
+            float cfx = 0.f, cfb = 0.f;
+            if (sub < cnt) {
+                const uint32_t t = tb + sub;
+                const bool first = t < Di;
+                const uint32_t p = first ? __ldg(perm_i + a0 + t) : __ldg(perm_j + b0 + (t - Di));
+                const uint2 ij = __ldg(pr + p);
+                const float4 cf = __ldg(coef + p);
+                other = first ? ij.y : ij.x;
+                cfx = cf.x;
+                cfb = first ? cf.y : cf.z;
+            }
+            for (int u0 = 0; u0 < cnt; u0 += kRows) {
+                float4 row[kRows][CPL];
+                float cx[kRows], cb[kRows];
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    const int t = u0 + u;
+                    const uint32_t o = __shfl_sync(hmask, other, t & (kTpp - 1), kTpp);
+                    cx[u] = __shfl_sync(hmask, cfx, t & (kTpp - 1), kTpp);
+                    cb[u] = __shfl_sync(hmask, cfb, t & (kTpp - 1), kTpp);
+                    const float4 *eo = e4 + (int64_t)o * d4;
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) {
+                        const int k = sub + c * kTpp;
+                        row[u][c] = t < cnt && k < d4 ? __ldg(eo + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    if (u0 + u >= cnt) break;
+                    beta += cb[u];
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) {
+                        acc[c].x = fmaf(cx[u], row[u][c].x, acc[c].x);
+                        acc[c].y = fmaf(cx[u], row[u][c].y, acc[c].y);
+                        acc[c].z = fmaf(cx[u], row[u][c].z, acc[c].z);
+                        acc[c].w = fmaf(cx[u], row[u][c].w, acc[c].w);
+                    }
+                }
+            }
+        }
+        float *mine = s_part + half * (d + 1);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int k = sub + c * kTpp;
+            if (k < d4) {
+                mine[4 * k] = acc[c].x;
+                mine[4 * k + 1] = acc[c].y;
+                mine[4 * k + 2] = acc[c].z;
+                mine[4 * k + 3] = acc[c].w;
+            }
+        }
+        if (sub == 0) mine[d] = beta;
+        __syncthreads();
+        for (int f = threadIdx.x; f < d; f += blockDim.x) {
+            float a = 0.f, bsum = 0.f;
+            for (int h = 0; h < kHalves; ++h) {
+                a += s_part[h * (d + 1) + f];
+                bsum += s_part[h * (d + 1) + d];
+            }
+            grad_emb[(int64_t)v * d + f] = fmaf(bsum, __ldg(emb + (int64_t)v * d + f), a);
+        }
+        __syncthreads();  // s_part is rewritten for the next sequence
+    }
+}
+
+// Embedding gradient through the pair index: sequences of at most
+// kHeavyPairs pairs by one half-warp each (emb_grad_kernel), longer ones by a
+// block each (emb_grad_heavy_kernel, rows of at most 256 floats); list and
+// count in the caller's scratch.
+constexpr uint32_t kHeavyPairs = 128;
+
+int launch_emb_grad(subquad_ctx *ctx, const uint32_t *pairs, const float4 *coef, const float *emb, int64_t n, int d,
+                    const uint32_t *perm_i, const uint32_t *off_i, const uint32_t *perm_j, const uint32_t *off_j,
+                    float *grad_emb, uint32_t *heavy_list, uint32_t *heavy_count)
+{
+    const int cpl = (d / 4 + kTpp - 1) / kTpp;
+    const bool heavy = d <= 4 * 4 * kTpp;
+    const uint32_t heavy_min = heavy ? kHeavyPairs : 0xffffffffu;
+    const unsigned g2 = sq_grid(ctx, n * kTpp, kFuseThreads, 8);
+#define SQ_EMB(C)                                                                                                  \
+    emb_grad_kernel<C><<<g2, kFuseThreads, 0, ctx->stream>>>(pairs, coef, emb, n, d, perm_i, off_i, perm_j, off_j,  \
+                                                            grad_emb, heavy_min)
+    if (cpl <= 1) SQ_EMB(1);
+    else if (cpl <= 2) SQ_EMB(2);
+    else if (cpl <= 4) SQ_EMB(4);
+    else if (cpl <= 8) SQ_EMB(8);
+    else SQ_EMB(16);
+#undef SQ_EMB
+    SQ_LAUNCH_CHECK();
+    if (!heavy) return SUBQUAD_OK;
+    SQ_TRY_CUDA(cudaMemsetAsync(heavy_count, 0, sizeof(uint32_t), ctx->stream));
+    heavy_list_kernel<<<sq_grid(ctx, n, 256, 8), 256, 0, ctx->stream>>>(off_i, off_j, n, heavy_min, heavy_list,
+                                                                          heavy_count);
+    SQ_LAUNCH_CHECK();
+    const size_t smem = sizeof(float) * (kFuseThreads / kTpp) * (size_t)(d + 1);
+    const unsigned g3 = (unsigned)ctx->num_sms * 4;
+#define SQ_EMBH(C)                                                                                                 \
+    emb_grad_heavy_kernel<C><<<g3, kFuseThreads, smem, ctx->stream>>>(pairs, coef, emb, d, perm_i, off_i, perm_j,   \
+                                                                     off_j, heavy_list, heavy_count, grad_emb)
+    if (cpl <= 1) SQ_EMBH(1);
+    else if (cpl <= 2) SQ_EMBH(2);
+    else SQ_EMBH(4);
+#undef SQ_EMBH
+    SQ_LAUNCH_CHECK();
+    return SUBQUAD_OK;
 }
 
 template <int WORDS, int CPL>
@@ -525,11 +721,16 @@ extern "C" int subquad_fuse_backward(subquad_ctx *ctx, const uint32_t *pairs, in
     const unsigned grid = (unsigned)ctx->num_sms * 4;
     SqArena measure(nullptr);
     measure.take<double>((size_t)grid * P);
-    if (grad_emb) measure.take<float4>((size_t)m);
+    if (grad_emb) {
+        measure.take<float4>((size_t)m);
+        measure.take<uint32_t>((size_t)n + 1);
+    }
     SQ_TRY(sq_scratch_reserve(ctx, measure.off));
     SqArena arena(ctx->scratch);
     double *partials = arena.take<double>((size_t)grid * P);
     float4 *coef = grad_emb ? arena.take<float4>((size_t)m) : nullptr;
+    uint32_t *heavy_list = grad_emb ? arena.take<uint32_t>((size_t)n + 1) : nullptr;
+    uint32_t *heavy_count = heavy_list ? heavy_list + n : nullptr;
     if (pack_stride == 16)
         SQ_TRY(launch_backward<2>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, gate_params, hidden, dL_dfused,
                                   coef, partials));
@@ -538,20 +739,9 @@ extern "C" int subquad_fuse_backward(subquad_ctx *ctx, const uint32_t *pairs, in
                                   coef, partials));
     reduce_partials_kernel<<<1, 352, 0, ctx->stream>>>(partials, (int)grid, P, grad_params);
     SQ_LAUNCH_CHECK();
-    if (grad_emb && n > 0) {
-        const int cpl = (d / 4 + kTpp - 1) / kTpp;
-        const unsigned g2 = sq_grid(ctx, n * kTpp, kFuseThreads, 8);
-#define SQ_EMB(C)                                                                                                  \
-    emb_grad_kernel<C><<<g2, kFuseThreads, 0, ctx->stream>>>(pairs, coef, emb, n, d, perm_i, off_i, perm_j, off_j,  \
-                                                            grad_emb)
-        if (cpl <= 1) SQ_EMB(1);
-        else if (cpl <= 2) SQ_EMB(2);
-        else if (cpl <= 4) SQ_EMB(4);
-        else if (cpl <= 8) SQ_EMB(8);
-        else SQ_EMB(16);
-#undef SQ_EMB
-        SQ_LAUNCH_CHECK();
-    }
+    if (grad_emb && n > 0)
+        SQ_TRY(launch_emb_grad(ctx, pairs, coef, emb, n, d, perm_i, off_i, perm_j, off_j, grad_emb, heavy_list,
+                               heavy_count));
     return SUBQUAD_OK;
 }
 
@@ -1094,11 +1284,16 @@ extern "C" int subquad_fuse_backward_mc(subquad_ctx *ctx, const uint32_t *pairs,
     const unsigned grid = (unsigned)ctx->num_sms * 4;  // fixed: the reduction order does not depend on m
     SqArena measure(nullptr);
     measure.take<double>((size_t)grid * P);
-    if (grad_emb) measure.take<float4>((size_t)m);
+    if (grad_emb) {
+        measure.take<float4>((size_t)m);
+        measure.take<uint32_t>((size_t)n + 1);
+    }
     SQ_TRY(sq_scratch_reserve(ctx, measure.off));
     SqArena arena(ctx->scratch);
     double *partials = arena.take<double>((size_t)grid * P);
     float4 *coef = grad_emb ? arena.take<float4>((size_t)m) : nullptr;
+    uint32_t *heavy_list = grad_emb ? arena.take<uint32_t>((size_t)n + 1) : nullptr;
+    uint32_t *heavy_count = heavy_list ? heavy_list + n : nullptr;
 #define SQ_MCB(MM, W)                                                                                              \
     SQ_TRY((launch_backward_mc<MM, W>(ctx, grid, pairs, m, sw, self_scores, packed, emb, d, sig_seq, hashes,       \
                                       gate_params, hidden, dL_dfused, coef, partials)))
@@ -1112,20 +1307,9 @@ extern "C" int subquad_fuse_backward_mc(subquad_ctx *ctx, const uint32_t *pairs,
 #undef SQ_MCB
     reduce_partials_kernel<<<1, 352, 0, ctx->stream>>>(partials, (int)grid, P, grad_params);
     SQ_LAUNCH_CHECK();
-    if (grad_emb && n > 0) {
-        const int cpl = (d / 4 + kTpp - 1) / kTpp;
-        const unsigned g2 = sq_grid(ctx, n * kTpp, kFuseThreads, 8);
-#define SQ_EMB(C)                                                                                                  \
-    emb_grad_kernel<C><<<g2, kFuseThreads, 0, ctx->stream>>>(pairs, coef, emb, n, d, perm_i, off_i, perm_j, off_j,  \
-                                                            grad_emb)
-        if (cpl <= 1) SQ_EMB(1);
-        else if (cpl <= 2) SQ_EMB(2);
-        else if (cpl <= 4) SQ_EMB(4);
-        else if (cpl <= 8) SQ_EMB(8);
-        else SQ_EMB(16);
-#undef SQ_EMB
-        SQ_LAUNCH_CHECK();
-    }
+    if (grad_emb && n > 0)
+        SQ_TRY(launch_emb_grad(ctx, pairs, coef, emb, n, d, perm_i, off_i, perm_j, off_j, grad_emb, heavy_list,
+                               heavy_count));
     return SUBQUAD_OK;
 }
 

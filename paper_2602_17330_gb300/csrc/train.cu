@@ -61,7 +61,11 @@ __global__ void group_weight_kernel(const int32_t *__restrict__ group, int64_t m
     }
 }
 
-// Per block: FP64 partial sums of w and w * l in a fixed order.
+// Per block: FP64 partial sums of w and w * l in a fixed order.  The label
+// is 0 or 1, so each pair's loss is one logarithm, -log(q) or -log(1 - q),
+// taken in FP32 (one or two ulps of a term, far inside the loss tolerance;
+// the FP64 logarithm issues on the slow FP64 pipe); the clamp and the sums
+// stay in FP64.
 __global__ void __launch_bounds__(kThreads) bce_partial_kernel(const float *__restrict__ fused,
                                                                const uint8_t *__restrict__ label,
                                                                const float *__restrict__ weight, int64_t m,
@@ -70,12 +74,12 @@ __global__ void __launch_bounds__(kThreads) bce_partial_kernel(const float *__re
     __shared__ double s_w[kThreads], s_l[kThreads];
     double sw = 0.0, sl = 0.0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
-        const double w = weight[p];
+        const float w = weight[p];
         double q = fused[p];
         q = q < kClamp ? kClamp : (q > 1.0 - kClamp ? 1.0 - kClamp : q);
-        const double y = label[p];
-        sw += w;
-        sl += w * -(y * log(q) + (1.0 - y) * log(1.0 - q));
+        const float arg = label[p] ? (float)q : (float)(1.0 - q);
+        sw += (double)w;
+        sl += (double)w * (double)(-logf(arg));
     }
     s_w[threadIdx.x] = sw;
     s_l[threadIdx.x] = sl;
@@ -110,12 +114,15 @@ __global__ void bce_grad_kernel(const float *__restrict__ fused, const uint8_t *
                                 const float *__restrict__ weight, int64_t m, const double *__restrict__ wsum,
                                 float *__restrict__ dL)
 {
-    const double inv = *wsum > 0.0 ? 1.0 / *wsum : 0.0;
+    // the clamp test in FP64 (as the loss), the adjoint w (q - y) / (q (1 - q)) / sum(w)
+    // in FP32: q - y is exact for y in {0, 1} and q in [1/2, 1] or y = 0, the
+    // rest a few roundings, far inside the gradient tolerance
+    const float inv = *wsum > 0.0 ? (float)(1.0 / *wsum) : 0.f;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
-        const double q = fused[p];
-        const bool inside = q > kClamp && q < 1.0 - kClamp;
-        const double y = label[p];
-        dL[p] = inside ? (float)((double)weight[p] * (q - y) / (q * (1.0 - q)) * inv) : 0.f;
+        const float q = fused[p];
+        const bool inside = (double)q > kClamp && (double)q < 1.0 - kClamp;
+        const float y = label[p] ? 1.f : 0.f;
+        dL[p] = inside ? weight[p] * (q - y) / (q * (1.f - q)) * inv : 0.f;
     }
 }
 

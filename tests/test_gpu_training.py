@@ -150,6 +150,43 @@ def test_backward_of_weighted_bce_matches_oracle(ctx, torch, oracle_mod, case):
     check_backward(ctx, torch, oracle_mod, case, dL, "weighted-BCE dL")
 
 
+@pytest.mark.parametrize("d", [128, 64, 256, 260])
+def test_backward_with_heavy_sequences(ctx, torch, oracle_mod, case, d):
+    """Sequences in thousands of pairs (as the members of a bucket of 2,000
+    are) take the embedding gradient's block-per-sequence path (rows up to 256
+    floats; d = 260 stays on the half-warp path): first members with 1,500 and
+    400 partners, a second member with 900, beside ordinary pairs."""
+    rep = case["rep"]
+    rng = np.random.default_rng(d)
+    n = rep.n
+    parts = [case["pairs_np"][:20_000].astype(np.int64)]
+    for head, deg in ((5, 1500), (777, 400)):
+        parts.append(np.stack([np.full(deg, head), rng.choice(np.arange(head + 1, n), deg, replace=False)], 1))
+    tail = n - 10
+    parts.append(np.stack([rng.choice(np.arange(tail), 900, replace=False), np.full(900, tail)], 1))
+    pairs_np = np.unique(np.concatenate(parts), axis=0)
+    pairs_np = pairs_np[pairs_np[:, 0] < pairs_np[:, 1]].astype(np.uint32)
+    sw_np = oracle_mod.sw_pairs(rep.codes, rep.lens, pairs_np)
+    emb = np.ascontiguousarray(synth.family_embeddings(rep.family, d, seed=d) *
+                               rng.uniform(0.5, 2.0, (n, 1)).astype(np.float32))
+    m = pairs_np.shape[0]
+    dL = (rng.standard_normal(m) / m).astype(np.float32)
+    dev = ctx.device
+    args_t = (torch.from_numpy(pairs_np.view(np.int32)).to(dev), torch.from_numpy(sw_np).to(dev), case["self"],
+              case["packed"], torch.from_numpy(emb).to(dev), case["params_t"], case["hidden"],
+              torch.from_numpy(dL).to(dev))
+    gp, ge = ctx.fuse_backward(*args_t)
+    gp2, ge2 = ctx.fuse_backward(*args_t)
+    assert torch.equal(gp, gp2) and torch.equal(ge, ge2), "backward is not bitwise reproducible"
+    args = (pairs_np, sw_np, case["self_np"], rep.lens, emb, case["params"], case["hidden"], dL.astype(np.float64))
+    want_p, want_e = oracle_mod.fuse_backward(*args)
+    scale_p, scale_e = oracle_mod.fuse_backward_scale(*args)
+    ok, worst = grads_close(to_np(gp), want_p, scale_p, f"heavy sequences d={d}, parameters")
+    assert ok, f"parameter gradient worst error / bound = {worst:.3f}"
+    ok, worst = grads_close(to_np(ge), want_e, scale_e, f"heavy sequences d={d}, embeddings")
+    assert ok, f"embedding gradient worst error / bound = {worst:.3f}"
+
+
 def test_backward_without_embedding_gradient(ctx, torch, oracle_mod, case):
     m = case["pairs_np"].shape[0]
     dL = torch.full((m,), 1.0 / m, dtype=torch.float32, device=ctx.device)
