@@ -210,19 +210,29 @@ def test_pair_index(ctx, torch, case):
         assert (off == want_off).all()
 
 
-def test_adam_against_oracle(ctx, torch, oracle_mod):
+@pytest.mark.parametrize("P", [1000, 1003, 3])
+def test_adam_against_oracle(ctx, torch, oracle_mod, P):
+    """Four elements per thread on 16-byte aligned buffers, a scalar tail;
+    buffers one element off alignment take the scalar kernel throughout and
+    must give the same bits."""
     rng = np.random.default_rng(4)
-    P = 1000
     p0 = rng.standard_normal(P).astype(np.float32)
     p_t = torch.from_numpy(p0.copy()).cuda()
     m1 = torch.zeros_like(p_t)
     m2 = torch.zeros_like(p_t)
+    # the same state one element into a larger buffer (4-byte aligned only)
+    big = torch.zeros((4, P + 1), dtype=torch.float32, device="cuda")
+    big[0, 1:] = p_t
+    pu, m1u, m2u, gu = big[0, 1:], big[1, 1:], big[2, 1:], big[3, 1:]
     pw, a1, a2 = p0.astype(np.float64), np.zeros(P), np.zeros(P)
     for t in range(1, 31):
         g = rng.standard_normal(P).astype(np.float32)
         ctx.adam_step(p_t, torch.from_numpy(g).cuda(), m1, m2, t, lr=1e-2)
+        gu.copy_(torch.from_numpy(g))
+        ctx.adam_step(pu, gu, m1u, m2u, t, lr=1e-2)
         oracle_mod.adam_step(pw, g.astype(np.float64), a1, a2, t, lr=1e-2)
     assert np.allclose(to_np(p_t), pw, rtol=0, atol=2e-5)
+    assert torch.equal(pu, p_t) and torch.equal(m1u, m1) and torch.equal(m2u, m2)
 
 
 def test_training_steps_track_oracle(ctx, torch, oracle_mod, case):
