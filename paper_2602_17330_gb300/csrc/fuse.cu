@@ -1042,10 +1042,13 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_backward_mc_kernel(
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int d4 = d >> 2;
     Kahan gW1[HPL][F], gb1[HPL], gW2[HPL][M - 1], gb2[M - 1];
+    const uint2 *pr = reinterpret_cast<const uint2 *>(pairs);
+    uint2 ij_next = warp * 2 + half < m ? __ldg(pr + warp * 2 + half) : make_uint2(0, 0);  // one iteration ahead
     for (int64_t pbase = warp * 2; pbase < m; pbase += nwarps * 2) {
         const int64_t p = pbase + half;
         const bool valid = p < m;
-        const uint2 ij = valid ? __ldg(reinterpret_cast<const uint2 *>(pairs) + p) : make_uint2(0, 0);
+        const uint2 ij = valid ? ij_next : make_uint2(0, 0);
+        ij_next = p + nwarps * 2 < m ? __ldg(pr + p + nwarps * 2) : make_uint2(0, 0);
         PairInputs<WORDS, CPL> in;
         in.load(ij, p, valid, sub, d4, emb, d, sw, self_sc, packed);
         const float dA = valid ? __ldg(dL + p) : 0.f;
