@@ -613,8 +613,8 @@ int launch_emb_grad(subquad_ctx *ctx, const uint32_t *pairs, const float4 *coef,
     const uint32_t heavy_min = heavy ? kHeavyPairs : 0xffffffffu;
     const unsigned g2 = sq_grid(ctx, n * kTpp, kFuseThreads, 8);
 #define SQ_EMB(C)                                                                                                  \
-    emb_grad_kernel<C><<<g2, kFuseThreads, 0, ctx->stream>>>(pairs, coef, emb, n, d, perm_i, off_i, perm_j, off_j,  \
-                                                            grad_emb, heavy_min)
+    emb_grad_kernel<C><<<sq_resident_grid(ctx, emb_grad_kernel<C>, kFuseThreads, 0, g2), kFuseThreads, 0,          \
+                         ctx->stream>>>(pairs, coef, emb, n, d, perm_i, off_i, perm_j, off_j, grad_emb, heavy_min)
     if (cpl <= 1) SQ_EMB(1);
     else if (cpl <= 2) SQ_EMB(2);
     else if (cpl <= 4) SQ_EMB(4);
@@ -1168,7 +1168,9 @@ int launch_forward_mc(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, in
         // 32-byte lane loads of the rows and signatures (whole lines per pair and load)
         const int cpl8 = (d / 8 + kTppF - 1) / kTppF;
 #define SQ_FWDMC8(C)                                                                                               \
-    fuse_forward_mc_kernel<M, WORDS, C, 2><<<grid, kFuseThreads, 0, ctx->stream>>>(                                \
+    fuse_forward_mc_kernel<M, WORDS, C, 2><<<sq_resident_grid(ctx, fuse_forward_mc_kernel<M, WORDS, C, 2>,          \
+                                                              kFuseThreads, 0, grid),                              \
+                                             kFuseThreads, 0, ctx->stream>>>(                                      \
         pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d, sig, H, params, hidden, fused, weights)
         if (cpl8 <= 1) SQ_FWDMC8(1);
         else if (cpl8 <= 2) SQ_FWDMC8(2);
@@ -1179,7 +1181,9 @@ int launch_forward_mc(subquad_ctx *ctx, unsigned grid, const uint32_t *pairs, in
     }
     const int cpl = (d / 4 + kTppF - 1) / kTppF;
 #define SQ_FWDMC(C)                                                                                                \
-    fuse_forward_mc_kernel<M, WORDS, C><<<grid, kFuseThreads, 0, ctx->stream>>>(                                   \
+    fuse_forward_mc_kernel<M, WORDS, C><<<sq_resident_grid(ctx, fuse_forward_mc_kernel<M, WORDS, C>, kFuseThreads, \
+                                                           0, grid),                                               \
+                                          kFuseThreads, 0, ctx->stream>>>(                                         \
         pairs, m, sw, self_scores, (const uint64_t *)packed, emb, d, sig, H, params, hidden, fused, weights)
     if (cpl <= 1) SQ_FWDMC(1);
     else if (cpl <= 2) SQ_FWDMC(2);

@@ -176,6 +176,22 @@ inline unsigned sq_grid(const subquad_ctx *ctx, int64_t work, int threads, int p
     return (unsigned)(need < cap ? need : cap);
 }
 
+// Blocks for a grid-stride kernel: at most `need`, and at most one wave of
+// the blocks that fit on the device at once (the kernel's occupancy times the
+// SM count), so no partial last wave trails the others.
+template <typename K>
+inline unsigned sq_resident_grid(const subquad_ctx *ctx, K kernel, int threads, size_t smem, int64_t need)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int64_t cap = (int64_t)ctx->num_sms * per_sm;
+    if (need < 1) need = 1;
+    return (unsigned)(need < cap ? need : cap);
+}
+
 // Packed sequence records (see subquad_pack in subquad.h).
 __device__ __forceinline__ int sq_record_len(uint64_t w0, uint64_t w1)
 {
