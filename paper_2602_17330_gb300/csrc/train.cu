@@ -61,28 +61,68 @@ __global__ void group_weight_kernel(const int32_t *__restrict__ group, int64_t m
     }
 }
 
-// Per block: FP64 partial sums of w and w * l in a fixed order.  The label
-// is 0 or 1, so each pair's loss is one logarithm, -log(q) or -log(1 - q),
-// taken in FP32 (one or two ulps of a term, far inside the loss tolerance;
-// the FP64 logarithm issues on the slow FP64 pipe); the clamp and the sums
-// stay in FP64.
+// The clamp of the loss and of its adjoint, for a float fused score q, as
+// float comparisons that decide exactly as the FP64 ones on the widened q:
+// q < c  <=>  q < lo_in, q > 1 - c  <=>  q > hi_in (loss), q > c  <=>  q >
+// lo_out, q < 1 - c  <=>  q < hi_out (adjoint), and the logarithm arguments
+// of the clamped cases as the FP64 clamp rounds them to float.
+struct BceClamp {
+    float lo_in, hi_in, lo_out, hi_out;
+    float arg_lo1, arg_hi1, arg_lo0, arg_hi0;  // label 1 / label 0 at the low / high clamp
+};
+
+BceClamp bce_clamp()
+{
+    auto ceil_f = [](double c) {  // smallest float >= c
+        float f = (float)c;
+        return (double)f < c ? nextafterf(f, INFINITY) : f;
+    };
+    auto floor_f = [](double c) {  // largest float <= c
+        float f = (float)c;
+        return (double)f > c ? nextafterf(f, -INFINITY) : f;
+    };
+    BceClamp k;
+    k.lo_in = ceil_f(kClamp);
+    k.hi_in = floor_f(1.0 - kClamp);
+    k.lo_out = floor_f(kClamp);
+    k.hi_out = ceil_f(1.0 - kClamp);
+    k.arg_lo1 = (float)kClamp;
+    k.arg_hi1 = (float)(1.0 - kClamp);
+    k.arg_lo0 = (float)(1.0 - kClamp);
+    k.arg_hi0 = (float)(1.0 - (1.0 - kClamp));
+    return k;
+}
+
+// Per block: partial sums of w and w * l in a fixed order.  The label is 0
+// or 1, so each pair's loss is one logarithm, -log(q) or -log(1 - q), taken in
+// FP32 (one or two ulps of a term, far inside the loss tolerance); each thread
+// sums its pairs with compensated FP32 additions and the block adds the
+// threads' sums in FP64 (the FP64 pipe is slow on this part).
 __global__ void __launch_bounds__(kThreads) bce_partial_kernel(const float *__restrict__ fused,
                                                                const uint8_t *__restrict__ label,
                                                                const float *__restrict__ weight, int64_t m,
-                                                               double *__restrict__ partials)
+                                                               BceClamp k, double *__restrict__ partials)
 {
     __shared__ double s_w[kThreads], s_l[kThreads];
-    double sw = 0.0, sl = 0.0;
+    float sw = 0.f, cw = 0.f, sl = 0.f, cl = 0.f;  // compensated sums
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
-        const float w = weight[p];
-        double q = fused[p];
-        q = q < kClamp ? kClamp : (q > 1.0 - kClamp ? 1.0 - kClamp : q);
-        const float arg = label[p] ? (float)q : (float)(1.0 - q);
-        sw += (double)w;
-        sl += (double)w * (double)(-logf(arg));
+        const float w = weight[p], q = fused[p];
+        float arg;
+        if (label[p])
+            arg = q < k.lo_in ? k.arg_lo1 : (q > k.hi_in ? k.arg_hi1 : q);
+        else
+            arg = q < k.lo_in ? k.arg_lo0 : (q > k.hi_in ? k.arg_hi0 : 1.f - q);  // 1 - q: one correctly rounded op
+        const float term = w * -logf(arg);
+        float y = w - cw, t = sw + y;
+        cw = (t - sw) - y;
+        sw = t;
+        y = term - cl;
+        t = sl + y;
+        cl = (t - sl) - y;
+        sl = t;
     }
-    s_w[threadIdx.x] = sw;
-    s_l[threadIdx.x] = sl;
+    s_w[threadIdx.x] = (double)sw - (double)cw;
+    s_l[threadIdx.x] = (double)sl - (double)cl;
     __syncthreads();
     for (int stride = kThreads / 2; stride > 0; stride >>= 1) {
         if (threadIdx.x < stride) {
@@ -111,16 +151,17 @@ __global__ void bce_final_kernel(const double *__restrict__ partials, int blocks
 }
 
 __global__ void bce_grad_kernel(const float *__restrict__ fused, const uint8_t *__restrict__ label,
-                                const float *__restrict__ weight, int64_t m, const double *__restrict__ wsum,
-                                float *__restrict__ dL)
+                                const float *__restrict__ weight, int64_t m, BceClamp k,
+                                const double *__restrict__ wsum, float *__restrict__ dL)
 {
-    // the clamp test in FP64 (as the loss), the adjoint w (q - y) / (q (1 - q)) / sum(w)
-    // in FP32: q - y is exact for y in {0, 1} and q in [1/2, 1] or y = 0, the
-    // rest a few roundings, far inside the gradient tolerance
+    // the clamp test as the loss's (exact float thresholds), the adjoint
+    // w (q - y) / (q (1 - q)) / sum(w) in FP32: q - y is exact for y in {0, 1}
+    // and q in [1/2, 1] or y = 0, the rest a few roundings, far inside the
+    // gradient tolerance
     const float inv = *wsum > 0.0 ? (float)(1.0 / *wsum) : 0.f;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
         const float q = fused[p];
-        const bool inside = (double)q > kClamp && (double)q < 1.0 - kClamp;
+        const bool inside = q > k.lo_out && q < k.hi_out;
         const float y = label[p] ? 1.f : 0.f;
         dL[p] = inside ? weight[p] * (q - y) / (q * (1.f - q)) * inv : 0.f;
     }
@@ -234,12 +275,13 @@ extern "C" int subquad_bce_loss(subquad_ctx *ctx, const float *fused, const uint
     SQ_TRY(sq_scratch_reserve(ctx, sizeof(double) * (2 * blocks + 1)));
     double *partials = static_cast<double *>(ctx->scratch);
     double *wsum = partials + 2 * blocks;
-    bce_partial_kernel<<<blocks, kThreads, 0, ctx->stream>>>(fused, label, weight, m, partials);
+    const BceClamp k = bce_clamp();
+    bce_partial_kernel<<<blocks, kThreads, 0, ctx->stream>>>(fused, label, weight, m, k, partials);
     SQ_LAUNCH_CHECK();
     bce_final_kernel<<<1, 32, 0, ctx->stream>>>(partials, blocks, loss_out, wsum);
     SQ_LAUNCH_CHECK();
     if (dL_dfused && m > 0) {
-        bce_grad_kernel<<<sq_grid(ctx, m, kThreads), kThreads, 0, ctx->stream>>>(fused, label, weight, m, wsum,
+        bce_grad_kernel<<<sq_grid(ctx, m, kThreads), kThreads, 0, ctx->stream>>>(fused, label, weight, m, k, wsum,
                                                                                  dL_dfused);
         SQ_LAUNCH_CHECK();
     }
