@@ -25,17 +25,28 @@ __global__ void pair_labels_kernel(const uint32_t *__restrict__ pairs, int64_t m
     }
 }
 
+// Per block: a shared-memory histogram of the groups (most pairs fall in a
+// handful of groups, so global atomics per pair serialise on those few
+// counters), then one global atomic per group and block.
 __global__ void group_count_kernel(const int32_t *__restrict__ group, int64_t m, int num_groups,
                                    uint32_t *__restrict__ counts, uint32_t *err)
 {
+    extern __shared__ uint32_t s_hist[];
+    for (int g = threadIdx.x; g < num_groups; g += blockDim.x) s_hist[g] = 0;
+    __syncthreads();
+    bool bad = false;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t g = group[p];
         if (g < 0 || g >= num_groups) {
-            atomicOr(err, SQ_DEVERR_INPUT);
+            bad = true;
             continue;
         }
-        atomicAdd(&counts[g], 1u);
+        atomicAdd(&s_hist[g], 1u);
     }
+    if (bad) atomicOr(err, SQ_DEVERR_INPUT);
+    __syncthreads();
+    for (int g = threadIdx.x; g < num_groups; g += blockDim.x)
+        if (s_hist[g]) atomicAdd(&counts[g], s_hist[g]);
 }
 
 // w_p = (m / count_g) * m / sum_q (m / count_{g(q)}) = m / (count_g * groups_present)
@@ -256,7 +267,8 @@ extern "C" int subquad_pair_weights(subquad_ctx *ctx, const int32_t *group, int6
     uint32_t *counts = static_cast<uint32_t *>(ctx->scratch);
     SQ_TRY_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * num_groups, ctx->stream));
     const unsigned grid = sq_grid(ctx, m, kThreads);
-    group_count_kernel<<<grid, kThreads, 0, ctx->stream>>>(group, m, num_groups, counts, ctx->d_err);
+    group_count_kernel<<<grid, kThreads, sizeof(uint32_t) * num_groups, ctx->stream>>>(group, m, num_groups, counts,
+                                                                                        ctx->d_err);
     SQ_LAUNCH_CHECK();
     group_weight_kernel<<<grid, kThreads, sizeof(uint32_t) * num_groups, ctx->stream>>>(group, m, num_groups, counts,
                                                                                         weight_out);
