@@ -319,9 +319,13 @@ __global__ void __launch_bounds__(kFuseThreads, bwd_min_blocks<CPL, HPL>()) fuse
         sii = group_sum(sii);
         sjj = group_sum(sjj);
         const float prod = (float)in.self_i * (float)in.self_j;
-        const float s = prod > 0.f ? (float)in.sw / sqrtf(prod) : 0.f;
+        // the same approximate reciprocal square roots and quotients as the
+        // forward (a few ulps, far inside the gradient tolerance; the
+        // correctly rounded forms are long instruction sequences in an
+        // instruction-bound kernel)
+        const float s = prod > 0.f ? (float)in.sw * rsqrtf(prod) : 0.f;
         const float nn = sii * sjj;
-        const float c = nn > 0.f ? dot / sqrtf(nn) : 0.f;
+        const float c = nn > 0.f ? dot * rsqrtf(nn) : 0.f;
         const float delta = fabsf((float)(in.len_i - in.len_j));
         float z[HPL];
         float acc = 0.f;
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(kFuseThreads, bwd_min_blocks<CPL, HPL>()) fuse
             }
         }
         const float g = group_sum(acc) + b2;
-        const float a = 1.f / (1.f + expf(-g));
+        const float a = __fdividef(1.f, 1.f + __expf(-g));
         const float d_g = dA * (s - 0.5f * (1.f + c)) * a * (1.f - a);
         float dc = 0.f;
 #pragma unroll
@@ -356,12 +360,11 @@ __global__ void __launch_bounds__(kFuseThreads, bwd_min_blocks<CPL, HPL>()) fuse
         if (sub == 0 && valid) {
             gb2.add(d_g);
             if (coef) {
-                const float ni = sqrtf(sii), nj = sqrtf(sjj);
                 float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (ni > 0.f && nj > 0.f) {
-                    cf.x = dc / (ni * nj);
-                    cf.y = -dc * c / sii;
-                    cf.z = -dc * c / sjj;
+                if (sii > 0.f && sjj > 0.f) {
+                    cf.x = dc * rsqrtf(sii * sjj);
+                    cf.y = __fdividef(-dc * c, sii);
+                    cf.z = __fdividef(-dc * c, sjj);
                 }
                 coef[p] = cf;
             }
@@ -1069,9 +1072,9 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_backward_mc_kernel(
             for (int o = kTpp / 2; o > 0; o >>= 1) agree += __shfl_xor_sync(0xffffffffu, agree, o, kTpp);
         }
         const float prod = (float)in.self_i * (float)in.self_j;
-        const float s = prod > 0.f ? (float)in.sw / sqrtf(prod) : 0.f;
+        const float s = prod > 0.f ? (float)in.sw * rsqrtf(prod) : 0.f;  // as the forward
         const float nn = sii * sjj;
-        const float c = nn > 0.f ? dot / sqrtf(nn) : 0.f;
+        const float c = nn > 0.f ? dot * rsqrtf(nn) : 0.f;
         const float f[4] = {s, c, fabsf((float)(in.len_i - in.len_j)), M == 3 ? (float)agree / (float)H : 0.f};
         float z[HPL];
         float acc0 = 0.f, acc1 = 0.f;
@@ -1092,9 +1095,10 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_backward_mc_kernel(
         const float g1 = group_sum(acc0) + b2[0];
         const float g3 = M == 3 ? group_sum(acc1) + b2[M - 2] : 0.f;
         const float mx = M == 3 ? fmaxf(fmaxf(g1, 0.f), g3) : fmaxf(g1, 0.f);
-        const float e1 = expf(g1 - mx), e2 = expf(-mx), e3 = M == 3 ? expf(g3 - mx) : 0.f;
+        const float e1 = __expf(g1 - mx), e2 = __expf(-mx), e3 = M == 3 ? __expf(g3 - mx) : 0.f;
         const float den = e1 + e2 + e3;
-        const float w1 = e1 / den, w2 = e2 / den, w3 = e3 / den;
+        const float inv_den = __fdividef(1.f, den);
+        const float w1 = e1 * inv_den, w2 = e2 * inv_den, w3 = e3 * inv_den;
         const float cp = 0.5f * (1.f + c);
         const float fused = M == 3 ? w1 * s + w2 * cp + w3 * f[3] : w1 * s + w2 * cp;
         const float d0 = dA * w1 * (s - fused);
@@ -1123,12 +1127,11 @@ __global__ void __launch_bounds__(kFuseThreads) fuse_backward_mc_kernel(
             gb2[0].add(d0);
             if (M == 3) gb2[M - 2].add(d1);
             if (coef) {
-                const float ni = sqrtf(sii), nj = sqrtf(sjj);
                 float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (ni > 0.f && nj > 0.f) {
-                    cf.x = dc / (ni * nj);
-                    cf.y = -dc * c / sii;
-                    cf.z = -dc * c / sjj;
+                if (sii > 0.f && sjj > 0.f) {
+                    cf.x = dc * rsqrtf(sii * sjj);
+                    cf.y = __fdividef(-dc * c, sii);
+                    cf.z = __fdividef(-dc * c, sjj);
                 }
                 coef[p] = cf;
             }
