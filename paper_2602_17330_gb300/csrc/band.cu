@@ -986,7 +986,7 @@ __global__ void __launch_bounds__(256) band_emit_kernel(
 // kRowMid, in place in global memory beyond.
 // Every count stays on the device.
 constexpr int kRowSmall = 32;
-constexpr int kRowWarp = 256;   // rows up to this size: one warp, registers
+constexpr int kRowWarp = 512;   // rows up to this size: one warp, registers
 constexpr int kRowMid = 8192;   // rows up to this size: one CTA, radix sort in shared memory
 constexpr int kRowThreads = 256;
 
