@@ -92,6 +92,33 @@ def test_bce_loss_and_gradient(ctx, torch, oracle_mod, case):
     assert np.allclose(to_np(dL), want_dL, rtol=1e-5, atol=1e-12)
 
 
+def test_bce_clamp_boundaries(ctx, torch, oracle_mod):
+    """Fused scores at and around the loss's clamp points (the float
+    neighbours of 1e-7 and 1 - 1e-7, 0, 1, 1/2) with both labels: the
+    kernels decide the clamp with float thresholds, which must decide every
+    float exactly as the oracle's FP64 comparisons (zero gradients in the same
+    places) and give the loss and the gradient within 1e-5."""
+    vals = []
+    for c in (1e-7, 1.0 - 1e-7):
+        f = np.float32(c)
+        for k in range(-3, 4):
+            v = f
+            for _ in range(abs(k)):
+                v = np.nextafter(v, np.float32(np.inf if k > 0 else -np.inf), dtype=np.float32)
+            vals.append(v)
+    vals += [np.float32(0.0), np.float32(1.0), np.float32(0.5), np.float32(1e-30), np.float32(0.999)]
+    f32 = np.array(vals * 2, dtype=np.float32)
+    y = np.array([0] * len(vals) + [1] * len(vals), dtype=np.uint8)
+    w32 = np.random.default_rng(11).uniform(0.5, 2.0, f32.shape[0]).astype(np.float32)
+    dev = ctx.device
+    loss, dL = ctx.bce_loss(torch.from_numpy(f32).to(dev), torch.from_numpy(y).to(dev), torch.from_numpy(w32).to(dev))
+    want_loss, want_dL = oracle_mod.bce_loss(f32.astype(np.float64), y, w32.astype(np.float64))
+    got = to_np(dL)
+    assert ((got == 0) == (want_dL == 0)).all(), "clamp decided differently"
+    assert abs(float(to_np(loss)[0]) - want_loss) <= 1e-5 * abs(want_loss)
+    assert np.allclose(got, want_dL, rtol=1e-5, atol=0)
+
+
 GRAD_RTOL = 1e-4
 GRAD_KAPPA = 2.0 ** -18
 
