@@ -152,39 +152,90 @@ __global__ void __launch_bounds__(kPartThreads) part_hist_kernel(const uint32_t 
     for (int q = threadIdx.x; q < P; q += blockDim.x) hist[((int64_t)gb * P + q) * ntiles + tile] = s_hist[q];
 }
 
-// Scatter: the tile's slice of every partition starts at the scanned offset;
-// each record takes the next position of its digit (shared-memory atomic), so
-// a partition's records come tile by tile, in any order within a tile.  All
-// positions are taken before any record is stored: the stores then leave as
-// one burst per thread, which keeps the partial-sector writes of neighbouring
-// runs together in L2.
-__global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const uint64_t *__restrict__ fd, int64_t n,
+// Scatter, staged in shared memory: every record takes a rank within its
+// digit (shared-memory atomic), the tile's digit counts are scanned into
+// local run starts, and the records are laid out digit by digit in shared
+// memory (fingerprint, digit and index within the tile in one word); thread t
+// then stores entry t of that layout at its run's scanned global offset.
+// Consecutive threads store consecutive positions of a run, so a run leaves
+// as one burst instead of one scattered 8-byte store per record.  A
+// partition's records come tile by tile, in any order within a tile.
+constexpr size_t part_scatter_smem(int P)
+{
+    return (size_t)kPartTile * sizeof(uint64_t) + 2 * (size_t)P * sizeof(uint32_t);
+}
+static_assert(part_scatter_smem(1 << kPartMaxBits) <= 48 * 1024, "the scatter needs no shared-memory opt-in");
+static_assert(kPartTile <= 4096 && kPartMaxBits <= 20, "index within the tile (12 bits) and digit fit one word");
+
+__global__ void __launch_bounds__(kPartThreads, 4) part_scatter_kernel(const uint64_t *__restrict__ fd, int64_t n,
                                                                     int pbits, int64_t ntiles,
                                                                     const uint32_t *__restrict__ offs,
                                                                     uint64_t *__restrict__ recs)
 {
-    extern __shared__ uint32_t s_pos[];  // [P]
+    extern __shared__ uint64_t s_stage[];  // [kPartTile] entries | [P] run starts | [P] global offsets
+    uint32_t *s_run = reinterpret_cast<uint32_t *>(s_stage + kPartTile);
     const int P = 1 << pbits, gb = blockIdx.y;
+    uint32_t *s_goff = s_run + P;
+    __shared__ uint32_t s_warp[kPartThreads / 32];
     const int64_t tile = blockIdx.x;
-    for (int q = threadIdx.x; q < P; q += blockDim.x) s_pos[q] = offs[((int64_t)gb * P + q) * ntiles + tile];
-    const uint64_t *band_fd = fd + (int64_t)gb * n;
+    const int64_t t0 = tile * kPartTile;
+    const int cnt = n - t0 < kPartTile ? (int)(n - t0) : kPartTile;
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+        s_run[q] = 0;
+        s_goff[q] = offs[((int64_t)gb * P + q) * ntiles + tile];
+    }
+    const uint64_t *band_fd = fd + (int64_t)gb * n + t0;
     uint64_t v[kPartItems];
-    uint32_t pos[kPartItems];
+    uint32_t rank[kPartItems];
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
-        const int64_t i = tile * kPartTile + r * kPartThreads + threadIdx.x;
-        v[r] = i < n ? band_fd[i] : ~0ull;
+        const int t = r * kPartThreads + threadIdx.x;
+        v[r] = t < cnt ? band_fd[t] : 0ull;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
-        const int64_t i = tile * kPartTile + r * kPartThreads + threadIdx.x;
-        pos[r] = i < n ? atomicAdd(&s_pos[(uint32_t)(v[r] >> 32)], 1u) : 0u;
+        const int t = r * kPartThreads + threadIdx.x;
+        rank[r] = t < cnt ? atomicAdd(&s_run[(uint32_t)(v[r] >> 32)], 1u) : 0u;
     }
+    __syncthreads();
+    // exclusive scan of the P <= 1024 counts: runs of P / 256 (at least one)
+    // consecutive digits per thread, then across the warps
+    {
+        const int per = (P + kPartThreads - 1) / kPartThreads;
+        const int q0 = threadIdx.x * per;
+        uint32_t own = 0;
+        for (int q = q0; q < q0 + per && q < P; ++q) own += s_run[q];
+        const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        uint32_t inc = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= (uint32_t)o) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (uint32_t w = 0; w < warp; ++w) wbase += s_warp[w];
+        uint32_t run = wbase + inc - own;
+        for (int q = q0; q < q0 + per && q < P; ++q) {
+            const uint32_t c = s_run[q];
+            s_run[q] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < kPartItems; ++r) {
-        const int64_t i = tile * kPartTile + r * kPartThreads + threadIdx.x;
-        if (i < n) recs[pos[r]] = (v[r] << 32) | (uint32_t)i;
+        const int t = r * kPartThreads + threadIdx.x;
+        const uint32_t dg = (uint32_t)(v[r] >> 32);
+        if (t < cnt) s_stage[s_run[dg] + rank[r]] = (v[r] << 32) | ((uint64_t)dg << 12) | (uint32_t)t;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += kPartThreads) {
+        const uint64_t e = s_stage[t];
+        const uint32_t dg = (uint32_t)(e >> 12) & 0xfffffu;
+        recs[s_goff[dg] + (uint32_t)t - s_run[dg]] = (e & 0xffffffff00000000ull) | (uint32_t)(t0 + (e & 0xfffu));
     }
 }
 
@@ -1525,8 +1576,8 @@ int band_index_build(subquad_ctx *ctx, const uint32_t *sig, int rows, int cap, c
                 sig, n, rows, band0, S.pbits, donor, S.ntiles, S.offs, S.fd);
             SQ_LAUNCH_CHECK();
             SQ_TRY(sq_scan_u32(ctx, S.offs, S.offs, hl, nullptr, false, false, nullptr, S.tmp, S.tmp_bytes));
-            part_scatter_kernel<<<grid, kPartThreads, S.P * sizeof(uint32_t), ctx->stream>>>(S.fd, n, S.pbits,
-                                                                                              S.ntiles, S.offs, S.recs);
+            part_scatter_kernel<<<grid, kPartThreads, part_scatter_smem((int)S.P), ctx->stream>>>(
+                S.fd, n, S.pbits, S.ntiles, S.offs, S.recs);
             SQ_LAUNCH_CHECK();
         }
         SqProfScope prof_grp(ctx, SUBQUAD_PROF_BAND_GROUP);

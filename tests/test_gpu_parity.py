@@ -300,6 +300,25 @@ def test_candidates_row_longer_than_shared_memory(ctx, torch, oracle_mod):
     assert got.shape == want.shape and (got == want).all()
 
 
+def test_candidates_rows_of_every_size_to_2049(ctx, torch, oracle_mod):
+    """One bucket of 2,050 members among 4,000 sequences: its members' rows
+    hold 1, 2, ..., 2,049 partners, so the register, warp and CTA row sorts
+    all run and both sides of each of their size boundaries (4/5, 8/9,
+    16/17, 32/33 and 512/513 partners) occur; the second band adds pairs
+    that the first band already owns."""
+    rng = np.random.default_rng(2049)
+    n, bands, rows = 4_000, 2, 3
+    sig = rng.integers(0, 1 << 31, (n, bands * rows)).astype(np.uint32)
+    ids = rng.permutation(n)[:2_050]
+    sig[ids, 0:rows] = rng.integers(0, 1 << 31, rows)
+    sig[ids[:700], rows:] = rng.integers(0, 1 << 31, rows)
+    got = gpu_candidates_from_sig(ctx, torch, sig, bands, rows, 0)
+    want = oracle_mod.candidates(sig, bands, rows, 0)
+    deg = np.bincount(want[:, 0].astype(np.int64), minlength=n)
+    assert set(range(1, 2_050)) <= set(deg.tolist())
+    assert got.shape == want.shape and (got == want).all()
+
+
 @pytest.mark.parametrize("n,nbig,size,cap", [(3_000, 3, 300, 64), (20_000, 40, 500, 64), (20_000, 40, 500, 499)])
 def test_candidates_several_buckets_above_cap(ctx, torch, oracle_mod, n, nbig, size, cap):
     """Several buckets above the cap in one partition: with 900 repeated keys
