@@ -157,14 +157,21 @@ def whole_job(total_ms: float, units: float, world: int, device) -> tuple[float,
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region (every 20 ms)."""
+    """nvidia-smi clock/throttle samples (every 20 ms) kept for the timed
+    region only: the sampler is started and waited for before the region
+    (nvidia-smi takes longer to come up than a short region lasts), every row
+    carries nvidia-smi's timestamp, and stop() keeps the rows between
+    mark_start() and mark_end() (20 ms of slack on either side)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    SLACK_S = 0.02
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, wait_s: float = 3.0):
         self.proc = None
+        self.t0 = self.t1 = None
         self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -172,6 +179,42 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        deadline = time.time() + wait_s
+        while time.time() < deadline and os.path.getsize(self.file.name) == 0 and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text: str):
+        import datetime
+
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    @classmethod
+    def summarise(cls, lines, t0, t1):
+        """Clock summary of the CSV rows stamped within [t0, t1] (plus slack)."""
+        rows = [r.split(",") for r in lines if r.strip()]
+        stamped = t0 is not None and t1 is not None and any(cls._stamp(r[0]) is not None for r in rows)
+        if stamped:
+            rows = [r for r in rows if (ts := cls._stamp(r[0])) is not None
+                    and t0 - cls.SLACK_S <= ts <= t1 + cls.SLACK_S]
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if len(r) > 2 and r[2].strip().replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if len(r) > 3 and r[3].strip().replace(".", "").isdigit()]
+        reasons = sorted({cls.REASONS[k] for r in rows for k in range(4)
+                          if len(r) > 6 + k and "Active" in r[6 + k] and "Not" not in r[6 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "timed_region_only": stamped}
 
     def stop(self):
         if self.proc is None:
@@ -183,17 +226,9 @@ class ClockSampler:
             self.proc.kill()
         self.file.flush()
         self.file.seek(0)
-        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        lines = self.file.read().strip().splitlines()
         os.unlink(self.file.name)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if len(r) > 5 + k and "Active" in r[5 + k]
-                          and "Not" not in r[5 + k]})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        return self.summarise(lines, self.t0, self.t1)
 
 
 # ---------------------------------------------------------------------------
@@ -363,6 +398,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ctx.profile(True)
     ctx.profile_reset()
     sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.mark_start()
     wall0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
@@ -416,6 +453,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             raise RuntimeError("graph replay produced a different |C|")
         graph_ms = [e0.elapsed_time(e1) for e0, e1 in times]
     wall = time.perf_counter() - wall0
+    if sampler:
+        sampler.mark_end()
     clocks = sampler.stop() if sampler else None
 
     # whole job: units over all ranks / max time over ranks
