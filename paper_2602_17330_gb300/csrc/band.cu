@@ -257,7 +257,7 @@ constexpr int kGrpFast = 3072;       // partitions up to this size are grouped w
 constexpr int kGrpFastSurv = 1024;   // ... when at most this many records pass the filter
 constexpr int kGrpFastSlots = 2048;  // their table (load <= 1/2)
 constexpr int kGrpVerify = 160;      // deferred key comparisons held in shared memory (more: compared at once)
-constexpr int kGrpBloomWords = 512;  // 16384-bit filter bitmaps (two), aliased on the table
+constexpr int kGrpBloomWords = 1024;  // 32768-bit filter bitmaps (two), aliased on the table
 constexpr uint32_t kFastEmpty = 0xffffffffu;
 constexpr uint16_t kNoSlot = 0xffffu;
 // fast-path layout: tab u32[2048] | cnt u32[2048] | rec u64[3072] | slot u16[3072] | surv u16[3072] |
@@ -268,7 +268,7 @@ constexpr size_t kGrpFastSmem = (size_t)kGrpFastSlots * 8 + (size_t)kGrpFast * 8
 constexpr size_t kGrpExactSmem = (size_t)kGrpSlots * (sizeof(unsigned long long) + sizeof(uint32_t));
 constexpr size_t kGrpSmem = kGrpFastSmem > kGrpExactSmem ? kGrpFastSmem : kGrpExactSmem;
 static_assert(kGrpFastSurv * 2 <= kGrpFastSlots, "a fast-path table is never more than half full");
-static_assert(2 * kGrpBloomWords <= 2 * kGrpFastSlots, "the filter bitmaps fit in the table");
+static_assert(2 * kGrpBloomWords <= kGrpFastSlots, "the two filter bitmaps fit in the table's words");
 static_assert(kGrpFast <= 4096, "record indices fit the 12 low bits of a fast-path table entry");
 static_assert(kGrpFastSmem <= 56 * 1024, "four fast-path CTAs share an SM");
 static_assert(kGrpFast <= 4096, "record indices fit the 12 low bits of a fast-path table entry");
