@@ -1,7 +1,7 @@
 // Device-wide scan (banding, binning) and stable LSD radix sort (pair index of
 // the gate training).
 //
-// Scan: reduce-then-scan over at most two chunks per SM, each chunk scanned
+// Scan: reduce-then-scan over at most eight chunks per SM, each chunk scanned
 // in tiles of 4096 elements (256 threads x 16).  Radix sort: 8-bit digits; per pass
 // a digit histogram per tile (warp-aggregated shared-memory counts), a scan of
 // the digit-major histogram, and a stable scatter in which each warp ranks its
@@ -77,13 +77,25 @@ __device__ __forceinline__ T block_exclusive(T v, T *total)
     return res;
 }
 
+// A tile's loads, all issued before any is used: element base + q * 256 + t
+// of thread t (zero at or past count).
 template <typename T>
-__device__ __forceinline__ void load_tile(const T *in, int64_t base, int64_t count, T *s_buf, T items[kScanItems])
+__device__ __forceinline__ void fetch_tile(const T *in, int64_t base, int64_t count, T v[kScanItems])
 {
-    for (int q = threadIdx.x; q < kScanTile; q += kScanThreads) {
-        int64_t g = base + q;
-        s_buf[pad(q)] = g < count ? in[g] : T(0);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        const int64_t g = base + q * kScanThreads + threadIdx.x;
+        v[q] = g < count ? in[g] : T(0);
     }
+}
+
+// Fetched (strided) elements to the blocked order: thread t's items are
+// elements t * 16 .. t * 16 + 15 of the tile.
+template <typename T>
+__device__ __forceinline__ void stage_tile(const T v[kScanItems], T *s_buf, T items[kScanItems])
+{
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) s_buf[pad(q * kScanThreads + threadIdx.x)] = v[q];
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kScanItems; ++q) items[q] = s_buf[pad(threadIdx.x * kScanItems + q)];
@@ -91,10 +103,14 @@ __device__ __forceinline__ void load_tile(const T *in, int64_t base, int64_t cou
 }
 
 // Reduce-then-scan over G contiguous chunks (whole tiles of kScanTile
-// elements; G at most two per SM): one kernel reduces every chunk, a second
-// one gives each chunk its prefix (the reduction of the chunk totals before
-// it) and scans the chunk tile by tile with a running carry.  Two passes over
-// the input, one over the output, and no waiting between CTAs.
+// elements; G at most kScanChunksPerSm per SM, so that small inputs still
+// spread over many CTAs): one kernel reduces every chunk, a second one gives
+// each chunk its prefix (the reduction of the chunk totals before it) and
+// scans the chunk tile by tile with a running carry.  Two passes over the
+// input, one over the output, and no waiting between CTAs.  Both kernels
+// issue a whole tile's loads (16 per thread) before using any of them: the
+// scans are small and latency-bound.
+constexpr int kScanChunksPerSm = 8;
 template <typename T, bool MAX>
 __device__ __forceinline__ T block_reduce(T v, T *s_warp)
 {
@@ -127,14 +143,18 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T *__re
     const int64_t count = eff_count(count_max, d_count);
     int64_t lo, hi;
     scan_chunk(count, blockIdx.x, gridDim.x, lo, hi);
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    int64_t g = lo + threadIdx.x;
-    for (; g + 3 * kScanThreads < hi; g += 4 * kScanThreads) {
+    T acc = T(0);
+    for (int64_t base = lo; base < hi; base += kScanTile) {
+        T v[kScanItems];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = op<T, MAX>(acc[u], in[g + u * kScanThreads]);
+        for (int q = 0; q < kScanItems; ++q) {
+            const int64_t g = base + q * kScanThreads + threadIdx.x;
+            v[q] = g < hi ? in[g] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) acc = op<T, MAX>(acc, v[q]);
     }
-    for (; g < hi; g += kScanThreads) acc[0] = op<T, MAX>(acc[0], in[g]);
-    const T r = block_reduce<T, MAX>(op<T, MAX>(op<T, MAX>(acc[0], acc[1]), op<T, MAX>(acc[2], acc[3])), s_warp);
+    const T r = block_reduce<T, MAX>(acc, s_warp);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
 }
 
@@ -150,13 +170,18 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const T *__res
     const int64_t count = eff_count(count_max, d_count);
     int64_t lo, hi;
     scan_chunk(count, blockIdx.x, gridDim.x, lo, hi);
-    // prefix of this chunk: the chunk totals before it
+    // the first tile's loads in flight while the prefix of this chunk (the
+    // chunk totals before it) is summed; each later tile's while the tile
+    // before it is scanned
+    T v[kScanItems];
+    fetch_tile(in, lo, hi, v);
     T pre = T(0);
     for (int k = threadIdx.x; k < (int)blockIdx.x; k += kScanThreads) pre = op<T, MAX>(pre, partial[k]);
     T carry = block_reduce<T, MAX>(pre, s_warp);
     for (int64_t base = lo; base < hi; base += kScanTile) {
         T items[kScanItems];
-        load_tile(in, base, hi, s_buf, items);
+        stage_tile(v, s_buf, items);
+        if (base + kScanTile < hi) fetch_tile(in, base + kScanTile, hi, v);
         T acc = items[0];
 #pragma unroll
         for (int q = 1; q < kScanItems; ++q) acc = op<T, MAX>(acc, items[q]);
@@ -189,7 +214,7 @@ int scan_impl(subquad_ctx *ctx, const T *in, T *out, int64_t count, const uint32
         return SUBQUAD_OK;
     }
     const int64_t ntiles = (count + kScanTile - 1) / kScanTile;
-    const int64_t G = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 2);
+    const int64_t G = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * kScanChunksPerSm);
     if ((size_t)G * sizeof(T) > tmp_bytes) return SUBQUAD_ERR_ARG;
     T *partial = static_cast<T *>(tmp);
     scan_reduce_kernel<T, MAX><<<(unsigned)G, kScanThreads, 0, ctx->stream>>>(in, count, d_count, partial);
