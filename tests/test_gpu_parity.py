@@ -227,6 +227,27 @@ def test_candidates_split_partitions(ctx, torch, oracle_mod, cap):
         ctx.set_tuning(subquad.TUNE_BAND_PART_LOG2, old)
 
 
+def test_candidates_most_partitions(ctx, torch, oracle_mod):
+    """A partition target of 2^6 keys over 70,000 sequences asks for more than
+    the 1,024 partitions per band the partition pass allows: every band is
+    split into 1,024 partitions of about 68 keys (four digits per thread in
+    the scatter's scan, digits up to 1,023 in its staged words) over 18
+    tiles, the last one ragged."""
+    from paper_2602_17330_gb300 import subquad
+
+    rep = synth.donor_repertoire(70_000, seed=6)
+    a, b = synth.hash_coefficients(64, seed=6)
+    _, sig = gpu_sig(ctx, torch, rep, 3, a, b, 16, 4, 16)
+    want = oracle_mod.candidates(oracle_mod.sign(rep.codes, rep.lens, 3, a, b), 16, 4, 0)
+    old = ctx.get_tuning(subquad.TUNE_BAND_PART_LOG2)
+    try:
+        ctx.set_tuning(subquad.TUNE_BAND_PART_LOG2, 6)
+        got = to_np(ctx.band_candidates(sig, rep.n, 16, 4, 0)).view(np.uint32)
+        assert got.shape == want.shape and (got == want).all()
+    finally:
+        ctx.set_tuning(subquad.TUNE_BAND_PART_LOG2, old)
+
+
 FP_MUL = 0x9E3779B1  # the library's fingerprint multiplier
 
 
