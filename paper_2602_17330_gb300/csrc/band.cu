@@ -271,7 +271,6 @@ static_assert(kGrpFastSurv * 2 <= kGrpFastSlots, "a fast-path table is never mor
 static_assert(2 * kGrpBloomWords <= kGrpFastSlots, "the two filter bitmaps fit in the table's words");
 static_assert(kGrpFast <= 4096, "record indices fit the 12 low bits of a fast-path table entry");
 static_assert(kGrpFastSmem <= 56 * 1024, "four fast-path CTAs share an SM");
-static_assert(kGrpFast <= 4096, "record indices fit the 12 low bits of a fast-path table entry");
 constexpr int kGrpStack = 48;
 constexpr int kGrpMaxLevel = 20;  // sub-ranges select fingerprint bits 12..31
 constexpr uint64_t kGrpEmpty = ~0ull;
