@@ -1403,19 +1403,6 @@ __global__ void __launch_bounds__(kRowThreads) rows_sort_mid_kernel(const uint32
     }
 }
 
-// raw pair count of the group = offset of the last chunk + its pairs
-__global__ void band_total_kernel(const uint64_t *__restrict__ poff, const uint32_t *__restrict__ sizes,
-                                  const uint32_t *__restrict__ d_nchunks, uint64_t *__restrict__ d_total)
-{
-    const uint32_t nc = *d_nchunks;
-    uint64_t total = 0;
-    if (nc > 0) {
-        const uint64_t s = sizes[nc - 1];
-        total = poff[nc - 1] + s * (s - 1) / 2;
-    }
-    *d_total = total;
-}
-
 // One CTA per row of more than kRowMid partners, sorted in place in global
 // memory by a bitonic network whose comparators all put the smaller value at
 // the lower index (a "flip" step, then half-cleaners), so positions past the
@@ -1586,12 +1573,10 @@ int band_index_build(subquad_ctx *ctx, const uint32_t *sig, int rows, int cap, c
         SQ_LAUNCH_CHECK();
     }
     SqProfScope prof_emit(ctx, SUBQUAD_PROF_BAND_EMIT);
-    // pair counts -> offsets.  Only the first nchunks entries are written;
-    // an exclusive prefix at entry c depends on entries < c only, so the
-    // unwritten tail never reaches a used offset.
-    SQ_TRY(sq_scan_u64(ctx, I.poff, I.poff, I.cmax, d_nchunks, nullptr, S.tmp, S.tmp_bytes));
-    band_total_kernel<<<1, 1, 0, ctx->stream>>>(I.poff, I.sizes, d_nchunks, d_total);
-    SQ_LAUNCH_CHECK();
+    // pair counts -> offsets, and their sum (the raw pair count) -> d_total.
+    // The scan reads the first nchunks entries only (the device count), the
+    // ones the grouping wrote.
+    SQ_TRY(sq_scan_u64(ctx, I.poff, I.poff, I.cmax, d_nchunks, d_total, S.tmp, S.tmp_bytes));
     band_warp_chunk_kernel<<<(unsigned)ctx->num_sms * 8, 256, 0, ctx->stream>>>(I.poff, d_nchunks, d_total, I.wchunk,
                                                                                 I.wmax);
     SQ_LAUNCH_CHECK();
