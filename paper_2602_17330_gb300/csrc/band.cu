@@ -1133,12 +1133,25 @@ __global__ void __launch_bounds__(kRowThreads) rows_classify_kernel(const uint32
     }
 }
 
-__global__ void pairs_scatter_kernel(const uint32_t *__restrict__ pairs, const unsigned long long *__restrict__ d_m,
+// The emitter's owned count is also finished here, by the first thread: it
+// is published (with the sticky CAPACITY error when it exceeds the
+// capacity) and clamped to the capacity for the kernels after this one; the
+// scatter itself takes the clamped count directly.
+__global__ void pairs_scatter_kernel(const uint32_t *__restrict__ pairs, const unsigned long long *__restrict__ d_count,
+                                     int64_t capacity, unsigned long long *__restrict__ d_out,
+                                     unsigned long long *__restrict__ d_clamped, uint32_t *err,
                                      const uint32_t *__restrict__ rowoff, uint32_t *__restrict__ fill,
                                      uint32_t *__restrict__ col)
 {
     constexpr int H = 4;  // groups of 32 pairs per warp and iteration, their loads in flight together
-    const int64_t m = (int64_t)*d_m;
+    const unsigned long long c = *d_count;
+    const unsigned long long clamped = c < (unsigned long long)capacity ? c : (unsigned long long)capacity;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (d_out) *d_out = c;
+        if (d_out && c > (unsigned long long)capacity) atomicOr(err, SQ_DEVERR_CAPACITY);
+        *d_clamped = clamped;
+    }
+    const int64_t m = (int64_t)clamped;
     const uint32_t lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1443,18 +1456,6 @@ __global__ void __launch_bounds__(1024) rows_sort_long_kernel(const uint32_t *__
     }
 }
 
-// Finish: publish |C| (asynchronous form: with the sticky CAPACITY bit on an
-// overflow), clamp the count of written pairs used by the sort.
-__global__ void band_finish_kernel(const unsigned long long *__restrict__ d_count, int64_t capacity,
-                                   unsigned long long *__restrict__ d_out, unsigned long long *__restrict__ d_clamped,
-                                   uint32_t *err)
-{
-    const unsigned long long c = *d_count;
-    if (d_out) *d_out = c;
-    if (d_out && c > (unsigned long long)capacity) atomicOr(err, SQ_DEVERR_CAPACITY);
-    *d_clamped = c < (unsigned long long)capacity ? c : (unsigned long long)capacity;
-}
-
 }  // namespace
 
 namespace {
@@ -1625,17 +1626,16 @@ int band_emit_sorted(subquad_ctx *ctx, const BandIndex &I, uint64_t raw0, uint64
             ctx->d_err);
         SQ_LAUNCH_CHECK();
     }
-    // the owned count published, an overflow flagged, the count of written
-    // pairs clamped to the capacity for the sort below
-    band_finish_kernel<<<1, 1, 0, ctx->stream>>>(d_count, capacity, d_publish, d_clamped, ctx->d_err);
-    SQ_LAUNCH_CHECK();
     // lexicographic order: row offsets by first member, the second members
     // scattered into their rows, row class lists, every row sorted
     SqProfScope prof_ps(ctx, SUBQUAD_PROF_BAND_PAIRSORT);
     const unsigned rgrid = sq_grid(ctx, n, kRowThreads, 8);
     SQ_TRY(sq_scan_u32(ctx, E.deg, E.rowoff, n, nullptr, false, false, nullptr, E.tmp, E.tmp_bytes));
-    pairs_scatter_kernel<<<sq_grid(ctx, cap1, 256, 8), 256, 0, ctx->stream>>>(pairs_out, d_clamped, E.rowoff, E.deg,
-                                                                              E.col);
+    // the scatter also publishes the owned count, flags an overflow and
+    // leaves the count of written pairs, clamped to the capacity, for the
+    // sort below
+    pairs_scatter_kernel<<<sq_grid(ctx, cap1, 256, 8), 256, 0, ctx->stream>>>(
+        pairs_out, d_count, capacity, d_publish, d_clamped, ctx->d_err, E.rowoff, E.deg, E.col);
     SQ_LAUNCH_CHECK();
     rows_classify_kernel<<<rgrid, kRowThreads, 0, ctx->stream>>>(E.rowoff, n, d_clamped, E.col, pairs_out, E.sa, E.sb,
                                                                  E.mid, E.lng, d_cls);
